@@ -1,0 +1,312 @@
+#!/usr/bin/env python
+"""Throughput of the Lloyd-preconditioned LBFGS SCVT solver on GB300.
+
+A step is one LBFGS iteration of the whole hot path: the two-loop direction,
+the line search (each trial re-bins the generators, rebuilds every Voronoi
+cell and integrates it) and the accepted-pair update.  The default workload
+is the 2,621,442-generator tanh-cap problem (gamma = (1/8)^4, alpha = 0.10,
+beta = pi/9, x_c at 45N 270E, LBFGS memory 7, FP64) from seeded uniform
+points; the metric is generator-updates/s = N x accepted iterations / s.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun, one process per GPU) every rank solves its own
+independent instance (replicas, weak scaling, no collective on the data
+path); rank 0 prints one JSON line.  ``--impl reference`` times the FP64 CPU
+oracle on the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_1709_06924_gb300 import inputs as I  # noqa: E402
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", default="tanh-2621442", choices=sorted(I.WORKLOADS))
+    p.add_argument("--seed", type=int, default=0)
+    p.add_argument("--cpu-sample-n", type=int, default=163842,
+                   help="generators of the bounded oracle sample (same density)")
+    p.add_argument("--cpu-sample-iters", type=int, default=3)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ----------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.uuid = uuid
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 10:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+
+    def summary(self):
+        rows = [r for r in self.rows if self.uuid is None or self.uuid in r[1]] or self.rows
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[2]) for r in rows if num(r[2]) is not None]
+        mx = [num(r[3]) for r in rows if num(r[3]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[6 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max((num(r[4]) or 0.0) for r in rows)}
+
+
+# ----------------------------------------------------------------- CPU oracle
+def oracle_sample(w: I.Workload, n_sample: int, iters: int, seed: int):
+    """Time the FP64 oracle's own solver on a bounded sample: the same density
+    and solver settings on n_sample seeded generators, `iters` iterations."""
+    import oracle
+    oracle.build()
+    z = I.uniform_sphere(n_sample, seed)
+    t0 = time.perf_counter()
+    _, rep, _ = oracle.lbfgs_solve(z, w.density, lbfgs_m=w.lbfgs_m, max_iter=iters, grad_tol=0.0)
+    t = time.perf_counter() - t0
+    return {"value": n_sample * rep["iters"] / t, "unit": "generator-updates/s", "cores": oracle.max_threads(),
+            "kind": "oracle", "seconds": t, "iters": rep["iters"], "fevals": rep["fevals"],
+            "sample": "%d seeded generators, same density and LBFGS memory, %d oracle iterations "
+                      "(including the initial evaluation)" % (n_sample, rep["iters"])}
+
+
+def run_reference(args, w):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    n = args.cpu_sample_n
+    z = I.uniform_sphere(n, args.seed)
+    if args.warmup > 0:
+        z, _, _ = oracle.lbfgs_solve(z, w.density, lbfgs_m=w.lbfgs_m, max_iter=args.warmup, grad_tol=0.0)
+    t0 = time.perf_counter()
+    _, rep, _ = oracle.lbfgs_solve(z, w.density, lbfgs_m=w.lbfgs_m, max_iter=args.steps, grad_tol=0.0)
+    t = time.perf_counter() - t0
+    value = n * rep["iters"] / t
+    cores = oracle.max_threads()
+    sample = ("%d seeded generators of the %s workload's density and solver settings; %d timed oracle "
+              "iterations after %d warm-up iterations (history restarts at the timed call)"
+              % (n, w.name, rep["iters"], args.warmup))
+    line = {
+        "impl": "reference", "metric": "generator-updates/s", "value": value, "unit": "generator-updates/s",
+        "n_gpus": 0, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / max(rep["iters"], 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "n_generators": w.n, "sample_generators": n, "lbfgs_m": w.lbfgs_m,
+                   "density": "tanh cap", "seed": args.seed},
+        "cpu_baseline": {"value": value, "unit": "generator-updates/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "generator-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------- our arm
+def run_ours(args, w):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    from paper_1709_06924_gb300.engine import Engine
+
+    seed = args.seed + rank
+    z_host = I.uniform_sphere(w.n, seed)
+    eng = Engine(w.n, w.density, lbfgs_m=w.lbfgs_m, device=local)
+    z = torch.from_numpy(z_host).cuda(local)
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    # warm-up: W LBFGS iterations from the seeded start (history is kept)
+    eng.lbfgs_solve(z, max_iter=args.warmup, grad_tol=0.0)
+    eng.reset_stats()
+    eng.set_profiling(True)
+    try:
+        uuid = torch.cuda.get_device_properties(local).uuid
+        uuid = str(uuid)
+    except Exception:
+        uuid = None
+    clocks = ClockSampler(uuid)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(eng.stream)
+    rep = eng.lbfgs_solve(z, max_iter=args.steps, grad_tol=0.0, warm_start=True)
+    ev1.record(eng.stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks.stop()
+    t = ev0.elapsed_time(ev1) / 1e3
+    st = eng.stats()
+    iters = rep["iters"]
+    t_max = t
+    if ws > 1:
+        tt = torch.tensor([t], device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(tt.item())
+    value = w.n * iters * ws / t_max
+
+    # dominant kernel: the first-pass cell kernel (clip + quadrature), timed by
+    # CUDA events on the engine stream around each launch
+    cell_ms = st["cell_kernel_ms"] / max(st["cell_kernel_timed"], 1)
+    flops_gen = fp64_flops_per_generator(w.density.kind)
+    peak = fp64_peak_tflops()
+    achieved = w.n * flops_gen / (cell_ms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "kernel": "k_cells (first pass)", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "flops_per_generator": flops_gen, "avg_launch_ms": cell_ms,
+                "peak_source": "FP64 pipe: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (derived, not measured)"}
+
+    # end to end through the C ABI with host buffers: every step copies Z in
+    # from pinned host memory and the result back (resume-if-unchanged mode)
+    e2e = None
+    if not args.no_e2e:
+        zp = torch.empty((w.n, 3), dtype=torch.float64, pin_memory=True)
+        zp.copy_(z.cpu())
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        eng.lbfgs_solve(zp.numpy(), max_iter=1, grad_tol=0.0, warm_start=2)  # settle
+        torch.cuda.synchronize()
+        e0.record(eng.stream)
+        k_e2e = 0
+        for _ in range(args.steps):
+            r = eng.lbfgs_solve(zp.numpy(), max_iter=1, grad_tol=0.0, warm_start=2)
+            k_e2e += r["iters"]
+        e1.record(eng.stream)
+        torch.cuda.synchronize()
+        te = e0.elapsed_time(e1) / 1e3
+        if ws > 1:
+            tt = torch.tensor([te], device="cuda")
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            te = float(tt.item())
+        e2e = {"value": w.n * k_e2e * ws / te, "unit": "generator-updates/s",
+               "h2d_bytes_per_step": w.n * 24, "d2h_bytes_per_step": w.n * 24}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = oracle_sample(w, args.cpu_sample_n, args.cpu_sample_iters, args.seed)
+
+    if rank == 0:
+        line = {
+            "metric": "generator-updates/s", "value": value, "unit": "generator-updates/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_max / max(iters, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": w.name, "n_generators": w.n, "density": "tanh cap",
+                       "gamma": w.density.gamma, "alpha": w.density.alpha, "beta": w.density.beta,
+                       "lbfgs_m": w.lbfgs_m, "quadrature": "7-point per sub-triangle", "seed": args.seed,
+                       "parallelism": "replicas" if ws > 1 else "single",
+                       "l2": "inputs larger than L2 (history %d MB per step)" % (2 * w.lbfgs_m * w.n * 24 >> 20),
+                       "iters_timed": iters, "fevals_timed": rep["fevals"]},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "clocks": clocks.summary(),
+            "gpu_launches": st["kernel_launches"],
+            "knn_retries": st["knn_retries"],
+            "ambiguous": st["ambiguous"],
+            "eval_ms_avg": st["eval_ms"] / max(st["evaluations"], 1),
+            "lbfgs_ms_total": st["lbfgs_ms"],
+        }
+        print(json.dumps(line), flush=True)
+    eng.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def fp64_peak_tflops() -> float:
+    return 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def fp64_flops_per_generator(kind: int) -> float:
+    """Algorithmic FP64 flop count of one cell, with transcendentals weighted
+    as FP64 flop equivalents (see the design notes for the derivation)."""
+    base = 7.2e3
+    per_point_density = {0: 0.0, 1: 6.0, 2: 25.0 + TR["sqrt"] + TR["atan2"] + TR["tanh"] + TR["div"],
+                         3: 28.0 + TR["sqrt"] + TR["atan2"] + TR["tanh"] + TR["div"]}[kind]
+    per_point_fixed = TR["sqrt"] + TR["div"]
+    per_tri = TR["atan2"]
+    return base + 84 * (per_point_density + per_point_fixed) + 12 * per_tri
+
+
+# FP64 flop-equivalents charged per transcendental call
+TR = {"sqrt": 8.0, "div": 8.0, "atan2": 40.0, "tanh": 30.0}
+
+
+def main():
+    args = parse()
+    w = I.WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, w)
+    else:
+        run_ours(args, w)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,195 @@
+/*
+ * scvt.h -- C ABI of the GB300 spherical centroidal Voronoi tessellation
+ * (SCVT) engine: Lloyd-preconditioned LBFGS (Yang, Gunzburger and Ju,
+ * "Fast spherical centroidal Voronoi mesh generation: a Lloyd-preconditioned
+ * LBFGS method in parallel").
+ *
+ * Problem (Sec. 2.1): for generators z_1..z_N on the unit sphere S^2 and a
+ * point density rho > 0, the spherical Voronoi region of z_i is
+ *     V_i = { x in S^2 : |x - z_i| < |x - z_j| for all j != i }
+ * (Euclidean distance restricted to the sphere) and the energy is
+ *     F(Z) = sum_i int_{V_i} |y - z_i|^2 rho(y) dsigma(y).
+ * With m_i = int_{V_i} rho and c_i = int_{V_i} y rho, the tangential gradient
+ * is g_i = 2 (c_i . z_i) z_i - 2 c_i and the Lloyd preconditioner is
+ * h_i = 1 / (2 c_i . z_i) (Sec. 3.1, spherical form).
+ *
+ * Conventions for every entry point below:
+ *   - Arrays of points or vectors are contiguous row-major N x 3 doubles
+ *     (x, y, z of point 0, then point 1, ...); per-point scalars are N doubles.
+ *   - The caller owns every array.  A pointer may be device memory or host
+ *     memory (pageable or pinned); host pointers are staged through the
+ *     handle's device buffers inside the call.
+ *   - All device work is ordered on the CUDA stream given to scvt_create.
+ *     Calls that return host scalars synchronise that stream.
+ *   - Errors are returned as scvt_status, never thrown or aborted; after an
+ *     error the outputs are unspecified and the handle remains usable.
+ *     scvt_last_error() then gives a one-line description.
+ *   - A handle is not thread-safe: one host thread at a time per handle.
+ */
+#ifndef SCVT_H
+#define SCVT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SCVT_OK = 0,
+    SCVT_ERR_INVALID = 1,       /* bad argument: N < 4, non-finite or non-unit point (| |z|-1 | > 1e-12),
+                                   duplicate points, null pointer, unsupported option */
+    SCVT_ERR_DEGENERATE = 2,    /* origin not strictly inside the hull of Z (some cell leaves its
+                                   hemisphere), or c_i . z_i <= 0 */
+    SCVT_ERR_OOM = 3,           /* device allocation failed */
+    SCVT_ERR_CUDA = 4,          /* a CUDA runtime call failed */
+    SCVT_ERR_KNN_EXHAUSTED = 5, /* a cell could not be certified (security radius) with any neighbour count */
+    SCVT_ERR_LINESEARCH = 6,    /* the line search found no decrease from a Lloyd direction (rounding floor) */
+    SCVT_ERR_TIMEOUT = 7,       /* a bounded device wait ran out */
+    SCVT_ERR_UNIMPLEMENTED = 8  /* option not available in this build */
+} scvt_status;
+
+/* Point densities of Sec. 4.  TANH_CAP: rho = (1-gamma)/2 (tanh((beta - d)/alpha) + 1) + gamma with
+ * d the geodesic distance to xc (radians); POLAR_X3: rho = (1-gamma) z^4 + gamma;
+ * TANH_CAP_POW4: the TANH_CAP value raised to the 4th power. */
+typedef enum {
+    SCVT_RHO_UNIFORM = 0,
+    SCVT_RHO_POLAR_X3 = 1,
+    SCVT_RHO_TANH_CAP = 2,
+    SCVT_RHO_TANH_CAP_POW4 = 3
+} scvt_rho_kind;
+
+typedef struct {
+    int kind;           /* scvt_rho_kind */
+    double gamma;       /* minimum density (rho >= gamma > 0) */
+    double alpha;       /* transition width (radians), TANH kinds */
+    double beta;        /* cap radius (radians), TANH kinds */
+    double xc[3];       /* cap centre (unit vector), TANH kinds */
+} scvt_density;
+
+typedef struct {
+    int64_t n;          /* number of generators, >= 4 */
+    scvt_density rho;
+    int quad_points;    /* points per sub-triangle; 7 (Radon degree-5 rule) is the only value */
+    int precision;      /* 0 = FP64 throughout (parity mode); 1 = mixed (reserved) */
+    int lbfgs_m;        /* number of (s, y) pairs kept, 0..32 (the paper uses 7) */
+    int knn_k0;         /* first-pass neighbour count, 0 = default (32); 8..32 */
+    int knn_kmax;       /* largest neighbour count of the retry passes, 0 = default (128) */
+} scvt_config;
+
+typedef struct {
+    int max_iter;         /* LBFGS iterations (accepted steps) at most */
+    double grad_tol;      /* stop when ||g||_2 <= grad_tol (2-norm over all 3N components) */
+    double rel_grad_tol;  /* stop when ||g||/F <= rel_grad_tol (0 = off; the paper uses 5e-4) */
+    double rel_df_tol;    /* stop when |F_k - F_{k-1}|/F_{k-1} < rel_df_tol (0 = off; paper 1e-7) */
+    double step_tol;      /* stop when max_i |z_i^{k+1} - z_i^k| <= step_tol (0 = off; paper 5e-4) */
+    int ls_max_evals;     /* function evaluations per line search, 0 = default (10, Sec. 4) */
+    double c1, c2;        /* strong Wolfe constants, 0 = defaults (1e-4, 0.9) */
+    int warm_start;       /* 0: start at z with an empty history.
+                             1: continue from the handle's state left by the previous
+                                scvt_lbfgs_solve (iterate, gradient and history); z's input
+                                value is ignored and z receives the result.
+                             2: as 1 if z holds exactly the iterate the previous solve
+                                returned (checked on the device), else as 0. */
+} scvt_solve_opts;
+
+typedef struct {
+    int iters;          /* accepted LBFGS steps in this call */
+    int fevals;         /* energy/gradient evaluations in this call */
+    int resets;         /* history resets (no descent, line-search trouble) */
+    int skipped;        /* pairs skipped by the curvature test */
+    int knn_retries;    /* cells that needed a retry pass, summed over evaluations */
+    double energy;      /* F at the returned iterate */
+    double grad_norm;   /* ||g||_2 at the returned iterate */
+    int converged;      /* 1 if a stopping tolerance was met */
+    int status;         /* scvt_status of the call */
+} scvt_solve_report;
+
+typedef struct {
+    int64_t evaluations;        /* energy/gradient evaluations since creation */
+    int64_t cell_launches;      /* launches of the cell kernel (first pass + retries) */
+    int64_t kernel_launches;    /* all kernel launches of this handle */
+    int64_t knn_retries;        /* cells sent to a retry pass */
+    int64_t ambiguous;          /* clip decisions within rounding of zero (0 on generic input) */
+    double cell_kernel_ms;      /* device time of the first-pass cell kernel (profiling on) */
+    double eval_ms;             /* device time of whole evaluations (profiling on) */
+    double lbfgs_ms;            /* device time of the two-loop / update kernels (profiling on) */
+    int64_t cell_kernel_timed;  /* first-pass launches included in cell_kernel_ms */
+    int64_t bytes_device;       /* device memory held by the handle */
+} scvt_stats;
+
+typedef struct scvt_handle scvt_handle;
+
+/* Create an engine for N generators.  cuda_stream: a cudaStream_t (NULL = the
+ * legacy default stream).  Allocates all device workspace for N, including
+ * the LBFGS history (2 * lbfgs_m * N * 3 doubles).  *out is set on success.
+ * Errors: INVALID (bad config), OOM, CUDA. */
+scvt_status scvt_create(const scvt_config *cfg, void *cuda_stream, scvt_handle **out);
+
+/* Destroy the engine and free its device memory.  NULL-safe. */
+void scvt_destroy(scvt_handle *h);
+
+/* Energy and gradient at z (Sec. 2.1 energy, Sec. 3.1 gradient).
+ * z: N x 3.  energy: host double (required).  grad: N x 3 (nullable).
+ * mass: N, m_i (nullable).  moment: N x 3, c_i (nullable).  Synchronises. */
+scvt_status scvt_energy_grad(scvt_handle *h, const double *z, double *energy, double *grad,
+                             double *mass, double *moment);
+
+/* Everything one evaluation produces.  Any array pointer may be NULL. */
+typedef struct {
+    double *grad;        /* N x 3, g_i = 2 (c_i.z_i) z_i - 2 c_i */
+    double *precond;     /* N, h_i = 1 / (2 c_i.z_i) */
+    double *mass;        /* N, m_i */
+    double *moment;      /* N x 3, c_i */
+    double *cell_energy; /* N, F_i = int_{V_i} |y - z_i|^2 rho */
+    double energy;       /* out: F = sum_i F_i */
+    double grad_norm;    /* out: ||g||_2 */
+} scvt_eval_out;
+
+scvt_status scvt_evaluate(scvt_handle *h, const double *z, scvt_eval_out *out);
+
+/* One Lloyd iteration (Sec. 2.2.1 on S^2): z_out_i = c_i / |c_i|.
+ * z_out may alias z_in.  Synchronises. */
+scvt_status scvt_lloyd_step(scvt_handle *h, const double *z_in, double *z_out);
+
+/* Lloyd-preconditioned LBFGS (Sec. 3.1; serial core of the algorithm of
+ * Sec. 3.3): two-loop recursion with diag(h) as initial inverse Hessian,
+ * strong-Wolfe line search from step 1 on alpha -> F(normalize(Z + alpha q)),
+ * re-projection onto S^2.  z: N x 3 in/out.  opts: NULL = defaults
+ * (200 iterations, grad_tol 1e-8).  report: host (nullable).
+ * Returns OK when a tolerance or max_iter ends the solve, LINESEARCH when no
+ * decrease can be found from a Lloyd direction (z then holds the last
+ * accepted iterate). */
+scvt_status scvt_lbfgs_solve(scvt_handle *h, double *z, const scvt_solve_opts *opts,
+                             scvt_solve_report *report);
+
+/* Voronoi topology (Sec. 2.1): deg[i] and the neighbour ids of cell i in
+ * counter-clockwise order seen from outside, nbr[i * max_deg + t],
+ * t < deg[i].  deg: N ints, nbr: N * max_deg ints (device or host).
+ * INVALID if a cell has more than max_deg neighbours.  Synchronises. */
+scvt_status scvt_voronoi(scvt_handle *h, const double *z, int *deg, int *nbr, int max_deg);
+
+/* LBFGS direction on caller-provided pairs (Sec. 2.2.2 two-loop with the
+ * Sec. 3.1 preconditioner): q = -H g with H0 = diag(h) applied per generator.
+ * S, Y: count x N x 3, oldest pair first; requires y_k . s_k > 0.
+ * g, h, q: N x 3, N, N x 3.  count <= 64.  Synchronises. */
+scvt_status scvt_lbfgs_direction(scvt_handle *h, const double *g, const double *hdiag, int count,
+                                 const double *S, const double *Y, double *q);
+
+/* Per-handle counters and (with profiling on) device times. */
+scvt_status scvt_get_stats(const scvt_handle *h, scvt_stats *out);
+scvt_status scvt_reset_stats(scvt_handle *h);
+/* Profiling: record CUDA events around the cell kernel and evaluations. */
+scvt_status scvt_set_profiling(scvt_handle *h, int enabled);
+
+const char *scvt_status_string(scvt_status s);
+/* Description of the handle's last error ("" if none); owned by the handle. */
+const char *scvt_last_error(const scvt_handle *h);
+/* Library build string (compute capability, precision modes). */
+const char *scvt_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SCVT_H */

@@ -1,0 +1,798 @@
+// capi.cu -- the C ABI (include/scvt.h): handle, workspace, evaluation
+// driver and the Lloyd-preconditioned LBFGS driver.
+//
+// The host side of the solver moves scalars only: per evaluation one
+// device-to-host copy of a small status block (energy, |g|^2, phi'(alpha),
+// flags); per iteration one more for the curvature pair's dot products.
+// Vectors (Z, g, h, q, the history ring) stay in HBM.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "scvt_internal.cuh"
+
+using namespace scvt;
+
+namespace {
+
+constexpr int kMaxM = 32;       // history pairs
+constexpr int kDefaultK0 = 32;
+
+struct Bufs {
+    double *z = nullptr, *zt = nullptr;      // current iterate, trial point
+    double *g = nullptr, *gt = nullptr;      // gradients
+    double *h = nullptr, *ht = nullptr;      // preconditioner
+    double *fc = nullptr;                    // per-cell energy (scratch)
+    double *q = nullptr;                     // direction
+    double *yv = nullptr;                    // y of the newest candidate pair (scratch)
+    double *nrm = nullptr;                   // |z + alpha q|
+    double *mass = nullptr, *moment = nullptr;
+    double *stage_a = nullptr, *stage_b = nullptr;  // host-pointer staging (3n each)
+    double *partials = nullptr;              // 4 * 1024
+    double *scal = nullptr;                  // 128 two-loop scalars
+    double *rho = nullptr;                   // kMaxM + 1
+    double *hist = nullptr;                  // (m + 1) slots of S and Y, 3n each
+    P4 *zs = nullptr;
+    int *bin_of = nullptr, *count = nullptr, *start = nullptr, *cursor = nullptr, *scan_tmp = nullptr;
+    int *sidx = nullptr, *list1 = nullptr, *list2 = nullptr;
+    int *deg = nullptr;
+    float *radius = nullptr;
+    DevStatus *st = nullptr;
+};
+
+}  // namespace
+
+struct scvt_handle {
+    scvt_config cfg;
+    int n = 0;
+    int G = 1;
+    int m = 0;
+    cudaStream_t stream = nullptr;
+    Bufs b;
+    DevStatus *st_host = nullptr;  // pinned
+    int64_t bytes = 0;
+    // history ring: slot order (oldest first) and one spare slot
+    int hist_slots[kMaxM + 1];
+    int hist_count = 0;
+    int spare = 0;
+    bool state_valid = false;  // z, g, h, F describe the current iterate
+    double F = 0.0, gnorm = 0.0;
+    bool radius_valid = false;
+    // stats
+    scvt_stats stats;
+    bool profiling = false;
+    cudaEvent_t ev_cell0 = nullptr, ev_cell1 = nullptr, ev_e0 = nullptr, ev_e1 = nullptr, ev_l0 = nullptr,
+                ev_l1 = nullptr;
+    std::string err;
+};
+
+namespace {
+
+scvt_status fail(scvt_handle *h, scvt_status s, const std::string &msg) {
+    if (h) h->err = msg;
+    return s;
+}
+
+scvt_status cuda_fail(scvt_handle *h, cudaError_t e, const char *what) {
+    cudaGetLastError();
+    return fail(h, e == cudaErrorMemoryAllocation ? SCVT_ERR_OOM : SCVT_ERR_CUDA,
+                std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                  \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return cuda_fail(H, e_, what); \
+    } while (0)
+
+template <class T>
+cudaError_t alloc(scvt_handle *H, T **p, size_t count) {
+    size_t bytes = sizeof(T) * (count ? count : 1);
+    cudaError_t e = cudaMalloc((void **)p, bytes);
+    if (e == cudaSuccess) H->bytes += (int64_t)bytes;
+    return e;
+}
+
+bool is_device_ptr(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+Density to_density(const scvt_density &r) {
+    Density d;
+    d.kind = r.kind;
+    d.gamma = r.gamma;
+    d.alpha = r.alpha;
+    d.beta = r.beta;
+    d.xc0 = r.xc[0];
+    d.xc1 = r.xc[1];
+    d.xc2 = r.xc[2];
+    return d;
+}
+
+double *slot_S(scvt_handle *H, int slot) { return H->b.hist + (size_t)slot * 2 * 3 * H->n; }
+double *slot_Y(scvt_handle *H, int slot) { return slot_S(H, slot) + (size_t)3 * H->n; }
+
+void profile_accumulate(scvt_handle *H) {
+    if (!H->profiling) return;
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, H->ev_cell0, H->ev_cell1) == cudaSuccess) {
+        H->stats.cell_kernel_ms += ms;
+        H->stats.cell_kernel_timed++;
+    }
+    if (cudaEventElapsedTime(&ms, H->ev_e0, H->ev_e1) == cudaSuccess) H->stats.eval_ms += ms;
+    cudaGetLastError();
+}
+
+// One energy/gradient evaluation at zdev (device).  Outputs go to the given
+// device arrays (grad, hdiag and fcell are required).  If q is given, phi'
+// (Sec. 3.1 line search on the projected path) is accumulated with nrm.
+scvt_status evaluate_dev(scvt_handle *H, const double *zdev, double *grad, double *hdiag, double *fcell,
+                         double *mass, double *moment, int *deg, int *nbr, int max_deg, const double *q,
+                         const double *nrm, double *F, double *gn2, double *dphi) {
+    const int n = H->n;
+    Bufs &B = H->b;
+    cudaStream_t s = H->stream;
+    int64_t *L = &H->stats.kernel_launches;
+    if (H->profiling) cudaEventRecord(H->ev_e0, s);
+    CK(cudaMemsetAsync(B.st, 0, sizeof(DevStatus), s), "reset status");
+    bin_points(zdev, n, H->G, B.bin_of, B.count, B.start, B.cursor, B.scan_tmp, B.zs, B.sidx, B.st, s, L);
+    Grid g;
+    g.n = n;
+    g.G = H->G;
+    g.nbins = 6 * H->G * H->G;
+    g.zs = B.zs;
+    g.sidx = B.sidx;
+    g.bstart = B.start;
+    CellOut out;
+    out.grad = grad;
+    out.hdiag = hdiag;
+    out.mass = mass;
+    out.moment = moment;
+    out.fcell = fcell;
+    out.deg = deg;
+    out.nbr = nbr;
+    out.max_deg = max_deg;
+    out.radius = B.radius;
+    if (!H->radius_valid) {
+        CK(cudaMemsetAsync(B.radius, 0, sizeof(float) * n, s), "reset radius hints");
+        H->radius_valid = true;
+    }
+    cell_passes(g, to_density(H->cfg.rho), out, nullptr, B.list1, B.list2, B.st, H->cfg.knn_k0, H->cfg.knn_kmax, s,
+                H->profiling ? H->ev_cell0 : nullptr, H->profiling ? H->ev_cell1 : nullptr, L,
+                &H->stats.cell_launches);
+    reduce_eval(n, fcell, grad, q, nrm, B.partials, B.st, s, L);
+    if (H->profiling) cudaEventRecord(H->ev_e1, s);
+    CK(cudaGetLastError(), "launch");
+    CK(cudaMemcpyAsync(H->st_host, B.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s), "status copy");
+    CK(cudaStreamSynchronize(s), "evaluation");
+    profile_accumulate(H);
+    const DevStatus &st = *H->st_host;
+    H->stats.evaluations++;
+    H->stats.knn_retries += st.retry_count[0];
+    H->stats.ambiguous += (int64_t)st.ambiguous;
+    if (st.flags & FLAG_BAD_POINT)
+        return fail(H, SCVT_ERR_INVALID, "a generator is not finite or not on the unit sphere (| |z|^2 - 1 | > 2e-12)");
+    if (st.flags & FLAG_DUPLICATE) return fail(H, SCVT_ERR_INVALID, "duplicate generators");
+    if (st.flags & (FLAG_UNBOUNDED | FLAG_EMPTY))
+        return fail(H, SCVT_ERR_DEGENERATE, "origin not strictly inside the convex hull of the generators");
+    if (st.flags & FLAG_EXHAUSTED)
+        return fail(H, SCVT_ERR_KNN_EXHAUSTED, "a Voronoi cell could not be certified by the security radius");
+    if (st.flags & FLAG_VMAX) return fail(H, SCVT_ERR_KNN_EXHAUSTED, "a Voronoi cell has more than 64 vertices");
+    if (st.flags & FLAG_NONPOSITIVE) return fail(H, SCVT_ERR_DEGENERATE, "a cell has c_i . z_i <= 0");
+    if (F) *F = st.red[0];
+    if (gn2) *gn2 = st.red[1];
+    if (dphi) *dphi = st.red[2];
+    H->err.clear();
+    return SCVT_OK;
+}
+
+// Resolve an input array of 3n (or n) doubles: device pointers are used
+// as they are, host pointers are copied into the given staging buffer.
+scvt_status stage_in(scvt_handle *H, const double *p, size_t count, double *stage, const double **dev) {
+    if (is_device_ptr(p)) {
+        *dev = p;
+        return SCVT_OK;
+    }
+    CK(cudaMemcpyAsync(stage, p, sizeof(double) * count, cudaMemcpyHostToDevice, H->stream), "host to device");
+    *dev = stage;
+    return SCVT_OK;
+}
+
+scvt_status copy_out(scvt_handle *H, double *dst, const double *src, size_t count) {
+    if (!dst) return SCVT_OK;
+    cudaMemcpyKind k = is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (dst != src) CK(cudaMemcpyAsync(dst, src, sizeof(double) * count, k, H->stream), "copy out");
+    return SCVT_OK;
+}
+
+// ------------------------------------------------ line search (More-Thuente)
+// Strong-Wolfe search of More & Thuente (1994): on the auxiliary function
+// psi(a) = phi(a) - phi(0) - ftol a phi'(0) until a step with psi <= 0 and
+// phi' >= 0 (up to ftol/gtol) is seen, then on phi; the interval of
+// uncertainty is updated with safeguarded cubic / quadratic / secant steps
+// and bisected when it fails to shrink by 2/3.
+class WolfeSearch {
+  public:
+    double ftol = 1e-4, gtol = 0.9, xtol = 1e-16, amin = 1e-20, amax = 1e20;
+    int maxfev = 10;
+
+    // phi(a, &f, &d) returns 0 on success.  On return a, f, d hold the last
+    // evaluated point.  Result: 1 strong Wolfe, 2 width below xtol, 3 maxfev,
+    // 4 at amin, 5 at amax, 6 rounding, 7 bad input, <0 callback failure.
+    template <class Phi>
+    int run(Phi &&phi, double f0, double d0, double &a, double &f, double &d, int &nfev) {
+        nfev = 0;
+        if (!(d0 < 0.0) || !(a > 0.0)) return 7;
+        lo_ = {0.0, f0, d0};
+        hi_ = {0.0, f0, d0};
+        brack_ = false;
+        bool first_stage = true;
+        const double slope = ftol * d0;
+        double width = amax - amin, width_prev = 2.0 * width;
+        double lo_bound = 0.0, hi_bound = a * 5.0;
+        for (;;) {
+            a = std::min(std::max(a, amin), amax);
+            bool last_chance = nfev >= maxfev - 1;
+            if ((brack_ && (a <= lo_bound || a >= hi_bound)) || last_chance ||
+                (brack_ && hi_bound - lo_bound <= xtol * hi_bound))
+                a = lo_.a;
+            int cb = phi(a, f, d);
+            ++nfev;
+            if (cb) return -1;
+            const double armijo = f0 + a * slope;
+            int info = 0;
+            if (brack_ && (a <= lo_bound || a >= hi_bound)) info = 6;
+            if (a == amax && f <= armijo && d <= slope) info = 5;
+            if (a == amin && (f > armijo || d >= slope)) info = 4;
+            if (nfev >= maxfev) info = 3;
+            if (brack_ && hi_bound - lo_bound <= xtol * hi_bound) info = 2;
+            if (f <= armijo && fabs(d) <= gtol * (-d0)) info = 1;
+            if (info) return info;
+            if (first_stage && f <= armijo && d >= std::min(ftol, gtol) * d0) first_stage = false;
+            double next;
+            if (first_stage && f <= lo_.f && f > armijo) {
+                // work on psi: shift values and slopes by the Armijo line
+                Pt l = {lo_.a, lo_.f - lo_.a * slope, lo_.d - slope};
+                Pt u = {hi_.a, hi_.f - hi_.a * slope, hi_.d - slope};
+                Pt t = {a, f - a * slope, d - slope};
+                std::swap(l, lo_);
+                std::swap(u, hi_);
+                next = update(t, lo_bound, hi_bound);
+                lo_ = {lo_.a, lo_.f + lo_.a * slope, lo_.d + slope};
+                hi_ = {hi_.a, hi_.f + hi_.a * slope, hi_.d + slope};
+            } else {
+                next = update({a, f, d}, lo_bound, hi_bound);
+            }
+            if (brack_) {
+                if (fabs(hi_.a - lo_.a) >= 0.66 * width_prev) next = lo_.a + 0.5 * (hi_.a - lo_.a);
+                width_prev = width;
+                width = fabs(hi_.a - lo_.a);
+                lo_bound = std::min(lo_.a, hi_.a);
+                hi_bound = std::max(lo_.a, hi_.a);
+            } else {
+                lo_bound = lo_.a;
+                hi_bound = next + 4.0 * (next - lo_.a);
+            }
+            a = next;
+        }
+    }
+
+  private:
+    struct Pt {
+        double a, f, d;
+    };
+    Pt lo_, hi_;  // best point so far and the other end of the interval
+    bool brack_ = false;
+
+    // minimiser of the cubic through (x, fx, dx) and (t, ft, dt), in the
+    // theta / gamma form; ok = false when it does not exist
+    static double cubic(const Pt &x, const Pt &t, bool &ok) {
+        double theta = 3.0 * (x.f - t.f) / (t.a - x.a) + x.d + t.d;
+        double sc = std::max(fabs(theta), std::max(fabs(x.d), fabs(t.d)));
+        double rad = (theta / sc) * (theta / sc) - (x.d / sc) * (t.d / sc);
+        ok = rad > 0.0;
+        double gamma = sc * sqrt(std::max(rad, 0.0));
+        if (t.a < x.a) gamma = -gamma;
+        double p = (gamma - x.d) + theta;
+        double q = ((gamma - x.d) + gamma) + t.d;
+        if (q == 0.0) {
+            ok = false;
+            return x.a;
+        }
+        return x.a + (p / q) * (t.a - x.a);
+    }
+
+    double update(Pt t, double lo_bound, double hi_bound) {
+        const Pt &x = lo_;
+        const double sx = (x.d > 0.0) - (x.d < 0.0);
+        const bool opposite = t.d * sx < 0.0;
+        bool ok;
+        double nxt;
+        if (t.f > x.f) {
+            double ac = cubic(x, t, ok);
+            double aq = x.a + (x.d / ((x.f - t.f) / (t.a - x.a) + x.d)) / 2.0 * (t.a - x.a);
+            nxt = (fabs(ac - x.a) < fabs(aq - x.a)) ? ac : ac + (aq - ac) / 2.0;
+            brack_ = true;
+        } else if (opposite) {
+            double ac = cubic(x, t, ok);
+            double as = t.a + t.d / (t.d - x.d) * (x.a - t.a);
+            nxt = (fabs(ac - t.a) > fabs(as - t.a)) ? ac : as;
+            brack_ = true;
+        } else if (fabs(t.d) < fabs(x.d)) {
+            double ac = cubic(x, t, ok);
+            bool beyond = ok && ((t.a > x.a) ? (ac > t.a) : (ac < t.a));
+            if (!beyond) ac = (t.a > x.a) ? hi_bound : lo_bound;
+            double as = t.a + t.d / (t.d - x.d) * (x.a - t.a);
+            if (brack_) {
+                nxt = (fabs(ac - t.a) < fabs(as - t.a)) ? ac : as;
+                nxt = (t.a > x.a) ? std::min(t.a + 0.66 * (hi_.a - t.a), nxt)
+                                  : std::max(t.a + 0.66 * (hi_.a - t.a), nxt);
+            } else {
+                nxt = (fabs(ac - t.a) > fabs(as - t.a)) ? ac : as;
+                nxt = std::min(hi_bound, std::max(lo_bound, nxt));
+            }
+        } else {
+            if (brack_) nxt = cubic(t, hi_, ok);
+            else nxt = (t.a > x.a) ? hi_bound : lo_bound;
+        }
+        if (t.f > x.f) {
+            hi_ = t;
+        } else {
+            if (opposite) hi_ = lo_;
+            lo_ = t;
+        }
+        return nxt;
+    }
+};
+
+// history bookkeeping
+void hist_reset(scvt_handle *H) {
+    H->hist_count = 0;
+    for (int k = 0; k <= H->m; ++k) H->hist_slots[k] = k;
+    H->spare = H->m;  // slot m is the first spare
+}
+
+scvt_status make_direction(scvt_handle *H, double *d0) {
+    const double *S[kMaxM], *Y[kMaxM], *R[kMaxM];
+    for (int k = 0; k < H->hist_count; ++k) {
+        int sl = H->hist_slots[k];
+        S[k] = slot_S(H, sl);
+        Y[k] = slot_Y(H, sl);
+        R[k] = H->b.rho + sl;
+    }
+    if (H->profiling) cudaEventRecord(H->ev_l0, H->stream);
+    two_loop(H->n, H->b.g, H->b.h, H->hist_count, S, Y, R, H->b.q, H->b.partials, H->b.scal, H->b.st, H->stream,
+             &H->stats.kernel_launches);
+    if (H->profiling) cudaEventRecord(H->ev_l1, H->stream);
+    CK(cudaGetLastError(), "two-loop launch");
+    CK(cudaMemcpyAsync(&H->st_host->dots[3], &H->b.st->dots[3], sizeof(double), cudaMemcpyDeviceToHost, H->stream),
+       "direction copy");
+    CK(cudaStreamSynchronize(H->stream), "two-loop");
+    if (H->profiling) {
+        float ms;
+        if (cudaEventElapsedTime(&ms, H->ev_l0, H->ev_l1) == cudaSuccess) H->stats.lbfgs_ms += ms;
+        cudaGetLastError();
+    }
+    *d0 = H->st_host->dots[3];
+    return SCVT_OK;
+}
+
+}  // namespace
+
+// ======================================================================
+extern "C" {
+
+const char *scvt_status_string(scvt_status s) {
+    switch (s) {
+    case SCVT_OK: return "ok";
+    case SCVT_ERR_INVALID: return "invalid argument";
+    case SCVT_ERR_DEGENERATE: return "degenerate input";
+    case SCVT_ERR_OOM: return "out of device memory";
+    case SCVT_ERR_CUDA: return "CUDA error";
+    case SCVT_ERR_KNN_EXHAUSTED: return "neighbour search exhausted";
+    case SCVT_ERR_LINESEARCH: return "line search failed";
+    case SCVT_ERR_TIMEOUT: return "device wait timed out";
+    case SCVT_ERR_UNIMPLEMENTED: return "not implemented";
+    }
+    return "unknown status";
+}
+
+const char *scvt_last_error(const scvt_handle *h) { return h ? h->err.c_str() : ""; }
+
+const char *scvt_version(void) { return "scvt-gb300 0.1 (sm_103a, FP64 parity mode)"; }
+
+void scvt_destroy(scvt_handle *H) {
+    if (!H) return;
+    Bufs &b = H->b;
+    void *ptrs[] = {b.z, b.zt, b.g, b.gt, b.h, b.ht, b.fc, b.q, b.yv, b.nrm, b.mass, b.moment, b.stage_a, b.stage_b,
+                    b.partials, b.scal, b.rho, b.hist, b.zs, b.bin_of, b.count, b.start, b.cursor, b.scan_tmp,
+                    b.sidx, b.list1, b.list2, b.deg, b.radius, b.st};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (H->st_host) cudaFreeHost(H->st_host);
+    cudaEvent_t evs[] = {H->ev_cell0, H->ev_cell1, H->ev_e0, H->ev_e1, H->ev_l0, H->ev_l1};
+    for (cudaEvent_t e : evs)
+        if (e) cudaEventDestroy(e);
+    delete H;
+}
+
+scvt_status scvt_create(const scvt_config *cfg, void *cuda_stream, scvt_handle **out) {
+    if (!cfg || !out) return SCVT_ERR_INVALID;
+    *out = nullptr;
+    if (cfg->n < 4 || cfg->n > (int64_t)200000000) return SCVT_ERR_INVALID;
+    if (cfg->lbfgs_m < 0 || cfg->lbfgs_m > kMaxM) return SCVT_ERR_INVALID;
+    if (cfg->quad_points != 0 && cfg->quad_points != 7) return SCVT_ERR_INVALID;
+    if (cfg->precision != 0) return SCVT_ERR_UNIMPLEMENTED;
+    if (cfg->rho.kind < 0 || cfg->rho.kind > 3) return SCVT_ERR_INVALID;
+    if (cfg->rho.kind != SCVT_RHO_UNIFORM) {
+        if (!(cfg->rho.gamma > 0.0) || !(cfg->rho.gamma <= 1.0)) return SCVT_ERR_INVALID;
+        if (cfg->rho.kind >= 2) {
+            double r = sqrt(cfg->rho.xc[0] * cfg->rho.xc[0] + cfg->rho.xc[1] * cfg->rho.xc[1] +
+                            cfg->rho.xc[2] * cfg->rho.xc[2]);
+            if (!(fabs(r - 1.0) < 1e-9) || !(cfg->rho.alpha > 0.0)) return SCVT_ERR_INVALID;
+        }
+    }
+    if (cfg->knn_k0 != 0 && (cfg->knn_k0 < 8 || cfg->knn_k0 > 32)) return SCVT_ERR_INVALID;
+    scvt_handle *H = new (std::nothrow) scvt_handle();
+    if (!H) return SCVT_ERR_OOM;
+    H->cfg = *cfg;
+    if (H->cfg.knn_k0 == 0) H->cfg.knn_k0 = kDefaultK0;
+    if (H->cfg.knn_kmax == 0) H->cfg.knn_kmax = 128;
+    H->n = (int)cfg->n;
+    H->m = cfg->lbfgs_m;
+    H->stream = (cudaStream_t)cuda_stream;
+    memset(&H->stats, 0, sizeof(H->stats));
+    // ~2 generators per bin on average
+    int G = (int)ceil(sqrt((double)H->n / 12.0));
+    H->G = std::max(1, std::min(G, 4096));
+    const int n = H->n;
+    const size_t n3 = 3 * (size_t)n;
+    const int nbins = 6 * H->G * H->G;
+    Bufs &b = H->b;
+    cudaError_t e = cudaSuccess;
+#define AL(ptr, cnt) \
+    if (e == cudaSuccess) e = alloc(H, &(ptr), (cnt))
+    AL(b.z, n3); AL(b.zt, n3); AL(b.g, n3); AL(b.gt, n3); AL(b.h, n); AL(b.ht, n); AL(b.fc, n);
+    AL(b.q, n3); AL(b.yv, n3); AL(b.nrm, n); AL(b.mass, n); AL(b.moment, n3);
+    AL(b.stage_a, n3); AL(b.stage_b, n3);
+    AL(b.partials, 4 * 1024); AL(b.scal, 128); AL(b.rho, kMaxM + 1);
+    AL(b.hist, (size_t)(H->m + 1) * 2 * n3);
+    AL(b.zs, n); AL(b.bin_of, n); AL(b.count, nbins); AL(b.start, nbins + 1); AL(b.cursor, nbins);
+    AL(b.scan_tmp, 2 * (nbins / 2048 + 64) + 64);
+    AL(b.sidx, n); AL(b.list1, n); AL(b.list2, n); AL(b.deg, n); AL(b.radius, n);
+    AL(b.st, 1);
+#undef AL
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&H->st_host, sizeof(DevStatus));
+    cudaEvent_t *evs[] = {&H->ev_cell0, &H->ev_cell1, &H->ev_e0, &H->ev_e1, &H->ev_l0, &H->ev_l1};
+    for (cudaEvent_t *ev : evs)
+        if (e == cudaSuccess) e = cudaEventCreate(ev);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        scvt_destroy(H);
+        return e == cudaErrorMemoryAllocation ? SCVT_ERR_OOM : SCVT_ERR_CUDA;
+    }
+    H->stats.bytes_device = H->bytes;
+    hist_reset(H);
+    *out = H;
+    return SCVT_OK;
+}
+
+scvt_status scvt_evaluate(scvt_handle *H, const double *z, scvt_eval_out *o) {
+    if (!H) return SCVT_ERR_INVALID;
+    if (!z || !o) return fail(H, SCVT_ERR_INVALID, "null argument");
+    const size_t n = H->n, n3 = 3 * n;
+    const double *zd;
+    scvt_status s = stage_in(H, z, n3, H->b.stage_a, &zd);
+    if (s) return s;
+    // kernels write into device memory; host outputs are copied afterwards
+    double *grad = (o->grad && is_device_ptr(o->grad)) ? o->grad : H->b.gt;
+    double *hd = (o->precond && is_device_ptr(o->precond)) ? o->precond : H->b.ht;
+    double *mass = o->mass ? ((is_device_ptr(o->mass)) ? o->mass : H->b.mass) : nullptr;
+    double *mom = o->moment ? ((is_device_ptr(o->moment)) ? o->moment : H->b.moment) : nullptr;
+    double *fc = (o->cell_energy && is_device_ptr(o->cell_energy)) ? o->cell_energy : H->b.fc;
+    double F, g2;
+    s = evaluate_dev(H, zd, grad, hd, fc, mass, mom, nullptr, nullptr, 0, nullptr, nullptr, &F, &g2, nullptr);
+    if (s) return s;
+    if ((s = copy_out(H, o->grad, grad, n3))) return s;
+    if ((s = copy_out(H, o->precond, hd, n))) return s;
+    if ((s = copy_out(H, o->mass, mass, n))) return s;
+    if ((s = copy_out(H, o->moment, mom, n3))) return s;
+    if ((s = copy_out(H, o->cell_energy, fc, n))) return s;
+    CK(cudaStreamSynchronize(H->stream), "copy out");
+    o->energy = F;
+    o->grad_norm = sqrt(g2);
+    return SCVT_OK;
+}
+
+scvt_status scvt_energy_grad(scvt_handle *H, const double *z, double *energy, double *grad, double *mass,
+                             double *moment) {
+    if (!H) return SCVT_ERR_INVALID;
+    if (!energy) return fail(H, SCVT_ERR_INVALID, "energy pointer is null");
+    scvt_eval_out o;
+    memset(&o, 0, sizeof(o));
+    o.grad = grad;
+    o.mass = mass;
+    o.moment = moment;
+    scvt_status s = scvt_evaluate(H, z, &o);
+    if (s == SCVT_OK) *energy = o.energy;
+    return s;
+}
+
+scvt_status scvt_lloyd_step(scvt_handle *H, const double *z_in, double *z_out) {
+    if (!H) return SCVT_ERR_INVALID;
+    if (!z_in || !z_out) return fail(H, SCVT_ERR_INVALID, "null argument");
+    const size_t n3 = 3 * (size_t)H->n;
+    const double *zd;
+    scvt_status s = stage_in(H, z_in, n3, H->b.stage_a, &zd);
+    if (s) return s;
+    double F, g2;
+    s = evaluate_dev(H, zd, H->b.gt, H->b.ht, H->b.fc, nullptr, H->b.moment, nullptr, nullptr, 0, nullptr, nullptr,
+                     &F, &g2, nullptr);
+    if (s) return s;
+    bool dev_out = is_device_ptr(z_out);
+    double *dst = dev_out ? z_out : H->b.stage_b;
+    lloyd_project(H->n, H->b.moment, dst, H->stream, &H->stats.kernel_launches);
+    CK(cudaGetLastError(), "lloyd launch");
+    if (!dev_out) CK(cudaMemcpyAsync(z_out, dst, sizeof(double) * n3, cudaMemcpyDeviceToHost, H->stream), "copy out");
+    CK(cudaStreamSynchronize(H->stream), "lloyd step");
+    return SCVT_OK;
+}
+
+scvt_status scvt_voronoi(scvt_handle *H, const double *z, int *deg, int *nbr, int max_deg) {
+    if (!H) return SCVT_ERR_INVALID;
+    if (!z || !deg || !nbr || max_deg < 3) return fail(H, SCVT_ERR_INVALID, "bad argument");
+    const size_t n = H->n;
+    const double *zd;
+    scvt_status s = stage_in(H, z, 3 * n, H->b.stage_a, &zd);
+    if (s) return s;
+    bool dev_deg = is_device_ptr(deg), dev_nbr = is_device_ptr(nbr);
+    int *ddeg = dev_deg ? deg : H->b.deg;
+    int *dnbr = nbr;
+    int *tmp = nullptr;
+    if (!dev_nbr) {
+        CK(cudaMallocAsync((void **)&tmp, sizeof(int) * n * max_deg, H->stream), "topology buffer");
+        dnbr = tmp;
+    }
+    double F, g2;
+    s = evaluate_dev(H, zd, H->b.gt, H->b.ht, H->b.fc, nullptr, nullptr, ddeg, dnbr, max_deg, nullptr, nullptr, &F,
+                     &g2, nullptr);
+    if (s == SCVT_OK) {
+        if (!dev_deg) cudaMemcpyAsync(deg, ddeg, sizeof(int) * n, cudaMemcpyDeviceToHost, H->stream);
+        if (!dev_nbr) cudaMemcpyAsync(nbr, dnbr, sizeof(int) * n * max_deg, cudaMemcpyDeviceToHost, H->stream);
+    }
+    if (tmp) cudaFreeAsync(tmp, H->stream);
+    CK(cudaStreamSynchronize(H->stream), "topology copy");
+    if (s) return s;
+    // degree check on the host copy
+    std::vector<int> hd;
+    const int *dp = deg;
+    if (dev_deg) {
+        hd.resize(n);
+        CK(cudaMemcpy(hd.data(), deg, sizeof(int) * n, cudaMemcpyDeviceToHost), "degree check");
+        dp = hd.data();
+    }
+    for (size_t i = 0; i < n; ++i)
+        if (dp[i] > max_deg) return fail(H, SCVT_ERR_INVALID, "a cell has more neighbours than max_deg");
+    return SCVT_OK;
+}
+
+scvt_status scvt_lbfgs_direction(scvt_handle *H, const double *g, const double *hdiag, int count, const double *S,
+                                 const double *Y, double *q) {
+    if (!H) return SCVT_ERR_INVALID;
+    if (!g || !hdiag || !q || count < 0 || count > 64 || (count > 0 && (!S || !Y)))
+        return fail(H, SCVT_ERR_INVALID, "bad argument");
+    for (const void *p : {(const void *)g, (const void *)hdiag, (const void *)q})
+        if (!is_device_ptr(p)) return fail(H, SCVT_ERR_INVALID, "scvt_lbfgs_direction takes device pointers");
+    if (count > 0 && (!is_device_ptr(S) || !is_device_ptr(Y)))
+        return fail(H, SCVT_ERR_INVALID, "scvt_lbfgs_direction takes device pointers");
+    const size_t n3 = 3 * (size_t)H->n;
+    std::vector<const double *> Sp(count), Yp(count), Rp(count);
+    double *rho = nullptr;
+    if (count > 0) CK(cudaMallocAsync((void **)&rho, sizeof(double) * count, H->stream), "rho buffer");
+    int64_t *L = &H->stats.kernel_launches;
+    for (int k = 0; k < count; ++k) {
+        Sp[k] = S + k * n3;
+        Yp[k] = Y + k * n3;
+        Rp[k] = rho + k;
+        dot_to((int64_t)n3, Yp[k], Sp[k], H->b.partials, &H->b.st->dots[0], H->stream, L);
+        set_rho(rho, k, H->b.st, H->stream, L);
+    }
+    two_loop(H->n, g, hdiag, count, Sp.data(), Yp.data(), Rp.data(), q, H->b.partials, H->b.scal, H->b.st, H->stream,
+             L);
+    if (rho) cudaFreeAsync(rho, H->stream);
+    CK(cudaGetLastError(), "two-loop launch");
+    CK(cudaStreamSynchronize(H->stream), "two-loop");
+    return SCVT_OK;
+}
+
+scvt_status scvt_lbfgs_solve(scvt_handle *H, double *z, const scvt_solve_opts *opts_in, scvt_solve_report *rep_out) {
+    if (!H) return SCVT_ERR_INVALID;
+    if (!z) return fail(H, SCVT_ERR_INVALID, "null argument");
+    scvt_solve_opts o;
+    memset(&o, 0, sizeof(o));
+    if (opts_in) o = *opts_in;
+    else { o.max_iter = 200; o.grad_tol = 1e-8; }
+    if (o.ls_max_evals <= 0) o.ls_max_evals = 10;
+    if (o.c1 <= 0.0) o.c1 = 1e-4;
+    if (o.c2 <= 0.0) o.c2 = 0.9;
+    if (o.max_iter < 0 || !(o.c1 < o.c2) || o.c2 >= 1.0) return fail(H, SCVT_ERR_INVALID, "bad solve options");
+    scvt_solve_report rep;
+    memset(&rep, 0, sizeof(rep));
+    const int n = H->n;
+    const size_t n3 = 3 * (size_t)n;
+    Bufs &B = H->b;
+    cudaStream_t s = H->stream;
+    scvt_status st = SCVT_OK;
+    const int64_t retries0 = H->stats.knn_retries;
+    bool resume = o.warm_start && H->state_valid;
+    const double *zin = nullptr;
+    if (resume && o.warm_start == 2) {
+        // resume only if the caller passes back the engine's own iterate
+        if ((st = stage_in(H, z, n3, B.stage_a, &zin))) return st;
+        vec_differs((int64_t)n3, zin, B.z, B.st, s, &H->stats.kernel_launches);
+        CK(cudaMemcpyAsync(&H->st_host->differs, &B.st->differs, sizeof(unsigned), cudaMemcpyDeviceToHost, s),
+           "compare copy");
+        CK(cudaStreamSynchronize(s), "compare");
+        resume = H->st_host->differs == 0;
+    }
+    if (!resume) {
+        const double *zd = zin;
+        if (!zd && (st = stage_in(H, z, n3, B.stage_a, &zd))) return st;
+        if (zd != B.z) CK(cudaMemcpyAsync(B.z, zd, sizeof(double) * n3, cudaMemcpyDeviceToDevice, s), "copy in");
+        double F, g2;
+        st = evaluate_dev(H, B.z, B.g, B.h, B.fc, nullptr, nullptr, nullptr, nullptr, 0, nullptr, nullptr, &F, &g2,
+                          nullptr);
+        rep.fevals = 1;
+        if (st) {
+            H->state_valid = false;
+            if (rep_out) { rep.status = st; *rep_out = rep; }
+            return st;
+        }
+        H->F = F;
+        H->gnorm = sqrt(g2);
+        H->state_valid = true;
+        hist_reset(H);
+    }
+    WolfeSearch ls;
+    ls.ftol = o.c1;
+    ls.gtol = o.c2;
+    ls.maxfev = o.ls_max_evals;
+    double Fprev = H->F;
+    int iters = 0;
+    for (;;) {
+        rep.energy = H->F;
+        rep.grad_norm = H->gnorm;
+        if (H->gnorm <= o.grad_tol) { rep.converged = 1; break; }
+        if (o.rel_grad_tol > 0 && H->gnorm / H->F <= o.rel_grad_tol) { rep.converged = 1; break; }
+        if (iters > 0 && o.rel_df_tol > 0 && fabs(H->F - Fprev) / Fprev < o.rel_df_tol) { rep.converged = 1; break; }
+        if (iters >= o.max_iter) break;
+        double d0;
+        if ((st = make_direction(H, &d0))) break;
+        if (!(d0 < 0.0)) {
+            hist_reset(H);
+            rep.resets++;
+            if ((st = make_direction(H, &d0))) break;
+            if (!(d0 < 0.0)) { st = fail(H, SCVT_ERR_DEGENERATE, "Lloyd direction is not a descent direction"); break; }
+        }
+        scvt_status cb_status = SCVT_OK;
+        auto phi = [&](double a, double &f, double &d) -> int {
+            trial_point(n, B.z, B.q, a, B.zt, B.nrm, s, &H->stats.kernel_launches);
+            double g2;
+            cb_status = evaluate_dev(H, B.zt, B.gt, B.ht, B.fc, nullptr, nullptr, nullptr, nullptr, 0, B.q, B.nrm, &f,
+                                     &g2, &d);
+            return cb_status != SCVT_OK;
+        };
+        double a = 1.0, fa = 0.0, da = 0.0;
+        int nfev = 0;
+        int info = ls.run(phi, H->F, d0, a, fa, da, nfev);
+        rep.fevals += nfev;
+        if (info < 0) { st = cb_status; break; }
+        if (info != 1) {
+            if (!(fa < H->F)) {
+                if (H->hist_count == 0) { st = fail(H, SCVT_ERR_LINESEARCH, "no decrease along the Lloyd direction"); break; }
+                hist_reset(H);
+                rep.resets++;
+                continue;
+            }
+            hist_reset(H);
+            rep.resets++;
+        }
+        // accept the last evaluated point: s = z+ - z, y = g+ - g into the spare slot
+        const int slot = H->spare;
+        CK(cudaMemsetAsync(&B.st->maxmove_bits, 0, sizeof(unsigned long long), s), "reset max move");
+        accept_pair(n, B.zt, B.z, B.gt, B.g, slot_S(H, slot), slot_Y(H, slot), B.partials, B.st, s,
+                    &H->stats.kernel_launches);
+        CK(cudaGetLastError(), "accept launch");
+        CK(cudaMemcpyAsync(H->st_host, B.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s), "pair copy");
+        CK(cudaStreamSynchronize(s), "accept");
+        const double ys = H->st_host->dots[0], yy = H->st_host->dots[1], ss = H->st_host->dots[2];
+        unsigned long long mb = H->st_host->maxmove_bits;
+        double maxmove;
+        memcpy(&maxmove, &mb, sizeof(double));
+        if (H->m > 0 && ys > 1e-12 * sqrt(yy) * sqrt(ss)) {
+            set_rho(B.rho, slot, B.st, s, &H->stats.kernel_launches);
+            if (H->hist_count == H->m) {
+                // the oldest pair's slot becomes the spare
+                int old = H->hist_slots[0];
+                for (int k = 1; k < H->hist_count; ++k) H->hist_slots[k - 1] = H->hist_slots[k];
+                H->hist_count--;
+                H->spare = old;
+            } else {
+                // take any slot not in use as the next spare
+                bool used[kMaxM + 1] = {false};
+                for (int k = 0; k < H->hist_count; ++k) used[H->hist_slots[k]] = true;
+                used[slot] = true;
+                for (int k = 0; k <= H->m; ++k)
+                    if (!used[k]) { H->spare = k; break; }
+            }
+            H->hist_slots[H->hist_count++] = slot;
+        } else {
+            rep.skipped++;
+        }
+        std::swap(B.z, B.zt);
+        std::swap(B.g, B.gt);
+        std::swap(B.h, B.ht);
+        Fprev = H->F;
+        H->F = fa;
+        // |g| at the accepted point: the last evaluation's reduction
+        H->gnorm = sqrt(H->st_host->red[1]);
+        iters++;
+        rep.iters = iters;
+        if (o.step_tol > 0 && maxmove <= o.step_tol) {
+            rep.energy = H->F;
+            rep.grad_norm = H->gnorm;
+            rep.converged = 1;
+            break;
+        }
+    }
+    rep.iters = iters;
+    rep.knn_retries = (int)(H->stats.knn_retries - retries0);
+    if (st == SCVT_OK || st == SCVT_ERR_LINESEARCH) {
+        rep.energy = H->F;
+        rep.grad_norm = H->gnorm;
+        scvt_status c = copy_out(H, z, B.z, n3);
+        if (c == SCVT_OK) {
+            cudaError_t e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) c = cuda_fail(H, e, "copy out");
+        }
+        if (c) st = c;
+    } else {
+        H->state_valid = false;
+    }
+    rep.status = st;
+    if (rep_out) *rep_out = rep;
+    return st;
+}
+
+scvt_status scvt_get_stats(const scvt_handle *H, scvt_stats *out) {
+    if (!H || !out) return SCVT_ERR_INVALID;
+    *out = H->stats;
+    out->bytes_device = H->bytes;
+    return SCVT_OK;
+}
+
+scvt_status scvt_reset_stats(scvt_handle *H) {
+    if (!H) return SCVT_ERR_INVALID;
+    memset(&H->stats, 0, sizeof(H->stats));
+    H->stats.bytes_device = H->bytes;
+    return SCVT_OK;
+}
+
+scvt_status scvt_set_profiling(scvt_handle *H, int enabled) {
+    if (!H) return SCVT_ERR_INVALID;
+    H->profiling = enabled != 0;
+    return SCVT_OK;
+}
+
+}  // extern "C"

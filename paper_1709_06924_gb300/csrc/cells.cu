@@ -1,0 +1,567 @@
+// cells.cu -- spherical Voronoi cells and their integrals, one thread per
+// generator.
+//
+// Per evaluation:
+//   1. cube-map binning: face = argmax |z_k|, (s, t) = the other two
+//      coordinates over |z_face|, G x G bins per face, counting sort;
+//   2. per generator z_i: its K nearest neighbours by chord distance, found by
+//      a complete cap query over the bins (every point within the cap's chord
+//      radius is seen, so "not kept" implies "at least d_K away");
+//   3. the cell V_i = {x in S^2 : x.(z_i - z_j) >= 0 for all j} (Sec. 2.1,
+//      Euclidean distance on the sphere) is clipped in the gnomonic plane at
+//      z_i, where each bisector great circle is a straight line; neighbours
+//      are taken nearest first and clipping stops once the next neighbour is
+//      farther than twice the largest vertex distance (security radius).  A
+//      cell that cannot be certified is queued for a pass with more
+//      neighbours;
+//   4. the cell is integrated over the paper's signed sub-triangles (Sec.
+//      3.2.2: generator, Delaunay-edge midpoint normalize(z_i+z_j), Voronoi
+//      vertex) with the 7-point degree-5 rule mapped radially to the sphere,
+//      weights scaled by the signed spherical area (Van Oosterom-Strackee);
+//   5. g_i = 2 (c_i.z_i) z_i - 2 c_i and h_i = 1/(2 c_i.z_i) (Sec. 3.1).
+// Results are written at the generator's original index, so that every
+// later reduction runs in index order and is independent of the binning.
+#include <math.h>
+
+#include "scvt_internal.cuh"
+
+namespace scvt {
+
+namespace {
+
+constexpr double kSinThetaMax = 0.28;   // caps stay clear of the far cube faces
+constexpr double kBoxL = 1.0e3;         // half-width of the starting square (gnomonic)
+constexpr double kCertMargin = 1.0 + 1e-9;
+
+// Radon's 7-point degree-5 rule: centroid (weight 9/40) and the orbits
+// (a, a, 1 - 2a) with a = (6 -+ sqrt 15)/21, weights (155 -+ sqrt 15)/1200.
+__constant__ double kQb[7][3] = {
+    {1.0 / 3.0, 1.0 / 3.0, 1.0 / 3.0},
+    {0.7974269853530873224, 0.1012865073234563388, 0.1012865073234563388},
+    {0.1012865073234563388, 0.7974269853530873224, 0.1012865073234563388},
+    {0.1012865073234563388, 0.1012865073234563388, 0.7974269853530873224},
+    {0.059715871789769820459, 0.47014206410511508977, 0.47014206410511508977},
+    {0.47014206410511508977, 0.059715871789769820459, 0.47014206410511508977},
+    {0.47014206410511508977, 0.47014206410511508977, 0.059715871789769820459},
+};
+__constant__ double kQw[7] = {0.225,
+                              0.1259391805448271526, 0.1259391805448271526, 0.1259391805448271526,
+                              0.13239415278850618074, 0.13239415278850618074, 0.13239415278850618074};
+
+struct V3 {
+    double x, y, z;
+};
+__device__ __forceinline__ V3 mk(double x, double y, double z) { return V3{x, y, z}; }
+__device__ __forceinline__ V3 sub(V3 a, V3 b) { return mk(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ V3 add(V3 a, V3 b) { return mk(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ V3 scl(V3 a, double s) { return mk(a.x * s, a.y * s, a.z * s); }
+__device__ __forceinline__ double dot(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ V3 crs(V3 a, V3 b) {
+    return mk(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ V3 unit(V3 a) { return scl(a, 1.0 / sqrt(dot(a, a))); }
+__device__ __forceinline__ V3 ld(const P4 *p) {
+    const P4 v = p[0];
+    return mk(v.x, v.y, v.z);
+}
+
+__device__ __forceinline__ int bin_index(double x, double y, double z, int G) {
+    double ax = fabs(x), ay = fabs(y), az = fabs(z);
+    int a;
+    double m, pb, pc;
+    if (ax >= ay && ax >= az) { a = 0; m = x; pb = y; pc = z; }
+    else if (ay >= az) { a = 1; m = y; pb = z; pc = x; }
+    else { a = 2; m = z; pb = x; pc = y; }
+    double am = fabs(m);
+    double s = pb / am, t = pc / am;
+    int iu = (int)floor((s + 1.0) * 0.5 * G);
+    int iv = (int)floor((t + 1.0) * 0.5 * G);
+    iu = min(max(iu, 0), G - 1);
+    iv = min(max(iv, 0), G - 1);
+    int face = 2 * a + (m < 0.0 ? 1 : 0);
+    return (face * G + iv) * G + iu;
+}
+
+// ---------------------------------------------------------------- binning
+__global__ void k_bin_count(const double *__restrict__ z, int n, int G, int *__restrict__ bin_of,
+                            int *__restrict__ count, DevStatus *st) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double x = z[3 * (size_t)i], y = z[3 * (size_t)i + 1], w = z[3 * (size_t)i + 2];
+    double r2 = x * x + y * y + w * w;
+    if (!(fabs(r2 - 1.0) <= 2e-12)) {  // also catches NaN / inf
+        atomicOr(&st->flags, FLAG_BAD_POINT);
+        bin_of[i] = 0;
+        atomicAdd(&count[0], 1);
+        return;
+    }
+    int b = bin_index(x, y, w, G);
+    bin_of[i] = b;
+    atomicAdd(&count[b], 1);
+}
+
+__global__ void k_bin_scatter(const double *__restrict__ z, int n, const int *__restrict__ bin_of,
+                              int *__restrict__ cursor, P4 *__restrict__ zs, int *__restrict__ sidx) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int pos = atomicAdd(&cursor[bin_of[i]], 1);
+    sidx[pos] = i;
+    zs[pos] = P4{z[3 * (size_t)i], z[3 * (size_t)i + 1], z[3 * (size_t)i + 2], 0.0};
+}
+
+// exclusive scan of 2048-element tiles; writes tile totals
+__global__ void k_scan_tiles(const int *__restrict__ in, int *__restrict__ out, int len, int *__restrict__ totals) {
+    __shared__ int warp_sums[32];
+    int base = blockIdx.x * 2048;
+    int t = threadIdx.x;  // 1024 threads, 2 elements each
+    int i0 = base + 2 * t, i1 = i0 + 1;
+    int v0 = (i0 < len) ? in[i0] : 0;
+    int v1 = (i1 < len) ? in[i1] : 0;
+    int s = v0 + v1;
+    int lane = t & 31, w = t >> 5;
+    int incl = s;
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) warp_sums[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        int ws = warp_sums[lane];
+        int wi = ws;
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        warp_sums[lane] = wi - ws;  // exclusive
+    }
+    __syncthreads();
+    int excl = warp_sums[w] + incl - s;
+    if (i0 < len) out[i0] = excl;
+    if (i1 < len) out[i1] = excl + v0;
+    if (t == 1023 && totals) totals[blockIdx.x] = excl + s;
+}
+
+__global__ void k_scan_add(int *__restrict__ out, int len, const int *__restrict__ offs) {
+    int i = blockIdx.x * 2048 + threadIdx.x * 2;
+    int add = offs[blockIdx.x];
+    if (i < len) out[i] += add;
+    if (i + 1 < len) out[i + 1] += add;
+}
+
+// recursive exclusive scan; tmp must hold sum over levels of ceil(len/2048)
+void exclusive_scan(const int *in, int *out, int len, int *tmp, cudaStream_t s, int64_t *launches) {
+    int tiles = (len + 2047) / 2048;
+    if (tiles <= 1) {
+        k_scan_tiles<<<1, 1024, 0, s>>>(in, out, len, nullptr);
+        (*launches)++;
+        return;
+    }
+    int *totals = tmp, *tot_scan = tmp + tiles;
+    k_scan_tiles<<<tiles, 1024, 0, s>>>(in, out, len, totals);
+    exclusive_scan(totals, tot_scan, tiles, tmp + 2 * tiles, s, launches);
+    k_scan_add<<<tiles, 1024, 0, s>>>(out, len, tot_scan);
+    (*launches) += 2;
+}
+
+__global__ void k_set_total(int *start, int nbins, int n) { start[nbins] = n; }
+
+// ------------------------------------------------------------ k-nearest
+template <int K>
+struct KnnList {
+    double d[K];
+    int j[K];
+    int cnt;
+    __device__ __forceinline__ void push(double d2, int jj) {
+        if (cnt == K && (d2 > d[K - 1] || (d2 == d[K - 1] && jj > j[K - 1]))) return;
+        int p = (cnt < K) ? cnt++ : K - 1;
+        while (p > 0 && (d[p - 1] > d2 || (d[p - 1] == d2 && j[p - 1] > jj))) {
+            d[p] = d[p - 1];
+            j[p] = j[p - 1];
+            --p;
+        }
+        d[p] = d2;
+        j[p] = jj;
+    }
+};
+
+// Every generator p (bin order) with chord^2 to zi <= r2, found through the
+// bins that the cap {x : x.q >= cos theta} can reach (sin theta = S < 0.28).
+// For face (a, sign) the values s = x_b / |x_a| attained in the cap lie
+// between the roots of (q_b - s sign q_a)^2 = S^2 (1 + s^2): the planes of
+// constant s are great circles through the c axis, and one meets the cap iff
+// q's distance to it is at most S.
+template <int K>
+__device__ void cap_query(const Grid &g, V3 q, int self, double S, double r2, KnnList<K> &L, unsigned *flags) {
+    const double S2 = S * S;
+    const double qv[3] = {q.x, q.y, q.z};
+    for (int a = 0; a < 3; ++a) {
+        double qa = qv[a];
+        double A = qa * qa - S2;
+        if (A <= 0.0) continue;  // the cap cannot reach face a (|x_a| >= 1/sqrt3 there)
+        double sg = qa > 0.0 ? 1.0 : -1.0;
+        int face = 2 * a + (qa < 0.0 ? 1 : 0);
+        int lo[2], hi[2];
+        bool empty = false;
+        for (int r = 0; r < 2; ++r) {
+            double qb = qv[(a + 1 + r) % 3];
+            double disc = qa * qa + qb * qb - S2;
+            double rt = S * sqrt(fmax(disc, 0.0));
+            double s0 = (sg * qa * qb - rt) / A - 1e-9;
+            double s1 = (sg * qa * qb + rt) / A + 1e-9;
+            if (s0 > 1.0 || s1 < -1.0) { empty = true; break; }
+            s0 = fmax(s0, -1.0);
+            s1 = fmin(s1, 1.0);
+            lo[r] = min(max((int)floor((s0 + 1.0) * 0.5 * g.G), 0), g.G - 1);
+            hi[r] = min(max((int)floor((s1 + 1.0) * 0.5 * g.G), 0), g.G - 1);
+        }
+        if (empty) continue;
+        for (int iv = lo[1]; iv <= hi[1]; ++iv) {
+            int row = (face * g.G + iv) * g.G;
+            int p0 = g.bstart[row + lo[0]], p1 = g.bstart[row + hi[0] + 1];
+            for (int p = p0; p < p1; ++p) {
+                if (p == self) continue;
+                V3 d = sub(ld(g.zs + p), q);
+                double d2 = dot(d, d);
+                if (d2 == 0.0) atomicOr(flags, FLAG_DUPLICATE);
+                if (d2 <= r2) L.push(d2, p);
+            }
+        }
+    }
+}
+
+template <int K>
+__device__ void all_query(const Grid &g, V3 q, int self, KnnList<K> &L, unsigned *flags) {
+    for (int p = 0; p < g.n; ++p) {
+        if (p == self) continue;
+        V3 d = sub(ld(g.zs + p), q);
+        double d2 = dot(d, d);
+        if (d2 == 0.0) atomicOr(flags, FLAG_DUPLICATE);
+        L.push(d2, p);
+    }
+}
+
+// ---------------------------------------------------------------- clipping
+// Convex polygon in the gnomonic plane at z_i: vertex k = (u, w); edge k runs
+// from vertex k to vertex k+1 on line k: a u + b w <= c, whose neighbour is
+// nb (bin-order index; < 0 for the starting square).  Vertex k is the
+// intersection of lines k-1 and k, computed from those two lines only.
+template <int VMAX>
+struct Poly {
+    double u[2][VMAX], w[2][VMAX], a[2][VMAX], b[2][VMAX], c[2][VMAX];
+    int nb[2][VMAX];
+    int nv, cur;
+};
+
+__device__ __forceinline__ void meet(double a1, double b1, double c1, double a2, double b2, double c2, double &u,
+                                     double &w) {
+    double det = a1 * b2 - a2 * b1;
+    u = (c1 * b2 - c2 * b1) / det;
+    w = (a1 * c2 - a2 * c1) / det;
+}
+
+__device__ __forceinline__ double chord2_of(double u, double w) {
+    // |normalize(z_i + u e1 + w e2) - z_i|^2 = 2 - 2/sqrt(1 + r^2), written without cancellation
+    double r2 = u * u + w * w;
+    double q = sqrt(1.0 + r2);
+    return 2.0 * r2 / (q * (1.0 + q));
+}
+
+// returns 1 if the polygon changed, 0 if not, -1 on capacity / empty errors
+template <int VMAX>
+__device__ int clip(Poly<VMAX> &P, double la, double lb, double lc, int nbj, unsigned *flags,
+                    unsigned long long *amb) {
+    const int c0 = P.cur, nv = P.nv;
+    unsigned long long out = 0ull;
+    int namb = 0;
+    for (int k = 0; k < nv; ++k) {
+        double uk = P.u[c0][k], wk = P.w[c0][k];
+        double sd = la * uk + lb * wk - lc;
+        double mag = fabs(la * uk) + fabs(lb * wk) + fabs(lc);
+        if (fabs(sd) <= 1e-14 * mag) ++namb;
+        if (sd > 0.0) out |= (1ull << k);
+    }
+    if (namb) atomicAdd(amb, (unsigned long long)namb);
+    if (!out) return 0;
+    unsigned long long full = (nv == 64) ? ~0ull : ((1ull << nv) - 1ull);
+    if (out == full) {
+        atomicOr(flags, FLAG_EMPTY);
+        return -1;
+    }
+    // the outside vertices form one cyclic run k0..k1 (convexity)
+    int k0 = -1, runs = 0;
+    for (int k = 0; k < nv; ++k) {
+        int prev = (k == 0) ? nv - 1 : k - 1;
+        if (((out >> k) & 1ull) && !((out >> prev) & 1ull)) {
+            if (k0 < 0) k0 = k;
+            ++runs;
+        }
+    }
+    if (runs > 1) atomicOr(flags, FLAG_NONCONVEX);
+    int k1 = k0, runlen = 1;
+    while (true) {
+        int nx = (k1 + 1 == nv) ? 0 : k1 + 1;
+        if (!((out >> nx) & 1ull)) break;
+        k1 = nx;
+        ++runlen;
+    }
+    int nnew = nv - runlen + 2;
+    if (nnew > VMAX) return -1;
+    const int c1 = c0 ^ 1;
+    int kin = (k0 == 0) ? nv - 1 : k0 - 1;  // last inside vertex before the run
+    double pu, pw, qu, qw;
+    meet(P.a[c0][kin], P.b[c0][kin], P.c[c0][kin], la, lb, lc, pu, pw);
+    meet(la, lb, lc, P.a[c0][k1], P.b[c0][k1], P.c[c0][k1], qu, qw);
+    P.u[c1][0] = pu; P.w[c1][0] = pw;
+    P.a[c1][0] = la; P.b[c1][0] = lb; P.c[c1][0] = lc; P.nb[c1][0] = nbj;
+    P.u[c1][1] = qu; P.w[c1][1] = qw;
+    P.a[c1][1] = P.a[c0][k1]; P.b[c1][1] = P.b[c0][k1]; P.c[c1][1] = P.c[c0][k1]; P.nb[c1][1] = P.nb[c0][k1];
+    int o = 2;
+    int k = (k1 + 1 == nv) ? 0 : k1 + 1;
+    for (int cnt = 0; cnt < nv - runlen; ++cnt) {
+        P.u[c1][o] = P.u[c0][k]; P.w[c1][o] = P.w[c0][k];
+        P.a[c1][o] = P.a[c0][k]; P.b[c1][o] = P.b[c0][k]; P.c[c1][o] = P.c[c0][k];
+        P.nb[c1][o] = P.nb[c0][k];
+        ++o;
+        k = (k + 1 == nv) ? 0 : k + 1;
+    }
+    P.nv = nnew;
+    P.cur = c1;
+    return 1;
+}
+
+// ------------------------------------------------------------- quadrature
+__device__ __forceinline__ double rho_at(const Density &r, V3 p) {
+    switch (r.kind) {
+    case 0:
+        return 1.0;
+    case 1: {
+        double z2 = p.z * p.z;
+        return (1.0 - r.gamma) * z2 * z2 + r.gamma;
+    }
+    default: {
+        V3 xc = mk(r.xc0, r.xc1, r.xc2);
+        V3 cr = crs(p, xc);
+        double d = atan2(sqrt(dot(cr, cr)), dot(p, xc));
+        double v = 0.5 * (1.0 - r.gamma) * (tanh((r.beta - d) / r.alpha) + 1.0) + r.gamma;
+        if (r.kind == 3) { v = v * v; v = v * v; }
+        return v;
+    }
+    }
+}
+
+struct Acc {
+    double m, cx, cy, cz, e;
+};
+
+// signed spherical triangle (A, B, C) with the 7-point rule; A = z_i
+__device__ __forceinline__ void tri(const Density &rho, V3 A, V3 B, V3 C, Acc &acc) {
+    V3 cr = crs(sub(B, A), sub(C, A));
+    double det = dot(A, cr);
+    double den = 1.0 + dot(A, B) + dot(B, C) + dot(C, A);
+    double area = 2.0 * atan2(det, den);
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+        V3 x = add(add(scl(A, kQb[k][0]), scl(B, kQb[k][1])), scl(C, kQb[k][2]));
+        V3 p = scl(x, 1.0 / sqrt(dot(x, x)));
+        double wr = kQw[k] * area * rho_at(rho, p);
+        V3 dp = sub(p, A);
+        acc.m += wr;
+        acc.cx += wr * p.x;
+        acc.cy += wr * p.y;
+        acc.cz += wr * p.z;
+        acc.e += wr * dot(dp, dp);
+    }
+}
+
+// --------------------------------------------------------------- the cell
+// mode 0: positions 0..n-1 are the work; otherwise the work is list[0..*count)
+// scan_all: consider every generator (small n / last resort)
+template <int K, int VMAX>
+__global__ void __launch_bounds__(128) k_cells(Grid g, Density rho, CellOut out, const int *__restrict__ list,
+                                               const unsigned *__restrict__ list_count, int *__restrict__ next_list,
+                                               unsigned *__restrict__ next_count, int last_pass, int scan_all,
+                                               DevStatus *st) {
+    int nwork = list ? (int)*list_count : g.n;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nwork; t += gridDim.x * blockDim.x) {
+        const int p = list ? list[t] : t;
+        const V3 zi = ld(g.zs + p);
+        const int i = g.sidx[p];
+
+        // ---- neighbours: nearest first, certified bound D2 on the rest
+        KnnList<K> L;
+        L.cnt = 0;
+        double D2;
+        if (scan_all || g.n - 1 <= K) {
+            all_query<K>(g, zi, p, L, &st->flags);
+            D2 = (L.cnt == g.n - 1) ? INFINITY : L.d[K - 1];
+        } else {
+            const double thmax = 0.28379410920832787;  // asin(0.28)
+            double th;
+            float hint = out.radius ? out.radius[i] : 0.0f;
+            if (hint > 0.0f && !last_pass) {
+                th = 1.1 * 2.0 * asin(fmin(0.5 * (double)hint, 1.0));
+            } else {
+                // local density from the own bin: lambda = count / solid angle
+                int b = bin_index(zi.x, zi.y, zi.z, g.G);
+                int cb = g.bstart[b + 1] - g.bstart[b];
+                double ax = fabs(zi.x), ay = fabs(zi.y), az = fabs(zi.z);
+                double am = fmax(ax, fmax(ay, az));
+                double s2 = (ax * ax + ay * ay + az * az) / (am * am);  // 1 + s^2 + t^2
+                double omega = (4.0 / ((double)g.G * g.G)) / (s2 * sqrt(s2));
+                double lam = fmax((double)cb, 1.0) / omega;
+                th = sqrt(1.5 * K / (3.141592653589793 * lam));
+                if (last_pass) th *= 2.0;
+            }
+            th = fmin(th, thmax);
+            double r2;
+            for (int attempt = 0;; ++attempt) {
+                double S = sin(th);
+                double hs = sin(0.5 * th);
+                r2 = 4.0 * hs * hs;
+                L.cnt = 0;
+                cap_query<K>(g, zi, p, S, r2, L, &st->flags);
+                if (L.cnt == K || th >= thmax || attempt > 8) break;
+                double grow = (L.cnt > 0) ? sqrt(1.3 * K / (double)L.cnt) : 2.0;
+                th = fmin(th * fmax(grow, 1.25), thmax);
+            }
+            D2 = (L.cnt == K) ? L.d[K - 1] : r2;
+        }
+        if (out.radius) out.radius[i] = (float)sqrt(L.cnt ? L.d[L.cnt - 1] : 0.0);
+
+        // ---- gnomonic frame at z_i: e1 x e2 = z_i
+        V3 ax;
+        {
+            double fx = fabs(zi.x), fy = fabs(zi.y), fz = fabs(zi.z);
+            ax = (fx <= fy && fx <= fz) ? mk(1, 0, 0) : ((fy <= fz) ? mk(0, 1, 0) : mk(0, 0, 1));
+        }
+        const V3 e1 = unit(crs(zi, ax));
+        const V3 e2 = crs(zi, e1);
+
+        // ---- clip, nearest first, with the security radius
+        Poly<VMAX> P;
+        P.cur = 0;
+        P.nv = 4;
+        {
+            // lines: 0 right (u <= L), 1 top (w <= L), 2 left (-u <= L), 3 bottom (-w <= L)
+            const double la[4] = {1, 0, -1, 0}, lb[4] = {0, 1, 0, -1};
+            const double vu[4] = {kBoxL, kBoxL, -kBoxL, -kBoxL}, vw[4] = {-kBoxL, kBoxL, kBoxL, -kBoxL};
+            for (int k = 0; k < 4; ++k) {
+                P.a[0][k] = la[k]; P.b[0][k] = lb[k]; P.c[0][k] = kBoxL; P.nb[0][k] = -1 - k;
+                P.u[0][k] = vu[k]; P.w[0][k] = vw[k];
+            }
+        }
+        double R2 = chord2_of(kBoxL, kBoxL);
+        bool ok = true, early = false;
+        for (int k = 0; k < L.cnt; ++k) {
+            if (L.d[k] > 4.0 * R2 * kCertMargin) { early = true; break; }
+            const int pj = L.j[k];
+            const V3 d = sub(ld(g.zs + pj), zi);
+            int r = clip<VMAX>(P, dot(e1, d), dot(e2, d), -dot(zi, d), pj, &st->flags, &st->ambiguous);
+            if (r < 0) { ok = false; break; }
+            if (r > 0) {
+                R2 = 0.0;
+                for (int v = 0; v < P.nv; ++v) R2 = fmax(R2, chord2_of(P.u[P.cur][v], P.w[P.cur][v]));
+            }
+        }
+        bool boxed = false;
+        for (int v = 0; v < P.nv; ++v) boxed |= (P.nb[P.cur][v] < 0);
+        bool certified = ok && !boxed && (early || D2 > 4.0 * R2 * kCertMargin);
+        if (ok && boxed && D2 == INFINITY) {
+            atomicOr(&st->flags, FLAG_UNBOUNDED);  // every point seen and the cell is still open
+            certified = false;
+        }
+        if (!certified) {
+            if (last_pass) {
+                atomicOr(&st->flags, ok ? FLAG_EXHAUSTED : FLAG_VMAX);
+            } else {
+                unsigned pos = atomicAdd(next_count, 1u);
+                next_list[pos] = p;
+            }
+            continue;
+        }
+
+        // ---- integrate over the signed sub-triangles of each edge, starting
+        // at the edge of the smallest neighbour id so that the summation
+        // order does not depend on the clipping history
+        const int c = P.cur, nv = P.nv;
+        int k0 = 0, best = g.sidx[P.nb[c][0]];
+        for (int k = 1; k < nv; ++k) {
+            int id = g.sidx[P.nb[c][k]];
+            if (id < best) { best = id; k0 = k; }
+        }
+        Acc acc = {0, 0, 0, 0, 0};
+        V3 vfirst = unit(add(zi, add(scl(e1, P.u[c][k0]), scl(e2, P.w[c][k0]))));
+        V3 va = vfirst;
+        for (int t = 0; t < nv; ++t) {
+            const int k = (k0 + t < nv) ? k0 + t : k0 + t - nv;
+            const int k1 = (k + 1 == nv) ? 0 : k + 1;
+            V3 vb = (t + 1 == nv) ? vfirst : unit(add(zi, add(scl(e1, P.u[c][k1]), scl(e2, P.w[c][k1]))));
+            V3 mu = unit(add(zi, ld(g.zs + P.nb[c][k])));
+            tri(rho, zi, va, mu, acc);
+            tri(rho, zi, mu, vb, acc);
+            va = vb;
+        }
+        const double cz = acc.cx * zi.x + acc.cy * zi.y + acc.cz * zi.z;
+        if (!(cz > 0.0)) atomicOr(&st->flags, FLAG_NONPOSITIVE);
+        if (out.grad) {
+            out.grad[3 * (size_t)i] = 2.0 * cz * zi.x - 2.0 * acc.cx;
+            out.grad[3 * (size_t)i + 1] = 2.0 * cz * zi.y - 2.0 * acc.cy;
+            out.grad[3 * (size_t)i + 2] = 2.0 * cz * zi.z - 2.0 * acc.cz;
+        }
+        if (out.hdiag) out.hdiag[i] = 1.0 / (2.0 * cz);
+        if (out.mass) out.mass[i] = acc.m;
+        if (out.moment) {
+            out.moment[3 * (size_t)i] = acc.cx;
+            out.moment[3 * (size_t)i + 1] = acc.cy;
+            out.moment[3 * (size_t)i + 2] = acc.cz;
+        }
+        if (out.fcell) out.fcell[i] = acc.e;
+        if (out.deg) {
+            out.deg[i] = nv;
+            if (nv <= out.max_deg)
+                for (int t = 0; t < nv; ++t)
+                    out.nbr[(size_t)i * out.max_deg + t] = g.sidx[P.nb[c][(k0 + t < nv) ? k0 + t : k0 + t - nv]];
+        }
+    }
+}
+
+}  // namespace
+
+void bin_points(const double *z, int n, int G, int *bin_of, int *count, int *start, int *cursor, int *scan_tmp,
+                P4 *zs, int *sidx, DevStatus *st, cudaStream_t s, int64_t *launches) {
+    const int nbins = 6 * G * G;
+    cudaMemsetAsync(count, 0, sizeof(int) * nbins, s);
+    int blocks = (n + 255) / 256;
+    k_bin_count<<<blocks, 256, 0, s>>>(z, n, G, bin_of, count, st);
+    exclusive_scan(count, start, nbins, scan_tmp, s, launches);
+    k_set_total<<<1, 1, 0, s>>>(start, nbins, n);
+    cudaMemcpyAsync(cursor, start, sizeof(int) * nbins, cudaMemcpyDeviceToDevice, s);
+    k_bin_scatter<<<blocks, 256, 0, s>>>(z, n, bin_of, cursor, zs, sidx);
+    (*launches) += 3;
+}
+
+void cell_passes(const Grid &g, const Density &rho, const CellOut &out, int *list0, int *list1, int *list2,
+                 DevStatus *st, int knn_k0, int knn_kmax, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1,
+                 int64_t *launches, int64_t *cell_launches) {
+    (void)list0;
+    (void)knn_kmax;
+    const int blocks0 = (g.n + 127) / 128;
+    if (ev0) cudaEventRecord(ev0, s);
+    if (knn_k0 <= 16)
+        k_cells<16, 32><<<blocks0, 128, 0, s>>>(g, rho, out, nullptr, nullptr, list1, &st->retry_count[0], 0, 0, st);
+    else
+        k_cells<32, 32><<<blocks0, 128, 0, s>>>(g, rho, out, nullptr, nullptr, list1, &st->retry_count[0], 0, 0, st);
+    if (ev1) cudaEventRecord(ev1, s);
+    // retry passes: sized for the worst case, they read their work count on the device
+    const int rblocks = 2 * 152;
+    k_cells<64, 64><<<rblocks, 64, 0, s>>>(g, rho, out, list1, &st->retry_count[0], list2, &st->retry_count[1], 0, 0,
+                                           st);
+    int scan_all = g.n <= 20000 ? 1 : 0;
+    k_cells<128, 64><<<rblocks, 64, 0, s>>>(g, rho, out, list2, &st->retry_count[1], list2 + 0, &st->retry_count[2],
+                                            1, scan_all, st);
+    (*launches) += 3;
+    (*cell_launches) += 3;
+}
+
+}  // namespace scvt

@@ -1,0 +1,285 @@
+// lbfgs.cu -- HBM-streaming kernels of the LBFGS iteration and the
+// deterministic reductions.
+//
+// Every reduction uses a fixed partition: the index range is cut into
+// reduce_blocks(n) contiguous chunks, each summed by one block in a fixed
+// order, and the chunk sums are added by one block in a fixed order.  The
+// result therefore depends only on n and the data, never on launch timing or
+// on the binning of an evaluation.
+//
+// The two-loop recursion (Sec. 2.2.2) keeps its scalars alpha_k, beta_k on
+// the device: each pass fuses the axpy of one step with the dot product of
+// the next, and a one-block kernel turns the chunk sums into the next
+// scalar, so the whole direction is computed without a host round trip.
+#include <math.h>
+
+#include "scvt_internal.cuh"
+
+namespace scvt {
+
+namespace {
+
+constexpr int kRT = 256;  // threads of the chunk kernels
+
+template <int NQ>
+__device__ __forceinline__ void block_sum_store(double (&v)[NQ], double *dst) {
+    __shared__ double sh[NQ][kRT / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        double x = v[q];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) sh[q][w] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            double s = 0.0;
+            for (int k = 0; k < kRT / 32; ++k) s += sh[q][k];
+            dst[q] = s;
+        }
+    }
+}
+
+__device__ __forceinline__ void chunk_of(int64_t n, int64_t &b0, int64_t &b1) {
+    int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+    b0 = (int64_t)blockIdx.x * chunk;
+    b1 = b0 + chunk < n ? b0 + chunk : n;
+}
+
+__global__ void k_reduce_eval(int n, const double *__restrict__ fcell, const double *__restrict__ g,
+                              const double *__restrict__ q, const double *__restrict__ nrm,
+                              double *__restrict__ partials) {
+    int64_t b0, b1;
+    chunk_of(n, b0, b1);
+    double v[3] = {0.0, 0.0, 0.0};
+    for (int64_t i = b0 + threadIdx.x; i < b1; i += kRT) {
+        double gx = g[3 * i], gy = g[3 * i + 1], gz = g[3 * i + 2];
+        v[0] += fcell[i];
+        v[1] += gx * gx + gy * gy + gz * gz;
+        if (q) v[2] += (gx * q[3 * i] + gy * q[3 * i + 1] + gz * q[3 * i + 2]) / nrm[i];
+    }
+    block_sum_store<3>(v, partials + 4 * blockIdx.x);
+}
+
+// one block: out[q] = sum_b partials[stride*b + q] in a fixed order
+template <int NQ>
+__global__ void k_finish(const double *__restrict__ partials, int nb, int stride, double *out) {
+    double v[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) v[q] = 0.0;
+    for (int b = threadIdx.x; b < nb; b += kRT)
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) v[q] += partials[(size_t)stride * b + q];
+    double res[NQ];
+    block_sum_store<NQ>(v, res);
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) out[q] = res[q];
+}
+
+// out = scale * sum (scale may be null); if minus_from: out = *minus_from - out
+__global__ void k_finish_scalar(const double *__restrict__ partials, int nb, const double *scale,
+                                const double *minus_from, double *out) {
+    double v[1] = {0.0};
+    for (int b = threadIdx.x; b < nb; b += kRT) v[0] += partials[b];
+    double res[1];
+    block_sum_store<1>(v, res);
+    if (threadIdx.x == 0) {
+        double r = scale ? scale[0] * res[0] : res[0];
+        if (minus_from) r = minus_from[0] - r;
+        out[0] = r;
+    }
+}
+
+__global__ void k_dot(int64_t len, const double *__restrict__ x, const double *__restrict__ y,
+                      double *__restrict__ partials) {
+    int64_t b0, b1;
+    chunk_of(len, b0, b1);
+    double v[1] = {0.0};
+    for (int64_t i = b0 + threadIdx.x; i < b1; i += kRT) v[0] += x[i] * y[i];
+    block_sum_store<1>(v, partials + blockIdx.x);
+}
+
+// q = -g (if h: q = -h g); partial dot w.q
+__global__ void k_neg(int64_t len, const double *__restrict__ g, const double *__restrict__ h,
+                      double *__restrict__ q, const double *__restrict__ w, double *__restrict__ partials) {
+    int64_t b0, b1;
+    chunk_of(len, b0, b1);
+    double v[1] = {0.0};
+    for (int64_t i = b0 + threadIdx.x; i < b1; i += kRT) {
+        double x = -g[i];
+        if (h) x *= h[i / 3];
+        q[i] = x;
+        v[0] += w[i] * x;
+    }
+    block_sum_store<1>(v, partials + blockIdx.x);
+}
+
+// q += sign * coef * x; if h: q *= h (per generator); partial dot w.q
+__global__ void k_axpy(int64_t len, double *__restrict__ q, const double *__restrict__ coef, double sign,
+                       const double *__restrict__ x, const double *__restrict__ h, const double *__restrict__ w,
+                       double *__restrict__ partials) {
+    int64_t b0, b1;
+    chunk_of(len, b0, b1);
+    const double a = sign * coef[0];
+    double v[1] = {0.0};
+    for (int64_t i = b0 + threadIdx.x; i < b1; i += kRT) {
+        double t = q[i] + a * x[i];
+        if (h) t *= h[i / 3];
+        q[i] = t;
+        v[0] += w[i] * t;
+    }
+    block_sum_store<1>(v, partials + blockIdx.x);
+}
+
+__global__ void k_trial(int n, const double *__restrict__ z, const double *__restrict__ q, double alpha,
+                        double *__restrict__ zt, double *__restrict__ nrm) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double x = z[3 * (size_t)i] + alpha * q[3 * (size_t)i];
+    double y = z[3 * (size_t)i + 1] + alpha * q[3 * (size_t)i + 1];
+    double w = z[3 * (size_t)i + 2] + alpha * q[3 * (size_t)i + 2];
+    double r = sqrt(x * x + y * y + w * w);
+    zt[3 * (size_t)i] = x / r;
+    zt[3 * (size_t)i + 1] = y / r;
+    zt[3 * (size_t)i + 2] = w / r;
+    nrm[i] = r;
+}
+
+__global__ void k_lloyd(int n, const double *__restrict__ c, double *__restrict__ zout) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double x = c[3 * (size_t)i], y = c[3 * (size_t)i + 1], w = c[3 * (size_t)i + 2];
+    double r = sqrt(x * x + y * y + w * w);
+    zout[3 * (size_t)i] = x / r;
+    zout[3 * (size_t)i + 1] = y / r;
+    zout[3 * (size_t)i + 2] = w / r;
+}
+
+// s = zt - z, y = gt - g; partial sums of y.s, y.y, s.s; max |s_i|
+__global__ void k_accept(int n, const double *__restrict__ zt, const double *__restrict__ z,
+                         const double *__restrict__ gt, const double *__restrict__ g, double *__restrict__ S,
+                         double *__restrict__ Y, double *__restrict__ partials, unsigned long long *maxmove) {
+    int64_t b0, b1;
+    chunk_of(n, b0, b1);
+    double v[3] = {0.0, 0.0, 0.0};
+    double mv = 0.0;
+    for (int64_t i = b0 + threadIdx.x; i < b1; i += kRT) {
+        double s2 = 0.0;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            double s = zt[3 * i + d] - z[3 * i + d];
+            double y = gt[3 * i + d] - g[3 * i + d];
+            S[3 * i + d] = s;
+            Y[3 * i + d] = y;
+            v[0] += y * s;
+            v[1] += y * y;
+            v[2] += s * s;
+            s2 += s * s;
+        }
+        mv = fmax(mv, s2);
+    }
+    // nonnegative doubles order like their bit patterns
+    if (mv > 0.0) atomicMax(maxmove, (unsigned long long)__double_as_longlong(sqrt(mv)));
+    block_sum_store<3>(v, partials + 4 * blockIdx.x);
+}
+
+__global__ void k_set_rho(double *rho, const DevStatus *st) { rho[0] = 1.0 / st->dots[0]; }
+
+__global__ void k_differs(int64_t len, const double *__restrict__ a, const double *__restrict__ b, unsigned *flag) {
+    int any = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x)
+        any |= (__double_as_longlong(a[i]) != __double_as_longlong(b[i]));
+    if (__syncthreads_or(any) && threadIdx.x == 0) atomicOr(flag, 1u);
+}
+
+}  // namespace
+
+int reduce_blocks(int64_t n) {
+    int64_t b = (n + 4095) / 4096;
+    if (b < 1) b = 1;
+    if (b > 1024) b = 1024;
+    return (int)b;
+}
+
+void reduce_eval(int n, const double *fcell, const double *grad, const double *q, const double *nrm,
+                 double *partials, DevStatus *st, cudaStream_t s, int64_t *launches) {
+    int nb = reduce_blocks(n);
+    k_reduce_eval<<<nb, kRT, 0, s>>>(n, fcell, grad, q, nrm, partials);
+    k_finish<3><<<1, kRT, 0, s>>>(partials, nb, 4, st->red);
+    (*launches) += 2;
+}
+
+void dot_to(int64_t len, const double *x, const double *y, double *partials, double *out, cudaStream_t s,
+            int64_t *launches) {
+    int nb = reduce_blocks(len);
+    k_dot<<<nb, kRT, 0, s>>>(len, x, y, partials);
+    k_finish_scalar<<<1, kRT, 0, s>>>(partials, nb, nullptr, nullptr, out);
+    (*launches) += 2;
+}
+
+void trial_point(int n, const double *z, const double *q, double alpha, double *zt, double *nrm, cudaStream_t s,
+                 int64_t *launches) {
+    k_trial<<<(n + 255) / 256, 256, 0, s>>>(n, z, q, alpha, zt, nrm);
+    (*launches)++;
+}
+
+void lloyd_project(int n, const double *c, double *zout, cudaStream_t s, int64_t *launches) {
+    k_lloyd<<<(n + 255) / 256, 256, 0, s>>>(n, c, zout);
+    (*launches)++;
+}
+
+void accept_pair(int n, const double *zt, const double *z, const double *gt, const double *g, double *S, double *Y,
+                 double *partials, DevStatus *st, cudaStream_t s, int64_t *launches) {
+    int nb = reduce_blocks(n);
+    k_accept<<<nb, kRT, 0, s>>>(n, zt, z, gt, g, S, Y, partials, &st->maxmove_bits);
+    k_finish<3><<<1, kRT, 0, s>>>(partials, nb, 4, st->dots);
+    (*launches) += 2;
+}
+
+void vec_differs(int64_t len, const double *a, const double *b, DevStatus *st, cudaStream_t s, int64_t *launches) {
+    cudaMemsetAsync(&st->differs, 0, sizeof(unsigned), s);
+    k_differs<<<4 * 152, 256, 0, s>>>(len, a, b, &st->differs);
+    (*launches)++;
+}
+
+void set_rho(double *rho_dev, int k, const DevStatus *st, cudaStream_t s, int64_t *launches) {
+    k_set_rho<<<1, 1, 0, s>>>(rho_dev + k, st);
+    (*launches)++;
+}
+
+void two_loop(int n, const double *g, const double *h, int count, const double *const *S, const double *const *Y,
+              const double *const *rho, double *q, double *partials, double *scal, DevStatus *st, cudaStream_t s,
+              int64_t *launches) {
+    const int64_t len = 3 * (int64_t)n;
+    const int nb = reduce_blocks(len);
+    double *alpha = scal, *coef = scal + 64;
+    if (count == 0) {
+        k_neg<<<nb, kRT, 0, s>>>(len, g, h, q, g, partials);
+        k_finish_scalar<<<1, kRT, 0, s>>>(partials, nb, nullptr, nullptr, &st->dots[3]);
+        (*launches) += 2;
+        return;
+    }
+    // backward: newest (count-1) .. oldest (0)
+    k_neg<<<nb, kRT, 0, s>>>(len, g, nullptr, q, S[count - 1], partials);
+    (*launches)++;
+    for (int k = count - 1; k >= 0; --k) {
+        k_finish_scalar<<<1, kRT, 0, s>>>(partials, nb, rho[k], nullptr, alpha + k);
+        const double *w = (k > 0) ? S[k - 1] : Y[0];
+        k_axpy<<<nb, kRT, 0, s>>>(len, q, alpha + k, -1.0, Y[k], (k > 0) ? nullptr : h, w, partials);
+        (*launches) += 2;
+    }
+    // forward: oldest .. newest
+    for (int k = 0; k < count; ++k) {
+        k_finish_scalar<<<1, kRT, 0, s>>>(partials, nb, rho[k], alpha + k, coef + k);
+        const double *w = (k + 1 < count) ? Y[k + 1] : g;
+        k_axpy<<<nb, kRT, 0, s>>>(len, q, coef + k, 1.0, S[k], nullptr, w, partials);
+        (*launches) += 2;
+    }
+    k_finish_scalar<<<1, kRT, 0, s>>>(partials, nb, nullptr, nullptr, &st->dots[3]);
+    (*launches)++;
+}
+
+}  // namespace scvt

@@ -1,0 +1,102 @@
+// scvt_internal.cuh -- shared definitions of the CUDA library (not installed).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "scvt.h"
+
+namespace scvt {
+
+// a generator in bin order: 32-byte aligned (x, y, z, unused)
+struct alignas(32) P4 {
+    double x, y, z, w;
+};
+
+// ---- status bits written by the kernels (DevStatus::flags) ----
+enum : unsigned {
+    FLAG_BAD_POINT = 1u,      // non-finite or |z|^2 off 1 by more than 2e-12
+    FLAG_DUPLICATE = 2u,      // two identical generators
+    FLAG_UNBOUNDED = 4u,      // a cell reached the bounding box with every point considered
+    FLAG_EXHAUSTED = 8u,      // a cell failed certification in the last retry pass
+    FLAG_VMAX = 16u,          // polygon vertex capacity exceeded in the last pass
+    FLAG_NONPOSITIVE = 32u,   // c_i . z_i <= 0
+    FLAG_NONCONVEX = 64u,     // clip pattern with more than one outside run
+    FLAG_EMPTY = 128u,        // clip removed every vertex
+};
+
+// Device-side status of one evaluation; reset before each evaluation and
+// copied to the host with the reduction results in a single transfer.
+struct DevStatus {
+    unsigned flags;
+    unsigned retry_count[3];        // cells queued for retry pass 1, 2, (3 = failed)
+    unsigned long long ambiguous;   // clip decisions within rounding of zero
+    double red[4];                  // sum F_i, sum |g_i|^2, phi'(alpha), spare
+    unsigned long long maxmove_bits;// max_i |s_i| as the bits of a nonnegative double
+    double dots[4];                 // y.s, y.y, s.s, g.q
+    unsigned differs;               // set by vec_differs
+};
+
+// Geometry of one evaluation (device pointers).
+struct Grid {
+    int n;
+    int G;                  // bins per face edge
+    int nbins;              // 6 G^2
+    const P4 *zs;      // generators in bin order (w unused)
+    const int *sidx;        // bin-order position -> original index
+    const int *bstart;      // nbins + 1 offsets into zs
+};
+
+struct Density {
+    int kind;
+    double gamma, alpha, beta;
+    double xc0, xc1, xc2;
+};
+
+// Per-cell outputs, indexed by ORIGINAL generator index.  Any may be null.
+struct CellOut {
+    double *grad;    // 3n
+    double *hdiag;   // n
+    double *mass;    // n
+    double *moment;  // 3n
+    double *fcell;   // n
+    int *deg;        // n
+    int *nbr;        // n * max_deg (original ids)
+    int max_deg;
+    float *radius;   // n, kNN search radius hint of the next evaluation (in/out)
+};
+
+// ---- binning (cells.cu) ----
+void bin_points(const double *z, int n, int G, int *bin_of, int *count, int *start, int *cursor,
+                int *scan_tmp, P4 *zs, int *sidx, DevStatus *st, cudaStream_t s, int64_t *launches);
+
+// ---- cell passes (cells.cu) ----
+// pass 0 over all cells; passes 1..2 over the retry lists.
+void cell_passes(const Grid &g, const Density &rho, const CellOut &out, int *retry_list0, int *retry_list1,
+                 int *retry_list2, DevStatus *st, int knn_k0, int knn_kmax, cudaStream_t s,
+                 cudaEvent_t ev0, cudaEvent_t ev1, int64_t *launches, int64_t *cell_launches);
+
+// ---- reductions and vector kernels (lbfgs.cu) ----
+int reduce_blocks(int64_t n);
+// red[0] = sum fcell, red[1] = sum |g|^2, red[2] = sum g_i.q_i / nrm_i (if q)
+void reduce_eval(int n, const double *fcell, const double *grad, const double *q, const double *nrm,
+                 double *partials, DevStatus *st, cudaStream_t s, int64_t *launches);
+// out[slot] = sum x.y (deterministic), optionally scaled: out[slot] = scale[si] * sum
+void dot_to(int64_t len, const double *x, const double *y, double *partials, double *out, cudaStream_t s,
+            int64_t *launches);
+void trial_point(int n, const double *z, const double *q, double alpha, double *zt, double *nrm, cudaStream_t s,
+                 int64_t *launches);
+void lloyd_project(int n, const double *c, double *zout, cudaStream_t s, int64_t *launches);
+void accept_pair(int n, const double *zt, const double *z, const double *gt, const double *g, double *S, double *Y,
+                 double *partials, DevStatus *st, cudaStream_t s, int64_t *launches);
+// q = -H g by the two-loop recursion; pairs are given oldest first as host
+// arrays of device pointers, rho[k] -> 1/(y_k.s_k) on the device;
+// scal: device scratch of 128 doubles.  Leaves g.q in st->dots[3].
+void two_loop(int n, const double *g, const double *h, int count, const double *const *S, const double *const *Y,
+              const double *const *rho, double *q, double *partials, double *scal, DevStatus *st, cudaStream_t s,
+              int64_t *launches);
+void set_rho(double *rho_dev, int k, const DevStatus *st, cudaStream_t s, int64_t *launches);
+// st->differs = 1 if a[i] != b[i] for some i < len (bitwise on the values)
+void vec_differs(int64_t len, const double *a, const double *b, DevStatus *st, cudaStream_t s, int64_t *launches);
+
+}  // namespace scvt

@@ -1,0 +1,150 @@
+"""Convenience wrapper over the C ABI for PyTorch users.
+
+Tensors supply device memory and the CUDA stream only; every step of the
+computation runs in the CUDA library.  Arrays are float64, contiguous,
+shaped (N, 3) for points and vectors and (N,) for per-point scalars.
+Numpy arrays (host memory) are accepted too: the library stages them.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import capi
+from .inputs import Density
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, torch.Tensor):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data
+    raise TypeError("expected a torch.Tensor or numpy.ndarray")
+
+
+def _density(d: Density) -> capi.scvt_density:
+    r = capi.scvt_density()
+    r.kind, r.gamma, r.alpha, r.beta = int(d.kind), float(d.gamma), float(d.alpha), float(d.beta)
+    for k in range(3):
+        r.xc[k] = float(d.xc[k])
+    return r
+
+
+class Engine:
+    def __init__(self, n: int, density: Density, lbfgs_m: int = 7, knn_k0: int = 0,
+                 device: int | torch.device = 0, stream: torch.cuda.Stream | None = None):
+        self.n = int(n)
+        self.device = torch.device("cuda", device) if isinstance(device, int) else torch.device(device)
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
+        cfg = capi.scvt_config()
+        cfg.n = self.n
+        cfg.rho = _density(density)
+        cfg.quad_points = 7
+        cfg.precision = 0
+        cfg.lbfgs_m = int(lbfgs_m)
+        cfg.knn_k0 = int(knn_k0)
+        cfg.knn_kmax = 0
+        with torch.cuda.device(self.device):
+            self._h = capi.scvt_create(cfg, self.stream.cuda_stream)
+
+    # -- lifetime
+    def close(self):
+        if getattr(self, "_h", None):
+            capi.scvt_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _sync_inputs(self):
+        # inputs written on torch's current stream must be visible on ours
+        self.stream.wait_stream(torch.cuda.current_stream(self.device))
+
+    def _tensor(self, *shape, dtype=torch.float64):
+        return torch.empty(*shape, dtype=dtype, device=self.device)
+
+    # -- entry points
+    def energy_grad(self, z):
+        g = self._tensor(self.n, 3)
+        m = self._tensor(self.n)
+        c = self._tensor(self.n, 3)
+        self._sync_inputs()
+        F = capi.scvt_energy_grad(self._h, _ptr(z), g.data_ptr(), m.data_ptr(), c.data_ptr())
+        torch.cuda.current_stream(self.device).wait_stream(self.stream)
+        return F, g, m, c
+
+    def evaluate(self, z):
+        """All per-cell outputs of one evaluation as tensors."""
+        out = {k: self._tensor(self.n, 3) if k in ("grad", "moment") else self._tensor(self.n)
+               for k in ("grad", "precond", "mass", "moment", "cell_energy")}
+        self._sync_inputs()
+        o = capi.scvt_eval_out()
+        for k, t in out.items():
+            setattr(o, k, t.data_ptr())
+        capi.scvt_evaluate(self._h, _ptr(z), o)
+        torch.cuda.current_stream(self.device).wait_stream(self.stream)
+        out["energy"] = o.energy
+        out["grad_norm"] = o.grad_norm
+        return out
+
+    def lloyd_step(self, z, out=None):
+        if out is None:
+            out = self._tensor(self.n, 3) if isinstance(z, torch.Tensor) else np.empty((self.n, 3))
+        self._sync_inputs()
+        capi.scvt_lloyd_step(self._h, _ptr(z), _ptr(out))
+        torch.cuda.current_stream(self.device).wait_stream(self.stream)
+        return out
+
+    def lbfgs_solve(self, z, max_iter=200, grad_tol=1e-8, rel_grad_tol=0.0, rel_df_tol=0.0, step_tol=0.0,
+                    ls_max_evals=10, c1=1e-4, c2=0.9, warm_start=False):
+        """In-place solve on z; returns the report as a dict."""
+        self._sync_inputs()
+        o = capi.scvt_solve_opts(int(max_iter), float(grad_tol), float(rel_grad_tol), float(rel_df_tol),
+                                 float(step_tol), int(ls_max_evals), float(c1), float(c2), int(warm_start))
+        rep = capi.scvt_lbfgs_solve(self._h, _ptr(z), o)
+        torch.cuda.current_stream(self.device).wait_stream(self.stream)
+        return {f: getattr(rep, f) for f, _ in capi.scvt_solve_report._fields_}
+
+    def voronoi(self, z, max_deg=32):
+        deg = self._tensor(self.n, dtype=torch.int32)
+        nbr = torch.full((self.n, max_deg), -1, dtype=torch.int32, device=self.device)
+        self._sync_inputs()
+        capi.scvt_voronoi(self._h, _ptr(z), deg.data_ptr(), nbr.data_ptr(), max_deg)
+        torch.cuda.current_stream(self.device).wait_stream(self.stream)
+        return deg, nbr
+
+    def lbfgs_direction(self, g, hdiag, S, Y):
+        """q = -H g; S, Y: tensors (count, N, 3), oldest pair first."""
+        q = self._tensor(self.n, 3)
+        self._sync_inputs()
+        count = 0 if S is None else int(S.shape[0])
+        capi.scvt_lbfgs_direction(self._h, _ptr(g), _ptr(hdiag), count, _ptr(S) if count else None,
+                                  _ptr(Y) if count else None, q.data_ptr())
+        torch.cuda.current_stream(self.device).wait_stream(self.stream)
+        return q
+
+    def stats(self):
+        s = capi.scvt_get_stats(self._h)
+        return {f: getattr(s, f) for f, _ in capi.scvt_stats._fields_}
+
+    def reset_stats(self):
+        capi.scvt_reset_stats(self._h)
+
+    def set_profiling(self, on=True):
+        capi.scvt_set_profiling(self._h, on)

@@ -1,0 +1,81 @@
+"""Host-side checks of the C ABI (no GPU needed): the library loads, exports
+every entry point include/scvt.h declares, the ctypes structures have the C
+layout (sizes and offsets printed by gcc from the header), and argument
+validation that happens before any device work rejects bad configurations."""
+import ctypes as C
+import os
+import subprocess
+
+import pytest
+
+from paper_1709_06924_gb300 import build as B
+from paper_1709_06924_gb300 import capi
+
+
+def test_library_exports_every_declared_symbol():
+    lib = capi.lib()
+    declared = capi.header_symbols()
+    assert len(declared) >= 14
+    for name in declared:
+        assert hasattr(lib, name), name
+        assert name in capi.SIGNATURES, name
+
+
+def test_struct_layout_matches_header(tmp_path):
+    structs = {
+        "scvt_density": capi.scvt_density,
+        "scvt_config": capi.scvt_config,
+        "scvt_solve_opts": capi.scvt_solve_opts,
+        "scvt_solve_report": capi.scvt_solve_report,
+        "scvt_stats": capi.scvt_stats,
+        "scvt_eval_out": capi.scvt_eval_out,
+    }
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "scvt.h"', "int main(void){"]
+    for sname, cls in structs.items():
+        lines.append('printf("%s %%zu\\n", sizeof(%s));' % (sname, sname))
+        for f, _ in cls._fields_:
+            lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (sname, f, sname, f))
+    lines.append("return 0;}")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", B.INCLUDE, str(src), "-o", str(exe)], check=True)
+    out = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                  check=True).stdout.splitlines())
+    for sname, cls in structs.items():
+        assert int(out[sname]) == C.sizeof(cls), sname
+        for f, _ in cls._fields_:
+            assert int(out["%s.%s" % (sname, f)]) == getattr(cls, f).offset, (sname, f)
+
+
+def test_status_strings_and_version():
+    lib = capi.lib()
+    for s in range(9):
+        assert lib.scvt_status_string(s)
+    assert b"sm_103a" in lib.scvt_version()
+
+
+@pytest.mark.parametrize("field,value", [("n", 3), ("lbfgs_m", 33), ("quad_points", 4), ("knn_k0", 4)])
+def test_create_rejects_bad_config_before_device_work(field, value):
+    cfg = capi.scvt_config()
+    cfg.n = 100
+    cfg.rho.kind = 0
+    cfg.quad_points = 7
+    cfg.lbfgs_m = 5
+    setattr(cfg, field, value)
+    h = C.c_void_p()
+    assert capi.lib().scvt_create(C.byref(cfg), None, C.byref(h)) == capi.ERR_INVALID
+    assert not h.value
+
+
+def test_null_handle_is_safe():
+    lib = capi.lib()
+    lib.scvt_destroy(None)
+    assert lib.scvt_last_error(None) == b""
+    assert lib.scvt_lloyd_step(None, None, None) == capi.ERR_INVALID
+
+
+def test_build_sources_target_sm103a():
+    assert B.ARCH == "-gencode=arch=compute_103a,code=sm_103a"
+    assert len(B.sources()) >= 3
+    assert os.path.exists(capi.lib()._name)
