@@ -39,6 +39,9 @@ struct Bufs {
     double *rho = nullptr;                   // kMaxM + 1
     double *hist = nullptr;                  // (m + 1) slots of S and Y, 3n each
     P4 *zs = nullptr;
+    float4 *zf = nullptr;
+    P4 *cvx = nullptr;
+    int *cdeg = nullptr, *cnb = nullptr;
     int *bin_of = nullptr, *count = nullptr, *start = nullptr, *cursor = nullptr, *scan_tmp = nullptr;
     int *sidx = nullptr, *list1 = nullptr, *list2 = nullptr;
     int *deg = nullptr;
@@ -146,12 +149,13 @@ scvt_status evaluate_dev(scvt_handle *H, const double *zdev, double *grad, doubl
     int64_t *L = &H->stats.kernel_launches;
     if (H->profiling) cudaEventRecord(H->ev_e0, s);
     CK(cudaMemsetAsync(B.st, 0, sizeof(DevStatus), s), "reset status");
-    bin_points(zdev, n, H->G, B.bin_of, B.count, B.start, B.cursor, B.scan_tmp, B.zs, B.sidx, B.st, s, L);
+    bin_points(zdev, n, H->G, B.bin_of, B.count, B.start, B.cursor, B.scan_tmp, B.zs, B.zf, B.sidx, B.st, s, L);
     Grid g;
     g.n = n;
     g.G = H->G;
     g.nbins = 6 * H->G * H->G;
     g.zs = B.zs;
+    g.zf = B.zf;
     g.sidx = B.sidx;
     g.bstart = B.start;
     CellOut out;
@@ -168,7 +172,11 @@ scvt_status evaluate_dev(scvt_handle *H, const double *zdev, double *grad, doubl
         CK(cudaMemsetAsync(B.radius, 0, sizeof(float) * n, s), "reset radius hints");
         H->radius_valid = true;
     }
-    cell_passes(g, to_density(H->cfg.rho), out, nullptr, B.list1, B.list2, B.st, H->cfg.knn_k0, H->cfg.knn_kmax, s,
+    CellBuf cb;
+    cb.deg = B.cdeg;
+    cb.vx = B.cvx;
+    cb.nb = B.cnb;
+    cell_passes(g, to_density(H->cfg.rho), out, cb, B.list1, B.list2, B.st, H->cfg.knn_k0, s,
                 H->profiling ? H->ev_cell0 : nullptr, H->profiling ? H->ev_cell1 : nullptr, L,
                 &H->stats.cell_launches);
     reduce_eval(n, fcell, grad, q, nrm, B.partials, B.st, s, L);
@@ -416,7 +424,7 @@ void scvt_destroy(scvt_handle *H) {
     if (!H) return;
     Bufs &b = H->b;
     void *ptrs[] = {b.z, b.zt, b.g, b.gt, b.h, b.ht, b.fc, b.q, b.yv, b.nrm, b.mass, b.moment, b.stage_a, b.stage_b,
-                    b.partials, b.scal, b.rho, b.hist, b.zs, b.bin_of, b.count, b.start, b.cursor, b.scan_tmp,
+                    b.partials, b.scal, b.rho, b.hist, b.zs, b.zf, b.cvx, b.cnb, b.cdeg, b.bin_of, b.count, b.start, b.cursor, b.scan_tmp,
                     b.sidx, b.list1, b.list2, b.deg, b.radius, b.st};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -468,7 +476,8 @@ scvt_status scvt_create(const scvt_config *cfg, void *cuda_stream, scvt_handle *
     AL(b.stage_a, n3); AL(b.stage_b, n3);
     AL(b.partials, 4 * 1024); AL(b.scal, 128); AL(b.rho, kMaxM + 1);
     AL(b.hist, (size_t)(H->m + 1) * 2 * n3);
-    AL(b.zs, n); AL(b.bin_of, n); AL(b.count, nbins); AL(b.start, nbins + 1); AL(b.cursor, nbins);
+    AL(b.zs, n); AL(b.zf, n); AL(b.cvx, (size_t)n * kCellSlots); AL(b.cnb, (size_t)n * kCellSlots);
+    AL(b.cdeg, n); AL(b.bin_of, n); AL(b.count, nbins); AL(b.start, nbins + 1); AL(b.cursor, nbins);
     AL(b.scan_tmp, 2 * (nbins / 2048 + 64) + 64);
     AL(b.sidx, n); AL(b.list1, n); AL(b.list2, n); AL(b.deg, n); AL(b.radius, n);
     AL(b.st, 1);

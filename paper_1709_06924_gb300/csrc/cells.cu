@@ -29,7 +29,6 @@ namespace scvt {
 
 namespace {
 
-constexpr double kSinThetaMax = 0.28;   // caps stay clear of the far cube faces
 constexpr double kBoxL = 1.0e3;         // half-width of the starting square (gnomonic)
 constexpr double kCertMargin = 1.0 + 1e-9;
 
@@ -101,12 +100,15 @@ __global__ void k_bin_count(const double *__restrict__ z, int n, int G, int *__r
 }
 
 __global__ void k_bin_scatter(const double *__restrict__ z, int n, const int *__restrict__ bin_of,
-                              int *__restrict__ cursor, P4 *__restrict__ zs, int *__restrict__ sidx) {
+                              int *__restrict__ cursor, P4 *__restrict__ zs, float4 *__restrict__ zf,
+                              int *__restrict__ sidx) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int pos = atomicAdd(&cursor[bin_of[i]], 1);
     sidx[pos] = i;
-    zs[pos] = P4{z[3 * (size_t)i], z[3 * (size_t)i + 1], z[3 * (size_t)i + 2], 0.0};
+    double x = z[3 * (size_t)i], y = z[3 * (size_t)i + 1], w = z[3 * (size_t)i + 2];
+    zs[pos] = P4{x, y, w, 0.0};
+    zf[pos] = make_float4((float)x, (float)y, (float)w, 0.0f);
 }
 
 // exclusive scan of 2048-element tiles; writes tile totals
@@ -167,12 +169,23 @@ void exclusive_scan(const int *in, int *out, int len, int *tmp, cudaStream_t s, 
 __global__ void k_set_total(int *start, int nbins, int n) { start[nbins] = n; }
 
 // ------------------------------------------------------------ k-nearest
+// The neighbour search runs on FP32 copies of the coordinates (the FP32 pipe
+// is ~70x the FP64 pipe on this part); it only has to produce candidates and a
+// certified lower bound on the distance of every generator it did not keep.
+// With coordinates rounded to FP32 (error <= 6e-8 each) and the FP32
+// difference and squared norm, the true chord d of a scanned point satisfies
+// d >= sqrt(d2f) (1 - 3e-7) - 4e-7; lower_d2() returns the square of that.
+__device__ __forceinline__ double lower_d2(float d2f) {
+    double d = sqrt((double)d2f) * (1.0 - 3e-7) - 4e-7;
+    return d > 0.0 ? d * d : 0.0;
+}
+
 template <int K>
 struct KnnList {
-    double d[K];
+    float d[K];
     int j[K];
     int cnt;
-    __device__ __forceinline__ void push(double d2, int jj) {
+    __device__ __forceinline__ void push(float d2, int jj) {
         if (cnt == K && (d2 > d[K - 1] || (d2 == d[K - 1] && jj > j[K - 1]))) return;
         int p = (cnt < K) ? cnt++ : K - 1;
         while (p > 0 && (d[p - 1] > d2 || (d[p - 1] == d2 && j[p - 1] > jj))) {
@@ -185,14 +198,24 @@ struct KnnList {
     }
 };
 
-// Every generator p (bin order) with chord^2 to zi <= r2, found through the
-// bins that the cap {x : x.q >= cos theta} can reach (sin theta = S < 0.28).
-// For face (a, sign) the values s = x_b / |x_a| attained in the cap lie
-// between the roots of (q_b - s sign q_a)^2 = S^2 (1 + s^2): the planes of
-// constant s are great circles through the c axis, and one meets the cap iff
-// q's distance to it is at most S.
+__device__ __forceinline__ float4 ldf(const float4 *p) { return p[0]; }
+
+// exact duplicate test on the FP64 coordinates for FP32 near-coincidences
+__device__ __forceinline__ void check_duplicate(const Grid &g, V3 q, int p, unsigned *flags) {
+    V3 d = sub(ld(g.zs + p), q);
+    if (d.x == 0.0 && d.y == 0.0 && d.z == 0.0) atomicOr(flags, FLAG_DUPLICATE);
+}
+
+// Every generator p (bin order) within chord r of q, found through the bins
+// that the cap {x : x.q >= cos theta} can reach (sin theta = S < 0.28), is
+// scanned; those with d2f <= r2acc are offered to the list.  For face
+// (a, sign) the values s = x_b / |x_a| attained in the cap lie between the
+// roots of (q_b - s sign q_a)^2 = S^2 (1 + s^2): the planes of constant s are
+// great circles through the c axis, and one meets the cap iff q's distance
+// to it is at most S.
 template <int K>
-__device__ void cap_query(const Grid &g, V3 q, int self, double S, double r2, KnnList<K> &L, unsigned *flags) {
+__device__ void cap_query(const Grid &g, V3 q, float4 qf, int self, double S, float r2acc, KnnList<K> &L,
+                          unsigned *flags) {
     const double S2 = S * S;
     const double qv[3] = {q.x, q.y, q.z};
     for (int a = 0; a < 3; ++a) {
@@ -221,64 +244,70 @@ __device__ void cap_query(const Grid &g, V3 q, int self, double S, double r2, Kn
             int p0 = g.bstart[row + lo[0]], p1 = g.bstart[row + hi[0] + 1];
             for (int p = p0; p < p1; ++p) {
                 if (p == self) continue;
-                V3 d = sub(ld(g.zs + p), q);
-                double d2 = dot(d, d);
-                if (d2 == 0.0) atomicOr(flags, FLAG_DUPLICATE);
-                if (d2 <= r2) L.push(d2, p);
+                float4 c = ldf(g.zf + p);
+                float dx = c.x - qf.x, dy = c.y - qf.y, dz = c.z - qf.z;
+                float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                if (d2 == 0.0f) check_duplicate(g, q, p, flags);
+                if (d2 <= r2acc) L.push(d2, p);
             }
         }
     }
 }
 
 template <int K>
-__device__ void all_query(const Grid &g, V3 q, int self, KnnList<K> &L, unsigned *flags) {
+__device__ void all_query(const Grid &g, V3 q, float4 qf, int self, KnnList<K> &L, unsigned *flags) {
     for (int p = 0; p < g.n; ++p) {
         if (p == self) continue;
-        V3 d = sub(ld(g.zs + p), q);
-        double d2 = dot(d, d);
-        if (d2 == 0.0) atomicOr(flags, FLAG_DUPLICATE);
+        float4 c = ldf(g.zf + p);
+        float dx = c.x - qf.x, dy = c.y - qf.y, dz = c.z - qf.z;
+        float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        if (d2 == 0.0f) check_duplicate(g, q, p, flags);
         L.push(d2, p);
     }
 }
 
 // ---------------------------------------------------------------- clipping
 // Convex polygon in the gnomonic plane at z_i: vertex k = (u, w); edge k runs
-// from vertex k to vertex k+1 on line k: a u + b w <= c, whose neighbour is
-// nb (bin-order index; < 0 for the starting square).  Vertex k is the
-// intersection of lines k-1 and k, computed from those two lines only.
-template <int VMAX>
+// from vertex k to vertex k+1 on line ln[k] (a u + b w <= c).  Lines live in
+// a side table: slots 0..K-1 follow the kNN list, K..K+3 are the starting
+// square, and K+4.. hold generators met by the exhaustive last-resort scan
+// (their ids in jx).  Each line is computed once, in FP64.  Vertex k is the
+// intersection of lines ln[k-1] and ln[k], computed from those two lines only,
+// so the final vertices do not depend on the order of clipping.
+template <int K, int VMAX>
 struct Poly {
-    double u[2][VMAX], w[2][VMAX], a[2][VMAX], b[2][VMAX], c[2][VMAX];
-    int nb[2][VMAX];
+    double u[2][VMAX], w[2][VMAX];
+    unsigned char ln[2][VMAX];
+    double la[K + 4 + VMAX], lb[K + 4 + VMAX], lc[K + 4 + VMAX];
+    int jx[VMAX];
     int nv, cur;
 };
 
 __device__ __forceinline__ void meet(double a1, double b1, double c1, double a2, double b2, double c2, double &u,
                                      double &w) {
-    double det = a1 * b2 - a2 * b1;
-    u = (c1 * b2 - c2 * b1) / det;
-    w = (a1 * c2 - a2 * c1) / det;
+    double inv = 1.0 / (a1 * b2 - a2 * b1);
+    u = (c1 * b2 - c2 * b1) * inv;
+    w = (a1 * c2 - a2 * c1) * inv;
 }
 
-__device__ __forceinline__ double chord2_of(double u, double w) {
-    // |normalize(z_i + u e1 + w e2) - z_i|^2 = 2 - 2/sqrt(1 + r^2), written without cancellation
-    double r2 = u * u + w * w;
+__device__ __forceinline__ double chord2_of_r2(double r2) {
+    // |normalize(z_i + u e1 + w e2) - z_i|^2 = 2 - 2/sqrt(1 + r^2), without cancellation
     double q = sqrt(1.0 + r2);
     return 2.0 * r2 / (q * (1.0 + q));
 }
 
-// returns 1 if the polygon changed, 0 if not, -1 on capacity / empty errors
-template <int VMAX>
-__device__ int clip(Poly<VMAX> &P, double la, double lb, double lc, int nbj, unsigned *flags,
-                    unsigned long long *amb) {
+// clip by line slot l; returns 1 if the polygon changed, 0 if not, -1 on
+// capacity / empty errors
+template <int K, int VMAX>
+__device__ int clip(Poly<K, VMAX> &P, int l, unsigned *flags, unsigned long long *amb) {
     const int c0 = P.cur, nv = P.nv;
+    const double la = P.la[l], lb = P.lb[l], lc = P.lc[l];
     unsigned long long out = 0ull;
     int namb = 0;
     for (int k = 0; k < nv; ++k) {
         double uk = P.u[c0][k], wk = P.w[c0][k];
         double sd = la * uk + lb * wk - lc;
-        double mag = fabs(la * uk) + fabs(lb * wk) + fabs(lc);
-        if (fabs(sd) <= 1e-14 * mag) ++namb;
+        if (fabs(sd) <= 1e-14 * (fabs(la * uk) + fabs(lb * wk) + fabs(lc))) ++namb;
         if (sd > 0.0) out |= (1ull << k);
     }
     if (namb) atomicAdd(amb, (unsigned long long)namb);
@@ -308,26 +337,32 @@ __device__ int clip(Poly<VMAX> &P, double la, double lb, double lc, int nbj, uns
     int nnew = nv - runlen + 2;
     if (nnew > VMAX) return -1;
     const int c1 = c0 ^ 1;
-    int kin = (k0 == 0) ? nv - 1 : k0 - 1;  // last inside vertex before the run
+    const int kin = (k0 == 0) ? nv - 1 : k0 - 1;  // last inside vertex before the run
+    const int lin = P.ln[c0][kin], lout = P.ln[c0][k1];
     double pu, pw, qu, qw;
-    meet(P.a[c0][kin], P.b[c0][kin], P.c[c0][kin], la, lb, lc, pu, pw);
-    meet(la, lb, lc, P.a[c0][k1], P.b[c0][k1], P.c[c0][k1], qu, qw);
-    P.u[c1][0] = pu; P.w[c1][0] = pw;
-    P.a[c1][0] = la; P.b[c1][0] = lb; P.c[c1][0] = lc; P.nb[c1][0] = nbj;
-    P.u[c1][1] = qu; P.w[c1][1] = qw;
-    P.a[c1][1] = P.a[c0][k1]; P.b[c1][1] = P.b[c0][k1]; P.c[c1][1] = P.c[c0][k1]; P.nb[c1][1] = P.nb[c0][k1];
+    meet(P.la[lin], P.lb[lin], P.lc[lin], la, lb, lc, pu, pw);
+    meet(la, lb, lc, P.la[lout], P.lb[lout], P.lc[lout], qu, qw);
+    P.u[c1][0] = pu; P.w[c1][0] = pw; P.ln[c1][0] = (unsigned char)l;
+    P.u[c1][1] = qu; P.w[c1][1] = qw; P.ln[c1][1] = (unsigned char)lout;
     int o = 2;
     int k = (k1 + 1 == nv) ? 0 : k1 + 1;
     for (int cnt = 0; cnt < nv - runlen; ++cnt) {
-        P.u[c1][o] = P.u[c0][k]; P.w[c1][o] = P.w[c0][k];
-        P.a[c1][o] = P.a[c0][k]; P.b[c1][o] = P.b[c0][k]; P.c[c1][o] = P.c[c0][k];
-        P.nb[c1][o] = P.nb[c0][k];
+        P.u[c1][o] = P.u[c0][k];
+        P.w[c1][o] = P.w[c0][k];
+        P.ln[c1][o] = P.ln[c0][k];
         ++o;
         k = (k + 1 == nv) ? 0 : k + 1;
     }
     P.nv = nnew;
     P.cur = c1;
     return 1;
+}
+
+template <int K, int VMAX>
+__device__ __forceinline__ double poly_r2max(const Poly<K, VMAX> &P) {
+    double r2 = 0.0;
+    for (int v = 0; v < P.nv; ++v) r2 = fmax(r2, P.u[P.cur][v] * P.u[P.cur][v] + P.w[P.cur][v] * P.w[P.cur][v]);
+    return r2;
 }
 
 // ------------------------------------------------------------- quadrature
@@ -360,7 +395,7 @@ __device__ __forceinline__ void tri(const Density &rho, V3 A, V3 B, V3 C, Acc &a
     double det = dot(A, cr);
     double den = 1.0 + dot(A, B) + dot(B, C) + dot(C, A);
     double area = 2.0 * atan2(det, den);
-#pragma unroll
+#pragma unroll 1
     for (int k = 0; k < 7; ++k) {
         V3 x = add(add(scl(A, kQb[k][0]), scl(B, kQb[k][1])), scl(C, kQb[k][2]));
         V3 p = scl(x, 1.0 / sqrt(dot(x, x)));
@@ -374,27 +409,53 @@ __device__ __forceinline__ void tri(const Density &rho, V3 A, V3 B, V3 C, Acc &a
     }
 }
 
-// --------------------------------------------------------------- the cell
-// mode 0: positions 0..n-1 are the work; otherwise the work is list[0..*count)
-// scan_all: consider every generator (small n / last resort)
+__device__ __forceinline__ void write_cell(const CellOut &out, int i, V3 zi, const Acc &acc, DevStatus *st) {
+    const double cz = acc.cx * zi.x + acc.cy * zi.y + acc.cz * zi.z;
+    if (!(cz > 0.0)) atomicOr(&st->flags, FLAG_NONPOSITIVE);
+    if (out.grad) {
+        out.grad[3 * (size_t)i] = 2.0 * cz * zi.x - 2.0 * acc.cx;
+        out.grad[3 * (size_t)i + 1] = 2.0 * cz * zi.y - 2.0 * acc.cy;
+        out.grad[3 * (size_t)i + 2] = 2.0 * cz * zi.z - 2.0 * acc.cz;
+    }
+    if (out.hdiag) out.hdiag[i] = 1.0 / (2.0 * cz);
+    if (out.mass) out.mass[i] = acc.m;
+    if (out.moment) {
+        out.moment[3 * (size_t)i] = acc.cx;
+        out.moment[3 * (size_t)i + 1] = acc.cy;
+        out.moment[3 * (size_t)i + 2] = acc.cz;
+    }
+    if (out.fcell) out.fcell[i] = acc.e;
+}
+
+__device__ __forceinline__ bool lex_less(V3 a, V3 b) {
+    return a.x < b.x || (a.x == b.x && (a.y < b.y || (a.y == b.y && a.z < b.z)));
+}
+
+// -------------------------------------------------------------- topology
+// One thread per cell.  mode: list == nullptr -> all bin positions, else the
+// retry list.  The certified polygon is written to the cell buffer with its
+// edges rotated to start at the neighbour with the lexicographically
+// smallest coordinates (so the layout is the same for any input order).
+// Cells with more than kCellSlots edges are integrated here, in-thread.
 template <int K, int VMAX>
-__global__ void __launch_bounds__(128) k_cells(Grid g, Density rho, CellOut out, const int *__restrict__ list,
-                                               const unsigned *__restrict__ list_count, int *__restrict__ next_list,
-                                               unsigned *__restrict__ next_count, int last_pass, int scan_all,
-                                               DevStatus *st) {
+__global__ void __launch_bounds__(128) k_topo(Grid g, Density rho, CellOut out, CellBuf cb,
+                                              const int *__restrict__ list, const unsigned *__restrict__ list_count,
+                                              int *__restrict__ next_list, unsigned *__restrict__ next_count,
+                                              int last_pass, int scan_all, DevStatus *st) {
     int nwork = list ? (int)*list_count : g.n;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nwork; t += gridDim.x * blockDim.x) {
         const int p = list ? list[t] : t;
         const V3 zi = ld(g.zs + p);
+        const float4 zif = ldf(g.zf + p);
         const int i = g.sidx[p];
 
-        // ---- neighbours: nearest first, certified bound D2 on the rest
+        // ---- neighbours (FP32): list of up to K, bound D2 on everything else
         KnnList<K> L;
         L.cnt = 0;
         double D2;
         if (scan_all || g.n - 1 <= K) {
-            all_query<K>(g, zi, p, L, &st->flags);
-            D2 = (L.cnt == g.n - 1) ? INFINITY : L.d[K - 1];
+            all_query<K>(g, zi, zif, p, L, &st->flags);
+            D2 = (L.cnt == g.n - 1) ? INFINITY : lower_d2(L.d[K - 1]);
         } else {
             const double thmax = 0.28379410920832787;  // asin(0.28)
             double th;
@@ -404,30 +465,33 @@ __global__ void __launch_bounds__(128) k_cells(Grid g, Density rho, CellOut out,
             } else {
                 // local density from the own bin: lambda = count / solid angle
                 int b = bin_index(zi.x, zi.y, zi.z, g.G);
-                int cb = g.bstart[b + 1] - g.bstart[b];
+                int cbn = g.bstart[b + 1] - g.bstart[b];
                 double ax = fabs(zi.x), ay = fabs(zi.y), az = fabs(zi.z);
                 double am = fmax(ax, fmax(ay, az));
                 double s2 = (ax * ax + ay * ay + az * az) / (am * am);  // 1 + s^2 + t^2
                 double omega = (4.0 / ((double)g.G * g.G)) / (s2 * sqrt(s2));
-                double lam = fmax((double)cb, 1.0) / omega;
+                double lam = fmax((double)cbn, 1.0) / omega;
                 th = sqrt(1.5 * K / (3.141592653589793 * lam));
                 if (last_pass) th *= 2.0;
             }
             th = fmin(th, thmax);
-            double r2;
+            double r2 = 0.0;
+            float r2acc = 0.0f;
             for (int attempt = 0;; ++attempt) {
                 double S = sin(th);
                 double hs = sin(0.5 * th);
                 r2 = 4.0 * hs * hs;
+                r2acc = (float)(r2 * 1.001) + 1e-12f;
                 L.cnt = 0;
-                cap_query<K>(g, zi, p, S, r2, L, &st->flags);
+                cap_query<K>(g, zi, zif, p, S, r2acc, L, &st->flags);
                 if (L.cnt == K || th >= thmax || attempt > 8) break;
                 double grow = (L.cnt > 0) ? sqrt(1.3 * K / (double)L.cnt) : 2.0;
                 th = fmin(th * fmax(grow, 1.25), thmax);
             }
-            D2 = (L.cnt == K) ? L.d[K - 1] : r2;
+            // unkept: inside the list's range -> >= lower(d_K); outside the cap -> > r
+            D2 = (L.cnt == K) ? fmin(lower_d2(L.d[K - 1]), r2) : fmin(lower_d2(r2acc), r2);
         }
-        if (out.radius) out.radius[i] = (float)sqrt(L.cnt ? L.d[L.cnt - 1] : 0.0);
+        if (out.radius) out.radius[i] = sqrtf(L.cnt ? L.d[L.cnt - 1] : 0.0f);
 
         // ---- gnomonic frame at z_i: e1 x e2 = z_i
         V3 ax;
@@ -438,38 +502,62 @@ __global__ void __launch_bounds__(128) k_cells(Grid g, Density rho, CellOut out,
         const V3 e1 = unit(crs(zi, ax));
         const V3 e2 = crs(zi, e1);
 
-        // ---- clip, nearest first, with the security radius
-        Poly<VMAX> P;
+        // ---- clip nearest first (FP64), with the security radius
+        Poly<K, VMAX> P;
         P.cur = 0;
         P.nv = 4;
         {
-            // lines: 0 right (u <= L), 1 top (w <= L), 2 left (-u <= L), 3 bottom (-w <= L)
+            // square lines: K right (u <= L), K+1 top (w <= L), K+2 left, K+3 bottom
             const double la[4] = {1, 0, -1, 0}, lb[4] = {0, 1, 0, -1};
             const double vu[4] = {kBoxL, kBoxL, -kBoxL, -kBoxL}, vw[4] = {-kBoxL, kBoxL, kBoxL, -kBoxL};
             for (int k = 0; k < 4; ++k) {
-                P.a[0][k] = la[k]; P.b[0][k] = lb[k]; P.c[0][k] = kBoxL; P.nb[0][k] = -1 - k;
+                P.la[K + k] = la[k]; P.lb[K + k] = lb[k]; P.lc[K + k] = kBoxL;
+                P.ln[0][k] = (unsigned char)(K + k);
                 P.u[0][k] = vu[k]; P.w[0][k] = vw[k];
             }
         }
-        double R2 = chord2_of(kBoxL, kBoxL);
+        double R2 = chord2_of_r2(2.0 * kBoxL * kBoxL);
         bool ok = true, early = false;
         for (int k = 0; k < L.cnt; ++k) {
-            if (L.d[k] > 4.0 * R2 * kCertMargin) { early = true; break; }
-            const int pj = L.j[k];
-            const V3 d = sub(ld(g.zs + pj), zi);
-            int r = clip<VMAX>(P, dot(e1, d), dot(e2, d), -dot(zi, d), pj, &st->flags, &st->ambiguous);
+            const double bound = fmin(lower_d2(L.d[k]), D2);
+            if (bound > 4.0 * R2 * kCertMargin) { early = true; break; }
+            const V3 d = sub(ld(g.zs + L.j[k]), zi);
+            P.la[k] = dot(e1, d);
+            P.lb[k] = dot(e2, d);
+            P.lc[k] = -dot(zi, d);
+            int r = clip<K, VMAX>(P, k, &st->flags, &st->ambiguous);
             if (r < 0) { ok = false; break; }
-            if (r > 0) {
-                R2 = 0.0;
-                for (int v = 0; v < P.nv; ++v) R2 = fmax(R2, chord2_of(P.u[P.cur][v], P.w[P.cur][v]));
-            }
+            if (r > 0) R2 = chord2_of_r2(poly_r2max(P));
         }
         bool boxed = false;
-        for (int v = 0; v < P.nv; ++v) boxed |= (P.nb[P.cur][v] < 0);
+        for (int v = 0; v < P.nv; ++v) boxed |= (P.ln[P.cur][v] >= K);  // no extra slots yet
         bool certified = ok && !boxed && (early || D2 > 4.0 * R2 * kCertMargin);
-        if (ok && boxed && D2 == INFINITY) {
-            atomicOr(&st->flags, FLAG_UNBOUNDED);  // every point seen and the cell is still open
-            certified = false;
+        if (ok && !certified && last_pass) {
+            // last resort: clip by every generator (the exact cell); points
+            // that cannot reach the polygon are skipped.  A new line goes to
+            // an extra slot that no current edge uses.
+            for (int q = 0; q < g.n && ok; ++q) {
+                if (q == p) continue;
+                const V3 d = sub(ld(g.zs + q), zi);
+                if (dot(d, d) > 4.0 * R2 * kCertMargin) continue;
+                unsigned long long used = 0ull;
+                for (int v = 0; v < P.nv; ++v)
+                    if (P.ln[P.cur][v] >= K + 4) used |= 1ull << (P.ln[P.cur][v] - (K + 4));
+                int x = __ffsll((long long)~used) - 1;
+                if (x < 0 || x >= VMAX) { ok = false; break; }
+                const int l = K + 4 + x;
+                P.la[l] = dot(e1, d);
+                P.lb[l] = dot(e2, d);
+                P.lc[l] = -dot(zi, d);
+                P.jx[x] = q;
+                int r = clip<K, VMAX>(P, l, &st->flags, &st->ambiguous);
+                if (r < 0) { ok = false; break; }
+                if (r > 0) R2 = chord2_of_r2(poly_r2max(P));
+            }
+            boxed = false;
+            for (int v = 0; v < P.nv; ++v) boxed |= (P.ln[P.cur][v] >= K && P.ln[P.cur][v] < K + 4);
+            if (ok && boxed) atomicOr(&st->flags, FLAG_UNBOUNDED);
+            certified = ok && !boxed;
         }
         if (!certified) {
             if (last_pass) {
@@ -478,58 +566,94 @@ __global__ void __launch_bounds__(128) k_cells(Grid g, Density rho, CellOut out,
                 unsigned pos = atomicAdd(next_count, 1u);
                 next_list[pos] = p;
             }
+            cb.deg[p] = 0;
             continue;
         }
 
-        // ---- integrate over the signed sub-triangles of each edge, starting
-        // at the edge of the smallest neighbour id so that the summation
-        // order does not depend on the clipping history
+        // ---- canonical edge order: start at the lexicographically smallest neighbour
         const int c = P.cur, nv = P.nv;
-        int k0 = 0, best = g.sidx[P.nb[c][0]];
+        auto nbj = [&](int k) -> int {
+            int l = P.ln[c][k];
+            return (l < K) ? L.j[l] : P.jx[l - (K + 4)];
+        };
+        int k0 = 0;
+        V3 best = ld(g.zs + nbj(0));
         for (int k = 1; k < nv; ++k) {
-            int id = g.sidx[P.nb[c][k]];
-            if (id < best) { best = id; k0 = k; }
+            V3 zn = ld(g.zs + nbj(k));
+            if (lex_less(zn, best)) { best = zn; k0 = k; }
         }
-        Acc acc = {0, 0, 0, 0, 0};
-        V3 vfirst = unit(add(zi, add(scl(e1, P.u[c][k0]), scl(e2, P.w[c][k0]))));
-        V3 va = vfirst;
-        for (int t = 0; t < nv; ++t) {
-            const int k = (k0 + t < nv) ? k0 + t : k0 + t - nv;
-            const int k1 = (k + 1 == nv) ? 0 : k + 1;
-            V3 vb = (t + 1 == nv) ? vfirst : unit(add(zi, add(scl(e1, P.u[c][k1]), scl(e2, P.w[c][k1]))));
-            V3 mu = unit(add(zi, ld(g.zs + P.nb[c][k])));
-            tri(rho, zi, va, mu, acc);
-            tri(rho, zi, mu, vb, acc);
-            va = vb;
-        }
-        const double cz = acc.cx * zi.x + acc.cy * zi.y + acc.cz * zi.z;
-        if (!(cz > 0.0)) atomicOr(&st->flags, FLAG_NONPOSITIVE);
-        if (out.grad) {
-            out.grad[3 * (size_t)i] = 2.0 * cz * zi.x - 2.0 * acc.cx;
-            out.grad[3 * (size_t)i + 1] = 2.0 * cz * zi.y - 2.0 * acc.cy;
-            out.grad[3 * (size_t)i + 2] = 2.0 * cz * zi.z - 2.0 * acc.cz;
-        }
-        if (out.hdiag) out.hdiag[i] = 1.0 / (2.0 * cz);
-        if (out.mass) out.mass[i] = acc.m;
-        if (out.moment) {
-            out.moment[3 * (size_t)i] = acc.cx;
-            out.moment[3 * (size_t)i + 1] = acc.cy;
-            out.moment[3 * (size_t)i + 2] = acc.cz;
-        }
-        if (out.fcell) out.fcell[i] = acc.e;
         if (out.deg) {
             out.deg[i] = nv;
             if (nv <= out.max_deg)
-                for (int t = 0; t < nv; ++t)
-                    out.nbr[(size_t)i * out.max_deg + t] = g.sidx[P.nb[c][(k0 + t < nv) ? k0 + t : k0 + t - nv]];
+                for (int t2 = 0; t2 < nv; ++t2)
+                    out.nbr[(size_t)i * out.max_deg + t2] = g.sidx[nbj((k0 + t2 < nv) ? k0 + t2 : k0 + t2 - nv)];
+        }
+        if (nv <= kCellSlots) {
+            cb.deg[p] = nv;
+            for (int t2 = 0; t2 < nv; ++t2) {
+                const int k = (k0 + t2 < nv) ? k0 + t2 : k0 + t2 - nv;
+                V3 v = unit(add(zi, add(scl(e1, P.u[c][k]), scl(e2, P.w[c][k]))));
+                cb.vx[(size_t)p * kCellSlots + t2] = P4{v.x, v.y, v.z, 0.0};
+                cb.nb[(size_t)p * kCellSlots + t2] = nbj(k);
+            }
+        } else {
+            // large cell: integrate here
+            cb.deg[p] = 0;
+            Acc acc = {0, 0, 0, 0, 0};
+            V3 vfirst = unit(add(zi, add(scl(e1, P.u[c][k0]), scl(e2, P.w[c][k0]))));
+            V3 va = vfirst;
+            for (int t2 = 0; t2 < nv; ++t2) {
+                const int k = (k0 + t2 < nv) ? k0 + t2 : k0 + t2 - nv;
+                const int k1 = (k + 1 == nv) ? 0 : k + 1;
+                V3 vb = (t2 + 1 == nv) ? vfirst : unit(add(zi, add(scl(e1, P.u[c][k1]), scl(e2, P.w[c][k1]))));
+                V3 mu = unit(add(zi, ld(g.zs + nbj(k))));
+                tri(rho, zi, va, mu, acc);
+                tri(rho, zi, mu, vb, acc);
+                va = vb;
+            }
+            write_cell(out, i, zi, acc, st);
         }
     }
+}
+
+// -------------------------------------------------------------- quadrature
+// Eight lanes per cell, four cells per warp: lane s integrates the edges
+// s, s+8, ... (two signed sub-triangles each, Sec. 3.2.2), then the group
+// sums by a fixed xor butterfly, so the result does not depend on timing.
+__global__ void __launch_bounds__(256) k_quad(Grid g, Density rho, CellOut out, CellBuf cb, DevStatus *st) {
+    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int p = (int)(gid >> 3);
+    const int s = (int)(gid & 7);
+    const int deg = (p < g.n) ? cb.deg[p] : 0;
+    Acc acc = {0, 0, 0, 0, 0};
+    V3 zi = mk(0, 0, 0);
+    if (deg > 0) {
+        zi = ld(g.zs + p);
+        const P4 *vx = cb.vx + (size_t)p * kCellSlots;
+        const int *nb = cb.nb + (size_t)p * kCellSlots;
+        for (int e = s; e < deg; e += 8) {
+            const V3 va = ld(vx + e);
+            const V3 vb = ld(vx + ((e + 1 == deg) ? 0 : e + 1));
+            const V3 mu = unit(add(zi, ld(g.zs + nb[e])));
+            tri(rho, zi, va, mu, acc);
+            tri(rho, zi, mu, vb, acc);
+        }
+    }
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) {
+        acc.m += __shfl_xor_sync(0xffffffffu, acc.m, o);
+        acc.cx += __shfl_xor_sync(0xffffffffu, acc.cx, o);
+        acc.cy += __shfl_xor_sync(0xffffffffu, acc.cy, o);
+        acc.cz += __shfl_xor_sync(0xffffffffu, acc.cz, o);
+        acc.e += __shfl_xor_sync(0xffffffffu, acc.e, o);
+    }
+    if (s == 0 && deg > 0) write_cell(out, g.sidx[p], zi, acc, st);
 }
 
 }  // namespace
 
 void bin_points(const double *z, int n, int G, int *bin_of, int *count, int *start, int *cursor, int *scan_tmp,
-                P4 *zs, int *sidx, DevStatus *st, cudaStream_t s, int64_t *launches) {
+                P4 *zs, float4 *zf, int *sidx, DevStatus *st, cudaStream_t s, int64_t *launches) {
     const int nbins = 6 * G * G;
     cudaMemsetAsync(count, 0, sizeof(int) * nbins, s);
     int blocks = (n + 255) / 256;
@@ -537,31 +661,31 @@ void bin_points(const double *z, int n, int G, int *bin_of, int *count, int *sta
     exclusive_scan(count, start, nbins, scan_tmp, s, launches);
     k_set_total<<<1, 1, 0, s>>>(start, nbins, n);
     cudaMemcpyAsync(cursor, start, sizeof(int) * nbins, cudaMemcpyDeviceToDevice, s);
-    k_bin_scatter<<<blocks, 256, 0, s>>>(z, n, bin_of, cursor, zs, sidx);
+    k_bin_scatter<<<blocks, 256, 0, s>>>(z, n, bin_of, cursor, zs, zf, sidx);
     (*launches) += 3;
 }
 
-void cell_passes(const Grid &g, const Density &rho, const CellOut &out, int *list0, int *list1, int *list2,
-                 DevStatus *st, int knn_k0, int knn_kmax, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1,
-                 int64_t *launches, int64_t *cell_launches) {
-    (void)list0;
-    (void)knn_kmax;
+void cell_passes(const Grid &g, const Density &rho, const CellOut &out, const CellBuf &cb, int *list1, int *list2,
+                 DevStatus *st, int knn_k0, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1, int64_t *launches,
+                 int64_t *cell_launches) {
     const int blocks0 = (g.n + 127) / 128;
-    if (ev0) cudaEventRecord(ev0, s);
     if (knn_k0 <= 16)
-        k_cells<16, 32><<<blocks0, 128, 0, s>>>(g, rho, out, nullptr, nullptr, list1, &st->retry_count[0], 0, 0, st);
+        k_topo<16, 32><<<blocks0, 128, 0, s>>>(g, rho, out, cb, nullptr, nullptr, list1, &st->retry_count[0], 0, 0, st);
     else
-        k_cells<32, 32><<<blocks0, 128, 0, s>>>(g, rho, out, nullptr, nullptr, list1, &st->retry_count[0], 0, 0, st);
-    if (ev1) cudaEventRecord(ev1, s);
+        k_topo<32, 32><<<blocks0, 128, 0, s>>>(g, rho, out, cb, nullptr, nullptr, list1, &st->retry_count[0], 0, 0, st);
     // retry passes: sized for the worst case, they read their work count on the device
     const int rblocks = 2 * 152;
-    k_cells<64, 64><<<rblocks, 64, 0, s>>>(g, rho, out, list1, &st->retry_count[0], list2, &st->retry_count[1], 0, 0,
-                                           st);
+    k_topo<64, 64><<<rblocks, 64, 0, s>>>(g, rho, out, cb, list1, &st->retry_count[0], list2, &st->retry_count[1], 0,
+                                          0, st);
     int scan_all = g.n <= 20000 ? 1 : 0;
-    k_cells<128, 64><<<rblocks, 64, 0, s>>>(g, rho, out, list2, &st->retry_count[1], list2 + 0, &st->retry_count[2],
-                                            1, scan_all, st);
-    (*launches) += 3;
-    (*cell_launches) += 3;
+    k_topo<128, 64><<<rblocks, 64, 0, s>>>(g, rho, out, cb, list2, &st->retry_count[1], nullptr, &st->retry_count[2],
+                                           1, scan_all, st);
+    if (ev0) cudaEventRecord(ev0, s);
+    const long long threads = 8LL * g.n;
+    k_quad<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(g, rho, out, cb, st);
+    if (ev1) cudaEventRecord(ev1, s);
+    (*launches) += 4;
+    (*cell_launches) += 4;
 }
 
 }  // namespace scvt

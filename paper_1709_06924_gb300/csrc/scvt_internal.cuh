@@ -42,7 +42,8 @@ struct Grid {
     int n;
     int G;                  // bins per face edge
     int nbins;              // 6 G^2
-    const P4 *zs;      // generators in bin order (w unused)
+    const P4 *zs;           // generators in bin order (w unused)
+    const float4 *zf;       // the same, rounded to FP32 (neighbour search)
     const int *sidx;        // bin-order position -> original index
     const int *bstart;      // nbins + 1 offsets into zs
 };
@@ -66,15 +67,26 @@ struct CellOut {
     float *radius;   // n, kNN search radius hint of the next evaluation (in/out)
 };
 
+// Certified cells between the topology and quadrature kernels, in bin
+// order: deg (0 = integrated elsewhere or failed), corners (unit vectors)
+// and the bin-order index of the neighbour across edge k (corner k -> k+1).
+constexpr int kCellSlots = 16;
+struct CellBuf {
+    int *deg;   // n
+    P4 *vx;     // n * kCellSlots
+    int *nb;    // n * kCellSlots
+};
+
 // ---- binning (cells.cu) ----
 void bin_points(const double *z, int n, int G, int *bin_of, int *count, int *start, int *cursor,
-                int *scan_tmp, P4 *zs, int *sidx, DevStatus *st, cudaStream_t s, int64_t *launches);
+                int *scan_tmp, P4 *zs, float4 *zf, int *sidx, DevStatus *st, cudaStream_t s, int64_t *launches);
 
 // ---- cell passes (cells.cu) ----
-// pass 0 over all cells; passes 1..2 over the retry lists.
-void cell_passes(const Grid &g, const Density &rho, const CellOut &out, int *retry_list0, int *retry_list1,
-                 int *retry_list2, DevStatus *st, int knn_k0, int knn_kmax, cudaStream_t s,
-                 cudaEvent_t ev0, cudaEvent_t ev1, int64_t *launches, int64_t *cell_launches);
+// topology pass 0 over all cells, passes 1..2 over the retry lists, then the
+// quadrature kernel over all cells (timed by ev0/ev1 when given).
+void cell_passes(const Grid &g, const Density &rho, const CellOut &out, const CellBuf &cb, int *list1, int *list2,
+                 DevStatus *st, int knn_k0, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1, int64_t *launches,
+                 int64_t *cell_launches);
 
 // ---- reductions and vector kernels (lbfgs.cu) ----
 int reduce_blocks(int64_t n);
