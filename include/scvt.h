@@ -176,6 +176,27 @@ scvt_status scvt_voronoi(scvt_handle *h, const double *z, int *deg, int *nbr, in
 scvt_status scvt_lbfgs_direction(scvt_handle *h, const double *g, const double *hdiag, int count,
                                  const double *S, const double *Y, double *q);
 
+/* Energy and gradient for callers that cannot allocate device memory (a
+ * memory budget fixed up front, an allocator that must not be re-entered, a
+ * host that forbids cudaMalloc after start-up).  The paper has no
+ * counterpart: this is a deployment variant of scvt_energy_grad.
+ * It needs no handle and allocates nothing: its scratch is one fixed array
+ * in device memory (about 11.4 MB, held on every GPU that loads the library
+ * until the process exits), sized for n <= SCVT_STATIC_MAX_N.
+ * n: generators (4 <= n <= SCVT_STATIC_MAX_N, else SCVT_ERR_INVALID before
+ * any device work).  rho: host.  z: N x 3 device.  cuda_stream: cudaStream_t
+ * (NULL = legacy default stream).  energy: host double (required).  grad
+ * (N x 3), mass (N), moment (N x 3): device, nullable.  Host pointers for
+ * z/grad/mass/moment are rejected (SCVT_ERR_INVALID).  Synchronises the
+ * stream.  The first call on a device looks up the array's device address
+ * with that device current; make it before any stream capture.  All calls
+ * share the one array and it keeps the previous call's contents; each call
+ * clears what must start at zero.  Calls whose GPU work overlaps (other
+ * streams or host threads) race on the array: serialise them. */
+#define SCVT_STATIC_MAX_N 16384
+scvt_status scvt_energy_grad_static(int64_t n, const scvt_density *rho, const double *z, void *cuda_stream,
+                                    double *energy, double *grad, double *mass, double *moment);
+
 /* Per-handle counters and (with profiling on) device times. */
 scvt_status scvt_get_stats(const scvt_handle *h, scvt_stats *out);
 scvt_status scvt_reset_stats(scvt_handle *h);

@@ -77,7 +77,11 @@ SIGNATURES = {
     "scvt_status_string": (C.c_char_p, [_st]),
     "scvt_last_error": (C.c_char_p, [_H]),
     "scvt_version": (C.c_char_p, []),
+    "scvt_energy_grad_static": (_st, [C.c_int64, C.POINTER(scvt_density), _vp, _vp, C.POINTER(C.c_double),
+                                      _vp, _vp, _vp]),
 }
+
+STATIC_MAX_N = 16384  # SCVT_STATIC_MAX_N
 
 
 def header_symbols():
