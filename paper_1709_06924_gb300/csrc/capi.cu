@@ -41,7 +41,8 @@ struct Bufs {
     P4 *zs = nullptr;
     float4 *zf = nullptr;
     P4 *cvx = nullptr;
-    int *cdeg = nullptr, *cnb = nullptr;
+    int *cdeg = nullptr, *cnb = nullptr, *eoff = nullptr, *ecell = nullptr, *escan = nullptr, *pcnt = nullptr;
+    double *pval = nullptr;
     int *bin_of = nullptr, *count = nullptr, *start = nullptr, *cursor = nullptr, *scan_tmp = nullptr;
     int *sidx = nullptr, *list1 = nullptr, *list2 = nullptr;
     int *deg = nullptr;
@@ -176,6 +177,12 @@ scvt_status evaluate_dev(scvt_handle *H, const double *zdev, double *grad, doubl
     cb.deg = B.cdeg;
     cb.vx = B.cvx;
     cb.nb = B.cnb;
+    cb.eoff = B.eoff;
+    cb.ecell = B.ecell;
+    cb.scan_tmp = B.escan;
+    cb.parts_val = B.pval;
+    cb.parts_cnt = B.pcnt;
+    CK(cudaMemsetAsync(B.pcnt, 0, sizeof(int) * n, s), "reset split-cell counters");
     cell_passes(g, to_density(H->cfg.rho), out, cb, B.list1, B.list2, B.st, H->cfg.knn_k0, s,
                 H->profiling ? H->ev_cell0 : nullptr, H->profiling ? H->ev_cell1 : nullptr, L,
                 &H->stats.cell_launches);
@@ -424,7 +431,7 @@ void scvt_destroy(scvt_handle *H) {
     if (!H) return;
     Bufs &b = H->b;
     void *ptrs[] = {b.z, b.zt, b.g, b.gt, b.h, b.ht, b.fc, b.q, b.yv, b.nrm, b.mass, b.moment, b.stage_a, b.stage_b,
-                    b.partials, b.scal, b.rho, b.hist, b.zs, b.zf, b.cvx, b.cnb, b.cdeg, b.bin_of, b.count, b.start, b.cursor, b.scan_tmp,
+                    b.partials, b.scal, b.rho, b.hist, b.zs, b.zf, b.cvx, b.cnb, b.cdeg, b.eoff, b.ecell, b.escan, b.pval, b.pcnt, b.bin_of, b.count, b.start, b.cursor, b.scan_tmp,
                     b.sidx, b.list1, b.list2, b.deg, b.radius, b.st};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -477,7 +484,9 @@ scvt_status scvt_create(const scvt_config *cfg, void *cuda_stream, scvt_handle *
     AL(b.partials, 4 * 1024); AL(b.scal, 128); AL(b.rho, kMaxM + 1);
     AL(b.hist, (size_t)(H->m + 1) * 2 * n3);
     AL(b.zs, n); AL(b.zf, n); AL(b.cvx, (size_t)n * kCellSlots); AL(b.cnb, (size_t)n * kCellSlots);
-    AL(b.cdeg, n); AL(b.bin_of, n); AL(b.count, nbins); AL(b.start, nbins + 1); AL(b.cursor, nbins);
+    AL(b.cdeg, n); AL(b.eoff, n + 1); AL(b.ecell, 6 * (size_t)n); AL(b.escan, 2 * (n / 2048 + 64) + 64);
+    AL(b.pval, 10 * (size_t)n); AL(b.pcnt, n);
+    AL(b.bin_of, n); AL(b.count, nbins); AL(b.start, nbins + 1); AL(b.cursor, nbins);
     AL(b.scan_tmp, 2 * (nbins / 2048 + 64) + 64);
     AL(b.sidx, n); AL(b.list1, n); AL(b.list2, n); AL(b.deg, n); AL(b.radius, n);
     AL(b.st, 1);

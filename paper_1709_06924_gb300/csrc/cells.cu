@@ -3,7 +3,8 @@
 //
 // Per evaluation:
 //   1. cube-map binning: face = argmax |z_k|, (s, t) = the other two
-//      coordinates over |z_face|, G x G bins per face, counting sort;
+//      coordinates over |z_face|, G x G bins per face, counting sort, each
+//      bin ordered by coordinates;
 //   2. per generator z_i: its K nearest neighbours by chord distance, found by
 //      a complete cap query over the bins (every point within the cap's chord
 //      radius is seen, so "not kept" implies "at least d_K away");
@@ -109,6 +110,36 @@ __global__ void k_bin_scatter(const double *__restrict__ z, int n, const int *__
     double x = z[3 * (size_t)i], y = z[3 * (size_t)i + 1], w = z[3 * (size_t)i + 2];
     zs[pos] = P4{x, y, w, 0.0};
     zf[pos] = make_float4((float)x, (float)y, (float)w, 0.0f);
+}
+
+// Order each bin's generators by their coordinates (lexicographic x, y, z).
+// The scatter above fills a bin in atomic order; sorting makes the bin
+// layout a function of the point set alone, so every later step (kNN ties,
+// the edge list of the quadrature and its reduction tree) is reproducible and
+// independent of the input order.  Bins hold a few generators: insertion sort.
+__global__ void k_bin_sort(const int *__restrict__ start, int nbins, P4 *__restrict__ zs, float4 *__restrict__ zf,
+                           int *__restrict__ sidx) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nbins) return;
+    const int p0 = start[b], p1 = start[b + 1];
+    for (int p = p0 + 1; p < p1; ++p) {
+        const P4 v = zs[p];
+        const float4 vf = zf[p];
+        const int id = sidx[p];
+        int q = p;
+        while (q > p0) {
+            const P4 u = zs[q - 1];
+            const bool greater = u.x > v.x || (u.x == v.x && (u.y > v.y || (u.y == v.y && u.z > v.z)));
+            if (!greater) break;
+            zs[q] = u;
+            zf[q] = zf[q - 1];
+            sidx[q] = sidx[q - 1];
+            --q;
+        }
+        zs[q] = v;
+        zf[q] = vf;
+        sidx[q] = id;
+    }
 }
 
 // exclusive scan of 2048-element tiles; writes tile totals
@@ -267,28 +298,51 @@ __device__ void all_query(const Grid &g, V3 q, float4 qf, int self, KnnList<K> &
 }
 
 // ---------------------------------------------------------------- clipping
-// Convex polygon in the gnomonic plane at z_i: vertex k = (u, w); edge k runs
-// from vertex k to vertex k+1 on line ln[k] (a u + b w <= c).  Lines live in
-// a side table: slots 0..K-1 follow the kNN list, K..K+3 are the starting
-// square, and K+4.. hold generators met by the exhaustive last-resort scan
-// (their ids in jx).  Each line is computed once, in FP64.  Vertex k is the
-// intersection of lines ln[k-1] and ln[k], computed from those two lines only,
-// so the final vertices do not depend on the order of clipping.
+// Convex polygon in the gnomonic plane at z_i: edge k runs from vertex k to
+// vertex k+1 on line ln[k] (a u + b w <= c).  Lines live in a side table:
+// slots 0..K-1 follow the kNN list, K..K+3 are the starting square, and
+// K+4.. hold generators met by the exhaustive last-resort scan (ids in jx).
+// Each line is computed once in FP64 and kept with an FP32 copy.  Vertex k
+// is the intersection of lines ln[k-1] and ln[k]; it is carried as an FP32
+// approximation (uf, wf) with a flag `ill` when that 2x2 system is poorly
+// conditioned.  Its FP64 value is only ever computed from its two lines
+// (meet64), so the final corners do not depend on the order of clipping.
+//
+// Inside/outside decisions are filtered: the FP32 side value
+// sd = a u + b w - c decides when |sd| > 2e-4 (|a u| + |b w| + |c|) and the
+// vertex is well conditioned (|det| >= (|a1 b2| + |a2 b1|)/30).  FP32 lines
+// carry a relative error of 6e-8 and the FP32 intersection an error of about
+// kappa * 3e-7 of the vertex scale (kappa <= 30 here), so the FP32 side value
+// is within 1e-5 of the magnitude and the filtered sign equals the FP64 sign.
+// Every other decision is taken in FP64.
 template <int K, int VMAX>
 struct Poly {
-    double u[2][VMAX], w[2][VMAX];
+    float uf[2][VMAX], wf[2][VMAX];
     unsigned char ln[2][VMAX];
+    unsigned char ill[2][VMAX];
     double la[K + 4 + VMAX], lb[K + 4 + VMAX], lc[K + 4 + VMAX];
+    float laf[K + 4 + VMAX], lbf[K + 4 + VMAX], lcf[K + 4 + VMAX];
     int jx[VMAX];
     int nv, cur;
-};
 
-__device__ __forceinline__ void meet(double a1, double b1, double c1, double a2, double b2, double c2, double &u,
-                                     double &w) {
-    double inv = 1.0 / (a1 * b2 - a2 * b1);
-    u = (c1 * b2 - c2 * b1) * inv;
-    w = (a1 * c2 - a2 * c1) * inv;
-}
+    __device__ __forceinline__ void set_line(int l, double a, double b, double c) {
+        la[l] = a; lb[l] = b; lc[l] = c;
+        laf[l] = (float)a; lbf[l] = (float)b; lcf[l] = (float)c;
+    }
+    __device__ __forceinline__ void meet64(int l1, int l2, double &u, double &w) const {
+        double inv = 1.0 / (la[l1] * lb[l2] - la[l2] * lb[l1]);
+        u = (lc[l1] * lb[l2] - lc[l2] * lb[l1]) * inv;
+        w = (la[l1] * lc[l2] - la[l2] * lc[l1]) * inv;
+    }
+    // FP32 intersection; returns true if it is ill conditioned
+    __device__ __forceinline__ bool meet32(int l1, int l2, float &u, float &w) const {
+        float p1 = laf[l1] * lbf[l2], p2 = laf[l2] * lbf[l1];
+        float det = p1 - p2;
+        u = (lcf[l1] * lbf[l2] - lcf[l2] * lbf[l1]) / det;
+        w = (laf[l1] * lcf[l2] - laf[l2] * lcf[l1]) / det;
+        return !(fabsf(det) * 30.0f >= fabsf(p1) + fabsf(p2));
+    }
+};
 
 __device__ __forceinline__ double chord2_of_r2(double r2) {
     // |normalize(z_i + u e1 + w e2) - z_i|^2 = 2 - 2/sqrt(1 + r^2), without cancellation
@@ -301,14 +355,26 @@ __device__ __forceinline__ double chord2_of_r2(double r2) {
 template <int K, int VMAX>
 __device__ int clip(Poly<K, VMAX> &P, int l, unsigned *flags, unsigned long long *amb) {
     const int c0 = P.cur, nv = P.nv;
-    const double la = P.la[l], lb = P.lb[l], lc = P.lc[l];
+    const float laf = P.laf[l], lbf = P.lbf[l], lcf = P.lcf[l];
     unsigned long long out = 0ull;
     int namb = 0;
     for (int k = 0; k < nv; ++k) {
-        double uk = P.u[c0][k], wk = P.w[c0][k];
-        double sd = la * uk + lb * wk - lc;
-        if (fabs(sd) <= 1e-14 * (fabs(la * uk) + fabs(lb * wk) + fabs(lc))) ++namb;
-        if (sd > 0.0) out |= (1ull << k);
+        const float uk = P.uf[c0][k], wk = P.wf[c0][k];
+        const float sd = fmaf(laf, uk, fmaf(lbf, wk, -lcf));
+        const float mag = fabsf(laf * uk) + fabsf(lbf * wk) + fabsf(lcf);
+        bool outside;
+        if (!P.ill[c0][k] && fabsf(sd) > 2e-4f * mag) {
+            outside = sd > 0.0f;
+        } else {
+            const int kp = (k == 0) ? nv - 1 : k - 1;
+            double u, w;
+            P.meet64(P.ln[c0][kp], P.ln[c0][k], u, w);
+            const double la = P.la[l], lb = P.lb[l], lc = P.lc[l];
+            const double sd64 = la * u + lb * w - lc;
+            if (fabs(sd64) <= 1e-14 * (fabs(la * u) + fabs(lb * w) + fabs(lc))) ++namb;
+            outside = sd64 > 0.0;
+        }
+        if (outside) out |= (1ull << k);
     }
     if (namb) atomicAdd(amb, (unsigned long long)namb);
     if (!out) return 0;
@@ -339,17 +405,18 @@ __device__ int clip(Poly<K, VMAX> &P, int l, unsigned *flags, unsigned long long
     const int c1 = c0 ^ 1;
     const int kin = (k0 == 0) ? nv - 1 : k0 - 1;  // last inside vertex before the run
     const int lin = P.ln[c0][kin], lout = P.ln[c0][k1];
-    double pu, pw, qu, qw;
-    meet(P.la[lin], P.lb[lin], P.lc[lin], la, lb, lc, pu, pw);
-    meet(la, lb, lc, P.la[lout], P.lb[lout], P.lc[lout], qu, qw);
-    P.u[c1][0] = pu; P.w[c1][0] = pw; P.ln[c1][0] = (unsigned char)l;
-    P.u[c1][1] = qu; P.w[c1][1] = qw; P.ln[c1][1] = (unsigned char)lout;
+    float pu, pw, qu, qw;
+    bool pill = P.meet32(lin, l, pu, pw);
+    bool qill = P.meet32(l, lout, qu, qw);
+    P.uf[c1][0] = pu; P.wf[c1][0] = pw; P.ln[c1][0] = (unsigned char)l; P.ill[c1][0] = pill;
+    P.uf[c1][1] = qu; P.wf[c1][1] = qw; P.ln[c1][1] = (unsigned char)lout; P.ill[c1][1] = qill;
     int o = 2;
     int k = (k1 + 1 == nv) ? 0 : k1 + 1;
     for (int cnt = 0; cnt < nv - runlen; ++cnt) {
-        P.u[c1][o] = P.u[c0][k];
-        P.w[c1][o] = P.w[c0][k];
+        P.uf[c1][o] = P.uf[c0][k];
+        P.wf[c1][o] = P.wf[c0][k];
         P.ln[c1][o] = P.ln[c0][k];
+        P.ill[c1][o] = P.ill[c0][k];
         ++o;
         k = (k + 1 == nv) ? 0 : k + 1;
     }
@@ -358,48 +425,55 @@ __device__ int clip(Poly<K, VMAX> &P, int l, unsigned *flags, unsigned long long
     return 1;
 }
 
+// an upper bound of the largest squared chord from z_i to a vertex
 template <int K, int VMAX>
-__device__ __forceinline__ double poly_r2max(const Poly<K, VMAX> &P) {
+__device__ __forceinline__ double poly_R2(const Poly<K, VMAX> &P) {
+    const int c = P.cur;
     double r2 = 0.0;
-    for (int v = 0; v < P.nv; ++v) r2 = fmax(r2, P.u[P.cur][v] * P.u[P.cur][v] + P.w[P.cur][v] * P.w[P.cur][v]);
-    return r2;
+    for (int v = 0; v < P.nv; ++v) {
+        double rv;
+        if (P.ill[c][v]) {
+            double u, w;
+            P.meet64(P.ln[c][(v == 0) ? P.nv - 1 : v - 1], P.ln[c][v], u, w);
+            rv = u * u + w * w;
+        } else {
+            rv = (double)P.uf[c][v] * P.uf[c][v] + (double)P.wf[c][v] * P.wf[c][v];
+        }
+        r2 = fmax(r2, rv);
+    }
+    return chord2_of_r2(r2 * 1.001);
 }
 
 // ------------------------------------------------------------- quadrature
-__device__ __forceinline__ double rho_at(const Density &r, V3 p) {
-    switch (r.kind) {
-    case 0:
-        return 1.0;
-    case 1: {
-        double z2 = p.z * p.z;
-        return (1.0 - r.gamma) * z2 * z2 + r.gamma;
-    }
-    default: {
-        V3 xc = mk(r.xc0, r.xc1, r.xc2);
-        V3 cr = crs(p, xc);
-        double d = atan2(sqrt(dot(cr, cr)), dot(p, xc));
-        double v = 0.5 * (1.0 - r.gamma) * (tanh((r.beta - d) / r.alpha) + 1.0) + r.gamma;
-        if (r.kind == 3) { v = v * v; v = v * v; }
-        return v;
-    }
-    }
-}
-
 struct Acc {
     double m, cx, cy, cz, e;
 };
 
-// signed spherical triangle (A, B, C) with the 7-point rule; A = z_i
-__device__ __forceinline__ void tri(const Density &rho, V3 A, V3 B, V3 C, Acc &acc) {
+// signed spherical triangle (A, B, C) with the 7-point rule; A = z_i.
+// inv_alpha: 1/alpha of the tanh cap.
+__device__ __forceinline__ void tri(const Density &r, double inv_alpha, V3 A, V3 B, V3 C, Acc &acc) {
     V3 cr = crs(sub(B, A), sub(C, A));
     double det = dot(A, cr);
     double den = 1.0 + dot(A, B) + dot(B, C) + dot(C, A);
     double area = 2.0 * atan2(det, den);
+    const V3 xc = mk(r.xc0, r.xc1, r.xc2);
 #pragma unroll 1
     for (int k = 0; k < 7; ++k) {
         V3 x = add(add(scl(A, kQb[k][0]), scl(B, kQb[k][1])), scl(C, kQb[k][2]));
-        V3 p = scl(x, 1.0 / sqrt(dot(x, x)));
-        double wr = kQw[k] * area * rho_at(rho, p);
+        V3 p = scl(x, rsqrt(dot(x, x)));
+        double rv;
+        if (r.kind == 0) {
+            rv = 1.0;
+        } else if (r.kind == 1) {
+            double z2 = p.z * p.z;
+            rv = (1.0 - r.gamma) * z2 * z2 + r.gamma;
+        } else {
+            V3 cx = crs(p, xc);
+            double d = atan2(sqrt(dot(cx, cx)), dot(p, xc));
+            rv = 0.5 * (1.0 - r.gamma) * (tanh((r.beta - d) * inv_alpha) + 1.0) + r.gamma;
+            if (r.kind == 3) { rv = rv * rv; rv = rv * rv; }
+        }
+        double wr = kQw[k] * area * rv;
         V3 dp = sub(p, A);
         acc.m += wr;
         acc.cx += wr * p.x;
@@ -457,11 +531,12 @@ __global__ void __launch_bounds__(128) k_topo(Grid g, Density rho, CellOut out, 
             all_query<K>(g, zi, zif, p, L, &st->flags);
             D2 = (L.cnt == g.n - 1) ? INFINITY : lower_d2(L.d[K - 1]);
         } else {
-            const double thmax = 0.28379410920832787;  // asin(0.28)
-            double th;
+            // caps are chord balls |x - z_i| <= r; sin(theta) = r sqrt(1 - r^2/4)
+            const double rmax = 0.28291;  // sin(theta) <= 0.28 keeps caps off the far faces
+            double r;
             float hint = out.radius ? out.radius[i] : 0.0f;
             if (hint > 0.0f && !last_pass) {
-                th = 1.1 * 2.0 * asin(fmin(0.5 * (double)hint, 1.0));
+                r = 1.1 * (double)hint;
             } else {
                 // local density from the own bin: lambda = count / solid angle
                 int b = bin_index(zi.x, zi.y, zi.z, g.G);
@@ -471,22 +546,21 @@ __global__ void __launch_bounds__(128) k_topo(Grid g, Density rho, CellOut out, 
                 double s2 = (ax * ax + ay * ay + az * az) / (am * am);  // 1 + s^2 + t^2
                 double omega = (4.0 / ((double)g.G * g.G)) / (s2 * sqrt(s2));
                 double lam = fmax((double)cbn, 1.0) / omega;
-                th = sqrt(1.5 * K / (3.141592653589793 * lam));
-                if (last_pass) th *= 2.0;
+                r = sqrt(1.5 * K / (3.141592653589793 * lam));
+                if (last_pass) r *= 2.0;
             }
-            th = fmin(th, thmax);
+            r = fmin(r, rmax);
             double r2 = 0.0;
             float r2acc = 0.0f;
             for (int attempt = 0;; ++attempt) {
-                double S = sin(th);
-                double hs = sin(0.5 * th);
-                r2 = 4.0 * hs * hs;
+                r2 = r * r;
+                const double S = r * sqrt(1.0 - 0.25 * r2) * (1.0 + 1e-9);
                 r2acc = (float)(r2 * 1.001) + 1e-12f;
                 L.cnt = 0;
                 cap_query<K>(g, zi, zif, p, S, r2acc, L, &st->flags);
-                if (L.cnt == K || th >= thmax || attempt > 8) break;
+                if (L.cnt == K || r >= rmax || attempt > 8) break;
                 double grow = (L.cnt > 0) ? sqrt(1.3 * K / (double)L.cnt) : 2.0;
-                th = fmin(th * fmax(grow, 1.25), thmax);
+                r = fmin(r * fmax(grow, 1.25), rmax);
             }
             // unkept: inside the list's range -> >= lower(d_K); outside the cap -> > r
             D2 = (L.cnt == K) ? fmin(lower_d2(L.d[K - 1]), r2) : fmin(lower_d2(r2acc), r2);
@@ -502,18 +576,21 @@ __global__ void __launch_bounds__(128) k_topo(Grid g, Density rho, CellOut out, 
         const V3 e1 = unit(crs(zi, ax));
         const V3 e2 = crs(zi, e1);
 
-        // ---- clip nearest first (FP64), with the security radius
+        // ---- clip nearest first, with the security radius
         Poly<K, VMAX> P;
         P.cur = 0;
         P.nv = 4;
         {
             // square lines: K right (u <= L), K+1 top (w <= L), K+2 left, K+3 bottom
             const double la[4] = {1, 0, -1, 0}, lb[4] = {0, 1, 0, -1};
-            const double vu[4] = {kBoxL, kBoxL, -kBoxL, -kBoxL}, vw[4] = {-kBoxL, kBoxL, kBoxL, -kBoxL};
+            const float vu[4] = {(float)kBoxL, (float)kBoxL, -(float)kBoxL, -(float)kBoxL};
+            const float vw[4] = {-(float)kBoxL, (float)kBoxL, (float)kBoxL, -(float)kBoxL};
             for (int k = 0; k < 4; ++k) {
-                P.la[K + k] = la[k]; P.lb[K + k] = lb[k]; P.lc[K + k] = kBoxL;
+                P.set_line(K + k, la[k], lb[k], kBoxL);
                 P.ln[0][k] = (unsigned char)(K + k);
-                P.u[0][k] = vu[k]; P.w[0][k] = vw[k];
+                P.uf[0][k] = vu[k];
+                P.wf[0][k] = vw[k];
+                P.ill[0][k] = 0;
             }
         }
         double R2 = chord2_of_r2(2.0 * kBoxL * kBoxL);
@@ -522,12 +599,10 @@ __global__ void __launch_bounds__(128) k_topo(Grid g, Density rho, CellOut out, 
             const double bound = fmin(lower_d2(L.d[k]), D2);
             if (bound > 4.0 * R2 * kCertMargin) { early = true; break; }
             const V3 d = sub(ld(g.zs + L.j[k]), zi);
-            P.la[k] = dot(e1, d);
-            P.lb[k] = dot(e2, d);
-            P.lc[k] = -dot(zi, d);
-            int r = clip<K, VMAX>(P, k, &st->flags, &st->ambiguous);
-            if (r < 0) { ok = false; break; }
-            if (r > 0) R2 = chord2_of_r2(poly_r2max(P));
+            P.set_line(k, dot(e1, d), dot(e2, d), -dot(zi, d));
+            int rc = clip<K, VMAX>(P, k, &st->flags, &st->ambiguous);
+            if (rc < 0) { ok = false; break; }
+            if (rc > 0) R2 = poly_R2(P);
         }
         bool boxed = false;
         for (int v = 0; v < P.nv; ++v) boxed |= (P.ln[P.cur][v] >= K);  // no extra slots yet
@@ -546,13 +621,11 @@ __global__ void __launch_bounds__(128) k_topo(Grid g, Density rho, CellOut out, 
                 int x = __ffsll((long long)~used) - 1;
                 if (x < 0 || x >= VMAX) { ok = false; break; }
                 const int l = K + 4 + x;
-                P.la[l] = dot(e1, d);
-                P.lb[l] = dot(e2, d);
-                P.lc[l] = -dot(zi, d);
+                P.set_line(l, dot(e1, d), dot(e2, d), -dot(zi, d));
                 P.jx[x] = q;
-                int r = clip<K, VMAX>(P, l, &st->flags, &st->ambiguous);
-                if (r < 0) { ok = false; break; }
-                if (r > 0) R2 = chord2_of_r2(poly_r2max(P));
+                int rc = clip<K, VMAX>(P, l, &st->flags, &st->ambiguous);
+                if (rc < 0) { ok = false; break; }
+                if (rc > 0) R2 = poly_R2(P);
             }
             boxed = false;
             for (int v = 0; v < P.nv; ++v) boxed |= (P.ln[P.cur][v] >= K && P.ln[P.cur][v] < K + 4);
@@ -582,6 +655,11 @@ __global__ void __launch_bounds__(128) k_topo(Grid g, Density rho, CellOut out, 
             V3 zn = ld(g.zs + nbj(k));
             if (lex_less(zn, best)) { best = zn; k0 = k; }
         }
+        auto corner = [&](int k) -> V3 {  // FP64 corner k from its two lines
+            double u, w;
+            P.meet64(P.ln[c][(k == 0) ? nv - 1 : k - 1], P.ln[c][k], u, w);
+            return unit(add(zi, add(scl(e1, u), scl(e2, w))));
+        };
         if (out.deg) {
             out.deg[i] = nv;
             if (nv <= out.max_deg)
@@ -592,23 +670,24 @@ __global__ void __launch_bounds__(128) k_topo(Grid g, Density rho, CellOut out, 
             cb.deg[p] = nv;
             for (int t2 = 0; t2 < nv; ++t2) {
                 const int k = (k0 + t2 < nv) ? k0 + t2 : k0 + t2 - nv;
-                V3 v = unit(add(zi, add(scl(e1, P.u[c][k]), scl(e2, P.w[c][k]))));
+                V3 v = corner(k);
                 cb.vx[(size_t)p * kCellSlots + t2] = P4{v.x, v.y, v.z, 0.0};
                 cb.nb[(size_t)p * kCellSlots + t2] = nbj(k);
             }
         } else {
-            // large cell: integrate here
+            // large cell: integrate here, edges in the canonical order
             cb.deg[p] = 0;
+            const double inv_alpha = 1.0 / rho.alpha;
             Acc acc = {0, 0, 0, 0, 0};
-            V3 vfirst = unit(add(zi, add(scl(e1, P.u[c][k0]), scl(e2, P.w[c][k0]))));
+            V3 vfirst = corner(k0);
             V3 va = vfirst;
             for (int t2 = 0; t2 < nv; ++t2) {
                 const int k = (k0 + t2 < nv) ? k0 + t2 : k0 + t2 - nv;
                 const int k1 = (k + 1 == nv) ? 0 : k + 1;
-                V3 vb = (t2 + 1 == nv) ? vfirst : unit(add(zi, add(scl(e1, P.u[c][k1]), scl(e2, P.w[c][k1]))));
+                V3 vb = (t2 + 1 == nv) ? vfirst : corner(k1);
                 V3 mu = unit(add(zi, ld(g.zs + nbj(k))));
-                tri(rho, zi, va, mu, acc);
-                tri(rho, zi, mu, vb, acc);
+                tri(rho, inv_alpha, zi, va, mu, acc);
+                tri(rho, inv_alpha, zi, mu, vb, acc);
                 va = vb;
             }
             write_cell(out, i, zi, acc, st);
@@ -617,37 +696,89 @@ __global__ void __launch_bounds__(128) k_topo(Grid g, Density rho, CellOut out, 
 }
 
 // -------------------------------------------------------------- quadrature
-// Eight lanes per cell, four cells per warp: lane s integrates the edges
-// s, s+8, ... (two signed sub-triangles each, Sec. 3.2.2), then the group
-// sums by a fixed xor butterfly, so the result does not depend on timing.
-__global__ void __launch_bounds__(256) k_quad(Grid g, Density rho, CellOut out, CellBuf cb, DevStatus *st) {
-    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const int p = (int)(gid >> 3);
-    const int s = (int)(gid & 7);
-    const int deg = (p < g.n) ? cb.deg[p] : 0;
+// Edge list: cells' edges laid end to end in bin order (eoff = exclusive
+// scan of the degrees), ecell[e] = the cell of edge e.
+__global__ void k_edge_cells(int n, const int *__restrict__ deg, const int *__restrict__ eoff,
+                             int *__restrict__ ecell) {
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    int d = deg[p], o = eoff[p];
+    for (int k = 0; k < d; ++k) ecell[o + k] = p;
+}
+
+// One thread per Voronoi edge (two signed sub-triangles of Sec. 3.2.2, 14
+// rule points).  The warp sums each cell's edges with a fixed segmented
+// suffix reduction; a cell whose edges straddle two warps is finished by the
+// second of its two parts to arrive, which adds them in a fixed order (the
+// part holding the cell's first edge + the other part), so results do not
+// depend on timing.
+__global__ void __launch_bounds__(256) k_quad(Grid g, Density rho, CellOut out, CellBuf cb, const int *eoff,
+                                              const int *ecell, double *__restrict__ parts_val,
+                                              int *__restrict__ parts_cnt, DevStatus *st) {
+    const int nedges = eoff[g.n];
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const long long wbase = e - lane;
+    int p = -1;
     Acc acc = {0, 0, 0, 0, 0};
     V3 zi = mk(0, 0, 0);
-    if (deg > 0) {
+    int e0 = 0, deg = 0;
+    if (e < nedges) {
+        p = ecell[e];
+        e0 = eoff[p];
+        deg = cb.deg[p];
+        const int k = (int)(e - e0);
         zi = ld(g.zs + p);
         const P4 *vx = cb.vx + (size_t)p * kCellSlots;
-        const int *nb = cb.nb + (size_t)p * kCellSlots;
-        for (int e = s; e < deg; e += 8) {
-            const V3 va = ld(vx + e);
-            const V3 vb = ld(vx + ((e + 1 == deg) ? 0 : e + 1));
-            const V3 mu = unit(add(zi, ld(g.zs + nb[e])));
-            tri(rho, zi, va, mu, acc);
-            tri(rho, zi, mu, vb, acc);
+        const V3 va = ld(vx + k);
+        const V3 vb = ld(vx + ((k + 1 == deg) ? 0 : k + 1));
+        const V3 mu = unit(add(zi, ld(g.zs + cb.nb[(size_t)p * kCellSlots + k])));
+        const double inv_alpha = 1.0 / rho.alpha;
+        tri(rho, inv_alpha, zi, va, mu, acc);
+        tri(rho, inv_alpha, zi, mu, vb, acc);
+    }
+    // segmented suffix sums: lane l ends with the sum of its segment from l on
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int po = __shfl_down_sync(0xffffffffu, p, o);
+        const double m = __shfl_down_sync(0xffffffffu, acc.m, o);
+        const double cx = __shfl_down_sync(0xffffffffu, acc.cx, o);
+        const double cy = __shfl_down_sync(0xffffffffu, acc.cy, o);
+        const double cz = __shfl_down_sync(0xffffffffu, acc.cz, o);
+        const double ee = __shfl_down_sync(0xffffffffu, acc.e, o);
+        if (lane + o < 32 && po == p) {
+            acc.m += m;
+            acc.cx += cx;
+            acc.cy += cy;
+            acc.cz += cz;
+            acc.e += ee;
         }
     }
-#pragma unroll
-    for (int o = 4; o > 0; o >>= 1) {
-        acc.m += __shfl_xor_sync(0xffffffffu, acc.m, o);
-        acc.cx += __shfl_xor_sync(0xffffffffu, acc.cx, o);
-        acc.cy += __shfl_xor_sync(0xffffffffu, acc.cy, o);
-        acc.cz += __shfl_xor_sync(0xffffffffu, acc.cz, o);
-        acc.e += __shfl_xor_sync(0xffffffffu, acc.e, o);
+    const int pprev = __shfl_up_sync(0xffffffffu, p, 1);
+    const bool head = (p >= 0) && (lane == 0 || pprev != p);
+    if (!head) return;
+    const bool starts_here = e0 >= wbase;
+    const bool ends_here = e0 + deg <= wbase + 32;
+    if (starts_here && ends_here) {
+        write_cell(out, g.sidx[p], zi, acc, st);
+        return;
     }
-    if (s == 0 && deg > 0) write_cell(out, g.sidx[p], zi, acc, st);
+    // split cell: publish this part, then the second arrival finishes
+    double *slot = parts_val + (size_t)p * 10 + (starts_here ? 0 : 5);
+    slot[0] = acc.m; slot[1] = acc.cx; slot[2] = acc.cy; slot[3] = acc.cz; slot[4] = acc.e;
+    __threadfence();
+    if (atomicAdd(&parts_cnt[p], 1) == 1) {
+        __threadfence();
+        const volatile double *a = parts_val + (size_t)p * 10;
+        Acc tot;
+        tot.m = a[0] + a[5];
+        tot.cx = a[1] + a[6];
+        tot.cy = a[2] + a[7];
+        tot.cz = a[3] + a[8];
+        tot.e = a[4] + a[9];
+        parts_cnt[p] = 0;  // ready for the next evaluation
+        write_cell(out, g.sidx[p], zi, tot, st);
+    }
 }
 
 }  // namespace
@@ -662,7 +793,13 @@ void bin_points(const double *z, int n, int G, int *bin_of, int *count, int *sta
     k_set_total<<<1, 1, 0, s>>>(start, nbins, n);
     cudaMemcpyAsync(cursor, start, sizeof(int) * nbins, cudaMemcpyDeviceToDevice, s);
     k_bin_scatter<<<blocks, 256, 0, s>>>(z, n, bin_of, cursor, zs, zf, sidx);
-    (*launches) += 3;
+    k_bin_sort<<<(nbins + 255) / 256, 256, 0, s>>>(start, nbins, zs, zf, sidx);
+    (*launches) += 4;
+}
+
+__global__ void k_set_total_from(int *arr, int n, const int *last_in) {
+    // arr[n] = arr[n-1] + last_in[n-1]: total of an exclusive scan
+    arr[n] = arr[n - 1] + last_in[n - 1];
 }
 
 void cell_passes(const Grid &g, const Density &rho, const CellOut &out, const CellBuf &cb, int *list1, int *list2,
@@ -680,11 +817,17 @@ void cell_passes(const Grid &g, const Density &rho, const CellOut &out, const Ce
     int scan_all = g.n <= 20000 ? 1 : 0;
     k_topo<128, 64><<<rblocks, 64, 0, s>>>(g, rho, out, cb, list2, &st->retry_count[1], nullptr, &st->retry_count[2],
                                            1, scan_all, st);
+    // edge list for the quadrature
+    exclusive_scan(cb.deg, cb.eoff, g.n, cb.scan_tmp, s, launches);
+    k_set_total_from<<<1, 1, 0, s>>>(cb.eoff, g.n, cb.deg);
+    k_edge_cells<<<(g.n + 255) / 256, 256, 0, s>>>(g.n, cb.deg, cb.eoff, cb.ecell);
     if (ev0) cudaEventRecord(ev0, s);
-    const long long threads = 8LL * g.n;
-    k_quad<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(g, rho, out, cb, st);
+    // Euler: a full tessellation has 6N - 12 edge sides; failed cells only lower the count
+    const long long max_edges = 6LL * g.n;
+    k_quad<<<(unsigned)((max_edges + 255) / 256), 256, 0, s>>>(g, rho, out, cb, cb.eoff, cb.ecell, cb.parts_val,
+                                                               cb.parts_cnt, st);
     if (ev1) cudaEventRecord(ev1, s);
-    (*launches) += 4;
+    (*launches) += 6;
     (*cell_launches) += 4;
 }
 

@@ -72,9 +72,14 @@ struct CellOut {
 // and the bin-order index of the neighbour across edge k (corner k -> k+1).
 constexpr int kCellSlots = 16;
 struct CellBuf {
-    int *deg;   // n
-    P4 *vx;     // n * kCellSlots
-    int *nb;    // n * kCellSlots
+    int *deg;          // n
+    P4 *vx;            // n * kCellSlots
+    int *nb;           // n * kCellSlots
+    int *eoff;         // n + 1: exclusive scan of deg (edge list offsets)
+    int *ecell;        // 6n: cell of each edge
+    int *scan_tmp;     // scratch of the scan over n (2 * (n / 2048 + 64) + 64 ints)
+    double *parts_val; // 10n: two partial sums per cell split across warps
+    int *parts_cnt;    // n: arrivals per split cell, zero between evaluations
 };
 
 // ---- binning (cells.cu) ----

@@ -56,7 +56,12 @@ constexpr size_t oCnb = oCvx + up(sizeof(P4) * kMaxN * kCellSlots);
 constexpr size_t oFc = oCnb + up(sizeof(int) * kMaxN * kCellSlots);
 constexpr size_t oH = oFc + up(sizeof(double) * kMaxN);
 constexpr size_t oG = oH + up(sizeof(double) * kMaxN);
-constexpr size_t kBytes = oG + up(sizeof(double) * 3 * kMaxN);  // about 11.4 MB
+constexpr size_t oEoff = oG + up(sizeof(double) * 3 * kMaxN);
+constexpr size_t oEcell = oEoff + up(sizeof(int) * (kMaxN + 1));
+constexpr size_t oEscan = oEcell + up(sizeof(int) * 6 * kMaxN);
+constexpr size_t oPval = oEscan + up(sizeof(int) * (2 * (kMaxN / 2048 + 64) + 64));
+constexpr size_t oPcnt = oPval + up(sizeof(double) * 10 * kMaxN);
+constexpr size_t kBytes = oPcnt + up(sizeof(int) * kMaxN);  // about 13.2 MB
 
 __device__ __align__(256) unsigned char g_scratch[kBytes];
 
@@ -156,6 +161,15 @@ extern "C" scvt_status scvt_energy_grad_static(int64_t n, const scvt_density *rh
     cb.deg = cdeg;
     cb.vx = cvx;
     cb.nb = cnb;
+    cb.eoff = (int *)(base + oEoff);
+    cb.ecell = (int *)(base + oEcell);
+    cb.scan_tmp = (int *)(base + oEscan);
+    cb.parts_val = (double *)(base + oPval);
+    cb.parts_cnt = (int *)(base + oPcnt);
+    if (cudaMemsetAsync(cb.parts_cnt, 0, sizeof(int) * N, s) != cudaSuccess) {
+        cudaGetLastError();
+        return SCVT_ERR_CUDA;
+    }
     Density d;
     d.kind = rho->kind;
     d.gamma = rho->gamma;
