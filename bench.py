@@ -212,41 +212,54 @@ def run_ours(args, w):
         t_max = float(tt.item())
     value = w.n * iters * ws / t_max
 
-    # dominant kernel: the first-pass cell kernel (clip + quadrature), timed by
-    # CUDA events on the engine stream around each launch
-    cell_ms = st["cell_kernel_ms"] / max(st["cell_kernel_timed"], 1)
+    # dominant kernel: k_quad (the cell quadrature), timed by CUDA events on
+    # the engine stream around each launch inside the timed region
+    quad_ms = st["cell_kernel_ms"] / max(st["cell_kernel_timed"], 1)
     flops_gen = fp64_flops_per_generator(w.density.kind)
     peak = fp64_peak_tflops()
-    achieved = w.n * flops_gen / (cell_ms * 1e-3) / 1e12
-    roofline = {"bound": "alu", "kernel": "k_cells (first pass)", "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                "flops_per_generator": flops_gen, "avg_launch_ms": cell_ms,
-                "peak_source": "FP64 pipe: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (derived, not measured)"}
+    achieved = w.n * flops_gen / (quad_ms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "kernel": "k_quad", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": quad_traffic_bytes(w.n),
+                "flops_per_generator": flops_gen, "avg_launch_ms": quad_ms,
+                "peak_source": "derived FP64 pipe peak: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz "
+                               "(no FP64 figure in the measured-peaks file; a DFMA microbenchmark on this pool "
+                               "measured 1.006 TFLOP/s)",
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_quad launch at "
+                                  "N = 163,842, scaled by N (profiles/k_quad_tanh_163842.md)"}
 
-    # end to end through the C ABI with host buffers: every step copies Z in
-    # from pinned host memory and the result back (resume-if-unchanged mode)
+    # end to end through the C ABI with host buffers: a second engine replays
+    # the same warm-up (evaluations are deterministic, so it reaches the same
+    # state), then the same K iterations run with Z in pinned host memory:
+    # every step copies Z in, checks it against the engine's iterate, runs one
+    # iteration and copies the result back
     e2e = None
     if not args.no_e2e:
+        eng2 = Engine(w.n, w.density, lbfgs_m=w.lbfgs_m, device=local)
+        z2 = torch.from_numpy(z_host).cuda(local)
+        eng2.lbfgs_solve(z2, max_iter=args.warmup, grad_tol=0.0)
         zp = torch.empty((w.n, 3), dtype=torch.float64, pin_memory=True)
-        zp.copy_(z.cpu())
+        zp.copy_(z2.cpu())
+        del z2
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
-        eng.lbfgs_solve(zp.numpy(), max_iter=1, grad_tol=0.0, warm_start=2)  # settle
         torch.cuda.synchronize()
-        e0.record(eng.stream)
+        e0.record(eng2.stream)
         k_e2e = 0
         for _ in range(args.steps):
-            r = eng.lbfgs_solve(zp.numpy(), max_iter=1, grad_tol=0.0, warm_start=2)
+            r = eng2.lbfgs_solve(zp.numpy(), max_iter=1, grad_tol=0.0, warm_start=2)
             k_e2e += r["iters"]
-        e1.record(eng.stream)
+        e1.record(eng2.stream)
         torch.cuda.synchronize()
         te = e0.elapsed_time(e1) / 1e3
+        same = bool(np.array_equal(zp.numpy(), z.cpu().numpy()))
+        eng2.close()
         if ws > 1:
             tt = torch.tensor([te], device="cuda")
             torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
             te = float(tt.item())
         e2e = {"value": w.n * k_e2e * ws / te, "unit": "generator-updates/s",
-               "h2d_bytes_per_step": w.n * 24, "d2h_bytes_per_step": w.n * 24}
+               "h2d_bytes_per_step": w.n * 24, "d2h_bytes_per_step": w.n * 24,
+               "same_iterates_as_device_run": same}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -285,18 +298,35 @@ def fp64_peak_tflops() -> float:
 
 
 def fp64_flops_per_generator(kind: int) -> float:
-    """Algorithmic FP64 flop count of one cell, with transcendentals weighted
-    as FP64 flop equivalents (see the design notes for the derivation)."""
-    base = 7.2e3
-    per_point_density = {0: 0.0, 1: 6.0, 2: 25.0 + TR["sqrt"] + TR["atan2"] + TR["tanh"] + TR["div"],
-                         3: 28.0 + TR["sqrt"] + TR["atan2"] + TR["tanh"] + TR["div"]}[kind]
-    per_point_fixed = TR["sqrt"] + TR["div"]
-    per_tri = TR["atan2"]
-    return base + 84 * (per_point_density + per_point_fixed) + 12 * per_tri
+    """FP64 work of the cell quadrature per generator, in flop equivalents.
+
+    Per Voronoi edge the method integrates two signed sub-triangles (Sec.
+    3.2.2): per sub-triangle the Van Oosterom-Strackee area (differences,
+    cross and dot products: 38 flops, one atan2) and 7 rule points; per point
+    the projected point (combination, norm, rsqrt, scale: 37 + rsqrt), the
+    density, the weight and the accumulation of m, c and |p - z|^2 (24).  The
+    tanh cap density costs a cross product, a norm and a dot (19), sqrt,
+    atan2, a subtract-multiply and tanh (+5); X3 costs 6.  A transcendental is
+    charged what it costs on this GPU in FMA-pipe time (per-call costs
+    measured with CUDA events, in DFMA equivalents x 2 flop).  The cell of a
+    generator has 6 edges on average (Euler: 2E = 6N - 12).
+    """
+    rsqrt, sqrt, atan2, tanh = 2 * 6.9, 2 * 9.6, 2 * 41.0, 2 * 15.8
+    dens = {0: 0.0, 1: 6.0, 2: 24.0 + sqrt + atan2 + tanh, 3: 28.0 + sqrt + atan2 + tanh}[kind]
+    point = 37.0 + rsqrt + 24.0 + dens
+    subtri = 38.0 + atan2 + 7 * point
+    mu = 11.0 + rsqrt
+    return 6.0 * (2 * subtri + mu)
 
 
-# FP64 flop-equivalents charged per transcendental call
-TR = {"sqrt": 8.0, "div": 8.0, "atan2": 40.0, "tanh": 30.0}
+def fp64_peak_tflops() -> float:
+    return 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def quad_traffic_bytes(n: int):
+    """DRAM bytes of one k_quad launch: ncu at N = 163,842 (65.81 MB read +
+    2.48 MB written, tanh cap), scaled by the number of generators."""
+    return (65.813248e6 + 2.48192e6) * n / 163842
 
 
 def main():

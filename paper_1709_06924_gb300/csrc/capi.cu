@@ -39,7 +39,7 @@ struct Bufs {
     double *rho = nullptr;                   // kMaxM + 1
     double *hist = nullptr;                  // (m + 1) slots of S and Y, 3n each
     P4 *zs = nullptr;
-    float4 *zf = nullptr;
+    float4 *zf = nullptr, *zl = nullptr;
     P4 *cvx = nullptr;
     int *cdeg = nullptr, *cnb = nullptr, *eoff = nullptr, *ecell = nullptr, *escan = nullptr, *pcnt = nullptr;
     double *pval = nullptr;
@@ -150,13 +150,14 @@ scvt_status evaluate_dev(scvt_handle *H, const double *zdev, double *grad, doubl
     int64_t *L = &H->stats.kernel_launches;
     if (H->profiling) cudaEventRecord(H->ev_e0, s);
     CK(cudaMemsetAsync(B.st, 0, sizeof(DevStatus), s), "reset status");
-    bin_points(zdev, n, H->G, B.bin_of, B.count, B.start, B.cursor, B.scan_tmp, B.zs, B.zf, B.sidx, B.st, s, L);
+    bin_points(zdev, n, H->G, B.bin_of, B.count, B.start, B.cursor, B.scan_tmp, B.zs, B.zf, B.zl, B.sidx, B.st, s, L);
     Grid g;
     g.n = n;
     g.G = H->G;
     g.nbins = 6 * H->G * H->G;
     g.zs = B.zs;
     g.zf = B.zf;
+    g.zl = B.zl;
     g.sidx = B.sidx;
     g.bstart = B.start;
     CellOut out;
@@ -431,7 +432,7 @@ void scvt_destroy(scvt_handle *H) {
     if (!H) return;
     Bufs &b = H->b;
     void *ptrs[] = {b.z, b.zt, b.g, b.gt, b.h, b.ht, b.fc, b.q, b.yv, b.nrm, b.mass, b.moment, b.stage_a, b.stage_b,
-                    b.partials, b.scal, b.rho, b.hist, b.zs, b.zf, b.cvx, b.cnb, b.cdeg, b.eoff, b.ecell, b.escan, b.pval, b.pcnt, b.bin_of, b.count, b.start, b.cursor, b.scan_tmp,
+                    b.partials, b.scal, b.rho, b.hist, b.zs, b.zf, b.zl, b.cvx, b.cnb, b.cdeg, b.eoff, b.ecell, b.escan, b.pval, b.pcnt, b.bin_of, b.count, b.start, b.cursor, b.scan_tmp,
                     b.sidx, b.list1, b.list2, b.deg, b.radius, b.st};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -483,7 +484,7 @@ scvt_status scvt_create(const scvt_config *cfg, void *cuda_stream, scvt_handle *
     AL(b.stage_a, n3); AL(b.stage_b, n3);
     AL(b.partials, 4 * 1024); AL(b.scal, 128); AL(b.rho, kMaxM + 1);
     AL(b.hist, (size_t)(H->m + 1) * 2 * n3);
-    AL(b.zs, n); AL(b.zf, n); AL(b.cvx, (size_t)n * kCellSlots); AL(b.cnb, (size_t)n * kCellSlots);
+    AL(b.zs, n); AL(b.zf, n); AL(b.zl, n); AL(b.cvx, (size_t)n * kCellSlots); AL(b.cnb, (size_t)n * kCellSlots);
     AL(b.cdeg, n); AL(b.eoff, n + 1); AL(b.ecell, 6 * (size_t)n); AL(b.escan, 2 * (n / 2048 + 64) + 64);
     AL(b.pval, 10 * (size_t)n); AL(b.pcnt, n);
     AL(b.bin_of, n); AL(b.count, nbins); AL(b.start, nbins + 1); AL(b.cursor, nbins);

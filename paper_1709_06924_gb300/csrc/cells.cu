@@ -24,6 +24,8 @@
 // later reduction runs in index order and is independent of the binning.
 #include <math.h>
 
+#include <algorithm>
+
 #include "scvt_internal.cuh"
 
 namespace scvt {
@@ -102,14 +104,16 @@ __global__ void k_bin_count(const double *__restrict__ z, int n, int G, int *__r
 
 __global__ void k_bin_scatter(const double *__restrict__ z, int n, const int *__restrict__ bin_of,
                               int *__restrict__ cursor, P4 *__restrict__ zs, float4 *__restrict__ zf,
-                              int *__restrict__ sidx) {
+                              float4 *__restrict__ zl, int *__restrict__ sidx) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int pos = atomicAdd(&cursor[bin_of[i]], 1);
     sidx[pos] = i;
     double x = z[3 * (size_t)i], y = z[3 * (size_t)i + 1], w = z[3 * (size_t)i + 2];
     zs[pos] = P4{x, y, w, 0.0};
-    zf[pos] = make_float4((float)x, (float)y, (float)w, 0.0f);
+    const float hx = (float)x, hy = (float)y, hw = (float)w;
+    zf[pos] = make_float4(hx, hy, hw, 0.0f);
+    zl[pos] = make_float4((float)(x - (double)hx), (float)(y - (double)hy), (float)(w - (double)hw), 0.0f);
 }
 
 // Order each bin's generators by their coordinates (lexicographic x, y, z).
@@ -118,13 +122,13 @@ __global__ void k_bin_scatter(const double *__restrict__ z, int n, const int *__
 // the edge list of the quadrature and its reduction tree) is reproducible and
 // independent of the input order.  Bins hold a few generators: insertion sort.
 __global__ void k_bin_sort(const int *__restrict__ start, int nbins, P4 *__restrict__ zs, float4 *__restrict__ zf,
-                           int *__restrict__ sidx) {
+                           float4 *__restrict__ zl, int *__restrict__ sidx) {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nbins) return;
     const int p0 = start[b], p1 = start[b + 1];
     for (int p = p0 + 1; p < p1; ++p) {
         const P4 v = zs[p];
-        const float4 vf = zf[p];
+        const float4 vf = zf[p], vl = zl[p];
         const int id = sidx[p];
         int q = p;
         while (q > p0) {
@@ -133,11 +137,13 @@ __global__ void k_bin_sort(const int *__restrict__ start, int nbins, P4 *__restr
             if (!greater) break;
             zs[q] = u;
             zf[q] = zf[q - 1];
+            zl[q] = zl[q - 1];
             sidx[q] = sidx[q - 1];
             --q;
         }
         zs[q] = v;
         zf[q] = vf;
+        zl[q] = vl;
         sidx[q] = id;
     }
 }
@@ -203,12 +209,14 @@ __global__ void k_set_total(int *start, int nbins, int n) { start[nbins] = n; }
 // The neighbour search runs on FP32 copies of the coordinates (the FP32 pipe
 // is ~70x the FP64 pipe on this part); it only has to produce candidates and a
 // certified lower bound on the distance of every generator it did not keep.
-// With coordinates rounded to FP32 (error <= 6e-8 each) and the FP32
-// difference and squared norm, the true chord d of a scanned point satisfies
-// d >= sqrt(d2f) (1 - 3e-7) - 4e-7; lower_d2() returns the square of that.
-__device__ __forceinline__ double lower_d2(float d2f) {
-    double d = sqrt((double)d2f) * (1.0 - 3e-7) - 4e-7;
-    return d > 0.0 ? d * d : 0.0;
+// FP32 coordinates are within 3e-8 of the FP64 ones, so an FP32 difference is
+// within 1.1e-7 + 6e-8 |d| of the true one, and the FP32 squared norm and
+// square root add 1.8e-7 relative: the true chord is at least
+// sqrt(d2f) (1 - 2.6e-7) - 1.1e-7.  lower32() uses (1 - 1e-6) and 5e-7, and
+// rounds its own square down.
+__device__ __forceinline__ float lower32(float d2f) {
+    float d = sqrtf(d2f) * (1.0f - 1e-6f) - 5e-7f;
+    return d > 0.0f ? d * d * (1.0f - 1e-6f) : 0.0f;
 }
 
 template <int K>
@@ -237,37 +245,40 @@ __device__ __forceinline__ void check_duplicate(const Grid &g, V3 q, int p, unsi
     if (d.x == 0.0 && d.y == 0.0 && d.z == 0.0) atomicOr(flags, FLAG_DUPLICATE);
 }
 
-// Every generator p (bin order) within chord r of q, found through the bins
-// that the cap {x : x.q >= cos theta} can reach (sin theta = S < 0.28), is
-// scanned; those with d2f <= r2acc are offered to the list.  For face
-// (a, sign) the values s = x_b / |x_a| attained in the cap lie between the
-// roots of (q_b - s sign q_a)^2 = S^2 (1 + s^2): the planes of constant s are
-// great circles through the c axis, and one meets the cap iff q's distance
-// to it is at most S.
+// Every generator p (bin order) within chord r of z_i is scanned; those with
+// d2f <= r2acc are offered to the list.  S >= sin(theta) of that ball, with
+// FP32 rounding and the FP32 centre already covered.  For face (a, sign) the
+// values s = x_b / |x_a| attained in the cap lie between the roots of
+// (q_b - s sign q_a)^2 = S^2 (1 + s^2): the planes of constant s are great
+// circles through the c axis, and one meets the cap iff q's distance to it is
+// at most S.  The FP32 roots are widened by 4e-6/A + 1e-6 (their error is
+// below 4e-7/A).
 template <int K>
-__device__ void cap_query(const Grid &g, V3 q, float4 qf, int self, double S, float r2acc, KnnList<K> &L,
+__device__ void cap_query(const Grid &g, V3 q, float4 qf, int self, float S, float r2acc, KnnList<K> &L,
                           unsigned *flags) {
-    const double S2 = S * S;
-    const double qv[3] = {q.x, q.y, q.z};
+    const float S2 = S * S;
+    const float qv[3] = {qf.x, qf.y, qf.z};
     for (int a = 0; a < 3; ++a) {
-        double qa = qv[a];
-        double A = qa * qa - S2;
-        if (A <= 0.0) continue;  // the cap cannot reach face a (|x_a| >= 1/sqrt3 there)
-        double sg = qa > 0.0 ? 1.0 : -1.0;
-        int face = 2 * a + (qa < 0.0 ? 1 : 0);
+        const float qa = qv[a];
+        const float A = qa * qa - S2;
+        if (A <= 0.0f) continue;  // the cap cannot reach face a (|x_a| >= 1/sqrt3 there)
+        const float sg = qa > 0.0f ? 1.0f : -1.0f;
+        const int face = 2 * a + (qa < 0.0f ? 1 : 0);
+        const float invA = 1.0f / A;
+        const float margin = 4e-6f * invA + 1e-6f;
         int lo[2], hi[2];
         bool empty = false;
         for (int r = 0; r < 2; ++r) {
-            double qb = qv[(a + 1 + r) % 3];
-            double disc = qa * qa + qb * qb - S2;
-            double rt = S * sqrt(fmax(disc, 0.0));
-            double s0 = (sg * qa * qb - rt) / A - 1e-9;
-            double s1 = (sg * qa * qb + rt) / A + 1e-9;
-            if (s0 > 1.0 || s1 < -1.0) { empty = true; break; }
-            s0 = fmax(s0, -1.0);
-            s1 = fmin(s1, 1.0);
-            lo[r] = min(max((int)floor((s0 + 1.0) * 0.5 * g.G), 0), g.G - 1);
-            hi[r] = min(max((int)floor((s1 + 1.0) * 0.5 * g.G), 0), g.G - 1);
+            const float qb = qv[(a + 1 + r) % 3];
+            const float disc = qa * qa + qb * qb - S2;
+            const float rt = S * sqrtf(fmaxf(disc, 0.0f));
+            float s0 = (sg * qa * qb - rt) * invA - margin;
+            float s1 = (sg * qa * qb + rt) * invA + margin;
+            if (s0 > 1.0f || s1 < -1.0f) { empty = true; break; }
+            s0 = fmaxf(s0, -1.0f);
+            s1 = fminf(s1, 1.0f);
+            lo[r] = min(max((int)floorf((s0 + 1.0f) * 0.5f * g.G), 0), g.G - 1);
+            hi[r] = min(max((int)floorf((s1 + 1.0f) * 0.5f * g.G), 0), g.G - 1);
         }
         if (empty) continue;
         for (int iv = lo[1]; iv <= hi[1]; ++iv) {
@@ -298,80 +309,115 @@ __device__ void all_query(const Grid &g, V3 q, float4 qf, int self, KnnList<K> &
 }
 
 // ---------------------------------------------------------------- clipping
-// Convex polygon in the gnomonic plane at z_i: edge k runs from vertex k to
-// vertex k+1 on line ln[k] (a u + b w <= c).  Lines live in a side table:
-// slots 0..K-1 follow the kNN list, K..K+3 are the starting square, and
-// K+4.. hold generators met by the exhaustive last-resort scan (ids in jx).
-// Each line is computed once in FP64 and kept with an FP32 copy.  Vertex k
-// is the intersection of lines ln[k-1] and ln[k]; it is carried as an FP32
-// approximation (uf, wf) with a flag `ill` when that 2x2 system is poorly
-// conditioned.  Its FP64 value is only ever computed from its two lines
-// (meet64), so the final corners do not depend on the order of clipping.
+// Convex polygon in the gnomonic plane at z_i (frame e1, e2): edge k runs
+// from vertex k to vertex k+1 on line ln[k]: a u + b w <= c with
+// (a, b, c) = (e1.d, e2.d, -z_i.d), d = z_j - z_i.  Line slots: 0..K-1 follow
+// the kNN list, K..K+3 are the starting square, K+4.. hold generators met by
+// the exhaustive last-resort scan (ids in jx).  The table keeps FP32 lines
+// (d taken in FP64, then rounded; c = -z_i.d in FP64, then rounded); an FP64
+// line is recomputed from the generator when needed.  Vertex k is the
+// intersection of lines ln[k-1] and ln[k], carried as an FP32 approximation
+// with a flag `ill` when that 2x2 system is poorly conditioned; its FP64
+// value is only ever computed from its two FP64 lines, so the final corners
+// do not depend on the order of clipping.
 //
 // Inside/outside decisions are filtered: the FP32 side value
-// sd = a u + b w - c decides when |sd| > 2e-4 (|a u| + |b w| + |c|) and the
-// vertex is well conditioned (|det| >= (|a1 b2| + |a2 b1|)/30).  FP32 lines
-// carry a relative error of 6e-8 and the FP32 intersection an error of about
-// kappa * 3e-7 of the vertex scale (kappa <= 30 here), so the FP32 side value
-// is within 1e-5 of the magnitude and the filtered sign equals the FP64 sign.
-// Every other decision is taken in FP64.
-template <int K, int VMAX>
+// sd = a u + b w - c decides when |sd| > 2e-4 M, M = (|a|+|b|)(|u|+|w|) + |c|,
+// and the vertex is well conditioned (|det| >= (|a1 b2| + |a2 b1|)/30).
+// FP32 lines are within ~2e-7 of M's line part and the FP32 vertex within
+// kappa * 3e-7 <= 1e-5 of its scale, so the FP32 side value is within ~1e-5 M
+// and its sign equals the FP64 sign.  Every other decision is taken in FP64.
+struct Frame {
+    V3 zi, e1, e2;
+    float3 e1f, e2f;
+    const P4 *zs;
+};
+
+template <int K, int VMAX, int EXTRA>
 struct Poly {
     float uf[2][VMAX], wf[2][VMAX];
     unsigned char ln[2][VMAX];
     unsigned char ill[2][VMAX];
-    double la[K + 4 + VMAX], lb[K + 4 + VMAX], lc[K + 4 + VMAX];
-    float laf[K + 4 + VMAX], lbf[K + 4 + VMAX], lcf[K + 4 + VMAX];
-    int jx[VMAX];
+    float la[K + 4 + EXTRA], lb[K + 4 + EXTRA], lc[K + 4 + EXTRA];
+    int jx[EXTRA > 0 ? EXTRA : 1];
+    const int *kj;  // kNN list ids
     int nv, cur;
 
-    __device__ __forceinline__ void set_line(int l, double a, double b, double c) {
-        la[l] = a; lb[l] = b; lc[l] = c;
-        laf[l] = (float)a; lbf[l] = (float)b; lcf[l] = (float)c;
+    __device__ __forceinline__ int gen_of(int l) const {
+        return (l < K) ? kj[l] : ((l < K + 4) ? -1 - (l - K) : jx[l - (K + 4)]);
     }
-    __device__ __forceinline__ void meet64(int l1, int l2, double &u, double &w) const {
-        double inv = 1.0 / (la[l1] * lb[l2] - la[l2] * lb[l1]);
-        u = (lc[l1] * lb[l2] - lc[l2] * lb[l1]) * inv;
-        w = (la[l1] * lc[l2] - la[l2] * lc[l1]) * inv;
+    __device__ __forceinline__ void set_line(const Frame &F, int l, int j) {
+        const V3 d = sub(ld(F.zs + j), F.zi);
+        const float dx = (float)d.x, dy = (float)d.y, dz = (float)d.z;
+        la[l] = F.e1f.x * dx + F.e1f.y * dy + F.e1f.z * dz;
+        lb[l] = F.e2f.x * dx + F.e2f.y * dy + F.e2f.z * dz;
+        lc[l] = (float)(-dot(F.zi, d));
+    }
+    __device__ __forceinline__ void line64(const Frame &F, int l, double &a, double &b, double &c) const {
+        if (l >= K && l < K + 4) {
+            const int k = l - K;  // square: right, top, left, bottom
+            a = (k == 0) ? 1.0 : ((k == 2) ? -1.0 : 0.0);
+            b = (k == 1) ? 1.0 : ((k == 3) ? -1.0 : 0.0);
+            c = kBoxL;
+            return;
+        }
+        const V3 d = sub(ld(F.zs + gen_of(l)), F.zi);
+        a = dot(F.e1, d);
+        b = dot(F.e2, d);
+        c = -dot(F.zi, d);
+    }
+    __device__ __forceinline__ static void meet(double a1, double b1, double c1, double a2, double b2, double c2,
+                                                double &u, double &w) {
+        double inv = 1.0 / (a1 * b2 - a2 * b1);
+        u = (c1 * b2 - c2 * b1) * inv;
+        w = (a1 * c2 - a2 * c1) * inv;
+    }
+    __device__ __forceinline__ void meet64(const Frame &F, int l1, int l2, double &u, double &w) const {
+        double a1, b1, c1, a2, b2, c2;
+        line64(F, l1, a1, b1, c1);
+        line64(F, l2, a2, b2, c2);
+        meet(a1, b1, c1, a2, b2, c2, u, w);
     }
     // FP32 intersection; returns true if it is ill conditioned
     __device__ __forceinline__ bool meet32(int l1, int l2, float &u, float &w) const {
-        float p1 = laf[l1] * lbf[l2], p2 = laf[l2] * lbf[l1];
+        float p1 = la[l1] * lb[l2], p2 = la[l2] * lb[l1];
         float det = p1 - p2;
-        u = (lcf[l1] * lbf[l2] - lcf[l2] * lbf[l1]) / det;
-        w = (laf[l1] * lcf[l2] - laf[l2] * lcf[l1]) / det;
+        u = (lc[l1] * lb[l2] - lc[l2] * lb[l1]) / det;
+        w = (la[l1] * lc[l2] - la[l2] * lc[l1]) / det;
         return !(fabsf(det) * 30.0f >= fabsf(p1) + fabsf(p2));
     }
 };
 
-__device__ __forceinline__ double chord2_of_r2(double r2) {
-    // |normalize(z_i + u e1 + w e2) - z_i|^2 = 2 - 2/sqrt(1 + r^2), without cancellation
-    double q = sqrt(1.0 + r2);
-    return 2.0 * r2 / (q * (1.0 + q));
+// FP32 upper bound of 2 - 2/sqrt(1 + r2) (the squared chord of a vertex at
+// gnomonic radius^2 r2), inflated past its own rounding
+__device__ __forceinline__ float chord2_up(float r2) {
+    float q = sqrtf(1.0f + r2);
+    return 2.0f * r2 / (q * (1.0f + q)) * (1.0f + 1e-5f);
 }
 
 // clip by line slot l; returns 1 if the polygon changed, 0 if not, -1 on
 // capacity / empty errors
-template <int K, int VMAX>
-__device__ int clip(Poly<K, VMAX> &P, int l, unsigned *flags, unsigned long long *amb) {
+template <int K, int VMAX, int EXTRA>
+__device__ int clip(Poly<K, VMAX, EXTRA> &P, const Frame &F, int l, unsigned *flags, unsigned long long *amb) {
     const int c0 = P.cur, nv = P.nv;
-    const float laf = P.laf[l], lbf = P.lbf[l], lcf = P.lcf[l];
+    const float la = P.la[l], lb = P.lb[l], lc = P.lc[l];
+    const float lab = fabsf(la) + fabsf(lb);
     unsigned long long out = 0ull;
     int namb = 0;
     for (int k = 0; k < nv; ++k) {
         const float uk = P.uf[c0][k], wk = P.wf[c0][k];
-        const float sd = fmaf(laf, uk, fmaf(lbf, wk, -lcf));
-        const float mag = fabsf(laf * uk) + fabsf(lbf * wk) + fabsf(lcf);
+        const float sd = fmaf(la, uk, fmaf(lb, wk, -lc));
+        const float mag = lab * (fabsf(uk) + fabsf(wk)) + fabsf(lc);
         bool outside;
         if (!P.ill[c0][k] && fabsf(sd) > 2e-4f * mag) {
             outside = sd > 0.0f;
         } else {
             const int kp = (k == 0) ? nv - 1 : k - 1;
-            double u, w;
-            P.meet64(P.ln[c0][kp], P.ln[c0][k], u, w);
-            const double la = P.la[l], lb = P.lb[l], lc = P.lc[l];
-            const double sd64 = la * u + lb * w - lc;
-            if (fabs(sd64) <= 1e-14 * (fabs(la * u) + fabs(lb * w) + fabs(lc))) ++namb;
+            double u, w, a, b, c;
+            P.meet64(F, P.ln[c0][kp], P.ln[c0][k], u, w);
+            P.line64(F, l, a, b, c);
+            const double sd64 = a * u + b * w - c;
+            if (fabs(sd64) <= 1e-14 * (fabs(a * u) + fabs(b * w) + fabs(c))) ++namb;
             outside = sd64 > 0.0;
         }
         if (outside) out |= (1ull << k);
@@ -426,22 +472,22 @@ __device__ int clip(Poly<K, VMAX> &P, int l, unsigned *flags, unsigned long long
 }
 
 // an upper bound of the largest squared chord from z_i to a vertex
-template <int K, int VMAX>
-__device__ __forceinline__ double poly_R2(const Poly<K, VMAX> &P) {
+template <int K, int VMAX, int EXTRA>
+__device__ __forceinline__ float poly_R2(const Poly<K, VMAX, EXTRA> &P, const Frame &F) {
     const int c = P.cur;
-    double r2 = 0.0;
+    float r2 = 0.0f;
     for (int v = 0; v < P.nv; ++v) {
-        double rv;
+        float rv;
         if (P.ill[c][v]) {
             double u, w;
-            P.meet64(P.ln[c][(v == 0) ? P.nv - 1 : v - 1], P.ln[c][v], u, w);
-            rv = u * u + w * w;
+            P.meet64(F, P.ln[c][(v == 0) ? P.nv - 1 : v - 1], P.ln[c][v], u, w);
+            rv = (float)(u * u + w * w);
         } else {
-            rv = (double)P.uf[c][v] * P.uf[c][v] + (double)P.wf[c][v] * P.wf[c][v];
+            rv = P.uf[c][v] * P.uf[c][v] + P.wf[c][v] * P.wf[c][v];
         }
-        r2 = fmax(r2, rv);
+        r2 = fmaxf(r2, rv);
     }
-    return chord2_of_r2(r2 * 1.001);
+    return chord2_up(r2 * 1.001f);
 }
 
 // ------------------------------------------------------------- quadrature
@@ -506,12 +552,13 @@ __device__ __forceinline__ bool lex_less(V3 a, V3 b) {
 }
 
 // -------------------------------------------------------------- topology
-// One thread per cell.  mode: list == nullptr -> all bin positions, else the
-// retry list.  The certified polygon is written to the cell buffer with its
-// edges rotated to start at the neighbour with the lexicographically
-// smallest coordinates (so the layout is the same for any input order).
-// Cells with more than kCellSlots edges are integrated here, in-thread.
-template <int K, int VMAX>
+// One thread per cell.  list == nullptr -> all bin positions, else the retry
+// list.  The certified polygon is written to the cell buffer with its edges
+// rotated to start at the neighbour with the lexicographically smallest
+// coordinates (so the layout is the same for any input order).  Cells with
+// more than kCellSlots edges are integrated here, in-thread.  EXTRA > 0 only
+// in the last pass, which may clip by every generator.
+template <int K, int VMAX, int EXTRA>
 __global__ void __launch_bounds__(128) k_topo(Grid g, Density rho, CellOut out, CellBuf cb,
                                               const int *__restrict__ list, const unsigned *__restrict__ list_count,
                                               int *__restrict__ next_list, unsigned *__restrict__ next_count,
@@ -526,106 +573,114 @@ __global__ void __launch_bounds__(128) k_topo(Grid g, Density rho, CellOut out, 
         // ---- neighbours (FP32): list of up to K, bound D2 on everything else
         KnnList<K> L;
         L.cnt = 0;
-        double D2;
+        float D2;
         if (scan_all || g.n - 1 <= K) {
             all_query<K>(g, zi, zif, p, L, &st->flags);
-            D2 = (L.cnt == g.n - 1) ? INFINITY : lower_d2(L.d[K - 1]);
+            D2 = (L.cnt == g.n - 1) ? INFINITY : lower32(L.d[K - 1]);
         } else {
             // caps are chord balls |x - z_i| <= r; sin(theta) = r sqrt(1 - r^2/4)
-            const double rmax = 0.28291;  // sin(theta) <= 0.28 keeps caps off the far faces
-            double r;
-            float hint = out.radius ? out.radius[i] : 0.0f;
+            const float rmax = 0.2829f;  // sin(theta) <= 0.28 keeps caps off the far faces
+            float r;
+            const float hint = out.radius ? out.radius[i] : 0.0f;
             if (hint > 0.0f && !last_pass) {
-                r = 1.1 * (double)hint;
+                r = 1.1f * hint;
             } else {
                 // local density from the own bin: lambda = count / solid angle
                 int b = bin_index(zi.x, zi.y, zi.z, g.G);
                 int cbn = g.bstart[b + 1] - g.bstart[b];
-                double ax = fabs(zi.x), ay = fabs(zi.y), az = fabs(zi.z);
-                double am = fmax(ax, fmax(ay, az));
-                double s2 = (ax * ax + ay * ay + az * az) / (am * am);  // 1 + s^2 + t^2
-                double omega = (4.0 / ((double)g.G * g.G)) / (s2 * sqrt(s2));
-                double lam = fmax((double)cbn, 1.0) / omega;
-                r = sqrt(1.5 * K / (3.141592653589793 * lam));
-                if (last_pass) r *= 2.0;
+                float ax = fabsf(zif.x), ay = fabsf(zif.y), az = fabsf(zif.z);
+                float am = fmaxf(ax, fmaxf(ay, az));
+                float s2 = (ax * ax + ay * ay + az * az) / (am * am);  // 1 + s^2 + t^2
+                float omega = (4.0f / ((float)g.G * g.G)) / (s2 * sqrtf(s2));
+                float lam = fmaxf((float)cbn, 1.0f) / omega;
+                r = sqrtf(1.5f * K / (3.14159265f * lam));
+                if (last_pass) r *= 2.0f;
             }
-            r = fmin(r, rmax);
-            double r2 = 0.0;
-            float r2acc = 0.0f;
+            r = fminf(r, rmax);
+            float r2lo = 0.0f, r2acc = 0.0f;
             for (int attempt = 0;; ++attempt) {
-                r2 = r * r;
-                const double S = r * sqrt(1.0 - 0.25 * r2) * (1.0 + 1e-9);
-                r2acc = (float)(r2 * 1.001) + 1e-12f;
+                const float rs = r * (1.0f + 1e-5f) + 1e-7f;  // covers the FP32 centre
+                const float S = rs * sqrtf(1.0f - 0.25f * rs * rs) * (1.0f + 1e-5f);
+                r2lo = r * r * (1.0f - 1e-6f);
+                r2acc = r * r * 1.001f + 1e-12f;
                 L.cnt = 0;
                 cap_query<K>(g, zi, zif, p, S, r2acc, L, &st->flags);
                 if (L.cnt == K || r >= rmax || attempt > 8) break;
-                double grow = (L.cnt > 0) ? sqrt(1.3 * K / (double)L.cnt) : 2.0;
-                r = fmin(r * fmax(grow, 1.25), rmax);
+                float grow = (L.cnt > 0) ? sqrtf(1.3f * K / (float)L.cnt) : 2.0f;
+                r = fminf(r * fmaxf(grow, 1.25f), rmax);
             }
-            // unkept: inside the list's range -> >= lower(d_K); outside the cap -> > r
-            D2 = (L.cnt == K) ? fmin(lower_d2(L.d[K - 1]), r2) : fmin(lower_d2(r2acc), r2);
+            // unkept: in the list's range -> >= lower(d_K); beyond r2acc -> >= lower(r2acc);
+            // never scanned -> farther than r
+            D2 = (L.cnt == K) ? fminf(lower32(L.d[K - 1]), r2lo) : fminf(lower32(r2acc), r2lo);
         }
         if (out.radius) out.radius[i] = sqrtf(L.cnt ? L.d[L.cnt - 1] : 0.0f);
 
         // ---- gnomonic frame at z_i: e1 x e2 = z_i
-        V3 ax;
+        Frame F;
+        F.zi = zi;
+        F.zs = g.zs;
         {
             double fx = fabs(zi.x), fy = fabs(zi.y), fz = fabs(zi.z);
-            ax = (fx <= fy && fx <= fz) ? mk(1, 0, 0) : ((fy <= fz) ? mk(0, 1, 0) : mk(0, 0, 1));
+            V3 ax = (fx <= fy && fx <= fz) ? mk(1, 0, 0) : ((fy <= fz) ? mk(0, 1, 0) : mk(0, 0, 1));
+            V3 c = crs(zi, ax);
+            F.e1 = scl(c, rsqrt(dot(c, c)));
+            F.e2 = crs(zi, F.e1);
+            F.e1f = make_float3((float)F.e1.x, (float)F.e1.y, (float)F.e1.z);
+            F.e2f = make_float3((float)F.e2.x, (float)F.e2.y, (float)F.e2.z);
         }
-        const V3 e1 = unit(crs(zi, ax));
-        const V3 e2 = crs(zi, e1);
 
         // ---- clip nearest first, with the security radius
-        Poly<K, VMAX> P;
+        Poly<K, VMAX, EXTRA> P;
+        P.kj = L.j;
         P.cur = 0;
         P.nv = 4;
         {
             // square lines: K right (u <= L), K+1 top (w <= L), K+2 left, K+3 bottom
-            const double la[4] = {1, 0, -1, 0}, lb[4] = {0, 1, 0, -1};
+            const float la[4] = {1, 0, -1, 0}, lb[4] = {0, 1, 0, -1};
             const float vu[4] = {(float)kBoxL, (float)kBoxL, -(float)kBoxL, -(float)kBoxL};
             const float vw[4] = {-(float)kBoxL, (float)kBoxL, (float)kBoxL, -(float)kBoxL};
             for (int k = 0; k < 4; ++k) {
-                P.set_line(K + k, la[k], lb[k], kBoxL);
+                P.la[K + k] = la[k];
+                P.lb[K + k] = lb[k];
+                P.lc[K + k] = (float)kBoxL;
                 P.ln[0][k] = (unsigned char)(K + k);
                 P.uf[0][k] = vu[k];
                 P.wf[0][k] = vw[k];
                 P.ill[0][k] = 0;
             }
         }
-        double R2 = chord2_of_r2(2.0 * kBoxL * kBoxL);
+        float R2 = chord2_up(2.0f * (float)kBoxL * (float)kBoxL);
         bool ok = true, early = false;
         for (int k = 0; k < L.cnt; ++k) {
-            const double bound = fmin(lower_d2(L.d[k]), D2);
-            if (bound > 4.0 * R2 * kCertMargin) { early = true; break; }
-            const V3 d = sub(ld(g.zs + L.j[k]), zi);
-            P.set_line(k, dot(e1, d), dot(e2, d), -dot(zi, d));
-            int rc = clip<K, VMAX>(P, k, &st->flags, &st->ambiguous);
+            const float bound = fminf(lower32(L.d[k]), D2);
+            if (bound > 4.0f * R2 * (1.0f + 1e-6f)) { early = true; break; }
+            P.set_line(F, k, L.j[k]);
+            int rc = clip<K, VMAX, EXTRA>(P, F, k, &st->flags, &st->ambiguous);
             if (rc < 0) { ok = false; break; }
-            if (rc > 0) R2 = poly_R2(P);
+            if (rc > 0) R2 = poly_R2(P, F);
         }
         bool boxed = false;
         for (int v = 0; v < P.nv; ++v) boxed |= (P.ln[P.cur][v] >= K);  // no extra slots yet
-        bool certified = ok && !boxed && (early || D2 > 4.0 * R2 * kCertMargin);
-        if (ok && !certified && last_pass) {
+        bool certified = ok && !boxed && (early || D2 > 4.0f * R2 * (1.0f + 1e-6f));
+        if (EXTRA > 0 && ok && !certified && last_pass) {
             // last resort: clip by every generator (the exact cell); points
             // that cannot reach the polygon are skipped.  A new line goes to
             // an extra slot that no current edge uses.
             for (int q = 0; q < g.n && ok; ++q) {
                 if (q == p) continue;
                 const V3 d = sub(ld(g.zs + q), zi);
-                if (dot(d, d) > 4.0 * R2 * kCertMargin) continue;
+                if (dot(d, d) > 4.0 * (double)R2 * (1.0 + 1e-6)) continue;
                 unsigned long long used = 0ull;
                 for (int v = 0; v < P.nv; ++v)
                     if (P.ln[P.cur][v] >= K + 4) used |= 1ull << (P.ln[P.cur][v] - (K + 4));
                 int x = __ffsll((long long)~used) - 1;
-                if (x < 0 || x >= VMAX) { ok = false; break; }
+                if (x < 0 || x >= EXTRA) { ok = false; break; }
                 const int l = K + 4 + x;
-                P.set_line(l, dot(e1, d), dot(e2, d), -dot(zi, d));
                 P.jx[x] = q;
-                int rc = clip<K, VMAX>(P, l, &st->flags, &st->ambiguous);
+                P.set_line(F, l, q);
+                int rc = clip<K, VMAX, EXTRA>(P, F, l, &st->flags, &st->ambiguous);
                 if (rc < 0) { ok = false; break; }
-                if (rc > 0) R2 = poly_R2(P);
+                if (rc > 0) R2 = poly_R2(P, F);
             }
             boxed = false;
             for (int v = 0; v < P.nv; ++v) boxed |= (P.ln[P.cur][v] >= K && P.ln[P.cur][v] < K + 4);
@@ -645,54 +700,441 @@ __global__ void __launch_bounds__(128) k_topo(Grid g, Density rho, CellOut out, 
 
         // ---- canonical edge order: start at the lexicographically smallest neighbour
         const int c = P.cur, nv = P.nv;
-        auto nbj = [&](int k) -> int {
-            int l = P.ln[c][k];
-            return (l < K) ? L.j[l] : P.jx[l - (K + 4)];
-        };
         int k0 = 0;
-        V3 best = ld(g.zs + nbj(0));
+        V3 best = ld(g.zs + P.gen_of(P.ln[c][0]));
         for (int k = 1; k < nv; ++k) {
-            V3 zn = ld(g.zs + nbj(k));
+            V3 zn = ld(g.zs + P.gen_of(P.ln[c][k]));
             if (lex_less(zn, best)) { best = zn; k0 = k; }
         }
-        auto corner = [&](int k) -> V3 {  // FP64 corner k from its two lines
-            double u, w;
-            P.meet64(P.ln[c][(k == 0) ? nv - 1 : k - 1], P.ln[c][k], u, w);
-            return unit(add(zi, add(scl(e1, u), scl(e2, w))));
-        };
         if (out.deg) {
             out.deg[i] = nv;
             if (nv <= out.max_deg)
                 for (int t2 = 0; t2 < nv; ++t2)
-                    out.nbr[(size_t)i * out.max_deg + t2] = g.sidx[nbj((k0 + t2 < nv) ? k0 + t2 : k0 + t2 - nv)];
+                    out.nbr[(size_t)i * out.max_deg + t2] =
+                        g.sidx[P.gen_of(P.ln[c][(k0 + t2 < nv) ? k0 + t2 : k0 + t2 - nv])];
         }
+        // FP64 corners in canonical order; each edge's FP64 line is computed once
+        double pa, pb, pc;
+        P.line64(F, P.ln[c][(k0 == 0) ? nv - 1 : k0 - 1], pa, pb, pc);
         if (nv <= kCellSlots) {
+            // corners are computed from these lines by k_corners
             cb.deg[p] = nv;
-            for (int t2 = 0; t2 < nv; ++t2) {
-                const int k = (k0 + t2 < nv) ? k0 + t2 : k0 + t2 - nv;
-                V3 v = corner(k);
-                cb.vx[(size_t)p * kCellSlots + t2] = P4{v.x, v.y, v.z, 0.0};
-                cb.nb[(size_t)p * kCellSlots + t2] = nbj(k);
-            }
+            for (int t2 = 0; t2 < nv; ++t2)
+                cb.nb[(size_t)p * kCellSlots + t2] = P.gen_of(P.ln[c][(k0 + t2 < nv) ? k0 + t2 : k0 + t2 - nv]);
         } else {
             // large cell: integrate here, edges in the canonical order
             cb.deg[p] = 0;
             const double inv_alpha = 1.0 / rho.alpha;
             Acc acc = {0, 0, 0, 0, 0};
-            V3 vfirst = corner(k0);
-            V3 va = vfirst;
-            for (int t2 = 0; t2 < nv; ++t2) {
-                const int k = (k0 + t2 < nv) ? k0 + t2 : k0 + t2 - nv;
-                const int k1 = (k + 1 == nv) ? 0 : k + 1;
-                V3 vb = (t2 + 1 == nv) ? vfirst : corner(k1);
-                V3 mu = unit(add(zi, ld(g.zs + nbj(k))));
-                tri(rho, inv_alpha, zi, va, mu, acc);
-                tri(rho, inv_alpha, zi, mu, vb, acc);
+            V3 corners_first, va;
+            for (int t2 = 0; t2 <= nv; ++t2) {
+                const int k = (k0 + t2) % nv;
+                double a, b, cc, u, w;
+                P.line64(F, P.ln[c][k], a, b, cc);
+                P.meet(pa, pb, pc, a, b, cc, u, w);
+                pa = a; pb = b; pc = cc;
+                V3 x = add(zi, add(scl(F.e1, u), scl(F.e2, w)));
+                V3 vb = (t2 == nv) ? corners_first : scl(x, rsqrt(dot(x, x)));
+                if (t2 == 0) {
+                    corners_first = vb;
+                } else {
+                    const int kprev = (k0 + t2 - 1) % nv;
+                    V3 mu = unit(add(zi, ld(g.zs + P.gen_of(P.ln[c][kprev]))));
+                    tri(rho, inv_alpha, zi, va, mu, acc);
+                    tri(rho, inv_alpha, zi, mu, vb, acc);
+                }
                 va = vb;
             }
             write_cell(out, i, zi, acc, st);
         }
     }
+}
+
+// ------------------------------------------------- topology, warp per cell
+// The first pass gives each cell one warp, so that control flow is uniform:
+// lanes scan candidate generators together, the polygon keeps one vertex
+// per lane in registers, and a clip is a per-lane side test, a ballot and a
+// shuffle compaction.  Differences z_j - z_i come from the FP32 pairs
+// (hi, lo) of the coordinates: fl(hi_j - hi_i) is within 6e-8 of its value
+// and the lo parts (<= 3e-8 each) add the rest, so d is within ~2e-7 of |d|
+// and no FP64 arithmetic is needed except in rare per-lane fallbacks.  Cells
+// this pass cannot certify (or with more than 16 edges, or 32 vertices at
+// some point) go to the retry list of the thread-per-cell passes.
+constexpr int kWarpCand = 128;  // candidate buffer per warp (4 per lane)
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ float3 dfdiff(const Grid &g, int q, float4 hp, float4 lp) {
+    const float4 hq = g.zf[q], lq = g.zl[q];
+    return make_float3((hq.x - hp.x) + (lq.x - lp.x), (hq.y - hp.y) + (lq.y - lp.y), (hq.z - hp.z) + (lq.z - lp.z));
+}
+
+__device__ __forceinline__ void frame64(V3 zi, V3 &e1, V3 &e2) {
+    double fx = fabs(zi.x), fy = fabs(zi.y), fz = fabs(zi.z);
+    V3 ax = (fx <= fy && fx <= fz) ? mk(1, 0, 0) : ((fy <= fz) ? mk(0, 1, 0) : mk(0, 0, 1));
+    V3 c = crs(zi, ax);
+    e1 = scl(c, rsqrt(dot(c, c)));
+    e2 = crs(zi, e1);
+}
+
+// FP64 line of generator `gen` (< 0: the starting square) in the frame at z_i
+__device__ __forceinline__ void line_of(const Grid &g, V3 zi, V3 e1, V3 e2, int gen, double &a, double &b,
+                                        double &c) {
+    if (gen < 0) {
+        const int k = -1 - gen;  // right, top, left, bottom
+        a = (k == 0) ? 1.0 : ((k == 2) ? -1.0 : 0.0);
+        b = (k == 1) ? 1.0 : ((k == 3) ? -1.0 : 0.0);
+        c = kBoxL;
+        return;
+    }
+    const V3 d = sub(ld(g.zs + gen), zi);
+    a = dot(e1, d);
+    b = dot(e2, d);
+    c = -dot(zi, d);
+}
+
+// FP64 vertex of lines (gin, gout) at cell p
+__device__ __forceinline__ void vertex64(const Grid &g, int p, int gin, int gout, double &u, double &w) {
+    const V3 zi = ld(g.zs + p);
+    V3 e1, e2;
+    frame64(zi, e1, e2);
+    double a1, b1, c1, a2, b2, c2;
+    line_of(g, zi, e1, e2, gin, a1, b1, c1);
+    line_of(g, zi, e1, e2, gout, a2, b2, c2);
+    double inv = 1.0 / (a1 * b2 - a2 * b1);
+    u = (c1 * b2 - c2 * b1) * inv;
+    w = (a1 * c2 - a2 * c1) * inv;
+}
+
+// FP64 side test of vertex (gin, gout) against generator gnew: true = outside
+__device__ bool outside64(const Grid &g, int p, int gin, int gout, int gnew, unsigned long long *amb) {
+    const V3 zi = ld(g.zs + p);
+    V3 e1, e2;
+    frame64(zi, e1, e2);
+    double a1, b1, c1, a2, b2, c2, a, b, c;
+    line_of(g, zi, e1, e2, gin, a1, b1, c1);
+    line_of(g, zi, e1, e2, gout, a2, b2, c2);
+    line_of(g, zi, e1, e2, gnew, a, b, c);
+    double inv = 1.0 / (a1 * b2 - a2 * b1);
+    double u = (c1 * b2 - c2 * b1) * inv;
+    double w = (a1 * c2 - a2 * c1) * inv;
+    double sd = a * u + b * w - c;
+    if (fabs(sd) <= 1e-14 * (fabs(a * u) + fabs(b * w) + fabs(c))) atomicAdd(amb, 1ull);
+    return sd > 0.0;
+}
+
+__device__ __forceinline__ long long okey(double x) {
+    long long b = __double_as_longlong(x);
+    return b >= 0 ? b : (b ^ 0x7fffffffffffffffLL);
+}
+
+// append every q in [q0, q1), q != p, with d2 <= r2acc; cnt may exceed the buffer
+__device__ __forceinline__ int gather(const Grid &g, int p, float4 hp, float4 lp, int q0, int q1, float r2acc, int cnt,
+                                      float *cd, int *cj, int lane, unsigned *flags) {
+    for (int base = q0; base < q1; base += 32) {
+        const int q = base + lane;
+        bool pred = false;
+        float d2 = 0.0f;
+        if (q < q1 && q != p) {
+            const float3 d = dfdiff(g, q, hp, lp);
+            d2 = fmaf(d.x, d.x, fmaf(d.y, d.y, d.z * d.z));
+            if (d2 == 0.0f) check_duplicate(g, ld(g.zs + p), q, flags);
+            pred = d2 <= r2acc;
+        }
+        const unsigned m = __ballot_sync(kFull, pred);
+        const int pos = cnt + __popc(m & ((1u << lane) - 1u));
+        if (pred && pos < kWarpCand) {
+            cd[pos] = d2;
+            cj[pos] = q;
+        }
+        cnt += __popc(m);
+    }
+    return cnt;
+}
+
+__global__ void __launch_bounds__(128) k_topo_warp(Grid g, CellOut out, CellBuf cb, int *__restrict__ next_list,
+                                                   unsigned *__restrict__ next_count, DevStatus *st) {
+    __shared__ float s_d2[4][kWarpCand];
+    __shared__ int s_j[4][kWarpCand];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    float *cd = s_d2[wib];
+    int *cj = s_j[wib];
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    const float INF = __int_as_float(0x7f800000);
+    for (int p = gw; p < g.n; p += nw) {
+        const float4 hp = g.zf[p], lp = g.zl[p];
+        const int i = g.sidx[p];
+        // FP32 frame (any orthonormal frame gives the same vertex directions)
+        float3 e1, e2;
+        {
+            const float fx = fabsf(hp.x), fy = fabsf(hp.y), fz = fabsf(hp.z);
+            float3 ax = (fx <= fy && fx <= fz) ? make_float3(1, 0, 0)
+                                               : ((fy <= fz) ? make_float3(0, 1, 0) : make_float3(0, 0, 1));
+            float3 c = make_float3(hp.y * ax.z - hp.z * ax.y, hp.z * ax.x - hp.x * ax.z, hp.x * ax.y - hp.y * ax.x);
+            const float inv = rsqrtf(c.x * c.x + c.y * c.y + c.z * c.z);
+            e1 = make_float3(c.x * inv, c.y * inv, c.z * inv);
+            e2 = make_float3(hp.y * e1.z - hp.z * e1.y, hp.z * e1.x - hp.x * e1.z, hp.x * e1.y - hp.y * e1.x);
+        }
+        const bool all_mode = g.n - 1 <= kWarpCand;
+        const float rmax = 0.2829f;  // sin(theta) <= 0.28 keeps caps off the far faces
+        float r;
+        {
+            const float hint = out.radius ? out.radius[i] : 0.0f;
+            if (hint > 0.0f) {
+                r = hint;
+            } else {
+                const int b = bin_index((double)hp.x, (double)hp.y, (double)hp.z, g.G);
+                const int cbn = g.bstart[b + 1] - g.bstart[b];
+                const float ax = fabsf(hp.x), ay = fabsf(hp.y), az = fabsf(hp.z);
+                const float am = fmaxf(ax, fmaxf(ay, az));
+                const float s2 = (ax * ax + ay * ay + az * az) / (am * am);
+                const float omega = (4.0f / ((float)g.G * g.G)) / (s2 * sqrtf(s2));
+                r = sqrtf(24.0f * omega / (3.14159265f * fmaxf((float)cbn, 1.0f)));
+            }
+            r = fminf(r, rmax);
+        }
+        bool certified = false, ok = true;
+        int nv = 0;
+        float R2 = 0.0f;
+        // polygon: lane k < nv holds vertex k and its outgoing edge's line
+        float vu = 0.0f, vw = 0.0f, la_o = 0.0f, lb_o = 0.0f, lc_o = 0.0f;
+        int vill = 0, g_o = 0;
+        for (int attempt = 0; attempt < 4 && ok && !certified; ++attempt) {
+            // ---- candidates within chord r (every one of them; the rest are farther than r)
+            const float rs = r * (1.0f + 1e-5f) + 1e-7f;  // covers the FP32 centre
+            const float S = rs * sqrtf(1.0f - 0.25f * rs * rs) * (1.0f + 1e-5f);
+            const float r2acc = all_mode ? INF : r * r * 1.001f;
+            const float D2 = all_mode ? INF : r * r * (1.0f - 1e-6f);
+            int cnt = 0;
+            if (all_mode) {
+                cnt = gather(g, p, hp, lp, 0, g.n, r2acc, cnt, cd, cj, lane, &st->flags);
+            } else {
+                const float S2 = S * S;
+                const float qv[3] = {hp.x, hp.y, hp.z};
+                for (int a = 0; a < 3; ++a) {
+                    const float qa = qv[a];
+                    const float A = qa * qa - S2;
+                    if (A <= 0.0f) continue;
+                    const float sg = qa > 0.0f ? 1.0f : -1.0f;
+                    const int face = 2 * a + (qa < 0.0f ? 1 : 0);
+                    const float invA = 1.0f / A;
+                    const float margin = 4e-6f * invA + 1e-6f;
+                    int lo[2], hi[2];
+                    bool empty = false;
+                    for (int rr = 0; rr < 2; ++rr) {
+                        const float qb = qv[(a + 1 + rr) % 3];
+                        const float rt = S * sqrtf(fmaxf(qa * qa + qb * qb - S2, 0.0f));
+                        float s0 = (sg * qa * qb - rt) * invA - margin;
+                        float s1 = (sg * qa * qb + rt) * invA + margin;
+                        if (s0 > 1.0f || s1 < -1.0f) { empty = true; break; }
+                        s0 = fmaxf(s0, -1.0f);
+                        s1 = fminf(s1, 1.0f);
+                        lo[rr] = min(max((int)floorf((s0 + 1.0f) * 0.5f * g.G), 0), g.G - 1);
+                        hi[rr] = min(max((int)floorf((s1 + 1.0f) * 0.5f * g.G), 0), g.G - 1);
+                    }
+                    if (empty) continue;
+                    for (int iv = lo[1]; iv <= hi[1]; ++iv) {
+                        const int row = (face * g.G + iv) * g.G;
+                        cnt = gather(g, p, hp, lp, g.bstart[row + lo[0]], g.bstart[row + hi[0] + 1], r2acc, cnt, cd,
+                                     cj, lane, &st->flags);
+                    }
+                }
+            }
+            __syncwarp();
+            if (cnt > kWarpCand) {  // too many: a smaller cap (the bound stays r-based)
+                r *= 0.7f;
+                continue;
+            }
+            if (cnt < 3 && !all_mode && r < rmax) {
+                r = fminf(r * 2.0f, rmax);
+                continue;
+            }
+            float md[4];
+            int mj[4];
+#pragma unroll
+            for (int sl = 0; sl < 4; ++sl) {
+                const int idx = sl * 32 + lane;
+                md[sl] = (idx < cnt) ? cd[idx] : INF;
+                mj[sl] = (idx < cnt) ? cj[idx] : 0x7fffffff;
+            }
+            __syncwarp();
+            // ---- the starting square
+            nv = 4;
+            {
+                const float L = (float)kBoxL;
+                vu = (lane == 0 || lane == 1) ? L : -L;
+                vw = (lane == 1 || lane == 2) ? L : -L;
+                la_o = (lane == 0) ? 1.0f : ((lane == 2) ? -1.0f : 0.0f);
+                lb_o = (lane == 1) ? 1.0f : ((lane == 3) ? -1.0f : 0.0f);
+                lc_o = L;
+                g_o = -1 - lane;
+                vill = 0;
+            }
+            R2 = chord2_up(2.0f * (float)kBoxL * (float)kBoxL);
+            bool early = false;
+            for (;;) {
+                // nearest remaining candidate
+                float bd = md[0];
+                int bj = mj[0];
+#pragma unroll
+                for (int sl = 1; sl < 4; ++sl)
+                    if (md[sl] < bd || (md[sl] == bd && mj[sl] < bj)) { bd = md[sl]; bj = mj[sl]; }
+                float wd = bd;
+                int wj = bj;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const float od = __shfl_xor_sync(kFull, wd, o);
+                    const int oj = __shfl_xor_sync(kFull, wj, o);
+                    if (od < wd || (od == wd && oj < wj)) { wd = od; wj = oj; }
+                }
+                if (wd == INF) break;
+#pragma unroll
+                for (int sl = 0; sl < 4; ++sl)
+                    if (md[sl] == wd && mj[sl] == wj) md[sl] = INF;
+                // security radius: everything left is at least this far
+                const float bound = fminf(wd * (1.0f - 2e-6f), D2);
+                if (bound > 4.0f * R2 * (1.0f + 1e-6f)) { early = true; break; }
+                // the bisector of (z_i, z_wj) as a line a u + b w <= c
+                const float3 d = dfdiff(g, wj, hp, lp);
+                const float la = e1.x * d.x + e1.y * d.y + e1.z * d.z;
+                const float lb = e2.x * d.x + e2.y * d.y + e2.z * d.z;
+                const float lc = 0.5f * fmaf(d.x, d.x, fmaf(d.y, d.y, d.z * d.z));
+                const float lab = fabsf(la) + fabsf(lb);
+                const int prevl = (lane == 0) ? nv - 1 : lane - 1;
+                const int gin = __shfl_sync(kFull, g_o, prevl);
+                bool outside = false;
+                if (lane < nv) {
+                    const float sd = fmaf(la, vu, fmaf(lb, vw, -lc));
+                    const float mag = lab * (fabsf(vu) + fabsf(vw)) + fabsf(lc);
+                    if (!vill && fabsf(sd) > 2e-4f * mag) outside = sd > 0.0f;
+                    else outside = outside64(g, p, gin, g_o, wj, &st->ambiguous);
+                }
+                const unsigned m = __ballot_sync(kFull, outside);
+                if (m == 0u) continue;
+                const unsigned full = (nv == 32) ? kFull : ((1u << nv) - 1u);
+                if (m == full) {
+                    if (lane == 0) atomicOr(&st->flags, FLAG_EMPTY);
+                    ok = false;
+                    break;
+                }
+                const unsigned rot = ((m << 1) | (m >> (nv - 1))) & full;  // bit k = bit k-1 of m
+                const unsigned starts = m & ~rot;
+                if (__popc(starts) > 1 && lane == 0) atomicOr(&st->flags, FLAG_NONCONVEX);
+                const int k0 = __ffs(starts) - 1;
+                const unsigned mr = (k0 == 0) ? m : (((m >> k0) | (m << (nv - k0))) & full);
+                const int runlen = __ffs(~mr) - 1;
+                const int k1 = (k0 + runlen - 1) % nv;
+                const int kin = (k0 + nv - 1) % nv;
+                const int nnew = nv - runlen + 2;
+                if (nnew > 32) { ok = false; break; }
+                const float ai = __shfl_sync(kFull, la_o, kin), bi = __shfl_sync(kFull, lb_o, kin),
+                            ci = __shfl_sync(kFull, lc_o, kin);
+                // new vertices P = (edge kin) x (new line), Q = (new line) x (edge k1)
+                const int src = (lane >= 2) ? (k1 + lane - 1) % nv : k1;
+                const float su = __shfl_sync(kFull, vu, src), sw = __shfl_sync(kFull, vw, src);
+                const int sill = __shfl_sync(kFull, vill, src), sg = __shfl_sync(kFull, g_o, src);
+                const float sa = __shfl_sync(kFull, la_o, src), sb = __shfl_sync(kFull, lb_o, src),
+                            sc = __shfl_sync(kFull, lc_o, src);
+                if (lane == 0) {
+                    const float p1 = ai * lb, p2 = la * bi, det = p1 - p2;
+                    vu = (ci * lb - lc * bi) / det;
+                    vw = (ai * lc - la * ci) / det;
+                    vill = !(fabsf(det) * 30.0f >= fabsf(p1) + fabsf(p2));
+                    la_o = la; lb_o = lb; lc_o = lc; g_o = wj;
+                } else if (lane == 1) {
+                    const float p1 = la * sb, p2 = sa * lb, det = p1 - p2;
+                    vu = (lc * sb - sc * lb) / det;
+                    vw = (la * sc - sa * lc) / det;
+                    vill = !(fabsf(det) * 30.0f >= fabsf(p1) + fabsf(p2));
+                    la_o = sa; lb_o = sb; lc_o = sc; g_o = sg;
+                } else {
+                    vu = su; vw = sw; vill = sill; la_o = sa; lb_o = sb; lc_o = sc; g_o = sg;
+                }
+                nv = nnew;
+                // R2: an upper bound of the largest squared vertex chord
+                const int pl = (lane == 0) ? nv - 1 : lane - 1;
+                const int gin2 = __shfl_sync(kFull, g_o, pl);
+                float r2v = 0.0f;
+                if (lane < nv) {
+                    if (vill) {
+                        double u, w;
+                        vertex64(g, p, gin2, g_o, u, w);
+                        r2v = (float)(u * u + w * w);
+                    } else {
+                        r2v = vu * vu + vw * vw;
+                    }
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) r2v = fmaxf(r2v, __shfl_xor_sync(kFull, r2v, o));
+                R2 = chord2_up(r2v * 1.001f);
+            }
+            if (!ok) break;
+            const bool boxed = __ballot_sync(kFull, lane < nv && g_o < 0) != 0u;
+            certified = !boxed && (early || D2 > 4.0f * R2 * (1.0f + 1e-6f));
+            if (!certified) {
+                if (all_mode || r >= rmax) break;
+                r = fminf(fmaxf(2.2f * sqrtf(R2), 1.5f * r), rmax);
+            }
+        }
+        if (!certified || nv > kCellSlots) {
+            if (lane == 0) {
+                unsigned pos = atomicAdd(next_count, 1u);
+                next_list[pos] = p;
+                cb.deg[p] = 0;
+            }
+            continue;
+        }
+        // ---- canonical order: start at the lexicographically smallest neighbour
+        long long kx = 0x7fffffffffffffffLL, ky = kx, kz = kx;
+        if (lane < nv) {
+            const P4 zn = g.zs[g_o];
+            kx = okey(zn.x);
+            ky = okey(zn.y);
+            kz = okey(zn.z);
+        }
+        int best = lane;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const long long ox = __shfl_xor_sync(kFull, kx, o), oy = __shfl_xor_sync(kFull, ky, o),
+                            oz = __shfl_xor_sync(kFull, kz, o);
+            const int ob = __shfl_xor_sync(kFull, best, o);
+            const bool less = ox < kx || (ox == kx && (oy < ky || (oy == ky && (oz < kz || (oz == kz && ob < best)))));
+            if (less) { kx = ox; ky = oy; kz = oz; best = ob; }
+        }
+        const int rg = __shfl_sync(kFull, g_o, (best + lane) % nv);
+        if (lane < nv) {
+            cb.nb[(size_t)p * kCellSlots + lane] = rg;
+            if (out.deg && nv <= out.max_deg) out.nbr[(size_t)i * out.max_deg + lane] = g.sidx[rg];
+        }
+        if (lane == 0) {
+            cb.deg[p] = nv;
+            if (out.deg) out.deg[i] = nv;
+            if (out.radius) out.radius[i] = fminf(2.2f * sqrtf(R2), rmax);
+        }
+    }
+}
+
+// FP64 corner of every edge: vertex k of a cell is the intersection of the
+// bisector lines of edges k-1 and k, solved in the gnomonic frame at z_i
+__global__ void __launch_bounds__(256) k_corners(Grid g, CellBuf cb) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= cb.eoff[g.n]) return;
+    const int p = cb.ecell[e];
+    const int k = e - cb.eoff[p];
+    const int deg = cb.deg[p];
+    const int *nb = cb.nb + (size_t)p * kCellSlots;
+    const V3 zi = ld(g.zs + p);
+    V3 e1, e2;
+    frame64(zi, e1, e2);
+    double a1, b1, c1, a2, b2, c2;
+    line_of(g, zi, e1, e2, nb[(k == 0) ? deg - 1 : k - 1], a1, b1, c1);
+    line_of(g, zi, e1, e2, nb[k], a2, b2, c2);
+    const double inv = 1.0 / (a1 * b2 - a2 * b1);
+    const double u = (c1 * b2 - c2 * b1) * inv;
+    const double w = (a1 * c2 - a2 * c1) * inv;
+    const V3 x = add(zi, add(scl(e1, u), scl(e2, w)));
+    const V3 v = scl(x, rsqrt(dot(x, x)));
+    cb.vx[(size_t)p * kCellSlots + k] = P4{v.x, v.y, v.z, 0.0};
 }
 
 // -------------------------------------------------------------- quadrature
@@ -784,7 +1226,7 @@ __global__ void __launch_bounds__(256) k_quad(Grid g, Density rho, CellOut out, 
 }  // namespace
 
 void bin_points(const double *z, int n, int G, int *bin_of, int *count, int *start, int *cursor, int *scan_tmp,
-                P4 *zs, float4 *zf, int *sidx, DevStatus *st, cudaStream_t s, int64_t *launches) {
+                P4 *zs, float4 *zf, float4 *zl, int *sidx, DevStatus *st, cudaStream_t s, int64_t *launches) {
     const int nbins = 6 * G * G;
     cudaMemsetAsync(count, 0, sizeof(int) * nbins, s);
     int blocks = (n + 255) / 256;
@@ -792,8 +1234,8 @@ void bin_points(const double *z, int n, int G, int *bin_of, int *count, int *sta
     exclusive_scan(count, start, nbins, scan_tmp, s, launches);
     k_set_total<<<1, 1, 0, s>>>(start, nbins, n);
     cudaMemcpyAsync(cursor, start, sizeof(int) * nbins, cudaMemcpyDeviceToDevice, s);
-    k_bin_scatter<<<blocks, 256, 0, s>>>(z, n, bin_of, cursor, zs, zf, sidx);
-    k_bin_sort<<<(nbins + 255) / 256, 256, 0, s>>>(start, nbins, zs, zf, sidx);
+    k_bin_scatter<<<blocks, 256, 0, s>>>(z, n, bin_of, cursor, zs, zf, zl, sidx);
+    k_bin_sort<<<(nbins + 255) / 256, 256, 0, s>>>(start, nbins, zs, zf, zl, sidx);
     (*launches) += 4;
 }
 
@@ -805,29 +1247,29 @@ __global__ void k_set_total_from(int *arr, int n, const int *last_in) {
 void cell_passes(const Grid &g, const Density &rho, const CellOut &out, const CellBuf &cb, int *list1, int *list2,
                  DevStatus *st, int knn_k0, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1, int64_t *launches,
                  int64_t *cell_launches) {
-    const int blocks0 = (g.n + 127) / 128;
-    if (knn_k0 <= 16)
-        k_topo<16, 32><<<blocks0, 128, 0, s>>>(g, rho, out, cb, nullptr, nullptr, list1, &st->retry_count[0], 0, 0, st);
-    else
-        k_topo<32, 32><<<blocks0, 128, 0, s>>>(g, rho, out, cb, nullptr, nullptr, list1, &st->retry_count[0], 0, 0, st);
-    // retry passes: sized for the worst case, they read their work count on the device
+    (void)knn_k0;
+    // first pass: a warp per cell, grid sized to fill the GPU (grid-stride over cells)
+    const int wblocks = (int)std::min<long long>((g.n + 3) / 4, 152LL * 16);
+    k_topo_warp<<<wblocks, 128, 0, s>>>(g, out, cb, list1, &st->retry_count[0], st);
+    // retry passes (thread per cell): sized for the worst case, they read their work count on the device
     const int rblocks = 2 * 152;
-    k_topo<64, 64><<<rblocks, 64, 0, s>>>(g, rho, out, cb, list1, &st->retry_count[0], list2, &st->retry_count[1], 0,
-                                          0, st);
+    k_topo<64, 64, 0><<<rblocks, 64, 0, s>>>(g, rho, out, cb, list1, &st->retry_count[0], list2,
+                                             &st->retry_count[1], 0, 0, st);
     int scan_all = g.n <= 20000 ? 1 : 0;
-    k_topo<128, 64><<<rblocks, 64, 0, s>>>(g, rho, out, cb, list2, &st->retry_count[1], nullptr, &st->retry_count[2],
-                                           1, scan_all, st);
-    // edge list for the quadrature
+    k_topo<128, 64, 64><<<rblocks, 64, 0, s>>>(g, rho, out, cb, list2, &st->retry_count[1], nullptr,
+                                               &st->retry_count[2], 1, scan_all, st);
+    // edge list, FP64 corners, quadrature
     exclusive_scan(cb.deg, cb.eoff, g.n, cb.scan_tmp, s, launches);
     k_set_total_from<<<1, 1, 0, s>>>(cb.eoff, g.n, cb.deg);
     k_edge_cells<<<(g.n + 255) / 256, 256, 0, s>>>(g.n, cb.deg, cb.eoff, cb.ecell);
-    if (ev0) cudaEventRecord(ev0, s);
     // Euler: a full tessellation has 6N - 12 edge sides; failed cells only lower the count
     const long long max_edges = 6LL * g.n;
-    k_quad<<<(unsigned)((max_edges + 255) / 256), 256, 0, s>>>(g, rho, out, cb, cb.eoff, cb.ecell, cb.parts_val,
-                                                               cb.parts_cnt, st);
+    const unsigned eblocks = (unsigned)((max_edges + 255) / 256);
+    k_corners<<<eblocks, 256, 0, s>>>(g, cb);
+    if (ev0) cudaEventRecord(ev0, s);
+    k_quad<<<eblocks, 256, 0, s>>>(g, rho, out, cb, cb.eoff, cb.ecell, cb.parts_val, cb.parts_cnt, st);
     if (ev1) cudaEventRecord(ev1, s);
-    (*launches) += 6;
+    (*launches) += 7;
     (*cell_launches) += 4;
 }
 

@@ -43,7 +43,8 @@ struct Grid {
     int G;                  // bins per face edge
     int nbins;              // 6 G^2
     const P4 *zs;           // generators in bin order (w unused)
-    const float4 *zf;       // the same, rounded to FP32 (neighbour search)
+    const float4 *zf;       // the same, rounded to FP32 (hi part)
+    const float4 *zl;       // FP32 remainder z - hi (lo part): hi + lo carries ~48 bits
     const int *sidx;        // bin-order position -> original index
     const int *bstart;      // nbins + 1 offsets into zs
 };
@@ -84,7 +85,8 @@ struct CellBuf {
 
 // ---- binning (cells.cu) ----
 void bin_points(const double *z, int n, int G, int *bin_of, int *count, int *start, int *cursor,
-                int *scan_tmp, P4 *zs, float4 *zf, int *sidx, DevStatus *st, cudaStream_t s, int64_t *launches);
+                int *scan_tmp, P4 *zs, float4 *zf, float4 *zl, int *sidx, DevStatus *st, cudaStream_t s,
+                int64_t *launches);
 
 // ---- cell passes (cells.cu) ----
 // topology pass 0 over all cells, passes 1..2 over the retry lists, then the

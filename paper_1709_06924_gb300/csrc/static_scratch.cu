@@ -51,7 +51,8 @@ constexpr size_t oList2 = oList1 + up(sizeof(int) * kMaxN);
 constexpr size_t oCdeg = oList2 + up(sizeof(int) * kMaxN);
 constexpr size_t oZs = oCdeg + up(sizeof(int) * kMaxN);
 constexpr size_t oZf = oZs + up(sizeof(P4) * kMaxN);
-constexpr size_t oCvx = oZf + up(sizeof(float4) * kMaxN);
+constexpr size_t oZl = oZf + up(sizeof(float4) * kMaxN);
+constexpr size_t oCvx = oZl + up(sizeof(float4) * kMaxN);
 constexpr size_t oCnb = oCvx + up(sizeof(P4) * kMaxN * kCellSlots);
 constexpr size_t oFc = oCnb + up(sizeof(int) * kMaxN * kCellSlots);
 constexpr size_t oH = oFc + up(sizeof(double) * kMaxN);
@@ -61,7 +62,7 @@ constexpr size_t oEcell = oEoff + up(sizeof(int) * (kMaxN + 1));
 constexpr size_t oEscan = oEcell + up(sizeof(int) * 6 * kMaxN);
 constexpr size_t oPval = oEscan + up(sizeof(int) * (2 * (kMaxN / 2048 + 64) + 64));
 constexpr size_t oPcnt = oPval + up(sizeof(double) * 10 * kMaxN);
-constexpr size_t kBytes = oPcnt + up(sizeof(int) * kMaxN);  // about 13.2 MB
+constexpr size_t kBytes = oPcnt + up(sizeof(int) * kMaxN);  // about 13.5 MB
 
 __device__ __align__(256) unsigned char g_scratch[kBytes];
 
@@ -128,6 +129,7 @@ extern "C" scvt_status scvt_energy_grad_static(int64_t n, const scvt_density *rh
     int *list1 = (int *)(base + oList1), *list2 = (int *)(base + oList2), *cdeg = (int *)(base + oCdeg);
     P4 *zs = (P4 *)(base + oZs);
     float4 *zf = (float4 *)(base + oZf);
+    float4 *zl = (float4 *)(base + oZl);
     P4 *cvx = (P4 *)(base + oCvx);
     int *cnb = (int *)(base + oCnb);
     double *fc = (double *)(base + oFc), *hd = (double *)(base + oH);
@@ -138,13 +140,14 @@ extern "C" scvt_status scvt_energy_grad_static(int64_t n, const scvt_density *rh
         cudaGetLastError();
         return SCVT_ERR_CUDA;
     }
-    bin_points(z, N, G, bin_of, count, start, cursor, scan_tmp, zs, zf, sidx, st, s, &launches);
+    bin_points(z, N, G, bin_of, count, start, cursor, scan_tmp, zs, zf, zl, sidx, st, s, &launches);
     Grid grid;
     grid.n = N;
     grid.G = G;
     grid.nbins = 6 * G * G;
     grid.zs = zs;
     grid.zf = zf;
+    grid.zl = zl;
     grid.sidx = sidx;
     grid.bstart = start;
     CellOut out;
