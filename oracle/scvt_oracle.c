@@ -31,7 +31,9 @@
  *   - the 7-point degree-5 Radon rule on each sub-triangle, mapped to the
  *     sphere by radial projection of the planar points with weights scaled
  *     by the signed spherical area (Van Oosterom-Strackee formula);
- *   - tanh cap prefactor (1-gamma)/2, geodesic distance via atan2;
+ *   - tanh cap prefactor (1-gamma)/2, geodesic distance via atan2, and
+ *     (1-gamma)/2 (tanh(x)+1) evaluated as (1-gamma)/(1+exp(-2x)) (equal,
+ *     without the cancellation of tanh(x)+1 far outside the cap);
  *   - energy accumulated directly as rho |p - z_i|^2 (no 2m - 2 z.c identity);
  *   - line search: More-Thuente (1994) with c1 = 1e-4, c2 = 0.9, step bounds
  *     [1e-20, 1e20], derivative along the projected path
@@ -635,7 +637,10 @@ static double rho_eval(const orc_density *r, const double *p)
         double cr[3];
         cross3(p, r->xc, cr);
         double d = atan2(sqrt(dot3(cr, cr)), dot3(p, r->xc));
-        double v = 0.5 * (1.0 - r->gamma) * (tanh((r->beta - d) / r->alpha) + 1.0) + r->gamma;
+        /* (tanh(x) + 1)/2 written as 1/(1 + exp(-2x)): the same function
+         * without the cancellation of tanh(x) + 1 for x << 0 */
+        double x = (r->beta - d) / r->alpha;
+        double v = (1.0 - r->gamma) / (1.0 + exp(-2.0 * x)) + r->gamma;
         if (r->kind == 3) { v = v * v; v = v * v; }
         return v;
     }
