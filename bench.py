@@ -47,6 +47,8 @@ def parse():
     p.add_argument("--cpu-sample-iters", type=int, default=3)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
+                   help="fp64: everything in FP64; mixed: FP32 corners/quadrature, FP64 sums and LBFGS")
     return p.parse_args()
 
 
@@ -173,7 +175,8 @@ def run_ours(args, w):
 
     seed = args.seed + rank
     z_host = I.uniform_sphere(w.n, seed)
-    eng = Engine(w.n, w.density, lbfgs_m=w.lbfgs_m, device=local)
+    prec = 1 if args.precision == "mixed" else 0
+    eng = Engine(w.n, w.density, lbfgs_m=w.lbfgs_m, device=local, precision=prec)
     z = torch.from_numpy(z_host).cuda(local)
 
     def barrier():
@@ -234,7 +237,7 @@ def run_ours(args, w):
     # iteration and copies the result back
     e2e = None
     if not args.no_e2e:
-        eng2 = Engine(w.n, w.density, lbfgs_m=w.lbfgs_m, device=local)
+        eng2 = Engine(w.n, w.density, lbfgs_m=w.lbfgs_m, device=local, precision=prec)
         z2 = torch.from_numpy(z_host).cuda(local)
         eng2.lbfgs_solve(z2, max_iter=args.warmup, grad_tol=0.0)
         zp = torch.empty((w.n, 3), dtype=torch.float64, pin_memory=True)
@@ -293,6 +296,10 @@ def run_ours(args, w):
         torch.distributed.destroy_process_group()
 
 
+# FP64 exp per call in DFMA equivalents (measured like the other per-call costs)
+EXP_DFMA = 17.9
+
+
 def fp64_peak_tflops() -> float:
     return 152 * 2 * 2 * 2.07e9 / 1e12
 
@@ -306,13 +313,13 @@ def fp64_flops_per_generator(kind: int) -> float:
     the projected point (combination, norm, rsqrt, scale: 37 + rsqrt), the
     density, the weight and the accumulation of m, c and |p - z|^2 (24).  The
     tanh cap density costs a cross product, a norm and a dot (19), sqrt,
-    atan2, a subtract-multiply and tanh (+5); X3 costs 6.  A transcendental is
+    atan2, exp and a division (its logistic form) (+5); X3 costs 6.  A transcendental is
     charged what it costs on this GPU in FMA-pipe time (per-call costs
     measured with CUDA events, in DFMA equivalents x 2 flop).  The cell of a
     generator has 6 edges on average (Euler: 2E = 6N - 12).
     """
-    rsqrt, sqrt, atan2, tanh = 2 * 6.9, 2 * 9.6, 2 * 41.0, 2 * 15.8
-    dens = {0: 0.0, 1: 6.0, 2: 24.0 + sqrt + atan2 + tanh, 3: 28.0 + sqrt + atan2 + tanh}[kind]
+    rsqrt, sqrt, atan2, exp, div = 2 * 6.9, 2 * 9.6, 2 * 41.0, 2 * EXP_DFMA, 2 * 10.4
+    dens = {0: 0.0, 1: 6.0, 2: 24.0 + sqrt + atan2 + exp + div, 3: 28.0 + sqrt + atan2 + exp + div}[kind]
     point = 37.0 + rsqrt + 24.0 + dens
     subtri = 38.0 + atan2 + 7 * point
     mu = 11.0 + rsqrt

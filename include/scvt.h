@@ -50,7 +50,8 @@ typedef enum {
 } scvt_status;
 
 /* Point densities of Sec. 4.  TANH_CAP: rho = (1-gamma)/2 (tanh((beta - d)/alpha) + 1) + gamma with
- * d the geodesic distance to xc (radians); POLAR_X3: rho = (1-gamma) z^4 + gamma;
+ * d the geodesic distance to xc (radians), evaluated as (1-gamma)/(1 + exp(-2(beta - d)/alpha))
+ * + gamma (equal; no cancellation far from the cap); POLAR_X3: rho = (1-gamma) z^4 + gamma;
  * TANH_CAP_POW4: the TANH_CAP value raised to the 4th power. */
 typedef enum {
     SCVT_RHO_UNIFORM = 0,
@@ -71,7 +72,10 @@ typedef struct {
     int64_t n;          /* number of generators, >= 4 */
     scvt_density rho;
     int quad_points;    /* points per sub-triangle; 7 (Radon degree-5 rule) is the only value */
-    int precision;      /* 0 = FP64 throughout (parity mode); 1 = mixed (reserved) */
+    int precision;      /* 0 = FP64 throughout (parity mode).  1 = mixed: Voronoi corners and the
+                           quadrature in FP32 local coordinates (offsets from z_i), the
+                           near-degenerate clipping decisions, the sums over edges and cells
+                           and all LBFGS vectors in FP64; the topology is the FP64 mode's */
     int lbfgs_m;        /* number of (s, y) pairs kept, 0..32 (the paper uses 7) */
     int knn_k0;         /* first-pass neighbour count, 0 = default (32); 8..32 */
     int knn_kmax;       /* largest neighbour count of the retry passes, 0 = default (128) */

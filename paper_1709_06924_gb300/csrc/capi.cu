@@ -43,6 +43,7 @@ struct Bufs {
     P4 *cvx = nullptr;
     int *cdeg = nullptr, *cnb = nullptr, *eoff = nullptr, *ecell = nullptr, *escan = nullptr, *pcnt = nullptr;
     double *pval = nullptr;
+    float4 *vo = nullptr;
     int *bin_of = nullptr, *count = nullptr, *start = nullptr, *cursor = nullptr, *scan_tmp = nullptr;
     int *sidx = nullptr, *list1 = nullptr, *list2 = nullptr;
     int *deg = nullptr;
@@ -183,8 +184,9 @@ scvt_status evaluate_dev(scvt_handle *H, const double *zdev, double *grad, doubl
     cb.scan_tmp = B.escan;
     cb.parts_val = B.pval;
     cb.parts_cnt = B.pcnt;
+    cb.vo = B.vo;
     CK(cudaMemsetAsync(B.pcnt, 0, sizeof(int) * n, s), "reset split-cell counters");
-    cell_passes(g, to_density(H->cfg.rho), out, cb, B.list1, B.list2, B.st, H->cfg.knn_k0, s,
+    cell_passes(g, to_density(H->cfg.rho), out, cb, B.list1, B.list2, B.st, H->cfg.knn_k0, H->cfg.precision == 1, s,
                 H->profiling ? H->ev_cell0 : nullptr, H->profiling ? H->ev_cell1 : nullptr, L,
                 &H->stats.cell_launches);
     reduce_eval(n, fcell, grad, q, nrm, B.partials, B.st, s, L);
@@ -426,13 +428,13 @@ const char *scvt_status_string(scvt_status s) {
 
 const char *scvt_last_error(const scvt_handle *h) { return h ? h->err.c_str() : ""; }
 
-const char *scvt_version(void) { return "scvt-gb300 0.1 (sm_103a, FP64 parity mode)"; }
+const char *scvt_version(void) { return "scvt-gb300 0.2 (sm_103a; FP64 parity mode, FP32/FP64 mixed mode)"; }
 
 void scvt_destroy(scvt_handle *H) {
     if (!H) return;
     Bufs &b = H->b;
     void *ptrs[] = {b.z, b.zt, b.g, b.gt, b.h, b.ht, b.fc, b.q, b.yv, b.nrm, b.mass, b.moment, b.stage_a, b.stage_b,
-                    b.partials, b.scal, b.rho, b.hist, b.zs, b.zf, b.zl, b.cvx, b.cnb, b.cdeg, b.eoff, b.ecell, b.escan, b.pval, b.pcnt, b.bin_of, b.count, b.start, b.cursor, b.scan_tmp,
+                    b.partials, b.scal, b.rho, b.hist, b.zs, b.zf, b.zl, b.cvx, b.cnb, b.cdeg, b.eoff, b.ecell, b.escan, b.pval, b.pcnt, b.vo, b.bin_of, b.count, b.start, b.cursor, b.scan_tmp,
                     b.sidx, b.list1, b.list2, b.deg, b.radius, b.st};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -449,7 +451,7 @@ scvt_status scvt_create(const scvt_config *cfg, void *cuda_stream, scvt_handle *
     if (cfg->n < 4 || cfg->n > (int64_t)200000000) return SCVT_ERR_INVALID;
     if (cfg->lbfgs_m < 0 || cfg->lbfgs_m > kMaxM) return SCVT_ERR_INVALID;
     if (cfg->quad_points != 0 && cfg->quad_points != 7) return SCVT_ERR_INVALID;
-    if (cfg->precision != 0) return SCVT_ERR_UNIMPLEMENTED;
+    if (cfg->precision != 0 && cfg->precision != 1) return SCVT_ERR_INVALID;
     if (cfg->rho.kind < 0 || cfg->rho.kind > 3) return SCVT_ERR_INVALID;
     if (cfg->rho.kind != SCVT_RHO_UNIFORM) {
         if (!(cfg->rho.gamma > 0.0) || !(cfg->rho.gamma <= 1.0)) return SCVT_ERR_INVALID;
@@ -487,6 +489,7 @@ scvt_status scvt_create(const scvt_config *cfg, void *cuda_stream, scvt_handle *
     AL(b.zs, n); AL(b.zf, n); AL(b.zl, n); AL(b.cvx, (size_t)n * kCellSlots); AL(b.cnb, (size_t)n * kCellSlots);
     AL(b.cdeg, n); AL(b.eoff, n + 1); AL(b.ecell, 6 * (size_t)n); AL(b.escan, 2 * (n / 2048 + 64) + 64);
     AL(b.pval, 10 * (size_t)n); AL(b.pcnt, n);
+    if (cfg->precision == 1) AL(b.vo, (size_t)n * kCellSlots);
     AL(b.bin_of, n); AL(b.count, nbins); AL(b.start, nbins + 1); AL(b.cursor, nbins);
     AL(b.scan_tmp, 2 * (nbins / 2048 + 64) + 64);
     AL(b.sidx, n); AL(b.list1, n); AL(b.list2, n); AL(b.deg, n); AL(b.radius, n);

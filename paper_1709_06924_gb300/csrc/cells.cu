@@ -50,6 +50,20 @@ __constant__ double kQw[7] = {0.225,
                               0.1259391805448271526, 0.1259391805448271526, 0.1259391805448271526,
                               0.13239415278850618074, 0.13239415278850618074, 0.13239415278850618074};
 
+// the same rule in FP32 for the mixed-precision quadrature
+__constant__ float kQbf[7][2] = {
+    {1.0f / 3.0f, 1.0f / 3.0f},
+    {0.1012865073234563388f, 0.1012865073234563388f},
+    {0.7974269853530873224f, 0.1012865073234563388f},
+    {0.1012865073234563388f, 0.7974269853530873224f},
+    {0.47014206410511508977f, 0.47014206410511508977f},
+    {0.059715871789769820459f, 0.47014206410511508977f},
+    {0.47014206410511508977f, 0.059715871789769820459f},
+};
+__constant__ float kQwf[7] = {0.225f,
+                              0.1259391805448271526f, 0.1259391805448271526f, 0.1259391805448271526f,
+                              0.13239415278850618074f, 0.13239415278850618074f, 0.13239415278850618074f};
+
 struct V3 {
     double x, y, z;
 };
@@ -516,7 +530,9 @@ __device__ __forceinline__ void tri(const Density &r, double inv_alpha, V3 A, V3
         } else {
             V3 cx = crs(p, xc);
             double d = atan2(sqrt(dot(cx, cx)), dot(p, xc));
-            rv = 0.5 * (1.0 - r.gamma) * (tanh((r.beta - d) * inv_alpha) + 1.0) + r.gamma;
+            // (1 - gamma)/2 (tanh(x) + 1) + gamma, as (1 - gamma)/(1 + exp(-2x)) + gamma:
+            // the same function without the cancellation of tanh(x) + 1 for x << 0
+            rv = (1.0 - r.gamma) / (1.0 + exp(-2.0 * (r.beta - d) * inv_alpha)) + r.gamma;
             if (r.kind == 3) { rv = rv * rv; rv = rv * rv; }
         }
         double wr = kQw[k] * area * rv;
@@ -1223,6 +1239,223 @@ __global__ void __launch_bounds__(256) k_quad(Grid g, Density rho, CellOut out, 
     }
 }
 
+// ------------------------------------------------ mixed precision (FP32)
+// Corners, edge midpoints and rule points are handled as offsets from z_i in
+// FP32: every quantity is formed without cancellation at the cell scale h,
+// so FP32 keeps ~1e-7 of h.  Per edge the 14 rule points are summed in FP32;
+// edges and cells are summed in FP64, and c_i = m_i z_i + sum w rho (p - z_i)
+// so that the gradient g_i = -2 (o - (o.z_i) z_i), o = sum w rho (p - z_i),
+// never subtracts m_i z_i from itself.
+
+// FP32 lines of generators gin, gout in the FP32 frame at z_p, their
+// intersection (u, w), and whether it is ill conditioned
+__device__ __forceinline__ bool vertex32(const Grid &g, int p, float4 hp, float4 lp, float3 e1, float3 e2, int gin,
+                                         int gout, float &u, float &w) {
+    const float3 d1 = dfdiff(g, gin, hp, lp), d2 = dfdiff(g, gout, hp, lp);
+    const float a1 = e1.x * d1.x + e1.y * d1.y + e1.z * d1.z, b1 = e2.x * d1.x + e2.y * d1.y + e2.z * d1.z;
+    const float c1 = 0.5f * fmaf(d1.x, d1.x, fmaf(d1.y, d1.y, d1.z * d1.z));
+    const float a2 = e1.x * d2.x + e1.y * d2.y + e1.z * d2.z, b2 = e2.x * d2.x + e2.y * d2.y + e2.z * d2.z;
+    const float c2 = 0.5f * fmaf(d2.x, d2.x, fmaf(d2.y, d2.y, d2.z * d2.z));
+    const float p1 = a1 * b2, p2 = a2 * b1, det = p1 - p2;
+    u = (c1 * b2 - c2 * b1) / det;
+    w = (a1 * c2 - a2 * c1) / det;
+    return !(fabsf(det) * 30.0f >= fabsf(p1) + fabsf(p2));
+}
+
+__device__ __forceinline__ void frame32(float4 hp, float3 &e1, float3 &e2) {
+    const float fx = fabsf(hp.x), fy = fabsf(hp.y), fz = fabsf(hp.z);
+    float3 ax = (fx <= fy && fx <= fz) ? make_float3(1, 0, 0)
+                                       : ((fy <= fz) ? make_float3(0, 1, 0) : make_float3(0, 0, 1));
+    float3 c = make_float3(hp.y * ax.z - hp.z * ax.y, hp.z * ax.x - hp.x * ax.z, hp.x * ax.y - hp.y * ax.x);
+    const float inv = rsqrtf(c.x * c.x + c.y * c.y + c.z * c.z);
+    e1 = make_float3(c.x * inv, c.y * inv, c.z * inv);
+    e2 = make_float3(hp.y * e1.z - hp.z * e1.y, hp.z * e1.x - hp.x * e1.z, hp.x * e1.y - hp.y * e1.x);
+}
+
+// offset of normalize(z + u e1 + w e2) from z: (u e1 + w e2)/q - z r^2/(q (1+q)), q = sqrt(1 + r^2)
+__device__ __forceinline__ float3 gnomonic_offset(float4 z, float3 e1, float3 e2, float u, float w) {
+    const float r2 = u * u + w * w;
+    const float q = sqrtf(1.0f + r2);
+    const float iq = 1.0f / q, t = r2 / (q * (1.0f + q));
+    return make_float3((u * e1.x + w * e2.x) * iq - z.x * t, (u * e1.y + w * e2.y) * iq - z.y * t,
+                       (u * e1.z + w * e2.z) * iq - z.z * t);
+}
+
+__global__ void __launch_bounds__(256) k_corners32(Grid g, CellBuf cb) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= cb.eoff[g.n]) return;
+    const int p = cb.ecell[e];
+    const int k = e - cb.eoff[p];
+    const int deg = cb.deg[p];
+    const int *nb = cb.nb + (size_t)p * kCellSlots;
+    const int gin = nb[(k == 0) ? deg - 1 : k - 1], gout = nb[k];
+    const float4 hp = g.zf[p], lp = g.zl[p];
+    float3 e1, e2;
+    frame32(hp, e1, e2);
+    float u, w;
+    float3 o;
+    if (!vertex32(g, p, hp, lp, e1, e2, gin, gout, u, w)) {
+        o = gnomonic_offset(hp, e1, e2, u, w);
+    } else {
+        // ill conditioned: the corner in FP64, then its offset
+        const V3 zi = ld(g.zs + p);
+        V3 f1, f2;
+        frame64(zi, f1, f2);
+        double a1, b1, c1, a2, b2, c2;
+        line_of(g, zi, f1, f2, gin, a1, b1, c1);
+        line_of(g, zi, f1, f2, gout, a2, b2, c2);
+        const double inv = 1.0 / (a1 * b2 - a2 * b1);
+        const double uu = (c1 * b2 - c2 * b1) * inv, ww = (a1 * c2 - a2 * c1) * inv;
+        const double r2 = uu * uu + ww * ww, q = sqrt(1.0 + r2), t = r2 / (q * (1.0 + q));
+        o = make_float3((float)((uu * f1.x + ww * f2.x) / q - zi.x * t), (float)((uu * f1.y + ww * f2.y) / q - zi.y * t),
+                        (float)((uu * f1.z + ww * f2.z) / q - zi.z * t));
+    }
+    cb.vo[(size_t)p * kCellSlots + k] = make_float4(o.x, o.y, o.z, 0.0f);
+}
+
+struct DensityF {
+    int kind;
+    float gamma, beta, inv_alpha, xc0, xc1, xc2;
+};
+
+struct AccF {
+    float m, ox, oy, oz, e;
+};
+
+__device__ __forceinline__ float rho32(const DensityF &r, float px, float py, float pz) {
+    if (r.kind == 0) return 1.0f;
+    if (r.kind == 1) {
+        const float z2 = pz * pz;
+        return (1.0f - r.gamma) * z2 * z2 + r.gamma;
+    }
+    const float cx = py * r.xc2 - pz * r.xc1, cy = pz * r.xc0 - px * r.xc2, cz = px * r.xc1 - py * r.xc0;
+    const float d = atan2f(sqrtf(cx * cx + cy * cy + cz * cz), px * r.xc0 + py * r.xc1 + pz * r.xc2);
+    // logistic form of (1 - gamma)/2 (tanh(x) + 1) + gamma: no cancellation in the tail
+    float v = (1.0f - r.gamma) / (1.0f + expf(-2.0f * (r.beta - d) * r.inv_alpha)) + r.gamma;
+    if (r.kind == 3) { v = v * v; v = v * v; }
+    return v;
+}
+
+// signed sub-triangle (z, z + oa, z + ob) with the 7-point rule, FP32
+__device__ __forceinline__ void tri32(const DensityF &r, float4 z, float3 oa, float3 ob, AccF &acc) {
+    const float cx = oa.y * ob.z - oa.z * ob.y, cy = oa.z * ob.x - oa.x * ob.z, cz = oa.x * ob.y - oa.y * ob.x;
+    const float det = z.x * cx + z.y * cy + z.z * cz;
+    const float zoa = z.x * oa.x + z.y * oa.y + z.z * oa.z, zob = z.x * ob.x + z.y * ob.y + z.z * ob.z;
+    const float den = 4.0f + 2.0f * zoa + 2.0f * zob + (oa.x * ob.x + oa.y * ob.y + oa.z * ob.z);
+    const float area = 2.0f * atan2f(det, den);
+#pragma unroll 1
+    for (int k = 0; k < 7; ++k) {
+        const float b1 = kQbf[k][0], b2 = kQbf[k][1];  // weights of the 2nd and 3rd vertex
+        const float dx = b1 * oa.x + b2 * ob.x, dy = b1 * oa.y + b2 * ob.y, dz = b1 * oa.z + b2 * ob.z;
+        const float zd = z.x * dx + z.y * dy + z.z * dz, dd = dx * dx + dy * dy + dz * dz;
+        const float n = sqrtf(1.0f + 2.0f * zd + dd);
+        const float t = (2.0f * zd + dd) / (n + 1.0f), in = 1.0f / n;
+        const float ox = (dx - z.x * t) * in, oy = (dy - z.y * t) * in, oz = (dz - z.z * t) * in;
+        const float wr = kQwf[k] * area * rho32(r, z.x + ox, z.y + oy, z.z + oz);
+        acc.m += wr;
+        acc.ox += wr * ox;
+        acc.oy += wr * oy;
+        acc.oz += wr * oz;
+        acc.e += wr * (ox * ox + oy * oy + oz * oz);
+    }
+}
+
+__device__ __forceinline__ void write_cell_offsets(const CellOut &out, int i, V3 zi, const Acc &a, DevStatus *st) {
+    // a.cx, a.cy, a.cz hold o = sum w rho (p - z_i)
+    const double oz = a.cx * zi.x + a.cy * zi.y + a.cz * zi.z;
+    const double cz = a.m + oz;  // c.z_i with |z_i| = 1
+    if (!(cz > 0.0)) atomicOr(&st->flags, FLAG_NONPOSITIVE);
+    if (out.grad) {
+        out.grad[3 * (size_t)i] = -2.0 * (a.cx - oz * zi.x);
+        out.grad[3 * (size_t)i + 1] = -2.0 * (a.cy - oz * zi.y);
+        out.grad[3 * (size_t)i + 2] = -2.0 * (a.cz - oz * zi.z);
+    }
+    if (out.hdiag) out.hdiag[i] = 1.0 / (2.0 * cz);
+    if (out.mass) out.mass[i] = a.m;
+    if (out.moment) {
+        out.moment[3 * (size_t)i] = a.m * zi.x + a.cx;
+        out.moment[3 * (size_t)i + 1] = a.m * zi.y + a.cy;
+        out.moment[3 * (size_t)i + 2] = a.m * zi.z + a.cz;
+    }
+    if (out.fcell) out.fcell[i] = a.e;
+}
+
+// one thread per edge; FP32 sub-triangles, FP64 sums (same reduction and
+// split-cell protocol as k_quad)
+__global__ void __launch_bounds__(256) k_quad32(Grid g, DensityF rho, CellOut out, CellBuf cb,
+                                                double *__restrict__ parts_val, int *__restrict__ parts_cnt,
+                                                DevStatus *st) {
+    const int nedges = cb.eoff[g.n];
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const long long wbase = e - lane;
+    int p = -1, e0 = 0, deg = 0;
+    Acc acc = {0, 0, 0, 0, 0};
+    if (e < nedges) {
+        p = cb.ecell[e];
+        e0 = cb.eoff[p];
+        deg = cb.deg[p];
+        const int k = (int)(e - e0);
+        const float4 hp = g.zf[p], lp = g.zl[p];
+        const float4 va = cb.vo[(size_t)p * kCellSlots + k];
+        const float4 vb = cb.vo[(size_t)p * kCellSlots + ((k + 1 == deg) ? 0 : k + 1)];
+        // edge midpoint normalize(z_i + z_j) as an offset: d/s + z |d|^2 / (s (2 + s)), s = sqrt(4 - |d|^2)
+        const float3 d = dfdiff(g, cb.nb[(size_t)p * kCellSlots + k], hp, lp);
+        const float dd = fmaf(d.x, d.x, fmaf(d.y, d.y, d.z * d.z));
+        const float sq = sqrtf(4.0f - dd), is = 1.0f / sq, t = dd / (sq * (2.0f + sq));
+        const float3 om = make_float3(d.x * is + hp.x * t, d.y * is + hp.y * t, d.z * is + hp.z * t);
+        AccF a1 = {0, 0, 0, 0, 0}, a2 = {0, 0, 0, 0, 0};
+        tri32(rho, hp, make_float3(va.x, va.y, va.z), om, a1);
+        tri32(rho, hp, om, make_float3(vb.x, vb.y, vb.z), a2);
+        acc.m = (double)a1.m + (double)a2.m;
+        acc.cx = (double)a1.ox + (double)a2.ox;
+        acc.cy = (double)a1.oy + (double)a2.oy;
+        acc.cz = (double)a1.oz + (double)a2.oz;
+        acc.e = (double)a1.e + (double)a2.e;
+    }
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int po = __shfl_down_sync(0xffffffffu, p, o);
+        const double m = __shfl_down_sync(0xffffffffu, acc.m, o);
+        const double cx = __shfl_down_sync(0xffffffffu, acc.cx, o);
+        const double cy = __shfl_down_sync(0xffffffffu, acc.cy, o);
+        const double cz = __shfl_down_sync(0xffffffffu, acc.cz, o);
+        const double ee = __shfl_down_sync(0xffffffffu, acc.e, o);
+        if (lane + o < 32 && po == p) {
+            acc.m += m;
+            acc.cx += cx;
+            acc.cy += cy;
+            acc.cz += cz;
+            acc.e += ee;
+        }
+    }
+    const int pprev = __shfl_up_sync(0xffffffffu, p, 1);
+    const bool head = (p >= 0) && (lane == 0 || pprev != p);
+    if (!head) return;
+    const V3 zi = ld(g.zs + p);
+    const bool starts_here = e0 >= wbase;
+    const bool ends_here = e0 + deg <= wbase + 32;
+    if (starts_here && ends_here) {
+        write_cell_offsets(out, g.sidx[p], zi, acc, st);
+        return;
+    }
+    double *slot = parts_val + (size_t)p * 10 + (starts_here ? 0 : 5);
+    slot[0] = acc.m; slot[1] = acc.cx; slot[2] = acc.cy; slot[3] = acc.cz; slot[4] = acc.e;
+    __threadfence();
+    if (atomicAdd(&parts_cnt[p], 1) == 1) {
+        __threadfence();
+        const volatile double *a = parts_val + (size_t)p * 10;
+        Acc tot;
+        tot.m = a[0] + a[5];
+        tot.cx = a[1] + a[6];
+        tot.cy = a[2] + a[7];
+        tot.cz = a[3] + a[8];
+        tot.e = a[4] + a[9];
+        parts_cnt[p] = 0;
+        write_cell_offsets(out, g.sidx[p], zi, tot, st);
+    }
+}
+
 }  // namespace
 
 void bin_points(const double *z, int n, int G, int *bin_of, int *count, int *start, int *cursor, int *scan_tmp,
@@ -1245,8 +1478,8 @@ __global__ void k_set_total_from(int *arr, int n, const int *last_in) {
 }
 
 void cell_passes(const Grid &g, const Density &rho, const CellOut &out, const CellBuf &cb, int *list1, int *list2,
-                 DevStatus *st, int knn_k0, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1, int64_t *launches,
-                 int64_t *cell_launches) {
+                 DevStatus *st, int knn_k0, bool mixed, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1,
+                 int64_t *launches, int64_t *cell_launches) {
     (void)knn_k0;
     // first pass: a warp per cell, grid sized to fill the GPU (grid-stride over cells)
     const int wblocks = (int)std::min<long long>((g.n + 3) / 4, 152LL * 16);
@@ -1265,10 +1498,25 @@ void cell_passes(const Grid &g, const Density &rho, const CellOut &out, const Ce
     // Euler: a full tessellation has 6N - 12 edge sides; failed cells only lower the count
     const long long max_edges = 6LL * g.n;
     const unsigned eblocks = (unsigned)((max_edges + 255) / 256);
-    k_corners<<<eblocks, 256, 0, s>>>(g, cb);
-    if (ev0) cudaEventRecord(ev0, s);
-    k_quad<<<eblocks, 256, 0, s>>>(g, rho, out, cb, cb.eoff, cb.ecell, cb.parts_val, cb.parts_cnt, st);
-    if (ev1) cudaEventRecord(ev1, s);
+    if (mixed) {
+        k_corners32<<<eblocks, 256, 0, s>>>(g, cb);
+        DensityF rf;
+        rf.kind = rho.kind;
+        rf.gamma = (float)rho.gamma;
+        rf.beta = (float)rho.beta;
+        rf.inv_alpha = (float)(1.0 / rho.alpha);
+        rf.xc0 = (float)rho.xc0;
+        rf.xc1 = (float)rho.xc1;
+        rf.xc2 = (float)rho.xc2;
+        if (ev0) cudaEventRecord(ev0, s);
+        k_quad32<<<eblocks, 256, 0, s>>>(g, rf, out, cb, cb.parts_val, cb.parts_cnt, st);
+        if (ev1) cudaEventRecord(ev1, s);
+    } else {
+        k_corners<<<eblocks, 256, 0, s>>>(g, cb);
+        if (ev0) cudaEventRecord(ev0, s);
+        k_quad<<<eblocks, 256, 0, s>>>(g, rho, out, cb, cb.eoff, cb.ecell, cb.parts_val, cb.parts_cnt, st);
+        if (ev1) cudaEventRecord(ev1, s);
+    }
     (*launches) += 7;
     (*cell_launches) += 4;
 }

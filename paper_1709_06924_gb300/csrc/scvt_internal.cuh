@@ -81,6 +81,7 @@ struct CellBuf {
     int *scan_tmp;     // scratch of the scan over n (2 * (n / 2048 + 64) + 64 ints)
     double *parts_val; // 10n: two partial sums per cell split across warps
     int *parts_cnt;    // n: arrivals per split cell, zero between evaluations
+    float4 *vo;        // n * kCellSlots corner offsets v - z_i in FP32 (mixed precision only)
 };
 
 // ---- binning (cells.cu) ----
@@ -91,9 +92,10 @@ void bin_points(const double *z, int n, int G, int *bin_of, int *count, int *sta
 // ---- cell passes (cells.cu) ----
 // topology pass 0 over all cells, passes 1..2 over the retry lists, then the
 // quadrature kernel over all cells (timed by ev0/ev1 when given).
+// mixed: corners and quadrature in FP32 local coordinates, FP64 accumulation
 void cell_passes(const Grid &g, const Density &rho, const CellOut &out, const CellBuf &cb, int *list1, int *list2,
-                 DevStatus *st, int knn_k0, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1, int64_t *launches,
-                 int64_t *cell_launches);
+                 DevStatus *st, int knn_k0, bool mixed, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1,
+                 int64_t *launches, int64_t *cell_launches);
 
 // ---- reductions and vector kernels (lbfgs.cu) ----
 int reduce_blocks(int64_t n);

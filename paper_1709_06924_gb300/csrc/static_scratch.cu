@@ -169,6 +169,7 @@ extern "C" scvt_status scvt_energy_grad_static(int64_t n, const scvt_density *rh
     cb.scan_tmp = (int *)(base + oEscan);
     cb.parts_val = (double *)(base + oPval);
     cb.parts_cnt = (int *)(base + oPcnt);
+    cb.vo = nullptr;
     if (cudaMemsetAsync(cb.parts_cnt, 0, sizeof(int) * N, s) != cudaSuccess) {
         cudaGetLastError();
         return SCVT_ERR_CUDA;
@@ -181,7 +182,7 @@ extern "C" scvt_status scvt_energy_grad_static(int64_t n, const scvt_density *rh
     d.xc0 = rho->xc[0];
     d.xc1 = rho->xc[1];
     d.xc2 = rho->xc[2];
-    cell_passes(grid, d, out, cb, list1, list2, st, 32, s, nullptr, nullptr, &launches, &cell_launches);
+    cell_passes(grid, d, out, cb, list1, list2, st, 32, false, s, nullptr, nullptr, &launches, &cell_launches);
     reduce_eval(N, fc, g, nullptr, nullptr, partials, st, s, &launches);
     DevStatus hs;
     cudaError_t e = cudaMemcpyAsync(&hs, st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s);

@@ -38,7 +38,9 @@ def _density(d: Density) -> capi.scvt_density:
 
 class Engine:
     def __init__(self, n: int, density: Density, lbfgs_m: int = 7, knn_k0: int = 0,
-                 device: int | torch.device = 0, stream: torch.cuda.Stream | None = None):
+                 device: int | torch.device = 0, stream: torch.cuda.Stream | None = None, precision: int = 0):
+        """precision: 0 = FP64 throughout, 1 = mixed (FP32 corners and quadrature in local
+        coordinates, FP64 predicates filter, sums and LBFGS)."""
         self.n = int(n)
         self.device = torch.device("cuda", device) if isinstance(device, int) else torch.device(device)
         with torch.cuda.device(self.device):
@@ -47,7 +49,7 @@ class Engine:
         cfg.n = self.n
         cfg.rho = _density(density)
         cfg.quad_points = 7
-        cfg.precision = 0
+        cfg.precision = int(precision)
         cfg.lbfgs_m = int(lbfgs_m)
         cfg.knn_k0 = int(knn_k0)
         cfg.knn_kmax = 0
