@@ -213,11 +213,16 @@ def two_loop(g, h, S, Y):
 
 
 def line_search(phi, f0, g0, stp0=1.0, ftol=1e-4, gtol=0.9, xtol=1e-16, stpmin=1e-20, stpmax=1e20, maxfev=10):
-    """More-Thuente search on a Python callable phi(a) -> (f, f')."""
+    """More-Thuente search on a Python callable phi(a) -> (f, f'), or None
+    when the trial point is not valid (the search then halves the step)."""
     calls = []
 
     def cb(_ctx, a, fp, gp):
-        f, g = phi(a)
+        r = phi(a)
+        if r is None:
+            calls.append((a, None, None))
+            return 2
+        f, g = r
         calls.append((a, f, g))
         fp[0] = f
         gp[0] = g

@@ -37,7 +37,9 @@
  *   - energy accumulated directly as rho |p - z_i|^2 (no 2m - 2 z.c identity);
  *   - line search: More-Thuente (1994) with c1 = 1e-4, c2 = 0.9, step bounds
  *     [1e-20, 1e20], derivative along the projected path
- *     phi'(a) = sum_i g_i(a).q_i / |z_i + a q_i|.
+ *     phi'(a) = sum_i g_i(a).q_i / |z_i + a q_i|; a trial step whose
+ *     generators do not form a valid tessellation is halved toward the best
+ *     step so far and never exceeded again.
  */
 #include <math.h>
 #include <stdint.h>
@@ -973,10 +975,12 @@ static int mt_search(orc_phi_fn phi, void *ctx, double f0, double g0, const mt_o
     double width = o->stpmax - o->stpmin, width1 = 2.0 * width;
     double tmin = 0.0, tmax = *stp + 4.0 * *stp;
     double t = *stp;
+    double cap = INFINITY; /* smallest step whose trial point was not a tessellation */
     *nfev = 0;
     for (;;) {
         t = fmax(t, o->stpmin);
         t = fmin(t, o->stpmax);
+        if (t >= cap) t = S.x + 0.5 * (cap - S.x);
         if ((S.brackt && (t <= tmin || t >= tmax)) || *nfev >= o->maxfev - 1 ||
             (S.brackt && tmax - tmin <= o->xtol * tmax))
             t = S.x; /* an unusual end is coming: evaluate the best step */
@@ -984,6 +988,14 @@ static int mt_search(orc_phi_fn phi, void *ctx, double f0, double g0, const mt_o
         int cb = phi(ctx, t, &ft, &dt);
         (*nfev)++;
         *stp = t; *f = ft; *g = dt;
+        if (cb == 2) {
+            /* invalid trial point: halve the step toward the best one */
+            *f = INFINITY;
+            if (*nfev >= o->maxfev) return 3;
+            cap = t;
+            t = S.x + 0.5 * (t - S.x);
+            continue;
+        }
         if (cb != 0) return -1;
         double ftest = f0 + t * gtest;
         if ((S.brackt && (t <= tmin || t >= tmax))) info = 6;
@@ -1077,6 +1089,7 @@ static int phi_eval(void *vctx, double a, double *f, double *dphi)
         for (int d = 0; d < 3; d++) C->zt[3 * (size_t)i + d] = x[d] / r;
     }
     int rc = eval_all(n, C->zt, C->rho, NULL, &C->Ft, C->gt, C->ht, NULL, NULL, NULL, NULL, NULL, C->nthreads);
+    if (rc == ORC_DEGENERATE || rc == ORC_INVALID) { free(nrm); free(tmp); return 2; } /* not a tessellation */
     if (rc != ORC_OK) { free(nrm); free(tmp); C->rc = rc; return 1; }
     for (int i = 0; i < n; i++)
         for (int d = 0; d < 3; d++)

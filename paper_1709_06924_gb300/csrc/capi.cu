@@ -245,9 +245,12 @@ class WolfeSearch {
     double ftol = 1e-4, gtol = 0.9, xtol = 1e-16, amin = 1e-20, amax = 1e20;
     int maxfev = 10;
 
-    // phi(a, &f, &d) returns 0 on success.  On return a, f, d hold the last
-    // evaluated point.  Result: 1 strong Wolfe, 2 width below xtol, 3 maxfev,
-    // 4 at amin, 5 at amax, 6 rounding, 7 bad input, <0 callback failure.
+    // phi(a, &f, &d) returns 0 on success, 1 when the trial point is not a
+    // valid tessellation (then the step is halved toward the best point and
+    // never exceeded again), < 0 on a hard failure.  On return a, f, d hold
+    // the last evaluated point (f = +inf if it was invalid).  Result:
+    // 1 strong Wolfe, 2 width below xtol, 3 maxfev, 4 at amin, 5 at amax,
+    // 6 rounding, 7 bad input, <0 callback failure.
     template <class Phi>
     int run(Phi &&phi, double f0, double d0, double &a, double &f, double &d, int &nfev) {
         nfev = 0;
@@ -259,15 +262,24 @@ class WolfeSearch {
         const double slope = ftol * d0;
         double width = amax - amin, width_prev = 2.0 * width;
         double lo_bound = 0.0, hi_bound = a * 5.0;
+        double cap = INFINITY;  // smallest step whose trial point was invalid
         for (;;) {
             a = std::min(std::max(a, amin), amax);
+            if (a >= cap) a = lo_.a + 0.5 * (cap - lo_.a);
             bool last_chance = nfev >= maxfev - 1;
             if ((brack_ && (a <= lo_bound || a >= hi_bound)) || last_chance ||
                 (brack_ && hi_bound - lo_bound <= xtol * hi_bound))
                 a = lo_.a;
             int cb = phi(a, f, d);
             ++nfev;
-            if (cb) return -1;
+            if (cb < 0) return -1;
+            if (cb > 0) {
+                f = INFINITY;
+                if (nfev >= maxfev) return 3;
+                cap = a;
+                a = lo_.a + 0.5 * (a - lo_.a);
+                continue;
+            }
             const double armijo = f0 + a * slope;
             int info = 0;
             if (brack_ && (a <= lo_bound || a >= hi_bound)) info = 6;
@@ -713,7 +725,14 @@ scvt_status scvt_lbfgs_solve(scvt_handle *H, double *z, const scvt_solve_opts *o
             double g2;
             cb_status = evaluate_dev(H, B.zt, B.gt, B.ht, B.fc, nullptr, nullptr, nullptr, nullptr, 0, B.q, B.nrm, &f,
                                      &g2, &d);
-            return cb_status != SCVT_OK;
+            if (cb_status == SCVT_OK) return 0;
+            // a step that breaks the tessellation is a failed trial, not an error
+            if (cb_status == SCVT_ERR_DEGENERATE || cb_status == SCVT_ERR_INVALID ||
+                cb_status == SCVT_ERR_KNN_EXHAUSTED) {
+                cb_status = SCVT_OK;
+                return 1;
+            }
+            return -1;
         };
         double a = 1.0, fa = 0.0, da = 0.0;
         int nfev = 0;

@@ -770,13 +770,16 @@ __global__ void __launch_bounds__(128) k_topo(Grid g, Density rho, CellOut out, 
 // The first pass gives each cell one warp, so that control flow is uniform:
 // lanes scan candidate generators together, the polygon keeps one vertex
 // per lane in registers, and a clip is a per-lane side test, a ballot and a
-// shuffle compaction.  Differences z_j - z_i come from the FP32 pairs
+// shuffle compaction.  A vertex whose two lines meet at a small angle
+// (|det| < (|a1 b2| + |a2 b1|)/30) is solved once in FP64 when it is created
+// and kept rounded to FP32, so later side tests on it stay FP32-filtered.
+// Differences z_j - z_i come from the FP32 pairs
 // (hi, lo) of the coordinates: fl(hi_j - hi_i) is within 6e-8 of its value
 // and the lo parts (<= 3e-8 each) add the rest, so d is within ~2e-7 of |d|
 // and no FP64 arithmetic is needed except in rare per-lane fallbacks.  Cells
 // this pass cannot certify (or with more than 16 edges, or 32 vertices at
 // some point) go to the retry list of the thread-per-cell passes.
-constexpr int kWarpCand = 128;  // candidate buffer per warp (4 per lane)
+constexpr int kWarpCand = 64;  // candidate buffer per warp (2 per lane, sorted once)
 constexpr unsigned kFull = 0xffffffffu;
 
 __device__ __forceinline__ float3 dfdiff(const Grid &g, int q, float4 hp, float4 lp) {
@@ -914,7 +917,7 @@ __global__ void __launch_bounds__(128) k_topo_warp(Grid g, CellOut out, CellBuf 
         float R2 = 0.0f;
         // polygon: lane k < nv holds vertex k and its outgoing edge's line
         float vu = 0.0f, vw = 0.0f, la_o = 0.0f, lb_o = 0.0f, lc_o = 0.0f;
-        int vill = 0, g_o = 0;
+        int vill = 0, g_o = 0, g_i = 0;
         for (int attempt = 0; attempt < 4 && ok && !certified; ++attempt) {
             // ---- candidates within chord r (every one of them; the rest are farther than r)
             const float rs = r * (1.0f + 1e-5f) + 1e-7f;  // covers the FP32 centre
@@ -965,13 +968,58 @@ __global__ void __launch_bounds__(128) k_topo_warp(Grid g, CellOut out, CellBuf 
                 r = fminf(r * 2.0f, rmax);
                 continue;
             }
-            float md[4];
-            int mj[4];
+            // ---- sort the candidates once: bitonic network over 64 slots, element
+            // e = 2 lane + s in register s of `lane`; empty slots sort last
+            float cdd[2];
+            int cjj[2];
 #pragma unroll
-            for (int sl = 0; sl < 4; ++sl) {
-                const int idx = sl * 32 + lane;
-                md[sl] = (idx < cnt) ? cd[idx] : INF;
-                mj[sl] = (idx < cnt) ? cj[idx] : 0x7fffffff;
+            for (int sl = 0; sl < 2; ++sl) {
+                const int idx = 2 * lane + sl;
+                cdd[sl] = (idx < cnt) ? cd[idx] : INF;
+                cjj[sl] = (idx < cnt) ? cj[idx] : 0x7fffffff;
+            }
+            __syncwarp();
+#pragma unroll
+            for (int k = 2; k <= 64; k <<= 1) {
+#pragma unroll
+                for (int j = k >> 1; j > 0; j >>= 1) {
+#pragma unroll
+                    for (int sl = 0; sl < 2; ++sl) {
+                        const int e = 2 * lane + sl;
+                        float od;
+                        int oj;
+                        if (j == 1) {
+                            od = cdd[sl ^ 1];
+                            oj = cjj[sl ^ 1];
+                        } else {
+                            od = __shfl_xor_sync(kFull, cdd[sl], j >> 1);
+                            oj = __shfl_xor_sync(kFull, cjj[sl], j >> 1);
+                        }
+                        const bool ascending = (e & k) == 0, lower = (e & j) == 0;
+                        const bool other_less = od < cdd[sl] || (od == cdd[sl] && oj < cjj[sl]);
+                        const bool take = (lower == ascending) ? other_less : !other_less;
+                        if (j == 1) {
+                            // both slots of the lane are the pair: decide once, from slot 0
+                            if (sl == 0) {
+                                if (take) {
+                                    const float td = cdd[0];
+                                    const int tj = cjj[0];
+                                    cdd[0] = cdd[1]; cjj[0] = cjj[1];
+                                    cdd[1] = td; cjj[1] = tj;
+                                }
+                            }
+                        } else if (take) {
+                            cdd[sl] = od;
+                            cjj[sl] = oj;
+                        }
+                    }
+                }
+            }
+            // sorted order back to shared memory: step t reads slot t by broadcast
+#pragma unroll
+            for (int sl = 0; sl < 2; ++sl) {
+                cd[2 * lane + sl] = cdd[sl];
+                cj[2 * lane + sl] = cjj[sl];
             }
             __syncwarp();
             // ---- the starting square
@@ -984,29 +1032,16 @@ __global__ void __launch_bounds__(128) k_topo_warp(Grid g, CellOut out, CellBuf 
                 lb_o = (lane == 1) ? 1.0f : ((lane == 3) ? -1.0f : 0.0f);
                 lc_o = L;
                 g_o = -1 - lane;
+                g_i = -1 - ((lane + 3) & 3);
                 vill = 0;
             }
             R2 = chord2_up(2.0f * (float)kBoxL * (float)kBoxL);
             bool early = false;
-            for (;;) {
-                // nearest remaining candidate
-                float bd = md[0];
-                int bj = mj[0];
-#pragma unroll
-                for (int sl = 1; sl < 4; ++sl)
-                    if (md[sl] < bd || (md[sl] == bd && mj[sl] < bj)) { bd = md[sl]; bj = mj[sl]; }
-                float wd = bd;
-                int wj = bj;
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    const float od = __shfl_xor_sync(kFull, wd, o);
-                    const int oj = __shfl_xor_sync(kFull, wj, o);
-                    if (od < wd || (od == wd && oj < wj)) { wd = od; wj = oj; }
-                }
-                if (wd == INF) break;
-#pragma unroll
-                for (int sl = 0; sl < 4; ++sl)
-                    if (md[sl] == wd && mj[sl] == wj) md[sl] = INF;
+            const int ncand = min(cnt, kWarpCand);
+            for (int t = 0; t < ncand; ++t) {
+                // candidate t (nearest first)
+                const float wd = cd[t];
+                const int wj = cj[t];
                 // security radius: everything left is at least this far
                 const float bound = fminf(wd * (1.0f - 2e-6f), D2);
                 if (bound > 4.0f * R2 * (1.0f + 1e-6f)) { early = true; break; }
@@ -1015,15 +1050,12 @@ __global__ void __launch_bounds__(128) k_topo_warp(Grid g, CellOut out, CellBuf 
                 const float la = e1.x * d.x + e1.y * d.y + e1.z * d.z;
                 const float lb = e2.x * d.x + e2.y * d.y + e2.z * d.z;
                 const float lc = 0.5f * fmaf(d.x, d.x, fmaf(d.y, d.y, d.z * d.z));
-                const float lab = fabsf(la) + fabsf(lb);
-                const int prevl = (lane == 0) ? nv - 1 : lane - 1;
-                const int gin = __shfl_sync(kFull, g_o, prevl);
                 bool outside = false;
                 if (lane < nv) {
                     const float sd = fmaf(la, vu, fmaf(lb, vw, -lc));
-                    const float mag = lab * (fabsf(vu) + fabsf(vw)) + fabsf(lc);
+                    const float mag = (fabsf(la) + fabsf(lb)) * (fabsf(vu) + fabsf(vw)) + fabsf(lc);
                     if (!vill && fabsf(sd) > 2e-4f * mag) outside = sd > 0.0f;
-                    else outside = outside64(g, p, gin, g_o, wj, &st->ambiguous);
+                    else outside = outside64(g, p, g_i, g_o, wj, &st->ambiguous);
                 }
                 const unsigned m = __ballot_sync(kFull, outside);
                 if (m == 0u) continue;
@@ -1045,41 +1077,46 @@ __global__ void __launch_bounds__(128) k_topo_warp(Grid g, CellOut out, CellBuf 
                 if (nnew > 32) { ok = false; break; }
                 const float ai = __shfl_sync(kFull, la_o, kin), bi = __shfl_sync(kFull, lb_o, kin),
                             ci = __shfl_sync(kFull, lc_o, kin);
-                // new vertices P = (edge kin) x (new line), Q = (new line) x (edge k1)
+                const int gkin = __shfl_sync(kFull, g_o, kin);
+                // new vertices P = (edge kin) x (new line), Q = (new line) x (edge k1);
+                // lanes >= 2 take the surviving vertices k1+1 .. kin
                 const int src = (lane >= 2) ? (k1 + lane - 1) % nv : k1;
                 const float su = __shfl_sync(kFull, vu, src), sw = __shfl_sync(kFull, vw, src);
                 const int sill = __shfl_sync(kFull, vill, src), sg = __shfl_sync(kFull, g_o, src);
+                const int sgi = __shfl_sync(kFull, g_i, src);
                 const float sa = __shfl_sync(kFull, la_o, src), sb = __shfl_sync(kFull, lb_o, src),
                             sc = __shfl_sync(kFull, lc_o, src);
                 if (lane == 0) {
-                    const float p1 = ai * lb, p2 = la * bi, det = p1 - p2;
-                    vu = (ci * lb - lc * bi) / det;
-                    vw = (ai * lc - la * ci) / det;
-                    vill = !(fabsf(det) * 30.0f >= fabsf(p1) + fabsf(p2));
-                    la_o = la; lb_o = lb; lc_o = lc; g_o = wj;
+                    const float p1 = ai * lb, p2 = la * bi, det = p1 - p2, inv = __frcp_rn(det);
+                    vu = (ci * lb - lc * bi) * inv;
+                    vw = (ai * lc - la * ci) * inv;
+                    vill = 0;
+                    if (!(fabsf(det) * 30.0f >= fabsf(p1) + fabsf(p2))) {
+                        // poorly conditioned in FP32: solve once in FP64, keep the rounded vertex
+                        double u, w;
+                        vertex64(g, p, gkin, wj, u, w);
+                        vu = (float)u;
+                        vw = (float)w;
+                    }
+                    la_o = la; lb_o = lb; lc_o = lc; g_o = wj; g_i = gkin;
                 } else if (lane == 1) {
-                    const float p1 = la * sb, p2 = sa * lb, det = p1 - p2;
-                    vu = (lc * sb - sc * lb) / det;
-                    vw = (la * sc - sa * lc) / det;
-                    vill = !(fabsf(det) * 30.0f >= fabsf(p1) + fabsf(p2));
-                    la_o = sa; lb_o = sb; lc_o = sc; g_o = sg;
+                    const float p1 = la * sb, p2 = sa * lb, det = p1 - p2, inv = __frcp_rn(det);
+                    vu = (lc * sb - sc * lb) * inv;
+                    vw = (la * sc - sa * lc) * inv;
+                    vill = 0;
+                    if (!(fabsf(det) * 30.0f >= fabsf(p1) + fabsf(p2))) {
+                        double u, w;
+                        vertex64(g, p, wj, sg, u, w);
+                        vu = (float)u;
+                        vw = (float)w;
+                    }
+                    la_o = sa; lb_o = sb; lc_o = sc; g_o = sg; g_i = wj;
                 } else {
-                    vu = su; vw = sw; vill = sill; la_o = sa; lb_o = sb; lc_o = sc; g_o = sg;
+                    vu = su; vw = sw; vill = sill; la_o = sa; lb_o = sb; lc_o = sc; g_o = sg; g_i = sgi;
                 }
                 nv = nnew;
                 // R2: an upper bound of the largest squared vertex chord
-                const int pl = (lane == 0) ? nv - 1 : lane - 1;
-                const int gin2 = __shfl_sync(kFull, g_o, pl);
-                float r2v = 0.0f;
-                if (lane < nv) {
-                    if (vill) {
-                        double u, w;
-                        vertex64(g, p, gin2, g_o, u, w);
-                        r2v = (float)(u * u + w * w);
-                    } else {
-                        r2v = vu * vu + vw * vw;
-                    }
-                }
+                float r2v = (lane < nv) ? vu * vu + vw * vw : 0.0f;
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) r2v = fmaxf(r2v, __shfl_xor_sync(kFull, r2v, o));
                 R2 = chord2_up(r2v * 1.001f);

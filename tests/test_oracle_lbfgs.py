@@ -127,6 +127,21 @@ def test_line_search_strong_wolfe_on_analytic_functions(a0):
         assert res["calls"][-1] == (res["stp"], res["f"], res["g"])
 
 
+def test_line_search_backs_off_invalid_trial_points():
+    # (a - 3)^2 whose trial points beyond a = 2.5 are not valid: the search
+    # halves toward the best step, never returns above the first invalid one
+    def phi(a):
+        return None if a > 2.5 else ((a - 3.0) ** 2, 2.0 * (a - 3.0))
+
+    res = oracle.line_search(phi, 9.0, -6.0, stp0=10.0, maxfev=20)
+    assert res["info"] == 1
+    assert res["stp"] <= 2.5 and _wolfe_ok(res, 9.0, -6.0)
+    bad = [a for a, f, g in res["calls"] if f is None]
+    assert bad and all(a > 2.5 for a in bad)
+    firstbad = bad[0]
+    assert all(a < firstbad for a, f, g in res["calls"][res["calls"].index((firstbad, None, None)) + 1:])
+
+
 def test_line_search_quadratic_unit_step_accepted():
     # phi(a) = (a - 1)^2: the unit step is the exact minimiser
     res = oracle.line_search(lambda a: ((a - 1) ** 2, 2 * (a - 1)), 1.0, -2.0, stp0=1.0)
