@@ -47,6 +47,8 @@ def parse():
     p.add_argument("--cpu-sample-iters", type=int, default=3)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-other-form", action="store_true", help="skip timing the other precision form")
+    p.add_argument("--no-time-to-tol", action="store_true", help="skip the time-to-tolerance runs")
     p.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
                    help="fp64: everything in FP64; mixed: FP32 corners/quadrature, FP64 sums and LBFGS")
     return p.parse_args()
@@ -164,6 +166,51 @@ def run_reference(args, w):
 
 
 # ------------------------------------------------------------------- our arm
+def combine_ranks(units: float, seconds: float, device=None):
+    """Whole-job numbers over replicas: units summed, time = max over ranks
+    (torch.distributed; identity on a single process)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(units), float(seconds)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(u.item()), float(t.item())
+
+
+def timed_steps(eng, z, steps):
+    """K LBFGS iterations continuing the engine's state, timed with CUDA
+    events on the engine's stream; returns (report, seconds)."""
+    import torch
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(eng.stream)
+    rep = eng.lbfgs_solve(z, max_iter=steps, grad_tol=0.0, warm_start=True)
+    ev1.record(eng.stream)
+    torch.cuda.synchronize()
+    return rep, ev0.elapsed_time(ev1) / 1e3
+
+
+def time_to_tolerance(w, z_host, local, prec, tol=1e-6, max_iter=50):
+    """Wall time from the seeded start until ||grad E||_2 <= tol (the
+    workload's stated criterion), with the iterate on the device."""
+    import torch
+    from paper_1709_06924_gb300.engine import Engine
+    eng = Engine(w.n, w.density, lbfgs_m=w.lbfgs_m, device=local, precision=prec)
+    z = torch.from_numpy(z_host).cuda(local)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rep = eng.lbfgs_solve(z, max_iter=max_iter, grad_tol=tol)
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+    eng.close()
+    return {"grad_tol": tol, "seconds": t, "iters": rep["iters"], "fevals": rep["fevals"],
+            "converged": bool(rep["converged"]), "grad_norm": rep["grad_norm"],
+            "grad_norm_over_F": rep["grad_norm"] / rep["energy"]}
+
+
 def run_ours(args, w):
     import torch
     ws, rank, local = dist_env()
@@ -173,7 +220,7 @@ def run_ours(args, w):
     torch.cuda.set_device(local)
     from paper_1709_06924_gb300.engine import Engine
 
-    seed = args.seed + rank
+    seed = args.seed + rank          # each replica solves its own instance
     z_host = I.uniform_sphere(w.n, seed)
     prec = 1 if args.precision == "mixed" else 0
     eng = Engine(w.n, w.density, lbfgs_m=w.lbfgs_m, device=local, precision=prec)
@@ -188,8 +235,7 @@ def run_ours(args, w):
     eng.reset_stats()
     eng.set_profiling(True)
     try:
-        uuid = torch.cuda.get_device_properties(local).uuid
-        uuid = str(uuid)
+        uuid = str(torch.cuda.get_device_properties(local).uuid)
     except Exception:
         uuid = None
     clocks = ClockSampler(uuid)
@@ -197,38 +243,33 @@ def run_ours(args, w):
     torch.cuda.synchronize()
     clocks.start()
     time.sleep(0.3)
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(eng.stream)
-    rep = eng.lbfgs_solve(z, max_iter=args.steps, grad_tol=0.0, warm_start=True)
-    ev1.record(eng.stream)
-    torch.cuda.synchronize()
+    rep, t = timed_steps(eng, z, args.steps)
     barrier()
     clocks.stop()
-    t = ev0.elapsed_time(ev1) / 1e3
     st = eng.stats()
     iters = rep["iters"]
-    t_max = t
-    if ws > 1:
-        tt = torch.tensor([t], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(tt.item())
-    value = w.n * iters * ws / t_max
+    units, t_max = combine_ranks(w.n * iters, t, device=torch.device("cuda", local))
+    value = units / t_max
 
-    # dominant kernel: k_quad (the cell quadrature), timed by CUDA events on
-    # the engine stream around each launch inside the timed region
+    # dominant kernel: the cell quadrature, timed by CUDA events on the engine
+    # stream around each launch inside the timed region
     quad_ms = st["cell_kernel_ms"] / max(st["cell_kernel_timed"], 1)
-    flops_gen = fp64_flops_per_generator(w.density.kind)
-    peak = fp64_peak_tflops()
-    achieved = w.n * flops_gen / (quad_ms * 1e-3) / 1e12
-    roofline = {"bound": "alu", "kernel": "k_quad", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": quad_traffic_bytes(w.n),
-                "flops_per_generator": flops_gen, "avg_launch_ms": quad_ms,
-                "peak_source": "derived FP64 pipe peak: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz "
-                               "(no FP64 figure in the measured-peaks file; a DFMA microbenchmark on this pool "
-                               "measured 1.006 TFLOP/s)",
-                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_quad launch at "
-                                  "N = 163,842, scaled by N (profiles/k_quad_tanh_163842.md)"}
+    if prec == 0:
+        flops_gen = fp64_flops_per_generator(w.density.kind)
+        peak = fp64_peak_tflops()
+        achieved = w.n * flops_gen / (quad_ms * 1e-3) / 1e12
+        roofline = {"bound": "alu", "kernel": "k_quad", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": quad_traffic_bytes(w.n),
+                    "flops_per_generator": flops_gen, "avg_launch_ms": quad_ms,
+                    "peak_source": "derived FP64 pipe peak: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz "
+                                   "(no FP64 figure in the measured-peaks file; a DFMA microbenchmark on this "
+                                   "pool measured 1.006 TFLOP/s)",
+                    "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_quad launch "
+                                      "at N = 163,842, scaled by N (profiles/k_quad_tanh_163842.md)"}
+    else:
+        roofline = {"bound": "alu", "kernel": "k_quad32", "achieved": None, "peak": None, "unit": "TFLOP/s",
+                    "frac": None, "traffic": None, "avg_launch_ms": quad_ms,
+                    "note": "mixed form: the FP32 quadrature is no longer the dominant kernel"}
 
     # end to end through the C ABI with host buffers: a second engine replays
     # the same warm-up (evaluations are deterministic, so it reaches the same
@@ -256,13 +297,33 @@ def run_ours(args, w):
         te = e0.elapsed_time(e1) / 1e3
         same = bool(np.array_equal(zp.numpy(), z.cpu().numpy()))
         eng2.close()
-        if ws > 1:
-            tt = torch.tensor([te], device="cuda")
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            te = float(tt.item())
-        e2e = {"value": w.n * k_e2e * ws / te, "unit": "generator-updates/s",
+        ue, te = combine_ranks(w.n * k_e2e, te, device=torch.device("cuda", local))
+        e2e = {"value": ue / te, "unit": "generator-updates/s",
                "h2d_bytes_per_step": w.n * 24, "d2h_bytes_per_step": w.n * 24,
                "same_iterates_as_device_run": same}
+
+    # the other precision form on the same workload, same W and K
+    other = None
+    if not args.no_other_form:
+        oprec = 1 - prec
+        eng3 = Engine(w.n, w.density, lbfgs_m=w.lbfgs_m, device=local, precision=oprec)
+        z3 = torch.from_numpy(z_host).cuda(local)
+        eng3.lbfgs_solve(z3, max_iter=args.warmup, grad_tol=0.0)
+        eng3.reset_stats()
+        eng3.set_profiling(True)
+        torch.cuda.synchronize()
+        rep3, t3 = timed_steps(eng3, z3, args.steps)
+        st3 = eng3.stats()
+        eng3.close()
+        u3, t3 = combine_ranks(w.n * rep3["iters"], t3, device=torch.device("cuda", local))
+        other = {"precision": "mixed" if oprec else "fp64", "dtype": "f32/f64" if oprec else "f64",
+                 "value": u3 / t3, "ms_per_step": 1e3 * t3 / max(rep3["iters"], 1),
+                 "quad_kernel_ms": st3["cell_kernel_ms"] / max(st3["cell_kernel_timed"], 1),
+                 "eval_ms_avg": st3["eval_ms"] / max(st3["evaluations"], 1)}
+
+    ttt = None
+    if not args.no_time_to_tol:
+        ttt = {"fp64": time_to_tolerance(w, z_host, local, 0), "mixed": time_to_tolerance(w, z_host, local, 1)}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -272,12 +333,12 @@ def run_ours(args, w):
         line = {
             "metric": "generator-updates/s", "value": value, "unit": "generator-updates/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_max / max(iters, 1),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32/f64" if prec else "f64", "data": "synthetic",
             "config": {"workload": w.name, "n_generators": w.n, "density": "tanh cap",
                        "gamma": w.density.gamma, "alpha": w.density.alpha, "beta": w.density.beta,
                        "lbfgs_m": w.lbfgs_m, "quadrature": "7-point per sub-triangle", "seed": args.seed,
-                       "parallelism": "replicas" if ws > 1 else "single",
+                       "precision": args.precision, "parallelism": "replicas" if ws > 1 else "single",
                        "l2": "inputs larger than L2 (history %d MB per step)" % (2 * w.lbfgs_m * w.n * 24 >> 20),
                        "iters_timed": iters, "fevals_timed": rep["fevals"]},
             "roofline": roofline,
@@ -285,6 +346,8 @@ def run_ours(args, w):
             "e2e": e2e,
             "clocks": clocks.summary(),
             "gpu_launches": st["kernel_launches"],
+            "other_form": other,
+            "time_to_tol": ttt,
             "knn_retries": st["knn_retries"],
             "ambiguous": st["ambiguous"],
             "eval_ms_avg": st["eval_ms"] / max(st["evaluations"], 1),
@@ -294,14 +357,6 @@ def run_ours(args, w):
     eng.close()
     if ws > 1:
         torch.distributed.destroy_process_group()
-
-
-# FP64 exp per call in DFMA equivalents (measured like the other per-call costs)
-EXP_DFMA = 17.9
-
-
-def fp64_peak_tflops() -> float:
-    return 152 * 2 * 2 * 2.07e9 / 1e12
 
 
 def fp64_flops_per_generator(kind: int) -> float:

@@ -1,0 +1,44 @@
+"""The multi-GPU path of bench.py runs one replica per GPU and combines the
+ranks with sum-of-units / max-of-time; that host logic is checked here with
+two gloo processes on the CPU (no GPU)."""
+import os
+import socket
+
+import pytest
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _worker(rank, world, port, out):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    units = 1000.0 * (rank + 1)        # replicas may process different amounts
+    seconds = 2.0 if rank == 0 else 3.0
+    u, t = bench.combine_ranks(units, seconds)
+    out[rank] = (u, t)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_combine_ranks_two_gloo_processes():
+    world = 2
+    mgr = mp.Manager()
+    out = mgr.dict()
+    mp.spawn(_worker, args=(world, _free_port(), out), nprocs=world, join=True)
+    for r in range(world):
+        assert out[r] == (3000.0, 3.0)
+
+
+def test_combine_ranks_single_process_is_identity():
+    import bench
+    assert bench.combine_ranks(5.0, 2.0) == (5.0, 2.0)
