@@ -359,6 +359,10 @@ def run_ours(args, w):
         torch.distributed.destroy_process_group()
 
 
+# FP64 exp per call in DFMA equivalents (measured like the other per-call costs)
+EXP_DFMA = 17.9
+
+
 def fp64_flops_per_generator(kind: int) -> float:
     """FP64 work of the cell quadrature per generator, in flop equivalents.
 
@@ -386,9 +390,9 @@ def fp64_peak_tflops() -> float:
 
 
 def quad_traffic_bytes(n: int):
-    """DRAM bytes of one k_quad launch: ncu at N = 163,842 (65.81 MB read +
-    2.48 MB written, tanh cap), scaled by the number of generators."""
-    return (65.813248e6 + 2.48192e6) * n / 163842
+    """DRAM bytes of one k_quad launch: ncu at N = 163,842 (66.84 MB read +
+    2.34 MB written, tanh cap), scaled by the number of generators."""
+    return (66.841856e6 + 2.33728e6) * n / 163842
 
 
 def main():

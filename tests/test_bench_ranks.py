@@ -42,3 +42,14 @@ def test_combine_ranks_two_gloo_processes():
 def test_combine_ranks_single_process_is_identity():
     import bench
     assert bench.combine_ranks(5.0, 2.0) == (5.0, 2.0)
+
+
+def test_roofline_figures_are_defined_for_every_density():
+    import bench
+    for kind in (0, 1, 2, 3):
+        assert bench.fp64_flops_per_generator(kind) > 0
+    # uniform < X3 < tanh cap: the density only adds work per rule point
+    f = [bench.fp64_flops_per_generator(k) for k in (0, 1, 2)]
+    assert f[0] < f[1] < f[2]
+    assert abs(bench.fp64_peak_tflops() - 1.25856) < 1e-9
+    assert bench.quad_traffic_bytes(163842) > 0
