@@ -49,6 +49,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-other-form", action="store_true", help="skip timing the other precision form")
     p.add_argument("--no-time-to-tol", action="store_true", help="skip the time-to-tolerance runs")
+    p.add_argument("--no-batched", action="store_true", help="skip the 64-problem batch")
     p.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
                    help="fp64: everything in FP64; mixed: FP32 corners/quadrature, FP64 sums and LBFGS")
     return p.parse_args()
@@ -211,6 +212,40 @@ def time_to_tolerance(w, z_host, local, prec, tol=1e-6, max_iter=50):
             "grad_norm_over_F": rep["grad_norm"] / rep["energy"]}
 
 
+def run_batched(args, local, prec, count=64):
+    """64 independent problems (N log-uniform in [10,242, 655,362], each its own
+    tanh cap) as one batch: autotuned, W warm-up and K timed lockstep LBFGS
+    iterations.  Units = sum over problems of N_b x iterations."""
+    import torch
+    from paper_1709_06924_gb300.engine import Batch
+    inst = I.sample_batched_instances(count, args.seed)
+    ns = [n for n, _, _ in inst]
+    zs = [I.uniform_sphere(n, sd) for n, _, sd in inst]
+    bt = Batch(ns, [d for _, d, _ in inst], lbfgs_m=7, precision=prec, device=local)
+    try:
+        z = torch.from_numpy(np.concatenate(zs)).cuda(local)
+        t0 = time.perf_counter()
+        tuning = bt.tune(z)
+        t_tune = time.perf_counter() - t0
+        bt.lbfgs_solve(z, max_iter=args.warmup, grad_tol=0.0)
+        bt.reset_stats()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        reps = bt.lbfgs_solve(z, max_iter=args.steps, grad_tol=0.0, warm_start=1)
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+        st = bt.stats()
+    finally:
+        bt.close()
+    units = sum(n * r["iters"] for n, r in zip(ns, reps))
+    return {"problems": count, "n_total": int(sum(ns)), "n_min": int(min(ns)), "n_max": int(max(ns)),
+            "precision": "mixed" if prec else "fp64", "value": units / t, "unit": "generator-updates/s",
+            "seconds": t, "iters": [r["iters"] for r in reps][:4] + ["..."],
+            "evaluations": st["evaluations"], "gpu_launches": st["kernel_launches"], "tuning": tuning,
+            "tune_seconds": t_tune, "timing": "host wall clock around the synchronous batch solve",
+            "statuses": sorted({r["status"] for r in reps})}
+
+
 def run_ours(args, w):
     import torch
     ws, rank, local = dist_env()
@@ -321,6 +356,13 @@ def run_ours(args, w):
                  "quad_kernel_ms": st3["cell_kernel_ms"] / max(st3["cell_kernel_timed"], 1),
                  "eval_ms_avg": st3["eval_ms"] / max(st3["evaluations"], 1)}
 
+    batched = None
+    if not args.no_batched:
+        try:
+            batched = {"fp64": run_batched(args, local, 0), "mixed": run_batched(args, local, 1)}
+        except Exception as ex:  # reported, not fatal to the headline line
+            batched = {"error": repr(ex)}
+
     ttt = None
     if not args.no_time_to_tol:
         ttt = {"fp64": time_to_tolerance(w, z_host, local, 0), "mixed": time_to_tolerance(w, z_host, local, 1)}
@@ -348,6 +390,7 @@ def run_ours(args, w):
             "gpu_launches": st["kernel_launches"],
             "other_form": other,
             "time_to_tol": ttt,
+            "batched": batched,
             "knn_retries": st["knn_retries"],
             "ambiguous": st["ambiguous"],
             "eval_ms_avg": st["eval_ms"] / max(st["evaluations"], 1),

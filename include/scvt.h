@@ -185,7 +185,7 @@ scvt_status scvt_lbfgs_direction(scvt_handle *h, const double *g, const double *
  * host that forbids cudaMalloc after start-up).  The paper has no
  * counterpart: this is a deployment variant of scvt_energy_grad.
  * It needs no handle and allocates nothing: its scratch is one fixed array
- * in device memory (about 13.5 MB, held on every GPU that loads the library
+ * in device memory (about 16.3 MB, held on every GPU that loads the library
  * until the process exits), sized for n <= SCVT_STATIC_MAX_N.
  * n: generators (4 <= n <= SCVT_STATIC_MAX_N, else SCVT_ERR_INVALID before
  * any device work).  rho: host.  z: N x 3 device.  cuda_stream: cudaStream_t
@@ -200,6 +200,77 @@ scvt_status scvt_lbfgs_direction(scvt_handle *h, const double *g, const double *
 #define SCVT_STATIC_MAX_N 16384
 scvt_status scvt_energy_grad_static(int64_t n, const scvt_density *rho, const double *z, void *cuda_stream,
                                     double *energy, double *grad, double *mass, double *moment);
+
+/* Launch shape and search parameters of an evaluation (not in the paper:
+ * GPU scheduling).  None of them changes a result -- a cell is unique, its
+ * corners come from its neighbour triples and its sums are taken in its own
+ * edge order -- only the time.  Defaults: 2, 24, 4, 16, 256. */
+typedef struct {
+    int bin_load;           /* target generators per cube-map bin, 1..16: G = ceil(sqrt(N / (6 bin_load)))
+                               bins per face edge */
+    int knn_target;         /* candidates the first search radius aims at when a cell has no radius
+                               from a previous evaluation, 8..64 */
+    int topo_warps;         /* warps per block of the topology pass (one warp per cell): 2, 4 or 8 */
+    int topo_blocks_per_sm; /* grid cap of the topology pass in blocks per SM, 1..64 */
+    int quad_block;         /* threads per block of the per-edge quadrature: 128, 256 or 512 */
+} scvt_tuning;
+
+/* Set / read the tuning of a handle.  INVALID when a field is out of range. */
+scvt_status scvt_set_tuning(scvt_handle *h, const scvt_tuning *t);
+scvt_status scvt_get_tuning(const scvt_handle *h, scvt_tuning *t);
+
+/* ---- Batches of independent problems ------------------------------------
+ * Many problems of Sec. 2.1 (uneven N, each with its own density) solved
+ * together on one GPU.  The paper solves one problem at a time; a batch is
+ * a deployment form of the same computation: every evaluation covers all
+ * problems' cells in one launch sequence (captured once as a CUDA graph and
+ * replayed), and the LBFGS of Sec. 3.1 runs for all problems in lockstep,
+ * each with its own line search, history, preconditioner and stopping test.
+ * Each problem's results equal, bit for bit, those of a single-problem
+ * handle with the same configuration (the tuning does not matter).
+ *
+ * Layout: problem b's generators are rows [off_b, off_b + n_b) of one
+ * concatenated N_tot x 3 array, off_b = n_0 + ... + n_(b-1); the same for
+ * gradients.  Per-problem scalars are host arrays of `count` entries.
+ * The batch owns a CUDA stream of its own; every call first waits for the
+ * work queued on the stream given at creation and synchronises before it
+ * returns. */
+typedef struct scvt_batch scvt_batch;
+
+/* cfgs: `count` configurations (1 <= count <= 65535).  All must share
+ * precision and lbfgs_m.  Allocates the workspace for N_tot = sum n_b
+ * generators (the LBFGS history included).  Errors: INVALID, OOM, CUDA. */
+scvt_status scvt_batch_create(const scvt_config *cfgs, int count, void *cuda_stream, scvt_batch **out);
+void scvt_batch_destroy(scvt_batch *b);  /* NULL-safe */
+
+/* Energies (host, count) and gradients (N_tot x 3, nullable) of every
+ * problem at z (N_tot x 3).  Device or host pointers.  The status is that of
+ * the first problem that failed (all problems are evaluated). */
+scvt_status scvt_batch_energy_grad(scvt_batch *b, const double *z, double *energy, double *grad);
+
+/* Lockstep Lloyd-preconditioned LBFGS of every problem, with the options of
+ * scvt_lbfgs_solve (warm_start 0 or 1; 1 continues every problem from the
+ * batch's previous solve).  z: N_tot x 3 in/out.  reports: host, count
+ * entries (required); reports[b].status is problem b's outcome.  Returns OK
+ * when every problem ended with OK or LINESEARCH, else the status of the
+ * first problem that failed (the others are still solved). */
+scvt_status scvt_batch_lbfgs_solve(scvt_batch *b, double *z, const scvt_solve_opts *opts,
+                                   scvt_solve_report *reports);
+
+/* Autotuner: times evaluations of the batch at z over a grid of tunings
+ * (bin load, first-pass target, topology block shape and grid cap,
+ * quadrature block), coordinate by coordinate, keeps the fastest and
+ * returns it in *chosen (nullable).  The knn_target candidates are timed
+ * without radius hints (the only evaluations that use it), the others on
+ * warm evaluations.  Results of later calls do not depend on the choice. */
+scvt_status scvt_batch_tune(scvt_batch *b, const double *z, scvt_tuning *chosen);
+scvt_status scvt_batch_set_tuning(scvt_batch *b, const scvt_tuning *t);
+scvt_status scvt_batch_get_tuning(const scvt_batch *b, scvt_tuning *t);
+
+/* Counters of the batch (evaluations count batch evaluations). */
+scvt_status scvt_batch_get_stats(const scvt_batch *b, scvt_stats *out);
+scvt_status scvt_batch_reset_stats(scvt_batch *b);
+const char *scvt_batch_last_error(const scvt_batch *b);
 
 /* Per-handle counters and (with profiling on) device times. */
 scvt_status scvt_get_stats(const scvt_handle *h, scvt_stats *out);

@@ -57,6 +57,11 @@ class scvt_eval_out(C.Structure):
                 ("cell_energy", C.c_void_p), ("energy", C.c_double), ("grad_norm", C.c_double)]
 
 
+class scvt_tuning(C.Structure):
+    _fields_ = [("bin_load", C.c_int), ("knn_target", C.c_int), ("topo_warps", C.c_int),
+                ("topo_blocks_per_sm", C.c_int), ("quad_block", C.c_int)]
+
+
 _H = C.c_void_p
 _vp = C.c_void_p
 _st = C.c_int
@@ -79,6 +84,18 @@ SIGNATURES = {
     "scvt_version": (C.c_char_p, []),
     "scvt_energy_grad_static": (_st, [C.c_int64, C.POINTER(scvt_density), _vp, _vp, C.POINTER(C.c_double),
                                       _vp, _vp, _vp]),
+    "scvt_set_tuning": (_st, [_H, C.POINTER(scvt_tuning)]),
+    "scvt_get_tuning": (_st, [_H, C.POINTER(scvt_tuning)]),
+    "scvt_batch_create": (_st, [C.POINTER(scvt_config), C.c_int, _vp, C.POINTER(_H)]),
+    "scvt_batch_destroy": (None, [_H]),
+    "scvt_batch_energy_grad": (_st, [_H, _vp, C.POINTER(C.c_double), _vp]),
+    "scvt_batch_lbfgs_solve": (_st, [_H, _vp, C.POINTER(scvt_solve_opts), C.POINTER(scvt_solve_report)]),
+    "scvt_batch_tune": (_st, [_H, _vp, C.POINTER(scvt_tuning)]),
+    "scvt_batch_set_tuning": (_st, [_H, C.POINTER(scvt_tuning)]),
+    "scvt_batch_get_tuning": (_st, [_H, C.POINTER(scvt_tuning)]),
+    "scvt_batch_get_stats": (_st, [_H, C.POINTER(scvt_stats)]),
+    "scvt_batch_reset_stats": (_st, [_H]),
+    "scvt_batch_last_error": (C.c_char_p, [_H]),
 }
 
 STATIC_MAX_N = 16384  # SCVT_STATIC_MAX_N
@@ -120,9 +137,14 @@ class ScvtError(RuntimeError):
         self.status = status
 
 
-def check(status: int, where: str, handle=None):
+def check(status: int, where: str, handle=None, batch=None):
     if status != OK:
-        detail = lib().scvt_last_error(handle).decode() if handle else ""
+        if handle:
+            detail = lib().scvt_last_error(handle).decode()
+        elif batch:
+            detail = lib().scvt_batch_last_error(batch).decode()
+        else:
+            detail = ""
         raise ScvtError(status, where, detail)
 
 
@@ -186,3 +208,65 @@ def scvt_set_profiling(h, on: bool):
 
 def scvt_version() -> str:
     return lib().scvt_version().decode()
+
+
+def scvt_set_tuning(h, t: scvt_tuning):
+    check(lib().scvt_set_tuning(h, C.byref(t)), "scvt_set_tuning", h)
+
+
+def scvt_get_tuning(h) -> scvt_tuning:
+    t = scvt_tuning()
+    check(lib().scvt_get_tuning(h, C.byref(t)), "scvt_get_tuning", h)
+    return t
+
+
+def scvt_batch_create(cfgs, stream: int | None = None):
+    arr = (scvt_config * len(cfgs))(*cfgs)
+    b = _H()
+    check(lib().scvt_batch_create(arr, len(cfgs), _vp(stream or 0), C.byref(b)), "scvt_batch_create")
+    return b
+
+
+def scvt_batch_destroy(b):
+    lib().scvt_batch_destroy(b)
+
+
+def scvt_batch_energy_grad(b, z_ptr: int, count: int, grad_ptr=None):
+    e = (C.c_double * count)()
+    check(lib().scvt_batch_energy_grad(b, _vp(z_ptr), e, _vp(grad_ptr)), "scvt_batch_energy_grad", batch=b)
+    return list(e)
+
+
+def scvt_batch_lbfgs_solve(b, z_ptr: int, opts: scvt_solve_opts | None, count: int):
+    reps = (scvt_solve_report * count)()
+    st = lib().scvt_batch_lbfgs_solve(b, _vp(z_ptr), C.byref(opts) if opts is not None else None, reps)
+    # a problem's own failure is reported in its entry; anything else raises
+    if st not in (OK, ERR_LINESEARCH) and not any(r.status == st for r in reps):
+        check(st, "scvt_batch_lbfgs_solve", batch=b)
+    return list(reps)
+
+
+def scvt_batch_tune(b, z_ptr: int) -> scvt_tuning:
+    t = scvt_tuning()
+    check(lib().scvt_batch_tune(b, _vp(z_ptr), C.byref(t)), "scvt_batch_tune", batch=b)
+    return t
+
+
+def scvt_batch_set_tuning(b, t: scvt_tuning):
+    check(lib().scvt_batch_set_tuning(b, C.byref(t)), "scvt_batch_set_tuning", batch=b)
+
+
+def scvt_batch_get_tuning(b) -> scvt_tuning:
+    t = scvt_tuning()
+    check(lib().scvt_batch_get_tuning(b, C.byref(t)), "scvt_batch_get_tuning", batch=b)
+    return t
+
+
+def scvt_batch_get_stats(b) -> scvt_stats:
+    s = scvt_stats()
+    check(lib().scvt_batch_get_stats(b, C.byref(s)), "scvt_batch_get_stats", batch=b)
+    return s
+
+
+def scvt_batch_reset_stats(b):
+    check(lib().scvt_batch_reset_stats(b), "scvt_batch_reset_stats", batch=b)

@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "scvt_internal.cuh"
+#include "wolfe.h"
 
 using namespace scvt;
 
@@ -41,8 +42,8 @@ struct Bufs {
     P4 *zs = nullptr;
     float4 *zf = nullptr, *zl = nullptr;
     P4 *cvx = nullptr;
-    int *cdeg = nullptr, *cnb = nullptr, *eoff = nullptr, *ecell = nullptr, *escan = nullptr, *pcnt = nullptr;
-    double *pval = nullptr;
+    int *cdeg = nullptr, *cnb = nullptr, *eoff = nullptr, *ecell = nullptr, *escan = nullptr;
+    double *eacc = nullptr;
     float4 *vo = nullptr;
     int *bin_of = nullptr, *count = nullptr, *start = nullptr, *cursor = nullptr, *scan_tmp = nullptr;
     int *sidx = nullptr, *list1 = nullptr, *list2 = nullptr;
@@ -58,6 +59,7 @@ struct scvt_handle {
     int n = 0;
     int G = 1;
     int m = 0;
+    Tune tune;
     cudaStream_t stream = nullptr;
     Bufs b;
     DevStatus *st_host = nullptr;  // pinned
@@ -113,18 +115,6 @@ bool is_device_ptr(const void *p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-Density to_density(const scvt_density &r) {
-    Density d;
-    d.kind = r.kind;
-    d.gamma = r.gamma;
-    d.alpha = r.alpha;
-    d.beta = r.beta;
-    d.xc0 = r.xc[0];
-    d.xc1 = r.xc[1];
-    d.xc2 = r.xc[2];
-    return d;
-}
-
 double *slot_S(scvt_handle *H, int slot) { return H->b.hist + (size_t)slot * 2 * 3 * H->n; }
 double *slot_Y(scvt_handle *H, int slot) { return slot_S(H, slot) + (size_t)3 * H->n; }
 
@@ -151,8 +141,8 @@ scvt_status evaluate_dev(scvt_handle *H, const double *zdev, double *grad, doubl
     int64_t *L = &H->stats.kernel_launches;
     if (H->profiling) cudaEventRecord(H->ev_e0, s);
     CK(cudaMemsetAsync(B.st, 0, sizeof(DevStatus), s), "reset status");
-    bin_points(zdev, n, H->G, B.bin_of, B.count, B.start, B.cursor, B.scan_tmp, B.zs, B.zf, B.zl, B.sidx, B.st, s, L);
     Grid g;
+    memset(&g, 0, sizeof(g));
     g.n = n;
     g.G = H->G;
     g.nbins = 6 * H->G * H->G;
@@ -161,6 +151,9 @@ scvt_status evaluate_dev(scvt_handle *H, const double *zdev, double *grad, doubl
     g.zl = B.zl;
     g.sidx = B.sidx;
     g.bstart = B.start;
+    g.rho0 = to_device_density(H->cfg.rho);
+    g.rho0f = to_density32(g.rho0);
+    bin_points(zdev, g, B.bin_of, B.count, B.start, B.cursor, B.scan_tmp, B.zs, B.zf, B.zl, B.sidx, B.st, s, L);
     CellOut out;
     out.grad = grad;
     out.hdiag = hdiag;
@@ -182,11 +175,9 @@ scvt_status evaluate_dev(scvt_handle *H, const double *zdev, double *grad, doubl
     cb.eoff = B.eoff;
     cb.ecell = B.ecell;
     cb.scan_tmp = B.escan;
-    cb.parts_val = B.pval;
-    cb.parts_cnt = B.pcnt;
+    cb.eacc = B.eacc;
     cb.vo = B.vo;
-    CK(cudaMemsetAsync(B.pcnt, 0, sizeof(int) * n, s), "reset split-cell counters");
-    cell_passes(g, to_density(H->cfg.rho), out, cb, B.list1, B.list2, B.st, H->cfg.knn_k0, H->cfg.precision == 1, s,
+    cell_passes(g, out, cb, B.list1, B.list2, B.st, H->cfg.precision == 1, H->tune, s,
                 H->profiling ? H->ev_cell0 : nullptr, H->profiling ? H->ev_cell1 : nullptr, L,
                 &H->stats.cell_launches);
     reduce_eval(n, fcell, grad, q, nrm, B.partials, B.st, s, L);
@@ -233,158 +224,6 @@ scvt_status copy_out(scvt_handle *H, double *dst, const double *src, size_t coun
     if (dst != src) CK(cudaMemcpyAsync(dst, src, sizeof(double) * count, k, H->stream), "copy out");
     return SCVT_OK;
 }
-
-// ------------------------------------------------ line search (More-Thuente)
-// Strong-Wolfe search of More & Thuente (1994): on the auxiliary function
-// psi(a) = phi(a) - phi(0) - ftol a phi'(0) until a step with psi <= 0 and
-// phi' >= 0 (up to ftol/gtol) is seen, then on phi; the interval of
-// uncertainty is updated with safeguarded cubic / quadratic / secant steps
-// and bisected when it fails to shrink by 2/3.
-class WolfeSearch {
-  public:
-    double ftol = 1e-4, gtol = 0.9, xtol = 1e-16, amin = 1e-20, amax = 1e20;
-    int maxfev = 10;
-
-    // phi(a, &f, &d) returns 0 on success, 1 when the trial point is not a
-    // valid tessellation (then the step is halved toward the best point and
-    // never exceeded again), < 0 on a hard failure.  On return a, f, d hold
-    // the last evaluated point (f = +inf if it was invalid).  Result:
-    // 1 strong Wolfe, 2 width below xtol, 3 maxfev, 4 at amin, 5 at amax,
-    // 6 rounding, 7 bad input, <0 callback failure.
-    template <class Phi>
-    int run(Phi &&phi, double f0, double d0, double &a, double &f, double &d, int &nfev) {
-        nfev = 0;
-        if (!(d0 < 0.0) || !(a > 0.0)) return 7;
-        lo_ = {0.0, f0, d0};
-        hi_ = {0.0, f0, d0};
-        brack_ = false;
-        bool first_stage = true;
-        const double slope = ftol * d0;
-        double width = amax - amin, width_prev = 2.0 * width;
-        double lo_bound = 0.0, hi_bound = a * 5.0;
-        double cap = INFINITY;  // smallest step whose trial point was invalid
-        for (;;) {
-            a = std::min(std::max(a, amin), amax);
-            if (a >= cap) a = lo_.a + 0.5 * (cap - lo_.a);
-            bool last_chance = nfev >= maxfev - 1;
-            if ((brack_ && (a <= lo_bound || a >= hi_bound)) || last_chance ||
-                (brack_ && hi_bound - lo_bound <= xtol * hi_bound))
-                a = lo_.a;
-            int cb = phi(a, f, d);
-            ++nfev;
-            if (cb < 0) return -1;
-            if (cb > 0) {
-                f = INFINITY;
-                if (nfev >= maxfev) return 3;
-                cap = a;
-                a = lo_.a + 0.5 * (a - lo_.a);
-                continue;
-            }
-            const double armijo = f0 + a * slope;
-            int info = 0;
-            if (brack_ && (a <= lo_bound || a >= hi_bound)) info = 6;
-            if (a == amax && f <= armijo && d <= slope) info = 5;
-            if (a == amin && (f > armijo || d >= slope)) info = 4;
-            if (nfev >= maxfev) info = 3;
-            if (brack_ && hi_bound - lo_bound <= xtol * hi_bound) info = 2;
-            if (f <= armijo && fabs(d) <= gtol * (-d0)) info = 1;
-            if (info) return info;
-            if (first_stage && f <= armijo && d >= std::min(ftol, gtol) * d0) first_stage = false;
-            double next;
-            if (first_stage && f <= lo_.f && f > armijo) {
-                // work on psi: shift values and slopes by the Armijo line
-                Pt l = {lo_.a, lo_.f - lo_.a * slope, lo_.d - slope};
-                Pt u = {hi_.a, hi_.f - hi_.a * slope, hi_.d - slope};
-                Pt t = {a, f - a * slope, d - slope};
-                std::swap(l, lo_);
-                std::swap(u, hi_);
-                next = update(t, lo_bound, hi_bound);
-                lo_ = {lo_.a, lo_.f + lo_.a * slope, lo_.d + slope};
-                hi_ = {hi_.a, hi_.f + hi_.a * slope, hi_.d + slope};
-            } else {
-                next = update({a, f, d}, lo_bound, hi_bound);
-            }
-            if (brack_) {
-                if (fabs(hi_.a - lo_.a) >= 0.66 * width_prev) next = lo_.a + 0.5 * (hi_.a - lo_.a);
-                width_prev = width;
-                width = fabs(hi_.a - lo_.a);
-                lo_bound = std::min(lo_.a, hi_.a);
-                hi_bound = std::max(lo_.a, hi_.a);
-            } else {
-                lo_bound = lo_.a;
-                hi_bound = next + 4.0 * (next - lo_.a);
-            }
-            a = next;
-        }
-    }
-
-  private:
-    struct Pt {
-        double a, f, d;
-    };
-    Pt lo_, hi_;  // best point so far and the other end of the interval
-    bool brack_ = false;
-
-    // minimiser of the cubic through (x, fx, dx) and (t, ft, dt), in the
-    // theta / gamma form; ok = false when it does not exist
-    static double cubic(const Pt &x, const Pt &t, bool &ok) {
-        double theta = 3.0 * (x.f - t.f) / (t.a - x.a) + x.d + t.d;
-        double sc = std::max(fabs(theta), std::max(fabs(x.d), fabs(t.d)));
-        double rad = (theta / sc) * (theta / sc) - (x.d / sc) * (t.d / sc);
-        ok = rad > 0.0;
-        double gamma = sc * sqrt(std::max(rad, 0.0));
-        if (t.a < x.a) gamma = -gamma;
-        double p = (gamma - x.d) + theta;
-        double q = ((gamma - x.d) + gamma) + t.d;
-        if (q == 0.0) {
-            ok = false;
-            return x.a;
-        }
-        return x.a + (p / q) * (t.a - x.a);
-    }
-
-    double update(Pt t, double lo_bound, double hi_bound) {
-        const Pt &x = lo_;
-        const double sx = (x.d > 0.0) - (x.d < 0.0);
-        const bool opposite = t.d * sx < 0.0;
-        bool ok;
-        double nxt;
-        if (t.f > x.f) {
-            double ac = cubic(x, t, ok);
-            double aq = x.a + (x.d / ((x.f - t.f) / (t.a - x.a) + x.d)) / 2.0 * (t.a - x.a);
-            nxt = (fabs(ac - x.a) < fabs(aq - x.a)) ? ac : ac + (aq - ac) / 2.0;
-            brack_ = true;
-        } else if (opposite) {
-            double ac = cubic(x, t, ok);
-            double as = t.a + t.d / (t.d - x.d) * (x.a - t.a);
-            nxt = (fabs(ac - t.a) > fabs(as - t.a)) ? ac : as;
-            brack_ = true;
-        } else if (fabs(t.d) < fabs(x.d)) {
-            double ac = cubic(x, t, ok);
-            bool beyond = ok && ((t.a > x.a) ? (ac > t.a) : (ac < t.a));
-            if (!beyond) ac = (t.a > x.a) ? hi_bound : lo_bound;
-            double as = t.a + t.d / (t.d - x.d) * (x.a - t.a);
-            if (brack_) {
-                nxt = (fabs(ac - t.a) < fabs(as - t.a)) ? ac : as;
-                nxt = (t.a > x.a) ? std::min(t.a + 0.66 * (hi_.a - t.a), nxt)
-                                  : std::max(t.a + 0.66 * (hi_.a - t.a), nxt);
-            } else {
-                nxt = (fabs(ac - t.a) > fabs(as - t.a)) ? ac : as;
-                nxt = std::min(hi_bound, std::max(lo_bound, nxt));
-            }
-        } else {
-            if (brack_) nxt = cubic(t, hi_, ok);
-            else nxt = (t.a > x.a) ? hi_bound : lo_bound;
-        }
-        if (t.f > x.f) {
-            hi_ = t;
-        } else {
-            if (opposite) hi_ = lo_;
-            lo_ = t;
-        }
-        return nxt;
-    }
-};
 
 // history bookkeeping
 void hist_reset(scvt_handle *H) {
@@ -446,7 +285,7 @@ void scvt_destroy(scvt_handle *H) {
     if (!H) return;
     Bufs &b = H->b;
     void *ptrs[] = {b.z, b.zt, b.g, b.gt, b.h, b.ht, b.fc, b.q, b.yv, b.nrm, b.mass, b.moment, b.stage_a, b.stage_b,
-                    b.partials, b.scal, b.rho, b.hist, b.zs, b.zf, b.zl, b.cvx, b.cnb, b.cdeg, b.eoff, b.ecell, b.escan, b.pval, b.pcnt, b.vo, b.bin_of, b.count, b.start, b.cursor, b.scan_tmp,
+                    b.partials, b.scal, b.rho, b.hist, b.zs, b.zf, b.zl, b.cvx, b.cnb, b.cdeg, b.eoff, b.ecell, b.escan, b.eacc, b.vo, b.bin_of, b.count, b.start, b.cursor, b.scan_tmp,
                     b.sidx, b.list1, b.list2, b.deg, b.radius, b.st};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -483,12 +322,12 @@ scvt_status scvt_create(const scvt_config *cfg, void *cuda_stream, scvt_handle *
     H->m = cfg->lbfgs_m;
     H->stream = (cudaStream_t)cuda_stream;
     memset(&H->stats, 0, sizeof(H->stats));
-    // ~2 generators per bin on average
-    int G = (int)ceil(sqrt((double)H->n / 12.0));
-    H->G = std::max(1, std::min(G, 4096));
+    // ~2 generators per bin on average; bins are allocated for the finest tuning (1 per bin)
+    H->G = bins_per_edge(H->n, H->tune.bin_load);
     const int n = H->n;
     const size_t n3 = 3 * (size_t)n;
-    const int nbins = 6 * H->G * H->G;
+    const int g1 = bins_per_edge(H->n, 1);
+    const int nbins = 6 * g1 * g1;
     Bufs &b = H->b;
     cudaError_t e = cudaSuccess;
 #define AL(ptr, cnt) \
@@ -500,7 +339,7 @@ scvt_status scvt_create(const scvt_config *cfg, void *cuda_stream, scvt_handle *
     AL(b.hist, (size_t)(H->m + 1) * 2 * n3);
     AL(b.zs, n); AL(b.zf, n); AL(b.zl, n); AL(b.cvx, (size_t)n * kCellSlots); AL(b.cnb, (size_t)n * kCellSlots);
     AL(b.cdeg, n); AL(b.eoff, n + 1); AL(b.ecell, 6 * (size_t)n); AL(b.escan, 2 * (n / 2048 + 64) + 64);
-    AL(b.pval, 10 * (size_t)n); AL(b.pcnt, n);
+    AL(b.eacc, 5 * 6 * (size_t)n);
     if (cfg->precision == 1) AL(b.vo, (size_t)n * kCellSlots);
     AL(b.bin_of, n); AL(b.count, nbins); AL(b.start, nbins + 1); AL(b.cursor, nbins);
     AL(b.scan_tmp, 2 * (nbins / 2048 + 64) + 64);
@@ -814,6 +653,23 @@ scvt_status scvt_lbfgs_solve(scvt_handle *H, double *z, const scvt_solve_opts *o
     rep.status = st;
     if (rep_out) *rep_out = rep;
     return st;
+}
+
+scvt_status scvt_set_tuning(scvt_handle *H, const scvt_tuning *t) {
+    if (!H) return SCVT_ERR_INVALID;
+    if (!t) return fail(H, SCVT_ERR_INVALID, "null argument");
+    Tune u;
+    scvt_status s = tune_from(*t, &u);
+    if (s) return fail(H, s, "tuning out of range");
+    H->tune = u;
+    H->G = bins_per_edge(H->n, u.bin_load);
+    return SCVT_OK;
+}
+
+scvt_status scvt_get_tuning(const scvt_handle *H, scvt_tuning *t) {
+    if (!H || !t) return SCVT_ERR_INVALID;
+    *t = tuning_of(H->tune);
+    return SCVT_OK;
 }
 
 scvt_status scvt_get_stats(const scvt_handle *H, scvt_stats *out) {

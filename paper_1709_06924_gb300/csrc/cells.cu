@@ -33,7 +33,6 @@ namespace scvt {
 namespace {
 
 constexpr double kBoxL = 1.0e3;         // half-width of the starting square (gnomonic)
-constexpr double kCertMargin = 1.0 + 1e-9;
 
 // Radon's 7-point degree-5 rule: centroid (weight 9/40) and the orbits
 // (a, a, 1 - 2a) with a = (6 -+ sqrt 15)/21, weights (155 -+ sqrt 15)/1200.
@@ -81,6 +80,23 @@ __device__ __forceinline__ V3 ld(const P4 *p) {
     return mk(v.x, v.y, v.z);
 }
 
+// The problem a position (or original index) belongs to, with its range,
+// bin resolution and bins; a single problem is problem 0 of itself.
+struct View {
+    int b, p0, n, G;
+    const int *bstart;
+};
+__device__ __forceinline__ View view_of(const Grid &g, int p) {
+    if (!g.inst) return View{0, 0, g.n, g.G, g.bstart};
+    const int b = g.pinst[p];
+    const InstGeom I = g.inst[b];
+    return View{b, I.p0, I.n, I.G, g.bstart + I.bin0};
+}
+__device__ __forceinline__ unsigned *flags_of(const Grid &g, DevStatus *st, int b) {
+    return g.ist ? &g.ist[b].flags : &st->flags;
+}
+__device__ __forceinline__ bool inactive(const Grid &g, int b) { return g.active && !g.active[b]; }
+
 __device__ __forceinline__ int bin_index(double x, double y, double z, int G) {
     double ax = fabs(x), ay = fabs(y), az = fabs(z);
     int a;
@@ -99,19 +115,21 @@ __device__ __forceinline__ int bin_index(double x, double y, double z, int G) {
 }
 
 // ---------------------------------------------------------------- binning
-__global__ void k_bin_count(const double *__restrict__ z, int n, int G, int *__restrict__ bin_of,
+__global__ void k_bin_count(const double *__restrict__ z, Grid g, int *__restrict__ bin_of,
                             int *__restrict__ count, DevStatus *st) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    if (i >= g.n) return;
+    const View v = view_of(g, i);
+    const int base = (int)(v.bstart - g.bstart);
     double x = z[3 * (size_t)i], y = z[3 * (size_t)i + 1], w = z[3 * (size_t)i + 2];
     double r2 = x * x + y * y + w * w;
     if (!(fabs(r2 - 1.0) <= 2e-12)) {  // also catches NaN / inf
-        atomicOr(&st->flags, FLAG_BAD_POINT);
-        bin_of[i] = 0;
-        atomicAdd(&count[0], 1);
+        atomicOr(flags_of(g, st, v.b), FLAG_BAD_POINT);
+        bin_of[i] = base;
+        atomicAdd(&count[base], 1);
         return;
     }
-    int b = bin_index(x, y, w, G);
+    int b = base + bin_index(x, y, w, v.G);
     bin_of[i] = b;
     atomicAdd(&count[b], 1);
 }
@@ -268,8 +286,8 @@ __device__ __forceinline__ void check_duplicate(const Grid &g, V3 q, int p, unsi
 // at most S.  The FP32 roots are widened by 4e-6/A + 1e-6 (their error is
 // below 4e-7/A).
 template <int K>
-__device__ void cap_query(const Grid &g, V3 q, float4 qf, int self, float S, float r2acc, KnnList<K> &L,
-                          unsigned *flags) {
+__device__ void cap_query(const Grid &g, const View &v, V3 q, float4 qf, int self, float S, float r2acc,
+                          KnnList<K> &L, unsigned *flags) {
     const float S2 = S * S;
     const float qv[3] = {qf.x, qf.y, qf.z};
     for (int a = 0; a < 3; ++a) {
@@ -291,13 +309,13 @@ __device__ void cap_query(const Grid &g, V3 q, float4 qf, int self, float S, flo
             if (s0 > 1.0f || s1 < -1.0f) { empty = true; break; }
             s0 = fmaxf(s0, -1.0f);
             s1 = fminf(s1, 1.0f);
-            lo[r] = min(max((int)floorf((s0 + 1.0f) * 0.5f * g.G), 0), g.G - 1);
-            hi[r] = min(max((int)floorf((s1 + 1.0f) * 0.5f * g.G), 0), g.G - 1);
+            lo[r] = min(max((int)floorf((s0 + 1.0f) * 0.5f * v.G), 0), v.G - 1);
+            hi[r] = min(max((int)floorf((s1 + 1.0f) * 0.5f * v.G), 0), v.G - 1);
         }
         if (empty) continue;
         for (int iv = lo[1]; iv <= hi[1]; ++iv) {
-            int row = (face * g.G + iv) * g.G;
-            int p0 = g.bstart[row + lo[0]], p1 = g.bstart[row + hi[0] + 1];
+            int row = (face * v.G + iv) * v.G;
+            int p0 = v.bstart[row + lo[0]], p1 = v.bstart[row + hi[0] + 1];
             for (int p = p0; p < p1; ++p) {
                 if (p == self) continue;
                 float4 c = ldf(g.zf + p);
@@ -311,8 +329,8 @@ __device__ void cap_query(const Grid &g, V3 q, float4 qf, int self, float S, flo
 }
 
 template <int K>
-__device__ void all_query(const Grid &g, V3 q, float4 qf, int self, KnnList<K> &L, unsigned *flags) {
-    for (int p = 0; p < g.n; ++p) {
+__device__ void all_query(const Grid &g, const View &v, V3 q, float4 qf, int self, KnnList<K> &L, unsigned *flags) {
+    for (int p = v.p0; p < v.p0 + v.n; ++p) {
         if (p == self) continue;
         float4 c = ldf(g.zf + p);
         float dx = c.x - qf.x, dy = c.y - qf.y, dz = c.z - qf.z;
@@ -545,9 +563,9 @@ __device__ __forceinline__ void tri(const Density &r, double inv_alpha, V3 A, V3
     }
 }
 
-__device__ __forceinline__ void write_cell(const CellOut &out, int i, V3 zi, const Acc &acc, DevStatus *st) {
+__device__ __forceinline__ void write_cell(const CellOut &out, int i, V3 zi, const Acc &acc, unsigned *flags) {
     const double cz = acc.cx * zi.x + acc.cy * zi.y + acc.cz * zi.z;
-    if (!(cz > 0.0)) atomicOr(&st->flags, FLAG_NONPOSITIVE);
+    if (!(cz > 0.0)) atomicOr(flags, FLAG_NONPOSITIVE);
     if (out.grad) {
         out.grad[3 * (size_t)i] = 2.0 * cz * zi.x - 2.0 * acc.cx;
         out.grad[3 * (size_t)i + 1] = 2.0 * cz * zi.y - 2.0 * acc.cy;
@@ -575,24 +593,31 @@ __device__ __forceinline__ bool lex_less(V3 a, V3 b) {
 // more than kCellSlots edges are integrated here, in-thread.  EXTRA > 0 only
 // in the last pass, which may clip by every generator.
 template <int K, int VMAX, int EXTRA>
-__global__ void __launch_bounds__(128) k_topo(Grid g, Density rho, CellOut out, CellBuf cb,
+__global__ void __launch_bounds__(128) k_topo(Grid g, CellOut out, CellBuf cb,
                                               const int *__restrict__ list, const unsigned *__restrict__ list_count,
                                               int *__restrict__ next_list, unsigned *__restrict__ next_count,
-                                              int last_pass, int scan_all, DevStatus *st) {
+                                              int last_pass, int scan_all_max, DevStatus *st) {
     int nwork = list ? (int)*list_count : g.n;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nwork; t += gridDim.x * blockDim.x) {
         const int p = list ? list[t] : t;
+        const View v = view_of(g, p);
+        if (!list && inactive(g, v.b)) {
+            cb.deg[p] = 0;
+            continue;
+        }
+        unsigned *flags = flags_of(g, st, v.b);
         const V3 zi = ld(g.zs + p);
         const float4 zif = ldf(g.zf + p);
         const int i = g.sidx[p];
+        const bool scan_all = v.n <= scan_all_max;
 
         // ---- neighbours (FP32): list of up to K, bound D2 on everything else
         KnnList<K> L;
         L.cnt = 0;
         float D2;
-        if (scan_all || g.n - 1 <= K) {
-            all_query<K>(g, zi, zif, p, L, &st->flags);
-            D2 = (L.cnt == g.n - 1) ? INFINITY : lower32(L.d[K - 1]);
+        if (scan_all || v.n - 1 <= K) {
+            all_query<K>(g, v, zi, zif, p, L, flags);
+            D2 = (L.cnt == v.n - 1) ? INFINITY : lower32(L.d[K - 1]);
         } else {
             // caps are chord balls |x - z_i| <= r; sin(theta) = r sqrt(1 - r^2/4)
             const float rmax = 0.2829f;  // sin(theta) <= 0.28 keeps caps off the far faces
@@ -602,12 +627,12 @@ __global__ void __launch_bounds__(128) k_topo(Grid g, Density rho, CellOut out, 
                 r = 1.1f * hint;
             } else {
                 // local density from the own bin: lambda = count / solid angle
-                int b = bin_index(zi.x, zi.y, zi.z, g.G);
-                int cbn = g.bstart[b + 1] - g.bstart[b];
+                int b = bin_index(zi.x, zi.y, zi.z, v.G);
+                int cbn = v.bstart[b + 1] - v.bstart[b];
                 float ax = fabsf(zif.x), ay = fabsf(zif.y), az = fabsf(zif.z);
                 float am = fmaxf(ax, fmaxf(ay, az));
                 float s2 = (ax * ax + ay * ay + az * az) / (am * am);  // 1 + s^2 + t^2
-                float omega = (4.0f / ((float)g.G * g.G)) / (s2 * sqrtf(s2));
+                float omega = (4.0f / ((float)v.G * v.G)) / (s2 * sqrtf(s2));
                 float lam = fmaxf((float)cbn, 1.0f) / omega;
                 r = sqrtf(1.5f * K / (3.14159265f * lam));
                 if (last_pass) r *= 2.0f;
@@ -620,7 +645,7 @@ __global__ void __launch_bounds__(128) k_topo(Grid g, Density rho, CellOut out, 
                 r2lo = r * r * (1.0f - 1e-6f);
                 r2acc = r * r * 1.001f + 1e-12f;
                 L.cnt = 0;
-                cap_query<K>(g, zi, zif, p, S, r2acc, L, &st->flags);
+                cap_query<K>(g, v, zi, zif, p, S, r2acc, L, flags);
                 if (L.cnt == K || r >= rmax || attempt > 8) break;
                 float grow = (L.cnt > 0) ? sqrtf(1.3f * K / (float)L.cnt) : 2.0f;
                 r = fminf(r * fmaxf(grow, 1.25f), rmax);
@@ -671,7 +696,7 @@ __global__ void __launch_bounds__(128) k_topo(Grid g, Density rho, CellOut out, 
             const float bound = fminf(lower32(L.d[k]), D2);
             if (bound > 4.0f * R2 * (1.0f + 1e-6f)) { early = true; break; }
             P.set_line(F, k, L.j[k]);
-            int rc = clip<K, VMAX, EXTRA>(P, F, k, &st->flags, &st->ambiguous);
+            int rc = clip<K, VMAX, EXTRA>(P, F, k, flags, &st->ambiguous);
             if (rc < 0) { ok = false; break; }
             if (rc > 0) R2 = poly_R2(P, F);
         }
@@ -682,7 +707,7 @@ __global__ void __launch_bounds__(128) k_topo(Grid g, Density rho, CellOut out, 
             // last resort: clip by every generator (the exact cell); points
             // that cannot reach the polygon are skipped.  A new line goes to
             // an extra slot that no current edge uses.
-            for (int q = 0; q < g.n && ok; ++q) {
+            for (int q = v.p0; q < v.p0 + v.n && ok; ++q) {
                 if (q == p) continue;
                 const V3 d = sub(ld(g.zs + q), zi);
                 if (dot(d, d) > 4.0 * (double)R2 * (1.0 + 1e-6)) continue;
@@ -694,18 +719,18 @@ __global__ void __launch_bounds__(128) k_topo(Grid g, Density rho, CellOut out, 
                 const int l = K + 4 + x;
                 P.jx[x] = q;
                 P.set_line(F, l, q);
-                int rc = clip<K, VMAX, EXTRA>(P, F, l, &st->flags, &st->ambiguous);
+                int rc = clip<K, VMAX, EXTRA>(P, F, l, flags, &st->ambiguous);
                 if (rc < 0) { ok = false; break; }
                 if (rc > 0) R2 = poly_R2(P, F);
             }
             boxed = false;
             for (int v = 0; v < P.nv; ++v) boxed |= (P.ln[P.cur][v] >= K && P.ln[P.cur][v] < K + 4);
-            if (ok && boxed) atomicOr(&st->flags, FLAG_UNBOUNDED);
+            if (ok && boxed) atomicOr(flags, FLAG_UNBOUNDED);
             certified = ok && !boxed;
         }
         if (!certified) {
             if (last_pass) {
-                atomicOr(&st->flags, ok ? FLAG_EXHAUSTED : FLAG_VMAX);
+                atomicOr(flags, ok ? FLAG_EXHAUSTED : FLAG_VMAX);
             } else {
                 unsigned pos = atomicAdd(next_count, 1u);
                 next_list[pos] = p;
@@ -740,6 +765,7 @@ __global__ void __launch_bounds__(128) k_topo(Grid g, Density rho, CellOut out, 
         } else {
             // large cell: integrate here, edges in the canonical order
             cb.deg[p] = 0;
+            const Density rho = g.rho ? g.rho[v.b] : g.rho0;
             const double inv_alpha = 1.0 / rho.alpha;
             Acc acc = {0, 0, 0, 0, 0};
             V3 corners_first, va;
@@ -761,7 +787,7 @@ __global__ void __launch_bounds__(128) k_topo(Grid g, Density rho, CellOut out, 
                 }
                 va = vb;
             }
-            write_cell(out, i, zi, acc, st);
+            write_cell(out, i, zi, acc, flags);
         }
     }
 }
@@ -870,10 +896,14 @@ __device__ __forceinline__ int gather(const Grid &g, int p, float4 hp, float4 lp
     return cnt;
 }
 
-__global__ void __launch_bounds__(128) k_topo_warp(Grid g, CellOut out, CellBuf cb, int *__restrict__ next_list,
-                                                   unsigned *__restrict__ next_count, DevStatus *st) {
-    __shared__ float s_d2[4][kWarpCand];
-    __shared__ int s_j[4][kWarpCand];
+// WPB warps per block; knn_target: the number of candidates the first radius
+// aims at when the cell has no radius hint from a previous evaluation
+template <int WPB>
+__global__ void __launch_bounds__(WPB * 32) k_topo_warp(Grid g, CellOut out, CellBuf cb, int *__restrict__ next_list,
+                                                        unsigned *__restrict__ next_count, DevStatus *st,
+                                                        float knn_target) {
+    __shared__ float s_d2[WPB][kWarpCand];
+    __shared__ int s_j[WPB][kWarpCand];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     float *cd = s_d2[wib];
     int *cj = s_j[wib];
@@ -881,6 +911,12 @@ __global__ void __launch_bounds__(128) k_topo_warp(Grid g, CellOut out, CellBuf 
     const int nw = (gridDim.x * blockDim.x) >> 5;
     const float INF = __int_as_float(0x7f800000);
     for (int p = gw; p < g.n; p += nw) {
+        const View v = view_of(g, p);
+        if (inactive(g, v.b)) {
+            if (lane == 0) cb.deg[p] = 0;
+            continue;
+        }
+        unsigned *flags = flags_of(g, st, v.b);
         const float4 hp = g.zf[p], lp = g.zl[p];
         const int i = g.sidx[p];
         // FP32 frame (any orthonormal frame gives the same vertex directions)
@@ -894,7 +930,7 @@ __global__ void __launch_bounds__(128) k_topo_warp(Grid g, CellOut out, CellBuf 
             e1 = make_float3(c.x * inv, c.y * inv, c.z * inv);
             e2 = make_float3(hp.y * e1.z - hp.z * e1.y, hp.z * e1.x - hp.x * e1.z, hp.x * e1.y - hp.y * e1.x);
         }
-        const bool all_mode = g.n - 1 <= kWarpCand;
+        const bool all_mode = v.n - 1 <= kWarpCand;
         const float rmax = 0.2829f;  // sin(theta) <= 0.28 keeps caps off the far faces
         float r;
         {
@@ -902,13 +938,13 @@ __global__ void __launch_bounds__(128) k_topo_warp(Grid g, CellOut out, CellBuf 
             if (hint > 0.0f) {
                 r = hint;
             } else {
-                const int b = bin_index((double)hp.x, (double)hp.y, (double)hp.z, g.G);
-                const int cbn = g.bstart[b + 1] - g.bstart[b];
+                const int b = bin_index((double)hp.x, (double)hp.y, (double)hp.z, v.G);
+                const int cbn = v.bstart[b + 1] - v.bstart[b];
                 const float ax = fabsf(hp.x), ay = fabsf(hp.y), az = fabsf(hp.z);
                 const float am = fmaxf(ax, fmaxf(ay, az));
                 const float s2 = (ax * ax + ay * ay + az * az) / (am * am);
-                const float omega = (4.0f / ((float)g.G * g.G)) / (s2 * sqrtf(s2));
-                r = sqrtf(24.0f * omega / (3.14159265f * fmaxf((float)cbn, 1.0f)));
+                const float omega = (4.0f / ((float)v.G * v.G)) / (s2 * sqrtf(s2));
+                r = sqrtf(knn_target * omega / (3.14159265f * fmaxf((float)cbn, 1.0f)));
             }
             r = fminf(r, rmax);
         }
@@ -926,7 +962,7 @@ __global__ void __launch_bounds__(128) k_topo_warp(Grid g, CellOut out, CellBuf 
             const float D2 = all_mode ? INF : r * r * (1.0f - 1e-6f);
             int cnt = 0;
             if (all_mode) {
-                cnt = gather(g, p, hp, lp, 0, g.n, r2acc, cnt, cd, cj, lane, &st->flags);
+                cnt = gather(g, p, hp, lp, v.p0, v.p0 + v.n, r2acc, cnt, cd, cj, lane, flags);
             } else {
                 const float S2 = S * S;
                 const float qv[3] = {hp.x, hp.y, hp.z};
@@ -948,14 +984,14 @@ __global__ void __launch_bounds__(128) k_topo_warp(Grid g, CellOut out, CellBuf 
                         if (s0 > 1.0f || s1 < -1.0f) { empty = true; break; }
                         s0 = fmaxf(s0, -1.0f);
                         s1 = fminf(s1, 1.0f);
-                        lo[rr] = min(max((int)floorf((s0 + 1.0f) * 0.5f * g.G), 0), g.G - 1);
-                        hi[rr] = min(max((int)floorf((s1 + 1.0f) * 0.5f * g.G), 0), g.G - 1);
+                        lo[rr] = min(max((int)floorf((s0 + 1.0f) * 0.5f * v.G), 0), v.G - 1);
+                        hi[rr] = min(max((int)floorf((s1 + 1.0f) * 0.5f * v.G), 0), v.G - 1);
                     }
                     if (empty) continue;
                     for (int iv = lo[1]; iv <= hi[1]; ++iv) {
-                        const int row = (face * g.G + iv) * g.G;
-                        cnt = gather(g, p, hp, lp, g.bstart[row + lo[0]], g.bstart[row + hi[0] + 1], r2acc, cnt, cd,
-                                     cj, lane, &st->flags);
+                        const int row = (face * v.G + iv) * v.G;
+                        cnt = gather(g, p, hp, lp, v.bstart[row + lo[0]], v.bstart[row + hi[0] + 1], r2acc, cnt, cd,
+                                     cj, lane, flags);
                     }
                 }
             }
@@ -1061,13 +1097,13 @@ __global__ void __launch_bounds__(128) k_topo_warp(Grid g, CellOut out, CellBuf 
                 if (m == 0u) continue;
                 const unsigned full = (nv == 32) ? kFull : ((1u << nv) - 1u);
                 if (m == full) {
-                    if (lane == 0) atomicOr(&st->flags, FLAG_EMPTY);
+                    if (lane == 0) atomicOr(flags, FLAG_EMPTY);
                     ok = false;
                     break;
                 }
                 const unsigned rot = ((m << 1) | (m >> (nv - 1))) & full;  // bit k = bit k-1 of m
                 const unsigned starts = m & ~rot;
-                if (__popc(starts) > 1 && lane == 0) atomicOr(&st->flags, FLAG_NONCONVEX);
+                if (__popc(starts) > 1 && lane == 0) atomicOr(flags, FLAG_NONCONVEX);
                 const int k0 = __ffs(starts) - 1;
                 const unsigned mr = (k0 == 0) ? m : (((m >> k0) | (m << (nv - k0))) & full);
                 const int runlen = __ffs(~mr) - 1;
@@ -1202,78 +1238,31 @@ __global__ void k_edge_cells(int n, const int *__restrict__ deg, const int *__re
 }
 
 // One thread per Voronoi edge (two signed sub-triangles of Sec. 3.2.2, 14
-// rule points).  The warp sums each cell's edges with a fixed segmented
-// suffix reduction; a cell whose edges straddle two warps is finished by the
-// second of its two parts to arrive, which adds them in a fixed order (the
-// part holding the cell's first edge + the other part), so results do not
-// depend on timing.
-__global__ void __launch_bounds__(256) k_quad(Grid g, Density rho, CellOut out, CellBuf cb, const int *eoff,
-                                              const int *ecell, double *__restrict__ parts_val,
-                                              int *__restrict__ parts_cnt, DevStatus *st) {
-    const int nedges = eoff[g.n];
-    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const int lane = threadIdx.x & 31;
-    const long long wbase = e - lane;
-    int p = -1;
+// rule points, summed in order).  The edge's five sums go to the edge list;
+// k_cell_sum adds a cell's edges in edge order, so a cell's result depends
+// on its own edges only (not on where they fall in the launch).
+__global__ void __launch_bounds__(512) k_quad(Grid g, CellBuf cb, int ecap) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= cb.eoff[g.n]) return;
+    const int p = cb.ecell[e];
+    const int k = e - cb.eoff[p];
+    const int deg = cb.deg[p];
+    const V3 zi = ld(g.zs + p);
+    const P4 *vx = cb.vx + (size_t)p * kCellSlots;
+    const V3 va = ld(vx + k);
+    const V3 vb = ld(vx + ((k + 1 == deg) ? 0 : k + 1));
+    const V3 mu = unit(add(zi, ld(g.zs + cb.nb[(size_t)p * kCellSlots + k])));
+    const Density rho = g.rho ? g.rho[view_of(g, p).b] : g.rho0;
+    const double inv_alpha = 1.0 / rho.alpha;
     Acc acc = {0, 0, 0, 0, 0};
-    V3 zi = mk(0, 0, 0);
-    int e0 = 0, deg = 0;
-    if (e < nedges) {
-        p = ecell[e];
-        e0 = eoff[p];
-        deg = cb.deg[p];
-        const int k = (int)(e - e0);
-        zi = ld(g.zs + p);
-        const P4 *vx = cb.vx + (size_t)p * kCellSlots;
-        const V3 va = ld(vx + k);
-        const V3 vb = ld(vx + ((k + 1 == deg) ? 0 : k + 1));
-        const V3 mu = unit(add(zi, ld(g.zs + cb.nb[(size_t)p * kCellSlots + k])));
-        const double inv_alpha = 1.0 / rho.alpha;
-        tri(rho, inv_alpha, zi, va, mu, acc);
-        tri(rho, inv_alpha, zi, mu, vb, acc);
-    }
-    // segmented suffix sums: lane l ends with the sum of its segment from l on
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int po = __shfl_down_sync(0xffffffffu, p, o);
-        const double m = __shfl_down_sync(0xffffffffu, acc.m, o);
-        const double cx = __shfl_down_sync(0xffffffffu, acc.cx, o);
-        const double cy = __shfl_down_sync(0xffffffffu, acc.cy, o);
-        const double cz = __shfl_down_sync(0xffffffffu, acc.cz, o);
-        const double ee = __shfl_down_sync(0xffffffffu, acc.e, o);
-        if (lane + o < 32 && po == p) {
-            acc.m += m;
-            acc.cx += cx;
-            acc.cy += cy;
-            acc.cz += cz;
-            acc.e += ee;
-        }
-    }
-    const int pprev = __shfl_up_sync(0xffffffffu, p, 1);
-    const bool head = (p >= 0) && (lane == 0 || pprev != p);
-    if (!head) return;
-    const bool starts_here = e0 >= wbase;
-    const bool ends_here = e0 + deg <= wbase + 32;
-    if (starts_here && ends_here) {
-        write_cell(out, g.sidx[p], zi, acc, st);
-        return;
-    }
-    // split cell: publish this part, then the second arrival finishes
-    double *slot = parts_val + (size_t)p * 10 + (starts_here ? 0 : 5);
-    slot[0] = acc.m; slot[1] = acc.cx; slot[2] = acc.cy; slot[3] = acc.cz; slot[4] = acc.e;
-    __threadfence();
-    if (atomicAdd(&parts_cnt[p], 1) == 1) {
-        __threadfence();
-        const volatile double *a = parts_val + (size_t)p * 10;
-        Acc tot;
-        tot.m = a[0] + a[5];
-        tot.cx = a[1] + a[6];
-        tot.cy = a[2] + a[7];
-        tot.cz = a[3] + a[8];
-        tot.e = a[4] + a[9];
-        parts_cnt[p] = 0;  // ready for the next evaluation
-        write_cell(out, g.sidx[p], zi, tot, st);
-    }
+    tri(rho, inv_alpha, zi, va, mu, acc);
+    tri(rho, inv_alpha, zi, mu, vb, acc);
+    double *ea = cb.eacc;
+    ea[e] = acc.m;
+    ea[(size_t)ecap + e] = acc.cx;
+    ea[2 * (size_t)ecap + e] = acc.cy;
+    ea[3 * (size_t)ecap + e] = acc.cz;
+    ea[4 * (size_t)ecap + e] = acc.e;
 }
 
 // ------------------------------------------------ mixed precision (FP32)
@@ -1350,11 +1339,6 @@ __global__ void __launch_bounds__(256) k_corners32(Grid g, CellBuf cb) {
     cb.vo[(size_t)p * kCellSlots + k] = make_float4(o.x, o.y, o.z, 0.0f);
 }
 
-struct DensityF {
-    int kind;
-    float gamma, beta, inv_alpha, xc0, xc1, xc2;
-};
-
 struct AccF {
     float m, ox, oy, oz, e;
 };
@@ -1397,11 +1381,11 @@ __device__ __forceinline__ void tri32(const DensityF &r, float4 z, float3 oa, fl
     }
 }
 
-__device__ __forceinline__ void write_cell_offsets(const CellOut &out, int i, V3 zi, const Acc &a, DevStatus *st) {
+__device__ __forceinline__ void write_cell_offsets(const CellOut &out, int i, V3 zi, const Acc &a, unsigned *flags) {
     // a.cx, a.cy, a.cz hold o = sum w rho (p - z_i)
     const double oz = a.cx * zi.x + a.cy * zi.y + a.cz * zi.z;
     const double cz = a.m + oz;  // c.z_i with |z_i| = 1
-    if (!(cz > 0.0)) atomicOr(&st->flags, FLAG_NONPOSITIVE);
+    if (!(cz > 0.0)) atomicOr(flags, FLAG_NONPOSITIVE);
     if (out.grad) {
         out.grad[3 * (size_t)i] = -2.0 * (a.cx - oz * zi.x);
         out.grad[3 * (size_t)i + 1] = -2.0 * (a.cy - oz * zi.y);
@@ -1417,90 +1401,82 @@ __device__ __forceinline__ void write_cell_offsets(const CellOut &out, int i, V3
     if (out.fcell) out.fcell[i] = a.e;
 }
 
-// one thread per edge; FP32 sub-triangles, FP64 sums (same reduction and
-// split-cell protocol as k_quad)
-__global__ void __launch_bounds__(256) k_quad32(Grid g, DensityF rho, CellOut out, CellBuf cb,
-                                                double *__restrict__ parts_val, int *__restrict__ parts_cnt,
-                                                DevStatus *st) {
-    const int nedges = cb.eoff[g.n];
-    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const int lane = threadIdx.x & 31;
-    const long long wbase = e - lane;
-    int p = -1, e0 = 0, deg = 0;
+// one thread per edge; the 14 rule points of the edge's two sub-triangles
+// summed in FP32, the edge's five sums stored in FP32 (edges and cells are
+// summed in FP64 by k_cell_sum)
+__global__ void __launch_bounds__(512) k_quad32(Grid g, CellBuf cb, int ecap) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= cb.eoff[g.n]) return;
+    const int p = cb.ecell[e];
+    const int k = e - cb.eoff[p];
+    const int deg = cb.deg[p];
+    const float4 hp = g.zf[p], lp = g.zl[p];
+    const float4 va = cb.vo[(size_t)p * kCellSlots + k];
+    const float4 vb = cb.vo[(size_t)p * kCellSlots + ((k + 1 == deg) ? 0 : k + 1)];
+    // edge midpoint normalize(z_i + z_j) as an offset: d/s + z |d|^2 / (s (2 + s)), s = sqrt(4 - |d|^2)
+    const float3 d = dfdiff(g, cb.nb[(size_t)p * kCellSlots + k], hp, lp);
+    const float dd = fmaf(d.x, d.x, fmaf(d.y, d.y, d.z * d.z));
+    const float sq = sqrtf(4.0f - dd), is = 1.0f / sq, t = dd / (sq * (2.0f + sq));
+    const float3 om = make_float3(d.x * is + hp.x * t, d.y * is + hp.y * t, d.z * is + hp.z * t);
+    const DensityF rf = g.rhof ? g.rhof[view_of(g, p).b] : g.rho0f;
+    AccF a = {0, 0, 0, 0, 0};
+    tri32(rf, hp, make_float3(va.x, va.y, va.z), om, a);
+    tri32(rf, hp, om, make_float3(vb.x, vb.y, vb.z), a);
+    float *ea = (float *)cb.eacc;
+    ea[e] = a.m;
+    ea[(size_t)ecap + e] = a.ox;
+    ea[2 * (size_t)ecap + e] = a.oy;
+    ea[3 * (size_t)ecap + e] = a.oz;
+    ea[4 * (size_t)ecap + e] = a.e;
+}
+
+// thread per cell: the cell's edge sums added in edge order (FP64), then the
+// cell's outputs (g_i, h_i, m_i, c_i, F_i at the original index)
+template <bool MIXED>
+__global__ void __launch_bounds__(256) k_cell_sum(Grid g, CellOut out, CellBuf cb, int ecap, DevStatus *st) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= g.n) return;
+    const int deg = cb.deg[p];
+    if (deg == 0) return;  // integrated by the topology kernel, failed, or inactive
+    const int e0 = cb.eoff[p];
     Acc acc = {0, 0, 0, 0, 0};
-    if (e < nedges) {
-        p = cb.ecell[e];
-        e0 = cb.eoff[p];
-        deg = cb.deg[p];
-        const int k = (int)(e - e0);
-        const float4 hp = g.zf[p], lp = g.zl[p];
-        const float4 va = cb.vo[(size_t)p * kCellSlots + k];
-        const float4 vb = cb.vo[(size_t)p * kCellSlots + ((k + 1 == deg) ? 0 : k + 1)];
-        // edge midpoint normalize(z_i + z_j) as an offset: d/s + z |d|^2 / (s (2 + s)), s = sqrt(4 - |d|^2)
-        const float3 d = dfdiff(g, cb.nb[(size_t)p * kCellSlots + k], hp, lp);
-        const float dd = fmaf(d.x, d.x, fmaf(d.y, d.y, d.z * d.z));
-        const float sq = sqrtf(4.0f - dd), is = 1.0f / sq, t = dd / (sq * (2.0f + sq));
-        const float3 om = make_float3(d.x * is + hp.x * t, d.y * is + hp.y * t, d.z * is + hp.z * t);
-        AccF a1 = {0, 0, 0, 0, 0}, a2 = {0, 0, 0, 0, 0};
-        tri32(rho, hp, make_float3(va.x, va.y, va.z), om, a1);
-        tri32(rho, hp, om, make_float3(vb.x, vb.y, vb.z), a2);
-        acc.m = (double)a1.m + (double)a2.m;
-        acc.cx = (double)a1.ox + (double)a2.ox;
-        acc.cy = (double)a1.oy + (double)a2.oy;
-        acc.cz = (double)a1.oz + (double)a2.oz;
-        acc.e = (double)a1.e + (double)a2.e;
-    }
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int po = __shfl_down_sync(0xffffffffu, p, o);
-        const double m = __shfl_down_sync(0xffffffffu, acc.m, o);
-        const double cx = __shfl_down_sync(0xffffffffu, acc.cx, o);
-        const double cy = __shfl_down_sync(0xffffffffu, acc.cy, o);
-        const double cz = __shfl_down_sync(0xffffffffu, acc.cz, o);
-        const double ee = __shfl_down_sync(0xffffffffu, acc.e, o);
-        if (lane + o < 32 && po == p) {
-            acc.m += m;
-            acc.cx += cx;
-            acc.cy += cy;
-            acc.cz += cz;
-            acc.e += ee;
+    if (MIXED) {
+        const float *ea = (const float *)cb.eacc;
+        for (int k = 0; k < deg; ++k) {
+            const int e = e0 + k;
+            acc.m += (double)ea[e];
+            acc.cx += (double)ea[(size_t)ecap + e];
+            acc.cy += (double)ea[2 * (size_t)ecap + e];
+            acc.cz += (double)ea[3 * (size_t)ecap + e];
+            acc.e += (double)ea[4 * (size_t)ecap + e];
+        }
+    } else {
+        const double *ea = cb.eacc;
+        for (int k = 0; k < deg; ++k) {
+            const int e = e0 + k;
+            acc.m += ea[e];
+            acc.cx += ea[(size_t)ecap + e];
+            acc.cy += ea[2 * (size_t)ecap + e];
+            acc.cz += ea[3 * (size_t)ecap + e];
+            acc.e += ea[4 * (size_t)ecap + e];
         }
     }
-    const int pprev = __shfl_up_sync(0xffffffffu, p, 1);
-    const bool head = (p >= 0) && (lane == 0 || pprev != p);
-    if (!head) return;
     const V3 zi = ld(g.zs + p);
-    const bool starts_here = e0 >= wbase;
-    const bool ends_here = e0 + deg <= wbase + 32;
-    if (starts_here && ends_here) {
-        write_cell_offsets(out, g.sidx[p], zi, acc, st);
-        return;
-    }
-    double *slot = parts_val + (size_t)p * 10 + (starts_here ? 0 : 5);
-    slot[0] = acc.m; slot[1] = acc.cx; slot[2] = acc.cy; slot[3] = acc.cz; slot[4] = acc.e;
-    __threadfence();
-    if (atomicAdd(&parts_cnt[p], 1) == 1) {
-        __threadfence();
-        const volatile double *a = parts_val + (size_t)p * 10;
-        Acc tot;
-        tot.m = a[0] + a[5];
-        tot.cx = a[1] + a[6];
-        tot.cy = a[2] + a[7];
-        tot.cz = a[3] + a[8];
-        tot.e = a[4] + a[9];
-        parts_cnt[p] = 0;
-        write_cell_offsets(out, g.sidx[p], zi, tot, st);
-    }
+    unsigned *flags = flags_of(g, st, view_of(g, p).b);
+    if (MIXED) write_cell_offsets(out, g.sidx[p], zi, acc, flags);
+    else write_cell(out, g.sidx[p], zi, acc, flags);
 }
 
 }  // namespace
 
-void bin_points(const double *z, int n, int G, int *bin_of, int *count, int *start, int *cursor, int *scan_tmp,
+void bin_points(const double *z, const Grid &g, int *bin_of, int *count, int *start, int *cursor, int *scan_tmp,
                 P4 *zs, float4 *zf, float4 *zl, int *sidx, DevStatus *st, cudaStream_t s, int64_t *launches) {
-    const int nbins = 6 * G * G;
+    const int n = g.n, nbins = g.nbins;
+    Grid gb = g;
+    gb.bstart = start;
     cudaMemsetAsync(count, 0, sizeof(int) * nbins, s);
     int blocks = (n + 255) / 256;
-    k_bin_count<<<blocks, 256, 0, s>>>(z, n, G, bin_of, count, st);
+    k_bin_count<<<blocks, 256, 0, s>>>(z, gb, bin_of, count, st);
     exclusive_scan(count, start, nbins, scan_tmp, s, launches);
     k_set_total<<<1, 1, 0, s>>>(start, nbins, n);
     cudaMemcpyAsync(cursor, start, sizeof(int) * nbins, cudaMemcpyDeviceToDevice, s);
@@ -1514,48 +1490,100 @@ __global__ void k_set_total_from(int *arr, int n, const int *last_in) {
     arr[n] = arr[n - 1] + last_in[n - 1];
 }
 
-void cell_passes(const Grid &g, const Density &rho, const CellOut &out, const CellBuf &cb, int *list1, int *list2,
-                 DevStatus *st, int knn_k0, bool mixed, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1,
-                 int64_t *launches, int64_t *cell_launches) {
-    (void)knn_k0;
-    // first pass: a warp per cell, grid sized to fill the GPU (grid-stride over cells)
-    const int wblocks = (int)std::min<long long>((g.n + 3) / 4, 152LL * 16);
-    k_topo_warp<<<wblocks, 128, 0, s>>>(g, out, cb, list1, &st->retry_count[0], st);
+int bins_per_edge(int64_t n, int bin_load) {
+    const int G = (int)ceil(sqrt((double)n / (6.0 * (double)bin_load)));
+    return std::max(1, std::min(G, 4096));
+}
+
+scvt_status tune_from(const scvt_tuning &t, Tune *out) {
+    if (t.bin_load < 1 || t.bin_load > 16) return SCVT_ERR_INVALID;
+    if (t.knn_target < 8 || t.knn_target > 64) return SCVT_ERR_INVALID;
+    if (t.topo_warps != 2 && t.topo_warps != 4 && t.topo_warps != 8) return SCVT_ERR_INVALID;
+    if (t.topo_blocks_per_sm < 1 || t.topo_blocks_per_sm > 64) return SCVT_ERR_INVALID;
+    if (t.quad_block != 128 && t.quad_block != 256 && t.quad_block != 512) return SCVT_ERR_INVALID;
+    out->bin_load = t.bin_load;
+    out->knn_target = t.knn_target;
+    out->topo_warps = t.topo_warps;
+    out->topo_bpsm = t.topo_blocks_per_sm;
+    out->quad_block = t.quad_block;
+    return SCVT_OK;
+}
+
+scvt_tuning tuning_of(const Tune &u) {
+    scvt_tuning t;
+    t.bin_load = u.bin_load;
+    t.knn_target = u.knn_target;
+    t.topo_warps = u.topo_warps;
+    t.topo_blocks_per_sm = u.topo_bpsm;
+    t.quad_block = u.quad_block;
+    return t;
+}
+
+Density to_device_density(const scvt_density &r) {
+    Density d;
+    d.kind = r.kind;
+    d.gamma = r.gamma;
+    d.alpha = r.alpha;
+    d.beta = r.beta;
+    d.xc0 = r.xc[0];
+    d.xc1 = r.xc[1];
+    d.xc2 = r.xc[2];
+    return d;
+}
+
+DensityF to_density32(const Density &d) {
+    DensityF f;
+    f.kind = d.kind;
+    f.gamma = (float)d.gamma;
+    f.beta = (float)d.beta;
+    f.inv_alpha = (float)(1.0 / d.alpha);
+    f.xc0 = (float)d.xc0;
+    f.xc1 = (float)d.xc1;
+    f.xc2 = (float)d.xc2;
+    return f;
+}
+
+void cell_passes(const Grid &g, const CellOut &out, const CellBuf &cb, int *list1, int *list2, DevStatus *st,
+                 bool mixed, const Tune &t, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1, int64_t *launches,
+                 int64_t *cell_launches) {
+    // first pass: a warp per cell, grid capped at topo_bpsm blocks per SM (grid-stride over cells)
+    const int wpb = t.topo_warps;
+    const int wblocks = (int)std::min<long long>((g.n + wpb - 1) / wpb, 152LL * t.topo_bpsm);
+    const float kt = (float)t.knn_target;
+    if (wpb == 2) k_topo_warp<2><<<wblocks, 64, 0, s>>>(g, out, cb, list1, &st->retry_count[0], st, kt);
+    else if (wpb == 8) k_topo_warp<8><<<wblocks, 256, 0, s>>>(g, out, cb, list1, &st->retry_count[0], st, kt);
+    else k_topo_warp<4><<<wblocks, 128, 0, s>>>(g, out, cb, list1, &st->retry_count[0], st, kt);
     // retry passes (thread per cell): sized for the worst case, they read their work count on the device
     const int rblocks = 2 * 152;
-    k_topo<64, 64, 0><<<rblocks, 64, 0, s>>>(g, rho, out, cb, list1, &st->retry_count[0], list2,
-                                             &st->retry_count[1], 0, 0, st);
-    int scan_all = g.n <= 20000 ? 1 : 0;
-    k_topo<128, 64, 64><<<rblocks, 64, 0, s>>>(g, rho, out, cb, list2, &st->retry_count[1], nullptr,
-                                               &st->retry_count[2], 1, scan_all, st);
-    // edge list, FP64 corners, quadrature
+    k_topo<64, 64, 0><<<rblocks, 64, 0, s>>>(g, out, cb, list1, &st->retry_count[0], list2, &st->retry_count[1], 0,
+                                             0, st);
+    // the last pass scans every generator of problems up to 20,000 generators
+    k_topo<128, 64, 64><<<rblocks, 64, 0, s>>>(g, out, cb, list2, &st->retry_count[1], nullptr,
+                                               &st->retry_count[2], 1, 20000, st);
+    // edge list, corners, quadrature per edge, sums per cell
     exclusive_scan(cb.deg, cb.eoff, g.n, cb.scan_tmp, s, launches);
     k_set_total_from<<<1, 1, 0, s>>>(cb.eoff, g.n, cb.deg);
     k_edge_cells<<<(g.n + 255) / 256, 256, 0, s>>>(g.n, cb.deg, cb.eoff, cb.ecell);
     // Euler: a full tessellation has 6N - 12 edge sides; failed cells only lower the count
-    const long long max_edges = 6LL * g.n;
-    const unsigned eblocks = (unsigned)((max_edges + 255) / 256);
+    const int ecap = 6 * g.n;
+    const int qb = t.quad_block;
+    const unsigned eblocks = (unsigned)((ecap + qb - 1) / qb);
+    const unsigned cblocks = (unsigned)((g.n + 255) / 256);
     if (mixed) {
-        k_corners32<<<eblocks, 256, 0, s>>>(g, cb);
-        DensityF rf;
-        rf.kind = rho.kind;
-        rf.gamma = (float)rho.gamma;
-        rf.beta = (float)rho.beta;
-        rf.inv_alpha = (float)(1.0 / rho.alpha);
-        rf.xc0 = (float)rho.xc0;
-        rf.xc1 = (float)rho.xc1;
-        rf.xc2 = (float)rho.xc2;
+        k_corners32<<<(ecap + 255) / 256, 256, 0, s>>>(g, cb);
         if (ev0) cudaEventRecord(ev0, s);
-        k_quad32<<<eblocks, 256, 0, s>>>(g, rf, out, cb, cb.parts_val, cb.parts_cnt, st);
+        k_quad32<<<eblocks, qb, 0, s>>>(g, cb, ecap);
         if (ev1) cudaEventRecord(ev1, s);
+        k_cell_sum<true><<<cblocks, 256, 0, s>>>(g, out, cb, ecap, st);
     } else {
-        k_corners<<<eblocks, 256, 0, s>>>(g, cb);
+        k_corners<<<(ecap + 255) / 256, 256, 0, s>>>(g, cb);
         if (ev0) cudaEventRecord(ev0, s);
-        k_quad<<<eblocks, 256, 0, s>>>(g, rho, out, cb, cb.eoff, cb.ecell, cb.parts_val, cb.parts_cnt, st);
+        k_quad<<<eblocks, qb, 0, s>>>(g, cb, ecap);
         if (ev1) cudaEventRecord(ev1, s);
+        k_cell_sum<false><<<cblocks, 256, 0, s>>>(g, out, cb, ecap, st);
     }
-    (*launches) += 7;
-    (*cell_launches) += 4;
+    (*launches) += 8;
+    (*cell_launches) += 5;
 }
 
 }  // namespace scvt

@@ -186,6 +186,51 @@ __global__ void k_accept(int n, const double *__restrict__ zt, const double *__r
     block_sum_store<3>(v, partials + 4 * blockIdx.x);
 }
 
+// the same per problem: blockIdx.y = problem, blockIdx.x = chunk of that
+// problem (reduce_blocks(n_b) chunks, as for a single problem of size n_b)
+__global__ void k_reduce_eval_batch(const InstGeom *__restrict__ inst, const int *__restrict__ pbase,
+                                    const int *__restrict__ active, const double *__restrict__ fcell,
+                                    const double *__restrict__ g, const double *__restrict__ q,
+                                    const double *__restrict__ nrm, double *__restrict__ partials) {
+    const int b = blockIdx.y;
+    if (active && !active[b]) return;
+    const InstGeom I = inst[b];
+    int64_t nb = (I.n + 4095) / 4096;
+    nb = nb < 1 ? 1 : (nb > 1024 ? 1024 : nb);
+    if (blockIdx.x >= nb) return;
+    const int64_t chunk = (I.n + nb - 1) / nb;
+    const int64_t b0 = (int64_t)blockIdx.x * chunk, b1 = b0 + chunk < I.n ? b0 + chunk : I.n;
+    double v[3] = {0.0, 0.0, 0.0};
+    for (int64_t j = b0 + threadIdx.x; j < b1; j += kRT) {
+        const int64_t i = I.p0 + j;
+        double gx = g[3 * i], gy = g[3 * i + 1], gz = g[3 * i + 2];
+        v[0] += fcell[i];
+        v[1] += gx * gx + gy * gy + gz * gz;
+        if (q) v[2] += (gx * q[3 * i] + gy * q[3 * i + 1] + gz * q[3 * i + 2]) / nrm[i];
+    }
+    block_sum_store<3>(v, partials + 4 * ((int64_t)pbase[b] + blockIdx.x));
+}
+
+// block b: ist[b].red[q] = sum of problem b's chunk sums, in chunk order
+__global__ void k_finish_batch(const InstGeom *__restrict__ inst, const int *__restrict__ pbase,
+                               const int *__restrict__ active, const double *__restrict__ partials,
+                               DevStatus *ist) {
+    const int b = blockIdx.x;
+    if (active && !active[b]) return;
+    int nb = (inst[b].n + 4095) / 4096;
+    nb = nb < 1 ? 1 : (nb > 1024 ? 1024 : nb);
+    const double *pp = partials + 4 * (int64_t)pbase[b];
+    double v[3] = {0.0, 0.0, 0.0};
+    for (int k = threadIdx.x; k < nb; k += kRT)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) v[q] += pp[4 * k + q];
+    double res[3];
+    block_sum_store<3>(v, res);
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) ist[b].red[q] = res[q];
+}
+
 __global__ void k_set_rho(double *rho, const DevStatus *st) { rho[0] = 1.0 / st->dots[0]; }
 
 __global__ void k_differs(int64_t len, const double *__restrict__ a, const double *__restrict__ b, unsigned *flag) {
@@ -209,6 +254,14 @@ void reduce_eval(int n, const double *fcell, const double *grad, const double *q
     int nb = reduce_blocks(n);
     k_reduce_eval<<<nb, kRT, 0, s>>>(n, fcell, grad, q, nrm, partials);
     k_finish<3><<<1, kRT, 0, s>>>(partials, nb, 4, st->red);
+    (*launches) += 2;
+}
+
+void reduce_eval_batch(int nprob, int max_nb, const InstGeom *inst, const int *pbase, const int *active,
+                       const double *fcell, const double *grad, const double *q, const double *nrm, double *partials,
+                       DevStatus *ist, cudaStream_t s, int64_t *launches) {
+    k_reduce_eval_batch<<<dim3(max_nb, nprob), kRT, 0, s>>>(inst, pbase, active, fcell, grad, q, nrm, partials);
+    k_finish_batch<<<nprob, kRT, 0, s>>>(inst, pbase, active, partials, ist);
     (*launches) += 2;
 }
 

@@ -37,22 +37,48 @@ struct DevStatus {
     unsigned differs;               // set by vec_differs
 };
 
-// Geometry of one evaluation (device pointers).
+struct Density {
+    int kind;
+    double gamma, alpha, beta;
+    double xc0, xc1, xc2;
+};
+
+// the density in FP32 for the mixed-precision quadrature (inv_alpha = 1/alpha)
+struct DensityF {
+    int kind;
+    float gamma, beta, inv_alpha, xc0, xc1, xc2;
+};
+
+// One problem of a batch: its generators occupy positions (and original
+// indices) [p0, p0 + n) of the concatenated arrays, its G x G x 6 bins start
+// at bin0 of the concatenated bin array.
+struct InstGeom {
+    int p0, n, G, bin0;
+};
+
+// Geometry of one evaluation (device pointers).  A single problem uses n, G,
+// bstart, rho0 and the caller's status block; a batch of problems sets inst
+// (with pinst: the problem of each position), per-problem densities and
+// per-problem status blocks, and may mark problems inactive (their cells are
+// skipped and their results left untouched).
 struct Grid {
-    int n;
-    int G;                  // bins per face edge
-    int nbins;              // 6 G^2
+    int n;                  // generators (all problems)
+    int G;                  // bins per face edge (single problem)
+    int nbins;              // bins (all problems)
     const P4 *zs;           // generators in bin order (w unused)
     const float4 *zf;       // the same, rounded to FP32 (hi part)
     const float4 *zl;       // FP32 remainder z - hi (lo part): hi + lo carries ~48 bits
     const int *sidx;        // bin-order position -> original index
     const int *bstart;      // nbins + 1 offsets into zs
-};
-
-struct Density {
-    int kind;
-    double gamma, alpha, beta;
-    double xc0, xc1, xc2;
+    Density rho0;           // density of a single problem
+    DensityF rho0f;
+    // batch of problems (all null for a single problem)
+    const InstGeom *inst;   // per problem
+    const int *pinst;       // problem of each position / original index
+    const Density *rho;     // per-problem densities
+    const DensityF *rhof;
+    DevStatus *ist;         // per-problem status (flags, sums)
+    const int *active;      // per-problem: evaluate (1) or skip (0); null = all
 };
 
 // Per-cell outputs, indexed by ORIGINAL generator index.  Any may be null.
@@ -79,29 +105,54 @@ struct CellBuf {
     int *eoff;         // n + 1: exclusive scan of deg (edge list offsets)
     int *ecell;        // 6n: cell of each edge
     int *scan_tmp;     // scratch of the scan over n (2 * (n / 2048 + 64) + 64 ints)
-    double *parts_val; // 10n: two partial sums per cell split across warps
-    int *parts_cnt;    // n: arrivals per split cell, zero between evaluations
+    double *eacc;      // 5 * 6n: per-edge sums (m, c or o, F), component-major; FP32 in the mixed form
     float4 *vo;        // n * kCellSlots corner offsets v - z_i in FP32 (mixed precision only)
 };
 
 // ---- binning (cells.cu) ----
-void bin_points(const double *z, int n, int G, int *bin_of, int *count, int *start, int *cursor,
-                int *scan_tmp, P4 *zs, float4 *zf, float4 *zl, int *sidx, DevStatus *st, cudaStream_t s,
-                int64_t *launches);
+// g supplies n, G / nbins and the batch fields (inst, pinst, ist); zs, zf,
+// zl, sidx and bstart (= start) are written here
+void bin_points(const double *z, const Grid &g, int *bin_of, int *count, int *start, int *cursor, int *scan_tmp,
+                P4 *zs, float4 *zf, float4 *zl, int *sidx, DevStatus *st, cudaStream_t s, int64_t *launches);
+
+// Launch shape and search parameters of an evaluation.  None of them changes
+// a result: the cell of a generator is unique, its corners are computed from
+// its neighbour triples and its sums are taken in its own edge order.
+struct Tune {
+    int bin_load = 2;      // target generators per bin: G = ceil(sqrt(n / (6 bin_load)))
+    int knn_target = 24;   // candidates aimed at by the first radius without a hint
+    int topo_warps = 4;    // warps per block of the topology pass (2, 4, 8)
+    int topo_bpsm = 16;    // grid cap of the topology pass, blocks per SM
+    int quad_block = 256;  // threads per block of the quadrature (128, 256, 512)
+};
+int bins_per_edge(int64_t n, int bin_load);
+// public tuning record <-> Tune (SCVT_ERR_INVALID when out of range)
+scvt_status tune_from(const scvt_tuning &t, Tune *out);
+scvt_tuning tuning_of(const Tune &t);
 
 // ---- cell passes (cells.cu) ----
 // topology pass 0 over all cells, passes 1..2 over the retry lists, then the
 // quadrature kernel over all cells (timed by ev0/ev1 when given).
 // mixed: corners and quadrature in FP32 local coordinates, FP64 accumulation
-void cell_passes(const Grid &g, const Density &rho, const CellOut &out, const CellBuf &cb, int *list1, int *list2,
-                 DevStatus *st, int knn_k0, bool mixed, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1,
-                 int64_t *launches, int64_t *cell_launches);
+void cell_passes(const Grid &g, const CellOut &out, const CellBuf &cb, int *list1, int *list2, DevStatus *st,
+                 bool mixed, const Tune &t, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1, int64_t *launches,
+                 int64_t *cell_launches);
+Density to_device_density(const scvt_density &r);
+DensityF to_density32(const Density &d);
 
 // ---- reductions and vector kernels (lbfgs.cu) ----
 int reduce_blocks(int64_t n);
 // red[0] = sum fcell, red[1] = sum |g|^2, red[2] = sum g_i.q_i / nrm_i (if q)
 void reduce_eval(int n, const double *fcell, const double *grad, const double *q, const double *nrm,
                  double *partials, DevStatus *st, cudaStream_t s, int64_t *launches);
+// the same per problem of a batch: problem b sums its own range with the
+// chunking a single problem of its size uses (reduce_blocks(n_b) chunks, the
+// chunk sums stored from partials + 4 * pbase[b]) into ist[b].red; inactive
+// problems are skipped.  max_nb = max_b reduce_blocks(n_b); inst, pbase and
+// active are device arrays.
+void reduce_eval_batch(int nprob, int max_nb, const InstGeom *inst, const int *pbase, const int *active,
+                       const double *fcell, const double *grad, const double *q, const double *nrm, double *partials,
+                       DevStatus *ist, cudaStream_t s, int64_t *launches);
 // out[slot] = sum x.y (deterministic), optionally scaled: out[slot] = scale[si] * sum
 void dot_to(int64_t len, const double *x, const double *y, double *partials, double *out, cudaStream_t s,
             int64_t *launches);

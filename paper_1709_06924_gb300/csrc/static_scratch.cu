@@ -21,6 +21,7 @@
 //     threads) race on it and must be serialised by the caller.
 #include <cuda_runtime.h>
 #include <math.h>
+#include <string.h>
 
 #include <mutex>
 
@@ -60,9 +61,8 @@ constexpr size_t oG = oH + up(sizeof(double) * kMaxN);
 constexpr size_t oEoff = oG + up(sizeof(double) * 3 * kMaxN);
 constexpr size_t oEcell = oEoff + up(sizeof(int) * (kMaxN + 1));
 constexpr size_t oEscan = oEcell + up(sizeof(int) * 6 * kMaxN);
-constexpr size_t oPval = oEscan + up(sizeof(int) * (2 * (kMaxN / 2048 + 64) + 64));
-constexpr size_t oPcnt = oPval + up(sizeof(double) * 10 * kMaxN);
-constexpr size_t kBytes = oPcnt + up(sizeof(int) * kMaxN);  // about 13.5 MB
+constexpr size_t oEacc = oEscan + up(sizeof(int) * (2 * (kMaxN / 2048 + 64) + 64));
+constexpr size_t kBytes = oEacc + up(sizeof(double) * 5 * 6 * kMaxN);  // about 16.3 MB
 
 __device__ __align__(256) unsigned char g_scratch[kBytes];
 
@@ -140,8 +140,8 @@ extern "C" scvt_status scvt_energy_grad_static(int64_t n, const scvt_density *rh
         cudaGetLastError();
         return SCVT_ERR_CUDA;
     }
-    bin_points(z, N, G, bin_of, count, start, cursor, scan_tmp, zs, zf, zl, sidx, st, s, &launches);
     Grid grid;
+    memset(&grid, 0, sizeof(grid));
     grid.n = N;
     grid.G = G;
     grid.nbins = 6 * G * G;
@@ -150,6 +150,9 @@ extern "C" scvt_status scvt_energy_grad_static(int64_t n, const scvt_density *rh
     grid.zl = zl;
     grid.sidx = sidx;
     grid.bstart = start;
+    grid.rho0 = to_device_density(*rho);
+    grid.rho0f = to_density32(grid.rho0);
+    bin_points(z, grid, bin_of, count, start, cursor, scan_tmp, zs, zf, zl, sidx, st, s, &launches);
     CellOut out;
     out.grad = g;
     out.hdiag = hd;
@@ -167,22 +170,9 @@ extern "C" scvt_status scvt_energy_grad_static(int64_t n, const scvt_density *rh
     cb.eoff = (int *)(base + oEoff);
     cb.ecell = (int *)(base + oEcell);
     cb.scan_tmp = (int *)(base + oEscan);
-    cb.parts_val = (double *)(base + oPval);
-    cb.parts_cnt = (int *)(base + oPcnt);
+    cb.eacc = (double *)(base + oEacc);
     cb.vo = nullptr;
-    if (cudaMemsetAsync(cb.parts_cnt, 0, sizeof(int) * N, s) != cudaSuccess) {
-        cudaGetLastError();
-        return SCVT_ERR_CUDA;
-    }
-    Density d;
-    d.kind = rho->kind;
-    d.gamma = rho->gamma;
-    d.alpha = rho->alpha;
-    d.beta = rho->beta;
-    d.xc0 = rho->xc[0];
-    d.xc1 = rho->xc[1];
-    d.xc2 = rho->xc[2];
-    cell_passes(grid, d, out, cb, list1, list2, st, 32, false, s, nullptr, nullptr, &launches, &cell_launches);
+    cell_passes(grid, out, cb, list1, list2, st, false, Tune(), s, nullptr, nullptr, &launches, &cell_launches);
     reduce_eval(N, fc, g, nullptr, nullptr, partials, st, s, &launches);
     DevStatus hs;
     cudaError_t e = cudaMemcpyAsync(&hs, st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s);

@@ -150,3 +150,106 @@ class Engine:
 
     def set_profiling(self, on=True):
         capi.scvt_set_profiling(self._h, on)
+
+    def set_tuning(self, **kw):
+        """Launch shape / search parameters (results do not depend on them)."""
+        t = capi.scvt_get_tuning(self._h)
+        for k, v in kw.items():
+            setattr(t, k, int(v))
+        capi.scvt_set_tuning(self._h, t)
+
+    def tuning(self):
+        t = capi.scvt_get_tuning(self._h)
+        return {f: getattr(t, f) for f, _ in capi.scvt_tuning._fields_}
+
+
+def _config(n, density, lbfgs_m, precision):
+    cfg = capi.scvt_config()
+    cfg.n = int(n)
+    cfg.rho = _density(density)
+    cfg.quad_points = 7
+    cfg.precision = int(precision)
+    cfg.lbfgs_m = int(lbfgs_m)
+    cfg.knn_k0 = 0
+    cfg.knn_kmax = 0
+    return cfg
+
+
+class Batch:
+    """Independent problems (sizes ns, densities) solved together.
+
+    Points of problem b are rows offsets[b]:offsets[b+1] of one (N_tot, 3)
+    array; use split() / concat() to move between the two views."""
+
+    def __init__(self, ns, densities, lbfgs_m: int = 7, precision: int = 0, device: int | torch.device = 0):
+        if len(ns) != len(densities):
+            raise ValueError("one density per problem")
+        self.ns = [int(n) for n in ns]
+        self.count = len(self.ns)
+        self.offsets = np.concatenate([[0], np.cumsum(self.ns)]).astype(np.int64)
+        self.ntot = int(self.offsets[-1])
+        self.device = torch.device("cuda", device) if isinstance(device, int) else torch.device(device)
+        cfgs = [_config(n, d, lbfgs_m, precision) for n, d in zip(self.ns, densities)]
+        with torch.cuda.device(self.device):
+            self._b = capi.scvt_batch_create(cfgs, torch.cuda.current_stream(self.device).cuda_stream)
+
+    def close(self):
+        if getattr(self, "_b", None):
+            capi.scvt_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def concat(self, zs):
+        if isinstance(zs[0], torch.Tensor):
+            return torch.cat([z.to(self.device) for z in zs]).contiguous()
+        return np.ascontiguousarray(np.concatenate(zs))
+
+    def split(self, z):
+        return [z[self.offsets[b]:self.offsets[b + 1]] for b in range(self.count)]
+
+    def energy_grad(self, z):
+        g = torch.empty((self.ntot, 3), dtype=torch.float64, device=self.device)
+        with torch.cuda.device(self.device):
+            e = capi.scvt_batch_energy_grad(self._b, _ptr(z), self.count, g.data_ptr())
+        return e, g
+
+    def lbfgs_solve(self, z, max_iter=200, grad_tol=1e-8, rel_grad_tol=0.0, rel_df_tol=0.0, step_tol=0.0,
+                    ls_max_evals=10, c1=1e-4, c2=0.9, warm_start=0):
+        o = capi.scvt_solve_opts(int(max_iter), float(grad_tol), float(rel_grad_tol), float(rel_df_tol),
+                                 float(step_tol), int(ls_max_evals), float(c1), float(c2), int(warm_start))
+        with torch.cuda.device(self.device):
+            reps = capi.scvt_batch_lbfgs_solve(self._b, _ptr(z), o, self.count)
+        return [{f: getattr(r, f) for f, _ in capi.scvt_solve_report._fields_} for r in reps]
+
+    def tune(self, z):
+        with torch.cuda.device(self.device):
+            t = capi.scvt_batch_tune(self._b, _ptr(z))
+        return {f: getattr(t, f) for f, _ in capi.scvt_tuning._fields_}
+
+    def set_tuning(self, **kw):
+        t = capi.scvt_batch_get_tuning(self._b)
+        for k, v in kw.items():
+            setattr(t, k, int(v))
+        capi.scvt_batch_set_tuning(self._b, t)
+
+    def tuning(self):
+        t = capi.scvt_batch_get_tuning(self._b)
+        return {f: getattr(t, f) for f, _ in capi.scvt_tuning._fields_}
+
+    def stats(self):
+        s = capi.scvt_batch_get_stats(self._b)
+        return {f: getattr(s, f) for f, _ in capi.scvt_stats._fields_}
+
+    def reset_stats(self):
+        capi.scvt_batch_reset_stats(self._b)

@@ -29,6 +29,7 @@ def test_struct_layout_matches_header(tmp_path):
         "scvt_solve_report": capi.scvt_solve_report,
         "scvt_stats": capi.scvt_stats,
         "scvt_eval_out": capi.scvt_eval_out,
+        "scvt_tuning": capi.scvt_tuning,
     }
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "scvt.h"', "int main(void){"]
     for sname, cls in structs.items():
@@ -73,6 +74,36 @@ def test_null_handle_is_safe():
     lib.scvt_destroy(None)
     assert lib.scvt_last_error(None) == b""
     assert lib.scvt_lloyd_step(None, None, None) == capi.ERR_INVALID
+    lib.scvt_batch_destroy(None)
+    assert lib.scvt_batch_last_error(None) == b""
+    assert lib.scvt_batch_energy_grad(None, None, None, None) == capi.ERR_INVALID
+    assert lib.scvt_set_tuning(None, None) == capi.ERR_INVALID
+
+
+def _cfg(n, m=5, precision=0):
+    cfg = capi.scvt_config()
+    cfg.n = n
+    cfg.rho.kind = 0
+    cfg.quad_points = 7
+    cfg.lbfgs_m = m
+    cfg.precision = precision
+    return cfg
+
+
+@pytest.mark.parametrize("case", ["empty", "bad_n", "mixed_m", "mixed_precision"])
+def test_batch_create_rejects_bad_configs_before_device_work(case):
+    if case == "empty":
+        cfgs = []
+    elif case == "bad_n":
+        cfgs = [_cfg(100), _cfg(3)]
+    elif case == "mixed_m":
+        cfgs = [_cfg(100, m=5), _cfg(100, m=7)]
+    else:
+        cfgs = [_cfg(100, precision=0), _cfg(100, precision=1)]
+    arr = (capi.scvt_config * max(len(cfgs), 1))(*cfgs)
+    b = C.c_void_p()
+    assert capi.lib().scvt_batch_create(arr, len(cfgs), None, C.byref(b)) == capi.ERR_INVALID
+    assert not b.value
 
 
 def test_build_sources_target_sm103a():
