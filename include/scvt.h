@@ -218,6 +218,13 @@ typedef struct {
 /* Set / read the tuning of a handle.  INVALID when a field is out of range. */
 scvt_status scvt_set_tuning(scvt_handle *h, const scvt_tuning *t);
 scvt_status scvt_get_tuning(const scvt_handle *h, scvt_tuning *t);
+/* Autotuner: times evaluations at z (N x 3, device or host) over a grid of
+ * tunings, one coordinate at a time (bin load 1/2/4/8; topology warps per
+ * block 2/4/8; topology grid cap 8/16/32 blocks per SM; quadrature block
+ * 128/256/512; first-pass target 16/24/32/48, the last compared on
+ * evaluations without radius hints), keeps the fastest and returns it in
+ * *chosen (nullable).  About 30 evaluations.  Synchronises. */
+scvt_status scvt_tune(scvt_handle *h, const double *z, scvt_tuning *chosen);
 
 /* ---- Batches of independent problems ------------------------------------
  * Many problems of Sec. 2.1 (uneven N, each with its own density) solved
@@ -257,12 +264,8 @@ scvt_status scvt_batch_energy_grad(scvt_batch *b, const double *z, double *energ
 scvt_status scvt_batch_lbfgs_solve(scvt_batch *b, double *z, const scvt_solve_opts *opts,
                                    scvt_solve_report *reports);
 
-/* Autotuner: times evaluations of the batch at z over a grid of tunings
- * (bin load, first-pass target, topology block shape and grid cap,
- * quadrature block), coordinate by coordinate, keeps the fastest and
- * returns it in *chosen (nullable).  The knn_target candidates are timed
- * without radius hints (the only evaluations that use it), the others on
- * warm evaluations.  Results of later calls do not depend on the choice. */
+/* Autotuner: as scvt_tune, on evaluations of the whole batch at z
+ * (N_tot x 3).  Results of later calls do not depend on the choice. */
 scvt_status scvt_batch_tune(scvt_batch *b, const double *z, scvt_tuning *chosen);
 scvt_status scvt_batch_set_tuning(scvt_batch *b, const scvt_tuning *t);
 scvt_status scvt_batch_get_tuning(const scvt_batch *b, scvt_tuning *t);

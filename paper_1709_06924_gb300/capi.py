@@ -86,6 +86,7 @@ SIGNATURES = {
                                       _vp, _vp, _vp]),
     "scvt_set_tuning": (_st, [_H, C.POINTER(scvt_tuning)]),
     "scvt_get_tuning": (_st, [_H, C.POINTER(scvt_tuning)]),
+    "scvt_tune": (_st, [_H, _vp, C.POINTER(scvt_tuning)]),
     "scvt_batch_create": (_st, [C.POINTER(scvt_config), C.c_int, _vp, C.POINTER(_H)]),
     "scvt_batch_destroy": (None, [_H]),
     "scvt_batch_energy_grad": (_st, [_H, _vp, C.POINTER(C.c_double), _vp]),
@@ -217,6 +218,12 @@ def scvt_set_tuning(h, t: scvt_tuning):
 def scvt_get_tuning(h) -> scvt_tuning:
     t = scvt_tuning()
     check(lib().scvt_get_tuning(h, C.byref(t)), "scvt_get_tuning", h)
+    return t
+
+
+def scvt_tune(h, z_ptr: int) -> scvt_tuning:
+    t = scvt_tuning()
+    check(lib().scvt_tune(h, _vp(z_ptr), C.byref(t)), "scvt_tune", h)
     return t
 
 

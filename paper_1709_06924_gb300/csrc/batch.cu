@@ -27,6 +27,7 @@
 #include <vector>
 
 #include "scvt_internal.cuh"
+#include "autotune.h"
 #include "wolfe.h"
 
 using namespace scvt;
@@ -746,45 +747,8 @@ scvt_status scvt_batch_tune(scvt_batch *BT, const double *z, scvt_tuning *chosen
         *ms = best;
         return SCVT_OK;
     };
-    Tune cur = BT->tune;
-    float cur_ms;
-    if ((s = time_cfg(cur, false, &cur_ms))) return s;
-    const int loads[] = {1, 2, 4, 8};
-    const int warps[] = {2, 4, 8};
-    const int bpsm[] = {8, 16, 32};
-    const int qblk[] = {128, 256, 512};
-    const int targets[] = {16, 24, 32, 48};
-    for (int coord = 0; coord < 5; ++coord) {
-        const int *vals;
-        int nv;
-        switch (coord) {
-        case 0: vals = loads; nv = 4; break;
-        case 1: vals = warps; nv = 3; break;
-        case 2: vals = bpsm; nv = 3; break;
-        case 3: vals = qblk; nv = 3; break;
-        default: vals = targets; nv = 4; break;
-        }
-        const bool cold = coord == 4;
-        Tune best = cur;
-        float best_ms = cur_ms;
-        if (cold && (s = time_cfg(cur, true, &best_ms))) return s;
-        for (int k = 0; k < nv; ++k) {
-            Tune u = cur;
-            switch (coord) {
-            case 0: u.bin_load = vals[k]; break;
-            case 1: u.topo_warps = vals[k]; break;
-            case 2: u.topo_bpsm = vals[k]; break;
-            case 3: u.quad_block = vals[k]; break;
-            default: u.knn_target = vals[k]; break;
-            }
-            if (memcmp(&u, &cur, sizeof(Tune)) == 0) continue;
-            float ms;
-            if ((s = time_cfg(u, cold, &ms))) return s;
-            if (ms < best_ms) { best_ms = ms; best = u; }
-        }
-        cur = best;
-        if (!cold) cur_ms = best_ms;
-    }
+    Tune cur;
+    if ((s = autotune(BT->tune, time_cfg, &cur))) return s;
     scvt_tuning t = tuning_of(cur);
     if ((s = scvt_batch_set_tuning(BT, &t))) return s;
     // leave warm hints for the chosen configuration

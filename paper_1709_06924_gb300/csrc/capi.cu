@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "scvt_internal.cuh"
+#include "autotune.h"
 #include "wolfe.h"
 
 using namespace scvt;
@@ -663,6 +664,56 @@ scvt_status scvt_set_tuning(scvt_handle *H, const scvt_tuning *t) {
     if (s) return fail(H, s, "tuning out of range");
     H->tune = u;
     H->G = bins_per_edge(H->n, u.bin_load);
+    return SCVT_OK;
+}
+
+scvt_status scvt_tune(scvt_handle *H, const double *z, scvt_tuning *chosen) {
+    if (!H) return SCVT_ERR_INVALID;
+    if (!z) return fail(H, SCVT_ERR_INVALID, "null argument");
+    const size_t n3 = 3 * (size_t)H->n;
+    const double *zd;
+    scvt_status s = stage_in(H, z, n3, H->b.stage_a, &zd);
+    if (s) return s;
+    Bufs &B = H->b;
+    double F, g2;
+    // one evaluation leaves radius hints for the warm timings; it must succeed
+    s = evaluate_dev(H, zd, B.gt, B.ht, B.fc, nullptr, nullptr, nullptr, nullptr, 0, nullptr, nullptr, &F, &g2,
+                     nullptr);
+    if (s) return s;
+    auto time_cfg = [&](const Tune &u, bool cold, float *ms) -> scvt_status {
+        H->tune = u;
+        H->G = bins_per_edge(H->n, u.bin_load);
+        float best = INFINITY;
+        for (int rep = 0; rep < 2; ++rep) {
+            if (cold) CK(cudaMemsetAsync(B.radius, 0, sizeof(float) * H->n, H->stream), "clear hints");
+            CK(cudaEventRecord(H->ev_l0, H->stream), "event");
+            scvt_status r = evaluate_dev(H, zd, B.gt, B.ht, B.fc, nullptr, nullptr, nullptr, nullptr, 0, nullptr,
+                                         nullptr, &F, &g2, nullptr);
+            if (r) return r;
+            CK(cudaEventRecord(H->ev_l1, H->stream), "event");
+            CK(cudaEventSynchronize(H->ev_l1), "event");
+            float t_ms = 0.0f;
+            CK(cudaEventElapsedTime(&t_ms, H->ev_l0, H->ev_l1), "event time");
+            best = std::min(best, t_ms);
+        }
+        *ms = best;
+        return SCVT_OK;
+    };
+    const Tune start = H->tune;
+    Tune best;
+    s = autotune(start, time_cfg, &best);
+    if (s) {
+        H->tune = start;
+        H->G = bins_per_edge(H->n, start.bin_load);
+        return s;
+    }
+    H->tune = best;
+    H->G = bins_per_edge(H->n, best.bin_load);
+    // leave warm hints for the chosen configuration
+    s = evaluate_dev(H, zd, B.gt, B.ht, B.fc, nullptr, nullptr, nullptr, nullptr, 0, nullptr, nullptr, &F, &g2,
+                     nullptr);
+    if (s) return s;
+    if (chosen) *chosen = tuning_of(best);
     return SCVT_OK;
 }
 

@@ -162,6 +162,12 @@ class Engine:
         t = capi.scvt_get_tuning(self._h)
         return {f: getattr(t, f) for f, _ in capi.scvt_tuning._fields_}
 
+    def tune(self, z):
+        """Run the autotuner on evaluations at z; returns the chosen tuning."""
+        self._sync_inputs()
+        t = capi.scvt_tune(self._h, _ptr(z))
+        return {f: getattr(t, f) for f, _ in capi.scvt_tuning._fields_}
+
 
 def _config(n, density, lbfgs_m, precision):
     cfg = capi.scvt_config()

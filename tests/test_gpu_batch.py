@@ -162,3 +162,14 @@ def test_autotuner_picks_a_valid_tuning_and_keeps_results():
         assert e1 == e0 and torch.equal(g1, g0)
         st = bt.stats()
         assert st["evaluations"] > 10 and st["kernel_launches"] > 0
+
+
+def test_single_problem_autotuner_keeps_results():
+    n, dens = 30001, I.WORKLOADS["tanh-2621442"].density
+    z = dev(I.uniform_sphere(n, 121))
+    with Engine(n, dens) as e:
+        F0, g0, _, _ = e.energy_grad(z)
+        t = e.tune(z)
+        assert t == e.tuning()
+        F1, g1, _, _ = e.energy_grad(z)
+    assert F1 == F0 and torch.equal(g1, g0)
