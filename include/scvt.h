@@ -275,6 +275,70 @@ scvt_status scvt_batch_get_stats(const scvt_batch *b, scvt_stats *out);
 scvt_status scvt_batch_reset_stats(scvt_batch *b);
 const char *scvt_batch_last_error(const scvt_batch *b);
 
+/* ---- Serving: continuous batching of solve requests ----------------------
+ * A request loop for many independent problems arriving over time (a
+ * deployment form; the paper solves one problem at a time).  Submitted jobs
+ * wait in a FIFO queue; each scvt_server_step() first admits queued jobs in
+ * order while the device-memory budget, the workspace rows and the job
+ * slots allow, then advances every job on the device by one LBFGS iteration
+ * (newly admitted jobs get their first evaluation in the same evaluation
+ * round), and retires the jobs that stopped.  A job's generators, gradient,
+ * preconditioner and LBFGS history stay resident on the device from
+ * admission to retirement; all jobs' evaluations share one launch sequence
+ * (the batch workspace above, re-laid out when the set of jobs changes).
+ * Each job's result equals, bit for bit, a single-problem scvt_lbfgs_solve
+ * with the same configuration and options from the same start.
+ * All calls are on the thread that owns the server. */
+typedef struct scvt_server scvt_server;
+
+typedef struct {
+    int64_t memory_budget;   /* device bytes for the workspace plus resident jobs; 0 = 80 % of the free
+                                memory at creation */
+    int64_t max_generators;  /* most generators on the device at once (sum of N of running jobs) */
+    int max_jobs;            /* most jobs on the device at once, 1..65535 */
+    int precision;           /* as scvt_config.precision, for every job */
+    int lbfgs_m;             /* as scvt_config.lbfgs_m, for every job */
+} scvt_server_config;
+
+typedef enum {
+    SCVT_JOB_QUEUED = 0,
+    SCVT_JOB_RUNNING = 1,
+    SCVT_JOB_DONE = 2,      /* stopped by a tolerance or max_iter (report.status OK or LINESEARCH) */
+    SCVT_JOB_FAILED = 3,    /* report.status holds the problem's error */
+    SCVT_JOB_FETCHED = 4    /* result handed out by scvt_server_fetch */
+} scvt_job_state;
+
+typedef struct {
+    int state;                     /* scvt_job_state */
+    int64_t n;
+    double t_submit, t_admit, t_done;  /* seconds on the server clock; -1 = not yet */
+    int64_t bytes_resident;        /* device bytes the job holds while running */
+    scvt_solve_report report;      /* progress so far; final once DONE or FAILED */
+} scvt_job_info;
+
+/* Errors: INVALID (bad config; workspace larger than the budget), OOM, CUDA. */
+scvt_status scvt_server_create(const scvt_server_config *cfg, void *cuda_stream, scvt_server **out);
+void scvt_server_destroy(scvt_server *s);  /* NULL-safe; drops queued and running jobs */
+/* Queue a job: n generators with density rho, start z0 (n x 3, host or
+ * device; copied before return), solve options as scvt_lbfgs_solve
+ * (warm_start must be 0; NULL = defaults).  INVALID when n exceeds
+ * max_generators, when the job alone exceeds the memory budget, or on a bad
+ * density or option.  *job_id receives the id (ids count from 0). */
+scvt_status scvt_server_submit(scvt_server *s, int64_t n, const scvt_density *rho, const double *z0,
+                               const scvt_solve_opts *opts, int64_t *job_id);
+/* One scheduling step (admit, one iteration of every running job, retire).
+ * running / queued (nullable) receive the counts after the step. */
+scvt_status scvt_server_step(scvt_server *s, int *running, int *queued);
+/* State and timing of a job. */
+scvt_status scvt_server_job(const scvt_server *s, int64_t job_id, scvt_job_info *info);
+/* Copy a finished job's generators (n x 3, host or device) and release them.
+ * INVALID if the job is not DONE or FAILED. */
+scvt_status scvt_server_fetch(scvt_server *s, int64_t job_id, double *z_out);
+/* Seconds since the server was created (the clock of scvt_job_info). */
+double scvt_server_clock(const scvt_server *s);
+scvt_status scvt_server_get_stats(const scvt_server *s, scvt_stats *out);
+const char *scvt_server_last_error(const scvt_server *s);
+
 /* Per-handle counters and (with profiling on) device times. */
 scvt_status scvt_get_stats(const scvt_handle *h, scvt_stats *out);
 scvt_status scvt_reset_stats(scvt_handle *h);

@@ -62,6 +62,18 @@ class scvt_tuning(C.Structure):
                 ("topo_blocks_per_sm", C.c_int), ("quad_block", C.c_int)]
 
 
+class scvt_server_config(C.Structure):
+    _fields_ = [("memory_budget", C.c_int64), ("max_generators", C.c_int64), ("max_jobs", C.c_int),
+                ("precision", C.c_int), ("lbfgs_m", C.c_int)]
+
+
+class scvt_job_info(C.Structure):
+    _fields_ = [("state", C.c_int), ("n", C.c_int64), ("t_submit", C.c_double), ("t_admit", C.c_double),
+                ("t_done", C.c_double), ("bytes_resident", C.c_int64), ("report", scvt_solve_report)]
+
+
+JOB_QUEUED, JOB_RUNNING, JOB_DONE, JOB_FAILED, JOB_FETCHED = range(5)
+
 _H = C.c_void_p
 _vp = C.c_void_p
 _st = C.c_int
@@ -97,6 +109,16 @@ SIGNATURES = {
     "scvt_batch_get_stats": (_st, [_H, C.POINTER(scvt_stats)]),
     "scvt_batch_reset_stats": (_st, [_H]),
     "scvt_batch_last_error": (C.c_char_p, [_H]),
+    "scvt_server_create": (_st, [C.POINTER(scvt_server_config), _vp, C.POINTER(_H)]),
+    "scvt_server_destroy": (None, [_H]),
+    "scvt_server_submit": (_st, [_H, C.c_int64, C.POINTER(scvt_density), _vp, C.POINTER(scvt_solve_opts),
+                                 C.POINTER(C.c_int64)]),
+    "scvt_server_step": (_st, [_H, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "scvt_server_job": (_st, [_H, C.c_int64, C.POINTER(scvt_job_info)]),
+    "scvt_server_fetch": (_st, [_H, C.c_int64, _vp]),
+    "scvt_server_clock": (C.c_double, [_H]),
+    "scvt_server_get_stats": (_st, [_H, C.POINTER(scvt_stats)]),
+    "scvt_server_last_error": (C.c_char_p, [_H]),
 }
 
 STATIC_MAX_N = 16384  # SCVT_STATIC_MAX_N
@@ -138,12 +160,14 @@ class ScvtError(RuntimeError):
         self.status = status
 
 
-def check(status: int, where: str, handle=None, batch=None):
+def check(status: int, where: str, handle=None, batch=None, server=None):
     if status != OK:
         if handle:
             detail = lib().scvt_last_error(handle).decode()
         elif batch:
             detail = lib().scvt_batch_last_error(batch).decode()
+        elif server:
+            detail = lib().scvt_server_last_error(server).decode()
         else:
             detail = ""
         raise ScvtError(status, where, detail)
@@ -277,3 +301,47 @@ def scvt_batch_get_stats(b) -> scvt_stats:
 
 def scvt_batch_reset_stats(b):
     check(lib().scvt_batch_reset_stats(b), "scvt_batch_reset_stats", batch=b)
+
+
+def scvt_server_create(cfg: scvt_server_config, stream: int | None = None):
+    s = _H()
+    check(lib().scvt_server_create(C.byref(cfg), _vp(stream or 0), C.byref(s)), "scvt_server_create")
+    return s
+
+
+def scvt_server_destroy(s):
+    lib().scvt_server_destroy(s)
+
+
+def scvt_server_submit(s, n: int, rho: scvt_density, z0_ptr: int, opts: scvt_solve_opts | None) -> int:
+    jid = C.c_int64()
+    check(lib().scvt_server_submit(s, int(n), C.byref(rho), _vp(z0_ptr),
+                                   C.byref(opts) if opts is not None else None, C.byref(jid)),
+          "scvt_server_submit", server=s)
+    return jid.value
+
+
+def scvt_server_step(s):
+    r, q = C.c_int(), C.c_int()
+    check(lib().scvt_server_step(s, C.byref(r), C.byref(q)), "scvt_server_step", server=s)
+    return r.value, q.value
+
+
+def scvt_server_job(s, jid: int) -> scvt_job_info:
+    info = scvt_job_info()
+    check(lib().scvt_server_job(s, int(jid), C.byref(info)), "scvt_server_job", server=s)
+    return info
+
+
+def scvt_server_fetch(s, jid: int, z_ptr: int):
+    check(lib().scvt_server_fetch(s, int(jid), _vp(z_ptr)), "scvt_server_fetch", server=s)
+
+
+def scvt_server_clock(s) -> float:
+    return lib().scvt_server_clock(s)
+
+
+def scvt_server_get_stats(s) -> scvt_stats:
+    st = scvt_stats()
+    check(lib().scvt_server_get_stats(s, C.byref(st)), "scvt_server_get_stats", server=s)
+    return st

@@ -1,0 +1,81 @@
+// evalset.cuh -- the evaluation workspace shared by batches and the server
+// (not installed).
+//
+// An EvalSet evaluates a set of independent problems laid out in rows: the
+// problem b of the current layout owns rows [p0_b, p0_b + n_b) of the row
+// arrays (zt, gt, ht, fc, q, nrm, radius) and its own block of cube-map
+// bins.  One evaluation = binning, topology passes, corners, per-edge
+// quadrature, per-cell sums over all problems' cells, then one reduction per
+// problem (the chunking of a single problem of its size), for the problems
+// marked active.  The sequence has fixed pointers and launch shapes for a
+// given layout and tuning, so it is captured once as a CUDA graph and
+// replayed; a new layout or tuning drops the graph.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "scvt_internal.cuh"
+
+namespace scvt {
+
+struct EvalSet {
+    // capacity
+    int64_t cap_n = 0;
+    int cap_b = 0;
+    int precision = 0;
+    cudaStream_t stream = nullptr;
+    // current layout
+    int B = 0;
+    int64_t ntot = 0;
+    std::vector<InstGeom> geom;
+    std::vector<int> pbase;
+    int max_nb = 1;
+    int nbins = 0;
+    Tune tune;
+    // device tables and their pinned mirrors
+    InstGeom *d_inst = nullptr;
+    int *d_pinst = nullptr, *d_pbase = nullptr, *d_active = nullptr;
+    Density *d_rho = nullptr;
+    DensityF *d_rhof = nullptr;
+    DevStatus *d_ist = nullptr, *d_st = nullptr;
+    DevStatus *h_ist = nullptr, *h_st = nullptr;
+    int *h_active = nullptr;
+    // row arrays
+    double *zt = nullptr, *gt = nullptr, *ht = nullptr, *fc = nullptr, *q = nullptr, *nrm = nullptr;
+    float *radius = nullptr;
+    double *partials = nullptr;
+    size_t partials_len = 0;
+    // workspace
+    P4 *zs = nullptr, *cvx = nullptr;
+    float4 *zf = nullptr, *zl = nullptr, *vo = nullptr;
+    int *cdeg = nullptr, *cnb = nullptr, *eoff = nullptr, *ecell = nullptr, *escan = nullptr;
+    double *eacc = nullptr;
+    int *bin_of = nullptr, *count = nullptr, *start = nullptr, *cursor = nullptr, *scan_tmp = nullptr;
+    int *sidx = nullptr, *list1 = nullptr, *list2 = nullptr;
+    // the captured evaluation
+    cudaGraphExec_t graph = nullptr;
+    int64_t graph_launches = 0, graph_cell_launches = 0;
+    int64_t bytes = 0;
+};
+
+// device bytes an EvalSet of this capacity allocates
+int64_t evalset_bytes(int64_t cap_n, int cap_b, int precision);
+// allocate for up to cap_n rows and cap_b problems; work is ordered on s
+cudaError_t evalset_alloc(EvalSet &E, int64_t cap_n, int cap_b, int precision, cudaStream_t s);
+void evalset_free(EvalSet &E);
+// lay out B problems (sizes ns, densities rhos) in rows 0.. in order; the
+// row arrays (radius hints included) are left as they are
+cudaError_t evalset_layout(EvalSet &E, int B, const int *ns, const scvt_density *rhos);
+// new tuning: re-bins the problems, drops the graph
+cudaError_t evalset_set_tune(EvalSet &E, const Tune &t);
+// one evaluation of the problems marked in h_active at their zt rows;
+// synchronises; per-problem results in h_ist, global counters in h_st
+cudaError_t evalset_run(EvalSet &E, scvt_stats *stats);
+// time evaluations (best of two, events on E.stream) with tuning u; cold
+// clears the radius hints first
+cudaError_t evalset_time(EvalSet &E, const Tune &u, bool cold, float *ms, scvt_stats *stats);
+scvt_status status_of_flags(unsigned f);
+
+}  // namespace scvt

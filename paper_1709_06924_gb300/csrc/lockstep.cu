@@ -1,0 +1,240 @@
+// lockstep.cu -- many problems' LBFGS iterations in lockstep (see lockstep.cuh).
+#include <math.h>
+#include <string.h>
+
+#include "lockstep.cuh"
+
+namespace scvt {
+
+namespace {
+
+double *slot_S(const Lane &L, int slot) { return L.hist + (size_t)slot * L.slot_stride; }
+double *slot_Y(const Lane &L, int slot) { return slot_S(L, slot) + L.y_off; }
+
+// two-loop direction of lane L into its q rows; g.q in the lane's status block
+void enqueue_direction(EvalSet &E, Lane &L, double *partials, double *scal, int64_t *launches) {
+    const double *S[kLaneMaxM], *Y[kLaneMaxM], *R[kLaneMaxM];
+    for (int k = 0; k < L.count; ++k) {
+        const int sl = L.slots[k];
+        S[k] = slot_S(L, sl);
+        Y[k] = slot_Y(L, sl);
+        R[k] = L.rho + sl;
+    }
+    two_loop(L.n, L.g, L.h, L.count, S, Y, R, E.q + 3 * L.row, partials, scal, &E.d_ist[L.b], E.stream, launches);
+}
+
+cudaError_t sync_statuses(EvalSet &E) {
+    cudaError_t e = cudaMemcpyAsync(E.h_ist, E.d_ist, sizeof(DevStatus) * E.B, cudaMemcpyDeviceToHost, E.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(E.stream);
+    return e;
+}
+
+}  // namespace
+
+void lane_reset_history(Lane &L, int m) {
+    L.count = 0;
+    for (int k = 0; k <= m; ++k) L.slots[k] = k;
+    L.spare = m;
+}
+
+scvt_status lane_options(const scvt_solve_opts *in, scvt_solve_opts *o) {
+    memset(o, 0, sizeof(*o));
+    if (in) *o = *in;
+    else {
+        o->max_iter = 200;
+        o->grad_tol = 1e-8;
+    }
+    if (o->ls_max_evals <= 0) o->ls_max_evals = 10;
+    if (o->c1 <= 0.0) o->c1 = 1e-4;
+    if (o->c2 <= 0.0) o->c2 = 0.9;
+    if (o->max_iter < 0 || !(o->c1 < o->c2) || o->c2 >= 1.0) return SCVT_ERR_INVALID;
+    return SCVT_OK;
+}
+
+cudaError_t lockstep_round(EvalSet &E, std::vector<Lane *> &lanes, int m, double *partials, double *scal,
+                           scvt_stats *stats) {
+    cudaStream_t s = E.stream;
+    int64_t *launches = &stats->kernel_launches;
+    cudaError_t e;
+    // ---- stopping tests of the running lanes
+    std::vector<Lane *> act, init;
+    for (Lane *L : lanes) {
+        if (L->done) continue;
+        if (L->need_init) {
+            init.push_back(L);
+            continue;
+        }
+        L->rep.energy = L->F;
+        L->rep.grad_norm = L->gnorm;
+        const scvt_solve_opts &o = L->opt;
+        bool stop = false;
+        if (L->gnorm <= o.grad_tol) { L->rep.converged = 1; stop = true; }
+        else if (o.rel_grad_tol > 0 && L->gnorm / L->F <= o.rel_grad_tol) { L->rep.converged = 1; stop = true; }
+        else if (L->rep.iters > 0 && o.rel_df_tol > 0 && fabs(L->F - L->Fprev) / L->Fprev < o.rel_df_tol) {
+            L->rep.converged = 1;
+            stop = true;
+        } else if (L->rep.iters >= o.max_iter) {
+            stop = true;
+        }
+        if (stop) L->done = true;
+        else act.push_back(L);
+    }
+    // ---- directions (again, from an empty history, where one is not a descent direction)
+    if (!act.empty()) {
+        for (Lane *L : act) enqueue_direction(E, *L, partials, scal, launches);
+        if ((e = sync_statuses(E)) != cudaSuccess) return e;
+        std::vector<Lane *> redo;
+        for (Lane *L : act) {
+            L->d0 = E.h_ist[L->b].dots[3];
+            if (!(L->d0 < 0.0)) redo.push_back(L);
+        }
+        if (!redo.empty()) {
+            for (Lane *L : redo) {
+                lane_reset_history(*L, m);
+                L->rep.resets++;
+                enqueue_direction(E, *L, partials, scal, launches);
+            }
+            if ((e = sync_statuses(E)) != cudaSuccess) return e;
+            for (Lane *L : redo) {
+                L->d0 = E.h_ist[L->b].dots[3];
+                if (!(L->d0 < 0.0)) {
+                    L->rep.status = SCVT_ERR_DEGENERATE;
+                    L->done = true;
+                    L->state_valid = false;
+                }
+            }
+        }
+    }
+    // ---- line searches in lockstep; the first round also evaluates the new lanes
+    std::vector<Lane *> ls;
+    for (Lane *L : act) {
+        if (L->done) continue;
+        L->ls.ftol = L->opt.c1;
+        L->ls.gtol = L->opt.c2;
+        L->ls.maxfev = L->opt.ls_max_evals;
+        L->ls_state = L->ls.begin(L->F, L->d0, 1.0);
+        if (L->ls_state == 0) ls.push_back(L);
+    }
+    bool first = true;
+    while (!ls.empty() || (first && !init.empty())) {
+        for (int b = 0; b < E.B; ++b) E.h_active[b] = 0;
+        for (Lane *L : ls) {
+            trial_point(L->n, L->z, E.q + 3 * L->row, L->ls.trial(), E.zt + 3 * L->row, E.nrm + L->row, s, launches);
+            E.h_active[L->b] = 1;
+        }
+        if (first) {
+            for (Lane *L : init) {
+                e = cudaMemcpyAsync(E.zt + 3 * L->row, L->z, sizeof(double) * 3 * L->n, cudaMemcpyDeviceToDevice, s);
+                if (e != cudaSuccess) return e;
+                E.h_active[L->b] = 1;
+            }
+        }
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if ((e = evalset_run(E, stats)) != cudaSuccess) return e;
+        if (first) {
+            for (Lane *L : init) {
+                const DevStatus &ds = E.h_ist[L->b];
+                L->need_init = false;
+                L->rep.fevals += 1;
+                const scvt_status sb = status_of_flags(ds.flags);
+                if (sb) {
+                    L->rep.status = sb;
+                    L->done = true;
+                    L->state_valid = false;
+                    continue;
+                }
+                L->F = ds.red[0];
+                L->Fprev = L->F;
+                L->gnorm = sqrt(ds.red[1]);
+                L->state_valid = true;
+                lane_reset_history(*L, m);
+                cudaMemcpyAsync(L->g, E.gt + 3 * L->row, sizeof(double) * 3 * L->n, cudaMemcpyDeviceToDevice, s);
+                cudaMemcpyAsync(L->h, E.ht + L->row, sizeof(double) * L->n, cudaMemcpyDeviceToDevice, s);
+            }
+            first = false;
+        }
+        std::vector<Lane *> next;
+        for (Lane *L : ls) {
+            const DevStatus &ds = E.h_ist[L->b];
+            const scvt_status sb = status_of_flags(ds.flags);
+            // a step that breaks the tessellation is a failed trial, not an error
+            L->g2_last = ds.red[1];
+            L->ls_state = L->ls.feed(sb ? 1 : 0, sb ? 0.0 : ds.red[0], sb ? 0.0 : ds.red[2]);
+            if (L->ls_state == 0) next.push_back(L);
+        }
+        ls.swap(next);
+    }
+    // ---- accept (or restart)
+    std::vector<Lane *> acc;
+    for (Lane *L : act) {
+        if (L->done) continue;
+        L->rep.fevals += L->ls.nfev;
+        const int info = L->ls_state;
+        const double fa = L->ls.last_f;
+        if (info != 1) {
+            if (!(fa < L->F)) {
+                if (L->count == 0) {
+                    L->rep.status = SCVT_ERR_LINESEARCH;
+                    L->done = true;
+                    continue;
+                }
+                lane_reset_history(*L, m);
+                L->rep.resets++;
+                continue;
+            }
+            lane_reset_history(*L, m);
+            L->rep.resets++;
+        }
+        const int slot = L->spare;
+        cudaMemsetAsync(&E.d_ist[L->b].maxmove_bits, 0, sizeof(unsigned long long), s);
+        accept_pair(L->n, E.zt + 3 * L->row, L->z, E.gt + 3 * L->row, L->g, slot_S(*L, slot), slot_Y(*L, slot),
+                    partials, &E.d_ist[L->b], s, launches);
+        acc.push_back(L);
+    }
+    if (!acc.empty()) {
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if ((e = sync_statuses(E)) != cudaSuccess) return e;
+    }
+    for (Lane *L : acc) {
+        const DevStatus &ds = E.h_ist[L->b];
+        const double ys = ds.dots[0], yy = ds.dots[1], ss = ds.dots[2];
+        double maxmove;
+        unsigned long long mb = ds.maxmove_bits;
+        memcpy(&maxmove, &mb, sizeof(double));
+        const int slot = L->spare;
+        if (m > 0 && ys > 1e-12 * sqrt(yy) * sqrt(ss)) {
+            set_rho(L->rho, slot, &E.d_ist[L->b], s, launches);
+            if (L->count == m) {
+                int old = L->slots[0];
+                for (int k = 1; k < L->count; ++k) L->slots[k - 1] = L->slots[k];
+                L->count--;
+                L->spare = old;
+            } else {
+                bool used[kLaneMaxM + 1] = {false};
+                for (int k = 0; k < L->count; ++k) used[L->slots[k]] = true;
+                used[slot] = true;
+                for (int k = 0; k <= m; ++k)
+                    if (!used[k]) { L->spare = k; break; }
+            }
+            L->slots[L->count++] = slot;
+        } else {
+            L->rep.skipped++;
+        }
+        cudaMemcpyAsync(L->z, E.zt + 3 * L->row, sizeof(double) * 3 * L->n, cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(L->g, E.gt + 3 * L->row, sizeof(double) * 3 * L->n, cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(L->h, E.ht + L->row, sizeof(double) * L->n, cudaMemcpyDeviceToDevice, s);
+        L->Fprev = L->F;
+        L->F = L->ls.last_f;
+        L->gnorm = sqrt(L->g2_last);
+        L->rep.iters++;
+        L->rep.energy = L->F;
+        L->rep.grad_norm = L->gnorm;
+        if (L->opt.step_tol > 0 && maxmove <= L->opt.step_tol) {
+            L->rep.converged = 1;
+            L->done = true;
+        }
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace scvt

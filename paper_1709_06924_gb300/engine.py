@@ -259,3 +259,66 @@ class Batch:
 
     def reset_stats(self):
         capi.scvt_batch_reset_stats(self._b)
+
+
+class Server:
+    """Continuous-batching request loop: submit jobs, step, read and fetch results."""
+
+    def __init__(self, max_generators: int, max_jobs: int, memory_budget: int = 0, precision: int = 0,
+                 lbfgs_m: int = 7, device: int | torch.device = 0):
+        self.device = torch.device("cuda", device) if isinstance(device, int) else torch.device(device)
+        cfg = capi.scvt_server_config(int(memory_budget), int(max_generators), int(max_jobs), int(precision),
+                                      int(lbfgs_m))
+        with torch.cuda.device(self.device):
+            self._s = capi.scvt_server_create(cfg, torch.cuda.current_stream(self.device).cuda_stream)
+        self.sizes = {}
+
+    def close(self):
+        if getattr(self, "_s", None):
+            capi.scvt_server_destroy(self._s)
+            self._s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def submit(self, z0, density: Density, max_iter=200, grad_tol=1e-8, rel_grad_tol=0.0, rel_df_tol=0.0,
+               step_tol=0.0, ls_max_evals=10, c1=1e-4, c2=0.9) -> int:
+        o = capi.scvt_solve_opts(int(max_iter), float(grad_tol), float(rel_grad_tol), float(rel_df_tol),
+                                 float(step_tol), int(ls_max_evals), float(c1), float(c2), 0)
+        n = int(z0.shape[0])
+        with torch.cuda.device(self.device):
+            jid = capi.scvt_server_submit(self._s, n, _density(density), _ptr(z0), o)
+        self.sizes[jid] = n
+        return jid
+
+    def step(self):
+        """One scheduling step; returns (running, queued)."""
+        with torch.cuda.device(self.device):
+            return capi.scvt_server_step(self._s)
+
+    def job(self, jid: int) -> dict:
+        i = capi.scvt_server_job(self._s, jid)
+        d = {f: getattr(i, f) for f, _ in capi.scvt_job_info._fields_ if f != "report"}
+        d["report"] = {f: getattr(i.report, f) for f, _ in capi.scvt_solve_report._fields_}
+        return d
+
+    def fetch(self, jid: int):
+        z = np.empty((self.sizes[jid], 3))
+        capi.scvt_server_fetch(self._s, jid, z.ctypes.data)
+        return z
+
+    def clock(self) -> float:
+        return capi.scvt_server_clock(self._s)
+
+    def stats(self):
+        s = capi.scvt_server_get_stats(self._s)
+        return {f: getattr(s, f) for f, _ in capi.scvt_stats._fields_}

@@ -30,6 +30,8 @@ def test_struct_layout_matches_header(tmp_path):
         "scvt_stats": capi.scvt_stats,
         "scvt_eval_out": capi.scvt_eval_out,
         "scvt_tuning": capi.scvt_tuning,
+        "scvt_server_config": capi.scvt_server_config,
+        "scvt_job_info": capi.scvt_job_info,
     }
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "scvt.h"', "int main(void){"]
     for sname, cls in structs.items():
@@ -110,3 +112,15 @@ def test_build_sources_target_sm103a():
     assert B.ARCH == "-gencode=arch=compute_103a,code=sm_103a"
     assert len(B.sources()) >= 3
     assert os.path.exists(capi.lib()._name)
+
+
+@pytest.mark.parametrize("field,value", [("max_jobs", 0), ("max_generators", 3), ("precision", 2),
+                                         ("lbfgs_m", 40), ("memory_budget", -1)])
+def test_server_create_rejects_bad_config_before_device_work(field, value):
+    cfg = capi.scvt_server_config(1 << 30, 100000, 8, 0, 7)
+    setattr(cfg, field, value)
+    s = C.c_void_p()
+    assert capi.lib().scvt_server_create(C.byref(cfg), None, C.byref(s)) == capi.ERR_INVALID
+    assert not s.value
+    capi.lib().scvt_server_destroy(None)
+    assert capi.lib().scvt_server_last_error(None) == b""
