@@ -51,6 +51,10 @@ def parse():
     p.add_argument("--no-time-to-tol", action="store_true", help="skip the time-to-tolerance runs")
     p.add_argument("--no-batched", action="store_true", help="skip the 64-problem batch")
     p.add_argument("--no-tune", action="store_true", help="keep the default tuning (no autotuner run)")
+    p.add_argument("--no-serving", action="store_true", help="skip the request-stream measurement")
+    p.add_argument("--serve-jobs", type=int, default=32, help="jobs in the request stream")
+    p.add_argument("--serve-n-hi", type=int, default=655362, help="largest job size of the request stream")
+    p.add_argument("--serve-max-iter", type=int, default=100, help="iteration cap per served job")
     p.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
                    help="fp64: everything in FP64; mixed: FP32 corners/quadrature, FP64 sums and LBFGS")
     return p.parse_args()
@@ -249,6 +253,70 @@ def run_batched(args, local, prec, count=64):
             "statuses": sorted({r["status"] for r in reps})}
 
 
+def serve_stream(srv, jobs, arrivals, max_iter, tol):
+    """Submit job k at arrivals[k] seconds (server clock, from the first
+    submission), stepping the server in between; returns per-job records."""
+    t0 = srv.clock()
+    ids = {}
+    k = 0
+    while True:
+        now = srv.clock() - t0
+        while k < len(jobs) and arrivals[k] <= now:
+            z, dens = jobs[k]
+            ids[k] = srv.submit(z, dens, max_iter=max_iter, grad_tol=tol)
+            k += 1
+        running, queued = srv.step()
+        if running == 0 and queued == 0:
+            if k == len(jobs):
+                break
+            time.sleep(max(0.0, min(arrivals[k] - (srv.clock() - t0), 0.05)))
+    recs = []
+    for j in range(len(jobs)):
+        info = srv.job(ids[j])
+        recs.append(info)
+        srv.fetch(ids[j])
+    return recs
+
+
+def run_serving(args, local, prec, count=None):
+    """A Poisson stream of solve requests through the continuous-batching
+    server: N log-uniform in [40,962, n_hi], random tanh caps (the batched
+    workloads' sampler), each job to ||grad E||_2 <= 1e-6 (at most max_iter
+    iterations).  A closed-loop pass (all jobs at t = 0) measures the service
+    capacity; the timed pass offers Poisson arrivals at 80 % of it."""
+    from paper_1709_06924_gb300.engine import Server
+    count = count or args.serve_jobs
+    inst = I.sample_batched_instances(count, args.seed + 7, n_lo=40962, n_hi=args.serve_n_hi)
+    jobs = [(I.uniform_sphere(n, sd), d) for n, d, sd in inst]
+    max_iter, tol = args.serve_max_iter, 1e-6
+    cap_n = max(4 * max(n for n, _, _ in inst), 2_000_000)
+    with Server(max_generators=cap_n, max_jobs=32, precision=prec, device=local) as srv:
+        closed = serve_stream(srv, jobs, [0.0] * count, max_iter, tol)
+        t_closed = max(r["t_done"] for r in closed) - min(r["t_submit"] for r in closed)
+        rate = 0.8 * count / t_closed
+        rng = np.random.default_rng(args.seed + 11)
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, size=count))
+        arrivals -= arrivals[0]
+        ev0 = srv.stats()["evaluations"]
+        recs = serve_stream(srv, jobs, list(arrivals), max_iter, tol)
+        evs = srv.stats()["evaluations"] - ev0
+    lat = np.array([r["t_done"] - r["t_submit"] for r in recs])
+    wait = np.array([r["t_admit"] - r["t_submit"] for r in recs])
+    span = max(r["t_done"] for r in recs) - min(r["t_submit"] for r in recs)
+    units = sum(n * r["report"]["iters"] for (n, _, _), r in zip(inst, recs))
+    iters = [r["report"]["iters"] for r in recs]
+    return {"jobs": count, "n_range": [40962, args.serve_n_hi], "precision": "mixed" if prec else "fp64",
+            "grad_tol": tol, "max_iter": max_iter,
+            "converged": int(sum(r["report"]["converged"] for r in recs)),
+            "closed_loop_seconds": t_closed, "arrival_rate_per_s": rate, "offered_load": 0.8,
+            "p50_time_to_tol_s": float(np.percentile(lat, 50)), "p99_time_to_tol_s": float(np.percentile(lat, 99)),
+            "p50_queue_wait_s": float(np.percentile(wait, 50)), "makespan_s": span,
+            "value": units / span, "unit": "generator-updates/s", "evaluations": evs,
+            "iters_min_median_max": [int(min(iters)), int(np.median(iters)), int(max(iters))],
+            "note": "jobs and N range scaled down from the 2,000-job stream for a minutes-long run"
+                    if count < 2000 else None}
+
+
 def run_ours(args, w):
     import torch
     ws, rank, local = dist_env()
@@ -371,6 +439,13 @@ def run_ours(args, w):
         except Exception as ex:  # reported, not fatal to the headline line
             batched = {"error": repr(ex)}
 
+    serving = None
+    if not args.no_serving:
+        try:
+            serving = run_serving(args, local, prec)
+        except Exception as ex:  # reported, not fatal to the headline line
+            serving = {"error": repr(ex)}
+
     ttt = None
     if not args.no_time_to_tol:
         for pr in (0, 1):
@@ -405,6 +480,7 @@ def run_ours(args, w):
             "other_form": other,
             "time_to_tol": ttt,
             "batched": batched,
+            "serving": serving,
             "knn_retries": st["knn_retries"],
             "ambiguous": st["ambiguous"],
             "eval_ms_avg": st["eval_ms"] / max(st["evaluations"], 1),
