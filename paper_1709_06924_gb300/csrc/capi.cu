@@ -154,7 +154,12 @@ scvt_status evaluate_dev(scvt_handle *H, const double *zdev, double *grad, doubl
     g.bstart = B.start;
     g.rho0 = to_device_density(H->cfg.rho);
     g.rho0f = to_density32(g.rho0);
-    bin_points(zdev, g, B.bin_of, B.count, B.start, B.cursor, B.scan_tmp, B.zs, B.zf, B.zl, B.sidx, B.st, s, L);
+    if (!H->radius_valid) {
+        CK(cudaMemsetAsync(B.radius, 0, sizeof(float) * n, s), "reset radius hints");
+        H->radius_valid = true;
+    }
+    bin_points(zdev, g, B.bin_of, B.count, B.start, B.cursor, B.scan_tmp, B.zs, B.zf, B.zl, B.sidx, B.radius, B.st, s,
+               L);
     CellOut out;
     out.grad = grad;
     out.hdiag = hdiag;
@@ -165,10 +170,6 @@ scvt_status evaluate_dev(scvt_handle *H, const double *zdev, double *grad, doubl
     out.nbr = nbr;
     out.max_deg = max_deg;
     out.radius = B.radius;
-    if (!H->radius_valid) {
-        CK(cudaMemsetAsync(B.radius, 0, sizeof(float) * n, s), "reset radius hints");
-        H->radius_valid = true;
-    }
     CellBuf cb;
     cb.deg = B.cdeg;
     cb.vx = B.cvx;

@@ -134,9 +134,12 @@ __global__ void k_bin_count(const double *__restrict__ z, Grid g, int *__restric
     atomicAdd(&count[b], 1);
 }
 
+// The FP32 copy carries the generator's search-radius hint (from the previous
+// evaluation, 0 = none) in its w component, so the topology pass reads it with
+// the coordinates instead of through the original index.
 __global__ void k_bin_scatter(const double *__restrict__ z, int n, const int *__restrict__ bin_of,
                               int *__restrict__ cursor, P4 *__restrict__ zs, float4 *__restrict__ zf,
-                              float4 *__restrict__ zl, int *__restrict__ sidx) {
+                              float4 *__restrict__ zl, int *__restrict__ sidx, const float *__restrict__ hint) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int pos = atomicAdd(&cursor[bin_of[i]], 1);
@@ -144,7 +147,7 @@ __global__ void k_bin_scatter(const double *__restrict__ z, int n, const int *__
     double x = z[3 * (size_t)i], y = z[3 * (size_t)i + 1], w = z[3 * (size_t)i + 2];
     zs[pos] = P4{x, y, w, 0.0};
     const float hx = (float)x, hy = (float)y, hw = (float)w;
-    zf[pos] = make_float4(hx, hy, hw, 0.0f);
+    zf[pos] = make_float4(hx, hy, hw, hint ? hint[i] : 0.0f);
     zl[pos] = make_float4((float)(x - (double)hx), (float)(y - (double)hy), (float)(w - (double)hw), 0.0f);
 }
 
@@ -581,8 +584,24 @@ __device__ __forceinline__ void write_cell(const CellOut &out, int i, V3 zi, con
     if (out.fcell) out.fcell[i] = acc.e;
 }
 
-__device__ __forceinline__ bool lex_less(V3 a, V3 b) {
-    return a.x < b.x || (a.x == b.x && (a.y < b.y || (a.y == b.y && a.z < b.z)));
+// order-preserving unsigned image of a float's bits (negative values reversed)
+__device__ __forceinline__ unsigned okey32(float x) {
+    const unsigned b = __float_as_uint(x);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+// Canonical start of a cell's edge cycle: the neighbour whose FP32 pair
+// coordinates (hi.x, lo.x, hi.y, lo.y, hi.z, lo.z) are lexicographically
+// smallest -- a function of the point alone, so the edge order (and every
+// per-cell sum) is the same whichever pass certifies the cell.
+__device__ __forceinline__ bool ckey_less(const Grid &g, int a, int b) {
+    const float4 ha = g.zf[a], hb = g.zf[b], la = g.zl[a], lb = g.zl[b];
+    const unsigned ka[6] = {okey32(ha.x), okey32(la.x), okey32(ha.y), okey32(la.y), okey32(ha.z), okey32(la.z)};
+    const unsigned kb[6] = {okey32(hb.x), okey32(lb.x), okey32(hb.y), okey32(lb.y), okey32(hb.z), okey32(lb.z)};
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+        if (ka[k] != kb[k]) return ka[k] < kb[k];
+    return false;
 }
 
 // -------------------------------------------------------------- topology
@@ -739,14 +758,11 @@ __global__ void __launch_bounds__(128) k_topo(Grid g, CellOut out, CellBuf cb,
             continue;
         }
 
-        // ---- canonical edge order: start at the lexicographically smallest neighbour
+        // ---- canonical edge order: start at the neighbour with the smallest key
         const int c = P.cur, nv = P.nv;
         int k0 = 0;
-        V3 best = ld(g.zs + P.gen_of(P.ln[c][0]));
-        for (int k = 1; k < nv; ++k) {
-            V3 zn = ld(g.zs + P.gen_of(P.ln[c][k]));
-            if (lex_less(zn, best)) { best = zn; k0 = k; }
-        }
+        for (int k = 1; k < nv; ++k)
+            if (ckey_less(g, P.gen_of(P.ln[c][k]), P.gen_of(P.ln[c][k0]))) k0 = k;
         if (out.deg) {
             out.deg[i] = nv;
             if (nv <= out.max_deg)
@@ -867,10 +883,6 @@ __device__ bool outside64(const Grid &g, int p, int gin, int gout, int gnew, uns
     return sd > 0.0;
 }
 
-__device__ __forceinline__ long long okey(double x) {
-    long long b = __double_as_longlong(x);
-    return b >= 0 ? b : (b ^ 0x7fffffffffffffffLL);
-}
 
 // append every q in [q0, q1), q != p, with d2 <= r2acc; cnt may exceed the buffer
 __device__ __forceinline__ int gather(const Grid &g, int p, float4 hp, float4 lp, int q0, int q1, float r2acc, int cnt,
@@ -899,7 +911,7 @@ __device__ __forceinline__ int gather(const Grid &g, int p, float4 hp, float4 lp
 // WPB warps per block; knn_target: the number of candidates the first radius
 // aims at when the cell has no radius hint from a previous evaluation
 template <int WPB>
-__global__ void __launch_bounds__(WPB * 32) k_topo_warp(Grid g, CellOut out, CellBuf cb, int *__restrict__ next_list,
+__global__ void __launch_bounds__(WPB * 32, 24 / WPB) k_topo_warp(Grid g, CellOut out, CellBuf cb, int *__restrict__ next_list,
                                                         unsigned *__restrict__ next_count, DevStatus *st,
                                                         float knn_target) {
     __shared__ float s_d2[WPB][kWarpCand];
@@ -934,7 +946,7 @@ __global__ void __launch_bounds__(WPB * 32) k_topo_warp(Grid g, CellOut out, Cel
         const float rmax = 0.2829f;  // sin(theta) <= 0.28 keeps caps off the far faces
         float r;
         {
-            const float hint = out.radius ? out.radius[i] : 0.0f;
+            const float hint = hp.w;  // the radius hint travels with the coordinates
             if (hint > 0.0f) {
                 r = hint;
             } else {
@@ -1173,22 +1185,40 @@ __global__ void __launch_bounds__(WPB * 32) k_topo_warp(Grid g, CellOut out, Cel
             }
             continue;
         }
-        // ---- canonical order: start at the lexicographically smallest neighbour
-        long long kx = 0x7fffffffffffffffLL, ky = kx, kz = kx;
-        if (lane < nv) {
-            const P4 zn = g.zs[g_o];
-            kx = okey(zn.x);
-            ky = okey(zn.y);
-            kz = okey(zn.z);
-        }
-        int best = lane;
+        // ---- canonical order: start at the neighbour with the smallest key
+        // (hi.x, lo.x, hi.y, lo.y, hi.z, lo.z) of its FP32 pair coordinates, a
+        // function of the point alone; the first key decides unless it ties
+        int best;
+        {
+            unsigned k0 = 0xffffffffu;
+            float4 nh = make_float4(0, 0, 0, 0);
+            if (lane < nv) {
+                nh = g.zf[g_o];
+                k0 = okey32(nh.x);
+            }
+            const unsigned kmin = __reduce_min_sync(kFull, k0);
+            const unsigned tie = __ballot_sync(kFull, k0 == kmin);
+            best = __ffs(tie) - 1;
+            if (__popc(tie) > 1) {
+                // rare: resolve on the whole key among the tied lanes
+                unsigned long long kx = ~0ull, ky = kx, kz = kx;
+                if ((tie >> lane) & 1u) {
+                    const float4 nl = g.zl[g_o];
+                    kx = ((unsigned long long)okey32(nh.x) << 32) | okey32(nl.x);
+                    ky = ((unsigned long long)okey32(nh.y) << 32) | okey32(nl.y);
+                    kz = ((unsigned long long)okey32(nh.z) << 32) | okey32(nl.z);
+                }
+                best = lane;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const long long ox = __shfl_xor_sync(kFull, kx, o), oy = __shfl_xor_sync(kFull, ky, o),
-                            oz = __shfl_xor_sync(kFull, kz, o);
-            const int ob = __shfl_xor_sync(kFull, best, o);
-            const bool less = ox < kx || (ox == kx && (oy < ky || (oy == ky && (oz < kz || (oz == kz && ob < best)))));
-            if (less) { kx = ox; ky = oy; kz = oz; best = ob; }
+                for (int o = 16; o > 0; o >>= 1) {
+                    const unsigned long long ox = __shfl_xor_sync(kFull, kx, o), oy = __shfl_xor_sync(kFull, ky, o),
+                                             oz = __shfl_xor_sync(kFull, kz, o);
+                    const int ob = __shfl_xor_sync(kFull, best, o);
+                    const bool less =
+                        ox < kx || (ox == kx && (oy < ky || (oy == ky && (oz < kz || (oz == kz && ob < best)))));
+                    if (less) { kx = ox; ky = oy; kz = oz; best = ob; }
+                }
+            }
         }
         const int rg = __shfl_sync(kFull, g_o, (best + lane) % nv);
         if (lane < nv) {
@@ -1470,7 +1500,8 @@ __global__ void __launch_bounds__(256) k_cell_sum(Grid g, CellOut out, CellBuf c
 }  // namespace
 
 void bin_points(const double *z, const Grid &g, int *bin_of, int *count, int *start, int *cursor, int *scan_tmp,
-                P4 *zs, float4 *zf, float4 *zl, int *sidx, DevStatus *st, cudaStream_t s, int64_t *launches) {
+                P4 *zs, float4 *zf, float4 *zl, int *sidx, const float *hint, DevStatus *st, cudaStream_t s,
+                int64_t *launches) {
     const int n = g.n, nbins = g.nbins;
     Grid gb = g;
     gb.bstart = start;
@@ -1480,7 +1511,7 @@ void bin_points(const double *z, const Grid &g, int *bin_of, int *count, int *st
     exclusive_scan(count, start, nbins, scan_tmp, s, launches);
     k_set_total<<<1, 1, 0, s>>>(start, nbins, n);
     cudaMemcpyAsync(cursor, start, sizeof(int) * nbins, cudaMemcpyDeviceToDevice, s);
-    k_bin_scatter<<<blocks, 256, 0, s>>>(z, n, bin_of, cursor, zs, zf, zl, sidx);
+    k_bin_scatter<<<blocks, 256, 0, s>>>(z, n, bin_of, cursor, zs, zf, zl, sidx, hint);
     k_bin_sort<<<(nbins + 255) / 256, 256, 0, s>>>(start, nbins, zs, zf, zl, sidx);
     (*launches) += 4;
 }

@@ -65,8 +65,8 @@ void enqueue_eval(EvalSet &E, int64_t *launches, int64_t *cell_launches) {
     cudaMemsetAsync(E.d_st, 0, sizeof(DevStatus), s);
     cudaMemsetAsync(E.d_ist, 0, sizeof(DevStatus) * E.B, s);
     Grid g = make_grid(E);
-    bin_points(E.zt, g, E.bin_of, E.count, E.start, E.cursor, E.scan_tmp, E.zs, E.zf, E.zl, E.sidx, E.d_st, s,
-               launches);
+    bin_points(E.zt, g, E.bin_of, E.count, E.start, E.cursor, E.scan_tmp, E.zs, E.zf, E.zl, E.sidx, E.radius, E.d_st,
+               s, launches);
     CellOut out;
     memset(&out, 0, sizeof(out));
     out.grad = E.gt;

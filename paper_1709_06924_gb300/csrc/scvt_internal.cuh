@@ -66,7 +66,7 @@ struct Grid {
     int G;                  // bins per face edge (single problem)
     int nbins;              // bins (all problems)
     const P4 *zs;           // generators in bin order (w unused)
-    const float4 *zf;       // the same, rounded to FP32 (hi part)
+    const float4 *zf;       // the same, rounded to FP32 (hi part); w = search-radius hint (0 = none)
     const float4 *zl;       // FP32 remainder z - hi (lo part): hi + lo carries ~48 bits
     const int *sidx;        // bin-order position -> original index
     const int *bstart;      // nbins + 1 offsets into zs
@@ -111,9 +111,11 @@ struct CellBuf {
 
 // ---- binning (cells.cu) ----
 // g supplies n, G / nbins and the batch fields (inst, pinst, ist); zs, zf,
-// zl, sidx and bstart (= start) are written here
+// zl, sidx and bstart (= start) are written here.  hint (nullable): search
+// radius per original index, carried into zf[].w
 void bin_points(const double *z, const Grid &g, int *bin_of, int *count, int *start, int *cursor, int *scan_tmp,
-                P4 *zs, float4 *zf, float4 *zl, int *sidx, DevStatus *st, cudaStream_t s, int64_t *launches);
+                P4 *zs, float4 *zf, float4 *zl, int *sidx, const float *hint, DevStatus *st, cudaStream_t s,
+                int64_t *launches);
 
 // Launch shape and search parameters of an evaluation.  None of them changes
 // a result: the cell of a generator is unique, its corners are computed from

@@ -152,7 +152,7 @@ extern "C" scvt_status scvt_energy_grad_static(int64_t n, const scvt_density *rh
     grid.bstart = start;
     grid.rho0 = to_device_density(*rho);
     grid.rho0f = to_density32(grid.rho0);
-    bin_points(z, grid, bin_of, count, start, cursor, scan_tmp, zs, zf, zl, sidx, st, s, &launches);
+    bin_points(z, grid, bin_of, count, start, cursor, scan_tmp, zs, zf, zl, sidx, nullptr, st, s, &launches);
     CellOut out;
     out.grad = g;
     out.hdiag = hd;
