@@ -364,12 +364,16 @@ def run_ours(args, w):
     # stream around each launch inside the timed region
     quad_ms = st["cell_kernel_ms"] / max(st["cell_kernel_timed"], 1)
     if prec == 0:
-        flops_gen = fp64_flops_per_generator(w.density.kind)
+        sfrac = st["series_cells"] / max(w.n * st["evaluations"], 1)
+        slen = st["series_terms"] / max(st["series_cells"], 1)
+        flops_gen = fp64_flops_per_generator(w.density.kind, sfrac, slen)
         peak = fp64_peak_tflops()
         achieved = w.n * flops_gen / (quad_ms * 1e-3) / 1e12
         roofline = {"bound": "alu", "kernel": "k_quad", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                     "frac": achieved / peak, "traffic": quad_traffic_bytes(w.n),
                     "flops_per_generator": flops_gen, "avg_launch_ms": quad_ms,
+                    "series_cell_fraction": sfrac, "series_terms_avg": slen,
+                    "flops_per_generator_direct_density": fp64_flops_per_generator(w.density.kind),
                     "peak_source": "derived FP64 pipe peak: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz "
                                    "(no FP64 figure in the measured-peaks file; a DFMA microbenchmark on this "
                                    "pool measured 1.006 TFLOP/s)",
@@ -496,22 +500,29 @@ def run_ours(args, w):
 EXP_DFMA = 17.9
 
 
-def fp64_flops_per_generator(kind: int) -> float:
-    """FP64 work of the cell quadrature per generator, in flop equivalents.
+def fp64_flops_per_generator(kind: int, series_frac: float = 0.0, series_len: float = 0.0) -> float:
+    """FP64 work of the quadrature kernel per generator, in flop equivalents.
 
     Per Voronoi edge the method integrates two signed sub-triangles (Sec.
     3.2.2): per sub-triangle the Van Oosterom-Strackee area (differences,
     cross and dot products: 38 flops, one atan2) and 7 rule points; per point
     the projected point (combination, norm, rsqrt, scale: 37 + rsqrt), the
     density, the weight and the accumulation of m, c and |p - z|^2 (24).  The
-    tanh cap density costs a cross product, a norm and a dot (19), sqrt,
-    atan2, exp and a division (its logistic form) (+5); X3 costs 6.  A transcendental is
-    charged what it costs on this GPU in FMA-pipe time (per-call costs
-    measured with CUDA events, in DFMA equivalents x 2 flop).  The cell of a
-    generator has 6 edges on average (Euler: 2E = 6N - 12).
+    tanh cap evaluated directly costs a cross product, a norm and a dot (19),
+    sqrt, atan2, exp and a division (its logistic form) (+5); from the
+    cell's Taylor series it costs a dot, a difference and a Horner sweep of
+    series_len terms (6 + 2 series_len), for the fraction series_frac of the
+    cells that use one (the series themselves are built by a separate
+    kernel).  X3 costs 6.  A transcendental is charged what it costs on this
+    GPU in FMA-pipe time (per-call costs measured with CUDA events, in DFMA
+    equivalents x 2 flop).  The cell of a generator has 6 edges on average
+    (Euler: 2E = 6N - 12).
     """
     rsqrt, sqrt, atan2, exp, div = 2 * 6.9, 2 * 9.6, 2 * 41.0, 2 * EXP_DFMA, 2 * 10.4
-    dens = {0: 0.0, 1: 6.0, 2: 24.0 + sqrt + atan2 + exp + div, 3: 28.0 + sqrt + atan2 + exp + div}[kind]
+    direct = {0: 0.0, 1: 6.0, 2: 24.0 + sqrt + atan2 + exp + div, 3: 28.0 + sqrt + atan2 + exp + div}[kind]
+    dens = direct
+    if kind >= 2:
+        dens = series_frac * (6.0 + 2.0 * series_len) + (1.0 - series_frac) * direct
     point = 37.0 + rsqrt + 24.0 + dens
     subtri = 38.0 + atan2 + 7 * point
     mu = 11.0 + rsqrt

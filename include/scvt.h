@@ -120,6 +120,8 @@ typedef struct {
     double lbfgs_ms;            /* device time of the two-loop / update kernels (profiling on) */
     int64_t cell_kernel_timed;  /* first-pass launches included in cell_kernel_ms */
     int64_t bytes_device;       /* device memory held by the handle */
+    int64_t series_cells;       /* FP64 form: cells whose density came from their Taylor series */
+    int64_t series_terms;       /* ... and the sum of those series' lengths */
 } scvt_stats;
 
 typedef struct scvt_handle scvt_handle;
@@ -185,7 +187,7 @@ scvt_status scvt_lbfgs_direction(scvt_handle *h, const double *g, const double *
  * host that forbids cudaMalloc after start-up).  The paper has no
  * counterpart: this is a deployment variant of scvt_energy_grad.
  * It needs no handle and allocates nothing: its scratch is one fixed array
- * in device memory (about 16.3 MB, held on every GPU that loads the library
+ * in device memory (about 19.1 MB, held on every GPU that loads the library
  * until the process exits), sized for n <= SCVT_STATIC_MAX_N.
  * n: generators (4 <= n <= SCVT_STATIC_MAX_N, else SCVT_ERR_INVALID before
  * any device work).  rho: host.  z: N x 3 device.  cuda_stream: cudaStream_t

@@ -44,7 +44,8 @@ struct Bufs {
     float4 *zf = nullptr, *zl = nullptr;
     P4 *cvx = nullptr;
     int *cdeg = nullptr, *cnb = nullptr, *eoff = nullptr, *ecell = nullptr, *escan = nullptr;
-    double *eacc = nullptr;
+    double *eacc = nullptr, *ser = nullptr;
+    int *serK = nullptr;
     float4 *vo = nullptr;
     int *bin_of = nullptr, *count = nullptr, *start = nullptr, *cursor = nullptr, *scan_tmp = nullptr;
     int *sidx = nullptr, *list1 = nullptr, *list2 = nullptr;
@@ -179,6 +180,8 @@ scvt_status evaluate_dev(scvt_handle *H, const double *zdev, double *grad, doubl
     cb.scan_tmp = B.escan;
     cb.eacc = B.eacc;
     cb.vo = B.vo;
+    cb.ser = B.ser;
+    cb.serK = B.serK;
     cell_passes(g, out, cb, B.list1, B.list2, B.st, H->cfg.precision == 1, H->tune, s,
                 H->profiling ? H->ev_cell0 : nullptr, H->profiling ? H->ev_cell1 : nullptr, L,
                 &H->stats.cell_launches);
@@ -192,6 +195,8 @@ scvt_status evaluate_dev(scvt_handle *H, const double *zdev, double *grad, doubl
     H->stats.evaluations++;
     H->stats.knn_retries += st.retry_count[0];
     H->stats.ambiguous += (int64_t)st.ambiguous;
+    H->stats.series_cells += (int64_t)st.ser_cells;
+    H->stats.series_terms += (int64_t)st.ser_terms;
     if (st.flags & FLAG_BAD_POINT)
         return fail(H, SCVT_ERR_INVALID, "a generator is not finite or not on the unit sphere (| |z|^2 - 1 | > 2e-12)");
     if (st.flags & FLAG_DUPLICATE) return fail(H, SCVT_ERR_INVALID, "duplicate generators");
@@ -287,7 +292,7 @@ void scvt_destroy(scvt_handle *H) {
     if (!H) return;
     Bufs &b = H->b;
     void *ptrs[] = {b.z, b.zt, b.g, b.gt, b.h, b.ht, b.fc, b.q, b.yv, b.nrm, b.mass, b.moment, b.stage_a, b.stage_b,
-                    b.partials, b.scal, b.rho, b.hist, b.zs, b.zf, b.zl, b.cvx, b.cnb, b.cdeg, b.eoff, b.ecell, b.escan, b.eacc, b.vo, b.bin_of, b.count, b.start, b.cursor, b.scan_tmp,
+                    b.partials, b.scal, b.rho, b.hist, b.zs, b.zf, b.zl, b.cvx, b.cnb, b.cdeg, b.eoff, b.ecell, b.escan, b.eacc, b.vo, b.ser, b.serK, b.bin_of, b.count, b.start, b.cursor, b.scan_tmp,
                     b.sidx, b.list1, b.list2, b.deg, b.radius, b.st};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -343,6 +348,7 @@ scvt_status scvt_create(const scvt_config *cfg, void *cuda_stream, scvt_handle *
     AL(b.cdeg, n); AL(b.eoff, n + 1); AL(b.ecell, 6 * (size_t)n); AL(b.escan, 2 * (n / 2048 + 64) + 64);
     AL(b.eacc, 5 * 6 * (size_t)n);
     if (cfg->precision == 1) AL(b.vo, (size_t)n * kCellSlots);
+    if (cfg->precision == 0) { AL(b.ser, (size_t)n * 21); AL(b.serK, n); }
     AL(b.bin_of, n); AL(b.count, nbins); AL(b.start, nbins + 1); AL(b.cursor, nbins);
     AL(b.scan_tmp, 2 * (nbins / 2048 + 64) + 64);
     AL(b.sidx, n); AL(b.list1, n); AL(b.list2, n); AL(b.deg, n); AL(b.radius, n);

@@ -530,9 +530,35 @@ struct Acc {
     double m, cx, cy, cz, e;
 };
 
+// the density at a unit vector p, directly from its definition (kinds 2, 3:
+// geodesic distance d to x_c, the tanh cap in its logistic form)
+__device__ __forceinline__ double rho_direct(const Density &r, double inv_alpha, V3 p) {
+    const V3 xc = mk(r.xc0, r.xc1, r.xc2);
+    V3 cx = crs(p, xc);
+    double d = atan2(sqrt(dot(cx, cx)), dot(p, xc));
+    // (1 - gamma)/2 (tanh(x) + 1) + gamma, as (1 - gamma)/(1 + exp(-2x)) + gamma:
+    // the same function without the cancellation of tanh(x) + 1 for x << 0
+    double rv = (1.0 - r.gamma) / (1.0 + exp(-2.0 * (r.beta - d) * inv_alpha)) + r.gamma;
+    if (r.kind == 3) { rv = rv * rv; rv = rv * rv; }
+    return rv;
+}
+
+// Per-cell Taylor series of the tanh-cap density in u = x_c.p - x_c.z_i
+// (k_rho_series): up to kSerMax coefficients, then the expansion point x_c.z_i.
+constexpr int kSerMax = 20;
+constexpr int kSerStride = kSerMax + 1;
+
+__device__ __forceinline__ double horner(const double *__restrict__ cf, int K, double u) {
+    double r = cf[K - 1];
+    for (int j = K - 2; j >= 0; --j) r = fma(r, u, cf[j]);
+    return r;
+}
+
 // signed spherical triangle (A, B, C) with the 7-point rule; A = z_i.
-// inv_alpha: 1/alpha of the tanh cap.
-__device__ __forceinline__ void tri(const Density &r, double inv_alpha, V3 A, V3 B, V3 C, Acc &acc) {
+// inv_alpha: 1/alpha of the tanh cap.  ser / K: the cell's density series
+// (K = 0: evaluate the density directly).
+__device__ __forceinline__ void tri(const Density &r, double inv_alpha, V3 A, V3 B, V3 C, Acc &acc,
+                                    const double *ser = nullptr, int K = 0) {
     V3 cr = crs(sub(B, A), sub(C, A));
     double det = dot(A, cr);
     double den = 1.0 + dot(A, B) + dot(B, C) + dot(C, A);
@@ -548,13 +574,10 @@ __device__ __forceinline__ void tri(const Density &r, double inv_alpha, V3 A, V3
         } else if (r.kind == 1) {
             double z2 = p.z * p.z;
             rv = (1.0 - r.gamma) * z2 * z2 + r.gamma;
+        } else if (K > 0) {
+            rv = horner(ser, K, dot(p, xc) - ser[kSerMax]);
         } else {
-            V3 cx = crs(p, xc);
-            double d = atan2(sqrt(dot(cx, cx)), dot(p, xc));
-            // (1 - gamma)/2 (tanh(x) + 1) + gamma, as (1 - gamma)/(1 + exp(-2x)) + gamma:
-            // the same function without the cancellation of tanh(x) + 1 for x << 0
-            rv = (1.0 - r.gamma) / (1.0 + exp(-2.0 * (r.beta - d) * inv_alpha)) + r.gamma;
-            if (r.kind == 3) { rv = rv * rv; rv = rv * rv; }
+            rv = rho_direct(r, inv_alpha, p);
         }
         double wr = kQw[k] * area * rv;
         V3 dp = sub(p, A);
@@ -1256,6 +1279,144 @@ __global__ void __launch_bounds__(256) k_corners(Grid g, CellBuf cb) {
     cb.vx[(size_t)p * kCellSlots + k] = P4{v.x, v.y, v.z, 0.0};
 }
 
+// -------------------------------------------- density series per cell
+// The tanh cap depends on p only through c = x_c.p, and inside one cell c
+// stays within a small interval around c_i = x_c.z_i.  Its Taylor series in
+// u = c - c_i is built once per cell by power-series arithmetic on the exact
+// composition rho = gamma + (1 - gamma) / (1 + exp(-x)), x = 2 (beta - acos c)
+// / alpha:  (1 - (c_i + u)^2)^(-1/2) by the binomial recurrence of
+// h^(-1/2), h = 1 + tau1 u + tau2 u^2, integrated to acos; exp of a series;
+// the reciprocal of a series; squared twice for the 4th power.  The number
+// of terms K is the first at which two successive terms fall below 1e-17 of
+// the value over |u| <= U (U bounds |u| over the cell's corners, edge
+// midpoints and the rule points between them); the truncated series is then
+// compared with the direct formula at the cell's two corners of extreme u
+// and used only if both agree to 1e-14 (the direct formula's own rounding
+// sensitivity is ~1e-14 for alpha = 0.05; the parity budget is 1e-12).
+// Otherwise (cells near the cap
+// centre or its antipode, where acos is singular, or cells wide against
+// alpha) K = 0 and the quadrature evaluates the density directly.
+__device__ __forceinline__ void count_series(int K, DevStatus *st) {
+    const unsigned cells = __reduce_add_sync(0xffffffffu, K > 0 ? 1u : 0u);
+    const unsigned terms = __reduce_add_sync(0xffffffffu, (unsigned)K);
+    if ((threadIdx.x & 31) == 0 && cells) {
+        atomicAdd(&st->ser_cells, (unsigned long long)cells);
+        atomicAdd(&st->ser_terms, (unsigned long long)terms);
+    }
+}
+
+__device__ void series_of_cell(const Grid &g, const CellBuf &cb, int p, double *__restrict__ ser,
+                               int *__restrict__ serK, int &Kout);
+
+__global__ void __launch_bounds__(128) k_rho_series(Grid g, CellBuf cb, double *__restrict__ ser, int *__restrict__ serK,
+                                                    DevStatus *st) {
+    const int p0 = blockIdx.x * blockDim.x + threadIdx.x;
+    int K = 0;
+    if (p0 < g.n) series_of_cell(g, cb, p0, ser, serK, K);
+    count_series(K, st);
+}
+
+__device__ void series_of_cell(const Grid &g, const CellBuf &cb, int p, double *__restrict__ ser,
+                               int *__restrict__ serK, int &Kout) {
+    const int deg = cb.deg[p];
+    const int b = view_of(g, p).b;
+    const Density r = g.rho ? g.rho[b] : g.rho0;
+    if (deg == 0 || r.kind < 2) {
+        serK[p] = 0;
+        return;
+    }
+    const V3 zi = ld(g.zs + p);
+    const V3 xc = mk(r.xc0, r.xc1, r.xc2);
+    const double ci = dot(xc, zi);
+    const double si = sqrt(dot(crs(xc, zi), crs(xc, zi)));
+    const double inv_alpha = 1.0 / r.alpha;
+    // the range of u over the cell
+    double umax = 0.0, umin = 0.0, h2 = 0.0;
+    int kmax = 0, kmin = 0;
+    for (int k = 0; k < deg; ++k) {
+        const V3 v = ld(cb.vx + (size_t)p * kCellSlots + k);
+        const double u = dot(xc, v) - ci;
+        if (u > umax) { umax = u; kmax = k; }
+        if (u < umin) { umin = u; kmin = k; }
+        const V3 dv = sub(v, zi);
+        h2 = fmax(h2, dot(dv, dv));
+        const V3 mu = unit(add(zi, ld(g.zs + cb.nb[(size_t)p * kCellSlots + k])));
+        const double um = dot(xc, mu) - ci;
+        umax = fmax(umax, um);
+        umin = fmin(umin, um);
+    }
+    const double U = 1.05 * fmax(umax, -umin) + fabs(ci) * h2;
+    int K = 0;
+    double cf[kSerMax + 1];
+    if (si > 1e-6) {
+        // h^(-1/2) with h = 1 + tau1 u + tau2 u^2; then acos, x, exp(-x), 1/(1+exp(-x))
+        const double tau1 = -2.0 * ci / (si * si), tau2 = -1.0 / (si * si);
+        double gs[kSerMax + 1], xs[kSerMax + 1], es[kSerMax + 1];
+        gs[0] = 1.0;
+        for (int k = 1; k <= kSerMax; ++k) {
+            double t = (0.5 - k) * tau1 * gs[k - 1];
+            if (k >= 2) t += (1.0 - k) * tau2 * gs[k - 2];
+            gs[k] = t / k;
+        }
+        const double theta = atan2(si, ci);
+        xs[0] = 2.0 * (r.beta - theta) * inv_alpha;
+        for (int k = 1; k <= kSerMax; ++k) xs[k] = 2.0 * inv_alpha * gs[k - 1] / (k * si);  // -2 a_k / alpha
+        es[0] = exp(-xs[0]);
+        for (int k = 1; k <= kSerMax; ++k) {
+            double t = 0.0;
+            for (int j = 1; j <= k; ++j) t += j * xs[j] * es[k - j];
+            es[k] = -t / k;
+        }
+        const double r0 = 1.0 / (1.0 + es[0]);
+        cf[0] = r0;
+        for (int k = 1; k <= kSerMax; ++k) {
+            double t = 0.0;
+            for (int j = 1; j <= k; ++j) t += es[j] * cf[k - j];
+            cf[k] = -r0 * t;
+        }
+        for (int k = 0; k <= kSerMax; ++k) cf[k] *= (1.0 - r.gamma);
+        cf[0] += r.gamma;
+        if (r.kind == 3) {
+            double sq[kSerMax + 1];
+            for (int pass = 0; pass < 2; ++pass) {
+                for (int k = 0; k <= kSerMax; ++k) {
+                    double t = 0.0;
+                    for (int j = 0; j <= k; ++j) t += cf[j] * cf[k - j];
+                    sq[k] = t;
+                }
+                for (int k = 0; k <= kSerMax; ++k) cf[k] = sq[k];
+            }
+        }
+        // terms: first k with |c_k| U^k and |c_k+1| U^(k+1) below 1e-17 |c_0|
+        const double tol = 1e-17 * fabs(cf[0]);
+        double Uk = U;
+        for (int k = 1; k < kSerMax; ++k) {
+            if (fabs(cf[k]) * Uk <= tol && fabs(cf[k + 1]) * Uk * U <= tol) {
+                K = k;
+                break;
+            }
+            Uk *= U;
+        }
+        if (K > 0) {
+            // both extreme corners must agree with the direct formula
+            const int ks[2] = {kmax, kmin};
+            for (int t = 0; t < 2 && K > 0; ++t) {
+                const V3 v = ld(cb.vx + (size_t)p * kCellSlots + ks[t]);
+                const double d = rho_direct(r, inv_alpha, v);
+                const double sv = horner(cf, K, dot(xc, v) - ci);
+                if (!(fabs(sv - d) <= 1e-14 * d)) K = 0;
+            }
+        }
+    }
+    serK[p] = K;
+    Kout = K;
+    if (K > 0) {
+        double *o = ser + (size_t)p * kSerStride;
+        for (int k = 0; k < K; ++k) o[k] = cf[k];
+        o[kSerMax] = ci;
+    }
+}
+
 // -------------------------------------------------------------- quadrature
 // Edge list: cells' edges laid end to end in bin order (eoff = exclusive
 // scan of the degrees), ecell[e] = the cell of edge e.
@@ -1284,9 +1445,11 @@ __global__ void __launch_bounds__(512) k_quad(Grid g, CellBuf cb, int ecap) {
     const V3 mu = unit(add(zi, ld(g.zs + cb.nb[(size_t)p * kCellSlots + k])));
     const Density rho = g.rho ? g.rho[view_of(g, p).b] : g.rho0;
     const double inv_alpha = 1.0 / rho.alpha;
+    const int K = cb.serK ? cb.serK[p] : 0;
+    const double *ser = cb.ser + (size_t)p * kSerStride;
     Acc acc = {0, 0, 0, 0, 0};
-    tri(rho, inv_alpha, zi, va, mu, acc);
-    tri(rho, inv_alpha, zi, mu, vb, acc);
+    tri(rho, inv_alpha, zi, va, mu, acc, ser, K);
+    tri(rho, inv_alpha, zi, mu, vb, acc, ser, K);
     double *ea = cb.eacc;
     ea[e] = acc.m;
     ea[(size_t)ecap + e] = acc.cx;
@@ -1608,6 +1771,7 @@ void cell_passes(const Grid &g, const CellOut &out, const CellBuf &cb, int *list
         k_cell_sum<true><<<cblocks, 256, 0, s>>>(g, out, cb, ecap, st);
     } else {
         k_corners<<<(ecap + 255) / 256, 256, 0, s>>>(g, cb);
+        if (cb.serK) k_rho_series<<<(g.n + 127) / 128, 128, 0, s>>>(g, cb, cb.ser, cb.serK, st);
         if (ev0) cudaEventRecord(ev0, s);
         k_quad<<<eblocks, qb, 0, s>>>(g, cb, ecap);
         if (ev1) cudaEventRecord(ev1, s);

@@ -82,6 +82,8 @@ void enqueue_eval(EvalSet &E, int64_t *launches, int64_t *cell_launches) {
     cb.scan_tmp = E.escan;
     cb.eacc = E.eacc;
     cb.vo = E.vo;
+    cb.ser = E.ser;
+    cb.serK = E.serK;
     cell_passes(g, out, cb, E.list1, E.list2, E.d_st, E.precision == 1, E.tune, s, nullptr, nullptr, launches,
                 cell_launches);
     reduce_eval_batch(E.B, E.max_nb, E.d_inst, E.d_pbase, E.d_active, E.fc, E.gt, E.q, E.nrm, E.partials, E.d_ist, s,
@@ -149,6 +151,7 @@ int64_t evalset_bytes(int64_t cap_n, int cap_b, int precision) {
                       + 32 + 32 + 16 * 32 + 16 * 4 + 4 + 4 + 24 + 240  // zs, zf+zl, cvx, cnb, cdeg, eoff, ecell, eacc
                       + 4 * 4;                // bin_of, sidx, list1, list2
     if (precision == 1) per_row += 16 * 16;   // vo
+    else per_row += 21 * 8 + 4;              // density series
     return N * per_row + nb * 12 + (int64_t)max_partials(cap_n, cap_b) * 8 + (int64_t)cap_b * 512 + (1 << 20);
 }
 
@@ -170,6 +173,7 @@ cudaError_t evalset_alloc(EvalSet &E, int64_t cap_n, int cap_b, int precision, c
     AL(E.cdeg, N); AL(E.eoff, N + 1); AL(E.ecell, 6 * N); AL(E.escan, 2 * (N / 2048 + 64) + 64);
     AL(E.eacc, 5 * 6 * N);
     if (precision == 1) AL(E.vo, N * kCellSlots);
+    if (precision == 0) { AL(E.ser, N * 21); AL(E.serK, N); }
     AL(E.bin_of, N); AL(E.count, nb); AL(E.start, nb + 1); AL(E.cursor, nb); AL(E.scan_tmp, 2 * (nb / 2048 + 64) + 64);
     AL(E.sidx, N); AL(E.list1, N); AL(E.list2, N);
 #undef AL
@@ -188,7 +192,7 @@ void evalset_free(EvalSet &E) {
     E.graph = nullptr;
     void *ptrs[] = {E.d_inst, E.d_pinst, E.d_pbase, E.d_active, E.d_rho, E.d_rhof, E.d_ist, E.d_st, E.zt, E.gt,
                     E.ht, E.fc, E.q, E.nrm, E.radius, E.partials, E.zs, E.zf, E.zl, E.cvx, E.cnb, E.cdeg, E.eoff,
-                    E.ecell, E.escan, E.eacc, E.vo, E.bin_of, E.count, E.start, E.cursor, E.scan_tmp, E.sidx,
+                    E.ecell, E.escan, E.eacc, E.vo, E.ser, E.serK, E.bin_of, E.count, E.start, E.cursor, E.scan_tmp, E.sidx,
                     E.list1, E.list2};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -255,6 +259,8 @@ cudaError_t evalset_run(EvalSet &E, scvt_stats *stats) {
         stats->cell_launches += E.graph_cell_launches;
         stats->knn_retries += E.h_st->retry_count[0];
         stats->ambiguous += (int64_t)E.h_st->ambiguous;
+        stats->series_cells += (int64_t)E.h_st->ser_cells;
+        stats->series_terms += (int64_t)E.h_st->ser_terms;
     }
     return cudaSuccess;
 }

@@ -51,7 +51,8 @@ struct EvalSet {
     P4 *zs = nullptr, *cvx = nullptr;
     float4 *zf = nullptr, *zl = nullptr, *vo = nullptr;
     int *cdeg = nullptr, *cnb = nullptr, *eoff = nullptr, *ecell = nullptr, *escan = nullptr;
-    double *eacc = nullptr;
+    double *eacc = nullptr, *ser = nullptr;
+    int *serK = nullptr;
     int *bin_of = nullptr, *count = nullptr, *start = nullptr, *cursor = nullptr, *scan_tmp = nullptr;
     int *sidx = nullptr, *list1 = nullptr, *list2 = nullptr;
     // the captured evaluation

@@ -35,6 +35,8 @@ struct DevStatus {
     unsigned long long maxmove_bits;// max_i |s_i| as the bits of a nonnegative double
     double dots[4];                 // y.s, y.y, s.s, g.q
     unsigned differs;               // set by vec_differs
+    unsigned long long ser_cells;   // cells whose density came from a series
+    unsigned long long ser_terms;   // their terms, summed
 };
 
 struct Density {
@@ -107,6 +109,8 @@ struct CellBuf {
     int *scan_tmp;     // scratch of the scan over n (2 * (n / 2048 + 64) + 64 ints)
     double *eacc;      // 5 * 6n: per-edge sums (m, c or o, F), component-major; FP32 in the mixed form
     float4 *vo;        // n * kCellSlots corner offsets v - z_i in FP32 (mixed precision only)
+    double *ser;       // n * 21: per-cell density series (20 coefficients, expansion point); FP64 form
+    int *serK;         // n: terms of the cell's series, 0 = evaluate directly; null = no series
 };
 
 // ---- binning (cells.cu) ----

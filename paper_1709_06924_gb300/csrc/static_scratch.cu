@@ -62,7 +62,9 @@ constexpr size_t oEoff = oG + up(sizeof(double) * 3 * kMaxN);
 constexpr size_t oEcell = oEoff + up(sizeof(int) * (kMaxN + 1));
 constexpr size_t oEscan = oEcell + up(sizeof(int) * 6 * kMaxN);
 constexpr size_t oEacc = oEscan + up(sizeof(int) * (2 * (kMaxN / 2048 + 64) + 64));
-constexpr size_t kBytes = oEacc + up(sizeof(double) * 5 * 6 * kMaxN);  // about 16.3 MB
+constexpr size_t oSer = oEacc + up(sizeof(double) * 5 * 6 * kMaxN);
+constexpr size_t oSerK = oSer + up(sizeof(double) * 21 * kMaxN);
+constexpr size_t kBytes = oSerK + up(sizeof(int) * kMaxN);  // about 19.1 MB
 
 __device__ __align__(256) unsigned char g_scratch[kBytes];
 
@@ -172,6 +174,8 @@ extern "C" scvt_status scvt_energy_grad_static(int64_t n, const scvt_density *rh
     cb.scan_tmp = (int *)(base + oEscan);
     cb.eacc = (double *)(base + oEacc);
     cb.vo = nullptr;
+    cb.ser = (double *)(base + oSer);
+    cb.serK = (int *)(base + oSerK);
     cell_passes(grid, out, cb, list1, list2, st, false, Tune(), s, nullptr, nullptr, &launches, &cell_launches);
     reduce_eval(N, fc, g, nullptr, nullptr, partials, st, s, &launches);
     DevStatus hs;
