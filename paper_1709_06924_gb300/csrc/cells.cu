@@ -547,6 +547,9 @@ __device__ __forceinline__ double rho_direct(const Density &r, double inv_alpha,
 // (k_rho_series): up to kSerMax coefficients, then the expansion point x_c.z_i.
 constexpr int kSerMax = 20;
 constexpr int kSerStride = kSerMax + 1;
+__constant__ double kInv[kSerMax + 1] = {0.0,        1.0,        1.0 / 2,  1.0 / 3,  1.0 / 4,  1.0 / 5,  1.0 / 6,
+                                         1.0 / 7,    1.0 / 8,    1.0 / 9,  1.0 / 10, 1.0 / 11, 1.0 / 12, 1.0 / 13,
+                                         1.0 / 14,   1.0 / 15,   1.0 / 16, 1.0 / 17, 1.0 / 18, 1.0 / 19, 1.0 / 20};
 
 __device__ __forceinline__ double horner(const double *__restrict__ cf, int K, double u) {
     double r = cf[K - 1];
@@ -1340,8 +1343,8 @@ __device__ void series_of_cell(const Grid &g, const CellBuf &cb, int p, double *
         if (u < umin) { umin = u; kmin = k; }
         const V3 dv = sub(v, zi);
         h2 = fmax(h2, dot(dv, dv));
-        const V3 mu = unit(add(zi, ld(g.zs + cb.nb[(size_t)p * kCellSlots + k])));
-        const double um = dot(xc, mu) - ci;
+        const V3 sm = add(zi, ld(g.zs + cb.nb[(size_t)p * kCellSlots + k]));
+        const double um = dot(xc, sm) * rsqrt(dot(sm, sm)) - ci;  // the edge midpoint
         umax = fmax(umax, um);
         umin = fmin(umin, um);
     }
@@ -1349,53 +1352,60 @@ __device__ void series_of_cell(const Grid &g, const CellBuf &cb, int p, double *
     int K = 0;
     double cf[kSerMax + 1];
     if (si > 1e-6) {
-        // h^(-1/2) with h = 1 + tau1 u + tau2 u^2; then acos, x, exp(-x), 1/(1+exp(-x))
-        const double tau1 = -2.0 * ci / (si * si), tau2 = -1.0 / (si * si);
-        double gs[kSerMax + 1], xs[kSerMax + 1], es[kSerMax + 1];
+        // h^(-1/2) with h = 1 + tau1 u + tau2 u^2; then acos, x, exp(-x), 1/(1+exp(-x)),
+        // built term by term until two successive terms are negligible over |u| <= U
+        const double isi = 1.0 / si;
+        const double tau1 = -2.0 * ci * isi * isi, tau2 = -isi * isi;
+        const double c2a = 2.0 * inv_alpha * isi;
+        const double om = 1.0 - r.gamma;
+        double gs[kSerMax + 1], xs[kSerMax + 1], es[kSerMax + 1], rs[kSerMax + 1], sq[kSerMax + 1];
         gs[0] = 1.0;
+        xs[0] = 2.0 * (r.beta - atan2(si, ci)) * inv_alpha;
+        es[0] = exp(-xs[0]);
+        const double r0 = 1.0 / (1.0 + es[0]);
+        rs[0] = r0;
+        cf[0] = om * r0 + r.gamma;
+        if (r.kind == 3) {
+            sq[0] = cf[0] * cf[0];
+            cf[0] = sq[0] * sq[0];
+        }
+        const double tol = 1e-17 * fabs(cf[0]);
+        double Uk = 1.0;
+        int small = 0;
         for (int k = 1; k <= kSerMax; ++k) {
+            const double ik = kInv[k];
             double t = (0.5 - k) * tau1 * gs[k - 1];
             if (k >= 2) t += (1.0 - k) * tau2 * gs[k - 2];
-            gs[k] = t / k;
-        }
-        const double theta = atan2(si, ci);
-        xs[0] = 2.0 * (r.beta - theta) * inv_alpha;
-        for (int k = 1; k <= kSerMax; ++k) xs[k] = 2.0 * inv_alpha * gs[k - 1] / (k * si);  // -2 a_k / alpha
-        es[0] = exp(-xs[0]);
-        for (int k = 1; k <= kSerMax; ++k) {
-            double t = 0.0;
+            gs[k] = t * ik;
+            xs[k] = c2a * gs[k - 1] * ik;  // -2 a_k / alpha
+            t = 0.0;
             for (int j = 1; j <= k; ++j) t += j * xs[j] * es[k - j];
-            es[k] = -t / k;
-        }
-        const double r0 = 1.0 / (1.0 + es[0]);
-        cf[0] = r0;
-        for (int k = 1; k <= kSerMax; ++k) {
-            double t = 0.0;
-            for (int j = 1; j <= k; ++j) t += es[j] * cf[k - j];
-            cf[k] = -r0 * t;
-        }
-        for (int k = 0; k <= kSerMax; ++k) cf[k] *= (1.0 - r.gamma);
-        cf[0] += r.gamma;
-        if (r.kind == 3) {
-            double sq[kSerMax + 1];
-            for (int pass = 0; pass < 2; ++pass) {
-                for (int k = 0; k <= kSerMax; ++k) {
-                    double t = 0.0;
-                    for (int j = 0; j <= k; ++j) t += cf[j] * cf[k - j];
-                    sq[k] = t;
+            es[k] = -t * ik;
+            t = 0.0;
+            for (int j = 1; j <= k; ++j) t += es[j] * rs[k - j];
+            rs[k] = -r0 * t;
+            if (r.kind == 3) {
+                // (gamma + om r)^4 as the square of the square: sq = rho^2 with
+                // rho_j = om rs_j (+ gamma at j = 0)
+                t = 0.0;
+                for (int j = 0; j <= k; ++j) {
+                    const double rj = j == 0 ? om * rs[0] + r.gamma : om * rs[j];
+                    const double rk = (k - j) == 0 ? om * rs[0] + r.gamma : om * rs[k - j];
+                    t += rj * rk;
                 }
-                for (int k = 0; k <= kSerMax; ++k) cf[k] = sq[k];
-            }
-        }
-        // terms: first k with |c_k| U^k and |c_k+1| U^(k+1) below 1e-17 |c_0|
-        const double tol = 1e-17 * fabs(cf[0]);
-        double Uk = U;
-        for (int k = 1; k < kSerMax; ++k) {
-            if (fabs(cf[k]) * Uk <= tol && fabs(cf[k + 1]) * Uk * U <= tol) {
-                K = k;
-                break;
+                sq[k] = t;
+                t = 0.0;
+                for (int j = 0; j <= k; ++j) t += sq[j] * sq[k - j];
+                cf[k] = t;
+            } else {
+                cf[k] = om * rs[k];
             }
             Uk *= U;
+            small = (fabs(cf[k]) * Uk <= tol) ? small + 1 : 0;
+            if (small == 2) {
+                K = k - 1;  // terms 0 .. k-2; terms k-1 and k are negligible
+                break;
+            }
         }
         if (K > 0) {
             // both extreme corners must agree with the direct formula
