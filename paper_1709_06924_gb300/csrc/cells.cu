@@ -565,7 +565,17 @@ __device__ __forceinline__ void tri(const Density &r, double inv_alpha, V3 A, V3
     V3 cr = crs(sub(B, A), sub(C, A));
     double det = dot(A, cr);
     double den = 1.0 + dot(A, B) + dot(B, C) + dot(C, A);
-    double area = 2.0 * atan2(det, den);
+    // signed area 2 atan(det / den) (Van Oosterom-Strackee); for the small
+    // triangles of a cell |det / den| < 1e-2 and the odd Taylor series of atan
+    // to the x^7 term is exact to 1e-17 relative
+    double area;
+    const double xa = det / den;
+    if (den > 0.0 && fabs(xa) < 1e-2) {
+        const double x2 = xa * xa;
+        area = 2.0 * xa * (1.0 + x2 * (-1.0 / 3.0 + x2 * (0.2 + x2 * (-1.0 / 7.0))));
+    } else {
+        area = 2.0 * atan2(det, den);
+    }
     const V3 xc = mk(r.xc0, r.xc1, r.xc2);
 #pragma unroll 1
     for (int k = 0; k < 7; ++k) {
@@ -847,8 +857,6 @@ __global__ void __launch_bounds__(128) k_topo(Grid g, CellOut out, CellBuf cb,
 // and no FP64 arithmetic is needed except in rare per-lane fallbacks.  Cells
 // this pass cannot certify (or with more than 16 edges, or 32 vertices at
 // some point) go to the retry list of the thread-per-cell passes.
-constexpr int kWarpCand = 64;  // candidate buffer per warp (2 per lane, sorted once)
-constexpr unsigned kFull = 0xffffffffu;
 
 __device__ __forceinline__ float3 dfdiff(const Grid &g, int q, float4 hp, float4 lp) {
     const float4 hq = g.zf[q], lq = g.zl[q];
@@ -910,11 +918,14 @@ __device__ bool outside64(const Grid &g, int p, int gin, int gout, int gnew, uns
 }
 
 
-// append every q in [q0, q1), q != p, with d2 <= r2acc; cnt may exceed the buffer
+// append every q in [q0, q1), q != p, with d2 <= r2acc, scanned by the L lanes
+// of a sub-warp (lane sl, first lane sbase, mask smask); cnt may exceed 2L
+template <int L>
 __device__ __forceinline__ int gather(const Grid &g, int p, float4 hp, float4 lp, int q0, int q1, float r2acc, int cnt,
-                                      float *cd, int *cj, int lane, unsigned *flags) {
-    for (int base = q0; base < q1; base += 32) {
-        const int q = base + lane;
+                                      float *cd, int *cj, int sl, int sbase, unsigned smask, unsigned *flags) {
+    constexpr unsigned lfull = (L == 32) ? 0xffffffffu : ((1u << L) - 1u);
+    for (int base = q0; base < q1; base += L) {
+        const int q = base + sl;
         bool pred = false;
         float d2 = 0.0f;
         if (q < q1 && q != p) {
@@ -923,9 +934,9 @@ __device__ __forceinline__ int gather(const Grid &g, int p, float4 hp, float4 lp
             if (d2 == 0.0f) check_duplicate(g, ld(g.zs + p), q, flags);
             pred = d2 <= r2acc;
         }
-        const unsigned m = __ballot_sync(kFull, pred);
-        const int pos = cnt + __popc(m & ((1u << lane) - 1u));
-        if (pred && pos < kWarpCand) {
+        const unsigned m = (__ballot_sync(smask, pred) >> sbase) & lfull;
+        const int pos = cnt + __popc(m & ((1u << sl) - 1u));
+        if (pred && pos < 2 * L) {
             cd[pos] = d2;
             cj[pos] = q;
         }
@@ -934,24 +945,29 @@ __device__ __forceinline__ int gather(const Grid &g, int p, float4 hp, float4 lp
     return cnt;
 }
 
-// WPB warps per block; knn_target: the number of candidates the first radius
-// aims at when the cell has no radius hint from a previous evaluation
-template <int WPB>
+// WPB warps per block, L lanes per cell (32: one cell per warp, 16: two);
+// every collective runs on the cell's sub-warp.  knn_target: the number of
+// candidates the first radius aims at when the cell has no radius hint
+template <int WPB, int L>
 __global__ void __launch_bounds__(WPB * 32, 24 / WPB) k_topo_warp(Grid g, CellOut out, CellBuf cb, int *__restrict__ next_list,
                                                         unsigned *__restrict__ next_count, DevStatus *st,
                                                         float knn_target) {
-    __shared__ float s_d2[WPB][kWarpCand];
-    __shared__ int s_j[WPB][kWarpCand];
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    float *cd = s_d2[wib];
-    int *cj = s_j[wib];
-    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nw = (gridDim.x * blockDim.x) >> 5;
+    constexpr int C = 2 * L;  // candidate slots per cell
+    constexpr unsigned lfull = (L == 32) ? 0xffffffffu : ((1u << L) - 1u);
+    __shared__ float s_d2[WPB * 32 / L][C];
+    __shared__ int s_j[WPB * 32 / L][C];
+    const int lane = threadIdx.x & 31;
+    const int sl = lane & (L - 1), sbase = lane & ~(L - 1);
+    const unsigned smask = lfull << sbase;
+    float *cd = s_d2[threadIdx.x / L];
+    int *cj = s_j[threadIdx.x / L];
+    const int gs = (blockIdx.x * blockDim.x + threadIdx.x) / L;
+    const int ns = (gridDim.x * blockDim.x) / L;
     const float INF = __int_as_float(0x7f800000);
-    for (int p = gw; p < g.n; p += nw) {
+    for (int p = gs; p < g.n; p += ns) {
         const View v = view_of(g, p);
         if (inactive(g, v.b)) {
-            if (lane == 0) cb.deg[p] = 0;
+            if (sl == 0) cb.deg[p] = 0;
             continue;
         }
         unsigned *flags = flags_of(g, st, v.b);
@@ -968,7 +984,7 @@ __global__ void __launch_bounds__(WPB * 32, 24 / WPB) k_topo_warp(Grid g, CellOu
             e1 = make_float3(c.x * inv, c.y * inv, c.z * inv);
             e2 = make_float3(hp.y * e1.z - hp.z * e1.y, hp.z * e1.x - hp.x * e1.z, hp.x * e1.y - hp.y * e1.x);
         }
-        const bool all_mode = v.n - 1 <= kWarpCand;
+        const bool all_mode = v.n - 1 <= C;
         const float rmax = 0.2829f;  // sin(theta) <= 0.28 keeps caps off the far faces
         float r;
         {
@@ -989,7 +1005,7 @@ __global__ void __launch_bounds__(WPB * 32, 24 / WPB) k_topo_warp(Grid g, CellOu
         bool certified = false, ok = true;
         int nv = 0;
         float R2 = 0.0f;
-        // polygon: lane k < nv holds vertex k and its outgoing edge's line
+        // polygon: sub-warp lane k < nv holds vertex k and its outgoing edge's line
         float vu = 0.0f, vw = 0.0f, la_o = 0.0f, lb_o = 0.0f, lc_o = 0.0f;
         int vill = 0, g_o = 0, g_i = 0;
         for (int attempt = 0; attempt < 4 && ok && !certified; ++attempt) {
@@ -1000,7 +1016,7 @@ __global__ void __launch_bounds__(WPB * 32, 24 / WPB) k_topo_warp(Grid g, CellOu
             const float D2 = all_mode ? INF : r * r * (1.0f - 1e-6f);
             int cnt = 0;
             if (all_mode) {
-                cnt = gather(g, p, hp, lp, v.p0, v.p0 + v.n, r2acc, cnt, cd, cj, lane, flags);
+                cnt = gather<L>(g, p, hp, lp, v.p0, v.p0 + v.n, r2acc, cnt, cd, cj, sl, sbase, smask, flags);
             } else {
                 const float S2 = S * S;
                 const float qv[3] = {hp.x, hp.y, hp.z};
@@ -1028,13 +1044,13 @@ __global__ void __launch_bounds__(WPB * 32, 24 / WPB) k_topo_warp(Grid g, CellOu
                     if (empty) continue;
                     for (int iv = lo[1]; iv <= hi[1]; ++iv) {
                         const int row = (face * v.G + iv) * v.G;
-                        cnt = gather(g, p, hp, lp, v.bstart[row + lo[0]], v.bstart[row + hi[0] + 1], r2acc, cnt, cd,
-                                     cj, lane, flags);
+                        cnt = gather<L>(g, p, hp, lp, v.bstart[row + lo[0]], v.bstart[row + hi[0] + 1], r2acc, cnt,
+                                        cd, cj, sl, sbase, smask, flags);
                     }
                 }
             }
-            __syncwarp();
-            if (cnt > kWarpCand) {  // too many: a smaller cap (the bound stays r-based)
+            __syncwarp(smask);
+            if (cnt > C) {  // too many: a smaller cap (the bound stays r-based)
                 r *= 0.7f;
                 continue;
             }
@@ -1042,76 +1058,101 @@ __global__ void __launch_bounds__(WPB * 32, 24 / WPB) k_topo_warp(Grid g, CellOu
                 r = fminf(r * 2.0f, rmax);
                 continue;
             }
-            // ---- sort the candidates once: bitonic network over 64 slots, element
-            // e = 2 lane + s in register s of `lane`; empty slots sort last
-            float cdd[2];
-            int cjj[2];
-#pragma unroll
-            for (int sl = 0; sl < 2; ++sl) {
-                const int idx = 2 * lane + sl;
-                cdd[sl] = (idx < cnt) ? cd[idx] : INF;
-                cjj[sl] = (idx < cnt) ? cj[idx] : 0x7fffffff;
-            }
-            __syncwarp();
-#pragma unroll
-            for (int k = 2; k <= 64; k <<= 1) {
-#pragma unroll
-                for (int j = k >> 1; j > 0; j >>= 1) {
-#pragma unroll
-                    for (int sl = 0; sl < 2; ++sl) {
-                        const int e = 2 * lane + sl;
-                        float od;
-                        int oj;
-                        if (j == 1) {
-                            od = cdd[sl ^ 1];
-                            oj = cjj[sl ^ 1];
-                        } else {
-                            od = __shfl_xor_sync(kFull, cdd[sl], j >> 1);
-                            oj = __shfl_xor_sync(kFull, cjj[sl], j >> 1);
-                        }
-                        const bool ascending = (e & k) == 0, lower = (e & j) == 0;
-                        const bool other_less = od < cdd[sl] || (od == cdd[sl] && oj < cjj[sl]);
-                        const bool take = (lower == ascending) ? other_less : !other_less;
-                        if (j == 1) {
-                            // both slots of the lane are the pair: decide once, from slot 0
-                            if (sl == 0) {
-                                if (take) {
-                                    const float td = cdd[0];
-                                    const int tj = cjj[0];
-                                    cdd[0] = cdd[1]; cjj[0] = cjj[1];
-                                    cdd[1] = td; cjj[1] = tj;
-                                }
-                            }
-                        } else if (take) {
-                            cdd[sl] = od;
-                            cjj[sl] = oj;
+            // ---- sort the candidates once by (d2, index), a total order, so the
+            // result does not depend on the network: up to L candidates one per
+            // lane over the next power of two >= cnt; more, two per lane over 2L
+            if (cnt <= L) {
+                int S = 2;
+                while (S < cnt) S <<= 1;
+                float dv = (sl < cnt) ? cd[sl] : INF;
+                int jv = (sl < cnt) ? cj[sl] : 0x7fffffff;
+                __syncwarp(smask);
+                for (int k = 2; k <= S; k <<= 1) {
+                    for (int j = k >> 1; j > 0; j >>= 1) {
+                        const float od = __shfl_xor_sync(smask, dv, j);
+                        const int oj = __shfl_xor_sync(smask, jv, j);
+                        const bool ascending = (sl & k) == 0, lower = (sl & j) == 0;
+                        const bool other_less = od < dv || (od == dv && oj < jv);
+                        if ((lower == ascending) ? other_less : !other_less) {
+                            dv = od;
+                            jv = oj;
                         }
                     }
                 }
-            }
-            // sorted order back to shared memory: step t reads slot t by broadcast
+                cd[sl] = dv;
+                cj[sl] = jv;
+                __syncwarp(smask);
+            } else {
+                float cdd[2];
+                int cjj[2];
 #pragma unroll
-            for (int sl = 0; sl < 2; ++sl) {
-                cd[2 * lane + sl] = cdd[sl];
-                cj[2 * lane + sl] = cjj[sl];
+                for (int s2 = 0; s2 < 2; ++s2) {
+                    const int idx = 2 * sl + s2;
+                    cdd[s2] = (idx < cnt) ? cd[idx] : INF;
+                    cjj[s2] = (idx < cnt) ? cj[idx] : 0x7fffffff;
+                }
+                __syncwarp(smask);
+#pragma unroll
+                for (int k = 2; k <= C; k <<= 1) {
+#pragma unroll
+                    for (int j = k >> 1; j > 0; j >>= 1) {
+#pragma unroll
+                        for (int s2 = 0; s2 < 2; ++s2) {
+                            const int e = 2 * sl + s2;
+                            float od;
+                            int oj;
+                            if (j == 1) {
+                                od = cdd[s2 ^ 1];
+                                oj = cjj[s2 ^ 1];
+                            } else {
+                                // partner lane sl ^ (j / 2): inside the sub-warp
+                                od = __shfl_xor_sync(smask, cdd[s2], j >> 1);
+                                oj = __shfl_xor_sync(smask, cjj[s2], j >> 1);
+                            }
+                            const bool ascending = (e & k) == 0, lower = (e & j) == 0;
+                            const bool other_less = od < cdd[s2] || (od == cdd[s2] && oj < cjj[s2]);
+                            const bool take = (lower == ascending) ? other_less : !other_less;
+                            if (j == 1) {
+                                // both slots of the lane are the pair: decide once, from slot 0
+                                if (s2 == 0) {
+                                    if (take) {
+                                        const float td = cdd[0];
+                                        const int tj = cjj[0];
+                                        cdd[0] = cdd[1]; cjj[0] = cjj[1];
+                                        cdd[1] = td; cjj[1] = tj;
+                                    }
+                                }
+                            } else if (take) {
+                                cdd[s2] = od;
+                                cjj[s2] = oj;
+                            }
+                        }
+                    }
+                }
+                // sorted order back to shared memory: step t reads slot t by broadcast
+#pragma unroll
+                for (int s2 = 0; s2 < 2; ++s2) {
+                    cd[2 * sl + s2] = cdd[s2];
+                    cj[2 * sl + s2] = cjj[s2];
+                }
+                __syncwarp(smask);
             }
-            __syncwarp();
             // ---- the starting square
             nv = 4;
             {
-                const float L = (float)kBoxL;
-                vu = (lane == 0 || lane == 1) ? L : -L;
-                vw = (lane == 1 || lane == 2) ? L : -L;
-                la_o = (lane == 0) ? 1.0f : ((lane == 2) ? -1.0f : 0.0f);
-                lb_o = (lane == 1) ? 1.0f : ((lane == 3) ? -1.0f : 0.0f);
-                lc_o = L;
-                g_o = -1 - lane;
-                g_i = -1 - ((lane + 3) & 3);
+                const float Lb = (float)kBoxL;
+                vu = (sl == 0 || sl == 1) ? Lb : -Lb;
+                vw = (sl == 1 || sl == 2) ? Lb : -Lb;
+                la_o = (sl == 0) ? 1.0f : ((sl == 2) ? -1.0f : 0.0f);
+                lb_o = (sl == 1) ? 1.0f : ((sl == 3) ? -1.0f : 0.0f);
+                lc_o = Lb;
+                g_o = -1 - sl;
+                g_i = -1 - ((sl + 3) & 3);
                 vill = 0;
             }
             R2 = chord2_up(2.0f * (float)kBoxL * (float)kBoxL);
             bool early = false;
-            const int ncand = min(cnt, kWarpCand);
+            const int ncand = min(cnt, C);
             for (int t = 0; t < ncand; ++t) {
                 // candidate t (nearest first)
                 const float wd = cd[t];
@@ -1125,42 +1166,42 @@ __global__ void __launch_bounds__(WPB * 32, 24 / WPB) k_topo_warp(Grid g, CellOu
                 const float lb = e2.x * d.x + e2.y * d.y + e2.z * d.z;
                 const float lc = 0.5f * fmaf(d.x, d.x, fmaf(d.y, d.y, d.z * d.z));
                 bool outside = false;
-                if (lane < nv) {
+                if (sl < nv) {
                     const float sd = fmaf(la, vu, fmaf(lb, vw, -lc));
                     const float mag = (fabsf(la) + fabsf(lb)) * (fabsf(vu) + fabsf(vw)) + fabsf(lc);
                     if (!vill && fabsf(sd) > 2e-4f * mag) outside = sd > 0.0f;
                     else outside = outside64(g, p, g_i, g_o, wj, &st->ambiguous);
                 }
-                const unsigned m = __ballot_sync(kFull, outside);
+                const unsigned m = (__ballot_sync(smask, outside) >> sbase) & lfull;
                 if (m == 0u) continue;
-                const unsigned full = (nv == 32) ? kFull : ((1u << nv) - 1u);
+                const unsigned full = (nv == 32) ? 0xffffffffu : ((1u << nv) - 1u);
                 if (m == full) {
-                    if (lane == 0) atomicOr(flags, FLAG_EMPTY);
+                    if (sl == 0) atomicOr(flags, FLAG_EMPTY);
                     ok = false;
                     break;
                 }
                 const unsigned rot = ((m << 1) | (m >> (nv - 1))) & full;  // bit k = bit k-1 of m
                 const unsigned starts = m & ~rot;
-                if (__popc(starts) > 1 && lane == 0) atomicOr(flags, FLAG_NONCONVEX);
+                if (__popc(starts) > 1 && sl == 0) atomicOr(flags, FLAG_NONCONVEX);
                 const int k0 = __ffs(starts) - 1;
                 const unsigned mr = (k0 == 0) ? m : (((m >> k0) | (m << (nv - k0))) & full);
                 const int runlen = __ffs(~mr) - 1;
                 const int k1 = (k0 + runlen - 1) % nv;
                 const int kin = (k0 + nv - 1) % nv;
                 const int nnew = nv - runlen + 2;
-                if (nnew > 32) { ok = false; break; }
-                const float ai = __shfl_sync(kFull, la_o, kin), bi = __shfl_sync(kFull, lb_o, kin),
-                            ci = __shfl_sync(kFull, lc_o, kin);
-                const int gkin = __shfl_sync(kFull, g_o, kin);
+                if (nnew > L) { ok = false; break; }
+                const float ai = __shfl_sync(smask, la_o, sbase + kin), bi = __shfl_sync(smask, lb_o, sbase + kin),
+                            ci = __shfl_sync(smask, lc_o, sbase + kin);
+                const int gkin = __shfl_sync(smask, g_o, sbase + kin);
                 // new vertices P = (edge kin) x (new line), Q = (new line) x (edge k1);
                 // lanes >= 2 take the surviving vertices k1+1 .. kin
-                const int src = (lane >= 2) ? (k1 + lane - 1) % nv : k1;
-                const float su = __shfl_sync(kFull, vu, src), sw = __shfl_sync(kFull, vw, src);
-                const int sill = __shfl_sync(kFull, vill, src), sg = __shfl_sync(kFull, g_o, src);
-                const int sgi = __shfl_sync(kFull, g_i, src);
-                const float sa = __shfl_sync(kFull, la_o, src), sb = __shfl_sync(kFull, lb_o, src),
-                            sc = __shfl_sync(kFull, lc_o, src);
-                if (lane == 0) {
+                const int src = sbase + ((sl >= 2) ? (k1 + sl - 1) % nv : k1);
+                const float su = __shfl_sync(smask, vu, src), sw = __shfl_sync(smask, vw, src);
+                const int sill = __shfl_sync(smask, vill, src), sg = __shfl_sync(smask, g_o, src);
+                const int sgi = __shfl_sync(smask, g_i, src);
+                const float sa = __shfl_sync(smask, la_o, src), sb = __shfl_sync(smask, lb_o, src),
+                            sc = __shfl_sync(smask, lc_o, src);
+                if (sl == 0) {
                     const float p1 = ai * lb, p2 = la * bi, det = p1 - p2, inv = __frcp_rn(det);
                     vu = (ci * lb - lc * bi) * inv;
                     vw = (ai * lc - la * ci) * inv;
@@ -1173,7 +1214,7 @@ __global__ void __launch_bounds__(WPB * 32, 24 / WPB) k_topo_warp(Grid g, CellOu
                         vw = (float)w;
                     }
                     la_o = la; lb_o = lb; lc_o = lc; g_o = wj; g_i = gkin;
-                } else if (lane == 1) {
+                } else if (sl == 1) {
                     const float p1 = la * sb, p2 = sa * lb, det = p1 - p2, inv = __frcp_rn(det);
                     vu = (lc * sb - sc * lb) * inv;
                     vw = (la * sc - sa * lc) * inv;
@@ -1190,13 +1231,13 @@ __global__ void __launch_bounds__(WPB * 32, 24 / WPB) k_topo_warp(Grid g, CellOu
                 }
                 nv = nnew;
                 // R2: an upper bound of the largest squared vertex chord
-                float r2v = (lane < nv) ? vu * vu + vw * vw : 0.0f;
+                float r2v = (sl < nv) ? vu * vu + vw * vw : 0.0f;
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) r2v = fmaxf(r2v, __shfl_xor_sync(kFull, r2v, o));
+                for (int o = L / 2; o > 0; o >>= 1) r2v = fmaxf(r2v, __shfl_xor_sync(smask, r2v, o));
                 R2 = chord2_up(r2v * 1.001f);
             }
             if (!ok) break;
-            const bool boxed = __ballot_sync(kFull, lane < nv && g_o < 0) != 0u;
+            const bool boxed = ((__ballot_sync(smask, sl < nv && g_o < 0) >> sbase) & lfull) != 0u;
             certified = !boxed && (early || D2 > 4.0f * R2 * (1.0f + 1e-6f));
             if (!certified) {
                 if (all_mode || r >= rmax) break;
@@ -1204,7 +1245,7 @@ __global__ void __launch_bounds__(WPB * 32, 24 / WPB) k_topo_warp(Grid g, CellOu
             }
         }
         if (!certified || nv > kCellSlots) {
-            if (lane == 0) {
+            if (sl == 0) {
                 unsigned pos = atomicAdd(next_count, 1u);
                 next_list[pos] = p;
                 cb.deg[p] = 0;
@@ -1218,40 +1259,40 @@ __global__ void __launch_bounds__(WPB * 32, 24 / WPB) k_topo_warp(Grid g, CellOu
         {
             unsigned k0 = 0xffffffffu;
             float4 nh = make_float4(0, 0, 0, 0);
-            if (lane < nv) {
+            if (sl < nv) {
                 nh = g.zf[g_o];
                 k0 = okey32(nh.x);
             }
-            const unsigned kmin = __reduce_min_sync(kFull, k0);
-            const unsigned tie = __ballot_sync(kFull, k0 == kmin);
+            const unsigned kmin = __reduce_min_sync(smask, k0);
+            const unsigned tie = (__ballot_sync(smask, k0 == kmin) >> sbase) & lfull;
             best = __ffs(tie) - 1;
             if (__popc(tie) > 1) {
                 // rare: resolve on the whole key among the tied lanes
                 unsigned long long kx = ~0ull, ky = kx, kz = kx;
-                if ((tie >> lane) & 1u) {
+                if ((tie >> sl) & 1u) {
                     const float4 nl = g.zl[g_o];
                     kx = ((unsigned long long)okey32(nh.x) << 32) | okey32(nl.x);
                     ky = ((unsigned long long)okey32(nh.y) << 32) | okey32(nl.y);
                     kz = ((unsigned long long)okey32(nh.z) << 32) | okey32(nl.z);
                 }
-                best = lane;
+                best = sl;
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    const unsigned long long ox = __shfl_xor_sync(kFull, kx, o), oy = __shfl_xor_sync(kFull, ky, o),
-                                             oz = __shfl_xor_sync(kFull, kz, o);
-                    const int ob = __shfl_xor_sync(kFull, best, o);
+                for (int o = L / 2; o > 0; o >>= 1) {
+                    const unsigned long long ox = __shfl_xor_sync(smask, kx, o), oy = __shfl_xor_sync(smask, ky, o),
+                                             oz = __shfl_xor_sync(smask, kz, o);
+                    const int ob = __shfl_xor_sync(smask, best, o);
                     const bool less =
                         ox < kx || (ox == kx && (oy < ky || (oy == ky && (oz < kz || (oz == kz && ob < best)))));
                     if (less) { kx = ox; ky = oy; kz = oz; best = ob; }
                 }
             }
         }
-        const int rg = __shfl_sync(kFull, g_o, (best + lane) % nv);
-        if (lane < nv) {
-            cb.nb[(size_t)p * kCellSlots + lane] = rg;
-            if (out.deg && nv <= out.max_deg) out.nbr[(size_t)i * out.max_deg + lane] = g.sidx[rg];
+        const int rg = __shfl_sync(smask, g_o, sbase + (best + sl) % nv);
+        if (sl < nv) {
+            cb.nb[(size_t)p * kCellSlots + sl] = rg;
+            if (out.deg && nv <= out.max_deg) out.nbr[(size_t)i * out.max_deg + sl] = g.sidx[rg];
         }
-        if (lane == 0) {
+        if (sl == 0) {
             cb.deg[p] = nv;
             if (out.deg) out.deg[i] = nv;
             if (out.radius) out.radius[i] = fminf(2.2f * sqrtf(R2), rmax);
@@ -1705,11 +1746,13 @@ scvt_status tune_from(const scvt_tuning &t, Tune *out) {
     if (t.topo_warps != 2 && t.topo_warps != 4 && t.topo_warps != 8) return SCVT_ERR_INVALID;
     if (t.topo_blocks_per_sm < 1 || t.topo_blocks_per_sm > 64) return SCVT_ERR_INVALID;
     if (t.quad_block != 128 && t.quad_block != 256 && t.quad_block != 512) return SCVT_ERR_INVALID;
+    if (t.topo_cell_lanes != 16 && t.topo_cell_lanes != 32) return SCVT_ERR_INVALID;
     out->bin_load = t.bin_load;
     out->knn_target = t.knn_target;
     out->topo_warps = t.topo_warps;
     out->topo_bpsm = t.topo_blocks_per_sm;
     out->quad_block = t.quad_block;
+    out->topo_lanes = t.topo_cell_lanes;
     return SCVT_OK;
 }
 
@@ -1720,6 +1763,7 @@ scvt_tuning tuning_of(const Tune &u) {
     t.topo_warps = u.topo_warps;
     t.topo_blocks_per_sm = u.topo_bpsm;
     t.quad_block = u.quad_block;
+    t.topo_cell_lanes = u.topo_lanes;
     return t;
 }
 
@@ -1752,11 +1796,19 @@ void cell_passes(const Grid &g, const CellOut &out, const CellBuf &cb, int *list
                  int64_t *cell_launches) {
     // first pass: a warp per cell, grid capped at topo_bpsm blocks per SM (grid-stride over cells)
     const int wpb = t.topo_warps;
-    const int wblocks = (int)std::min<long long>((g.n + wpb - 1) / wpb, 152LL * t.topo_bpsm);
+    const int cpw = 32 / t.topo_lanes;  // cells per warp
+    const int wblocks = (int)std::min<long long>((g.n + wpb * cpw - 1) / (wpb * cpw), 152LL * t.topo_bpsm);
     const float kt = (float)t.knn_target;
-    if (wpb == 2) k_topo_warp<2><<<wblocks, 64, 0, s>>>(g, out, cb, list1, &st->retry_count[0], st, kt);
-    else if (wpb == 8) k_topo_warp<8><<<wblocks, 256, 0, s>>>(g, out, cb, list1, &st->retry_count[0], st, kt);
-    else k_topo_warp<4><<<wblocks, 128, 0, s>>>(g, out, cb, list1, &st->retry_count[0], st, kt);
+    unsigned *rc0 = &st->retry_count[0];
+    if (t.topo_lanes == 16) {
+        if (wpb == 2) k_topo_warp<2, 16><<<wblocks, 64, 0, s>>>(g, out, cb, list1, rc0, st, kt);
+        else if (wpb == 8) k_topo_warp<8, 16><<<wblocks, 256, 0, s>>>(g, out, cb, list1, rc0, st, kt);
+        else k_topo_warp<4, 16><<<wblocks, 128, 0, s>>>(g, out, cb, list1, rc0, st, kt);
+    } else {
+        if (wpb == 2) k_topo_warp<2, 32><<<wblocks, 64, 0, s>>>(g, out, cb, list1, rc0, st, kt);
+        else if (wpb == 8) k_topo_warp<8, 32><<<wblocks, 256, 0, s>>>(g, out, cb, list1, rc0, st, kt);
+        else k_topo_warp<4, 32><<<wblocks, 128, 0, s>>>(g, out, cb, list1, rc0, st, kt);
+    }
     // retry passes (thread per cell): sized for the worst case, they read their work count on the device
     const int rblocks = 2 * 152;
     k_topo<64, 64, 0><<<rblocks, 64, 0, s>>>(g, out, cb, list1, &st->retry_count[0], list2, &st->retry_count[1], 0,
