@@ -63,7 +63,10 @@ class _Density(C.Structure):
 class _Opts(C.Structure):
     _fields_ = [("max_iter", C.c_int), ("grad_tol", C.c_double), ("rel_grad_tol", C.c_double),
                 ("rel_df_tol", C.c_double), ("step_tol", C.c_double), ("ls_max_evals", C.c_int),
-                ("c1", C.c_double), ("c2", C.c_double), ("lbfgs_m", C.c_int), ("nthreads", C.c_int)]
+                ("c1", C.c_double), ("c2", C.c_double), ("lbfgs_m", C.c_int), ("nthreads", C.c_int),
+                ("method", C.c_int)]
+
+METHODS = {"plbfgs": 0, "lbfgs": 1, "lloyd": 2}
 
 
 class _Report(C.Structure):
@@ -97,6 +100,8 @@ def lib():
             L.orc_lloyd_step.restype = C.c_int
             L.orc_two_loop.argtypes = [C.c_int, _dp, _dp, C.c_int, _dp, _dp, _dp]
             L.orc_two_loop.restype = C.c_int
+            L.orc_two_loop_scalar.argtypes = [C.c_int, _dp, C.c_double, C.c_int, _dp, _dp, _dp]
+            L.orc_two_loop_scalar.restype = C.c_int
             L.orc_line_search.argtypes = [PHI_FN, C.c_void_p, C.c_double, C.c_double, C.c_double,
                                           C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
                                           C.c_int, _dp, _dp, _dp, _ip]
@@ -212,6 +217,20 @@ def two_loop(g, h, S, Y):
     return q
 
 
+def two_loop_scalar(g, gamma, S, Y):
+    """q = -H g with H0 = gamma I (plain LBFGS); S, Y: lists of (n,3) arrays, oldest first."""
+    g = _f64(g)
+    n = g.shape[0]
+    mcount = len(S)
+    Sa = _f64(np.stack(S) if mcount else np.zeros((1, n, 3)))
+    Ya = _f64(np.stack(Y) if mcount else np.zeros((1, n, 3)))
+    q = np.zeros_like(g)
+    rc = lib().orc_two_loop_scalar(n, _p(g), C.c_double(float(gamma)), mcount, _p(Sa), _p(Ya), _p(q))
+    if rc != OK:
+        raise OracleError(rc, "two_loop_scalar")
+    return q
+
+
 def line_search(phi, f0, g0, stp0=1.0, ftol=1e-4, gtol=0.9, xtol=1e-16, stpmin=1e-20, stpmax=1e20, maxfev=10):
     """More-Thuente search on a Python callable phi(a) -> (f, f'), or None
     when the trial point is not valid (the search then halves the step)."""
@@ -236,12 +255,13 @@ def line_search(phi, f0, g0, stp0=1.0, ftol=1e-4, gtol=0.9, xtol=1e-16, stpmin=1
 
 
 def lbfgs_solve(z, density, lbfgs_m=5, max_iter=200, grad_tol=1e-8, rel_grad_tol=0.0, rel_df_tol=0.0,
-                step_tol=0.0, ls_max_evals=10, c1=1e-4, c2=0.9, nthreads=0):
-    """Lloyd-preconditioned LBFGS from z; returns (z_final, report, trace)."""
+                step_tol=0.0, ls_max_evals=10, c1=1e-4, c2=0.9, nthreads=0, method="plbfgs"):
+    """Solve from z with method "plbfgs" (Lloyd-preconditioned LBFGS), "lbfgs"
+    (H0 = gamma_n I) or "lloyd"; returns (z_final, report, trace)."""
     z = _f64(z).copy()
     n = z.shape[0]
     o = _Opts(int(max_iter), float(grad_tol), float(rel_grad_tol), float(rel_df_tol), float(step_tol),
-              int(ls_max_evals), float(c1), float(c2), int(lbfgs_m), int(nthreads))
+              int(ls_max_evals), float(c1), float(c2), int(lbfgs_m), int(nthreads), METHODS[method])
     rep = _Report()
     k = max(int(max_iter), 1)
     trF, trg, tra = np.zeros(k), np.zeros(k), np.zeros(k)

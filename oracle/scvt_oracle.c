@@ -859,8 +859,9 @@ int orc_lloyd_step(int n, const double *z, const orc_density *rho, double *zout,
  * Hessian replaced by diag(h) (Sec. 3.1): q = -H g.
  * S, Y hold mcount pairs, oldest first, each of length 3n.
  * ====================================================================== */
-int orc_two_loop(int n, const double *g, const double *h, int mcount,
-                 const double *S, const double *Y, double *q)
+/* h == NULL: the plain LBFGS initial matrix gamma I instead (Sec. 2.2.2) */
+static int two_loop_h0(int n, const double *g, const double *h, double gamma, int mcount,
+                       const double *S, const double *Y, double *q)
 {
     size_t L = 3 * (size_t)n;
     double alpha[64], rho[64];
@@ -872,13 +873,27 @@ int orc_two_loop(int n, const double *g, const double *h, int mcount,
         alpha[i] = rho[i] * pdot(s, q, L);
         for (size_t k = 0; k < L; k++) q[k] -= alpha[i] * y[k];
     }
-    for (size_t k = 0; k < L; k++) q[k] *= h[k / 3];
+    for (size_t k = 0; k < L; k++) q[k] *= h ? h[k / 3] : gamma;
     for (int i = 0; i < mcount; i++) {
         const double *s = S + (size_t)i * L, *y = Y + (size_t)i * L;
         double beta = rho[i] * pdot(y, q, L);
         for (size_t k = 0; k < L; k++) q[k] += s[k] * (alpha[i] - beta);
     }
     return ORC_OK;
+}
+
+int orc_two_loop(int n, const double *g, const double *h, int mcount,
+                 const double *S, const double *Y, double *q)
+{
+    return two_loop_h0(n, g, h, 1.0, mcount, S, Y, q);
+}
+
+/* plain LBFGS (Sec. 2.2.2): H0 = gamma I, gamma = y.s / y.y of the newest
+ * pair (the caller passes it; 1 with an empty history) */
+int orc_two_loop_scalar(int n, const double *g, double gamma, int mcount,
+                        const double *S, const double *Y, double *q)
+{
+    return two_loop_h0(n, g, NULL, gamma, mcount, S, Y, q);
 }
 
 /* ======================================================================
@@ -1055,6 +1070,7 @@ typedef struct {
     double c1, c2;
     int lbfgs_m;
     int nthreads;
+    int method;  /* 0 Lloyd-preconditioned LBFGS, 1 LBFGS with gamma_n I, 2 Lloyd */
 } orc_opts;
 
 typedef struct {
@@ -1102,14 +1118,21 @@ static int phi_eval(void *vctx, double a, double *f, double *dphi)
 }
 
 /* Per-iteration trace (optional, arrays of length >= max_iter):
- * energy after the iteration, ||g|| after, accepted step, evaluations used. */
+ * energy after the iteration, ||g|| after, accepted step, evaluations used.
+ * method 0: the Lloyd-preconditioned LBFGS (Sec. 3.1); method 1: LBFGS with
+ * H0 = gamma_n I, gamma_n = y.s / y.y of the newest stored pair and H0 = I
+ * with an empty memory (Sec. 2.2.2); method 2: Lloyd's iteration (Sec. 2.2.1)
+ * written as the step alpha = 1 along the Lloyd direction q = -h g, whose
+ * trial point normalize(z - h g) = c / |c| (since z - h g = c / (c.z)), with
+ * no line search and no memory. */
 int orc_lbfgs_solve(int n, double *z, const orc_density *rho, const orc_opts *o, orc_report *rep,
                     double *tr_F, double *tr_g, double *tr_a, int *tr_nfev)
 {
     size_t L = 3 * (size_t)n;
     int M = o->lbfgs_m;
     memset(rep, 0, sizeof(*rep));
-    if (n < 4 || M < 0 || M > 64) return ORC_INVALID;
+    if (n < 4 || M < 0 || M > 64 || o->method < 0 || o->method > 2) return ORC_INVALID;
+    if (o->method == 2) M = 0;
     double *g = (double *)malloc(sizeof(double) * L);
     double *h = (double *)malloc(sizeof(double) * n);
     double *q = (double *)malloc(sizeof(double) * L);
@@ -1126,6 +1149,7 @@ int orc_lbfgs_solve(int n, double *z, const orc_density *rho, const orc_opts *o,
     rep->fevals = 1;
     if (rc != ORC_OK) goto out;
     int hist = 0;
+    double gamma = 1.0;  /* method 1: y.s / y.y of the newest stored pair */
     mt_opts mo = {o->c1, o->c2, 1e-16, 1e-20, 1e20, o->ls_max_evals};
     double Fprev = F;
     for (;;) {
@@ -1136,19 +1160,30 @@ int orc_lbfgs_solve(int n, double *z, const orc_density *rho, const orc_opts *o,
         if (o->rel_grad_tol > 0 && gn / F <= o->rel_grad_tol) { rep->converged = 1; break; }
         if (rep->iters > 0 && o->rel_df_tol > 0 && fabs(F - Fprev) / Fprev < o->rel_df_tol) { rep->converged = 1; break; }
         if (rep->iters >= o->max_iter) break;
-        orc_two_loop(n, g, h, hist, S, Y, q);
+        if (o->method == 1) two_loop_h0(n, g, NULL, hist ? gamma : 1.0, hist, S, Y, q);
+        else orc_two_loop(n, g, h, hist, S, Y, q);
         double d0 = pdot(g, q, L);
         if (!(d0 < 0.0)) {
             hist = 0;
             rep->resets++;
-            orc_two_loop(n, g, h, 0, S, Y, q);
+            if (o->method == 1) two_loop_h0(n, g, NULL, 1.0, 0, S, Y, q);
+            else orc_two_loop(n, g, h, 0, S, Y, q);
             d0 = pdot(g, q, L);
             if (!(d0 < 0.0)) { rc = ORC_DEGENERATE; break; }
         }
         ls_ctx C = {n, z, q, rho, zt, gt, ht, 0.0, o->nthreads, ORC_OK};
         double a = 1.0, fa, ga;
         int nfev = 0;
-        int info = mt_search(phi_eval, &C, F, d0, &mo, &a, &fa, &ga, &nfev);
+        int info;
+        if (o->method == 2) {
+            /* Lloyd: the trial point at alpha = 1, accepted as it is */
+            int cb = phi_eval(&C, 1.0, &fa, &ga);
+            nfev = 1;
+            if (cb == 2) { rep->fevals += 1; rc = ORC_DEGENERATE; break; }
+            info = cb ? -1 : 1;
+        } else {
+            info = mt_search(phi_eval, &C, F, d0, &mo, &a, &fa, &ga, &nfev);
+        }
         rep->fevals += nfev;
         if (info < 0) { rc = C.rc; break; }
         if (info != 1) {
@@ -1182,7 +1217,8 @@ int orc_lbfgs_solve(int n, double *z, const orc_density *rho, const orc_opts *o,
             memcpy(S + L * hist, s_new, sizeof(double) * L);
             memcpy(Y + L * hist, y_new, sizeof(double) * L);
             hist++;
-        } else {
+            gamma = ys / pdot(y_new, y_new, L);
+        } else if (o->method != 2) {
             rep->skipped++;
         }
         memcpy(z, zt, sizeof(double) * L);

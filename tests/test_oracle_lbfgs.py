@@ -199,3 +199,48 @@ def test_solver_x3_energy_law_and_paper_value():
     # start) is 3.4% below ours: a 5% band around the printed value
     assert 0.95 <= rep["energy"] / pred <= 1.03
     assert abs(rep["energy"] / row["F"] - 1) < 5e-2
+
+
+@pytest.mark.parametrize("m", [0, 1, 4])
+def test_plain_lbfgs_two_loop_equals_dense_bfgs_with_scaled_identity(m):
+    # Sec. 2.2.2: H0 = gamma I with gamma = y.s / y.y of the newest pair
+    rng = np.random.default_rng(40 + m)
+    n = 10
+    L = 3 * n
+    A = rng.standard_normal((L, L))
+    A = A @ A.T + L * np.eye(L)
+    S, Y = [], []
+    for _ in range(m):
+        s = rng.standard_normal(L)
+        S.append(s.reshape(n, 3))
+        Y.append((A @ s).reshape(n, 3))
+    gamma = float(S[-1].ravel() @ Y[-1].ravel() / (Y[-1].ravel() @ Y[-1].ravel())) if m else 1.0
+    g = rng.standard_normal((n, 3))
+    q = oracle.two_loop_scalar(g, gamma, S, Y)
+    H = dense_bfgs_inverse(np.full(L, gamma), [s.ravel() for s in S], [y.ravel() for y in Y])
+    ref = -(H @ g.ravel())
+    assert np.abs(q.ravel() - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_lloyd_mode_is_the_iterated_lloyd_map():
+    # the Lloyd mode steps to normalize(z - h g) = c / |c| without a line search
+    z = I.uniform_sphere(162, 8)
+    dens = I.density_x3()
+    zl, rep, trace = oracle.lbfgs_solve(z, dens, method="lloyd", max_iter=6, grad_tol=0.0)
+    assert rep["iters"] == 6 and rep["fevals"] == 7
+    zr = z.copy()
+    for _ in range(6):
+        zr = oracle.lloyd_step(zr, dens)
+    assert np.abs(zl - zr).max() <= 1e-12
+    assert np.all(np.diff(trace["F"]) < 0)  # Lloyd decreases the energy
+
+
+@pytest.mark.parametrize("method", ["lbfgs", "lloyd"])
+def test_other_methods_decrease_energy_and_converge(method):
+    z = I.uniform_sphere(642, 9)
+    dens = I.density_uniform()
+    F0 = oracle.energy_grad(z, dens)["F"]
+    zf, rep, trace = oracle.lbfgs_solve(z, dens, method=method, max_iter=60, grad_tol=0.0, lbfgs_m=5)
+    assert rep["status"] == oracle.OK and rep["iters"] == 60
+    assert trace["F"][-1] < F0 and np.all(np.diff(trace["F"]) <= 1e-18)
+    assert trace["gnorm"][-1] < 0.2 * oracle.energy_grad(z, dens)["gnorm"]
