@@ -95,6 +95,11 @@ typedef struct {
                                 value is ignored and z receives the result.
                              2: as 1 if z holds exactly the iterate the previous solve
                                 returned (checked on the device), else as 0. */
+    int method;           /* 0: Lloyd-preconditioned LBFGS (Sec. 3.1).  1: plain LBFGS, H0 = gamma_n I
+                             with gamma_n = y.s / y.y of the newest stored pair, I with an empty
+                             memory (Sec. 2.2.2).  2: Lloyd's iteration (Sec. 2.2.1), taken as the
+                             unit step along q = -h g, whose trial point normalize(z - h g) is
+                             c / |c|, with no line search and no memory. */
 } scvt_solve_opts;
 
 typedef struct {

@@ -36,7 +36,7 @@ class scvt_config(C.Structure):
 class scvt_solve_opts(C.Structure):
     _fields_ = [("max_iter", C.c_int), ("grad_tol", C.c_double), ("rel_grad_tol", C.c_double),
                 ("rel_df_tol", C.c_double), ("step_tol", C.c_double), ("ls_max_evals", C.c_int),
-                ("c1", C.c_double), ("c2", C.c_double), ("warm_start", C.c_int)]
+                ("c1", C.c_double), ("c2", C.c_double), ("warm_start", C.c_int), ("method", C.c_int)]
 
 
 class scvt_solve_report(C.Structure):

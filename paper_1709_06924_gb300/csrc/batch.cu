@@ -152,7 +152,7 @@ scvt_status scvt_batch_create(const scvt_config *cfgs, int count, void *cuda_str
 #define AL(ptr, cnt) \
     if (e == cudaSuccess) e = balloc(BT, &(ptr), (cnt))
     AL(BT->z, n3); AL(BT->g, n3); AL(BT->h, N);
-    AL(BT->hist, (size_t)(BT->m + 1) * 2 * n3); AL(BT->rho_hist, (size_t)count * (kLaneMaxM + 1));
+    AL(BT->hist, (size_t)(BT->m + 1) * 2 * n3); AL(BT->rho_hist, (size_t)count * kLaneRho);
     AL(BT->partials, 4 * 1024); AL(BT->scal, 128);
 #undef AL
     std::vector<int> ns(count);
@@ -181,7 +181,7 @@ scvt_status scvt_batch_create(const scvt_config *cfgs, int count, void *cuda_str
         L.hist = BT->hist + 3 * off;
         L.slot_stride = 2 * n3;
         L.y_off = n3;
-        L.rho = BT->rho_hist + (size_t)b * (kLaneMaxM + 1);
+        L.rho = BT->rho_hist + (size_t)b * kLaneRho;
         BT->off[b] = off;
         off += ns[b];
     }

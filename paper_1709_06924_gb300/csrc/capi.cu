@@ -39,6 +39,7 @@ struct Bufs {
     double *partials = nullptr;              // 4 * 1024
     double *scal = nullptr;                  // 128 two-loop scalars
     double *rho = nullptr;                   // kMaxM + 1
+    double *gamma = nullptr;                 // plain LBFGS scaling of H0
     double *hist = nullptr;                  // (m + 1) slots of S and Y, 3n each
     P4 *zs = nullptr;
     float4 *zf = nullptr, *zl = nullptr;
@@ -239,17 +240,19 @@ void hist_reset(scvt_handle *H) {
     H->spare = H->m;  // slot m is the first spare
 }
 
-scvt_status make_direction(scvt_handle *H, double *d0) {
+// method 0: H0 = diag(h); 1: gamma I (I with an empty memory); 2: Lloyd, diag(h) and no memory
+scvt_status make_direction(scvt_handle *H, double *d0, int method) {
     const double *S[kMaxM], *Y[kMaxM], *R[kMaxM];
-    for (int k = 0; k < H->hist_count; ++k) {
+    const int count = (method == 2) ? 0 : H->hist_count;
+    for (int k = 0; k < count; ++k) {
         int sl = H->hist_slots[k];
         S[k] = slot_S(H, sl);
         Y[k] = slot_Y(H, sl);
         R[k] = H->b.rho + sl;
     }
     if (H->profiling) cudaEventRecord(H->ev_l0, H->stream);
-    two_loop(H->n, H->b.g, H->b.h, H->hist_count, S, Y, R, H->b.q, H->b.partials, H->b.scal, H->b.st, H->stream,
-             &H->stats.kernel_launches);
+    two_loop(H->n, H->b.g, method == 1 ? nullptr : H->b.h, (method == 1 && count > 0) ? H->b.gamma : nullptr, count,
+             S, Y, R, H->b.q, H->b.partials, H->b.scal, H->b.st, H->stream, &H->stats.kernel_launches);
     if (H->profiling) cudaEventRecord(H->ev_l1, H->stream);
     CK(cudaGetLastError(), "two-loop launch");
     CK(cudaMemcpyAsync(&H->st_host->dots[3], &H->b.st->dots[3], sizeof(double), cudaMemcpyDeviceToHost, H->stream),
@@ -292,7 +295,7 @@ void scvt_destroy(scvt_handle *H) {
     if (!H) return;
     Bufs &b = H->b;
     void *ptrs[] = {b.z, b.zt, b.g, b.gt, b.h, b.ht, b.fc, b.q, b.yv, b.nrm, b.mass, b.moment, b.stage_a, b.stage_b,
-                    b.partials, b.scal, b.rho, b.hist, b.zs, b.zf, b.zl, b.cvx, b.cnb, b.cdeg, b.eoff, b.ecell, b.escan, b.eacc, b.vo, b.ser, b.serK, b.bin_of, b.count, b.start, b.cursor, b.scan_tmp,
+                    b.partials, b.scal, b.rho, b.gamma, b.hist, b.zs, b.zf, b.zl, b.cvx, b.cnb, b.cdeg, b.eoff, b.ecell, b.escan, b.eacc, b.vo, b.ser, b.serK, b.bin_of, b.count, b.start, b.cursor, b.scan_tmp,
                     b.sidx, b.list1, b.list2, b.deg, b.radius, b.st};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -342,7 +345,7 @@ scvt_status scvt_create(const scvt_config *cfg, void *cuda_stream, scvt_handle *
     AL(b.z, n3); AL(b.zt, n3); AL(b.g, n3); AL(b.gt, n3); AL(b.h, n); AL(b.ht, n); AL(b.fc, n);
     AL(b.q, n3); AL(b.yv, n3); AL(b.nrm, n); AL(b.mass, n); AL(b.moment, n3);
     AL(b.stage_a, n3); AL(b.stage_b, n3);
-    AL(b.partials, 4 * 1024); AL(b.scal, 128); AL(b.rho, kMaxM + 1);
+    AL(b.partials, 4 * 1024); AL(b.scal, 128); AL(b.rho, kMaxM + 1); AL(b.gamma, 1);
     AL(b.hist, (size_t)(H->m + 1) * 2 * n3);
     AL(b.zs, n); AL(b.zf, n); AL(b.zl, n); AL(b.cvx, (size_t)n * kCellSlots); AL(b.cnb, (size_t)n * kCellSlots);
     AL(b.cdeg, n); AL(b.eoff, n + 1); AL(b.ecell, 6 * (size_t)n); AL(b.escan, 2 * (n / 2048 + 64) + 64);
@@ -489,8 +492,8 @@ scvt_status scvt_lbfgs_direction(scvt_handle *H, const double *g, const double *
         dot_to((int64_t)n3, Yp[k], Sp[k], H->b.partials, &H->b.st->dots[0], H->stream, L);
         set_rho(rho, k, H->b.st, H->stream, L);
     }
-    two_loop(H->n, g, hdiag, count, Sp.data(), Yp.data(), Rp.data(), q, H->b.partials, H->b.scal, H->b.st, H->stream,
-             L);
+    two_loop(H->n, g, hdiag, nullptr, count, Sp.data(), Yp.data(), Rp.data(), q, H->b.partials, H->b.scal, H->b.st,
+             H->stream, L);
     if (rho) cudaFreeAsync(rho, H->stream);
     CK(cudaGetLastError(), "two-loop launch");
     CK(cudaStreamSynchronize(H->stream), "two-loop");
@@ -507,7 +510,8 @@ scvt_status scvt_lbfgs_solve(scvt_handle *H, double *z, const scvt_solve_opts *o
     if (o.ls_max_evals <= 0) o.ls_max_evals = 10;
     if (o.c1 <= 0.0) o.c1 = 1e-4;
     if (o.c2 <= 0.0) o.c2 = 0.9;
-    if (o.max_iter < 0 || !(o.c1 < o.c2) || o.c2 >= 1.0) return fail(H, SCVT_ERR_INVALID, "bad solve options");
+    if (o.max_iter < 0 || !(o.c1 < o.c2) || o.c2 >= 1.0 || o.method < 0 || o.method > 2)
+        return fail(H, SCVT_ERR_INVALID, "bad solve options");
     scvt_solve_report rep;
     memset(&rep, 0, sizeof(rep));
     const int n = H->n;
@@ -559,11 +563,11 @@ scvt_status scvt_lbfgs_solve(scvt_handle *H, double *z, const scvt_solve_opts *o
         if (iters > 0 && o.rel_df_tol > 0 && fabs(H->F - Fprev) / Fprev < o.rel_df_tol) { rep.converged = 1; break; }
         if (iters >= o.max_iter) break;
         double d0;
-        if ((st = make_direction(H, &d0))) break;
+        if ((st = make_direction(H, &d0, o.method))) break;
         if (!(d0 < 0.0)) {
             hist_reset(H);
             rep.resets++;
-            if ((st = make_direction(H, &d0))) break;
+            if ((st = make_direction(H, &d0, o.method))) break;
             if (!(d0 < 0.0)) { st = fail(H, SCVT_ERR_DEGENERATE, "Lloyd direction is not a descent direction"); break; }
         }
         scvt_status cb_status = SCVT_OK;
@@ -583,7 +587,20 @@ scvt_status scvt_lbfgs_solve(scvt_handle *H, double *z, const scvt_solve_opts *o
         };
         double a = 1.0, fa = 0.0, da = 0.0;
         int nfev = 0;
-        int info = ls.run(phi, H->F, d0, a, fa, da, nfev);
+        int info;
+        if (o.method == 2) {
+            // Lloyd: the unit step, accepted as it is
+            const int cb = phi(1.0, fa, da);
+            nfev = 1;
+            if (cb > 0) {
+                rep.fevals += 1;
+                st = fail(H, SCVT_ERR_DEGENERATE, "the Lloyd step is not a valid tessellation");
+                break;
+            }
+            info = cb < 0 ? -1 : 1;
+        } else {
+            info = ls.run(phi, H->F, d0, a, fa, da, nfev);
+        }
         rep.fevals += nfev;
         if (info < 0) { st = cb_status; break; }
         if (info != 1) {
@@ -608,8 +625,9 @@ scvt_status scvt_lbfgs_solve(scvt_handle *H, double *z, const scvt_solve_opts *o
         unsigned long long mb = H->st_host->maxmove_bits;
         double maxmove;
         memcpy(&maxmove, &mb, sizeof(double));
-        if (H->m > 0 && ys > 1e-12 * sqrt(yy) * sqrt(ss)) {
+        if (o.method != 2 && H->m > 0 && ys > 1e-12 * sqrt(yy) * sqrt(ss)) {
             set_rho(B.rho, slot, B.st, s, &H->stats.kernel_launches);
+            if (o.method == 1) set_gamma(B.gamma, B.st, s, &H->stats.kernel_launches);
             if (H->hist_count == H->m) {
                 // the oldest pair's slot becomes the spare
                 int old = H->hist_slots[0];
@@ -625,7 +643,7 @@ scvt_status scvt_lbfgs_solve(scvt_handle *H, double *z, const scvt_solve_opts *o
                     if (!used[k]) { H->spare = k; break; }
             }
             H->hist_slots[H->hist_count++] = slot;
-        } else {
+        } else if (o.method != 2) {
             rep.skipped++;
         }
         std::swap(B.z, B.zt);

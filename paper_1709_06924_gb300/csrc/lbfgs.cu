@@ -102,32 +102,38 @@ __global__ void k_dot(int64_t len, const double *__restrict__ x, const double *_
     block_sum_store<1>(v, partials + blockIdx.x);
 }
 
-// q = -g (if h: q = -h g); partial dot w.q
+// q = -g (if h: q = -h g; else if hs: q = -hs[0] g); partial dot w.q
 __global__ void k_neg(int64_t len, const double *__restrict__ g, const double *__restrict__ h,
-                      double *__restrict__ q, const double *__restrict__ w, double *__restrict__ partials) {
+                      const double *__restrict__ hs, double *__restrict__ q, const double *__restrict__ w,
+                      double *__restrict__ partials) {
     int64_t b0, b1;
     chunk_of(len, b0, b1);
+    const double sc = hs ? hs[0] : 1.0;
     double v[1] = {0.0};
     for (int64_t i = b0 + threadIdx.x; i < b1; i += kRT) {
         double x = -g[i];
         if (h) x *= h[i / 3];
+        else if (hs) x *= sc;
         q[i] = x;
         v[0] += w[i] * x;
     }
     block_sum_store<1>(v, partials + blockIdx.x);
 }
 
-// q += sign * coef * x; if h: q *= h (per generator); partial dot w.q
+// q += sign * coef * x; if h: q *= h (per generator), else if hs: q *= hs[0];
+// partial dot w.q
 __global__ void k_axpy(int64_t len, double *__restrict__ q, const double *__restrict__ coef, double sign,
-                       const double *__restrict__ x, const double *__restrict__ h, const double *__restrict__ w,
-                       double *__restrict__ partials) {
+                       const double *__restrict__ x, const double *__restrict__ h, const double *__restrict__ hs,
+                       const double *__restrict__ w, double *__restrict__ partials) {
     int64_t b0, b1;
     chunk_of(len, b0, b1);
     const double a = sign * coef[0];
+    const double sc = hs ? hs[0] : 1.0;
     double v[1] = {0.0};
     for (int64_t i = b0 + threadIdx.x; i < b1; i += kRT) {
         double t = q[i] + a * x[i];
         if (h) t *= h[i / 3];
+        else if (hs) t *= sc;
         q[i] = t;
         v[0] += w[i] * t;
     }
@@ -233,6 +239,9 @@ __global__ void k_finish_batch(const InstGeom *__restrict__ inst, const int *__r
 
 __global__ void k_set_rho(double *rho, const DevStatus *st) { rho[0] = 1.0 / st->dots[0]; }
 
+// plain LBFGS: gamma = y.s / y.y of the newest pair (Sec. 2.2.2)
+__global__ void k_set_gamma(double *gamma, const DevStatus *st) { gamma[0] = st->dots[0] / st->dots[1]; }
+
 __global__ void k_differs(int64_t len, const double *__restrict__ a, const double *__restrict__ b, unsigned *flag) {
     int any = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x)
@@ -303,32 +312,38 @@ void set_rho(double *rho_dev, int k, const DevStatus *st, cudaStream_t s, int64_
     (*launches)++;
 }
 
-void two_loop(int n, const double *g, const double *h, int count, const double *const *S, const double *const *Y,
-              const double *const *rho, double *q, double *partials, double *scal, DevStatus *st, cudaStream_t s,
-              int64_t *launches) {
+void set_gamma(double *gamma_dev, const DevStatus *st, cudaStream_t s, int64_t *launches) {
+    k_set_gamma<<<1, 1, 0, s>>>(gamma_dev, st);
+    (*launches)++;
+}
+
+void two_loop(int n, const double *g, const double *h, const double *hs, int count, const double *const *S,
+              const double *const *Y, const double *const *rho, double *q, double *partials, double *scal,
+              DevStatus *st, cudaStream_t s, int64_t *launches) {
     const int64_t len = 3 * (int64_t)n;
     const int nb = reduce_blocks(len);
     double *alpha = scal, *coef = scal + 64;
     if (count == 0) {
-        k_neg<<<nb, kRT, 0, s>>>(len, g, h, q, g, partials);
+        k_neg<<<nb, kRT, 0, s>>>(len, g, h, hs, q, g, partials);
         k_finish_scalar<<<1, kRT, 0, s>>>(partials, nb, nullptr, nullptr, &st->dots[3]);
         (*launches) += 2;
         return;
     }
     // backward: newest (count-1) .. oldest (0)
-    k_neg<<<nb, kRT, 0, s>>>(len, g, nullptr, q, S[count - 1], partials);
+    k_neg<<<nb, kRT, 0, s>>>(len, g, nullptr, nullptr, q, S[count - 1], partials);
     (*launches)++;
     for (int k = count - 1; k >= 0; --k) {
         k_finish_scalar<<<1, kRT, 0, s>>>(partials, nb, rho[k], nullptr, alpha + k);
         const double *w = (k > 0) ? S[k - 1] : Y[0];
-        k_axpy<<<nb, kRT, 0, s>>>(len, q, alpha + k, -1.0, Y[k], (k > 0) ? nullptr : h, w, partials);
+        k_axpy<<<nb, kRT, 0, s>>>(len, q, alpha + k, -1.0, Y[k], (k > 0) ? nullptr : h, (k > 0) ? nullptr : hs, w,
+                                  partials);
         (*launches) += 2;
     }
     // forward: oldest .. newest
     for (int k = 0; k < count; ++k) {
         k_finish_scalar<<<1, kRT, 0, s>>>(partials, nb, rho[k], alpha + k, coef + k);
         const double *w = (k + 1 < count) ? Y[k + 1] : g;
-        k_axpy<<<nb, kRT, 0, s>>>(len, q, coef + k, 1.0, S[k], nullptr, w, partials);
+        k_axpy<<<nb, kRT, 0, s>>>(len, q, coef + k, 1.0, S[k], nullptr, nullptr, w, partials);
         (*launches) += 2;
     }
     k_finish_scalar<<<1, kRT, 0, s>>>(partials, nb, nullptr, nullptr, &st->dots[3]);

@@ -14,13 +14,16 @@ double *slot_Y(const Lane &L, int slot) { return slot_S(L, slot) + L.y_off; }
 // two-loop direction of lane L into its q rows; g.q in the lane's status block
 void enqueue_direction(EvalSet &E, Lane &L, double *partials, double *scal, int64_t *launches) {
     const double *S[kLaneMaxM], *Y[kLaneMaxM], *R[kLaneMaxM];
-    for (int k = 0; k < L.count; ++k) {
+    const int method = L.opt.method;
+    const int count = (method == 2) ? 0 : L.count;
+    for (int k = 0; k < count; ++k) {
         const int sl = L.slots[k];
         S[k] = slot_S(L, sl);
         Y[k] = slot_Y(L, sl);
         R[k] = L.rho + sl;
     }
-    two_loop(L.n, L.g, L.h, L.count, S, Y, R, E.q + 3 * L.row, partials, scal, &E.d_ist[L.b], E.stream, launches);
+    two_loop(L.n, L.g, method == 1 ? nullptr : L.h, (method == 1 && count > 0) ? L.rho + kLaneMaxM + 1 : nullptr,
+             count, S, Y, R, E.q + 3 * L.row, partials, scal, &E.d_ist[L.b], E.stream, launches);
 }
 
 cudaError_t sync_statuses(EvalSet &E) {
@@ -47,7 +50,8 @@ scvt_status lane_options(const scvt_solve_opts *in, scvt_solve_opts *o) {
     if (o->ls_max_evals <= 0) o->ls_max_evals = 10;
     if (o->c1 <= 0.0) o->c1 = 1e-4;
     if (o->c2 <= 0.0) o->c2 = 0.9;
-    if (o->max_iter < 0 || !(o->c1 < o->c2) || o->c2 >= 1.0) return SCVT_ERR_INVALID;
+    if (o->max_iter < 0 || !(o->c1 < o->c2) || o->c2 >= 1.0 || o->method < 0 || o->method > 2)
+        return SCVT_ERR_INVALID;
     return SCVT_OK;
 }
 
@@ -112,14 +116,16 @@ cudaError_t lockstep_round(EvalSet &E, std::vector<Lane *> &lanes, int m, double
         L->ls.ftol = L->opt.c1;
         L->ls.gtol = L->opt.c2;
         L->ls.maxfev = L->opt.ls_max_evals;
-        L->ls_state = L->ls.begin(L->F, L->d0, 1.0);
+        L->unit_step = L->opt.method == 2;
+        L->ls_state = L->unit_step ? 0 : L->ls.begin(L->F, L->d0, 1.0);
         if (L->ls_state == 0) ls.push_back(L);
     }
     bool first = true;
     while (!ls.empty() || (first && !init.empty())) {
         for (int b = 0; b < E.B; ++b) E.h_active[b] = 0;
         for (Lane *L : ls) {
-            trial_point(L->n, L->z, E.q + 3 * L->row, L->ls.trial(), E.zt + 3 * L->row, E.nrm + L->row, s, launches);
+            const double a = L->unit_step ? 1.0 : L->ls.trial();
+            trial_point(L->n, L->z, E.q + 3 * L->row, a, E.zt + 3 * L->row, E.nrm + L->row, s, launches);
             E.h_active[L->b] = 1;
         }
         if (first) {
@@ -157,8 +163,23 @@ cudaError_t lockstep_round(EvalSet &E, std::vector<Lane *> &lanes, int m, double
         for (Lane *L : ls) {
             const DevStatus &ds = E.h_ist[L->b];
             const scvt_status sb = status_of_flags(ds.flags);
-            // a step that breaks the tessellation is a failed trial, not an error
             L->g2_last = ds.red[1];
+            if (L->unit_step) {
+                // Lloyd: the unit step is taken as it is; a broken tessellation ends the lane
+                L->ls.nfev = 1;
+                L->ls.last_a = 1.0;
+                L->ls.last_f = ds.red[0];
+                L->ls.last_d = ds.red[2];
+                if (sb) {
+                    L->rep.fevals += 1;
+                    L->rep.status = SCVT_ERR_DEGENERATE;
+                    L->done = true;
+                    L->state_valid = false;
+                }
+                L->ls_state = 1;
+                continue;
+            }
+            // a step that breaks the tessellation is a failed trial, not an error
             L->ls_state = L->ls.feed(sb ? 1 : 0, sb ? 0.0 : ds.red[0], sb ? 0.0 : ds.red[2]);
             if (L->ls_state == 0) next.push_back(L);
         }
@@ -202,8 +223,9 @@ cudaError_t lockstep_round(EvalSet &E, std::vector<Lane *> &lanes, int m, double
         unsigned long long mb = ds.maxmove_bits;
         memcpy(&maxmove, &mb, sizeof(double));
         const int slot = L->spare;
-        if (m > 0 && ys > 1e-12 * sqrt(yy) * sqrt(ss)) {
+        if (L->opt.method != 2 && m > 0 && ys > 1e-12 * sqrt(yy) * sqrt(ss)) {
             set_rho(L->rho, slot, &E.d_ist[L->b], s, launches);
+            if (L->opt.method == 1) set_gamma(L->rho + kLaneMaxM + 1, &E.d_ist[L->b], s, launches);
             if (L->count == m) {
                 int old = L->slots[0];
                 for (int k = 1; k < L->count; ++k) L->slots[k - 1] = L->slots[k];
@@ -217,7 +239,7 @@ cudaError_t lockstep_round(EvalSet &E, std::vector<Lane *> &lanes, int m, double
                     if (!used[k]) { L->spare = k; break; }
             }
             L->slots[L->count++] = slot;
-        } else {
+        } else if (L->opt.method != 2) {
             L->rep.skipped++;
         }
         cudaMemcpyAsync(L->z, E.zt + 3 * L->row, sizeof(double) * 3 * L->n, cudaMemcpyDeviceToDevice, s);

@@ -21,6 +21,7 @@
 namespace scvt {
 
 constexpr int kLaneMaxM = 32;
+constexpr int kLaneRho = kLaneMaxM + 2;  // per-lane scalars: 1/(y.s) per slot, plain-LBFGS gamma last
 
 struct Lane {
     int b = 0;            // problem index in the EvalSet layout
@@ -29,7 +30,7 @@ struct Lane {
     double *z = nullptr, *g = nullptr, *h = nullptr;  // resident state (n x 3, n x 3, n)
     double *hist = nullptr;                 // S of slot k at hist + k slot_stride, Y at S + y_off
     size_t slot_stride = 0, y_off = 0;
-    double *rho = nullptr;                  // m + 1 doubles: 1 / (y.s) of each slot
+    double *rho = nullptr;                  // kLaneRho doubles: 1 / (y.s) of each slot, then gamma
     scvt_solve_opts opt;                    // this lane's options (defaults filled in)
     // solver state
     int slots[kLaneMaxM + 1];
@@ -40,6 +41,7 @@ struct Lane {
     WolfeSearch ls;
     int ls_state = 0;
     double d0 = 0.0, g2_last = 0.0;
+    bool unit_step = false;  // Lloyd: one evaluation at alpha = 1, no line search
 };
 
 void lane_reset_history(Lane &L, int m);

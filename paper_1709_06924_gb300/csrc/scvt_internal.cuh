@@ -171,9 +171,12 @@ void accept_pair(int n, const double *zt, const double *z, const double *gt, con
 // q = -H g by the two-loop recursion; pairs are given oldest first as host
 // arrays of device pointers, rho[k] -> 1/(y_k.s_k) on the device;
 // scal: device scratch of 128 doubles.  Leaves g.q in st->dots[3].
-void two_loop(int n, const double *g, const double *h, int count, const double *const *S, const double *const *Y,
-              const double *const *rho, double *q, double *partials, double *scal, DevStatus *st, cudaStream_t s,
-              int64_t *launches);
+// H0 = diag(h) per generator, or (h null) hs[0] I, or (both null) I.
+void two_loop(int n, const double *g, const double *h, const double *hs, int count, const double *const *S,
+              const double *const *Y, const double *const *rho, double *q, double *partials, double *scal,
+              DevStatus *st, cudaStream_t s, int64_t *launches);
+// gamma_dev[0] = y.s / y.y from st->dots (plain LBFGS scaling)
+void set_gamma(double *gamma_dev, const DevStatus *st, cudaStream_t s, int64_t *launches);
 void set_rho(double *rho_dev, int k, const DevStatus *st, cudaStream_t s, int64_t *launches);
 // st->differs = 1 if a[i] != b[i] for some i < len (bitwise on the values)
 void vec_differs(int64_t len, const double *a, const double *b, DevStatus *st, cudaStream_t s, int64_t *launches);

@@ -53,7 +53,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 size_t job_bytes(int64_t n, int m) {
     const size_t n3 = 3 * (size_t)n;
     return align256(8 * n3) * 2 + align256(8 * (size_t)n) + align256(8 * (size_t)(m + 1) * 2 * n3) +
-           align256(8 * (kLaneMaxM + 1)) + align256(4 * (size_t)n);
+           align256(8 * kLaneRho) + align256(4 * (size_t)n);
 }
 
 bool dev_ptr(const void *p) {
@@ -139,7 +139,7 @@ scvt_status admit(scvt_server *S) {
         L.hist = (double *)p;
         p += align256(8 * (size_t)(m + 1) * 2 * n3);
         L.rho = (double *)p;
-        p += align256(8 * (kLaneMaxM + 1));
+        p += align256(8 * kLaneRho);
         J.hints = (float *)p;
         L.n = J.n;
         L.slot_stride = 2 * n3;

@@ -14,6 +14,9 @@ from . import capi
 from .inputs import Density
 
 
+METHODS = {"plbfgs": 0, "lbfgs": 1, "lloyd": 2}
+
+
 def _ptr(x):
     if x is None:
         return None
@@ -114,11 +117,13 @@ class Engine:
         return out
 
     def lbfgs_solve(self, z, max_iter=200, grad_tol=1e-8, rel_grad_tol=0.0, rel_df_tol=0.0, step_tol=0.0,
-                    ls_max_evals=10, c1=1e-4, c2=0.9, warm_start=False):
-        """In-place solve on z; returns the report as a dict."""
+                    ls_max_evals=10, c1=1e-4, c2=0.9, warm_start=False, method="plbfgs"):
+        """In-place solve on z; returns the report as a dict.  method: "plbfgs"
+        (Lloyd-preconditioned LBFGS), "lbfgs" (H0 = gamma_n I) or "lloyd"."""
         self._sync_inputs()
         o = capi.scvt_solve_opts(int(max_iter), float(grad_tol), float(rel_grad_tol), float(rel_df_tol),
-                                 float(step_tol), int(ls_max_evals), float(c1), float(c2), int(warm_start))
+                                 float(step_tol), int(ls_max_evals), float(c1), float(c2), int(warm_start),
+                                 METHODS[method])
         rep = capi.scvt_lbfgs_solve(self._h, _ptr(z), o)
         torch.cuda.current_stream(self.device).wait_stream(self.stream)
         return {f: getattr(rep, f) for f, _ in capi.scvt_solve_report._fields_}
@@ -231,9 +236,10 @@ class Batch:
         return e, g
 
     def lbfgs_solve(self, z, max_iter=200, grad_tol=1e-8, rel_grad_tol=0.0, rel_df_tol=0.0, step_tol=0.0,
-                    ls_max_evals=10, c1=1e-4, c2=0.9, warm_start=0):
+                    ls_max_evals=10, c1=1e-4, c2=0.9, warm_start=0, method="plbfgs"):
         o = capi.scvt_solve_opts(int(max_iter), float(grad_tol), float(rel_grad_tol), float(rel_df_tol),
-                                 float(step_tol), int(ls_max_evals), float(c1), float(c2), int(warm_start))
+                                 float(step_tol), int(ls_max_evals), float(c1), float(c2), int(warm_start),
+                                 METHODS[method])
         with torch.cuda.device(self.device):
             reps = capi.scvt_batch_lbfgs_solve(self._b, _ptr(z), o, self.count)
         return [{f: getattr(r, f) for f, _ in capi.scvt_solve_report._fields_} for r in reps]
@@ -291,9 +297,9 @@ class Server:
         self.close()
 
     def submit(self, z0, density: Density, max_iter=200, grad_tol=1e-8, rel_grad_tol=0.0, rel_df_tol=0.0,
-               step_tol=0.0, ls_max_evals=10, c1=1e-4, c2=0.9) -> int:
+               step_tol=0.0, ls_max_evals=10, c1=1e-4, c2=0.9, method="plbfgs") -> int:
         o = capi.scvt_solve_opts(int(max_iter), float(grad_tol), float(rel_grad_tol), float(rel_df_tol),
-                                 float(step_tol), int(ls_max_evals), float(c1), float(c2), 0)
+                                 float(step_tol), int(ls_max_evals), float(c1), float(c2), 0, METHODS[method])
         n = int(z0.shape[0])
         with torch.cuda.device(self.device):
             jid = capi.scvt_server_submit(self._s, n, _density(density), _ptr(z0), o)

@@ -71,22 +71,22 @@ def test_batch_matches_the_oracle():
         assert np.max(np.abs(gs[k] - o["g"]) / cn) <= RTOL, k
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_batch_solve_equals_single_problem_solves_bitwise(precision):
+@pytest.mark.parametrize("precision,method", [(0, "plbfgs"), (1, "plbfgs"), (0, "lbfgs"), (0, "lloyd")])
+def test_batch_solve_equals_single_problem_solves_bitwise(precision, method):
     probs = PROBLEMS[:4]
     zs = inputs(probs, seed0=51)
     with Batch([n for n, _ in probs], [d for _, d in probs], precision=precision) as bt:
         zb = bt.concat([dev(z) for z in zs])
-        reps = bt.lbfgs_solve(zb, max_iter=12, grad_tol=0.0)
+        reps = bt.lbfgs_solve(zb, max_iter=12, grad_tol=0.0, method=method)
         # and a continuation of the same solve
-        reps2 = bt.lbfgs_solve(zb, max_iter=3, grad_tol=0.0, warm_start=1)
+        reps2 = bt.lbfgs_solve(zb, max_iter=3, grad_tol=0.0, warm_start=1, method=method)
         zb_out = bt.split(zb.cpu().numpy())
     keys = ("iters", "fevals", "resets", "skipped", "energy", "grad_norm", "converged", "status")
     for k, (n, dens) in enumerate(probs):
         with Engine(n, dens, precision=precision) as e:
             z = dev(zs[k])
-            r = e.lbfgs_solve(z, max_iter=12, grad_tol=0.0)
-            r2 = e.lbfgs_solve(z, max_iter=3, grad_tol=0.0, warm_start=1)
+            r = e.lbfgs_solve(z, max_iter=12, grad_tol=0.0, method=method)
+            r2 = e.lbfgs_solve(z, max_iter=3, grad_tol=0.0, warm_start=1, method=method)
             zk = z.cpu().numpy()
         for key in keys:
             assert reps[k][key] == r[key], (k, key, reps[k][key], r[key])

@@ -266,3 +266,30 @@ def test_density_series_and_its_fallback_match_oracle(kind):
     assert 3 <= st["series_terms"] / st["series_cells"] <= 19
     assert_geometry_close(g, o)
     assert abs(g["energy"] - o["F"]) <= RTOL * o["F"]
+
+
+@pytest.mark.parametrize("method", ["lbfgs", "lloyd"])
+@pytest.mark.parametrize("iters", [1, 5])
+def test_other_methods_lockstep_with_oracle(method, iters):
+    z = I.uniform_sphere(2562, 19)
+    dens = DENS["x3"]
+    zo, rep_o, tr = oracle.lbfgs_solve(z, dens, lbfgs_m=5, max_iter=iters, grad_tol=0.0, method=method)
+    with Engine(len(z), dens, lbfgs_m=5) as e:
+        zt = dev(z)
+        rep = e.lbfgs_solve(zt, max_iter=iters, grad_tol=0.0, method=method)
+    assert rep["iters"] == rep_o["iters"] == iters
+    assert rep["fevals"] == rep_o["fevals"]
+    assert rep["skipped"] == rep_o["skipped"] and rep["resets"] == rep_o["resets"]
+    assert abs(rep["energy"] - rep_o["energy"]) <= 1e-12 * rep_o["energy"]
+    assert np.abs(zt.cpu().numpy() - zo).max() <= 1e-11
+
+
+def test_lloyd_mode_matches_the_lloyd_step_entry():
+    z = I.uniform_sphere(4001, 21)
+    dens = DENS["tanh163842"]
+    with Engine(len(z), dens, lbfgs_m=5) as e:
+        zt = dev(z)
+        rep = e.lbfgs_solve(zt, max_iter=1, grad_tol=0.0, method="lloyd")
+        zl = e.lloyd_step(dev(z)).cpu().numpy()
+    assert rep["iters"] == 1 and rep["fevals"] == 2
+    assert np.abs(zt.cpu().numpy() - zl).max() <= 1e-14
