@@ -348,6 +348,18 @@ double scvt_server_clock(const scvt_server *s);
 scvt_status scvt_server_get_stats(const scvt_server *s, scvt_stats *out);
 const char *scvt_server_last_error(const scvt_server *s);
 
+/* Monte Carlo initialisation by the density (Sec. 4.1 starts its serial
+ * tests from it): candidate k is kept when u_k * rho_max <= rho(cand_k),
+ * rho_max the density's largest value (1 for rho = 1 and X3, the cap centre
+ * for the tanh kinds); the first n_target kept candidates, in candidate
+ * order, are written to z_out.  cand: m x 3 unit vectors (the caller draws
+ * them uniformly on S^2), u: m values in [0, 1), z_out: n_target x 3 -- each
+ * device or host.  *n_out (host) receives the number written, below
+ * n_target if the candidates run out.  1 <= m < 2^31.  Allocates and frees
+ * temporaries on the stream; synchronises it. */
+scvt_status scvt_sample_density(const scvt_density *rho, const double *cand, const double *u, int64_t m,
+                                int64_t n_target, double *z_out, int64_t *n_out, void *cuda_stream);
+
 /* Per-handle counters and (with profiling on) device times. */
 scvt_status scvt_get_stats(const scvt_handle *h, scvt_stats *out);
 scvt_status scvt_reset_stats(scvt_handle *h);

@@ -109,6 +109,8 @@ def lib():
             L.orc_lbfgs_solve.argtypes = [C.c_int, _dp, C.POINTER(_Density), C.POINTER(_Opts),
                                           C.POINTER(_Report), _dp, _dp, _dp, _ip]
             L.orc_lbfgs_solve.restype = C.c_int
+            L.orc_sample_density.argtypes = [C.POINTER(_Density), _dp, _dp, C.c_longlong, C.c_longlong, _dp]
+            L.orc_sample_density.restype = C.c_longlong
             L.orc_max_threads.argtypes = []
             L.orc_max_threads.restype = C.c_int
             _lib = L
@@ -276,6 +278,16 @@ def lbfgs_solve(z, density, lbfgs_m=5, max_iter=200, grad_tol=1e-8, rel_grad_tol
     if rc not in (OK, LINESEARCH):
         raise OracleError(rc, "lbfgs_solve")
     return z, report, trace
+
+
+def sample_density(density, cand, u, n_target):
+    """Monte Carlo initialisation: the first n_target candidates with
+    u_k rho_max <= rho(cand_k), in order."""
+    cand = _f64(cand)
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    out = np.zeros((int(n_target), 3))
+    k = lib().orc_sample_density(C.byref(_density(density)), _p(cand), _p(u), len(u), int(n_target), _p(out))
+    return out[:k]
 
 
 def max_threads() -> int:

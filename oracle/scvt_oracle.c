@@ -653,6 +653,35 @@ static double rho_eval(const orc_density *r, const double *p)
 
 double orc_rho(const orc_density *r, const double *p) { return rho_eval(r, p); }
 
+/* largest value of the density on S^2: 1 for rho = 1 and X3 (at the poles);
+ * the tanh cap at its centre (d = 0), to the 4th power for that kind */
+static double rho_max(const orc_density *r)
+{
+    if (r->kind == 0 || r->kind == 1) return 1.0;
+    double v = (1.0 - r->gamma) / (1.0 + exp(-2.0 * r->beta / r->alpha)) + r->gamma;
+    if (r->kind == 3) { v = v * v; v = v * v; }
+    return v;
+}
+
+/* Monte Carlo initialisation by the density (Sec. 4.1): candidate k (a
+ * uniform point on S^2) is kept when u_k rho_max <= rho(cand_k), u_k uniform
+ * on [0, 1); the first n_target kept candidates, in candidate order, are the
+ * generators.  Returns the number written (fewer than n_target when the
+ * candidates run out). */
+long long orc_sample_density(const orc_density *r, const double *cand, const double *u, long long m,
+                             long long n_target, double *z_out)
+{
+    const double rm = rho_max(r);
+    long long k = 0;
+    for (long long i = 0; i < m && k < n_target; i++) {
+        if (u[i] * rm <= rho_eval(r, cand + 3 * i)) {
+            for (int d = 0; d < 3; d++) z_out[3 * k + d] = cand[3 * i + d];
+            k++;
+        }
+    }
+    return k;
+}
+
 /* ======================================================================
  * Quadrature over signed spherical sub-triangles (Sec. 3.2.2)
  * ====================================================================== */

@@ -119,6 +119,8 @@ SIGNATURES = {
     "scvt_server_clock": (C.c_double, [_H]),
     "scvt_server_get_stats": (_st, [_H, C.POINTER(scvt_stats)]),
     "scvt_server_last_error": (C.c_char_p, [_H]),
+    "scvt_sample_density": (_st, [C.POINTER(scvt_density), _vp, _vp, C.c_int64, C.c_int64, _vp,
+                                  C.POINTER(C.c_int64), _vp]),
 }
 
 STATIC_MAX_N = 16384  # SCVT_STATIC_MAX_N
@@ -345,3 +347,11 @@ def scvt_server_get_stats(s) -> scvt_stats:
     st = scvt_stats()
     check(lib().scvt_server_get_stats(s, C.byref(st)), "scvt_server_get_stats", server=s)
     return st
+
+
+def scvt_sample_density(rho: scvt_density, cand_ptr: int, u_ptr: int, m: int, n_target: int, out_ptr: int,
+                        stream: int | None = None) -> int:
+    k = C.c_int64()
+    check(lib().scvt_sample_density(C.byref(rho), _vp(cand_ptr), _vp(u_ptr), int(m), int(n_target), _vp(out_ptr),
+                                    C.byref(k), _vp(stream or 0)), "scvt_sample_density")
+    return k.value

@@ -224,7 +224,7 @@ __global__ void k_scan_add(int *__restrict__ out, int len, const int *__restrict
 }
 
 // recursive exclusive scan; tmp must hold sum over levels of ceil(len/2048)
-void exclusive_scan(const int *in, int *out, int len, int *tmp, cudaStream_t s, int64_t *launches) {
+void scan_rec(const int *in, int *out, int len, int *tmp, cudaStream_t s, int64_t *launches) {
     int tiles = (len + 2047) / 2048;
     if (tiles <= 1) {
         k_scan_tiles<<<1, 1024, 0, s>>>(in, out, len, nullptr);
@@ -233,7 +233,7 @@ void exclusive_scan(const int *in, int *out, int len, int *tmp, cudaStream_t s, 
     }
     int *totals = tmp, *tot_scan = tmp + tiles;
     k_scan_tiles<<<tiles, 1024, 0, s>>>(in, out, len, totals);
-    exclusive_scan(totals, tot_scan, tiles, tmp + 2 * tiles, s, launches);
+    scan_rec(totals, tot_scan, tiles, tmp + 2 * tiles, s, launches);
     k_scan_add<<<tiles, 1024, 0, s>>>(out, len, tot_scan);
     (*launches) += 2;
 }
@@ -1733,6 +1733,10 @@ void bin_points(const double *z, const Grid &g, int *bin_of, int *count, int *st
 __global__ void k_set_total_from(int *arr, int n, const int *last_in) {
     // arr[n] = arr[n-1] + last_in[n-1]: total of an exclusive scan
     arr[n] = arr[n - 1] + last_in[n - 1];
+}
+
+void exclusive_scan(const int *in, int *out, int len, int *tmp, cudaStream_t s, int64_t *launches) {
+    scan_rec(in, out, len, tmp, s, launches);
 }
 
 int bins_per_edge(int64_t n, int bin_load) {

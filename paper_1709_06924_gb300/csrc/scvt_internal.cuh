@@ -51,6 +51,27 @@ struct DensityF {
     float gamma, beta, inv_alpha, xc0, xc1, xc2;
 };
 
+// The density at a unit vector p, directly from its definition: 1; X3
+// (1 - gamma) z^4 + gamma; the tanh cap on the geodesic distance d to x_c in
+// its logistic form (1 - gamma) / (1 + exp(-2 (beta - d) / alpha)) + gamma,
+// to the 4th power for kind 3.
+__device__ __forceinline__ double rho_value(const Density &r, double px, double py, double pz) {
+    if (r.kind == 0) return 1.0;
+    if (r.kind == 1) {
+        const double z2 = pz * pz;
+        return (1.0 - r.gamma) * z2 * z2 + r.gamma;
+    }
+    const double cx = py * r.xc2 - pz * r.xc1, cy = pz * r.xc0 - px * r.xc2, cz = px * r.xc1 - py * r.xc0;
+    const double d = atan2(sqrt(cx * cx + cy * cy + cz * cz), px * r.xc0 + py * r.xc1 + pz * r.xc2);
+    const double inv_alpha = 1.0 / r.alpha;
+    double v = (1.0 - r.gamma) / (1.0 + exp(-2.0 * (r.beta - d) * inv_alpha)) + r.gamma;
+    if (r.kind == 3) {
+        v = v * v;
+        v = v * v;
+    }
+    return v;
+}
+
 // One problem of a batch: its generators occupy positions (and original
 // indices) [p0, p0 + n) of the concatenated arrays, its G x G x 6 bins start
 // at bin0 of the concatenated bin array.
@@ -145,6 +166,8 @@ void cell_passes(const Grid &g, const CellOut &out, const CellBuf &cb, int *list
                  bool mixed, const Tune &t, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1, int64_t *launches,
                  int64_t *cell_launches);
 Density to_device_density(const scvt_density &r);
+// exclusive scan of len ints (tmp: 2 * (len / 2048 + 64) + 64 ints)
+void exclusive_scan(const int *in, int *out, int len, int *tmp, cudaStream_t s, int64_t *launches);
 DensityF to_density32(const Density &d);
 
 // ---- reductions and vector kernels (lbfgs.cu) ----

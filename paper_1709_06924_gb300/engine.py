@@ -328,3 +328,15 @@ class Server:
     def stats(self):
         s = capi.scvt_server_get_stats(self._s)
         return {f: getattr(s, f) for f, _ in capi.scvt_stats._fields_}
+
+
+def sample_density(density: Density, cand, u, n_target: int):
+    """Monte Carlo initialisation by the density on the GPU: the first
+    n_target candidates with u_k rho_max <= rho(cand_k), in order (numpy in,
+    numpy out)."""
+    cand = np.ascontiguousarray(cand, dtype=np.float64)
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    out = np.empty((int(n_target), 3))
+    k = capi.scvt_sample_density(_density(density), cand.ctypes.data, u.ctypes.data, len(u), int(n_target),
+                                 out.ctypes.data)
+    return out[:k]

@@ -47,6 +47,14 @@ def latlon_to_xyz(lat_deg: float, lon_deg: float) -> tuple:
     return tuple(v)
 
 
+def mc_candidates(m: int, seed: int):
+    """Inputs of the Monte Carlo initialisation: m candidate points uniform on
+    S^2 and m acceptance variates uniform on [0, 1) (seeded)."""
+    cand = uniform_sphere(m, seed)
+    u = np.random.default_rng(seed + 7919).random(m)
+    return cand, u
+
+
 def uniform_sphere(n: int, seed: int) -> np.ndarray:
     """n points uniform on S^2 as a contiguous (n, 3) float64 array."""
     if n < 0:
