@@ -109,6 +109,10 @@ def lib():
             L.orc_lbfgs_solve.argtypes = [C.c_int, _dp, C.POINTER(_Density), C.POINTER(_Opts),
                                           C.POINTER(_Report), _dp, _dp, _dp, _ip]
             L.orc_lbfgs_solve.restype = C.c_int
+            L.orc_bisect.argtypes = [C.c_int, _dp, _dp, C.c_int, _ip]
+            L.orc_bisect.restype = C.c_int
+            L.orc_mesh_quality.argtypes = [C.c_int, _dp, _dp, _dp, C.c_int, _ip]
+            L.orc_mesh_quality.restype = C.c_int
             L.orc_sample_density.argtypes = [C.POINTER(_Density), _dp, _dp, C.c_longlong, C.c_longlong, _dp]
             L.orc_sample_density.restype = C.c_longlong
             L.orc_max_threads.argtypes = []
@@ -278,6 +282,32 @@ def lbfgs_solve(z, density, lbfgs_m=5, max_iter=200, grad_tol=1e-8, rel_grad_tol
     if rc not in (OK, LINESEARCH):
         raise OracleError(rc, "lbfgs_solve")
     return z, report, trace
+
+
+def bisect(z):
+    """Bisection refinement: z followed by the Delaunay-edge midpoints (i < j, lexicographic)."""
+    z = _f64(z)
+    n = z.shape[0]
+    cap = 4 * n
+    out = np.zeros((cap, 3))
+    k = C.c_int()
+    rc = lib().orc_bisect(n, _p(z), _p(out), cap, C.byref(k))
+    if rc != OK:
+        raise OracleError(rc, "bisect")
+    return out[:k.value]
+
+
+def mesh_quality(z):
+    """(cellQ per generator, triQ per Delaunay triangle in sorted-triple order)."""
+    z = _f64(z)
+    n = z.shape[0]
+    cq = np.zeros(n)
+    tq = np.zeros(2 * n)
+    k = C.c_int()
+    rc = lib().orc_mesh_quality(n, _p(z), _p(cq), _p(tq), 2 * n, C.byref(k))
+    if rc != OK:
+        raise OracleError(rc, "mesh_quality")
+    return cq, tq[:k.value]
 
 
 def sample_density(density, cand, u, n_target):

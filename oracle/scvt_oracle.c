@@ -621,6 +621,114 @@ int orc_voronoi(int n, const double *z, int *deg, int *nbr, double *vx, int cap)
     return ORC_OK;
 }
 
+static double arc3(const double *a, const double *b)
+{
+    double c[3];
+    cross3(a, b, c);
+    return atan2(sqrt(dot3(c, c)), dot3(a, b));
+}
+
+static int cmp_int(const void *a, const void *b)
+{
+    int x = *(const int *)a, y = *(const int *)b;
+    return (x > y) - (x < y);
+}
+
+static int cmp_tri(const void *a, const void *b)
+{
+    const int *x = (const int *)a, *y = (const int *)b;
+    for (int k = 0; k < 3; k++)
+        if (x[k] != y[k]) return (x[k] > y[k]) - (x[k] < y[k]);
+    return 0;
+}
+
+/* Bisection refinement (Sec. 4.3, the optimisation-bisection initialisation):
+ * the n generators followed by the midpoints normalize(z_i + z_j) of the
+ * Delaunay edges (i < j), in lexicographic (i, j) order.  *n_out = n + E. */
+int orc_bisect(int n, const double *z, double *out, int cap, int *n_out)
+{
+    vor_t V;
+    int rc = build_voronoi(n, z, &V);
+    if (rc != ORC_OK) return rc;
+    int m = n + V.off[n] / 2;
+    if (m > cap) { vor_free(&V); return ORC_INVALID; }
+    memcpy(out, z, sizeof(double) * 3 * (size_t)n);
+    int t = n, js[256];
+    for (int i = 0; i < n; i++) {
+        int d = 0;
+        for (int e = V.off[i]; e < V.off[i + 1]; e++)
+            if (V.nbr[e] > i && d < 256) js[d++] = V.nbr[e];
+        qsort(js, (size_t)d, sizeof(int), cmp_int);
+        for (int k = 0; k < d; k++) {
+            double mp[3];
+            for (int c = 0; c < 3; c++) mp[c] = z[3 * (size_t)i + c] + z[3 * (size_t)js[k] + c];
+            double r = sqrt(dot3(mp, mp));
+            for (int c = 0; c < 3; c++) out[3 * (size_t)t + c] = mp[c] / r;
+            t++;
+        }
+    }
+    vor_free(&V);
+    *n_out = t;
+    return t == m ? ORC_OK : ORC_DEGENERATE;
+}
+
+/* Mesh quality measures (Sec. 4): cellQ(V) = min / max edge length of the
+ * Voronoi cell, triQ = (a+b-c)(b+c-a)(c+a-b)/(abc) of a Delaunay triangle
+ * with edge lengths a, b, c; lengths are great-circle arc lengths.  cellq:
+ * n values (nullable); triq: the triangles ordered by their sorted vertex
+ * triple (i < j < k), *n_tri of them (2n - 4). */
+int orc_mesh_quality(int n, const double *z, double *cellq, double *triq, int tri_cap, int *n_tri)
+{
+    hull_t H;
+    int rc = hull_build(&H, n, z);
+    if (rc != ORC_OK) return rc;
+    vor_t V;
+    rc = voronoi_from_hull(&H, &V);
+    if (rc != ORC_OK) { hull_free(&H); return rc; }
+    if (cellq) {
+        for (int i = 0; i < n; i++) {
+            int d = V.off[i + 1] - V.off[i];
+            double lo = INFINITY, hi = 0.0;
+            for (int k = 0; k < d; k++) {
+                const double *a = V.vx + 3 * (size_t)(V.off[i] + k);
+                const double *b = V.vx + 3 * (size_t)(V.off[i] + (k + 1) % d);
+                double L = arc3(a, b);
+                if (L < lo) lo = L;
+                if (L > hi) hi = L;
+            }
+            cellq[i] = lo / hi;
+        }
+    }
+    int nt = 0;
+    for (int f = 0; f < H.nf; f++)
+        if (H.f[f].alive) nt++;
+    int *tri = (int *)malloc(sizeof(int) * 3 * (size_t)(nt ? nt : 1));
+    if (!tri) { vor_free(&V); hull_free(&H); return ORC_NOMEM; }
+    int t = 0;
+    for (int f = 0; f < H.nf; f++) {
+        if (!H.f[f].alive) continue;
+        int v[3] = {H.f[f].v[0], H.f[f].v[1], H.f[f].v[2]};
+        qsort(v, 3, sizeof(int), cmp_int);
+        memcpy(tri + 3 * (size_t)t, v, sizeof(v));
+        t++;
+    }
+    qsort(tri, (size_t)nt, 3 * sizeof(int), cmp_tri);
+    if (triq) {
+        if (nt > tri_cap) { free(tri); vor_free(&V); hull_free(&H); return ORC_INVALID; }
+        for (int k = 0; k < nt; k++) {
+            const double *A = z + 3 * (size_t)tri[3 * k], *B = z + 3 * (size_t)tri[3 * k + 1];
+            const double *Cp = z + 3 * (size_t)tri[3 * k + 2];
+            double a = arc3(B, Cp), b = arc3(Cp, A), c = arc3(A, B);
+            triq[k] = (a + b - c) * (b + c - a) * (c + a - b) / (a * b * c);
+        }
+    }
+    if (n_tri) *n_tri = nt;
+    free(tri);
+    vor_free(&V);
+    hull_free(&H);
+    return ORC_OK;
+}
+
 /* ======================================================================
  * Point densities (Sec. 4)
  * ====================================================================== */
