@@ -348,17 +348,37 @@ double scvt_server_clock(const scvt_server *s);
 scvt_status scvt_server_get_stats(const scvt_server *s, scvt_stats *out);
 const char *scvt_server_last_error(const scvt_server *s);
 
+/* Bisection refinement (Sec. 4.3: the optimisation-bisection procedure
+ * that initialises the large meshes): z_out receives the N generators z
+ * followed by the midpoints normalize(z_i + z_j) of all Delaunay edges
+ * i < j, in lexicographic (i, j) order -- 4N - 6 points for a full
+ * triangulation.  z: N x 3; z_out: cap x 3 (device or host).  *n_out (host)
+ * receives the count; INVALID if it exceeds cap or a cell has more than 32
+ * neighbours.  Synchronises. */
+scvt_status scvt_bisect(scvt_handle *h, const double *z, double *z_out, int64_t cap, int64_t *n_out);
+
+/* Mesh quality measures of Sec. 4: cellq[i] = min / max great-circle length
+ * of the edges of Voronoi cell i (N values, nullable); triq = (a+b-c)(b+c-a)
+ * (c+a-b)/(abc) of every Delaunay triangle with arc lengths a, b, c (1 for
+ * an equilateral triangle), triangles (i < j < k) in lexicographic order,
+ * up to tri_cap values (nullable).  *n_tri (host) receives the number of
+ * triangles (2N - 4); INVALID if it exceeds tri_cap or a cell has more than
+ * 32 neighbours.  Device or host arrays.  Synchronises. */
+scvt_status scvt_mesh_quality(scvt_handle *h, const double *z, double *cellq, double *triq, int64_t tri_cap,
+                              int64_t *n_tri);
+
 /* Monte Carlo initialisation by the density (Sec. 4.1 starts its serial
- * tests from it): candidate k is kept when u_k * rho_max <= rho(cand_k),
+ * tests from it): candidate k is kept when u_k * rho_max^e <= rho(cand_k)^e,
  * rho_max the density's largest value (1 for rho = 1 and X3, the cap centre
  * for the tanh kinds); the first n_target kept candidates, in candidate
- * order, are written to z_out.  cand: m x 3 unit vectors (the caller draws
+ * order, are written to z_out.  exponent e in (0, 4]: 1 samples by rho,
+ * 1/2 by rho^(1/2), the asymptotic CVT generator density on a surface.  cand: m x 3 unit vectors (the caller draws
  * them uniformly on S^2), u: m values in [0, 1), z_out: n_target x 3 -- each
  * device or host.  *n_out (host) receives the number written, below
  * n_target if the candidates run out.  1 <= m < 2^31.  Allocates and frees
  * temporaries on the stream; synchronises it. */
-scvt_status scvt_sample_density(const scvt_density *rho, const double *cand, const double *u, int64_t m,
-                                int64_t n_target, double *z_out, int64_t *n_out, void *cuda_stream);
+scvt_status scvt_sample_density(const scvt_density *rho, double exponent, const double *cand, const double *u,
+                                int64_t m, int64_t n_target, double *z_out, int64_t *n_out, void *cuda_stream);
 
 /* Per-handle counters and (with profiling on) device times. */
 scvt_status scvt_get_stats(const scvt_handle *h, scvt_stats *out);

@@ -113,7 +113,8 @@ def lib():
             L.orc_bisect.restype = C.c_int
             L.orc_mesh_quality.argtypes = [C.c_int, _dp, _dp, _dp, C.c_int, _ip]
             L.orc_mesh_quality.restype = C.c_int
-            L.orc_sample_density.argtypes = [C.POINTER(_Density), _dp, _dp, C.c_longlong, C.c_longlong, _dp]
+            L.orc_sample_density.argtypes = [C.POINTER(_Density), C.c_double, _dp, _dp, C.c_longlong, C.c_longlong,
+                                             _dp]
             L.orc_sample_density.restype = C.c_longlong
             L.orc_max_threads.argtypes = []
             L.orc_max_threads.restype = C.c_int
@@ -310,13 +311,14 @@ def mesh_quality(z):
     return cq, tq[:k.value]
 
 
-def sample_density(density, cand, u, n_target):
+def sample_density(density, cand, u, n_target, exponent=1.0):
     """Monte Carlo initialisation: the first n_target candidates with
-    u_k rho_max <= rho(cand_k), in order."""
+    u_k rho_max^e <= rho(cand_k)^e, in order."""
     cand = _f64(cand)
     u = np.ascontiguousarray(u, dtype=np.float64)
     out = np.zeros((int(n_target), 3))
-    k = lib().orc_sample_density(C.byref(_density(density)), _p(cand), _p(u), len(u), int(n_target), _p(out))
+    k = lib().orc_sample_density(C.byref(_density(density)), float(exponent), _p(cand), _p(u), len(u),
+                                 int(n_target), _p(out))
     return out[:k]
 
 

@@ -771,18 +771,25 @@ static double rho_max(const orc_density *r)
     return v;
 }
 
+/* rho^e: e = 1 and e = 1/2 exactly, pow otherwise */
+static double rho_pow(double v, double e)
+{
+    return e == 1.0 ? v : (e == 0.5 ? sqrt(v) : pow(v, e));
+}
+
 /* Monte Carlo initialisation by the density (Sec. 4.1): candidate k (a
- * uniform point on S^2) is kept when u_k rho_max <= rho(cand_k), u_k uniform
- * on [0, 1); the first n_target kept candidates, in candidate order, are the
- * generators.  Returns the number written (fewer than n_target when the
- * candidates run out). */
-long long orc_sample_density(const orc_density *r, const double *cand, const double *u, long long m,
+ * uniform point on S^2) is kept when u_k rho_max^e <= rho(cand_k)^e, u_k
+ * uniform on [0, 1); the first n_target kept candidates, in candidate order,
+ * are the generators (e = 1: sampled by rho; e = 1/2: by the asymptotic CVT
+ * point density rho^(1/2) of a surface).  Returns the number written (fewer
+ * than n_target when the candidates run out). */
+long long orc_sample_density(const orc_density *r, double e, const double *cand, const double *u, long long m,
                              long long n_target, double *z_out)
 {
-    const double rm = rho_max(r);
+    const double rm = rho_pow(rho_max(r), e);
     long long k = 0;
     for (long long i = 0; i < m && k < n_target; i++) {
-        if (u[i] * rm <= rho_eval(r, cand + 3 * i)) {
+        if (u[i] * rm <= rho_pow(rho_eval(r, cand + 3 * i), e)) {
             for (int d = 0; d < 3; d++) z_out[3 * k + d] = cand[3 * i + d];
             k++;
         }

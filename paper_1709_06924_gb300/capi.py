@@ -119,7 +119,9 @@ SIGNATURES = {
     "scvt_server_clock": (C.c_double, [_H]),
     "scvt_server_get_stats": (_st, [_H, C.POINTER(scvt_stats)]),
     "scvt_server_last_error": (C.c_char_p, [_H]),
-    "scvt_sample_density": (_st, [C.POINTER(scvt_density), _vp, _vp, C.c_int64, C.c_int64, _vp,
+    "scvt_bisect": (_st, [_H, _vp, _vp, C.c_int64, C.POINTER(C.c_int64)]),
+    "scvt_mesh_quality": (_st, [_H, _vp, _vp, _vp, C.c_int64, C.POINTER(C.c_int64)]),
+    "scvt_sample_density": (_st, [C.POINTER(scvt_density), C.c_double, _vp, _vp, C.c_int64, C.c_int64, _vp,
                                   C.POINTER(C.c_int64), _vp]),
 }
 
@@ -349,9 +351,22 @@ def scvt_server_get_stats(s) -> scvt_stats:
     return st
 
 
-def scvt_sample_density(rho: scvt_density, cand_ptr: int, u_ptr: int, m: int, n_target: int, out_ptr: int,
-                        stream: int | None = None) -> int:
+def scvt_sample_density(rho: scvt_density, exponent: float, cand_ptr: int, u_ptr: int, m: int, n_target: int,
+                        out_ptr: int, stream: int | None = None) -> int:
     k = C.c_int64()
-    check(lib().scvt_sample_density(C.byref(rho), _vp(cand_ptr), _vp(u_ptr), int(m), int(n_target), _vp(out_ptr),
-                                    C.byref(k), _vp(stream or 0)), "scvt_sample_density")
+    check(lib().scvt_sample_density(C.byref(rho), float(exponent), _vp(cand_ptr), _vp(u_ptr), int(m), int(n_target),
+                                    _vp(out_ptr), C.byref(k), _vp(stream or 0)), "scvt_sample_density")
+    return k.value
+
+
+def scvt_bisect(h, z_ptr: int, out_ptr: int, cap: int) -> int:
+    k = C.c_int64()
+    check(lib().scvt_bisect(h, _vp(z_ptr), _vp(out_ptr), int(cap), C.byref(k)), "scvt_bisect", h)
+    return k.value
+
+
+def scvt_mesh_quality(h, z_ptr: int, cellq_ptr, triq_ptr, tri_cap: int) -> int:
+    k = C.c_int64()
+    check(lib().scvt_mesh_quality(h, _vp(z_ptr), _vp(cellq_ptr), _vp(triq_ptr), int(tri_cap), C.byref(k)),
+          "scvt_mesh_quality", h)
     return k.value

@@ -269,6 +269,29 @@ scvt_status make_direction(scvt_handle *H, double *d0, int method) {
 
 }  // namespace
 
+namespace {
+
+// topology of z into deg (n) and nbr (n x 32) allocated on the stream; every
+// cell must have at most 32 neighbours
+scvt_status topology32(scvt_handle *H, const double *zd, int **deg, int **nbr) {
+    const size_t n = H->n;
+    *deg = nullptr;
+    *nbr = nullptr;
+    CK(cudaMallocAsync((void **)deg, sizeof(int) * n, H->stream), "degree buffer");
+    CK(cudaMallocAsync((void **)nbr, sizeof(int) * n * 32, H->stream), "neighbour buffer");
+    double F, g2;
+    scvt_status s = evaluate_dev(H, zd, H->b.gt, H->b.ht, H->b.fc, nullptr, nullptr, *deg, *nbr, 32, nullptr,
+                                 nullptr, &F, &g2, nullptr);
+    if (s) return s;
+    std::vector<int> hd(n);
+    CK(cudaMemcpy(hd.data(), *deg, sizeof(int) * n, cudaMemcpyDeviceToHost), "degree check");
+    for (size_t i = 0; i < n; ++i)
+        if (hd[i] > 32) return fail(H, SCVT_ERR_INVALID, "a cell has more than 32 neighbours");
+    return SCVT_OK;
+}
+
+}  // namespace
+
 // ======================================================================
 extern "C" {
 
@@ -471,7 +494,78 @@ scvt_status scvt_voronoi(scvt_handle *H, const double *z, int *deg, int *nbr, in
     return SCVT_OK;
 }
 
-scvt_status scvt_lbfgs_direction(scvt_handle *H, const double *g, const double *hdiag, int count, const double *S,
+scvt_status scvt_bisect(scvt_handle *H, const double *z, double *z_out, int64_t cap, int64_t *n_out) {
+    if (!H) return SCVT_ERR_INVALID;
+    if (!z || !z_out || !n_out || cap < 0) return fail(H, SCVT_ERR_INVALID, "bad argument");
+    const int n = H->n;
+    const double *zd;
+    scvt_status s = stage_in(H, z, 3 * (size_t)n, H->b.stage_a, &zd);
+    if (s) return s;
+    int *deg = nullptr, *nbr = nullptr;
+    double *tmp = nullptr;
+    s = topology32(H, zd, &deg, &nbr);
+    const bool dev_out = is_device_ptr(z_out);
+    if (s == SCVT_OK && !dev_out && cap > 0) {
+        cudaError_t e = cudaMallocAsync((void **)&tmp, sizeof(double) * 3 * (size_t)cap, H->stream);
+        if (e != cudaSuccess) s = cuda_fail(H, e, "output buffer");
+    }
+    if (s == SCVT_OK) {
+        cudaError_t e = bisect_midpoints(n, zd, deg, nbr, 32, H->b.list1, H->b.list2, H->b.escan,
+                                         dev_out ? z_out : tmp, cap, n_out, H->stream);
+        if (e != cudaSuccess) s = cuda_fail(H, e, "bisection");
+        else if (*n_out > cap) s = fail(H, SCVT_ERR_INVALID, "z_out holds fewer points than the refinement");
+        else if (!dev_out && *n_out > 0) {
+            e = cudaMemcpyAsync(z_out, tmp, sizeof(double) * 3 * (size_t)*n_out, cudaMemcpyDeviceToHost, H->stream);
+            if (e != cudaSuccess) s = cuda_fail(H, e, "copy out");
+        }
+    }
+    void *bufs[] = {deg, nbr, tmp};
+    for (void *p : bufs)
+        if (p) cudaFreeAsync(p, H->stream);
+    cudaError_t e = cudaStreamSynchronize(H->stream);
+    if (s == SCVT_OK && e != cudaSuccess) s = cuda_fail(H, e, "bisection");
+    return s;
+}
+
+scvt_status scvt_mesh_quality(scvt_handle *H, const double *z, double *cellq, double *triq,
+                                         int64_t tri_cap, int64_t *n_tri) {
+    if (!H) return SCVT_ERR_INVALID;
+    if (!z || !n_tri || (triq && tri_cap < 0)) return fail(H, SCVT_ERR_INVALID, "bad argument");
+    const int n = H->n;
+    const double *zd;
+    scvt_status s = stage_in(H, z, 3 * (size_t)n, H->b.stage_a, &zd);
+    if (s) return s;
+    int *deg = nullptr, *nbr = nullptr;
+    double *tc = nullptr, *tt = nullptr;
+    s = topology32(H, zd, &deg, &nbr);
+    const bool dev_c = cellq && is_device_ptr(cellq), dev_t = triq && is_device_ptr(triq);
+    cudaError_t e = cudaSuccess;
+    if (s == SCVT_OK && cellq && !dev_c) e = cudaMallocAsync((void **)&tc, sizeof(double) * (size_t)n, H->stream);
+    if (s == SCVT_OK && e == cudaSuccess && triq && !dev_t && tri_cap > 0)
+        e = cudaMallocAsync((void **)&tt, sizeof(double) * (size_t)tri_cap, H->stream);
+    if (e != cudaSuccess) s = cuda_fail(H, e, "output buffers");
+    if (s == SCVT_OK) {
+        e = mesh_quality(n, zd, deg, nbr, 32, H->b.list1, H->b.list2, H->b.escan, cellq ? (dev_c ? cellq : tc) : nullptr,
+                         triq ? (dev_t ? triq : tt) : nullptr, tri_cap, n_tri, H->stream);
+        if (e != cudaSuccess) s = cuda_fail(H, e, "mesh quality");
+        else if (triq && *n_tri > tri_cap) s = fail(H, SCVT_ERR_INVALID, "triq holds fewer values than triangles");
+        else {
+            if (tc) e = cudaMemcpyAsync(cellq, tc, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, H->stream);
+            if (e == cudaSuccess && tt && *n_tri > 0)
+                e = cudaMemcpyAsync(triq, tt, sizeof(double) * (size_t)*n_tri, cudaMemcpyDeviceToHost, H->stream);
+            if (e != cudaSuccess) s = cuda_fail(H, e, "copy out");
+        }
+    }
+    void *bufs[] = {deg, nbr, tc, tt};
+    for (void *p : bufs)
+        if (p) cudaFreeAsync(p, H->stream);
+    e = cudaStreamSynchronize(H->stream);
+    if (s == SCVT_OK && e != cudaSuccess) s = cuda_fail(H, e, "mesh quality");
+    return s;
+}
+
+scvt_status scvt_lbfgs_direction(scvt_handle *H, const double *g, const double *hdiag, int count,
+                                            const double *S,
                                  const double *Y, double *q) {
     if (!H) return SCVT_ERR_INVALID;
     if (!g || !hdiag || !q || count < 0 || count > 64 || (count > 0 && (!S || !Y)))

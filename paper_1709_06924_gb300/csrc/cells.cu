@@ -766,6 +766,12 @@ __global__ void __launch_bounds__(128) k_topo(Grid g, CellOut out, CellBuf cb,
                 if (q == p) continue;
                 const V3 d = sub(ld(g.zs + q), zi);
                 if (dot(d, d) > 4.0 * (double)R2 * (1.0 + 1e-6)) continue;
+                // every listed neighbour has been clipped by already: its bisector
+                // may be an edge now, and clipping by a line of the polygon again
+                // would solve two identical lines for a corner
+                bool listed = false;
+                for (int t = 0; t < L.cnt && !listed; ++t) listed = L.j[t] == q;
+                if (listed) continue;
                 unsigned long long used = 0ull;
                 for (int v = 0; v < P.nv; ++v)
                     if (P.ln[P.cur][v] >= K + 4) used |= 1ull << (P.ln[P.cur][v] - (K + 4));

@@ -17,12 +17,17 @@ using namespace scvt;
 
 namespace {
 
-__global__ void k_sample_flags(Density r, double rmax, const double *__restrict__ cand, const double *__restrict__ u,
-                               int m, int *__restrict__ flag) {
+// rho^e: e = 1 and e = 1/2 exactly, pow otherwise
+__host__ __device__ __forceinline__ double rho_pow(double v, double e) {
+    return e == 1.0 ? v : (e == 0.5 ? sqrt(v) : pow(v, e));
+}
+
+__global__ void k_sample_flags(Density r, double e, double rmax, const double *__restrict__ cand,
+                               const double *__restrict__ u, int m, int *__restrict__ flag) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m) return;
     const double v = rho_value(r, cand[3 * (size_t)i], cand[3 * (size_t)i + 1], cand[3 * (size_t)i + 2]);
-    flag[i] = (u[i] * rmax <= v) ? 1 : 0;
+    flag[i] = (u[i] * rmax <= rho_pow(v, e)) ? 1 : 0;
 }
 
 __global__ void k_sample_scatter(const double *__restrict__ cand, const int *__restrict__ flag,
@@ -63,9 +68,11 @@ double rho_max(const Density &r) {
 
 }  // namespace
 
-extern "C" scvt_status scvt_sample_density(const scvt_density *rho, const double *cand, const double *u, int64_t m,
-                                           int64_t n_target, double *z_out, int64_t *n_out, void *cuda_stream) {
+extern "C" scvt_status scvt_sample_density(const scvt_density *rho, double exponent, const double *cand,
+                                           const double *u, int64_t m, int64_t n_target, double *z_out,
+                                           int64_t *n_out, void *cuda_stream) {
     if (!rho || !cand || !u || !z_out || !n_out || m < 1 || m > INT_MAX - 1 || n_target < 0) return SCVT_ERR_INVALID;
+    if (!(exponent > 0.0) || !(exponent <= 4.0)) return SCVT_ERR_INVALID;
     if (rho->kind < 0 || rho->kind > 3) return SCVT_ERR_INVALID;
     if (rho->kind >= 2 && !(rho->alpha > 0.0)) return SCVT_ERR_INVALID;
     cudaStream_t s = (cudaStream_t)cuda_stream;
@@ -93,7 +100,7 @@ extern "C" scvt_status scvt_sample_density(const scvt_density *rho, const double
         double *o = dout ? dout : z_out;
         int64_t launches = 0;
         const unsigned blocks = (unsigned)((M + 255) / 256);
-        k_sample_flags<<<blocks, 256, 0, s>>>(d, rho_max(d), c, uu, M, flag);
+        k_sample_flags<<<blocks, 256, 0, s>>>(d, exponent, rho_pow(rho_max(d), exponent), c, uu, M, flag);
         exclusive_scan(flag, pos, M, tmp, s, &launches);
         k_sample_scatter<<<blocks, 256, 0, s>>>(c, flag, pos, M, (long long)n_target, o, cnt);
         e = cudaGetLastError();

@@ -170,6 +170,15 @@ Density to_device_density(const scvt_density &r);
 void exclusive_scan(const int *in, int *out, int len, int *tmp, cudaStream_t s, int64_t *launches);
 DensityF to_density32(const Density &d);
 
+// ---- bisection refinement and mesh quality (refine.cu) ----
+// deg / nbr: neighbour cycles with original ids, at most maxd per cell;
+// cnt, off: n ints of scratch; scan_tmp as for exclusive_scan.  *n_out /
+// *n_tri receive the sizes; nothing is written when they exceed cap.
+cudaError_t bisect_midpoints(int n, const double *z, const int *deg, const int *nbr, int maxd, int *cnt, int *off,
+                             int *scan_tmp, double *out, int64_t cap, int64_t *n_out, cudaStream_t s);
+cudaError_t mesh_quality(int n, const double *z, const int *deg, const int *nbr, int maxd, int *cnt, int *off,
+                         int *scan_tmp, double *cellq, double *triq, int64_t cap, int64_t *n_tri, cudaStream_t s);
+
 // ---- reductions and vector kernels (lbfgs.cu) ----
 int reduce_blocks(int64_t n);
 // red[0] = sum fcell, red[1] = sum |g|^2, red[2] = sum g_i.q_i / nrm_i (if q)

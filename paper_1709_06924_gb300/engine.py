@@ -156,6 +156,23 @@ class Engine:
     def set_profiling(self, on=True):
         capi.scvt_set_profiling(self._h, on)
 
+    def bisect(self, z):
+        """Bisection refinement: z followed by its Delaunay-edge midpoints (i < j, lexicographic)."""
+        out = self._tensor(4 * self.n, 3)
+        self._sync_inputs()
+        k = capi.scvt_bisect(self._h, _ptr(z), out.data_ptr(), 4 * self.n)
+        torch.cuda.current_stream(self.device).wait_stream(self.stream)
+        return out[:k]
+
+    def mesh_quality(self, z):
+        """(cellQ per generator, triQ per Delaunay triangle in lexicographic order)."""
+        cq = self._tensor(self.n)
+        tq = self._tensor(2 * self.n)
+        self._sync_inputs()
+        k = capi.scvt_mesh_quality(self._h, _ptr(z), cq.data_ptr(), tq.data_ptr(), 2 * self.n)
+        torch.cuda.current_stream(self.device).wait_stream(self.stream)
+        return cq, tq[:k]
+
     def set_tuning(self, **kw):
         """Launch shape / search parameters (results do not depend on them)."""
         t = capi.scvt_get_tuning(self._h)
@@ -330,13 +347,13 @@ class Server:
         return {f: getattr(s, f) for f, _ in capi.scvt_stats._fields_}
 
 
-def sample_density(density: Density, cand, u, n_target: int):
+def sample_density(density: Density, cand, u, n_target: int, exponent: float = 1.0):
     """Monte Carlo initialisation by the density on the GPU: the first
-    n_target candidates with u_k rho_max <= rho(cand_k), in order (numpy in,
-    numpy out)."""
+    n_target candidates with u_k rho_max^e <= rho(cand_k)^e, in order (numpy
+    in, numpy out)."""
     cand = np.ascontiguousarray(cand, dtype=np.float64)
     u = np.ascontiguousarray(u, dtype=np.float64)
     out = np.empty((int(n_target), 3))
-    k = capi.scvt_sample_density(_density(density), cand.ctypes.data, u.ctypes.data, len(u), int(n_target),
-                                 out.ctypes.data)
+    k = capi.scvt_sample_density(_density(density), float(exponent), cand.ctypes.data, u.ctypes.data, len(u),
+                                 int(n_target), out.ctypes.data)
     return out[:k]

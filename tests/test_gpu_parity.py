@@ -293,3 +293,17 @@ def test_lloyd_mode_matches_the_lloyd_step_entry():
         zl = e.lloyd_step(dev(z)).cpu().numpy()
     assert rep["iters"] == 1 and rep["fevals"] == 2
     assert np.abs(zt.cpu().numpy() - zl).max() <= 1e-14
+
+
+def test_cells_wider_than_the_neighbour_search_match_oracle():
+    # a narrow cap sampled by rho^(1/2) at small N: most generators inside the
+    # cap, a few hundred outside with cells reaching ~60 degrees; those cells
+    # need the last pass's clip by every generator within the security radius
+    dens = I.density_x64()
+    cand, u = I.mc_candidates(400000, 2024)
+    z = oracle.sample_density(dens, cand, u, 2562, 0.5)
+    g = gpu_eval(z, dens)
+    o = oracle.energy_grad(z, dens)
+    _, nbr_o, _ = oracle.voronoi(z)
+    assert_topology_equal(g["deg"], g["nbr"], nbr_o)
+    assert_geometry_close(g, o)

@@ -47,3 +47,14 @@ def test_tanh_cap_kept_fraction():
     p = zonal_integral(rho_of_cos) / (4 * math.pi * rmax)
     frac, _ = _kept_fraction(d)
     assert abs(frac - p) <= 5 * math.sqrt(p * (1 - p) / 200000)
+
+
+def test_square_root_sampling_kept_fraction():
+    # e = 1/2: kept with probability sqrt(rho / rho_max); for X3 that is the
+    # mean of sqrt((1 - g) z^4 + g), a zonal integral
+    d = I.density_x3()
+    cand, u = I.mc_candidates(200000, 8)
+    z = oracle.sample_density(d, cand, u, 200000, exponent=0.5)
+    p = zonal_integral(lambda t: np.sqrt((1 - d.gamma) * t ** 4 + d.gamma)) / (4 * math.pi)
+    frac = len(z) / 200000
+    assert abs(frac - p) <= 5 * math.sqrt(p * (1 - p) / 200000)
