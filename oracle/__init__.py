@@ -174,10 +174,12 @@ def voronoi(z):
     return deg, [nbr[off[i]:off[i + 1]].copy() for i in range(n)], [vx[off[i]:off[i + 1]].copy() for i in range(n)]
 
 
-def energy_grad(z, density, rule=None, exact_jacobian=False, nthreads=0):
+def energy_grad(z, density, rule=None, exact_jacobian=False, nthreads=0, fan=False):
     """Evaluate the Sec. 3.1 quantities.  ``rule`` = (bary[nq,3], w[nq]) replaces
     the 7-point rule (weights summing to 1); ``exact_jacobian`` integrates with
-    the exact Jacobian of the radial projection instead of area scaling."""
+    the exact Jacobian of the radial projection instead of area scaling;
+    ``fan`` integrates one triangle (z_i, v_a, v_b) per Voronoi edge instead of
+    the two sub-triangles through the Delaunay-edge midpoint."""
     z = _f64(z)
     n = z.shape[0]
     F = C.c_double(0.0)
@@ -193,6 +195,8 @@ def energy_grad(z, density, rule=None, exact_jacobian=False, nthreads=0):
         qb = _f64(rule[0], (-1, 3))
         qw = _f64(rule[1], (-1,))
         mode, nq = (2 if exact_jacobian else 1), qb.shape[0]
+    if fan:
+        mode |= 4
     rc = lib().orc_energy_grad(n, _p(z), C.byref(_density(density)), mode, nq, _p(qb), _p(qw),
                                C.byref(F), _p(g), _p(h), _p(m), _p(c), _p(Fi), C.byref(gn), int(nthreads))
     if rc != OK:

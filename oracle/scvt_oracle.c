@@ -806,6 +806,8 @@ typedef struct {
     double bary[64][3];
     double w[64];     /* weights summing to 1 over the triangle */
     int exact_jac;    /* 0: area-scaled radial projection, 1: exact Jacobian */
+    int fan;          /* 1: one triangle (z_i, v_a, v_b) per Voronoi edge instead of the
+                         two sub-triangles through the Delaunay-edge midpoint */
 } qrule_t;
 
 /* 7-point degree-5 rule (Radon): centroid, and two orbits (a, a, 1-2a) with
@@ -817,6 +819,7 @@ static void rule_radon7(qrule_t *R)
     double w1 = (155.0 - s15) / 1200.0, w2 = (155.0 + s15) / 1200.0;
     R->nq = 7;
     R->exact_jac = 0;
+    R->fan = 0;
     R->bary[0][0] = R->bary[0][1] = R->bary[0][2] = 1.0 / 3.0;
     R->w[0] = 9.0 / 40.0;
     double orb[2][2] = {{a1, w1}, {a2, w2}};
@@ -877,6 +880,10 @@ static void cell_integrals(const vor_t *V, const double *z, int i, const qrule_t
     for (int t = 0; t < d; t++) {
         const double *va = V->vx + 3 * (size_t)(b0 + t);
         const double *vb = V->vx + 3 * (size_t)(b0 + (t + 1) % d);
+        if (R->fan) {
+            tri_accum(R, rho, zi, zi, va, vb, m, cm, e);
+            continue;
+        }
         const double *zj = z + 3 * (size_t)V->nbr[b0 + t];
         double mu[3] = {zi[0] + zj[0], zi[1] + zj[1], zi[2] + zj[2]};
         normalize3(mu);
@@ -958,6 +965,7 @@ static int eval_all(int n, const double *z, const orc_density *rho, const qrule_
 }
 
 /* Exported evaluation.  rule_mode 0: Radon 7-point (the method's rule).
+ * rule_mode | 4: the fan decomposition (one triangle per Voronoi edge).
  * rule_mode 1/2: caller-supplied rule (nq points, barycentric qb[nq*3], weights
  * qw[nq] summing to 1) with area scaling (1) or the exact Jacobian of the
  * radial projection det[a,b,c]/|x|^3 (2). */
@@ -967,9 +975,17 @@ int orc_energy_grad(int n, const double *z, const orc_density *rho, int rule_mod
 {
     if (n < 4 || !z || !rho) return ORC_INVALID;
     qrule_t R, *rp = NULL;
+    const int fan = (rule_mode & 4) != 0;
+    rule_mode &= 3;
+    if (rule_mode == 0 && fan) {
+        rule_radon7(&R);
+        R.fan = 1;
+        rp = &R;
+    }
     if (rule_mode != 0) {
         if (nq < 1 || nq > 64 || !qb || !qw) return ORC_INVALID;
         R.nq = nq;
+        R.fan = fan;
         R.exact_jac = (rule_mode == 2);
         for (int k = 0; k < nq; k++) {
             R.bary[k][0] = qb[3 * k]; R.bary[k][1] = qb[3 * k + 1]; R.bary[k][2] = qb[3 * k + 2];

@@ -216,3 +216,34 @@ def test_gradient_matches_finite_differences():
         worst_7 = max(worst_7, abs(fd_7 - r_7["g"][i] @ t) / scale)
     assert worst_hi < 1e-7
     assert worst_7 < 1e-3
+
+
+# ---- the fan decomposition: one triangle (z_i, v_a, v_b) per Voronoi edge
+@pytest.mark.parametrize("n,seed", [(12, None), (2562, 2)])
+def test_fan_total_area_and_platonic_symmetry(n, seed):
+    z = I.platonic(12) if seed is None else I.uniform_sphere(n, seed)
+    r = oracle.energy_grad(z, UNI, fan=True)
+    assert abs(r["m"].sum() / (4 * math.pi) - 1) < 1e-13
+    if seed is None:
+        assert np.allclose(r["m"], math.pi / 3, rtol=1e-13, atol=0)
+        assert np.abs(r["g"]).max() <= 1e-14 * r["m"].max()
+
+
+def test_fan_integrates_the_voronoi_cell_itself():
+    # the fan covers exactly the Voronoi polygon: areas exact, first moments
+    # and energies approach the Stokes closed form of the polygon
+    errs = []
+    for n in (642, 2562, 10242):
+        z = I.uniform_sphere(n, 5)
+        r = oracle.energy_grad(z, UNI, fan=True)
+        _, nbr, vx = oracle.voronoi(z)
+        me = np.array([polygon_area(z[i], vx[i]) for i in range(n)])
+        ce = np.array([polygon_first_moment(vx[i]) for i in range(n)])
+        assert np.allclose(r["m"], me, rtol=1e-12, atol=0)
+        errs.append(np.max(np.abs(r["c"] - ce).max(axis=1) / np.linalg.norm(ce, axis=1)))
+    assert errs[0] > errs[1] > errs[2] and errs[2] < 1e-5
+    # and both decompositions approximate the same integrals
+    z = I.uniform_sphere(10242, 5)
+    a = oracle.energy_grad(z, I.density_x3(), fan=True)
+    b = oracle.energy_grad(z, I.density_x3())
+    assert abs(a["F"] - b["F"]) / b["F"] < 1e-4
