@@ -79,6 +79,10 @@ typedef struct {
     int lbfgs_m;        /* number of (s, y) pairs kept, 0..32 (the paper uses 7) */
     int knn_k0;         /* first-pass neighbour count, 0 = default (32); 8..32 */
     int knn_kmax;       /* largest neighbour count of the retry passes, 0 = default (128) */
+    int decomposition;  /* 0: per Voronoi edge the two signed sub-triangles (z_i, v_a, mu), (z_i, mu, v_b)
+                           through the Delaunay-edge midpoint mu (Sec. 3.2.2, the paper's six
+                           sub-triangles per Delaunay triangle).  1: the fan, one triangle
+                           (z_i, v_a, v_b) per Voronoi edge. */
 } scvt_config;
 
 typedef struct {

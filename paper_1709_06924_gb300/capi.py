@@ -30,7 +30,7 @@ class scvt_density(C.Structure):
 
 class scvt_config(C.Structure):
     _fields_ = [("n", C.c_int64), ("rho", scvt_density), ("quad_points", C.c_int), ("precision", C.c_int),
-                ("lbfgs_m", C.c_int), ("knn_k0", C.c_int), ("knn_kmax", C.c_int)]
+                ("lbfgs_m", C.c_int), ("knn_k0", C.c_int), ("knn_kmax", C.c_int), ("decomposition", C.c_int)]
 
 
 class scvt_solve_opts(C.Structure):

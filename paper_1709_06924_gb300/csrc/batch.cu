@@ -82,6 +82,7 @@ scvt_status validate_config(const scvt_config &c) {
     if (c.lbfgs_m < 0 || c.lbfgs_m > kLaneMaxM) return SCVT_ERR_INVALID;
     if (c.quad_points != 0 && c.quad_points != 7) return SCVT_ERR_INVALID;
     if (c.precision != 0 && c.precision != 1) return SCVT_ERR_INVALID;
+    if (c.decomposition != 0 && c.decomposition != 1) return SCVT_ERR_INVALID;
     if (c.rho.kind < 0 || c.rho.kind > 3) return SCVT_ERR_INVALID;
     if (c.rho.kind != SCVT_RHO_UNIFORM) {
         if (!(c.rho.gamma > 0.0) || !(c.rho.gamma <= 1.0)) return SCVT_ERR_INVALID;
@@ -133,7 +134,9 @@ scvt_status scvt_batch_create(const scvt_config *cfgs, int count, void *cuda_str
     int64_t ntot = 0;
     for (int b = 0; b < count; ++b) {
         if (validate_config(cfgs[b])) return SCVT_ERR_INVALID;
-        if (cfgs[b].precision != cfgs[0].precision || cfgs[b].lbfgs_m != cfgs[0].lbfgs_m) return SCVT_ERR_INVALID;
+        if (cfgs[b].precision != cfgs[0].precision || cfgs[b].lbfgs_m != cfgs[0].lbfgs_m ||
+            cfgs[b].decomposition != cfgs[0].decomposition)
+            return SCVT_ERR_INVALID;
         ntot += cfgs[b].n;
     }
     if (ntot > (int64_t)200000000) return SCVT_ERR_INVALID;
@@ -149,6 +152,7 @@ scvt_status scvt_batch_create(const scvt_config *cfgs, int count, void *cuda_str
     cudaError_t e = cudaStreamCreateWithFlags(&BT->stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreate(&BT->ev_in);
     if (e == cudaSuccess) e = evalset_alloc(BT->E, ntot, count, cfgs[0].precision, BT->stream);
+    BT->E.fan = cfgs[0].decomposition;
 #define AL(ptr, cnt) \
     if (e == cudaSuccess) e = balloc(BT, &(ptr), (cnt))
     AL(BT->z, n3); AL(BT->g, n3); AL(BT->h, N);

@@ -156,6 +156,7 @@ scvt_status evaluate_dev(scvt_handle *H, const double *zdev, double *grad, doubl
     g.bstart = B.start;
     g.rho0 = to_device_density(H->cfg.rho);
     g.rho0f = to_density32(g.rho0);
+    g.fan = H->cfg.decomposition;
     if (!H->radius_valid) {
         CK(cudaMemsetAsync(B.radius, 0, sizeof(float) * n, s), "reset radius hints");
         H->radius_valid = true;
@@ -336,6 +337,7 @@ scvt_status scvt_create(const scvt_config *cfg, void *cuda_stream, scvt_handle *
     if (cfg->lbfgs_m < 0 || cfg->lbfgs_m > kMaxM) return SCVT_ERR_INVALID;
     if (cfg->quad_points != 0 && cfg->quad_points != 7) return SCVT_ERR_INVALID;
     if (cfg->precision != 0 && cfg->precision != 1) return SCVT_ERR_INVALID;
+    if (cfg->decomposition != 0 && cfg->decomposition != 1) return SCVT_ERR_INVALID;
     if (cfg->rho.kind < 0 || cfg->rho.kind > 3) return SCVT_ERR_INVALID;
     if (cfg->rho.kind != SCVT_RHO_UNIFORM) {
         if (!(cfg->rho.gamma > 0.0) || !(cfg->rho.gamma <= 1.0)) return SCVT_ERR_INVALID;

@@ -839,9 +839,13 @@ __global__ void __launch_bounds__(128) k_topo(Grid g, CellOut out, CellBuf cb,
                     corners_first = vb;
                 } else {
                     const int kprev = (k0 + t2 - 1) % nv;
-                    V3 mu = unit(add(zi, ld(g.zs + P.gen_of(P.ln[c][kprev]))));
-                    tri(rho, inv_alpha, zi, va, mu, acc);
-                    tri(rho, inv_alpha, zi, mu, vb, acc);
+                    if (g.fan) {
+                        tri(rho, inv_alpha, zi, va, vb, acc);
+                    } else {
+                        V3 mu = unit(add(zi, ld(g.zs + P.gen_of(P.ln[c][kprev]))));
+                        tri(rho, inv_alpha, zi, va, mu, acc);
+                        tri(rho, inv_alpha, zi, mu, vb, acc);
+                    }
                 }
                 va = vb;
             }
@@ -1505,8 +1509,12 @@ __global__ void __launch_bounds__(512) k_quad(Grid g, CellBuf cb, int ecap) {
     const int K = cb.serK ? cb.serK[p] : 0;
     const double *ser = cb.ser + (size_t)p * kSerStride;
     Acc acc = {0, 0, 0, 0, 0};
-    tri(rho, inv_alpha, zi, va, mu, acc, ser, K);
-    tri(rho, inv_alpha, zi, mu, vb, acc, ser, K);
+    if (g.fan) {
+        tri(rho, inv_alpha, zi, va, vb, acc, ser, K);
+    } else {
+        tri(rho, inv_alpha, zi, va, mu, acc, ser, K);
+        tri(rho, inv_alpha, zi, mu, vb, acc, ser, K);
+    }
     double *ea = cb.eacc;
     ea[e] = acc.m;
     ea[(size_t)ecap + e] = acc.cx;
@@ -1670,8 +1678,12 @@ __global__ void __launch_bounds__(512) k_quad32(Grid g, CellBuf cb, int ecap) {
     const float3 om = make_float3(d.x * is + hp.x * t, d.y * is + hp.y * t, d.z * is + hp.z * t);
     const DensityF rf = g.rhof ? g.rhof[view_of(g, p).b] : g.rho0f;
     AccF a = {0, 0, 0, 0, 0};
-    tri32(rf, hp, make_float3(va.x, va.y, va.z), om, a);
-    tri32(rf, hp, om, make_float3(vb.x, vb.y, vb.z), a);
+    if (g.fan) {
+        tri32(rf, hp, make_float3(va.x, va.y, va.z), make_float3(vb.x, vb.y, vb.z), a);
+    } else {
+        tri32(rf, hp, make_float3(va.x, va.y, va.z), om, a);
+        tri32(rf, hp, om, make_float3(vb.x, vb.y, vb.z), a);
+    }
     float *ea = (float *)cb.eacc;
     ea[e] = a.m;
     ea[(size_t)ecap + e] = a.ox;

@@ -57,6 +57,7 @@ Grid make_grid(const EvalSet &E) {
     g.rhof = E.d_rhof;
     g.ist = E.d_ist;
     g.active = E.d_active;
+    g.fan = E.fan;
     return g;
 }
 

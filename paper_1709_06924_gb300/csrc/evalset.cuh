@@ -25,6 +25,7 @@ struct EvalSet {
     int64_t cap_n = 0;
     int cap_b = 0;
     int precision = 0;
+    int fan = 0;
     cudaStream_t stream = nullptr;
     // current layout
     int B = 0;

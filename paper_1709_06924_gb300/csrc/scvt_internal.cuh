@@ -95,6 +95,7 @@ struct Grid {
     const int *bstart;      // nbins + 1 offsets into zs
     Density rho0;           // density of a single problem
     DensityF rho0f;
+    int fan;                // 1: one triangle (z_i, v_a, v_b) per Voronoi edge
     // batch of problems (all null for a single problem)
     const InstGeom *inst;   // per problem
     const int *pinst;       // problem of each position / original index

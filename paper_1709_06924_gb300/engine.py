@@ -41,9 +41,11 @@ def _density(d: Density) -> capi.scvt_density:
 
 class Engine:
     def __init__(self, n: int, density: Density, lbfgs_m: int = 7, knn_k0: int = 0,
-                 device: int | torch.device = 0, stream: torch.cuda.Stream | None = None, precision: int = 0):
+                 device: int | torch.device = 0, stream: torch.cuda.Stream | None = None, precision: int = 0,
+                 decomposition: int = 0):
         """precision: 0 = FP64 throughout, 1 = mixed (FP32 corners and quadrature in local
-        coordinates, FP64 predicates filter, sums and LBFGS)."""
+        coordinates, FP64 predicates filter, sums and LBFGS).  decomposition: 0 = the
+        paper's sub-triangles through the Delaunay-edge midpoints, 1 = the fan."""
         self.n = int(n)
         self.device = torch.device("cuda", device) if isinstance(device, int) else torch.device(device)
         with torch.cuda.device(self.device):
@@ -56,6 +58,7 @@ class Engine:
         cfg.lbfgs_m = int(lbfgs_m)
         cfg.knn_k0 = int(knn_k0)
         cfg.knn_kmax = 0
+        cfg.decomposition = int(decomposition)
         with torch.cuda.device(self.device):
             self._h = capi.scvt_create(cfg, self.stream.cuda_stream)
 
@@ -191,7 +194,7 @@ class Engine:
         return {f: getattr(t, f) for f, _ in capi.scvt_tuning._fields_}
 
 
-def _config(n, density, lbfgs_m, precision):
+def _config(n, density, lbfgs_m, precision, decomposition=0):
     cfg = capi.scvt_config()
     cfg.n = int(n)
     cfg.rho = _density(density)
@@ -200,6 +203,7 @@ def _config(n, density, lbfgs_m, precision):
     cfg.lbfgs_m = int(lbfgs_m)
     cfg.knn_k0 = 0
     cfg.knn_kmax = 0
+    cfg.decomposition = int(decomposition)
     return cfg
 
 
@@ -209,7 +213,8 @@ class Batch:
     Points of problem b are rows offsets[b]:offsets[b+1] of one (N_tot, 3)
     array; use split() / concat() to move between the two views."""
 
-    def __init__(self, ns, densities, lbfgs_m: int = 7, precision: int = 0, device: int | torch.device = 0):
+    def __init__(self, ns, densities, lbfgs_m: int = 7, precision: int = 0, device: int | torch.device = 0,
+                 decomposition: int = 0):
         if len(ns) != len(densities):
             raise ValueError("one density per problem")
         self.ns = [int(n) for n in ns]
@@ -217,7 +222,7 @@ class Batch:
         self.offsets = np.concatenate([[0], np.cumsum(self.ns)]).astype(np.int64)
         self.ntot = int(self.offsets[-1])
         self.device = torch.device("cuda", device) if isinstance(device, int) else torch.device(device)
-        cfgs = [_config(n, d, lbfgs_m, precision) for n, d in zip(self.ns, densities)]
+        cfgs = [_config(n, d, lbfgs_m, precision, decomposition) for n, d in zip(self.ns, densities)]
         with torch.cuda.device(self.device):
             self._b = capi.scvt_batch_create(cfgs, torch.cuda.current_stream(self.device).cuda_stream)
 

@@ -175,3 +175,14 @@ def test_single_problem_autotuner_keeps_results():
         assert t == e.tuning()
         F1, g1, _, _ = e.energy_grad(z)
     assert F1 == F0 and torch.equal(g1, g0)
+
+
+def test_fan_batch_equals_fan_single_problems():
+    zs = inputs(PROBLEMS[:3], seed0=141)
+    with Batch([n for n, _ in PROBLEMS[:3]], [d for _, d in PROBLEMS[:3]], decomposition=1) as bt:
+        e, g = bt.energy_grad(bt.concat([dev(z) for z in zs]))
+        gs = bt.split(g.cpu().numpy())
+    for k, (n, dens) in enumerate(PROBLEMS[:3]):
+        with Engine(n, dens, decomposition=1) as en:
+            F, gk, _, _ = en.energy_grad(dev(zs[k]))
+        assert e[k] == F and np.array_equal(gs[k], gk.cpu().numpy())

@@ -25,8 +25,8 @@ from tests.parity import assert_topology_equal
 BOUNDS = {"m": 1e-5, "c": 1e-5, "F_i": 2e-5, "g": 1e-6, "h": 1e-5, "F": 2e-6, "gnorm": 2e-6}
 
 
-def mixed_eval(z, dens):
-    with Engine(len(z), dens, precision=1) as e:
+def mixed_eval(z, dens, decomposition=0):
+    with Engine(len(z), dens, precision=1, decomposition=decomposition) as e:
         zt = torch.from_numpy(z).cuda()
         out = e.evaluate(zt)
         deg, nbr = e.voronoi(zt, max_deg=64)
@@ -35,16 +35,17 @@ def mixed_eval(z, dens):
     return res
 
 
-@pytest.mark.parametrize("n,seed,dens", [
-    (2562, 0, I.density_uniform()),
-    (5001, 1, I.density_x3()),
-    (40962, 2, I.density_x64()),
-    (163842, 3, I.WORKLOADS["tanh-2621442"].density),
+@pytest.mark.parametrize("n,seed,dens,fan", [
+    (2562, 0, I.density_uniform(), 0),
+    (5001, 1, I.density_x3(), 0),
+    (40962, 2, I.density_x64(), 0),
+    (163842, 3, I.WORKLOADS["tanh-2621442"].density, 0),
+    (40962, 4, I.WORKLOADS["tanh-163842"].density, 1),
 ])
-def test_mixed_precision_error_against_oracle(n, seed, dens):
+def test_mixed_precision_error_against_oracle(n, seed, dens, fan):
     z = I.uniform_sphere(n, seed)
-    r = mixed_eval(z, dens)
-    o = oracle.energy_grad(z, dens)
+    r = mixed_eval(z, dens, fan)
+    o = oracle.energy_grad(z, dens, fan=bool(fan))
     _, nbr_o, _ = oracle.voronoi(z)
     assert_topology_equal(r["deg"], r["nbr"], nbr_o)
     cn = np.linalg.norm(o["c"], axis=1)

@@ -307,3 +307,14 @@ def test_cells_wider_than_the_neighbour_search_match_oracle():
     _, nbr_o, _ = oracle.voronoi(z)
     assert_topology_equal(g["deg"], g["nbr"], nbr_o)
     assert_geometry_close(g, o)
+
+
+@pytest.mark.parametrize("n,seed,dname", [(2562, 30, "uniform"), (5001, 31, "x3"), (40962, 32, "tanh2621442"),
+                                          (12, None, "uniform")])
+def test_fan_decomposition_matches_oracle(n, seed, dname):
+    z = I.platonic(12) if seed is None else I.uniform_sphere(n, seed)
+    dens = DENS[dname]
+    g = gpu_eval(z, dens, decomposition=1)
+    o = oracle.energy_grad(z, dens, fan=True)
+    assert_geometry_close(g, o)
+    assert abs(g["energy"] - o["F"]) <= RTOL * o["F"]
