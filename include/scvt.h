@@ -215,7 +215,7 @@ scvt_status scvt_energy_grad_static(int64_t n, const scvt_density *rho, const do
 /* Launch shape and search parameters of an evaluation (not in the paper:
  * GPU scheduling).  None of them changes a result -- a cell is unique, its
  * corners come from its neighbour triples and its sums are taken in its own
- * edge order -- only the time.  Defaults: 2, 24, 4, 16, 256, 32. */
+ * edge order -- only the time.  Defaults: 2, 24, 4, 16, 256, 32, 1. */
 typedef struct {
     int bin_load;           /* target generators per cube-map bin, 1..16: G = ceil(sqrt(N / (6 bin_load)))
                                bins per face edge */
@@ -225,13 +225,15 @@ typedef struct {
     int topo_blocks_per_sm; /* grid cap of the topology pass in blocks per SM, 1..64 */
     int quad_block;         /* threads per block of the per-edge quadrature: 128, 256 or 512 */
     int topo_cell_lanes;    /* lanes per cell in the topology pass: 32 (one cell per warp) or 16 (two) */
+    int chunks;             /* cell pipelines run concurrently on forked streams, 1..4 */
 } scvt_tuning;
 
 /* Set / read the tuning of a handle.  INVALID when a field is out of range. */
 scvt_status scvt_set_tuning(scvt_handle *h, const scvt_tuning *t);
 scvt_status scvt_get_tuning(const scvt_handle *h, scvt_tuning *t);
 /* Autotuner: times evaluations at z (N x 3, device or host) over a grid of
- * tunings, one coordinate at a time (topology lanes per cell 32/16; bin
+ * tunings, one coordinate at a time (concurrent chunks 1/2/4; topology
+ * lanes per cell 32/16; bin
  * load 1/2/4/8; topology warps per block 2/4/8; topology grid cap 8/16/32
  * blocks per SM; quadrature block 128/256/512; first-pass target
  * 16/24/32/48, the last compared on

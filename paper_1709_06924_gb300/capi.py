@@ -59,7 +59,8 @@ class scvt_eval_out(C.Structure):
 
 class scvt_tuning(C.Structure):
     _fields_ = [("bin_load", C.c_int), ("knn_target", C.c_int), ("topo_warps", C.c_int),
-                ("topo_blocks_per_sm", C.c_int), ("quad_block", C.c_int), ("topo_cell_lanes", C.c_int)]
+                ("topo_blocks_per_sm", C.c_int), ("quad_block", C.c_int), ("topo_cell_lanes", C.c_int),
+                ("chunks", C.c_int)]
 
 
 class scvt_server_config(C.Structure):

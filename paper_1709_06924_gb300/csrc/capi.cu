@@ -63,6 +63,7 @@ struct scvt_handle {
     int G = 1;
     int m = 0;
     Tune tune;
+    Pipes pipes;
     cudaStream_t stream = nullptr;
     Bufs b;
     DevStatus *st_host = nullptr;  // pinned
@@ -186,7 +187,7 @@ scvt_status evaluate_dev(scvt_handle *H, const double *zdev, double *grad, doubl
     cb.serK = B.serK;
     cell_passes(g, out, cb, B.list1, B.list2, B.st, H->cfg.precision == 1, H->tune, s,
                 H->profiling ? H->ev_cell0 : nullptr, H->profiling ? H->ev_cell1 : nullptr, L,
-                &H->stats.cell_launches);
+                &H->stats.cell_launches, &H->pipes);
     reduce_eval(n, fcell, grad, q, nrm, B.partials, B.st, s, L);
     if (H->profiling) cudaEventRecord(H->ev_e1, s);
     CK(cudaGetLastError(), "launch");
@@ -324,6 +325,7 @@ void scvt_destroy(scvt_handle *H) {
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (H->st_host) cudaFreeHost(H->st_host);
+    pipes_destroy(H->pipes);
     cudaEvent_t evs[] = {H->ev_cell0, H->ev_cell1, H->ev_e0, H->ev_e1, H->ev_l0, H->ev_l1};
     for (cudaEvent_t e : evs)
         if (e) cudaEventDestroy(e);
@@ -373,7 +375,7 @@ scvt_status scvt_create(const scvt_config *cfg, void *cuda_stream, scvt_handle *
     AL(b.partials, 4 * 1024); AL(b.scal, 128); AL(b.rho, kMaxM + 1); AL(b.gamma, 1);
     AL(b.hist, (size_t)(H->m + 1) * 2 * n3);
     AL(b.zs, n); AL(b.zf, n); AL(b.zl, n); AL(b.cvx, (size_t)n * kCellSlots); AL(b.cnb, (size_t)n * kCellSlots);
-    AL(b.cdeg, n); AL(b.eoff, n + 1); AL(b.ecell, 6 * (size_t)n); AL(b.escan, 2 * (n / 2048 + 64) + 64);
+    AL(b.cdeg, n); AL(b.eoff, n + 1); AL(b.ecell, 6 * (size_t)n); AL(b.escan, scan_tmp_ints(n));
     AL(b.eacc, 5 * 6 * (size_t)n);
     if (cfg->precision == 1) AL(b.vo, (size_t)n * kCellSlots);
     if (cfg->precision == 0) { AL(b.ser, (size_t)n * 21); AL(b.serK, n); }
@@ -383,6 +385,7 @@ scvt_status scvt_create(const scvt_config *cfg, void *cuda_stream, scvt_handle *
     AL(b.st, 1);
 #undef AL
     if (e == cudaSuccess) e = cudaMallocHost((void **)&H->st_host, sizeof(DevStatus));
+    if (e == cudaSuccess) e = pipes_create(H->pipes, kMaxChunks - 1);
     cudaEvent_t *evs[] = {&H->ev_cell0, &H->ev_cell1, &H->ev_e0, &H->ev_e1, &H->ev_l0, &H->ev_l1};
     for (cudaEvent_t *ev : evs)
         if (e == cudaSuccess) e = cudaEventCreate(ev);

@@ -97,6 +97,14 @@ __device__ __forceinline__ unsigned *flags_of(const Grid &g, DevStatus *st, int 
 }
 __device__ __forceinline__ bool inactive(const Grid &g, int b) { return g.active && !g.active[b]; }
 
+// One chunk of the cell pipeline: cells [p0, p1) in bin order, their edges
+// [*e0, *e0 + *etot) of the edge list (both known on the device only: a
+// chunk's edges follow the previous chunk's).
+struct Span {
+    int p0, p1;
+    const int *e0, *etot;
+};
+
 __device__ __forceinline__ int bin_index(double x, double y, double z, int G) {
     double ax = fabs(x), ay = fabs(y), az = fabs(z);
     int a;
@@ -961,7 +969,7 @@ __device__ __forceinline__ int gather(const Grid &g, int p, float4 hp, float4 lp
 template <int WPB, int L>
 __global__ void __launch_bounds__(WPB * 32, 24 / WPB) k_topo_warp(Grid g, CellOut out, CellBuf cb, int *__restrict__ next_list,
                                                         unsigned *__restrict__ next_count, DevStatus *st,
-                                                        float knn_target) {
+                                                        float knn_target, int pbeg, int pend) {
     constexpr int C = 2 * L;  // candidate slots per cell
     constexpr unsigned lfull = (L == 32) ? 0xffffffffu : ((1u << L) - 1u);
     __shared__ float s_d2[WPB * 32 / L][C];
@@ -974,7 +982,7 @@ __global__ void __launch_bounds__(WPB * 32, 24 / WPB) k_topo_warp(Grid g, CellOu
     const int gs = (blockIdx.x * blockDim.x + threadIdx.x) / L;
     const int ns = (gridDim.x * blockDim.x) / L;
     const float INF = __int_as_float(0x7f800000);
-    for (int p = gs; p < g.n; p += ns) {
+    for (int p = pbeg + gs; p < pend; p += ns) {
         const View v = view_of(g, p);
         if (inactive(g, v.b)) {
             if (sl == 0) cb.deg[p] = 0;
@@ -1312,25 +1320,27 @@ __global__ void __launch_bounds__(WPB * 32, 24 / WPB) k_topo_warp(Grid g, CellOu
 
 // FP64 corner of every edge: vertex k of a cell is the intersection of the
 // bisector lines of edges k-1 and k, solved in the gnomonic frame at z_i
-__global__ void __launch_bounds__(256) k_corners(Grid g, CellBuf cb) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= cb.eoff[g.n]) return;
-    const int p = cb.ecell[e];
-    const int k = e - cb.eoff[p];
-    const int deg = cb.deg[p];
-    const int *nb = cb.nb + (size_t)p * kCellSlots;
-    const V3 zi = ld(g.zs + p);
-    V3 e1, e2;
-    frame64(zi, e1, e2);
-    double a1, b1, c1, a2, b2, c2;
-    line_of(g, zi, e1, e2, nb[(k == 0) ? deg - 1 : k - 1], a1, b1, c1);
-    line_of(g, zi, e1, e2, nb[k], a2, b2, c2);
-    const double inv = 1.0 / (a1 * b2 - a2 * b1);
-    const double u = (c1 * b2 - c2 * b1) * inv;
-    const double w = (a1 * c2 - a2 * c1) * inv;
-    const V3 x = add(zi, add(scl(e1, u), scl(e2, w)));
-    const V3 v = scl(x, rsqrt(dot(x, x)));
-    cb.vx[(size_t)p * kCellSlots + k] = P4{v.x, v.y, v.z, 0.0};
+__global__ void __launch_bounds__(256) k_corners(Grid g, CellBuf cb, Span sp) {
+    const int ne = *sp.etot, eb = *sp.e0;
+    for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < ne; it += gridDim.x * blockDim.x) {
+        const int e = eb + it;
+        const int p = cb.ecell[e];
+        const int k = e - cb.eoff[p];
+        const int deg = cb.deg[p];
+        const int *nb = cb.nb + (size_t)p * kCellSlots;
+        const V3 zi = ld(g.zs + p);
+        V3 e1, e2;
+        frame64(zi, e1, e2);
+        double a1, b1, c1, a2, b2, c2;
+        line_of(g, zi, e1, e2, nb[(k == 0) ? deg - 1 : k - 1], a1, b1, c1);
+        line_of(g, zi, e1, e2, nb[k], a2, b2, c2);
+        const double inv = 1.0 / (a1 * b2 - a2 * b1);
+        const double u = (c1 * b2 - c2 * b1) * inv;
+        const double w = (a1 * c2 - a2 * c1) * inv;
+        const V3 x = add(zi, add(scl(e1, u), scl(e2, w)));
+        const V3 v = scl(x, rsqrt(dot(x, x)));
+        cb.vx[(size_t)p * kCellSlots + k] = P4{v.x, v.y, v.z, 0.0};
+    }
 }
 
 // -------------------------------------------- density series per cell
@@ -1363,10 +1373,10 @@ __device__ void series_of_cell(const Grid &g, const CellBuf &cb, int p, double *
                                int *__restrict__ serK, int &Kout);
 
 __global__ void __launch_bounds__(128) k_rho_series(Grid g, CellBuf cb, double *__restrict__ ser, int *__restrict__ serK,
-                                                    DevStatus *st) {
-    const int p0 = blockIdx.x * blockDim.x + threadIdx.x;
+                                                    DevStatus *st, Span sp) {
+    const int p0 = sp.p0 + blockIdx.x * blockDim.x + threadIdx.x;
     int K = 0;
-    if (p0 < g.n) series_of_cell(g, cb, p0, ser, serK, K);
+    if (p0 < sp.p1) series_of_cell(g, cb, p0, ser, serK, K);
     count_series(K, st);
 }
 
@@ -1481,46 +1491,78 @@ __device__ void series_of_cell(const Grid &g, const CellBuf &cb, int p, double *
 // -------------------------------------------------------------- quadrature
 // Edge list: cells' edges laid end to end in bin order (eoff = exclusive
 // scan of the degrees), ecell[e] = the cell of edge e.
-__global__ void k_edge_cells(int n, const int *__restrict__ deg, const int *__restrict__ eoff,
+__global__ void k_edge_cells(int p0, int p1, const int *__restrict__ deg, const int *__restrict__ eoff,
                              int *__restrict__ ecell) {
-    int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n) return;
+    int p = p0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= p1) return;
     int d = deg[p], o = eoff[p];
     for (int k = 0; k < d; ++k) ecell[o + k] = p;
+}
+
+// Chunk words (kChunkWords per chunk): retry counts of the three topology
+// passes, the chunk's edge count, the chunk's first edge.
+constexpr int kChunkWords = 8;
+enum { CW_R0 = 0, CW_R1 = 1, CW_R2 = 2, CW_ETOT = 3, CW_EBASE = 4 };
+
+// a chunk's exclusive scan of the degrees, moved to the chunk's first edge,
+// which follows the previous chunk's edges (prev: that chunk's words, null
+// for the first chunk); the last cell writes the chunk's edge count
+__global__ void k_rebase(int p0, int p1, const int *__restrict__ deg, int *__restrict__ eoff,
+                         const int *__restrict__ prev, int *__restrict__ mine) {
+    const int p = p0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= p1) return;
+    const int base = prev ? prev[CW_EBASE] + prev[CW_ETOT] : 0;
+    const int local = eoff[p];
+    eoff[p] = local + base;
+    if (p == p1 - 1) {
+        mine[CW_ETOT] = local + deg[p];
+        mine[CW_EBASE] = base;
+    }
+}
+
+// retry counts of all chunks into the evaluation's status block
+__global__ void k_sum_counts(const unsigned *__restrict__ counts, int nch, DevStatus *st) {
+    for (int k = 0; k < 3; ++k) {
+        unsigned t = 0;
+        for (int c = 0; c < nch; ++c) t += counts[kChunkWords * c + k];
+        st->retry_count[k] = t;
+    }
 }
 
 // One thread per Voronoi edge (two signed sub-triangles of Sec. 3.2.2, 14
 // rule points, summed in order).  The edge's five sums go to the edge list;
 // k_cell_sum adds a cell's edges in edge order, so a cell's result depends
 // on its own edges only (not on where they fall in the launch).
-__global__ void __launch_bounds__(512) k_quad(Grid g, CellBuf cb, int ecap) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= cb.eoff[g.n]) return;
-    const int p = cb.ecell[e];
-    const int k = e - cb.eoff[p];
-    const int deg = cb.deg[p];
-    const V3 zi = ld(g.zs + p);
-    const P4 *vx = cb.vx + (size_t)p * kCellSlots;
-    const V3 va = ld(vx + k);
-    const V3 vb = ld(vx + ((k + 1 == deg) ? 0 : k + 1));
-    const V3 mu = unit(add(zi, ld(g.zs + cb.nb[(size_t)p * kCellSlots + k])));
-    const Density rho = g.rho ? g.rho[view_of(g, p).b] : g.rho0;
-    const double inv_alpha = 1.0 / rho.alpha;
-    const int K = cb.serK ? cb.serK[p] : 0;
-    const double *ser = cb.ser + (size_t)p * kSerStride;
-    Acc acc = {0, 0, 0, 0, 0};
-    if (g.fan) {
-        tri(rho, inv_alpha, zi, va, vb, acc, ser, K);
-    } else {
-        tri(rho, inv_alpha, zi, va, mu, acc, ser, K);
-        tri(rho, inv_alpha, zi, mu, vb, acc, ser, K);
+__global__ void __launch_bounds__(512) k_quad(Grid g, CellBuf cb, int ecap, Span sp) {
+    const int ne = *sp.etot, eb = *sp.e0;
+    for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < ne; it += gridDim.x * blockDim.x) {
+        const int e = eb + it;
+        const int p = cb.ecell[e];
+        const int k = e - cb.eoff[p];
+        const int deg = cb.deg[p];
+        const V3 zi = ld(g.zs + p);
+        const P4 *vx = cb.vx + (size_t)p * kCellSlots;
+        const V3 va = ld(vx + k);
+        const V3 vb = ld(vx + ((k + 1 == deg) ? 0 : k + 1));
+        const V3 mu = unit(add(zi, ld(g.zs + cb.nb[(size_t)p * kCellSlots + k])));
+        const Density rho = g.rho ? g.rho[view_of(g, p).b] : g.rho0;
+        const double inv_alpha = 1.0 / rho.alpha;
+        const int K = cb.serK ? cb.serK[p] : 0;
+        const double *ser = cb.ser + (size_t)p * kSerStride;
+        Acc acc = {0, 0, 0, 0, 0};
+        if (g.fan) {
+            tri(rho, inv_alpha, zi, va, vb, acc, ser, K);
+        } else {
+            tri(rho, inv_alpha, zi, va, mu, acc, ser, K);
+            tri(rho, inv_alpha, zi, mu, vb, acc, ser, K);
+        }
+        double *ea = cb.eacc;
+        ea[e] = acc.m;
+        ea[(size_t)ecap + e] = acc.cx;
+        ea[2 * (size_t)ecap + e] = acc.cy;
+        ea[3 * (size_t)ecap + e] = acc.cz;
+        ea[4 * (size_t)ecap + e] = acc.e;
     }
-    double *ea = cb.eacc;
-    ea[e] = acc.m;
-    ea[(size_t)ecap + e] = acc.cx;
-    ea[2 * (size_t)ecap + e] = acc.cy;
-    ea[3 * (size_t)ecap + e] = acc.cz;
-    ea[4 * (size_t)ecap + e] = acc.e;
 }
 
 // ------------------------------------------------ mixed precision (FP32)
@@ -1565,36 +1607,38 @@ __device__ __forceinline__ float3 gnomonic_offset(float4 z, float3 e1, float3 e2
                        (u * e1.z + w * e2.z) * iq - z.z * t);
 }
 
-__global__ void __launch_bounds__(256) k_corners32(Grid g, CellBuf cb) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= cb.eoff[g.n]) return;
-    const int p = cb.ecell[e];
-    const int k = e - cb.eoff[p];
-    const int deg = cb.deg[p];
-    const int *nb = cb.nb + (size_t)p * kCellSlots;
-    const int gin = nb[(k == 0) ? deg - 1 : k - 1], gout = nb[k];
-    const float4 hp = g.zf[p], lp = g.zl[p];
-    float3 e1, e2;
-    frame32(hp, e1, e2);
-    float u, w;
-    float3 o;
-    if (!vertex32(g, p, hp, lp, e1, e2, gin, gout, u, w)) {
-        o = gnomonic_offset(hp, e1, e2, u, w);
-    } else {
-        // ill conditioned: the corner in FP64, then its offset
-        const V3 zi = ld(g.zs + p);
-        V3 f1, f2;
-        frame64(zi, f1, f2);
-        double a1, b1, c1, a2, b2, c2;
-        line_of(g, zi, f1, f2, gin, a1, b1, c1);
-        line_of(g, zi, f1, f2, gout, a2, b2, c2);
-        const double inv = 1.0 / (a1 * b2 - a2 * b1);
-        const double uu = (c1 * b2 - c2 * b1) * inv, ww = (a1 * c2 - a2 * c1) * inv;
-        const double r2 = uu * uu + ww * ww, q = sqrt(1.0 + r2), t = r2 / (q * (1.0 + q));
-        o = make_float3((float)((uu * f1.x + ww * f2.x) / q - zi.x * t), (float)((uu * f1.y + ww * f2.y) / q - zi.y * t),
-                        (float)((uu * f1.z + ww * f2.z) / q - zi.z * t));
+__global__ void __launch_bounds__(256) k_corners32(Grid g, CellBuf cb, Span sp) {
+    const int ne = *sp.etot, eb = *sp.e0;
+    for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < ne; it += gridDim.x * blockDim.x) {
+        const int e = eb + it;
+        const int p = cb.ecell[e];
+        const int k = e - cb.eoff[p];
+        const int deg = cb.deg[p];
+        const int *nb = cb.nb + (size_t)p * kCellSlots;
+        const int gin = nb[(k == 0) ? deg - 1 : k - 1], gout = nb[k];
+        const float4 hp = g.zf[p], lp = g.zl[p];
+        float3 e1, e2;
+        frame32(hp, e1, e2);
+        float u, w;
+        float3 o;
+        if (!vertex32(g, p, hp, lp, e1, e2, gin, gout, u, w)) {
+            o = gnomonic_offset(hp, e1, e2, u, w);
+        } else {
+            // ill conditioned: the corner in FP64, then its offset
+            const V3 zi = ld(g.zs + p);
+            V3 f1, f2;
+            frame64(zi, f1, f2);
+            double a1, b1, c1, a2, b2, c2;
+            line_of(g, zi, f1, f2, gin, a1, b1, c1);
+            line_of(g, zi, f1, f2, gout, a2, b2, c2);
+            const double inv = 1.0 / (a1 * b2 - a2 * b1);
+            const double uu = (c1 * b2 - c2 * b1) * inv, ww = (a1 * c2 - a2 * c1) * inv;
+            const double r2 = uu * uu + ww * ww, q = sqrt(1.0 + r2), t = r2 / (q * (1.0 + q));
+            o = make_float3((float)((uu * f1.x + ww * f2.x) / q - zi.x * t), (float)((uu * f1.y + ww * f2.y) / q - zi.y * t),
+                            (float)((uu * f1.z + ww * f2.z) / q - zi.z * t));
+        }
+        cb.vo[(size_t)p * kCellSlots + k] = make_float4(o.x, o.y, o.z, 0.0f);
     }
-    cb.vo[(size_t)p * kCellSlots + k] = make_float4(o.x, o.y, o.z, 0.0f);
 }
 
 struct AccF {
@@ -1662,42 +1706,44 @@ __device__ __forceinline__ void write_cell_offsets(const CellOut &out, int i, V3
 // one thread per edge; the 14 rule points of the edge's two sub-triangles
 // summed in FP32, the edge's five sums stored in FP32 (edges and cells are
 // summed in FP64 by k_cell_sum)
-__global__ void __launch_bounds__(512) k_quad32(Grid g, CellBuf cb, int ecap) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= cb.eoff[g.n]) return;
-    const int p = cb.ecell[e];
-    const int k = e - cb.eoff[p];
-    const int deg = cb.deg[p];
-    const float4 hp = g.zf[p], lp = g.zl[p];
-    const float4 va = cb.vo[(size_t)p * kCellSlots + k];
-    const float4 vb = cb.vo[(size_t)p * kCellSlots + ((k + 1 == deg) ? 0 : k + 1)];
-    // edge midpoint normalize(z_i + z_j) as an offset: d/s + z |d|^2 / (s (2 + s)), s = sqrt(4 - |d|^2)
-    const float3 d = dfdiff(g, cb.nb[(size_t)p * kCellSlots + k], hp, lp);
-    const float dd = fmaf(d.x, d.x, fmaf(d.y, d.y, d.z * d.z));
-    const float sq = sqrtf(4.0f - dd), is = 1.0f / sq, t = dd / (sq * (2.0f + sq));
-    const float3 om = make_float3(d.x * is + hp.x * t, d.y * is + hp.y * t, d.z * is + hp.z * t);
-    const DensityF rf = g.rhof ? g.rhof[view_of(g, p).b] : g.rho0f;
-    AccF a = {0, 0, 0, 0, 0};
-    if (g.fan) {
-        tri32(rf, hp, make_float3(va.x, va.y, va.z), make_float3(vb.x, vb.y, vb.z), a);
-    } else {
-        tri32(rf, hp, make_float3(va.x, va.y, va.z), om, a);
-        tri32(rf, hp, om, make_float3(vb.x, vb.y, vb.z), a);
+__global__ void __launch_bounds__(512) k_quad32(Grid g, CellBuf cb, int ecap, Span sp) {
+    const int ne = *sp.etot, eb = *sp.e0;
+    for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < ne; it += gridDim.x * blockDim.x) {
+        const int e = eb + it;
+        const int p = cb.ecell[e];
+        const int k = e - cb.eoff[p];
+        const int deg = cb.deg[p];
+        const float4 hp = g.zf[p], lp = g.zl[p];
+        const float4 va = cb.vo[(size_t)p * kCellSlots + k];
+        const float4 vb = cb.vo[(size_t)p * kCellSlots + ((k + 1 == deg) ? 0 : k + 1)];
+        // edge midpoint normalize(z_i + z_j) as an offset: d/s + z |d|^2 / (s (2 + s)), s = sqrt(4 - |d|^2)
+        const float3 d = dfdiff(g, cb.nb[(size_t)p * kCellSlots + k], hp, lp);
+        const float dd = fmaf(d.x, d.x, fmaf(d.y, d.y, d.z * d.z));
+        const float sq = sqrtf(4.0f - dd), is = 1.0f / sq, t = dd / (sq * (2.0f + sq));
+        const float3 om = make_float3(d.x * is + hp.x * t, d.y * is + hp.y * t, d.z * is + hp.z * t);
+        const DensityF rf = g.rhof ? g.rhof[view_of(g, p).b] : g.rho0f;
+        AccF a = {0, 0, 0, 0, 0};
+        if (g.fan) {
+            tri32(rf, hp, make_float3(va.x, va.y, va.z), make_float3(vb.x, vb.y, vb.z), a);
+        } else {
+            tri32(rf, hp, make_float3(va.x, va.y, va.z), om, a);
+            tri32(rf, hp, om, make_float3(vb.x, vb.y, vb.z), a);
+        }
+        float *ea = (float *)cb.eacc;
+        ea[e] = a.m;
+        ea[(size_t)ecap + e] = a.ox;
+        ea[2 * (size_t)ecap + e] = a.oy;
+        ea[3 * (size_t)ecap + e] = a.oz;
+        ea[4 * (size_t)ecap + e] = a.e;
     }
-    float *ea = (float *)cb.eacc;
-    ea[e] = a.m;
-    ea[(size_t)ecap + e] = a.ox;
-    ea[2 * (size_t)ecap + e] = a.oy;
-    ea[3 * (size_t)ecap + e] = a.oz;
-    ea[4 * (size_t)ecap + e] = a.e;
 }
 
 // thread per cell: the cell's edge sums added in edge order (FP64), then the
 // cell's outputs (g_i, h_i, m_i, c_i, F_i at the original index)
 template <bool MIXED>
-__global__ void __launch_bounds__(256) k_cell_sum(Grid g, CellOut out, CellBuf cb, int ecap, DevStatus *st) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= g.n) return;
+__global__ void __launch_bounds__(256) k_cell_sum(Grid g, CellOut out, CellBuf cb, int ecap, DevStatus *st, Span sp) {
+    const int p = sp.p0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= sp.p1) return;
     const int deg = cb.deg[p];
     if (deg == 0) return;  // integrated by the topology kernel, failed, or inactive
     const int e0 = cb.eoff[p];
@@ -1748,10 +1794,6 @@ void bin_points(const double *z, const Grid &g, int *bin_of, int *count, int *st
     (*launches) += 4;
 }
 
-__global__ void k_set_total_from(int *arr, int n, const int *last_in) {
-    // arr[n] = arr[n-1] + last_in[n-1]: total of an exclusive scan
-    arr[n] = arr[n - 1] + last_in[n - 1];
-}
 
 void exclusive_scan(const int *in, int *out, int len, int *tmp, cudaStream_t s, int64_t *launches) {
     scan_rec(in, out, len, tmp, s, launches);
@@ -1769,12 +1811,14 @@ scvt_status tune_from(const scvt_tuning &t, Tune *out) {
     if (t.topo_blocks_per_sm < 1 || t.topo_blocks_per_sm > 64) return SCVT_ERR_INVALID;
     if (t.quad_block != 128 && t.quad_block != 256 && t.quad_block != 512) return SCVT_ERR_INVALID;
     if (t.topo_cell_lanes != 16 && t.topo_cell_lanes != 32) return SCVT_ERR_INVALID;
+    if (t.chunks < 1 || t.chunks > kMaxChunks) return SCVT_ERR_INVALID;
     out->bin_load = t.bin_load;
     out->knn_target = t.knn_target;
     out->topo_warps = t.topo_warps;
     out->topo_bpsm = t.topo_blocks_per_sm;
     out->quad_block = t.quad_block;
     out->topo_lanes = t.topo_cell_lanes;
+    out->chunks = t.chunks;
     return SCVT_OK;
 }
 
@@ -1786,6 +1830,7 @@ scvt_tuning tuning_of(const Tune &u) {
     t.topo_blocks_per_sm = u.topo_bpsm;
     t.quad_block = u.quad_block;
     t.topo_cell_lanes = u.topo_lanes;
+    t.chunks = u.chunks;
     return t;
 }
 
@@ -1815,54 +1860,115 @@ DensityF to_density32(const Density &d) {
 
 void cell_passes(const Grid &g, const CellOut &out, const CellBuf &cb, int *list1, int *list2, DevStatus *st,
                  bool mixed, const Tune &t, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1, int64_t *launches,
-                 int64_t *cell_launches) {
-    // first pass: a warp per cell, grid capped at topo_bpsm blocks per SM (grid-stride over cells)
+                 int64_t *cell_launches, const Pipes *px) {
+    // the cells are cut into nch chunks of consecutive bin positions, each run
+    // through the whole pipeline on its own stream (the first on s); chunks
+    // share nothing but the read-only generators, so their kernels overlap
+    const int nch = std::max(1, std::min(t.chunks, px->n_aux + 1));
+    unsigned *counts = px->counts;
+    cudaMemsetAsync(counts, 0, sizeof(unsigned) * kChunkWords * kMaxChunks, s);
+    if (nch > 1) {
+        cudaEventRecord(px->fork, s);
+        for (int c = 1; c < nch; ++c) cudaStreamWaitEvent(px->aux[c - 1], px->fork, 0);
+    }
+    const int scan_len = 2 * (g.n / 2048 + 64) + 64;
     const int wpb = t.topo_warps;
     const int cpw = 32 / t.topo_lanes;  // cells per warp
-    const int wblocks = (int)std::min<long long>((g.n + wpb * cpw - 1) / (wpb * cpw), 152LL * t.topo_bpsm);
     const float kt = (float)t.knn_target;
-    unsigned *rc0 = &st->retry_count[0];
-    if (t.topo_lanes == 16) {
-        if (wpb == 2) k_topo_warp<2, 16><<<wblocks, 64, 0, s>>>(g, out, cb, list1, rc0, st, kt);
-        else if (wpb == 8) k_topo_warp<8, 16><<<wblocks, 256, 0, s>>>(g, out, cb, list1, rc0, st, kt);
-        else k_topo_warp<4, 16><<<wblocks, 128, 0, s>>>(g, out, cb, list1, rc0, st, kt);
-    } else {
-        if (wpb == 2) k_topo_warp<2, 32><<<wblocks, 64, 0, s>>>(g, out, cb, list1, rc0, st, kt);
-        else if (wpb == 8) k_topo_warp<8, 32><<<wblocks, 256, 0, s>>>(g, out, cb, list1, rc0, st, kt);
-        else k_topo_warp<4, 32><<<wblocks, 128, 0, s>>>(g, out, cb, list1, rc0, st, kt);
-    }
-    // retry passes (thread per cell): sized for the worst case, they read their work count on the device
-    const int rblocks = 2 * 152;
-    k_topo<64, 64, 0><<<rblocks, 64, 0, s>>>(g, out, cb, list1, &st->retry_count[0], list2, &st->retry_count[1], 0,
-                                             0, st);
-    // the last pass scans every generator of problems up to 20,000 generators
-    k_topo<128, 64, 64><<<rblocks, 64, 0, s>>>(g, out, cb, list2, &st->retry_count[1], nullptr,
-                                               &st->retry_count[2], 1, 20000, st);
-    // edge list, corners, quadrature per edge, sums per cell
-    exclusive_scan(cb.deg, cb.eoff, g.n, cb.scan_tmp, s, launches);
-    k_set_total_from<<<1, 1, 0, s>>>(cb.eoff, g.n, cb.deg);
-    k_edge_cells<<<(g.n + 255) / 256, 256, 0, s>>>(g.n, cb.deg, cb.eoff, cb.ecell);
-    // Euler: a full tessellation has 6N - 12 edge sides; failed cells only lower the count
-    const int ecap = 6 * g.n;
     const int qb = t.quad_block;
-    const unsigned eblocks = (unsigned)((ecap + qb - 1) / qb);
-    const unsigned cblocks = (unsigned)((g.n + 255) / 256);
-    if (mixed) {
-        k_corners32<<<(ecap + 255) / 256, 256, 0, s>>>(g, cb);
-        if (ev0) cudaEventRecord(ev0, s);
-        k_quad32<<<eblocks, qb, 0, s>>>(g, cb, ecap);
-        if (ev1) cudaEventRecord(ev1, s);
-        k_cell_sum<true><<<cblocks, 256, 0, s>>>(g, out, cb, ecap, st);
-    } else {
-        k_corners<<<(ecap + 255) / 256, 256, 0, s>>>(g, cb);
-        if (cb.serK) k_rho_series<<<(g.n + 127) / 128, 128, 0, s>>>(g, cb, cb.ser, cb.serK, st);
-        if (ev0) cudaEventRecord(ev0, s);
-        k_quad<<<eblocks, qb, 0, s>>>(g, cb, ecap);
-        if (ev1) cudaEventRecord(ev1, s);
-        k_cell_sum<false><<<cblocks, 256, 0, s>>>(g, out, cb, ecap, st);
+    for (int c = 0; c < nch; ++c) {
+        const cudaStream_t sc = (c == 0) ? s : px->aux[c - 1];
+        const int p0 = (int)((long long)g.n * c / nch), p1 = (int)((long long)g.n * (c + 1) / nch);
+        const int len = p1 - p0;
+        if (len <= 0) continue;
+        unsigned *rc = counts + kChunkWords * c;
+        int *cw = (int *)rc;  // this chunk's words
+        // first pass: a warp (or half warp) per cell, grid capped at topo_bpsm blocks per SM
+        const int wblocks =
+            (int)std::max<long long>(1, std::min<long long>((len + wpb * cpw - 1) / (wpb * cpw), 152LL * t.topo_bpsm / nch));
+        if (t.topo_lanes == 16) {
+            if (wpb == 2) k_topo_warp<2, 16><<<wblocks, 64, 0, sc>>>(g, out, cb, list1 + p0, rc, st, kt, p0, p1);
+            else if (wpb == 8) k_topo_warp<8, 16><<<wblocks, 256, 0, sc>>>(g, out, cb, list1 + p0, rc, st, kt, p0, p1);
+            else k_topo_warp<4, 16><<<wblocks, 128, 0, sc>>>(g, out, cb, list1 + p0, rc, st, kt, p0, p1);
+        } else {
+            if (wpb == 2) k_topo_warp<2, 32><<<wblocks, 64, 0, sc>>>(g, out, cb, list1 + p0, rc, st, kt, p0, p1);
+            else if (wpb == 8) k_topo_warp<8, 32><<<wblocks, 256, 0, sc>>>(g, out, cb, list1 + p0, rc, st, kt, p0, p1);
+            else k_topo_warp<4, 32><<<wblocks, 128, 0, sc>>>(g, out, cb, list1 + p0, rc, st, kt, p0, p1);
+        }
+        // retry passes (thread per cell): sized for the worst case, they read their work count on the device
+        const int rblocks = std::max(1, 2 * 152 / nch);
+        k_topo<64, 64, 0><<<rblocks, 64, 0, sc>>>(g, out, cb, list1 + p0, rc, list2 + p0, rc + 1, 0, 0, st);
+        // the last pass scans every generator of problems up to 20,000 generators
+        k_topo<128, 64, 64><<<rblocks, 64, 0, sc>>>(g, out, cb, list2 + p0, rc + 1, nullptr, rc + 2, 1, 20000, st);
+        // the chunk's edge list follows the previous chunk's: its first edge is
+        // known once that chunk's count is, so the rebase waits for it
+        exclusive_scan(cb.deg + p0, cb.eoff + p0, len, cb.scan_tmp + (size_t)c * scan_len, sc, launches);
+        if (c > 0) cudaStreamWaitEvent(sc, px->rebased[c - 1], 0);
+        k_rebase<<<(len + 255) / 256, 256, 0, sc>>>(p0, p1, cb.deg, cb.eoff,
+                                                     c > 0 ? (const int *)(counts + kChunkWords * (c - 1)) : nullptr, cw);
+        if (c + 1 < nch) cudaEventRecord(px->rebased[c], sc);
+        k_edge_cells<<<(len + 255) / 256, 256, 0, sc>>>(p0, p1, cb.deg, cb.eoff, cb.ecell);
+        // the edge kernels loop over the chunk's edges (grid sized for about 6 per
+        // cell; Euler: a full tessellation has 6N - 12 edge sides in all)
+        const Span sp{p0, p1, cw + CW_EBASE, cw + CW_ETOT};
+        const int ecap = 6 * g.n;
+        const unsigned eblocks = (unsigned)((6 * len + qb - 1) / qb);
+        const unsigned e256 = (unsigned)((6 * len + 255) / 256);
+        const unsigned cblocks = (unsigned)((len + 255) / 256);
+        const bool timed = (c == 0 && nch == 1);
+        if (mixed) {
+            k_corners32<<<e256, 256, 0, sc>>>(g, cb, sp);
+            if (timed && ev0) cudaEventRecord(ev0, sc);
+            k_quad32<<<eblocks, qb, 0, sc>>>(g, cb, ecap, sp);
+            if (timed && ev1) cudaEventRecord(ev1, sc);
+            k_cell_sum<true><<<cblocks, 256, 0, sc>>>(g, out, cb, ecap, st, sp);
+        } else {
+            k_corners<<<e256, 256, 0, sc>>>(g, cb, sp);
+            if (cb.serK) k_rho_series<<<(len + 127) / 128, 128, 0, sc>>>(g, cb, cb.ser, cb.serK, st, sp);
+            if (timed && ev0) cudaEventRecord(ev0, sc);
+            k_quad<<<eblocks, qb, 0, sc>>>(g, cb, ecap, sp);
+            if (timed && ev1) cudaEventRecord(ev1, sc);
+            k_cell_sum<false><<<cblocks, 256, 0, sc>>>(g, out, cb, ecap, st, sp);
+        }
+        (*launches) += 10;
+        (*cell_launches) += 5;
     }
-    (*launches) += 8;
-    (*cell_launches) += 5;
+    if (nch > 1) {
+        for (int c = 1; c < nch; ++c) {
+            cudaEventRecord(px->join[c - 1], px->aux[c - 1]);
+            cudaStreamWaitEvent(s, px->join[c - 1], 0);
+        }
+    }
+    k_sum_counts<<<1, 1, 0, s>>>(counts, nch, st);
+    (*launches)++;
+}
+
+}  // namespace scvt
+
+namespace scvt {
+
+cudaError_t pipes_create(Pipes &px, int n_aux) {
+    px = Pipes();
+    cudaError_t e = cudaMalloc((void **)&px.counts, sizeof(unsigned) * kChunkWords * kMaxChunks);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&px.fork, cudaEventDisableTiming);
+    for (int k = 0; k < n_aux && k < kMaxChunks - 1 && e == cudaSuccess; ++k) {
+        e = cudaStreamCreateWithFlags(&px.aux[k], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&px.join[k], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&px.rebased[k], cudaEventDisableTiming);
+        if (e == cudaSuccess) px.n_aux = k + 1;
+    }
+    return e;
+}
+
+void pipes_destroy(Pipes &px) {
+    for (int k = 0; k < px.n_aux; ++k) {
+        if (px.aux[k]) cudaStreamDestroy(px.aux[k]);
+        if (px.join[k]) cudaEventDestroy(px.join[k]);
+        if (px.rebased[k]) cudaEventDestroy(px.rebased[k]);
+    }
+    if (px.fork) cudaEventDestroy(px.fork);
+    if (px.counts) cudaFree(px.counts);
+    px = Pipes();
 }
 
 }  // namespace scvt

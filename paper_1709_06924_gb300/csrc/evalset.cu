@@ -86,7 +86,7 @@ void enqueue_eval(EvalSet &E, int64_t *launches, int64_t *cell_launches) {
     cb.ser = E.ser;
     cb.serK = E.serK;
     cell_passes(g, out, cb, E.list1, E.list2, E.d_st, E.precision == 1, E.tune, s, nullptr, nullptr, launches,
-                cell_launches);
+                cell_launches, &E.pipes);
     reduce_eval_batch(E.B, E.max_nb, E.d_inst, E.d_pbase, E.d_active, E.fc, E.gt, E.q, E.nrm, E.partials, E.d_ist, s,
                       launches);
     cudaMemcpyAsync(E.h_ist, E.d_ist, sizeof(DevStatus) * E.B, cudaMemcpyDeviceToHost, s);
@@ -171,13 +171,14 @@ cudaError_t evalset_alloc(EvalSet &E, int64_t cap_n, int cap_b, int precision, c
     AL(E.zt, n3); AL(E.gt, n3); AL(E.ht, N); AL(E.fc, N); AL(E.q, n3); AL(E.nrm, N); AL(E.radius, N);
     AL(E.partials, E.partials_len);
     AL(E.zs, N); AL(E.zf, N); AL(E.zl, N); AL(E.cvx, N * kCellSlots); AL(E.cnb, N * kCellSlots);
-    AL(E.cdeg, N); AL(E.eoff, N + 1); AL(E.ecell, 6 * N); AL(E.escan, 2 * (N / 2048 + 64) + 64);
+    AL(E.cdeg, N); AL(E.eoff, N + 1); AL(E.ecell, 6 * N); AL(E.escan, scan_tmp_ints(N));
     AL(E.eacc, 5 * 6 * N);
     if (precision == 1) AL(E.vo, N * kCellSlots);
     if (precision == 0) { AL(E.ser, N * 21); AL(E.serK, N); }
     AL(E.bin_of, N); AL(E.count, nb); AL(E.start, nb + 1); AL(E.cursor, nb); AL(E.scan_tmp, 2 * (nb / 2048 + 64) + 64);
     AL(E.sidx, N); AL(E.list1, N); AL(E.list2, N);
 #undef AL
+    if (e == cudaSuccess) e = pipes_create(E.pipes, kMaxChunks - 1);
     if (e == cudaSuccess) e = cudaMallocHost((void **)&E.h_ist, sizeof(DevStatus) * cap_b);
     if (e == cudaSuccess) e = cudaMallocHost((void **)&E.h_st, sizeof(DevStatus));
     if (e == cudaSuccess) e = cudaMallocHost((void **)&E.h_active, sizeof(int) * cap_b);
@@ -200,6 +201,7 @@ void evalset_free(EvalSet &E) {
     void *hp[] = {E.h_ist, E.h_st, E.h_active};
     for (void *p : hp)
         if (p) cudaFreeHost(p);
+    pipes_destroy(E.pipes);
     E = EvalSet();
 }
 

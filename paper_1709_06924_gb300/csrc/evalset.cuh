@@ -35,6 +35,7 @@ struct EvalSet {
     int max_nb = 1;
     int nbins = 0;
     Tune tune;
+    Pipes pipes;
     // device tables and their pinned mirrors
     InstGeom *d_inst = nullptr;
     int *d_pinst = nullptr, *d_pbase = nullptr, *d_active = nullptr;

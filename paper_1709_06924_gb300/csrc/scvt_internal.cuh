@@ -152,6 +152,7 @@ struct Tune {
     int topo_warps = 4;    // warps per block of the topology pass (2, 4, 8)
     int topo_bpsm = 16;    // grid cap of the topology pass, blocks per SM
     int topo_lanes = 32;   // lanes per cell in the topology pass (32, 16)
+    int chunks = 1;        // cell pipelines run concurrently on forked streams (1..kMaxChunks)
     int quad_block = 256;  // threads per block of the quadrature (128, 256, 512)
 };
 int bins_per_edge(int64_t n, int bin_load);
@@ -163,9 +164,27 @@ scvt_tuning tuning_of(const Tune &t);
 // topology pass 0 over all cells, passes 1..2 over the retry lists, then the
 // quadrature kernel over all cells (timed by ev0/ev1 when given).
 // mixed: corners and quadrature in FP32 local coordinates, FP64 accumulation
+// Concurrent cell pipelines: up to kMaxChunks chunks of cells, the first on
+// the caller's stream, the others on n_aux auxiliary streams forked from it
+// (fork / join events; rebased[c]: chunk c's first edge and edge count are
+// known, which chunk c + 1 waits for); counts: 8 * kMaxChunks device words
+// (per chunk: the retry counts of the three passes, the edge count, the
+// first edge), cleared by every evaluation.  cb.scan_tmp holds kMaxChunks
+// scan scratch areas.
+constexpr int kMaxChunks = 4;
+struct Pipes {
+    int n_aux = 0;
+    cudaStream_t aux[kMaxChunks - 1] = {};
+    cudaEvent_t fork = nullptr, join[kMaxChunks - 1] = {}, rebased[kMaxChunks - 1] = {};
+    unsigned *counts = nullptr;
+};
+cudaError_t pipes_create(Pipes &px, int n_aux);
+void pipes_destroy(Pipes &px);
+inline size_t scan_tmp_ints(int64_t n) { return (size_t)kMaxChunks * (2 * ((size_t)n / 2048 + 64) + 64); }
+
 void cell_passes(const Grid &g, const CellOut &out, const CellBuf &cb, int *list1, int *list2, DevStatus *st,
                  bool mixed, const Tune &t, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1, int64_t *launches,
-                 int64_t *cell_launches);
+                 int64_t *cell_launches, const Pipes *px);
 Density to_device_density(const scvt_density &r);
 // exclusive scan of len ints (tmp: 2 * (len / 2048 + 64) + 64 ints)
 void exclusive_scan(const int *in, int *out, int len, int *tmp, cudaStream_t s, int64_t *launches);

@@ -64,7 +64,8 @@ constexpr size_t oEscan = oEcell + up(sizeof(int) * 6 * kMaxN);
 constexpr size_t oEacc = oEscan + up(sizeof(int) * (2 * (kMaxN / 2048 + 64) + 64));
 constexpr size_t oSer = oEacc + up(sizeof(double) * 5 * 6 * kMaxN);
 constexpr size_t oSerK = oSer + up(sizeof(double) * 21 * kMaxN);
-constexpr size_t kBytes = oSerK + up(sizeof(int) * kMaxN);  // about 19.1 MB
+constexpr size_t oCounts = oSerK + up(sizeof(int) * kMaxN);
+constexpr size_t kBytes = oCounts + up(sizeof(unsigned) * 8 * kMaxChunks);  // about 19.1 MB
 
 __device__ __align__(256) unsigned char g_scratch[kBytes];
 
@@ -176,7 +177,9 @@ extern "C" scvt_status scvt_energy_grad_static(int64_t n, const scvt_density *rh
     cb.vo = nullptr;
     cb.ser = (double *)(base + oSer);
     cb.serK = (int *)(base + oSerK);
-    cell_passes(grid, out, cb, list1, list2, st, false, Tune(), s, nullptr, nullptr, &launches, &cell_launches);
+    Pipes px;  // one pipeline on the caller's stream, its counters in the scratch array
+    px.counts = (unsigned *)(base + oCounts);
+    cell_passes(grid, out, cb, list1, list2, st, false, Tune(), s, nullptr, nullptr, &launches, &cell_launches, &px);
     reduce_eval(N, fc, g, nullptr, nullptr, partials, st, s, &launches);
     DevStatus hs;
     cudaError_t e = cudaMemcpyAsync(&hs, st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s);

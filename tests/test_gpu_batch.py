@@ -136,7 +136,7 @@ TUNINGS = [
     dict(bin_load=1), dict(bin_load=4), dict(bin_load=8), dict(topo_warps=2), dict(topo_warps=8),
     dict(topo_blocks_per_sm=4), dict(quad_block=128), dict(quad_block=512), dict(knn_target=12),
     dict(knn_target=48), dict(topo_cell_lanes=16), dict(topo_cell_lanes=16, topo_warps=8, bin_load=1),
-    dict(topo_cell_lanes=16, knn_target=48),
+    dict(topo_cell_lanes=16, knn_target=48), dict(chunks=2), dict(chunks=4), dict(chunks=3, topo_cell_lanes=16),
 ]
 
 
@@ -150,6 +150,21 @@ def test_tuning_never_changes_a_result(precision):
         assert F == F0 and np.array_equal(g, g0), t
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batch_chunked_pipelines_keep_results(precision):
+    """Cells split into concurrent chunks (edge lists chained on the device)
+    give the batch's results bit for bit, graph replay included."""
+    zs = inputs(PROBLEMS, seed0=77)
+    with Batch([n for n, _ in PROBLEMS], [d for _, d in PROBLEMS], precision=precision) as bt:
+        zb = bt.concat([dev(z) for z in zs])
+        e0, g0 = bt.energy_grad(zb)
+        for c in (2, 3, 4):
+            bt.set_tuning(chunks=c)
+            for _ in range(2):
+                e1, g1 = bt.energy_grad(zb)
+                assert e1 == e0 and torch.equal(g1, g0), c
+
+
 def test_autotuner_picks_a_valid_tuning_and_keeps_results():
     zs = inputs(PROBLEMS, seed0=101)
     with Batch([n for n, _ in PROBLEMS], [d for _, d in PROBLEMS]) as bt:
@@ -159,7 +174,7 @@ def test_autotuner_picks_a_valid_tuning_and_keeps_results():
         assert t == bt.tuning()
         assert t["bin_load"] in (1, 2, 4, 8) and t["topo_warps"] in (2, 4, 8)
         assert t["quad_block"] in (128, 256, 512) and t["knn_target"] in (16, 24, 32, 48)
-        assert t["topo_cell_lanes"] in (16, 32)
+        assert t["topo_cell_lanes"] in (16, 32) and t["chunks"] in (1, 2, 4)
         e1, g1 = bt.energy_grad(zb)
         assert e1 == e0 and torch.equal(g1, g0)
         st = bt.stats()
