@@ -51,6 +51,8 @@ def parse():
     p.add_argument("--no-time-to-tol", action="store_true", help="skip the time-to-tolerance runs")
     p.add_argument("--no-batched", action="store_true", help="skip the 64-problem batch")
     p.add_argument("--no-tune", action="store_true", help="keep the default tuning (no autotuner run)")
+    p.add_argument("--tuning", default="",
+                   help="fixed tuning instead of the autotuner, e.g. chunks=4,bin_load=8 (other fields default)")
     p.add_argument("--no-serving", action="store_true", help="skip the request-stream measurement")
     p.add_argument("--no-table1", action="store_true", help="skip the 2,562-generator method comparison")
     p.add_argument("--no-chain", action="store_true", help="skip the 2,562 -> 655,362 bisection chain")
@@ -199,6 +201,25 @@ def timed_steps(eng, z, steps):
     ev1.record(eng.stream)
     torch.cuda.synchronize()
     return rep, ev0.elapsed_time(ev1) / 1e3
+
+
+def parse_tuning(text):
+    """'k=v,k=v' -> {k: int(v)} (empty text: {})."""
+    out = {}
+    for item in filter(None, (t.strip() for t in text.split(","))):
+        k, v = item.split("=")
+        out[k.strip()] = int(v)
+    return out
+
+
+def pick_tuning(args, eng, z):
+    """The autotuner's choice, the default tuning (--no-tune), or the fixed
+    fields of --tuning on top of the default."""
+    fixed = parse_tuning(args.tuning)
+    if fixed:
+        eng.set_tuning(**fixed)
+        return eng.tuning()
+    return eng.tune(z) if not args.no_tune else eng.tuning()
 
 
 def time_to_tolerance(w, z_host, local, prec, tuning, tol=1e-6, max_iter=50):
@@ -414,7 +435,7 @@ def run_ours(args, w):
             torch.distributed.barrier()
 
     # the library's autotuner picks launch shapes for this workload (results do not depend on them)
-    tuning = {prec: eng.tune(z)} if not args.no_tune else {prec: eng.tuning()}
+    tuning = {prec: pick_tuning(args, eng, z)}
 
     # warm-up: W LBFGS iterations from the seeded start (history is kept)
     eng.lbfgs_solve(z, max_iter=args.warmup, grad_tol=0.0)
@@ -513,7 +534,7 @@ def run_ours(args, w):
         oprec = 1 - prec
         eng3 = Engine(w.n, w.density, lbfgs_m=w.lbfgs_m, device=local, precision=oprec)
         z3 = torch.from_numpy(z_host).cuda(local)
-        tuning[oprec] = eng3.tune(z3) if not args.no_tune else eng3.tuning()
+        tuning[oprec] = pick_tuning(args, eng3, z3)
         eng3.lbfgs_solve(z3, max_iter=args.warmup, grad_tol=0.0)
         eng3.reset_stats()
         eng3.set_profiling(True)
@@ -562,7 +583,7 @@ def run_ours(args, w):
             if pr not in tuning:
                 with Engine(w.n, w.density, lbfgs_m=w.lbfgs_m, device=local, precision=pr) as et:
                     zt_ = torch.from_numpy(z_host).cuda(local)
-                    tuning[pr] = et.tune(zt_) if not args.no_tune else et.tuning()
+                    tuning[pr] = pick_tuning(args, et, zt_)
         ttt = {"fp64": time_to_tolerance(w, z_host, local, 0, tuning[0]),
                "mixed": time_to_tolerance(w, z_host, local, 1, tuning[1])}
 

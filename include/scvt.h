@@ -215,7 +215,7 @@ scvt_status scvt_energy_grad_static(int64_t n, const scvt_density *rho, const do
 /* Launch shape and search parameters of an evaluation (not in the paper:
  * GPU scheduling).  None of them changes a result -- a cell is unique, its
  * corners come from its neighbour triples and its sums are taken in its own
- * edge order -- only the time.  Defaults: 2, 24, 4, 16, 256, 32, 1. */
+ * edge order -- only the time.  Defaults: 2, 24, 4, 16, 256, 32, 3. */
 typedef struct {
     int bin_load;           /* target generators per cube-map bin, 1..16: G = ceil(sqrt(N / (6 bin_load)))
                                bins per face edge */
@@ -232,7 +232,7 @@ typedef struct {
 scvt_status scvt_set_tuning(scvt_handle *h, const scvt_tuning *t);
 scvt_status scvt_get_tuning(const scvt_handle *h, scvt_tuning *t);
 /* Autotuner: times evaluations at z (N x 3, device or host) over a grid of
- * tunings, one coordinate at a time (concurrent chunks 1/2/4; topology
+ * tunings, one coordinate at a time (concurrent chunks 1/2/3/4; topology
  * lanes per cell 32/16; bin
  * load 1/2/4/8; topology warps per block 2/4/8; topology grid cap 8/16/32
  * blocks per SM; quadrature block 128/256/512; first-pass target

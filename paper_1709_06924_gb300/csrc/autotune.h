@@ -22,7 +22,7 @@ scvt_status autotune(Tune cur, TimeFn &&time, Tune *out) {
     static const int qblk[] = {128, 256, 512};
     static const int targets[] = {16, 24, 32, 48};
     static const int lanes[] = {32, 16};
-    static const int chunks[] = {1, 2, 4};
+    static const int chunks[] = {1, 2, 3, 4};
     float cur_ms;
     scvt_status s = time(cur, false, &cur_ms);
     if (s) return s;
@@ -30,7 +30,7 @@ scvt_status autotune(Tune cur, TimeFn &&time, Tune *out) {
         const int *vals;
         int nv;
         switch (coord) {
-        case 0: vals = chunks; nv = 3; break;
+        case 0: vals = chunks; nv = 4; break;
         case 1: vals = lanes; nv = 2; break;
         case 2: vals = loads; nv = 4; break;
         case 3: vals = warps; nv = 3; break;

@@ -807,6 +807,8 @@ __global__ void __launch_bounds__(128) k_topo(Grid g, CellOut out, CellBuf cb,
             cb.deg[p] = 0;
             continue;
         }
+        // the next evaluation's first pass starts from this cell's own size
+        if (out.radius) out.radius[i] = fminf(2.2f * sqrtf(R2), 0.2829f);
 
         // ---- canonical edge order: start at the neighbour with the smallest key
         const int c = P.cur, nv = P.nv;
@@ -974,11 +976,13 @@ __global__ void __launch_bounds__(WPB * 32, 24 / WPB) k_topo_warp(Grid g, CellOu
     constexpr unsigned lfull = (L == 32) ? 0xffffffffu : ((1u << L) - 1u);
     __shared__ float s_d2[WPB * 32 / L][C];
     __shared__ int s_j[WPB * 32 / L][C];
+    __shared__ float4 s_ln[WPB * 32 / L][L];
     const int lane = threadIdx.x & 31;
     const int sl = lane & (L - 1), sbase = lane & ~(L - 1);
     const unsigned smask = lfull << sbase;
     float *cd = s_d2[threadIdx.x / L];
     int *cj = s_j[threadIdx.x / L];
+    float4 *ln = s_ln[threadIdx.x / L];
     const int gs = (blockIdx.x * blockDim.x + threadIdx.x) / L;
     const int ns = (gridDim.x * blockDim.x) / L;
     const float INF = __int_as_float(0x7f800000);
@@ -1076,6 +1080,111 @@ __global__ void __launch_bounds__(WPB * 32, 24 / WPB) k_topo_warp(Grid g, CellOu
                 r = fminf(r * 2.0f, rmax);
                 continue;
             }
+            bool early = false, fast = false;
+            if (cnt + 4 <= L) {
+                // ---- all lines at once: lane l holds line l (candidates, then the
+                // square) and proposes the piece of it inside every other line, the
+                // lines bounding that piece at its two ends being its polygon
+                // neighbours.  The proposal is then certified with the clipping
+                // test's own FP32 filter: every proposed vertex well conditioned and
+                // strictly inside every other line, the neighbour links one
+                // counter-clockwise cycle.  Then it is the exact cell; otherwise the
+                // cell is clipped one candidate at a time below.
+                const int nl = cnt + 4;
+                float fa = 0.0f, fb = 0.0f, fc = 0.0f;
+                int gen = 0;
+                if (sl < cnt) {
+                    gen = cj[sl];
+                    const float3 d = dfdiff(g, gen, hp, lp);
+                    fa = e1.x * d.x + e1.y * d.y + e1.z * d.z;
+                    fb = e2.x * d.x + e2.y * d.y + e2.z * d.z;
+                    fc = 0.5f * fmaf(d.x, d.x, fmaf(d.y, d.y, d.z * d.z));
+                } else if (sl < nl) {
+                    const int k = sl - cnt;  // right, top, left, bottom
+                    fa = (k == 0) ? 1.0f : ((k == 2) ? -1.0f : 0.0f);
+                    fb = (k == 1) ? 1.0f : ((k == 3) ? -1.0f : 0.0f);
+                    fc = (float)kBoxL;
+                    gen = -1 - k;
+                }
+                ln[sl] = make_float4(fa, fb, fc, 0.0f);
+                __syncwarp(smask);
+                // line l: the point pu, pw on it, direction (-fb, fa) (counter-clockwise
+                // along the boundary); line i bounds the parameter t by h / s
+                const float n2 = fa * fa + fb * fb;
+                const float pu = __fdividef(fc * fa, n2), pw = __fdividef(fc * fb, n2);
+                float tmax = INF, tmin = -INF;
+                int imax = -1, imin = -1;
+                bool infeasible = false;
+                for (int i = 0; i < nl; ++i) {
+                    const float4 li = ln[i];
+                    const float sv = li.y * fa - li.x * fb;
+                    const float h = li.z - fmaf(li.x, pu, li.y * pw);
+                    const float t = __fdividef(h, sv);
+                    if (i != sl) {
+                        if (sv > 0.0f) {
+                            if (t < tmax) { tmax = t; imax = i; }
+                        } else if (sv < 0.0f) {
+                            if (t > tmin) { tmin = t; imin = i; }
+                        } else if (h < 0.0f) {
+                            infeasible = true;
+                        }
+                    }
+                }
+                const bool present = sl < nl && !infeasible && imax >= 0 && imin >= 0 && tmin < tmax;
+                const unsigned pm = (__ballot_sync(smask, present) >> sbase) & lfull;
+                const int m = __popc(pm);
+                const int nx = present ? imax : sl;  // successor (counter-clockwise)
+                const int pv = __shfl_sync(smask, imin, sbase + (nx & (L - 1)));
+                bool good = !present || ((((pm >> nx) & 1u) != 0u) && pv == sl);
+                int pos = -1;
+                if (m >= 3) {
+                    const int start = __ffs(pm) - 1;
+                    int cur = start;
+                    if (sl == start) pos = 0;
+                    for (int k = 1; k < m; ++k) {
+                        cur = __shfl_sync(smask, nx, sbase + cur);
+                        if (sl == cur) pos = k;
+                    }
+                    cur = __shfl_sync(smask, nx, sbase + cur);
+                    good = good && cur == start && (!present || pos >= 0);
+                } else {
+                    good = false;
+                }
+                float r2v = 0.0f;
+                if (good && present) {
+                    const float4 ls = ln[nx];
+                    const float p1 = fa * ls.y, p2 = ls.x * fb, det = p1 - p2;
+                    if (!(det > 0.0f) || !(fabsf(det) * 30.0f >= fabsf(p1) + fabsf(p2))) {
+                        good = false;
+                    } else {
+                        const float inv = __fdividef(1.0f, det);
+                        const float xu = (fc * ls.y - ls.z * fb) * inv;
+                        const float xw = (fa * ls.z - ls.x * fc) * inv;
+                        const float su = fabsf(xu) + fabsf(xw);
+                        for (int i = 0; i < nl; ++i) {
+                            const float4 li = ln[i];
+                            const float sd = fmaf(li.x, xu, fmaf(li.y, xw, -li.z));
+                            const float mag = (fabsf(li.x) + fabsf(li.y)) * su + fabsf(li.z);
+                            if (i != sl && i != nx && !(sd < -2e-4f * mag)) good = false;
+                        }
+                        r2v = xu * xu + xw * xw;
+                    }
+                }
+                fast = ((__ballot_sync(smask, !good) >> sbase) & lfull) == 0u;
+                if (fast) {
+                    // lane k takes the edge at position k of the cycle
+                    if (present) cj[pos] = sl;
+                    __syncwarp(smask);
+                    const int from = (sl < m) ? cj[sl] : sl;
+                    g_o = __shfl_sync(smask, gen, sbase + (from & (L - 1)));
+                    nv = m;
+#pragma unroll
+                    for (int o = L / 2; o > 0; o >>= 1) r2v = fmaxf(r2v, __shfl_xor_sync(smask, r2v, o));
+                    R2 = r2v * (1.001f * (1.0f + 1e-5f));
+                }
+                __syncwarp(smask);
+            }
+            if (!fast) {
             // ---- sort the candidates once by (d2, index), a total order, so the
             // result does not depend on the network: up to L candidates one per
             // lane over the next power of two >= cnt; more, two per lane over 2L
@@ -1169,7 +1278,6 @@ __global__ void __launch_bounds__(WPB * 32, 24 / WPB) k_topo_warp(Grid g, CellOu
                 vill = 0;
             }
             R2 = chord2_up(2.0f * (float)kBoxL * (float)kBoxL);
-            bool early = false;
             const int ncand = min(cnt, C);
             for (int t = 0; t < ncand; ++t) {
                 // candidate t (nearest first)
@@ -1201,65 +1309,67 @@ __global__ void __launch_bounds__(WPB * 32, 24 / WPB) k_topo_warp(Grid g, CellOu
                 const unsigned rot = ((m << 1) | (m >> (nv - 1))) & full;  // bit k = bit k-1 of m
                 const unsigned starts = m & ~rot;
                 if (__popc(starts) > 1 && sl == 0) atomicOr(flags, FLAG_NONCONVEX);
+                // indices mod nv by one conditional subtraction (operands < 2 nv)
                 const int k0 = __ffs(starts) - 1;
                 const unsigned mr = (k0 == 0) ? m : (((m >> k0) | (m << (nv - k0))) & full);
                 const int runlen = __ffs(~mr) - 1;
-                const int k1 = (k0 + runlen - 1) % nv;
-                const int kin = (k0 + nv - 1) % nv;
+                const int k1r = k0 + runlen - 1;
+                const int k1 = (k1r >= nv) ? k1r - nv : k1r;
+                const int kin = (k0 == 0) ? nv - 1 : k0 - 1;
                 const int nnew = nv - runlen + 2;
                 if (nnew > L) { ok = false; break; }
                 const float ai = __shfl_sync(smask, la_o, sbase + kin), bi = __shfl_sync(smask, lb_o, sbase + kin),
                             ci = __shfl_sync(smask, lc_o, sbase + kin);
                 const int gkin = __shfl_sync(smask, g_o, sbase + kin);
                 // new vertices P = (edge kin) x (new line), Q = (new line) x (edge k1);
-                // lanes >= 2 take the surviving vertices k1+1 .. kin
-                const int src = sbase + ((sl >= 2) ? (k1 + sl - 1) % nv : k1);
+                // lanes 2 .. nnew-1 take the surviving vertices k1+1 .. kin (k1 + sl - 1
+                // < 2 nv there); the lanes above carry any lane's values, unused
+                const int sr = (sl >= 2) ? k1 + sl - 1 : k1;
+                const int src = sbase + (((sr >= nv) ? sr - nv : sr) & (L - 1));
                 const float su = __shfl_sync(smask, vu, src), sw = __shfl_sync(smask, vw, src);
                 const int sill = __shfl_sync(smask, vill, src), sg = __shfl_sync(smask, g_o, src);
                 const int sgi = __shfl_sync(smask, g_i, src);
                 const float sa = __shfl_sync(smask, la_o, src), sb = __shfl_sync(smask, lb_o, src),
                             sc = __shfl_sync(smask, lc_o, src);
-                if (sl == 0) {
-                    const float p1 = ai * lb, p2 = la * bi, det = p1 - p2, inv = __frcp_rn(det);
-                    vu = (ci * lb - lc * bi) * inv;
-                    vw = (ai * lc - la * ci) * inv;
+                if (sl < 2) {
+                    // lane 0: P meets lines (kin, new); lane 1: Q meets lines (new, k1's outgoing)
+                    const bool l0 = sl == 0;
+                    const float a1 = l0 ? ai : la, b1 = l0 ? bi : lb, c1 = l0 ? ci : lc;
+                    const float a2 = l0 ? la : sa, b2 = l0 ? lb : sb, c2 = l0 ? lc : sc;
+                    const int gA = l0 ? gkin : wj, gB = l0 ? wj : sg;
+                    const float p1 = a1 * b2, p2 = a2 * b1, det = p1 - p2, inv = __fdividef(1.0f, det);
+                    vu = (c1 * b2 - c2 * b1) * inv;
+                    vw = (a1 * c2 - a2 * c1) * inv;
                     vill = 0;
                     if (!(fabsf(det) * 30.0f >= fabsf(p1) + fabsf(p2))) {
                         // poorly conditioned in FP32: solve once in FP64, keep the rounded vertex
                         double u, w;
-                        vertex64(g, p, gkin, wj, u, w);
+                        vertex64(g, p, gA, gB, u, w);
                         vu = (float)u;
                         vw = (float)w;
                     }
-                    la_o = la; lb_o = lb; lc_o = lc; g_o = wj; g_i = gkin;
-                } else if (sl == 1) {
-                    const float p1 = la * sb, p2 = sa * lb, det = p1 - p2, inv = __frcp_rn(det);
-                    vu = (lc * sb - sc * lb) * inv;
-                    vw = (la * sc - sa * lc) * inv;
-                    vill = 0;
-                    if (!(fabsf(det) * 30.0f >= fabsf(p1) + fabsf(p2))) {
-                        double u, w;
-                        vertex64(g, p, wj, sg, u, w);
-                        vu = (float)u;
-                        vw = (float)w;
-                    }
-                    la_o = sa; lb_o = sb; lc_o = sc; g_o = sg; g_i = wj;
+                    la_o = l0 ? la : sa; lb_o = l0 ? lb : sb; lc_o = l0 ? lc : sc;
+                    g_o = gB; g_i = gA;
                 } else {
                     vu = su; vw = sw; vill = sill; la_o = sa; lb_o = sb; lc_o = sc; g_o = sg; g_i = sgi;
                 }
                 nv = nnew;
-                // R2: an upper bound of the largest squared vertex chord
+                // R2: an upper bound of the largest squared vertex chord; the
+                // squared gnomonic radius t^2 bounds the squared chord
+                // 2 - 2 / sqrt(1 + t^2) of its point from above
                 float r2v = (sl < nv) ? vu * vu + vw * vw : 0.0f;
 #pragma unroll
                 for (int o = L / 2; o > 0; o >>= 1) r2v = fmaxf(r2v, __shfl_xor_sync(smask, r2v, o));
-                R2 = chord2_up(r2v * 1.001f);
+                R2 = r2v * (1.001f * (1.0f + 1e-5f));
             }
             if (!ok) break;
+            }
             const bool boxed = ((__ballot_sync(smask, sl < nv && g_o < 0) >> sbase) & lfull) != 0u;
             certified = !boxed && (early || D2 > 4.0f * R2 * (1.0f + 1e-6f));
             if (!certified) {
                 if (all_mode || r >= rmax) break;
-                r = fminf(fmaxf(2.2f * sqrtf(R2), 1.5f * r), rmax);
+                // an open polygon says nothing of the cell's size: widen the cap
+                r = boxed ? fminf(2.0f * r, rmax) : fminf(fmaxf(2.2f * sqrtf(R2), 1.5f * r), rmax);
             }
         }
         if (!certified || nv > kCellSlots) {
@@ -1305,7 +1415,8 @@ __global__ void __launch_bounds__(WPB * 32, 24 / WPB) k_topo_warp(Grid g, CellOu
                 }
             }
         }
-        const int rg = __shfl_sync(smask, g_o, sbase + (best + sl) % nv);
+        const int rgs = best + sl;  // < 2 nv on the lanes that keep it
+        const int rg = __shfl_sync(smask, g_o, sbase + (((rgs >= nv) ? rgs - nv : rgs) & (L - 1)));
         if (sl < nv) {
             cb.nb[(size_t)p * kCellSlots + sl] = rg;
             if (out.deg && nv <= out.max_deg) out.nbr[(size_t)i * out.max_deg + sl] = g.sidx[rg];

@@ -152,7 +152,7 @@ struct Tune {
     int topo_warps = 4;    // warps per block of the topology pass (2, 4, 8)
     int topo_bpsm = 16;    // grid cap of the topology pass, blocks per SM
     int topo_lanes = 32;   // lanes per cell in the topology pass (32, 16)
-    int chunks = 1;        // cell pipelines run concurrently on forked streams (1..kMaxChunks)
+    int chunks = 3;        // cell pipelines run concurrently on forked streams (1..kMaxChunks)
     int quad_block = 256;  // threads per block of the quadrature (128, 256, 512)
 };
 int bins_per_edge(int64_t n, int bin_load);

@@ -53,3 +53,9 @@ def test_roofline_figures_are_defined_for_every_density():
     assert f[0] < f[1] < f[2]
     assert abs(bench.fp64_peak_tflops() - 1.25856) < 1e-9
     assert bench.quad_traffic_bytes(163842) > 0
+
+
+def test_parse_tuning():
+    import bench
+    assert bench.parse_tuning("") == {}
+    assert bench.parse_tuning("chunks=4, bin_load=8") == {"chunks": 4, "bin_load": 8}

@@ -136,7 +136,7 @@ TUNINGS = [
     dict(bin_load=1), dict(bin_load=4), dict(bin_load=8), dict(topo_warps=2), dict(topo_warps=8),
     dict(topo_blocks_per_sm=4), dict(quad_block=128), dict(quad_block=512), dict(knn_target=12),
     dict(knn_target=48), dict(topo_cell_lanes=16), dict(topo_cell_lanes=16, topo_warps=8, bin_load=1),
-    dict(topo_cell_lanes=16, knn_target=48), dict(chunks=2), dict(chunks=4), dict(chunks=3, topo_cell_lanes=16),
+    dict(topo_cell_lanes=16, knn_target=48), dict(chunks=1), dict(chunks=2), dict(chunks=4), dict(chunks=3, topo_cell_lanes=16),
 ]
 
 
@@ -174,7 +174,7 @@ def test_autotuner_picks_a_valid_tuning_and_keeps_results():
         assert t == bt.tuning()
         assert t["bin_load"] in (1, 2, 4, 8) and t["topo_warps"] in (2, 4, 8)
         assert t["quad_block"] in (128, 256, 512) and t["knn_target"] in (16, 24, 32, 48)
-        assert t["topo_cell_lanes"] in (16, 32) and t["chunks"] in (1, 2, 4)
+        assert t["topo_cell_lanes"] in (16, 32) and t["chunks"] in (1, 2, 3, 4)
         e1, g1 = bt.energy_grad(zb)
         assert e1 == e0 and torch.equal(g1, g0)
         st = bt.stats()
