@@ -305,6 +305,9 @@ __device__ void cap_query(const Grid &g, const View &v, V3 q, float4 qf, int sel
         const float qa = qv[a];
         const float A = qa * qa - S2;
         if (A <= 0.0f) continue;  // the cap cannot reach face a (|x_a| >= 1/sqrt3 there)
+        // nor when |x_a| <= |q_a| + S stays below 1/sqrt3 on the whole cap; this
+        // also keeps A away from 0, where the roots below lose their accuracy
+        if (fabsf(qa) + S + 1e-6f < 0.5773f) continue;
         const float sg = qa > 0.0f ? 1.0f : -1.0f;
         const int face = 2 * a + (qa < 0.0f ? 1 : 0);
         const float invA = 1.0f / A;
@@ -1045,7 +1048,7 @@ __global__ void __launch_bounds__(WPB * 32, 24 / WPB) k_topo_warp(Grid g, CellOu
                 for (int a = 0; a < 3; ++a) {
                     const float qa = qv[a];
                     const float A = qa * qa - S2;
-                    if (A <= 0.0f) continue;
+                    if (A <= 0.0f || fabsf(qa) + S + 1e-6f < 0.5773f) continue;  // cap off face a
                     const float sg = qa > 0.0f ? 1.0f : -1.0f;
                     const int face = 2 * a + (qa < 0.0f ? 1 : 0);
                     const float invA = 1.0f / A;
