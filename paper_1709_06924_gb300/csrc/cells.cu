@@ -779,9 +779,21 @@ __global__ void __launch_bounds__(128) k_topo(Grid g, CellOut out, CellBuf cb,
                 if (dot(d, d) > 4.0 * (double)R2 * (1.0 + 1e-6)) continue;
                 // every listed neighbour has been clipped by already: its bisector
                 // may be an edge now, and clipping by a line of the polygon again
-                // would solve two identical lines for a corner
+                // would solve two identical lines for a corner.  The list is sorted
+                // by (FP32 d2, index) with d2 computed as here: binary search
                 bool listed = false;
-                for (int t = 0; t < L.cnt && !listed; ++t) listed = L.j[t] == q;
+                if (L.cnt > 0) {
+                    const float4 c = ldf(g.zf + q);
+                    const float dx = c.x - zif.x, dy = c.y - zif.y, dz = c.z - zif.z;
+                    const float d2f = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    int lo = 0, hi = L.cnt;
+                    while (lo < hi) {
+                        const int mid = (lo + hi) >> 1;
+                        if (L.d[mid] < d2f || (L.d[mid] == d2f && L.j[mid] < q)) lo = mid + 1;
+                        else hi = mid;
+                    }
+                    listed = lo < L.cnt && L.d[lo] == d2f && L.j[lo] == q;
+                }
                 if (listed) continue;
                 unsigned long long used = 0ull;
                 for (int v = 0; v < P.nv; ++v)
@@ -811,7 +823,7 @@ __global__ void __launch_bounds__(128) k_topo(Grid g, CellOut out, CellBuf cb,
             continue;
         }
         // the next evaluation's first pass starts from this cell's own size
-        if (out.radius) out.radius[i] = fminf(2.2f * sqrtf(R2), 0.2829f);
+        if (out.radius) out.radius[i] = fminf(2.2f * sqrtf(R2), 2.0f);
 
         // ---- canonical edge order: start at the neighbour with the smallest key
         const int c = P.cur, nv = P.nv;
@@ -1010,7 +1022,10 @@ __global__ void __launch_bounds__(WPB * 32, 24 / WPB) k_topo_warp(Grid g, CellOu
             e2 = make_float3(hp.y * e1.z - hp.z * e1.y, hp.z * e1.x - hp.x * e1.z, hp.x * e1.y - hp.y * e1.x);
         }
         const bool all_mode = v.n - 1 <= C;
-        const float rmax = 0.2829f;  // sin(theta) <= 0.28 keeps caps off the far faces
+        // caps up to chord rmax are cube-map queries (sin(theta) <= 0.28 keeps
+        // them off the far faces); wider ones, for cells that large, scan every
+        // generator of the problem; chord 2 takes them all
+        const float rmax = 0.2829f, rwide = 2.0f;
         float r;
         {
             const float hint = hp.w;  // the radius hint travels with the coordinates
@@ -1025,7 +1040,7 @@ __global__ void __launch_bounds__(WPB * 32, 24 / WPB) k_topo_warp(Grid g, CellOu
                 const float omega = (4.0f / ((float)v.G * v.G)) / (s2 * sqrtf(s2));
                 r = sqrtf(knn_target * omega / (3.14159265f * fmaxf((float)cbn, 1.0f)));
             }
-            r = fminf(r, rmax);
+            r = fminf(r, rwide);
         }
         bool certified = false, ok = true;
         int nv = 0;
@@ -1033,14 +1048,14 @@ __global__ void __launch_bounds__(WPB * 32, 24 / WPB) k_topo_warp(Grid g, CellOu
         // polygon: sub-warp lane k < nv holds vertex k and its outgoing edge's line
         float vu = 0.0f, vw = 0.0f, la_o = 0.0f, lb_o = 0.0f, lc_o = 0.0f;
         int vill = 0, g_o = 0, g_i = 0;
-        for (int attempt = 0; attempt < 4 && ok && !certified; ++attempt) {
+        for (int attempt = 0; attempt < 6 && ok && !certified; ++attempt) {
             // ---- candidates within chord r (every one of them; the rest are farther than r)
             const float rs = r * (1.0f + 1e-5f) + 1e-7f;  // covers the FP32 centre
-            const float S = rs * sqrtf(1.0f - 0.25f * rs * rs) * (1.0f + 1e-5f);
+            const float S = rs * sqrtf(fmaxf(1.0f - 0.25f * rs * rs, 0.0f)) * (1.0f + 1e-5f);
             const float r2acc = all_mode ? INF : r * r * 1.001f;
-            const float D2 = all_mode ? INF : r * r * (1.0f - 1e-6f);
+            const float D2 = (all_mode || r >= rwide) ? INF : r * r * (1.0f - 1e-6f);
             int cnt = 0;
-            if (all_mode) {
+            if (all_mode || r > rmax) {
                 cnt = gather<L>(g, p, hp, lp, v.p0, v.p0 + v.n, r2acc, cnt, cd, cj, sl, sbase, smask, flags);
             } else {
                 const float S2 = S * S;
@@ -1079,8 +1094,8 @@ __global__ void __launch_bounds__(WPB * 32, 24 / WPB) k_topo_warp(Grid g, CellOu
                 r *= 0.7f;
                 continue;
             }
-            if (cnt < 3 && !all_mode && r < rmax) {
-                r = fminf(r * 2.0f, rmax);
+            if (cnt < 3 && !all_mode && r < rwide) {
+                r = fminf(r * 2.0f, rwide);
                 continue;
             }
             bool early = false, fast = false;
@@ -1370,9 +1385,9 @@ __global__ void __launch_bounds__(WPB * 32, 24 / WPB) k_topo_warp(Grid g, CellOu
             const bool boxed = ((__ballot_sync(smask, sl < nv && g_o < 0) >> sbase) & lfull) != 0u;
             certified = !boxed && (early || D2 > 4.0f * R2 * (1.0f + 1e-6f));
             if (!certified) {
-                if (all_mode || r >= rmax) break;
+                if (all_mode || r >= rwide) break;
                 // an open polygon says nothing of the cell's size: widen the cap
-                r = boxed ? fminf(2.0f * r, rmax) : fminf(fmaxf(2.2f * sqrtf(R2), 1.5f * r), rmax);
+                r = boxed ? fminf(2.0f * r, rwide) : fminf(fmaxf(2.2f * sqrtf(R2), 1.5f * r), rwide);
             }
         }
         if (!certified || nv > kCellSlots) {
@@ -1427,7 +1442,7 @@ __global__ void __launch_bounds__(WPB * 32, 24 / WPB) k_topo_warp(Grid g, CellOu
         if (sl == 0) {
             cb.deg[p] = nv;
             if (out.deg) out.deg[i] = nv;
-            if (out.radius) out.radius[i] = fminf(2.2f * sqrtf(R2), rmax);
+            if (out.radius) out.radius[i] = fminf(2.2f * sqrtf(R2), rwide);
         }
     }
 }
