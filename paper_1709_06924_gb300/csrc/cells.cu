@@ -1024,8 +1024,10 @@ __global__ void __launch_bounds__(WPB * 32, 24 / WPB) k_topo_warp(Grid g, CellOu
         const bool all_mode = v.n - 1 <= C;
         // caps up to chord rmax are cube-map queries (sin(theta) <= 0.28 keeps
         // them off the far faces); wider ones, for cells that large, scan every
-        // generator of the problem; chord 2 takes them all
-        const float rmax = 0.2829f, rwide = 2.0f;
+        // generator of the problem (chord 2 takes them all) in problems of up to
+        // 131,072 generators, where such cells occur; in larger problems the
+        // thread passes take a cell that needs more than rmax
+        const float rmax = 0.2829f, rwide = (v.n <= (1 << 17)) ? 2.0f : rmax;
         float r;
         {
             const float hint = hp.w;  // the radius hint travels with the coordinates
@@ -1053,7 +1055,7 @@ __global__ void __launch_bounds__(WPB * 32, 24 / WPB) k_topo_warp(Grid g, CellOu
             const float rs = r * (1.0f + 1e-5f) + 1e-7f;  // covers the FP32 centre
             const float S = rs * sqrtf(fmaxf(1.0f - 0.25f * rs * rs, 0.0f)) * (1.0f + 1e-5f);
             const float r2acc = all_mode ? INF : r * r * 1.001f;
-            const float D2 = (all_mode || r >= rwide) ? INF : r * r * (1.0f - 1e-6f);
+            const float D2 = (all_mode || r >= 2.0f) ? INF : r * r * (1.0f - 1e-6f);  // chord 2: every generator
             int cnt = 0;
             if (all_mode || r > rmax) {
                 cnt = gather<L>(g, p, hp, lp, v.p0, v.p0 + v.n, r2acc, cnt, cd, cj, sl, sbase, smask, flags);
@@ -1386,8 +1388,11 @@ __global__ void __launch_bounds__(WPB * 32, 24 / WPB) k_topo_warp(Grid g, CellOu
             certified = !boxed && (early || D2 > 4.0f * R2 * (1.0f + 1e-6f));
             if (!certified) {
                 if (all_mode || r >= rwide) break;
-                // an open polygon says nothing of the cell's size: widen the cap
-                r = boxed ? fminf(2.0f * r, rwide) : fminf(fmaxf(2.2f * sqrtf(R2), 1.5f * r), rwide);
+                // an open polygon says nothing of the cell's size: widen the cap; a
+                // closed one needs chord 2 sqrt(R2), but R2 of a polygon clipped by
+                // too few candidates overstates the cell, so grow at most twofold
+                r = boxed ? fminf(2.0f * r, rwide)
+                          : fminf(fmaxf(fminf(2.2f * sqrtf(R2), 2.0f * r), 1.25f * r), rwide);
             }
         }
         if (!certified || nv > kCellSlots) {
