@@ -663,9 +663,10 @@ def fp64_peak_tflops() -> float:
 
 
 def quad_traffic_bytes(n: int):
-    """DRAM bytes of one k_quad launch: ncu at N = 163,842 (66.84 MB read +
-    2.34 MB written, tanh cap), scaled by the number of generators."""
-    return (66.841856e6 + 2.33728e6) * n / 163842
+    """DRAM bytes of one k_quad launch: ncu at N = 163,842 (90.95 MB read +
+    14.42 MB written, tanh cap, density series on), scaled by the number of
+    generators."""
+    return (90.947328e6 + 14.423552e6) * n / 163842
 
 
 def main():
