@@ -590,26 +590,33 @@ __device__ __forceinline__ void tri(const Density &r, double inv_alpha, V3 A, V3
     const V3 xc = mk(r.xc0, r.xc1, r.xc2);
 #pragma unroll 1
     for (int k = 0; k < 7; ++k) {
-        V3 x = add(add(scl(A, kQb[k][0]), scl(B, kQb[k][1])), scl(C, kQb[k][2]));
-        V3 p = scl(x, rsqrt(dot(x, x)));
+        // rule point x in the flat triangle, projected to p = x / |x|.  A small
+        // triangle's points lie within delta = 1 - |x|^2 < 1e-4 of the sphere,
+        // where (1 - delta)^(-1/2) to the delta^3 term (binomial series 1, 1/2,
+        // 3/8, 5/16) is exact to 3e-17; larger triangles take rsqrt
+        const V3 x = add(add(scl(A, kQb[k][0]), scl(B, kQb[k][1])), scl(C, kQb[k][2]));
+        const double x2 = dot(x, x);
+        const double dl = 1.0 - x2;
+        const double inv = (fabs(dl) < 1e-4) ? 1.0 + dl * (0.5 + dl * (0.375 + dl * 0.3125)) : rsqrt(x2);
         double rv;
         if (r.kind == 0) {
             rv = 1.0;
         } else if (r.kind == 1) {
-            double z2 = p.z * p.z;
+            const double pz = x.z * inv, z2 = pz * pz;
             rv = (1.0 - r.gamma) * z2 * z2 + r.gamma;
         } else if (K > 0) {
-            rv = horner(ser, K, dot(p, xc) - ser[kSerMax]);
+            rv = horner(ser, K, inv * dot(x, xc) - ser[kSerMax]);
         } else {
-            rv = rho_direct(r, inv_alpha, p);
+            rv = rho_direct(r, inv_alpha, scl(x, inv));
         }
-        double wr = kQw[k] * area * rv;
-        V3 dp = sub(p, A);
+        const double wr = kQw[k] * area * rv;
+        const double wi = wr * inv;  // wr p = wi x
+        const V3 dp = mk(fma(x.x, inv, -A.x), fma(x.y, inv, -A.y), fma(x.z, inv, -A.z));
         acc.m += wr;
-        acc.cx += wr * p.x;
-        acc.cy += wr * p.y;
-        acc.cz += wr * p.z;
-        acc.e += wr * dot(dp, dp);
+        acc.cx = fma(wi, x.x, acc.cx);
+        acc.cy = fma(wi, x.y, acc.cy);
+        acc.cz = fma(wi, x.z, acc.cz);
+        acc.e = fma(wr, dot(dp, dp), acc.e);
     }
 }
 
@@ -1680,8 +1687,8 @@ __global__ void __launch_bounds__(512) k_quad(Grid g, CellBuf cb, int ecap, Span
         const V3 vb = ld(vx + ((k + 1 == deg) ? 0 : k + 1));
         const V3 mu = unit(add(zi, ld(g.zs + cb.nb[(size_t)p * kCellSlots + k])));
         const Density rho = g.rho ? g.rho[view_of(g, p).b] : g.rho0;
-        const double inv_alpha = 1.0 / rho.alpha;
         const int K = cb.serK ? cb.serK[p] : 0;
+        const double inv_alpha = (K > 0 || rho.kind < 2) ? 0.0 : 1.0 / rho.alpha;  // direct tanh cap only
         const double *ser = cb.ser + (size_t)p * kSerStride;
         Acc acc = {0, 0, 0, 0, 0};
         if (g.fan) {
