@@ -378,7 +378,7 @@ scvt_status scvt_create(const scvt_config *cfg, void *cuda_stream, scvt_handle *
     AL(b.cdeg, n); AL(b.eoff, n + 1); AL(b.ecell, 6 * (size_t)n); AL(b.escan, scan_tmp_ints(n));
     AL(b.eacc, 5 * 6 * (size_t)n);
     if (cfg->precision == 1) AL(b.vo, (size_t)n * kCellSlots);
-    if (cfg->precision == 0) { AL(b.ser, (size_t)n * 21); AL(b.serK, n); }
+    if (cfg->precision == 0) { AL(b.ser, (size_t)n * kSerWords); AL(b.serK, n); }
     AL(b.bin_of, n); AL(b.count, nbins); AL(b.start, nbins + 1); AL(b.cursor, nbins);
     AL(b.scan_tmp, 2 * (nbins / 2048 + 64) + 64);
     AL(b.sidx, n); AL(b.list1, n); AL(b.list2, n); AL(b.deg, n); AL(b.radius, n);

@@ -26,6 +26,7 @@
 
 #include <algorithm>
 
+#include "df.cuh"
 #include "scvt_internal.cuh"
 
 namespace scvt {
@@ -48,6 +49,19 @@ __constant__ double kQb[7][3] = {
 __constant__ double kQw[7] = {0.225,
                               0.1259391805448271526, 0.1259391805448271526, 0.1259391805448271526,
                               0.13239415278850618074, 0.13239415278850618074, 0.13239415278850618074};
+
+// the same rule as double-float pairs (weights of the 2nd and 3rd vertex, point weight)
+#define SCVT_DF(x) {(float)(x), (float)((x) - (double)(float)(x))}
+__constant__ float kQdf[7][3][2] = {
+    {SCVT_DF(1.0 / 3.0), SCVT_DF(1.0 / 3.0), SCVT_DF(0.225)},
+    {SCVT_DF(0.1012865073234563388), SCVT_DF(0.1012865073234563388), SCVT_DF(0.1259391805448271526)},
+    {SCVT_DF(0.7974269853530873224), SCVT_DF(0.1012865073234563388), SCVT_DF(0.1259391805448271526)},
+    {SCVT_DF(0.1012865073234563388), SCVT_DF(0.7974269853530873224), SCVT_DF(0.1259391805448271526)},
+    {SCVT_DF(0.47014206410511508977), SCVT_DF(0.47014206410511508977), SCVT_DF(0.13239415278850618074)},
+    {SCVT_DF(0.059715871789769820459), SCVT_DF(0.47014206410511508977), SCVT_DF(0.13239415278850618074)},
+    {SCVT_DF(0.47014206410511508977), SCVT_DF(0.059715871789769820459), SCVT_DF(0.13239415278850618074)},
+};
+#undef SCVT_DF
 
 // the same rule in FP32 for the mixed-precision quadrature
 __constant__ float kQbf[7][2] = {
@@ -557,7 +571,8 @@ __device__ __forceinline__ double rho_direct(const Density &r, double inv_alpha,
 // Per-cell Taylor series of the tanh-cap density in u = x_c.p - x_c.z_i
 // (k_rho_series): up to kSerMax coefficients, then the expansion point x_c.z_i.
 constexpr int kSerMax = 20;
-constexpr int kSerStride = kSerMax + 1;
+constexpr int kSerStride = kSerWords;  // coefficients, expansion point, double-float pairs
+static_assert(kSerWords >= 2 * kSerMax + 2, "series buffer too short");
 __constant__ double kInv[kSerMax + 1] = {0.0,        1.0,        1.0 / 2,  1.0 / 3,  1.0 / 4,  1.0 / 5,  1.0 / 6,
                                          1.0 / 7,    1.0 / 8,    1.0 / 9,  1.0 / 10, 1.0 / 11, 1.0 / 12, 1.0 / 13,
                                          1.0 / 14,   1.0 / 15,   1.0 / 16, 1.0 / 17, 1.0 / 18, 1.0 / 19, 1.0 / 20};
@@ -1624,8 +1639,18 @@ __device__ void series_of_cell(const Grid &g, const CellBuf &cb, int p, double *
     Kout = K;
     if (K > 0) {
         double *o = ser + (size_t)p * kSerStride;
-        for (int k = 0; k < K; ++k) o[k] = cf[k];
+        // double-float copy in v = u / 2^e with 2^e >= U (exact scaling), so
+        // that the coefficients stay in FP32 range where 1 - c_i is small
+        int ex = 0;
+        if (U > 0.0) frexp(U, &ex);
+        float2 *od = reinterpret_cast<float2 *>(o + kSerMax + 1);
+        for (int k = 0; k < K; ++k) {
+            o[k] = cf[k];
+            const df c = df_from(ldexp(cf[k], ex * k));
+            od[k] = make_float2(c.hi, c.lo);
+        }
         o[kSerMax] = ci;
+        o[2 * kSerMax + 1] = ldexp(1.0, -ex);
     }
 }
 
@@ -1670,6 +1695,68 @@ __global__ void k_sum_counts(const unsigned *__restrict__ counts, int nch, DevSt
     }
 }
 
+// ------------------------------------------- quadrature in double-float
+// The FP64 form's rule points in double-float arithmetic (df.cuh): FP32
+// pairs carrying ~48 bits, several times cheaper here than FP64.  Everything
+// is taken relative to z_i: a sub-triangle (A, A + b, A + c) has FP64
+// offsets b, c (rounded to pairs: 3.6e-15 of their size), and rule point k
+// is x = A + w, w = b1 b + b2 c, projected to p = x / |x| = A + q with
+//   delta = 1 - |x|^2 = -(|A|^2 - 1) - 2 A.w - |w|^2      (|A|^2 - 1 from FP64)
+//   m     = 1/|x| - 1 = delta/2 + 3 delta^2/8 + 5 delta^3/16 + 35 delta^4/128
+//           + 63 delta^5/256, exact to 3e-19 for delta <= 1e-3
+//   q     = w + m (A + w)
+// so the density's argument x_c.p - x_c.z_i = (x_c.z_i - c_i) + x_c.q, the
+// energy |p - z_i|^2 = |q|^2 and the moment sum wr p = z_i sum wr + sum wr q
+// use offsets only, and no difference of nearby values is formed.  The
+// signed area is 2 atan(t), t = A.(b x c) / (4 + 3 (|A|^2 - 1) + 2 A.(b + c)
+// + b.c) (Van Oosterom-Strackee with B = A + b, C = A + c), atan(t) = t - t^3/3
+// to 1e-18 for the t <= 3e-4 of such triangles.  The result (per-edge
+// mass, moment, energy) matches the FP64 evaluation to ~1e-14 relative.
+struct AccDF {
+    df m, qx, qy, qz, e;
+};
+
+__device__ __forceinline__ void tri_df(int kind, df g1, df gam, df3 A, df aA1, df3 b, df3 c, df3 xc, df u0,
+                                       const float2 *__restrict__ sdf, float vs, int K, AccDF &acc) {
+    const df Ab = df3_dot(A, b), Ac = df3_dot(A, c);
+    const df det = df3_dot(A, df3_cross(b, c));
+    const df den = df_add(df_add_f(df_mul_f(aA1, 3.0f), 4.0f), df_add(df_mul_f(df_add(Ab, Ac), 2.0f), df3_dot(b, c)));
+    const df t = df_div(det, den);
+    const df area = df_mul_f(df_add_f(t, -t.hi * t.hi * t.hi * (1.0f / 3.0f)), 2.0f);
+#pragma unroll 1
+    for (int k = 0; k < 7; ++k) {
+        const df b1{kQdf[k][0][0], kQdf[k][0][1]}, b2{kQdf[k][1][0], kQdf[k][1][1]}, W{kQdf[k][2][0], kQdf[k][2][1]};
+        const df3 w{df_add(df_mul(b1, b.x), df_mul(b2, c.x)), df_add(df_mul(b1, b.y), df_mul(b2, c.y)),
+                    df_add(df_mul(b1, b.z), df_mul(b2, c.z))};
+        const df Aw = df_add(df_mul(b1, Ab), df_mul(b2, Ac));
+        const df dl = df_neg(df_add(df_add(aA1, df_mul_f(Aw, 2.0f)), df3_dot(w, w)));
+        const df d2 = df_mul(dl, dl);
+        const float tail = d2.hi * dl.hi * (0.3125f + dl.hi * (0.2734375f + dl.hi * 0.24609375f));
+        const df m = df_add_f(df_add(df_mul_f(dl, 0.5f), df_mul_f(d2, 0.375f)), tail);
+        const df3 q{df_add(w.x, df_mul(m, df_add(A.x, w.x))), df_add(w.y, df_mul(m, df_add(A.y, w.y))),
+                    df_add(w.z, df_mul(m, df_add(A.z, w.z)))};
+        df rv;
+        if (kind == 0) {
+            rv = df{1.0f, 0.0f};
+        } else if (kind == 1) {
+            const df pz = df_add(A.z, q.z), z2 = df_mul(pz, pz);
+            rv = df_add(df_mul(g1, df_mul(z2, z2)), gam);
+        } else {
+            // the argument of the cell's series, scaled by its power of two
+            const df u = df_add(u0, df3_dot(xc, q));
+            const df v{u.hi * vs, u.lo * vs};
+            rv = df{sdf[K - 1].x, sdf[K - 1].y};
+            for (int j = K - 2; j >= 0; --j) rv = df_fma(rv, v, df{sdf[j].x, sdf[j].y});
+        }
+        const df wr = df_mul(df_mul(W, area), rv);
+        acc.m = df_add(acc.m, wr);
+        acc.qx = df_add(acc.qx, df_mul(wr, q.x));
+        acc.qy = df_add(acc.qy, df_mul(wr, q.y));
+        acc.qz = df_add(acc.qz, df_mul(wr, q.z));
+        acc.e = df_add(acc.e, df_mul(wr, df3_dot(q, q)));
+    }
+}
+
 // One thread per Voronoi edge (two signed sub-triangles of Sec. 3.2.2, 14
 // rule points, summed in order).  The edge's five sums go to the edge list;
 // k_cell_sum adds a cell's edges in edge order, so a cell's result depends
@@ -1688,8 +1775,38 @@ __global__ void __launch_bounds__(512) k_quad(Grid g, CellBuf cb, int ecap, Span
         const V3 mu = unit(add(zi, ld(g.zs + cb.nb[(size_t)p * kCellSlots + k])));
         const Density rho = g.rho ? g.rho[view_of(g, p).b] : g.rho0;
         const int K = cb.serK ? cb.serK[p] : 0;
-        const double inv_alpha = (K > 0 || rho.kind < 2) ? 0.0 : 1.0 / rho.alpha;  // direct tanh cap only
         const double *ser = cb.ser + (size_t)p * kSerStride;
+        double *ea = cb.eacc;
+        // double-float path: offsets of the edge's points from z_i below chord
+        // 0.03 (then delta <= 1e-3 at every rule point) and a density without
+        // direct evaluation; otherwise FP64
+        const V3 ba = sub(va, zi), bm = sub(mu, zi), bb = sub(vb, zi);
+        const float r2 = fmaxf(fmaxf((float)dot(ba, ba), (float)dot(bb, bb)), (float)dot(bm, bm));
+        if (r2 <= 1e-3f && (rho.kind < 2 || K > 0)) {
+            const df3 A{df{g.zf[p].x, g.zl[p].x}, df{g.zf[p].y, g.zl[p].y}, df{g.zf[p].z, g.zl[p].z}};
+            const df aA1 = df_from(dot(zi, zi) - 1.0);
+            const df3 xc = df3_from(rho.xc0, rho.xc1, rho.xc2);
+            const df u0 = (K > 0) ? df_from(dot(mk(rho.xc0, rho.xc1, rho.xc2), zi) - ser[kSerMax]) : df{0.0f, 0.0f};
+            const df g1 = df_from(1.0 - rho.gamma), gam = df_from(rho.gamma);
+            const float2 *sdf = reinterpret_cast<const float2 *>(ser + kSerMax + 1);
+            const float vs = (K > 0) ? (float)ser[2 * kSerMax + 1] : 1.0f;
+            const df3 da = df3_from(ba.x, ba.y, ba.z), dm = df3_from(bm.x, bm.y, bm.z), db = df3_from(bb.x, bb.y, bb.z);
+            AccDF ad{};
+            if (g.fan) {
+                tri_df(rho.kind, g1, gam, A, aA1, da, db, xc, u0, sdf, vs, K, ad);
+            } else {
+                tri_df(rho.kind, g1, gam, A, aA1, da, dm, xc, u0, sdf, vs, K, ad);
+                tri_df(rho.kind, g1, gam, A, aA1, dm, db, xc, u0, sdf, vs, K, ad);
+            }
+            const double m = df_to(ad.m);
+            ea[e] = m;
+            ea[(size_t)ecap + e] = fma(zi.x, m, df_to(ad.qx));
+            ea[2 * (size_t)ecap + e] = fma(zi.y, m, df_to(ad.qy));
+            ea[3 * (size_t)ecap + e] = fma(zi.z, m, df_to(ad.qz));
+            ea[4 * (size_t)ecap + e] = df_to(ad.e);
+            continue;
+        }
+        const double inv_alpha = (K > 0 || rho.kind < 2) ? 0.0 : 1.0 / rho.alpha;  // direct tanh cap only
         Acc acc = {0, 0, 0, 0, 0};
         if (g.fan) {
             tri(rho, inv_alpha, zi, va, vb, acc, ser, K);
@@ -1697,7 +1814,6 @@ __global__ void __launch_bounds__(512) k_quad(Grid g, CellBuf cb, int ecap, Span
             tri(rho, inv_alpha, zi, va, mu, acc, ser, K);
             tri(rho, inv_alpha, zi, mu, vb, acc, ser, K);
         }
-        double *ea = cb.eacc;
         ea[e] = acc.m;
         ea[(size_t)ecap + e] = acc.cx;
         ea[2 * (size_t)ecap + e] = acc.cy;

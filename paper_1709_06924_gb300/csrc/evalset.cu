@@ -152,7 +152,7 @@ int64_t evalset_bytes(int64_t cap_n, int cap_b, int precision) {
                       + 32 + 32 + 16 * 32 + 16 * 4 + 4 + 4 + 24 + 240  // zs, zf+zl, cvx, cnb, cdeg, eoff, ecell, eacc
                       + 4 * 4;                // bin_of, sidx, list1, list2
     if (precision == 1) per_row += 16 * 16;   // vo
-    else per_row += 21 * 8 + 4;              // density series
+    else per_row += kSerWords * 8 + 4;       // density series
     return N * per_row + nb * 12 + (int64_t)max_partials(cap_n, cap_b) * 8 + (int64_t)cap_b * 512 + (1 << 20);
 }
 
@@ -174,7 +174,7 @@ cudaError_t evalset_alloc(EvalSet &E, int64_t cap_n, int cap_b, int precision, c
     AL(E.cdeg, N); AL(E.eoff, N + 1); AL(E.ecell, 6 * N); AL(E.escan, scan_tmp_ints(N));
     AL(E.eacc, 5 * 6 * N);
     if (precision == 1) AL(E.vo, N * kCellSlots);
-    if (precision == 0) { AL(E.ser, N * 21); AL(E.serK, N); }
+    if (precision == 0) { AL(E.ser, N * kSerWords); AL(E.serK, N); }
     AL(E.bin_of, N); AL(E.count, nb); AL(E.start, nb + 1); AL(E.cursor, nb); AL(E.scan_tmp, 2 * (nb / 2048 + 64) + 64);
     AL(E.sidx, N); AL(E.list1, N); AL(E.list2, N);
 #undef AL

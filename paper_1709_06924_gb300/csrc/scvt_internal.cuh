@@ -122,6 +122,9 @@ struct CellOut {
 // order: deg (0 = integrated elsewhere or failed), corners (unit vectors)
 // and the bin-order index of the neighbour across edge k (corner k -> k+1).
 constexpr int kCellSlots = 16;
+// doubles per cell of the density-series buffer
+constexpr int kSerWords = 42;
+
 struct CellBuf {
     int *deg;          // n
     P4 *vx;            // n * kCellSlots
@@ -131,7 +134,9 @@ struct CellBuf {
     int *scan_tmp;     // scratch of the scan over n (2 * (n / 2048 + 64) + 64 ints)
     double *eacc;      // 5 * 6n: per-edge sums (m, c or o, F), component-major; FP32 in the mixed form
     float4 *vo;        // n * kCellSlots corner offsets v - z_i in FP32 (mixed precision only)
-    double *ser;       // n * 21: per-cell density series (20 coefficients, expansion point); FP64 form
+    double *ser;       // n * kSerWords: per-cell density series (FP64 form): 20 coefficients, the
+                       // expansion point, the coefficients of the series in u / 2^e as
+                       // double-float pairs, 2^-e
     int *serK;         // n: terms of the cell's series, 0 = evaluate directly; null = no series
 };
 

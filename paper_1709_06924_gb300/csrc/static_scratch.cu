@@ -63,7 +63,7 @@ constexpr size_t oEcell = oEoff + up(sizeof(int) * (kMaxN + 1));
 constexpr size_t oEscan = oEcell + up(sizeof(int) * 6 * kMaxN);
 constexpr size_t oEacc = oEscan + up(sizeof(int) * (2 * (kMaxN / 2048 + 64) + 64));
 constexpr size_t oSer = oEacc + up(sizeof(double) * 5 * 6 * kMaxN);
-constexpr size_t oSerK = oSer + up(sizeof(double) * 21 * kMaxN);
+constexpr size_t oSerK = oSer + up(sizeof(double) * kSerWords * kMaxN);
 constexpr size_t oCounts = oSerK + up(sizeof(int) * kMaxN);
 constexpr size_t kBytes = oCounts + up(sizeof(unsigned) * 8 * kMaxChunks);  // about 19.1 MB
 
