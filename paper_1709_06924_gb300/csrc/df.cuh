@@ -54,13 +54,13 @@ SCVT_HD double df_to(df x) { return (double)x.hi + (double)x.lo; }
 
 SCVT_HD df df_neg(df x) { return df{-x.hi, -x.lo}; }
 
-// x + y, relative error <= ~2^-47 also under cancellation
+// x + y with error <= ~2^-47 (|x| + |y|): exact sum of the high parts, the
+// low parts added in FP32.  Its error is relative to the operands, not to the
+// result, which is what every sum here needs (no result is a small difference
+// of large double-float operands whose relative accuracy matters)
 SCVT_HD df df_add(df x, df y) {
     df s = two_sum(x.hi, y.hi);
-    const df t = two_sum(x.lo, y.lo);
-    s.lo += t.hi;
-    s = fast_two_sum(s.hi, s.lo);
-    s.lo += t.lo;
+    s.lo += x.lo + y.lo;
     return fast_two_sum(s.hi, s.lo);
 }
 
