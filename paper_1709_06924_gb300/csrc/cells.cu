@@ -50,17 +50,21 @@ __constant__ double kQw[7] = {0.225,
                               0.1259391805448271526, 0.1259391805448271526, 0.1259391805448271526,
                               0.13239415278850618074, 0.13239415278850618074, 0.13239415278850618074};
 
-// the same rule as double-float pairs (weights of the 2nd and 3rd vertex, point weight)
+// the same rule as double-float pairs: weights b1, b2 of the 2nd and 3rd
+// vertex, point weight W, and b1^2, 2 b1 b2, b2^2
 #define SCVT_DF(x) {(float)(x), (float)((x) - (double)(float)(x))}
-__constant__ float kQdf[7][3][2] = {
-    {SCVT_DF(1.0 / 3.0), SCVT_DF(1.0 / 3.0), SCVT_DF(0.225)},
-    {SCVT_DF(0.1012865073234563388), SCVT_DF(0.1012865073234563388), SCVT_DF(0.1259391805448271526)},
-    {SCVT_DF(0.7974269853530873224), SCVT_DF(0.1012865073234563388), SCVT_DF(0.1259391805448271526)},
-    {SCVT_DF(0.1012865073234563388), SCVT_DF(0.7974269853530873224), SCVT_DF(0.1259391805448271526)},
-    {SCVT_DF(0.47014206410511508977), SCVT_DF(0.47014206410511508977), SCVT_DF(0.13239415278850618074)},
-    {SCVT_DF(0.059715871789769820459), SCVT_DF(0.47014206410511508977), SCVT_DF(0.13239415278850618074)},
-    {SCVT_DF(0.47014206410511508977), SCVT_DF(0.059715871789769820459), SCVT_DF(0.13239415278850618074)},
+#define SCVT_QP(b1, b2, w) {SCVT_DF(b1), SCVT_DF(b2), SCVT_DF(w), SCVT_DF((b1) * (b1)), SCVT_DF(2.0 * (b1) * (b2)), \
+                            SCVT_DF((b2) * (b2))}
+__constant__ float kQdf[7][6][2] = {
+    SCVT_QP(1.0 / 3.0, 1.0 / 3.0, 0.225),
+    SCVT_QP(0.1012865073234563388, 0.1012865073234563388, 0.1259391805448271526),
+    SCVT_QP(0.7974269853530873224, 0.1012865073234563388, 0.1259391805448271526),
+    SCVT_QP(0.1012865073234563388, 0.7974269853530873224, 0.1259391805448271526),
+    SCVT_QP(0.47014206410511508977, 0.47014206410511508977, 0.13239415278850618074),
+    SCVT_QP(0.059715871789769820459, 0.47014206410511508977, 0.13239415278850618074),
+    SCVT_QP(0.47014206410511508977, 0.059715871789769820459, 0.13239415278850618074),
 };
+#undef SCVT_QP
 #undef SCVT_DF
 
 // the same rule in FP32 for the mixed-precision quadrature
@@ -1700,61 +1704,82 @@ __global__ void k_sum_counts(const unsigned *__restrict__ counts, int nch, DevSt
 // pairs carrying ~48 bits, several times cheaper here than FP64.  Everything
 // is taken relative to z_i: a sub-triangle (A, A + b, A + c) has FP64
 // offsets b, c (rounded to pairs: 3.6e-15 of their size), and rule point k
-// is x = A + w, w = b1 b + b2 c, projected to p = x / |x| = A + q with
-//   delta = 1 - |x|^2 = -(|A|^2 - 1) - 2 A.w - |w|^2      (|A|^2 - 1 from FP64)
-//   m     = 1/|x| - 1 = delta/2 + 3 delta^2/8 + 5 delta^3/16 + 35 delta^4/128
-//           + 63 delta^5/256, exact to 3e-19 for delta <= 1e-3
-//   q     = w + m (A + w)
-// so the density's argument x_c.p - x_c.z_i = (x_c.z_i - c_i) + x_c.q, the
-// energy |p - z_i|^2 = |q|^2 and the moment sum wr p = z_i sum wr + sum wr q
-// use offsets only, and no difference of nearby values is formed.  The
-// signed area is 2 atan(t), t = A.(b x c) / (4 + 3 (|A|^2 - 1) + 2 A.(b + c)
-// + b.c) (Van Oosterom-Strackee with B = A + b, C = A + c), atan(t) = t - t^3/3
-// to 1e-18 for the t <= 3e-4 of such triangles.  The result (per-edge
-// mass, moment, energy) matches the FP64 evaluation to ~1e-14 relative.
+// is x = A + w, w = b1 b + b2 c, projected to p = x / |x| = A + q,
+// q = (1 + m) w + m A, m = 1/|x| - 1.  Every per-point quantity is a
+// combination of per-triangle scalars (A.b, A.c, b.b, b.c, c.c, e.b, e.c,
+// e.A for the density's direction e) with the rule's constants:
+//   A.w   = b1 A.b + b2 A.c,   |w|^2 = b1^2 b.b + 2 b1 b2 b.c + b2^2 c.c
+//   delta = 1 - |x|^2 = -(|A|^2 - 1) - 2 A.w - |w|^2   (|A|^2 - 1 from FP64)
+//   m     = delta/2 + 3 delta^2/8 + 5 delta^3/16 + 35 delta^4/128 + 63 delta^5/256,
+//           exact to 3e-19 for delta <= 1e-3
+//   e.q   = e.w + m (e.A + e.w)  (the density's argument: x_c.p - c_i = (x_c.z_i - c_i)
+//           + x_c.q for the tanh cap, p_z = A_z + e_z.q for X3)
+//   |q|^2 = |w|^2 + 2 m (|w|^2 + A.w) + m^2 |x|^2 = |p - z_i|^2
+// and sum wr q = b (S1 + T1) + c (S2 + T2) + A T0 with S = sums of wr (b1, b2),
+// T = sums of wr m (1, b1, b2), so wr p sums to z_i sum wr + sum wr q.  No
+// difference of nearby values is formed.  The signed area is 2 atan(t),
+// t = A.(b x c) / (4 + 3 (|A|^2 - 1) + 2 A.(b + c) + b.c) (Van Oosterom-Strackee
+// with B = A + b, C = A + c), atan(t) = t - t^3/3 to 1e-18 for the t <= 3e-4
+// of such triangles.  Per-edge mass, moment and energy match the FP64
+// evaluation to ~1e-14 relative.
 struct AccDF {
     df m, qx, qy, qz, e;
 };
 
-__device__ __forceinline__ void tri_df(int kind, df g1, df gam, df3 A, df aA1, df3 b, df3 c, df3 xc, df u0,
+__device__ __forceinline__ void tri_df(int kind, df g1, df gam, df3 A, df aA1, df3 b, df3 c, df3 ev, df eA, df u0,
                                        const float2 *__restrict__ sdf, float vs, int K, AccDF &acc) {
     const df Ab = df3_dot(A, b), Ac = df3_dot(A, c);
+    const df bb = df3_dot(b, b), cc = df3_dot(c, c), bc = df3_dot(b, c);
+    const df eb = df3_dot(ev, b), ec = df3_dot(ev, c);
     const df det = df3_dot(A, df3_cross(b, c));
-    const df den = df_add(df_add_f(df_mul_f(aA1, 3.0f), 4.0f), df_add(df_mul_f(df_add(Ab, Ac), 2.0f), df3_dot(b, c)));
+    const df den = df_add(df_add_f(df_mul_f(aA1, 3.0f), 4.0f), df_add(df_mul_f(df_add(Ab, Ac), 2.0f), bc));
     const df t = df_div(det, den);
     const df area = df_mul_f(df_add_f(t, -t.hi * t.hi * t.hi * (1.0f / 3.0f)), 2.0f);
+    df S0{0.0f, 0.0f}, S1{0.0f, 0.0f}, S2{0.0f, 0.0f}, T0{0.0f, 0.0f}, T1{0.0f, 0.0f}, T2{0.0f, 0.0f}, E{0.0f, 0.0f};
 #pragma unroll 1
     for (int k = 0; k < 7; ++k) {
         const df b1{kQdf[k][0][0], kQdf[k][0][1]}, b2{kQdf[k][1][0], kQdf[k][1][1]}, W{kQdf[k][2][0], kQdf[k][2][1]};
-        const df3 w{df_add(df_mul(b1, b.x), df_mul(b2, c.x)), df_add(df_mul(b1, b.y), df_mul(b2, c.y)),
-                    df_add(df_mul(b1, b.z), df_mul(b2, c.z))};
+        const df B11{kQdf[k][3][0], kQdf[k][3][1]}, B12{kQdf[k][4][0], kQdf[k][4][1]}, B22{kQdf[k][5][0], kQdf[k][5][1]};
         const df Aw = df_add(df_mul(b1, Ab), df_mul(b2, Ac));
-        const df dl = df_neg(df_add(df_add(aA1, df_mul_f(Aw, 2.0f)), df3_dot(w, w)));
+        const df ww = df_add(df_add(df_mul(B11, bb), df_mul(B12, bc)), df_mul(B22, cc));
+        const df dl = df_neg(df_add(df_add(aA1, df{2.0f * Aw.hi, 2.0f * Aw.lo}), ww));
         const df d2 = df_mul(dl, dl);
         const float tail = d2.hi * dl.hi * (0.3125f + dl.hi * (0.2734375f + dl.hi * 0.24609375f));
-        const df m = df_add_f(df_add(df_mul_f(dl, 0.5f), df_mul_f(d2, 0.375f)), tail);
-        const df3 q{df_add(w.x, df_mul(m, df_add(A.x, w.x))), df_add(w.y, df_mul(m, df_add(A.y, w.y))),
-                    df_add(w.z, df_mul(m, df_add(A.z, w.z)))};
+        const df m = df_add_f(df_add(df{0.5f * dl.hi, 0.5f * dl.lo}, df_mul_f(d2, 0.375f)), tail);
+        const df xw = df_add(df_mul(b1, eb), df_mul(b2, ec));
+        const df eq = df_add(xw, df_mul(m, df_add(eA, xw)));
         df rv;
         if (kind == 0) {
             rv = df{1.0f, 0.0f};
         } else if (kind == 1) {
-            const df pz = df_add(A.z, q.z), z2 = df_mul(pz, pz);
+            const df pz = df_add(eA, eq), z2 = df_mul(pz, pz);
             rv = df_add(df_mul(g1, df_mul(z2, z2)), gam);
         } else {
             // the argument of the cell's series, scaled by its power of two
-            const df u = df_add(u0, df3_dot(xc, q));
+            const df u = df_add(u0, eq);
             const df v{u.hi * vs, u.lo * vs};
             rv = df{sdf[K - 1].x, sdf[K - 1].y};
             for (int j = K - 2; j >= 0; --j) rv = df_fma(rv, v, df{sdf[j].x, sdf[j].y});
         }
         const df wr = df_mul(df_mul(W, area), rv);
-        acc.m = df_add(acc.m, wr);
-        acc.qx = df_add(acc.qx, df_mul(wr, q.x));
-        acc.qy = df_add(acc.qy, df_mul(wr, q.y));
-        acc.qz = df_add(acc.qz, df_mul(wr, q.z));
-        acc.e = df_add(acc.e, df_mul(wr, df3_dot(q, q)));
+        const df wm = df_mul(wr, m);
+        // |q|^2 = |w|^2 + 2 m (|w|^2 + A.w) + m^2 - m^2 delta
+        const df mwa = df_mul(m, df_add(ww, Aw)), msq = df_mul(m, m);
+        const df e = df_add_f(df_add(df_add(ww, df{2.0f * mwa.hi, 2.0f * mwa.lo}), msq), -msq.hi * dl.hi);
+        S0 = df_add(S0, wr);
+        S1 = df_add(S1, df_mul(wr, b1));
+        S2 = df_add(S2, df_mul(wr, b2));
+        T0 = df_add(T0, wm);
+        T1 = df_add(T1, df_mul(wm, b1));
+        T2 = df_add(T2, df_mul(wm, b2));
+        E = df_add(E, df_mul(wr, e));
     }
+    const df a1 = df_add(S1, T1), a2 = df_add(S2, T2);
+    acc.m = df_add(acc.m, S0);
+    acc.qx = df_add(acc.qx, df_add(df_add(df_mul(a1, b.x), df_mul(a2, c.x)), df_mul(T0, A.x)));
+    acc.qy = df_add(acc.qy, df_add(df_add(df_mul(a1, b.y), df_mul(a2, c.y)), df_mul(T0, A.y)));
+    acc.qz = df_add(acc.qz, df_add(df_add(df_mul(a1, b.z), df_mul(a2, c.z)), df_mul(T0, A.z)));
+    acc.e = df_add(acc.e, E);
 }
 
 // One thread per Voronoi edge (two signed sub-triangles of Sec. 3.2.2, 14
@@ -1785,7 +1810,10 @@ __global__ void __launch_bounds__(512) k_quad(Grid g, CellBuf cb, int ecap, Span
         if (r2 <= 1e-3f && (rho.kind < 2 || K > 0)) {
             const df3 A{df{g.zf[p].x, g.zl[p].x}, df{g.zf[p].y, g.zl[p].y}, df{g.zf[p].z, g.zl[p].z}};
             const df aA1 = df_from(dot(zi, zi) - 1.0);
-            const df3 xc = df3_from(rho.xc0, rho.xc1, rho.xc2);
+            // the density's direction: x_c for the tanh cap, e_z for X3
+            const df3 ev = (rho.kind == 1) ? df3{df{0.0f, 0.0f}, df{0.0f, 0.0f}, df{1.0f, 0.0f}}
+                                           : df3_from(rho.xc0, rho.xc1, rho.xc2);
+            const df eA = df3_dot(ev, A);
             const df u0 = (K > 0) ? df_from(dot(mk(rho.xc0, rho.xc1, rho.xc2), zi) - ser[kSerMax]) : df{0.0f, 0.0f};
             const df g1 = df_from(1.0 - rho.gamma), gam = df_from(rho.gamma);
             const float2 *sdf = reinterpret_cast<const float2 *>(ser + kSerMax + 1);
@@ -1793,10 +1821,10 @@ __global__ void __launch_bounds__(512) k_quad(Grid g, CellBuf cb, int ecap, Span
             const df3 da = df3_from(ba.x, ba.y, ba.z), dm = df3_from(bm.x, bm.y, bm.z), db = df3_from(bb.x, bb.y, bb.z);
             AccDF ad{};
             if (g.fan) {
-                tri_df(rho.kind, g1, gam, A, aA1, da, db, xc, u0, sdf, vs, K, ad);
+                tri_df(rho.kind, g1, gam, A, aA1, da, db, ev, eA, u0, sdf, vs, K, ad);
             } else {
-                tri_df(rho.kind, g1, gam, A, aA1, da, dm, xc, u0, sdf, vs, K, ad);
-                tri_df(rho.kind, g1, gam, A, aA1, dm, db, xc, u0, sdf, vs, K, ad);
+                tri_df(rho.kind, g1, gam, A, aA1, da, dm, ev, eA, u0, sdf, vs, K, ad);
+                tri_df(rho.kind, g1, gam, A, aA1, dm, db, ev, eA, u0, sdf, vs, K, ad);
             }
             const double m = df_to(ad.m);
             ea[e] = m;
