@@ -1786,8 +1786,23 @@ __device__ __forceinline__ void tri_df(int kind, df g1, df gam, df3 A, df aA1, d
 // rule points, summed in order).  The edge's five sums go to the edge list;
 // k_cell_sum adds a cell's edges in edge order, so a cell's result depends
 // on its own edges only (not on where they fall in the launch).
+// the density's direction as a double-float vector (x_c for the tanh cap,
+// e_z for X3) and its constants 1 - gamma, gamma
+struct DensDF {
+    df3 ev;
+    df g1, gam;
+};
+__device__ __forceinline__ DensDF dens_df(const Density &r) {
+    DensDF d;
+    d.ev = (r.kind == 1) ? df3{df{0.0f, 0.0f}, df{0.0f, 0.0f}, df{1.0f, 0.0f}} : df3_from(r.xc0, r.xc1, r.xc2);
+    d.g1 = df_from(1.0 - r.gamma);
+    d.gam = df_from(r.gamma);
+    return d;
+}
+
 __global__ void __launch_bounds__(512) k_quad(Grid g, CellBuf cb, int ecap, Span sp) {
     const int ne = *sp.etot, eb = *sp.e0;
+    const DensDF dd0 = dens_df(g.rho0);  // single-problem density, converted once
     for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < ne; it += gridDim.x * blockDim.x) {
         const int e = eb + it;
         const int p = cb.ecell[e];
@@ -1797,34 +1812,45 @@ __global__ void __launch_bounds__(512) k_quad(Grid g, CellBuf cb, int ecap, Span
         const P4 *vx = cb.vx + (size_t)p * kCellSlots;
         const V3 va = ld(vx + k);
         const V3 vb = ld(vx + ((k + 1 == deg) ? 0 : k + 1));
-        const V3 mu = unit(add(zi, ld(g.zs + cb.nb[(size_t)p * kCellSlots + k])));
+        const V3 zj = ld(g.zs + cb.nb[(size_t)p * kCellSlots + k]);
         const Density rho = g.rho ? g.rho[view_of(g, p).b] : g.rho0;
         const int K = cb.serK ? cb.serK[p] : 0;
         const double *ser = cb.ser + (size_t)p * kSerStride;
         double *ea = cb.eacc;
         // double-float path: offsets of the edge's points from z_i below chord
         // 0.03 (then delta <= 1e-3 at every rule point) and a density without
-        // direct evaluation; otherwise FP64
-        const V3 ba = sub(va, zi), bm = sub(mu, zi), bb = sub(vb, zi);
-        const float r2 = fmaxf(fmaxf((float)dot(ba, ba), (float)dot(bb, bb)), (float)dot(bm, bm));
-        if (r2 <= 1e-3f && (rho.kind < 2 || K > 0)) {
+        // direct evaluation; otherwise FP64.  Offsets are FP64 differences of
+        // nearby points (exact to 1e-16 of their size), rounded to pairs.
+        const V3 ba = sub(va, zi), bb = sub(vb, zi), bj = sub(zj, zi);
+        const df3 da = df3_from(ba.x, ba.y, ba.z), db = df3_from(bb.x, bb.y, bb.z), dj = df3_from(bj.x, bj.y, bj.z);
+        const float r2 = fmaxf(fmaxf(da.x.hi * da.x.hi + da.y.hi * da.y.hi + da.z.hi * da.z.hi,
+                                     db.x.hi * db.x.hi + db.y.hi * db.y.hi + db.z.hi * db.z.hi),
+                               0.25f * (dj.x.hi * dj.x.hi + dj.y.hi * dj.y.hi + dj.z.hi * dj.z.hi));
+        if (r2 <= 0.9e-3f && (rho.kind < 2 || K > 0)) {
             const df3 A{df{g.zf[p].x, g.zl[p].x}, df{g.zf[p].y, g.zl[p].y}, df{g.zf[p].z, g.zl[p].z}};
             const df aA1 = df_from(dot(zi, zi) - 1.0);
-            // the density's direction: x_c for the tanh cap, e_z for X3
-            const df3 ev = (rho.kind == 1) ? df3{df{0.0f, 0.0f}, df{0.0f, 0.0f}, df{1.0f, 0.0f}}
-                                           : df3_from(rho.xc0, rho.xc1, rho.xc2);
-            const df eA = df3_dot(ev, A);
+            const DensDF dd = g.rho ? dens_df(rho) : dd0;
+            const df eA = df3_dot(dd.ev, A);
             const df u0 = (K > 0) ? df_from(dot(mk(rho.xc0, rho.xc1, rho.xc2), zi) - ser[kSerMax]) : df{0.0f, 0.0f};
-            const df g1 = df_from(1.0 - rho.gamma), gam = df_from(rho.gamma);
             const float2 *sdf = reinterpret_cast<const float2 *>(ser + kSerMax + 1);
             const float vs = (K > 0) ? (float)ser[2 * kSerMax + 1] : 1.0f;
-            const df3 da = df3_from(ba.x, ba.y, ba.z), dm = df3_from(bm.x, bm.y, bm.z), db = df3_from(bb.x, bb.y, bb.z);
+            // edge midpoint mu = (z_i + z_j) / |z_i + z_j|: with h = (z_j - z_i) / 2,
+            // mu - z_i = h + m (A + h), 1 - |A + h|^2 = -(|A|^2 - 1) - 2 A.h - |h|^2
+            const df3 hh{df{0.5f * dj.x.hi, 0.5f * dj.x.lo}, df{0.5f * dj.y.hi, 0.5f * dj.y.lo},
+                         df{0.5f * dj.z.hi, 0.5f * dj.z.lo}};
+            const df Ah = df3_dot(A, hh);
+            const df dl = df_neg(df_add(df_add(aA1, df{2.0f * Ah.hi, 2.0f * Ah.lo}), df3_dot(hh, hh)));
+            const df d2 = df_mul(dl, dl);
+            const float tail = d2.hi * dl.hi * (0.3125f + dl.hi * (0.2734375f + dl.hi * 0.24609375f));
+            const df mm = df_add_f(df_add(df{0.5f * dl.hi, 0.5f * dl.lo}, df_mul_f(d2, 0.375f)), tail);
+            const df3 dm{df_add(hh.x, df_mul(mm, df_add(A.x, hh.x))), df_add(hh.y, df_mul(mm, df_add(A.y, hh.y))),
+                         df_add(hh.z, df_mul(mm, df_add(A.z, hh.z)))};
             AccDF ad{};
             if (g.fan) {
-                tri_df(rho.kind, g1, gam, A, aA1, da, db, ev, eA, u0, sdf, vs, K, ad);
+                tri_df(rho.kind, dd.g1, dd.gam, A, aA1, da, db, dd.ev, eA, u0, sdf, vs, K, ad);
             } else {
-                tri_df(rho.kind, g1, gam, A, aA1, da, dm, ev, eA, u0, sdf, vs, K, ad);
-                tri_df(rho.kind, g1, gam, A, aA1, dm, db, ev, eA, u0, sdf, vs, K, ad);
+                tri_df(rho.kind, dd.g1, dd.gam, A, aA1, da, dm, dd.ev, eA, u0, sdf, vs, K, ad);
+                tri_df(rho.kind, dd.g1, dd.gam, A, aA1, dm, db, dd.ev, eA, u0, sdf, vs, K, ad);
             }
             const double m = df_to(ad.m);
             ea[e] = m;
@@ -1834,6 +1860,7 @@ __global__ void __launch_bounds__(512) k_quad(Grid g, CellBuf cb, int ecap, Span
             ea[4 * (size_t)ecap + e] = df_to(ad.e);
             continue;
         }
+        const V3 mu = unit(add(zi, zj));
         const double inv_alpha = (K > 0 || rho.kind < 2) ? 0.0 : 1.0 / rho.alpha;  // direct tanh cap only
         Acc acc = {0, 0, 0, 0, 0};
         if (g.fan) {
