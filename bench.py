@@ -458,43 +458,12 @@ def run_ours(args, w):
     units, t_max = combine_ranks(w.n * iters, t, device=torch.device("cuda", local))
     value = units / t_max
 
-    # dominant kernel: the cell quadrature, timed by CUDA events on the engine
-    # stream around each launch; with concurrent cell pipelines its launches
-    # overlap other kernels, so it is timed on a few further evaluations of
-    # the same iterate with one pipeline
-    if st["cell_kernel_timed"] == 0:
-        tsave = eng.tuning()
-        eng.set_tuning(**dict(tsave, chunks=1))
-        eng.evaluate(z)
-        eng.reset_stats()
-        for _ in range(3):
-            eng.evaluate(z)
-        stq = eng.stats()
-        eng.set_tuning(**tsave)
-        quad_ms = stq["cell_kernel_ms"] / max(stq["cell_kernel_timed"], 1)
-    else:
-        stq = st
-        quad_ms = st["cell_kernel_ms"] / max(st["cell_kernel_timed"], 1)
-    if prec == 0:
-        sfrac = stq["series_cells"] / max(w.n * stq["evaluations"], 1)
-        slen = stq["series_terms"] / max(stq["series_cells"], 1)
-        flops_gen = fp64_flops_per_generator(w.density.kind, sfrac, slen)
-        peak = fp64_peak_tflops()
-        achieved = w.n * flops_gen / (quad_ms * 1e-3) / 1e12
-        roofline = {"bound": "alu", "kernel": "k_quad", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": quad_traffic_bytes(w.n),
-                    "flops_per_generator": flops_gen, "avg_launch_ms": quad_ms,
-                    "series_cell_fraction": sfrac, "series_terms_avg": slen,
-                    "flops_per_generator_direct_density": fp64_flops_per_generator(w.density.kind),
-                    "peak_source": "derived FP64 pipe peak: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz "
-                                   "(no FP64 figure in the measured-peaks file; a DFMA microbenchmark on this "
-                                   "pool measured 1.006 TFLOP/s)",
-                    "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_quad launch "
-                                      "at N = 163,842, scaled by N (profiles/k_quad_tanh_163842.md)"}
-    else:
-        roofline = {"bound": "alu", "kernel": "k_quad32", "achieved": None, "peak": None, "unit": "TFLOP/s",
-                    "frac": None, "traffic": None, "avg_launch_ms": quad_ms,
-                    "note": "mixed form: the FP32 quadrature is no longer the dominant kernel"}
+    # dominant kernel, timed by CUDA events on the engine stream around each
+    # launch; with concurrent cell pipelines the cell kernels overlap, so they
+    # are timed on three further evaluations of the same iterate with one
+    # pipeline
+    quad_ms, topo_ms, stq = one_pipeline_kernel_ms(eng, z)
+    roofline = roofline_of(prec, w, quad_ms, topo_ms, stq)
 
     # end to end through the C ABI with host buffers: a second engine replays
     # the same warm-up (evaluations are deterministic, so it reaches the same
@@ -541,12 +510,12 @@ def run_ours(args, w):
         torch.cuda.synchronize()
         rep3, t3 = timed_steps(eng3, z3, args.steps)
         st3 = eng3.stats()
+        q3, tp3, stq3 = one_pipeline_kernel_ms(eng3, z3)
         eng3.close()
         u3, t3 = combine_ranks(w.n * rep3["iters"], t3, device=torch.device("cuda", local))
-        other = {"precision": "mixed" if oprec else "fp64", "dtype": "f32/f64" if oprec else "f64",
+        other = {"precision": "mixed" if oprec else "fp64", "dtype": "f32/f64" if oprec else "f64+f32x2",
                  "value": u3 / t3, "ms_per_step": 1e3 * t3 / max(rep3["iters"], 1),
-                 "quad_kernel_ms": (st3["cell_kernel_ms"] / st3["cell_kernel_timed"]
-                                    if st3["cell_kernel_timed"] else None),
+                 "roofline": roofline_of(oprec, w, q3, tp3, stq3),
                  "eval_ms_avg": st3["eval_ms"] / max(st3["evaluations"], 1), "tuning": tuning[oprec]}
 
     batched = None
@@ -596,7 +565,7 @@ def run_ours(args, w):
             "metric": "generator-updates/s", "value": value, "unit": "generator-updates/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_max / max(iters, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32/f64" if prec else "f64", "data": "synthetic",
+            "dtype": "f32/f64" if prec else "f64+f32x2", "data": "synthetic",
             "config": {"workload": w.name, "n_generators": w.n, "density": "tanh cap",
                        "gamma": w.density.gamma, "alpha": w.density.alpha, "beta": w.density.beta,
                        "lbfgs_m": w.lbfgs_m, "quadrature": "7-point per sub-triangle", "seed": args.seed,
@@ -660,6 +629,63 @@ def fp64_flops_per_generator(kind: int, series_frac: float = 0.0, series_len: fl
 
 def fp64_peak_tflops() -> float:
     return 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+# Instruction issue is what bounds the double-float quadrature and the
+# topology pass: each of the 152 SMs' four schedulers issues at most one warp
+# instruction per clock (2.07 GHz), 1.2586e12 warp instructions per second.
+# The work per unit is the instruction count ncu measured for one launch at
+# N = 163,842 (smsp__inst_executed.sum / units; profiles/k_quad_tanh_163842.md,
+# profiles/k_topo_warp_tanh_163842.md).
+ISSUE_PEAK = 152 * 4 * 2.07e9
+QUAD_INST_PER_GENERATOR = 329820340 / 163842
+TOPO_INST_PER_CELL = 277051660 / 163842
+
+
+def one_pipeline_kernel_ms(eng, z, evals=3):
+    """Average CUDA-event time of the quadrature and of the first topology
+    pass over `evals` evaluations of z with one cell pipeline (the engine's
+    tuning is restored afterwards; stats are reset)."""
+    tsave = eng.tuning()
+    eng.set_tuning(**dict(tsave, chunks=1))
+    eng.set_profiling(True)
+    eng.evaluate(z)
+    eng.reset_stats()
+    for _ in range(evals):
+        eng.evaluate(z)
+    st = eng.stats()
+    eng.set_tuning(**tsave)
+    quad = st["cell_kernel_ms"] / max(st["cell_kernel_timed"], 1)
+    topo = st["topo_kernel_ms"] / max(st["topo_kernel_timed"], 1)
+    return quad, topo, st
+
+
+def roofline_of(prec, w, quad_ms, topo_ms, st):
+    """Roofline of the step's dominant kernel: the double-float quadrature in
+    the FP64 form, the topology pass in the mixed form; both issue-bound."""
+    if prec == 0:
+        sfrac = st["series_cells"] / max(w.n * st["evaluations"], 1)
+        slen = st["series_terms"] / max(st["series_cells"], 1)
+        flops_gen = fp64_flops_per_generator(w.density.kind, sfrac, slen)
+        achieved = w.n * QUAD_INST_PER_GENERATOR / (quad_ms * 1e-3) / 1e12
+        return {"bound": "alu", "kernel": "k_quad", "achieved": achieved, "peak": ISSUE_PEAK / 1e12,
+                "unit": "Twarp-inst/s", "frac": achieved * 1e12 / ISSUE_PEAK, "traffic": quad_traffic_bytes(w.n),
+                "avg_launch_ms": quad_ms, "inst_per_generator": QUAD_INST_PER_GENERATOR,
+                "fp64_equivalent_tflops": w.n * flops_gen / (quad_ms * 1e-3) / 1e12,
+                "fp64_flop_equivalents_per_generator": flops_gen,
+                "fp64_pipe_peak_tflops": fp64_peak_tflops(),
+                "series_cell_fraction": sfrac, "series_terms_avg": slen,
+                "peak_source": "instruction issue: 152 SMs x 4 schedulers x 1 warp-instruction/clk x 2.07 GHz",
+                "work_source": "ncu smsp__inst_executed.sum of one k_quad launch at N = 163,842 per generator "
+                               "(double-float arithmetic: FP32 pairs, FP64 only for per-edge offsets)",
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_quad launch "
+                                  "at N = 163,842, scaled by N (profiles/k_quad_tanh_163842.md)"}
+    achieved = w.n * TOPO_INST_PER_CELL / (topo_ms * 1e-3) / 1e12
+    return {"bound": "alu", "kernel": "k_topo_warp", "achieved": achieved, "peak": ISSUE_PEAK / 1e12,
+            "unit": "Twarp-inst/s", "frac": achieved * 1e12 / ISSUE_PEAK, "traffic": None,
+            "avg_launch_ms": topo_ms, "quad_kernel_ms": quad_ms, "inst_per_cell": TOPO_INST_PER_CELL,
+            "peak_source": "instruction issue: 152 SMs x 4 schedulers x 1 warp-instruction/clk x 2.07 GHz",
+            "work_source": "ncu smsp__inst_executed.sum of one k_topo_warp launch at N = 163,842 per cell"}
 
 
 def quad_traffic_bytes(n: int):

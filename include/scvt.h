@@ -131,6 +131,8 @@ typedef struct {
     int64_t bytes_device;       /* device memory held by the handle */
     int64_t series_cells;       /* FP64 form: cells whose density came from their Taylor series */
     int64_t series_terms;       /* ... and the sum of those series' lengths */
+    double topo_kernel_ms;      /* device time of the first topology pass (profiling on, one pipeline) */
+    int64_t topo_kernel_timed;  /* first topology passes included in topo_kernel_ms */
 } scvt_stats;
 
 typedef struct scvt_handle scvt_handle;

@@ -78,6 +78,7 @@ struct scvt_handle {
     // stats
     scvt_stats stats;
     bool profiling = false;
+    cudaEvent_t ev_topo[2] = {nullptr, nullptr};
     cudaEvent_t ev_cell0 = nullptr, ev_cell1 = nullptr, ev_e0 = nullptr, ev_e1 = nullptr, ev_l0 = nullptr,
                 ev_l1 = nullptr;
     std::string err;
@@ -125,9 +126,15 @@ double *slot_Y(scvt_handle *H, int slot) { return slot_S(H, slot) + (size_t)3 * 
 void profile_accumulate(scvt_handle *H) {
     if (!H->profiling) return;
     float ms = 0.0f;
-    if (cudaEventElapsedTime(&ms, H->ev_cell0, H->ev_cell1) == cudaSuccess) {
+    // the cell kernels are timed only when the cells run as one pipeline
+    const bool one = H->tune.chunks <= 1 || H->pipes.n_aux == 0;
+    if (one && cudaEventElapsedTime(&ms, H->ev_cell0, H->ev_cell1) == cudaSuccess) {
         H->stats.cell_kernel_ms += ms;
         H->stats.cell_kernel_timed++;
+    }
+    if (one && cudaEventElapsedTime(&ms, H->ev_topo[0], H->ev_topo[1]) == cudaSuccess) {
+        H->stats.topo_kernel_ms += ms;
+        H->stats.topo_kernel_timed++;
     }
     if (cudaEventElapsedTime(&ms, H->ev_e0, H->ev_e1) == cudaSuccess) H->stats.eval_ms += ms;
     cudaGetLastError();
@@ -187,7 +194,7 @@ scvt_status evaluate_dev(scvt_handle *H, const double *zdev, double *grad, doubl
     cb.serK = B.serK;
     cell_passes(g, out, cb, B.list1, B.list2, B.st, H->cfg.precision == 1, H->tune, s,
                 H->profiling ? H->ev_cell0 : nullptr, H->profiling ? H->ev_cell1 : nullptr, L,
-                &H->stats.cell_launches, &H->pipes);
+                &H->stats.cell_launches, &H->pipes, H->profiling ? H->ev_topo : nullptr);
     reduce_eval(n, fcell, grad, q, nrm, B.partials, B.st, s, L);
     if (H->profiling) cudaEventRecord(H->ev_e1, s);
     CK(cudaGetLastError(), "launch");
@@ -326,7 +333,7 @@ void scvt_destroy(scvt_handle *H) {
         if (p) cudaFree(p);
     if (H->st_host) cudaFreeHost(H->st_host);
     pipes_destroy(H->pipes);
-    cudaEvent_t evs[] = {H->ev_cell0, H->ev_cell1, H->ev_e0, H->ev_e1, H->ev_l0, H->ev_l1};
+    cudaEvent_t evs[] = {H->ev_cell0, H->ev_cell1, H->ev_e0, H->ev_e1, H->ev_l0, H->ev_l1, H->ev_topo[0], H->ev_topo[1]};
     for (cudaEvent_t e : evs)
         if (e) cudaEventDestroy(e);
     delete H;
@@ -386,7 +393,8 @@ scvt_status scvt_create(const scvt_config *cfg, void *cuda_stream, scvt_handle *
 #undef AL
     if (e == cudaSuccess) e = cudaMallocHost((void **)&H->st_host, sizeof(DevStatus));
     if (e == cudaSuccess) e = pipes_create(H->pipes, kMaxChunks - 1);
-    cudaEvent_t *evs[] = {&H->ev_cell0, &H->ev_cell1, &H->ev_e0, &H->ev_e1, &H->ev_l0, &H->ev_l1};
+    cudaEvent_t *evs[] = {&H->ev_cell0, &H->ev_cell1, &H->ev_e0, &H->ev_e1, &H->ev_l0, &H->ev_l1, &H->ev_topo[0],
+                          &H->ev_topo[1]};
     for (cudaEvent_t *ev : evs)
         if (e == cudaSuccess) e = cudaEventCreate(ev);
     if (e != cudaSuccess) {

@@ -2172,7 +2172,7 @@ DensityF to_density32(const Density &d) {
 
 void cell_passes(const Grid &g, const CellOut &out, const CellBuf &cb, int *list1, int *list2, DevStatus *st,
                  bool mixed, const Tune &t, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1, int64_t *launches,
-                 int64_t *cell_launches, const Pipes *px) {
+                 int64_t *cell_launches, const Pipes *px, const cudaEvent_t *topo_ev) {
     // the cells are cut into nch chunks of consecutive bin positions, each run
     // through the whole pipeline on its own stream (the first on s); chunks
     // share nothing but the read-only generators, so their kernels overlap
@@ -2195,6 +2195,8 @@ void cell_passes(const Grid &g, const CellOut &out, const CellBuf &cb, int *list
         if (len <= 0) continue;
         unsigned *rc = counts + kChunkWords * c;
         int *cw = (int *)rc;  // this chunk's words
+        const bool timed = (c == 0 && nch == 1);
+        if (timed && topo_ev) cudaEventRecord(topo_ev[0], sc);
         // first pass: a warp (or half warp) per cell, grid capped at topo_bpsm blocks per SM
         const int wblocks =
             (int)std::max<long long>(1, std::min<long long>((len + wpb * cpw - 1) / (wpb * cpw), 152LL * t.topo_bpsm / nch));
@@ -2207,6 +2209,7 @@ void cell_passes(const Grid &g, const CellOut &out, const CellBuf &cb, int *list
             else if (wpb == 8) k_topo_warp<8, 32><<<wblocks, 256, 0, sc>>>(g, out, cb, list1 + p0, rc, st, kt, p0, p1);
             else k_topo_warp<4, 32><<<wblocks, 128, 0, sc>>>(g, out, cb, list1 + p0, rc, st, kt, p0, p1);
         }
+        if (timed && topo_ev) cudaEventRecord(topo_ev[1], sc);
         // retry passes (thread per cell): sized for the worst case, they read their work count on the device
         const int rblocks = std::max(1, 2 * 152 / nch);
         k_topo<64, 64, 0><<<rblocks, 64, 0, sc>>>(g, out, cb, list1 + p0, rc, list2 + p0, rc + 1, 0, 0, st);
@@ -2227,7 +2230,6 @@ void cell_passes(const Grid &g, const CellOut &out, const CellBuf &cb, int *list
         const unsigned eblocks = (unsigned)((6 * len + qb - 1) / qb);
         const unsigned e256 = (unsigned)((6 * len + 255) / 256);
         const unsigned cblocks = (unsigned)((len + 255) / 256);
-        const bool timed = (c == 0 && nch == 1);
         if (mixed) {
             k_corners32<<<e256, 256, 0, sc>>>(g, cb, sp);
             if (timed && ev0) cudaEventRecord(ev0, sc);

@@ -187,9 +187,11 @@ cudaError_t pipes_create(Pipes &px, int n_aux);
 void pipes_destroy(Pipes &px);
 inline size_t scan_tmp_ints(int64_t n) { return (size_t)kMaxChunks * (2 * ((size_t)n / 2048 + 64) + 64); }
 
+// topo_ev (nullable): two events recorded around the first topology pass,
+// like ev0 / ev1 around the quadrature, when the cells run as one pipeline
 void cell_passes(const Grid &g, const CellOut &out, const CellBuf &cb, int *list1, int *list2, DevStatus *st,
                  bool mixed, const Tune &t, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1, int64_t *launches,
-                 int64_t *cell_launches, const Pipes *px);
+                 int64_t *cell_launches, const Pipes *px, const cudaEvent_t *topo_ev = nullptr);
 Density to_device_density(const scvt_density &r);
 // exclusive scan of len ints (tmp: 2 * (len / 2048 + 64) + 64 ints)
 void exclusive_scan(const int *in, int *out, int len, int *tmp, cudaStream_t s, int64_t *launches);

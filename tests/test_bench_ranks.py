@@ -55,6 +55,22 @@ def test_roofline_figures_are_defined_for_every_density():
     assert bench.quad_traffic_bytes(163842) > 0
 
 
+def test_roofline_of_both_forms():
+    import bench
+    from paper_1709_06924_gb300 import inputs as I
+    w = I.WORKLOADS["tanh-2621442"]
+    st = {"series_cells": w.n * 3, "series_terms": w.n * 3 * 5, "evaluations": 3}
+    r0 = bench.roofline_of(0, w, 5.0, 4.0, st)
+    r1 = bench.roofline_of(1, w, 1.0, 4.0, st)
+    for r, ms in ((r0, 5.0), (r1, 4.0)):
+        assert r["bound"] == "alu" and r["unit"] == "Twarp-inst/s"
+        assert abs(r["peak"] - 152 * 4 * 2.07e9 / 1e12) < 1e-12
+        assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-12
+        assert r["avg_launch_ms"] == ms
+    assert r0["kernel"] == "k_quad" and r1["kernel"] == "k_topo_warp"
+    assert r0["series_cell_fraction"] == 1.0 and r0["series_terms_avg"] == 5.0
+
+
 def test_parse_tuning():
     import bench
     assert bench.parse_tuning("") == {}
