@@ -638,7 +638,7 @@ def fp64_peak_tflops() -> float:
 # N = 163,842 (smsp__inst_executed.sum / units; profiles/k_quad_tanh_163842.md,
 # profiles/k_topo_warp_tanh_163842.md).
 ISSUE_PEAK = 152 * 4 * 2.07e9
-QUAD_INST_PER_GENERATOR = 329820340 / 163842
+QUAD_INST_PER_GENERATOR = 330606408 / 163842
 TOPO_INST_PER_CELL = 277051660 / 163842
 
 
@@ -689,10 +689,10 @@ def roofline_of(prec, w, quad_ms, topo_ms, st):
 
 
 def quad_traffic_bytes(n: int):
-    """DRAM bytes of one k_quad launch: ncu at N = 163,842 (90.95 MB read +
-    14.42 MB written, tanh cap, density series on), scaled by the number of
+    """DRAM bytes of one k_quad launch: ncu at N = 163,842 (115.63 MB read +
+    18.54 MB written, tanh cap, density series on), scaled by the number of
     generators."""
-    return (90.947328e6 + 14.423552e6) * n / 163842
+    return (115.627520e6 + 18.537984e6) * n / 163842
 
 
 def main():

@@ -198,7 +198,7 @@ scvt_status scvt_lbfgs_direction(scvt_handle *h, const double *g, const double *
  * host that forbids cudaMalloc after start-up).  The paper has no
  * counterpart: this is a deployment variant of scvt_energy_grad.
  * It needs no handle and allocates nothing: its scratch is one fixed array
- * in device memory (about 19.1 MB, held on every GPU that loads the library
+ * in device memory (about 21.9 MB, held on every GPU that loads the library
  * until the process exits), sized for n <= SCVT_STATIC_MAX_N.
  * n: generators (4 <= n <= SCVT_STATIC_MAX_N, else SCVT_ERR_INVALID before
  * any device work).  rho: host.  z: N x 3 device.  cuda_stream: cudaStream_t

@@ -65,7 +65,7 @@ constexpr size_t oEacc = oEscan + up(sizeof(int) * (2 * (kMaxN / 2048 + 64) + 64
 constexpr size_t oSer = oEacc + up(sizeof(double) * 5 * 6 * kMaxN);
 constexpr size_t oSerK = oSer + up(sizeof(double) * kSerWords * kMaxN);
 constexpr size_t oCounts = oSerK + up(sizeof(int) * kMaxN);
-constexpr size_t kBytes = oCounts + up(sizeof(unsigned) * 8 * kMaxChunks);  // about 19.1 MB
+constexpr size_t kBytes = oCounts + up(sizeof(unsigned) * 8 * kMaxChunks);  // about 21.9 MB
 
 __device__ __align__(256) unsigned char g_scratch[kBytes];
 
