@@ -42,7 +42,7 @@ struct Bufs {
     double *gamma = nullptr;                 // plain LBFGS scaling of H0
     double *hist = nullptr;                  // (m + 1) slots of S and Y, 3n each
     P4 *zs = nullptr;
-    float4 *zf = nullptr, *zl = nullptr;
+    float4 *zf = nullptr, *zl = nullptr, *zll = nullptr;
     P4 *cvx = nullptr;
     int *cdeg = nullptr, *cnb = nullptr, *eoff = nullptr, *ecell = nullptr, *escan = nullptr;
     double *eacc = nullptr, *ser = nullptr;
@@ -160,6 +160,7 @@ scvt_status evaluate_dev(scvt_handle *H, const double *zdev, double *grad, doubl
     g.zs = B.zs;
     g.zf = B.zf;
     g.zl = B.zl;
+    g.zll = B.zll;
     g.sidx = B.sidx;
     g.bstart = B.start;
     g.rho0 = to_device_density(H->cfg.rho);
@@ -169,7 +170,7 @@ scvt_status evaluate_dev(scvt_handle *H, const double *zdev, double *grad, doubl
         CK(cudaMemsetAsync(B.radius, 0, sizeof(float) * n, s), "reset radius hints");
         H->radius_valid = true;
     }
-    bin_points(zdev, g, B.bin_of, B.count, B.start, B.cursor, B.scan_tmp, B.zs, B.zf, B.zl, B.sidx, B.radius, B.st, s,
+    bin_points(zdev, g, B.bin_of, B.count, B.start, B.cursor, B.scan_tmp, B.zs, B.zf, B.zl, H->cfg.precision == 0 ? B.zll : nullptr, B.sidx, B.radius, B.st, s,
                L);
     CellOut out;
     out.grad = grad;
@@ -327,7 +328,7 @@ void scvt_destroy(scvt_handle *H) {
     if (!H) return;
     Bufs &b = H->b;
     void *ptrs[] = {b.z, b.zt, b.g, b.gt, b.h, b.ht, b.fc, b.q, b.yv, b.nrm, b.mass, b.moment, b.stage_a, b.stage_b,
-                    b.partials, b.scal, b.rho, b.gamma, b.hist, b.zs, b.zf, b.zl, b.cvx, b.cnb, b.cdeg, b.eoff, b.ecell, b.escan, b.eacc, b.vo, b.ser, b.serK, b.bin_of, b.count, b.start, b.cursor, b.scan_tmp,
+                    b.partials, b.scal, b.rho, b.gamma, b.hist, b.zs, b.zf, b.zl, b.zll, b.cvx, b.cnb, b.cdeg, b.eoff, b.ecell, b.escan, b.eacc, b.vo, b.ser, b.serK, b.bin_of, b.count, b.start, b.cursor, b.scan_tmp,
                     b.sidx, b.list1, b.list2, b.deg, b.radius, b.st};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -381,7 +382,7 @@ scvt_status scvt_create(const scvt_config *cfg, void *cuda_stream, scvt_handle *
     AL(b.stage_a, n3); AL(b.stage_b, n3);
     AL(b.partials, 4 * 1024); AL(b.scal, 128); AL(b.rho, kMaxM + 1); AL(b.gamma, 1);
     AL(b.hist, (size_t)(H->m + 1) * 2 * n3);
-    AL(b.zs, n); AL(b.zf, n); AL(b.zl, n); AL(b.cvx, (size_t)n * kCellSlots); AL(b.cnb, (size_t)n * kCellSlots);
+    AL(b.zs, n); AL(b.zf, n); AL(b.zl, n); AL(b.zll, n); AL(b.cvx, (size_t)n * kCellSlots); AL(b.cnb, (size_t)n * kCellSlots);
     AL(b.cdeg, n); AL(b.eoff, n + 1); AL(b.ecell, 6 * (size_t)n); AL(b.escan, scan_tmp_ints(n));
     AL(b.eacc, 5 * 6 * (size_t)n);
     if (cfg->precision == 1) AL(b.vo, (size_t)n * kCellSlots);

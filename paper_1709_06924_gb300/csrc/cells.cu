@@ -209,6 +209,26 @@ __global__ void k_bin_sort(const int *__restrict__ start, int nbins, P4 *__restr
     }
 }
 
+// Third FP32 part of each coordinate (z - hi - lo, exact: hi + lo + ll == z
+// since z - hi and then the remainder after lo are exact in FP64 and the last
+// fits in 24 bits) and |z|^2 - 1: the squares by the FMA form of TwoProduct,
+// their sum by TwoSum, so s - 1 plus the error terms is |z|^2 - 1 to ~1e-32.
+__global__ void k_bin_fine(const P4 *__restrict__ zs, const float4 *__restrict__ zf, const float4 *__restrict__ zl,
+                           float4 *__restrict__ zll, int n) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const P4 v = zs[p];
+    const float4 h = zf[p], l = zl[p];
+    const double rx = (v.x - (double)h.x) - (double)l.x, ry = (v.y - (double)h.y) - (double)l.y,
+                 rz = (v.z - (double)h.z) - (double)l.z;
+    const double px = v.x * v.x, py = v.y * v.y, pz = v.z * v.z;
+    const double ex = fma(v.x, v.x, -px), ey = fma(v.y, v.y, -py), ez = fma(v.z, v.z, -pz);
+    const double s1 = px + py, b1 = s1 - px, t1 = (px - (s1 - b1)) + (py - b1);
+    const double s2 = s1 + pz, b2 = s2 - s1, t2 = (s1 - (s2 - b2)) + (pz - b2);
+    const double eps = (s2 - 1.0) + ((t1 + t2) + (ex + ey + ez));
+    zll[p] = make_float4((float)rx, (float)ry, (float)rz, (float)eps);
+}
+
 // exclusive scan of 2048-element tiles; writes tile totals
 __global__ void k_scan_tiles(const int *__restrict__ in, int *__restrict__ out, int len, int *__restrict__ totals) {
     __shared__ int warp_sums[32];
@@ -1478,8 +1498,36 @@ __global__ void __launch_bounds__(WPB * 32, 24 / WPB) k_topo_warp(Grid g, CellOu
     }
 }
 
-// FP64 corner of every edge: vertex k of a cell is the intersection of the
-// bisector lines of edges k-1 and k, solved in the gnomonic frame at z_i
+// z_q - z_p as a double-float from the three FP32 parts of each coordinate
+// (both differences of parts are exact by TwoSum; the third parts are tiny)
+__device__ __forceinline__ df3 gen_diff(const Grid &g, int q, float4 hp, float4 lp, float4 llp) {
+    const float4 hq = g.zf[q], lq = g.zl[q], llq = g.zll[q];
+    return df3{df_add_f(df_add(two_sum(hq.x, -hp.x), two_sum(lq.x, -lp.x)), llq.x - llp.x),
+               df_add_f(df_add(two_sum(hq.y, -hp.y), two_sum(lq.y, -lp.y)), llq.y - llp.y),
+               df_add_f(df_add(two_sum(hq.z, -hp.z), two_sum(lq.z, -lp.z)), llq.z - llp.z)};
+}
+
+// 1/|x| - 1 for delta = 1 - |x|^2 <= 1e-3 (binomial series, exact to 3e-19)
+__device__ __forceinline__ df inv_norm_m1(df dl) {
+    const df d2 = df_mul(dl, dl);
+    const float tail = d2.hi * dl.hi * (0.3125f + dl.hi * (0.2734375f + dl.hi * 0.24609375f));
+    return df_add_f(df_add(df{0.5f * dl.hi, 0.5f * dl.lo}, df_mul_f(d2, 0.375f)), tail);
+}
+
+// Corner of every edge: vertex k of a cell is where the bisector planes of
+// edges k-1 and k meet the plane z_i + u e1 + w e2 (then projected).
+// Double-float path: e1, e2 are any FP32 vectors spanning a plane through
+// z_i (the two bisector planes meet in a line through the origin, which
+// crosses it at the corner's direction whatever the tilt); the line of
+// neighbour j is a u + b w = c with (a, b) = (e1.d, e2.d), d = z_j - z_i from
+// the three-part coordinates, and c = -z_i.d = (|d|^2 + (|z_i|^2 - 1) -
+// (|z_j|^2 - 1)) / 2 without cancellation.  The 2x2 solve (well conditioned:
+// |det| >= (|a1 b2| + |a2 b1|) / 8, so the pairs' 2^-47 stays below 3e-14 of
+// u and w) gives the offset x - z_i = u e1 + w e2;
+// projecting, v - z_i = (1 + m)(x - z_i) + m z_i with m = 1/|x| - 1 from
+// delta = -(|z_i|^2 - 1) - 2 z_i.(x - z_i) - |x - z_i|^2.  Corners farther
+// than chord 0.03 or poorly conditioned are solved in FP64 in the gnomonic
+// frame at z_i.
 __global__ void __launch_bounds__(256) k_corners(Grid g, CellBuf cb, Span sp) {
     const int ne = *sp.etot, eb = *sp.e0;
     for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < ne; it += gridDim.x * blockDim.x) {
@@ -1488,12 +1536,58 @@ __global__ void __launch_bounds__(256) k_corners(Grid g, CellBuf cb, Span sp) {
         const int k = e - cb.eoff[p];
         const int deg = cb.deg[p];
         const int *nb = cb.nb + (size_t)p * kCellSlots;
+        const int ga = nb[(k == 0) ? deg - 1 : k - 1], gb = nb[k];
         const V3 zi = ld(g.zs + p);
+        {
+            const float4 hp = g.zf[p], lp = g.zl[p], llp = g.zll[p];
+            float3 e1, e2;
+            {
+                const float fx = fabsf(hp.x), fy = fabsf(hp.y), fz = fabsf(hp.z);
+                const float3 ax = (fx <= fy && fx <= fz) ? make_float3(1, 0, 0)
+                                                         : ((fy <= fz) ? make_float3(0, 1, 0) : make_float3(0, 0, 1));
+                const float3 c = make_float3(hp.y * ax.z - hp.z * ax.y, hp.z * ax.x - hp.x * ax.z,
+                                             hp.x * ax.y - hp.y * ax.x);
+                const float inv = rsqrtf(c.x * c.x + c.y * c.y + c.z * c.z);
+                e1 = make_float3(c.x * inv, c.y * inv, c.z * inv);
+                e2 = make_float3(hp.y * e1.z - hp.z * e1.y, hp.z * e1.x - hp.x * e1.z, hp.x * e1.y - hp.y * e1.x);
+            }
+            df la[2], lb[2], lc[2];
+#pragma unroll
+            for (int t = 0; t < 2; ++t) {
+                const int q = t == 0 ? ga : gb;
+                const df3 d = gen_diff(g, q, hp, lp, llp);
+                la[t] = df_add(df_add(df_mul_f(d.x, e1.x), df_mul_f(d.y, e1.y)), df_mul_f(d.z, e1.z));
+                lb[t] = df_add(df_add(df_mul_f(d.x, e2.x), df_mul_f(d.y, e2.y)), df_mul_f(d.z, e2.z));
+                const df c2 = df_add_f(df3_dot(d, d), llp.w - g.zll[q].w);
+                lc[t] = df{0.5f * c2.hi, 0.5f * c2.lo};
+            }
+            const df p1 = df_mul(la[0], lb[1]), p2 = df_mul(la[1], lb[0]);
+            const df det = df_sub(p1, p2);
+            if (fabsf(det.hi) * 8.0f >= fabsf(p1.hi) + fabsf(p2.hi)) {
+                const df u = df_div(df_sub(df_mul(lc[0], lb[1]), df_mul(lc[1], lb[0])), det);
+                const df w = df_div(df_sub(df_mul(la[0], lc[1]), df_mul(la[1], lc[0])), det);
+                const df3 dx{df_add(df_mul_f(u, e1.x), df_mul_f(w, e2.x)), df_add(df_mul_f(u, e1.y), df_mul_f(w, e2.y)),
+                             df_add(df_mul_f(u, e1.z), df_mul_f(w, e2.z))};
+                const float r2 = dx.x.hi * dx.x.hi + dx.y.hi * dx.y.hi + dx.z.hi * dx.z.hi;
+                if (r2 <= 0.9e-3f) {
+                    const df3 Z{df{hp.x, lp.x}, df{hp.y, lp.y}, df{hp.z, lp.z}};
+                    const df zd = df3_dot(Z, dx);
+                    const df dl = df_neg(df_add(df_add_f(df{2.0f * zd.hi, 2.0f * zd.lo}, llp.w), df3_dot(dx, dx)));
+                    const df m = inv_norm_m1(dl);
+                    const df ox = df_add(dx.x, df_mul(m, df_add(Z.x, dx.x)));
+                    const df oy = df_add(dx.y, df_mul(m, df_add(Z.y, dx.y)));
+                    const df oz = df_add(dx.z, df_mul(m, df_add(Z.z, dx.z)));
+                    cb.vx[(size_t)p * kCellSlots + k] =
+                        P4{zi.x + df_to(ox), zi.y + df_to(oy), zi.z + df_to(oz), 0.0};
+                    continue;
+                }
+            }
+        }
         V3 e1, e2;
         frame64(zi, e1, e2);
         double a1, b1, c1, a2, b2, c2;
-        line_of(g, zi, e1, e2, nb[(k == 0) ? deg - 1 : k - 1], a1, b1, c1);
-        line_of(g, zi, e1, e2, nb[k], a2, b2, c2);
+        line_of(g, zi, e1, e2, ga, a1, b1, c1);
+        line_of(g, zi, e1, e2, gb, a2, b2, c2);
         const double inv = 1.0 / (a1 * b2 - a2 * b1);
         const double u = (c1 * b2 - c2 * b1) * inv;
         const double w = (a1 * c2 - a2 * c1) * inv;
@@ -1812,7 +1906,6 @@ __global__ void __launch_bounds__(512) k_quad(Grid g, CellBuf cb, int ecap, Span
         const P4 *vx = cb.vx + (size_t)p * kCellSlots;
         const V3 va = ld(vx + k);
         const V3 vb = ld(vx + ((k + 1 == deg) ? 0 : k + 1));
-        const V3 zj = ld(g.zs + cb.nb[(size_t)p * kCellSlots + k]);
         const Density rho = g.rho ? g.rho[view_of(g, p).b] : g.rho0;
         const int K = cb.serK ? cb.serK[p] : 0;
         const double *ser = cb.ser + (size_t)p * kSerStride;
@@ -1821,14 +1914,16 @@ __global__ void __launch_bounds__(512) k_quad(Grid g, CellBuf cb, int ecap, Span
         // 0.03 (then delta <= 1e-3 at every rule point) and a density without
         // direct evaluation; otherwise FP64.  Offsets are FP64 differences of
         // nearby points (exact to 1e-16 of their size), rounded to pairs.
-        const V3 ba = sub(va, zi), bb = sub(vb, zi), bj = sub(zj, zi);
-        const df3 da = df3_from(ba.x, ba.y, ba.z), db = df3_from(bb.x, bb.y, bb.z), dj = df3_from(bj.x, bj.y, bj.z);
+        const V3 ba = sub(va, zi), bb = sub(vb, zi);
+        const df3 da = df3_from(ba.x, ba.y, ba.z), db = df3_from(bb.x, bb.y, bb.z);
+        const float4 hp = g.zf[p], lp = g.zl[p], llp = g.zll[p];
+        const df3 dj = gen_diff(g, cb.nb[(size_t)p * kCellSlots + k], hp, lp, llp);
         const float r2 = fmaxf(fmaxf(da.x.hi * da.x.hi + da.y.hi * da.y.hi + da.z.hi * da.z.hi,
                                      db.x.hi * db.x.hi + db.y.hi * db.y.hi + db.z.hi * db.z.hi),
                                0.25f * (dj.x.hi * dj.x.hi + dj.y.hi * dj.y.hi + dj.z.hi * dj.z.hi));
         if (r2 <= 0.9e-3f && (rho.kind < 2 || K > 0)) {
-            const df3 A{df{g.zf[p].x, g.zl[p].x}, df{g.zf[p].y, g.zl[p].y}, df{g.zf[p].z, g.zl[p].z}};
-            const df aA1 = df_from(dot(zi, zi) - 1.0);
+            const df3 A{df{hp.x, lp.x}, df{hp.y, lp.y}, df{hp.z, lp.z}};
+            const df aA1{llp.w, 0.0f};
             const DensDF dd = g.rho ? dens_df(rho) : dd0;
             const df eA = df3_dot(dd.ev, A);
             const df u0 = (K > 0) ? df_from(dot(mk(rho.xc0, rho.xc1, rho.xc2), zi) - ser[kSerMax]) : df{0.0f, 0.0f};
@@ -1860,7 +1955,7 @@ __global__ void __launch_bounds__(512) k_quad(Grid g, CellBuf cb, int ecap, Span
             ea[4 * (size_t)ecap + e] = df_to(ad.e);
             continue;
         }
-        const V3 mu = unit(add(zi, zj));
+        const V3 mu = unit(add(zi, ld(g.zs + cb.nb[(size_t)p * kCellSlots + k])));
         const double inv_alpha = (K > 0 || rho.kind < 2) ? 0.0 : 1.0 / rho.alpha;  // direct tanh cap only
         Acc acc = {0, 0, 0, 0, 0};
         if (g.fan) {
@@ -2090,7 +2185,7 @@ __global__ void __launch_bounds__(256) k_cell_sum(Grid g, CellOut out, CellBuf c
 }  // namespace
 
 void bin_points(const double *z, const Grid &g, int *bin_of, int *count, int *start, int *cursor, int *scan_tmp,
-                P4 *zs, float4 *zf, float4 *zl, int *sidx, const float *hint, DevStatus *st, cudaStream_t s,
+                P4 *zs, float4 *zf, float4 *zl, float4 *zll, int *sidx, const float *hint, DevStatus *st, cudaStream_t s,
                 int64_t *launches) {
     const int n = g.n, nbins = g.nbins;
     Grid gb = g;
@@ -2103,7 +2198,8 @@ void bin_points(const double *z, const Grid &g, int *bin_of, int *count, int *st
     cudaMemcpyAsync(cursor, start, sizeof(int) * nbins, cudaMemcpyDeviceToDevice, s);
     k_bin_scatter<<<blocks, 256, 0, s>>>(z, n, bin_of, cursor, zs, zf, zl, sidx, hint);
     k_bin_sort<<<(nbins + 255) / 256, 256, 0, s>>>(start, nbins, zs, zf, zl, sidx);
-    (*launches) += 4;
+    if (zll) k_bin_fine<<<blocks, 256, 0, s>>>(zs, zf, zl, zll, n);
+    (*launches) += zll ? 5 : 4;
 }
 
 

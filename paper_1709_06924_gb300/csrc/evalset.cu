@@ -49,6 +49,7 @@ Grid make_grid(const EvalSet &E) {
     g.zs = E.zs;
     g.zf = E.zf;
     g.zl = E.zl;
+    g.zll = E.zll;
     g.sidx = E.sidx;
     g.bstart = E.start;
     g.inst = E.d_inst;
@@ -66,7 +67,7 @@ void enqueue_eval(EvalSet &E, int64_t *launches, int64_t *cell_launches) {
     cudaMemsetAsync(E.d_st, 0, sizeof(DevStatus), s);
     cudaMemsetAsync(E.d_ist, 0, sizeof(DevStatus) * E.B, s);
     Grid g = make_grid(E);
-    bin_points(E.zt, g, E.bin_of, E.count, E.start, E.cursor, E.scan_tmp, E.zs, E.zf, E.zl, E.sidx, E.radius, E.d_st,
+    bin_points(E.zt, g, E.bin_of, E.count, E.start, E.cursor, E.scan_tmp, E.zs, E.zf, E.zl, E.precision == 0 ? E.zll : nullptr, E.sidx, E.radius, E.d_st,
                s, launches);
     CellOut out;
     memset(&out, 0, sizeof(out));
@@ -149,7 +150,7 @@ scvt_status status_of_flags(unsigned f) {
 int64_t evalset_bytes(int64_t cap_n, int cap_b, int precision) {
     const int64_t N = cap_n, nb = (int64_t)max_bins(cap_n, cap_b);
     int64_t per_row = 24 * 2 + 8 * 4 + 4      // zt, gt, q; ht, fc, nrm, (pinst); radius
-                      + 32 + 32 + 16 * 32 + 16 * 4 + 4 + 4 + 24 + 240  // zs, zf+zl, cvx, cnb, cdeg, eoff, ecell, eacc
+                      + 32 + 48 + 16 * 32 + 16 * 4 + 4 + 4 + 24 + 240  // zs, zf+zl+zll, cvx, cnb, cdeg, eoff, ecell, eacc
                       + 4 * 4;                // bin_of, sidx, list1, list2
     if (precision == 1) per_row += 16 * 16;   // vo
     else per_row += kSerWords * 8 + 4;       // density series
@@ -170,7 +171,7 @@ cudaError_t evalset_alloc(EvalSet &E, int64_t cap_n, int cap_b, int precision, c
     AL(E.d_rho, cap_b); AL(E.d_rhof, cap_b); AL(E.d_ist, cap_b); AL(E.d_st, 1);
     AL(E.zt, n3); AL(E.gt, n3); AL(E.ht, N); AL(E.fc, N); AL(E.q, n3); AL(E.nrm, N); AL(E.radius, N);
     AL(E.partials, E.partials_len);
-    AL(E.zs, N); AL(E.zf, N); AL(E.zl, N); AL(E.cvx, N * kCellSlots); AL(E.cnb, N * kCellSlots);
+    AL(E.zs, N); AL(E.zf, N); AL(E.zl, N); AL(E.zll, N); AL(E.cvx, N * kCellSlots); AL(E.cnb, N * kCellSlots);
     AL(E.cdeg, N); AL(E.eoff, N + 1); AL(E.ecell, 6 * N); AL(E.escan, scan_tmp_ints(N));
     AL(E.eacc, 5 * 6 * N);
     if (precision == 1) AL(E.vo, N * kCellSlots);
@@ -193,7 +194,7 @@ void evalset_free(EvalSet &E) {
     if (E.graph) cudaGraphExecDestroy(E.graph);
     E.graph = nullptr;
     void *ptrs[] = {E.d_inst, E.d_pinst, E.d_pbase, E.d_active, E.d_rho, E.d_rhof, E.d_ist, E.d_st, E.zt, E.gt,
-                    E.ht, E.fc, E.q, E.nrm, E.radius, E.partials, E.zs, E.zf, E.zl, E.cvx, E.cnb, E.cdeg, E.eoff,
+                    E.ht, E.fc, E.q, E.nrm, E.radius, E.partials, E.zs, E.zf, E.zl, E.zll, E.cvx, E.cnb, E.cdeg, E.eoff,
                     E.ecell, E.escan, E.eacc, E.vo, E.ser, E.serK, E.bin_of, E.count, E.start, E.cursor, E.scan_tmp, E.sidx,
                     E.list1, E.list2};
     for (void *p : ptrs)

@@ -91,6 +91,8 @@ struct Grid {
     const P4 *zs;           // generators in bin order (w unused)
     const float4 *zf;       // the same, rounded to FP32 (hi part); w = search-radius hint (0 = none)
     const float4 *zl;       // FP32 remainder z - hi (lo part): hi + lo carries ~48 bits
+    const float4 *zll;      // the third part z - hi - lo (hi + lo + ll == z exactly) and, in w,
+                            // |z|^2 - 1 from exact products and sums, rounded to FP32
     const int *sidx;        // bin-order position -> original index
     const int *bstart;      // nbins + 1 offsets into zs
     Density rho0;           // density of a single problem
@@ -145,7 +147,7 @@ struct CellBuf {
 // zl, sidx and bstart (= start) are written here.  hint (nullable): search
 // radius per original index, carried into zf[].w
 void bin_points(const double *z, const Grid &g, int *bin_of, int *count, int *start, int *cursor, int *scan_tmp,
-                P4 *zs, float4 *zf, float4 *zl, int *sidx, const float *hint, DevStatus *st, cudaStream_t s,
+                P4 *zs, float4 *zf, float4 *zl, float4 *zll, int *sidx, const float *hint, DevStatus *st, cudaStream_t s,
                 int64_t *launches);
 
 // Launch shape and search parameters of an evaluation.  None of them changes

@@ -53,7 +53,8 @@ constexpr size_t oCdeg = oList2 + up(sizeof(int) * kMaxN);
 constexpr size_t oZs = oCdeg + up(sizeof(int) * kMaxN);
 constexpr size_t oZf = oZs + up(sizeof(P4) * kMaxN);
 constexpr size_t oZl = oZf + up(sizeof(float4) * kMaxN);
-constexpr size_t oCvx = oZl + up(sizeof(float4) * kMaxN);
+constexpr size_t oZll = oZl + up(sizeof(float4) * kMaxN);
+constexpr size_t oCvx = oZll + up(sizeof(float4) * kMaxN);
 constexpr size_t oCnb = oCvx + up(sizeof(P4) * kMaxN * kCellSlots);
 constexpr size_t oFc = oCnb + up(sizeof(int) * kMaxN * kCellSlots);
 constexpr size_t oH = oFc + up(sizeof(double) * kMaxN);
@@ -133,6 +134,7 @@ extern "C" scvt_status scvt_energy_grad_static(int64_t n, const scvt_density *rh
     P4 *zs = (P4 *)(base + oZs);
     float4 *zf = (float4 *)(base + oZf);
     float4 *zl = (float4 *)(base + oZl);
+    float4 *zll = (float4 *)(base + oZll);
     P4 *cvx = (P4 *)(base + oCvx);
     int *cnb = (int *)(base + oCnb);
     double *fc = (double *)(base + oFc), *hd = (double *)(base + oH);
@@ -151,11 +153,12 @@ extern "C" scvt_status scvt_energy_grad_static(int64_t n, const scvt_density *rh
     grid.zs = zs;
     grid.zf = zf;
     grid.zl = zl;
+    grid.zll = zll;
     grid.sidx = sidx;
     grid.bstart = start;
     grid.rho0 = to_device_density(*rho);
     grid.rho0f = to_density32(grid.rho0);
-    bin_points(z, grid, bin_of, count, start, cursor, scan_tmp, zs, zf, zl, sidx, nullptr, st, s, &launches);
+    bin_points(z, grid, bin_of, count, start, cursor, scan_tmp, zs, zf, zl, zll, sidx, nullptr, st, s, &launches);
     CellOut out;
     out.grad = g;
     out.hdiag = hd;
