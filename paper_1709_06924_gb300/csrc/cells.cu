@@ -1648,22 +1648,28 @@ __device__ void series_of_cell(const Grid &g, const CellBuf &cb, int p, double *
     const double ci = dot(xc, zi);
     const double si = sqrt(dot(crs(xc, zi), crs(xc, zi)));
     const double inv_alpha = 1.0 / r.alpha;
-    // the range of u over the cell
-    double umax = 0.0, umin = 0.0, h2 = 0.0;
+    // the range of u over the cell, in FP32 from offsets (a bound only: the
+    // FP32 errors, ~1e-7, are covered by the 5 % and the 1e-6 below): u =
+    // x_c.(v - z_i) at the corners and x_c.(z_j - z_i) / 2 at the edge
+    // midpoints, whose radial part (<= |c_i| |z_j - z_i|^2 / 8) the |c_i| h^2
+    // term covers with the rule points' between them
+    const float3 xf = make_float3((float)r.xc0, (float)r.xc1, (float)r.xc2);
+    const float4 hp = g.zf[p];
+    float umax = 0.0f, umin = 0.0f, h2 = 0.0f;
     int kmax = 0, kmin = 0;
     for (int k = 0; k < deg; ++k) {
-        const V3 v = ld(cb.vx + (size_t)p * kCellSlots + k);
-        const double u = dot(xc, v) - ci;
+        const P4 v = cb.vx[(size_t)p * kCellSlots + k];
+        const float dx = (float)v.x - hp.x, dy = (float)v.y - hp.y, dz = (float)v.z - hp.z;
+        const float u = xf.x * dx + xf.y * dy + xf.z * dz;
         if (u > umax) { umax = u; kmax = k; }
         if (u < umin) { umin = u; kmin = k; }
-        const V3 dv = sub(v, zi);
-        h2 = fmax(h2, dot(dv, dv));
-        const V3 sm = add(zi, ld(g.zs + cb.nb[(size_t)p * kCellSlots + k]));
-        const double um = dot(xc, sm) * rsqrt(dot(sm, sm)) - ci;  // the edge midpoint
-        umax = fmax(umax, um);
-        umin = fmin(umin, um);
+        h2 = fmaxf(h2, dx * dx + dy * dy + dz * dz);
+        const float4 hq = g.zf[cb.nb[(size_t)p * kCellSlots + k]];
+        const float um = 0.5f * (xf.x * (hq.x - hp.x) + xf.y * (hq.y - hp.y) + xf.z * (hq.z - hp.z));
+        umax = fmaxf(umax, um);
+        umin = fminf(umin, um);
     }
-    const double U = 1.05 * fmax(umax, -umin) + fabs(ci) * h2;
+    const double U = 1.05 * (double)fmaxf(umax, -umin) + fabs(ci) * (double)h2 + 1e-6;
     int K = 0;
     double cf[kSerMax + 1];
     if (si > 1e-6) {
