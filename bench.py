@@ -436,9 +436,13 @@ def run_ours(args, w):
 
     # warm-up: W LBFGS iterations from the seeded start (history is kept);
     # then the library's autotuner picks launch shapes at the warmed iterate,
-    # the state the timed steps run in (results do not depend on them)
+    # the state the timed steps run in (a fixed --tuning applies from the
+    # start; results do not depend on either)
+    if args.tuning:
+        tuning = {prec: pick_tuning(args, eng, z)}
     eng.lbfgs_solve(z, max_iter=args.warmup, grad_tol=0.0)
-    tuning = {prec: pick_tuning(args, eng, z)}
+    if not args.tuning:
+        tuning = {prec: pick_tuning(args, eng, z)}
     eng.reset_stats()
     eng.set_profiling(True)
     try:
@@ -463,7 +467,7 @@ def run_ours(args, w):
     # are timed on three further evaluations of the same iterate with one
     # pipeline
     quad_ms, topo_ms, stq = one_pipeline_kernel_ms(eng, z)
-    roofline = roofline_of(prec, w, quad_ms, topo_ms, stq)
+    roofline = roofline_of(prec, w, quad_ms, topo_ms, stq, tuning[prec]["topo_cell_lanes"])
 
     # end to end through the C ABI with host buffers: a second engine replays
     # the same warm-up (evaluations are deterministic, so it reaches the same
@@ -503,8 +507,11 @@ def run_ours(args, w):
         oprec = 1 - prec
         eng3 = Engine(w.n, w.density, lbfgs_m=w.lbfgs_m, device=local, precision=oprec)
         z3 = torch.from_numpy(z_host).cuda(local)
+        if args.tuning:
+            tuning[oprec] = pick_tuning(args, eng3, z3)
         eng3.lbfgs_solve(z3, max_iter=args.warmup, grad_tol=0.0)
-        tuning[oprec] = pick_tuning(args, eng3, z3)
+        if not args.tuning:
+            tuning[oprec] = pick_tuning(args, eng3, z3)
         eng3.reset_stats()
         eng3.set_profiling(True)
         torch.cuda.synchronize()
@@ -515,7 +522,7 @@ def run_ours(args, w):
         u3, t3 = combine_ranks(w.n * rep3["iters"], t3, device=torch.device("cuda", local))
         other = {"precision": "mixed" if oprec else "fp64", "dtype": "f32/f64" if oprec else "f64+f32x2",
                  "value": u3 / t3, "ms_per_step": 1e3 * t3 / max(rep3["iters"], 1),
-                 "roofline": roofline_of(oprec, w, q3, tp3, stq3),
+                 "roofline": roofline_of(oprec, w, q3, tp3, stq3, tuning[oprec]["topo_cell_lanes"]),
                  "eval_ms_avg": st3["eval_ms"] / max(st3["evaluations"], 1), "tuning": tuning[oprec]}
 
     batched = None
@@ -634,12 +641,13 @@ def fp64_peak_tflops() -> float:
 # Instruction issue is what bounds the double-float quadrature and the
 # topology pass: each of the 152 SMs' four schedulers issues at most one warp
 # instruction per clock (2.07 GHz), 1.2586e12 warp instructions per second.
-# The work per unit is the instruction count ncu measured for one launch at
-# N = 163,842 (smsp__inst_executed.sum / units; profiles/k_quad_tanh_163842.md,
-# profiles/k_topo_warp_tanh_163842.md).
+# The work per unit is the instruction count ncu measured (one-pass
+# smsp__inst_executed.sum) for a launch of the timed steps of this bench at
+# N = 2,621,442, divided by N (profiles/launches_tanh_2621442.md); the
+# topology pass's count depends on its lanes per cell.
 ISSUE_PEAK = 152 * 4 * 2.07e9
-QUAD_INST_PER_GENERATOR = 330606408 / 163842
-TOPO_INST_PER_CELL = 277051660 / 163842
+QUAD_INST_PER_GENERATOR = 4740408363 / 2621442
+TOPO_INST_PER_CELL = {32: 3686138734 / 2621442, 16: 2145689134 / 2621442}
 
 
 def one_pipeline_kernel_ms(eng, z, evals=3):
@@ -660,7 +668,7 @@ def one_pipeline_kernel_ms(eng, z, evals=3):
     return quad, topo, st
 
 
-def roofline_of(prec, w, quad_ms, topo_ms, st):
+def roofline_of(prec, w, quad_ms, topo_ms, st, lanes=32):
     """Roofline of the step's dominant kernel: the double-float quadrature in
     the FP64 form, the topology pass in the mixed form; both issue-bound."""
     if prec == 0:
@@ -676,23 +684,26 @@ def roofline_of(prec, w, quad_ms, topo_ms, st):
                 "fp64_pipe_peak_tflops": fp64_peak_tflops(),
                 "series_cell_fraction": sfrac, "series_terms_avg": slen,
                 "peak_source": "instruction issue: 152 SMs x 4 schedulers x 1 warp-instruction/clk x 2.07 GHz",
-                "work_source": "ncu smsp__inst_executed.sum of one k_quad launch at N = 163,842 per generator "
-                               "(double-float arithmetic: FP32 pairs, FP64 only for per-edge offsets)",
+                "work_source": "ncu smsp__inst_executed.sum of a k_quad launch of the timed steps at "
+                               "N = 2,621,442, per generator (double-float arithmetic: FP32 pairs, FP64 for "
+                               "per-edge offsets)",
                 "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_quad launch "
                                   "at N = 163,842, scaled by N (profiles/k_quad_tanh_163842.md)"}
-    achieved = w.n * TOPO_INST_PER_CELL / (topo_ms * 1e-3) / 1e12
+    ipc = TOPO_INST_PER_CELL[lanes]
+    achieved = w.n * ipc / (topo_ms * 1e-3) / 1e12
     return {"bound": "alu", "kernel": "k_topo_warp", "achieved": achieved, "peak": ISSUE_PEAK / 1e12,
             "unit": "Twarp-inst/s", "frac": achieved * 1e12 / ISSUE_PEAK, "traffic": None,
-            "avg_launch_ms": topo_ms, "quad_kernel_ms": quad_ms, "inst_per_cell": TOPO_INST_PER_CELL,
+            "avg_launch_ms": topo_ms, "quad_kernel_ms": quad_ms, "inst_per_cell": ipc, "lanes_per_cell": lanes,
             "peak_source": "instruction issue: 152 SMs x 4 schedulers x 1 warp-instruction/clk x 2.07 GHz",
-            "work_source": "ncu smsp__inst_executed.sum of one k_topo_warp launch at N = 163,842 per cell"}
+            "work_source": "ncu smsp__inst_executed.sum of a k_topo_warp launch of the timed steps at "
+                           "N = 2,621,442, per cell"}
 
 
 def quad_traffic_bytes(n: int):
-    """DRAM bytes of one k_quad launch: ncu at N = 163,842 (115.63 MB read +
-    18.54 MB written, tanh cap, density series on), scaled by the number of
+    """DRAM bytes of one k_quad launch: ncu at N = 163,842 (118.31 MB read +
+    19.11 MB written, tanh cap, density series on), scaled by the number of
     generators."""
-    return (115.627520e6 + 18.537984e6) * n / 163842
+    return (118.309376e6 + 19.114240e6) * n / 163842
 
 
 def main():

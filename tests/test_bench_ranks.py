@@ -61,7 +61,7 @@ def test_roofline_of_both_forms():
     w = I.WORKLOADS["tanh-2621442"]
     st = {"series_cells": w.n * 3, "series_terms": w.n * 3 * 5, "evaluations": 3}
     r0 = bench.roofline_of(0, w, 5.0, 4.0, st)
-    r1 = bench.roofline_of(1, w, 1.0, 4.0, st)
+    r1 = bench.roofline_of(1, w, 1.0, 4.0, st, 16)
     for r, ms in ((r0, 5.0), (r1, 4.0)):
         assert r["bound"] == "alu" and r["unit"] == "Twarp-inst/s"
         assert abs(r["peak"] - 152 * 4 * 2.07e9 / 1e12) < 1e-12
