@@ -594,6 +594,8 @@ def run_ours(args, w):
             "ambiguous": st["ambiguous"],
             "eval_ms_avg": st["eval_ms"] / max(st["evaluations"], 1),
             "lbfgs_ms_total": st["lbfgs_ms"],
+            "fevals_per_s": st["evaluations"] / t_max if t_max > 0 else None,
+            "roofline_two_loop": two_loop_roofline(w, args.warmup, iters, st["lbfgs_ms"]),
         }
         print(json.dumps(line), flush=True)
     eng.close()
@@ -632,6 +634,36 @@ def fp64_flops_per_generator(kind: int, series_frac: float = 0.0, series_len: fl
     subtri = 38.0 + atan2 + 7 * point
     mu = 11.0 + rsqrt
     return 6.0 * (2 * subtri + mu)
+
+
+def measured_hbm_gbs():
+    """HBM copy bandwidth measured on this machine (MEASURED_PEAKS.json), else
+    the fallback figure."""
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def two_loop_roofline(w, warmup, iters, lbfgs_ms):
+    """HBM roofline of the two-loop recursion (Sec. 2.2.2 with diag(h) as the
+    initial inverse Hessian): algorithmic traffic per generator (4c + 2) x 24
+    bytes with c stored pairs (each history vector read twice, g read, q
+    written), c = min(warm-up + i, m) in timed iteration i, over the CUDA-event
+    time of the two-loop launches in the timed steps.  The fused kernels read
+    and write q once per pair step, 72 + 192 c bytes per generator."""
+    if not iters or lbfgs_ms <= 0:
+        return None
+    counts = [min(warmup + i, w.lbfgs_m) for i in range(iters)]
+    alg = sum((4 * c + 2) * 24 for c in counts) * w.n
+    impl = sum(72 + 192 * c for c in counts) * w.n
+    peak, src = measured_hbm_gbs()
+    achieved = alg / (lbfgs_ms * 1e-3) / 1e9
+    return {"bound": "hbm", "kernel": "two-loop (k_neg, k_axpy, k_finish_scalar)", "achieved": achieved,
+            "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+            "algorithmic_bytes": alg, "implementation_bytes": impl,
+            "implementation_gbs": impl / (lbfgs_ms * 1e-3) / 1e9, "peak_source": src, "pairs_per_iteration": counts}
 
 
 def fp64_peak_tflops() -> float:

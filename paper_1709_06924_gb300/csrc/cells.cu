@@ -1147,16 +1147,18 @@ __global__ void __launch_bounds__(WPB * 32, 24 / WPB) k_topo_warp(Grid g, CellOu
                 continue;
             }
             bool early = false, fast = false;
-            if (cnt + 4 <= L) {
-                // ---- all lines at once: lane l holds line l (candidates, then the
-                // square) and proposes the piece of it inside every other line, the
-                // lines bounding that piece at its two ends being its polygon
+            if (cnt <= L) {
+                // ---- all lines at once: lane l holds candidate l's line and
+                // proposes the piece of it inside every other line, the lines
+                // bounding that piece at its two ends being its polygon
                 // neighbours.  The proposal is then certified with the clipping
                 // test's own FP32 filter: every proposed vertex well conditioned and
                 // strictly inside every other line, the neighbour links one
-                // counter-clockwise cycle.  Then it is the exact cell; otherwise the
-                // cell is clipped one candidate at a time below.
-                const int nl = cnt + 4;
+                // counter-clockwise cycle.  Then it is the exact cell.  A
+                // polygon the candidates leave open has lines with an unbounded
+                // piece, which breaks the cycle; such cells, like any other that
+                // fails, are clipped one candidate at a time from the square below.
+                const int nl = cnt;
                 float fa = 0.0f, fb = 0.0f, fc = 0.0f;
                 int gen = 0;
                 if (sl < cnt) {
@@ -1165,12 +1167,6 @@ __global__ void __launch_bounds__(WPB * 32, 24 / WPB) k_topo_warp(Grid g, CellOu
                     fa = e1.x * d.x + e1.y * d.y + e1.z * d.z;
                     fb = e2.x * d.x + e2.y * d.y + e2.z * d.z;
                     fc = 0.5f * fmaf(d.x, d.x, fmaf(d.y, d.y, d.z * d.z));
-                } else if (sl < nl) {
-                    const int k = sl - cnt;  // right, top, left, bottom
-                    fa = (k == 0) ? 1.0f : ((k == 2) ? -1.0f : 0.0f);
-                    fb = (k == 1) ? 1.0f : ((k == 3) ? -1.0f : 0.0f);
-                    fc = (float)kBoxL;
-                    gen = -1 - k;
                 }
                 ln[sl] = make_float4(fa, fb, fc, 0.0f);
                 __syncwarp(smask);

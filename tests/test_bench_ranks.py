@@ -75,3 +75,14 @@ def test_parse_tuning():
     import bench
     assert bench.parse_tuning("") == {}
     assert bench.parse_tuning("chunks=4, bin_load=8") == {"chunks": 4, "bin_load": 8}
+
+
+def test_two_loop_roofline():
+    import bench
+    from paper_1709_06924_gb300 import inputs as I
+    w = I.WORKLOADS["tanh-2621442"]
+    r = bench.two_loop_roofline(w, 3, 5, 4.0)
+    assert r["bound"] == "hbm" and r["pairs_per_iteration"] == [3, 4, 5, 6, 7]
+    assert r["algorithmic_bytes"] == sum((4 * c + 2) * 24 for c in (3, 4, 5, 6, 7)) * w.n
+    assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-12
+    assert bench.two_loop_roofline(w, 3, 0, 4.0) is None
