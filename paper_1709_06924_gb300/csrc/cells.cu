@@ -1096,7 +1096,7 @@ __global__ void __launch_bounds__(WPB * 32, 24 / WPB) k_topo_warp(Grid g, CellOu
         // polygon: sub-warp lane k < nv holds vertex k and its outgoing edge's line
         float vu = 0.0f, vw = 0.0f, la_o = 0.0f, lb_o = 0.0f, lc_o = 0.0f;
         int vill = 0, g_o = 0, g_i = 0;
-        for (int attempt = 0; attempt < 6 && ok && !certified; ++attempt) {
+        for (int attempt = 0; attempt < 8 && ok && !certified; ++attempt) {
             // ---- candidates within chord r (every one of them; the rest are farther than r)
             const float rs = r * (1.0f + 1e-5f) + 1e-7f;  // covers the FP32 centre
             const float S = rs * sqrtf(fmaxf(1.0f - 0.25f * rs * rs, 0.0f)) * (1.0f + 1e-5f);
@@ -1138,8 +1138,10 @@ __global__ void __launch_bounds__(WPB * 32, 24 / WPB) k_topo_warp(Grid g, CellOu
                 }
             }
             __syncwarp(smask);
-            if (cnt > C) {  // too many: a smaller cap (the bound stays r-based)
-                r *= 0.7f;
+            if (cnt > C) {
+                // too many: the cap that holds about 90 % of the slots (counts
+                // grow as r^2), at least halving r; the bound stays r-based
+                r *= fmaxf(0.5f, sqrtf(0.9f * (float)C / (float)cnt));
                 continue;
             }
             if (cnt < 3 && !all_mode && r < rwide) {
@@ -1431,10 +1433,12 @@ __global__ void __launch_bounds__(WPB * 32, 24 / WPB) k_topo_warp(Grid g, CellOu
             if (!certified) {
                 if (all_mode || r >= rwide) break;
                 // an open polygon says nothing of the cell's size: widen the cap; a
-                // closed one needs chord 2 sqrt(R2), but R2 of a polygon clipped by
-                // too few candidates overstates the cell, so grow at most twofold
+                // closed one needs chord 2 sqrt(R2) (taken with 2.5 % to spare, so
+                // that large cells' caps still fit the slots), but R2 of a polygon
+                // clipped by too few candidates overstates the cell, so grow at
+                // most twofold
                 r = boxed ? fminf(2.0f * r, rwide)
-                          : fminf(fmaxf(fminf(2.2f * sqrtf(R2), 2.0f * r), 1.25f * r), rwide);
+                          : fminf(fmaxf(fminf(2.05f * sqrtf(R2), 2.0f * r), 1.25f * r), rwide);
             }
         }
         if (!certified || nv > kCellSlots) {
