@@ -163,9 +163,25 @@ __global__ void k_bin_count(const double *__restrict__ z, Grid g, int *__restric
 // The FP32 copy carries the generator's search-radius hint (from the previous
 // evaluation, 0 = none) in its w component, so the topology pass reads it with
 // the coordinates instead of through the original index.
+// Third FP32 part of a point (z - hi - lo, exact: hi + lo + ll == z since
+// z - hi and then the remainder after lo are exact in FP64 and the last fits
+// in 24 bits) and |z|^2 - 1: the squares by the FMA form of TwoProduct,
+// their sum by TwoSum, so s - 1 plus the error terms is |z|^2 - 1 to ~1e-32.
+__device__ __forceinline__ float4 fine_parts(double x, double y, double w, float4 h, float4 l) {
+    const double rx = (x - (double)h.x) - (double)l.x, ry = (y - (double)h.y) - (double)l.y,
+                 rz = (w - (double)h.z) - (double)l.z;
+    const double px = x * x, py = y * y, pz = w * w;
+    const double ex = fma(x, x, -px), ey = fma(y, y, -py), ez = fma(w, w, -pz);
+    const double s1 = px + py, b1 = s1 - px, t1 = (px - (s1 - b1)) + (py - b1);
+    const double s2 = s1 + pz, b2 = s2 - s1, t2 = (s1 - (s2 - b2)) + (pz - b2);
+    const double eps = (s2 - 1.0) + ((t1 + t2) + (ex + ey + ez));
+    return make_float4((float)rx, (float)ry, (float)rz, (float)eps);
+}
+
 __global__ void k_bin_scatter(const double *__restrict__ z, int n, const int *__restrict__ bin_of,
                               int *__restrict__ cursor, P4 *__restrict__ zs, float4 *__restrict__ zf,
-                              float4 *__restrict__ zl, int *__restrict__ sidx, const float *__restrict__ hint) {
+                              float4 *__restrict__ zl, float4 *__restrict__ zll, int *__restrict__ sidx,
+                              const float *__restrict__ hint) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int pos = atomicAdd(&cursor[bin_of[i]], 1);
@@ -173,8 +189,11 @@ __global__ void k_bin_scatter(const double *__restrict__ z, int n, const int *__
     double x = z[3 * (size_t)i], y = z[3 * (size_t)i + 1], w = z[3 * (size_t)i + 2];
     zs[pos] = P4{x, y, w, 0.0};
     const float hx = (float)x, hy = (float)y, hw = (float)w;
-    zf[pos] = make_float4(hx, hy, hw, hint ? hint[i] : 0.0f);
-    zl[pos] = make_float4((float)(x - (double)hx), (float)(y - (double)hy), (float)(w - (double)hw), 0.0f);
+    const float4 h = make_float4(hx, hy, hw, hint ? hint[i] : 0.0f);
+    const float4 l = make_float4((float)(x - (double)hx), (float)(y - (double)hy), (float)(w - (double)hw), 0.0f);
+    zf[pos] = h;
+    zl[pos] = l;
+    if (zll) zll[pos] = fine_parts(x, y, w, h, l);
 }
 
 // Order each bin's generators by their coordinates (lexicographic x, y, z).
@@ -183,13 +202,13 @@ __global__ void k_bin_scatter(const double *__restrict__ z, int n, const int *__
 // the edge list of the quadrature and its reduction tree) is reproducible and
 // independent of the input order.  Bins hold a few generators: insertion sort.
 __global__ void k_bin_sort(const int *__restrict__ start, int nbins, P4 *__restrict__ zs, float4 *__restrict__ zf,
-                           float4 *__restrict__ zl, int *__restrict__ sidx) {
+                           float4 *__restrict__ zl, float4 *__restrict__ zll, int *__restrict__ sidx) {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nbins) return;
     const int p0 = start[b], p1 = start[b + 1];
     for (int p = p0 + 1; p < p1; ++p) {
         const P4 v = zs[p];
-        const float4 vf = zf[p], vl = zl[p];
+        const float4 vf = zf[p], vl = zl[p], vll = zll ? zll[p] : make_float4(0, 0, 0, 0);
         const int id = sidx[p];
         int q = p;
         while (q > p0) {
@@ -199,34 +218,16 @@ __global__ void k_bin_sort(const int *__restrict__ start, int nbins, P4 *__restr
             zs[q] = u;
             zf[q] = zf[q - 1];
             zl[q] = zl[q - 1];
+            if (zll) zll[q] = zll[q - 1];
             sidx[q] = sidx[q - 1];
             --q;
         }
         zs[q] = v;
         zf[q] = vf;
         zl[q] = vl;
+        if (zll) zll[q] = vll;
         sidx[q] = id;
     }
-}
-
-// Third FP32 part of each coordinate (z - hi - lo, exact: hi + lo + ll == z
-// since z - hi and then the remainder after lo are exact in FP64 and the last
-// fits in 24 bits) and |z|^2 - 1: the squares by the FMA form of TwoProduct,
-// their sum by TwoSum, so s - 1 plus the error terms is |z|^2 - 1 to ~1e-32.
-__global__ void k_bin_fine(const P4 *__restrict__ zs, const float4 *__restrict__ zf, const float4 *__restrict__ zl,
-                           float4 *__restrict__ zll, int n) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n) return;
-    const P4 v = zs[p];
-    const float4 h = zf[p], l = zl[p];
-    const double rx = (v.x - (double)h.x) - (double)l.x, ry = (v.y - (double)h.y) - (double)l.y,
-                 rz = (v.z - (double)h.z) - (double)l.z;
-    const double px = v.x * v.x, py = v.y * v.y, pz = v.z * v.z;
-    const double ex = fma(v.x, v.x, -px), ey = fma(v.y, v.y, -py), ez = fma(v.z, v.z, -pz);
-    const double s1 = px + py, b1 = s1 - px, t1 = (px - (s1 - b1)) + (py - b1);
-    const double s2 = s1 + pz, b2 = s2 - s1, t2 = (s1 - (s2 - b2)) + (pz - b2);
-    const double eps = (s2 - 1.0) + ((t1 + t2) + (ex + ey + ez));
-    zll[p] = make_float4((float)rx, (float)ry, (float)rz, (float)eps);
 }
 
 // exclusive scan of 2048-element tiles; writes tile totals
@@ -2202,10 +2203,9 @@ void bin_points(const double *z, const Grid &g, int *bin_of, int *count, int *st
     exclusive_scan(count, start, nbins, scan_tmp, s, launches);
     k_set_total<<<1, 1, 0, s>>>(start, nbins, n);
     cudaMemcpyAsync(cursor, start, sizeof(int) * nbins, cudaMemcpyDeviceToDevice, s);
-    k_bin_scatter<<<blocks, 256, 0, s>>>(z, n, bin_of, cursor, zs, zf, zl, sidx, hint);
-    k_bin_sort<<<(nbins + 255) / 256, 256, 0, s>>>(start, nbins, zs, zf, zl, sidx);
-    if (zll) k_bin_fine<<<blocks, 256, 0, s>>>(zs, zf, zl, zll, n);
-    (*launches) += zll ? 5 : 4;
+    k_bin_scatter<<<blocks, 256, 0, s>>>(z, n, bin_of, cursor, zs, zf, zl, zll, sidx, hint);
+    k_bin_sort<<<(nbins + 255) / 256, 256, 0, s>>>(start, nbins, zs, zf, zl, zll, sidx);
+    (*launches) += 4;
 }
 
 
