@@ -679,7 +679,7 @@ def fp64_peak_tflops() -> float:
 # topology pass's count depends on its lanes per cell.
 ISSUE_PEAK = 152 * 4 * 2.07e9
 QUAD_INST_PER_GENERATOR = 4740408363 / 2621442
-TOPO_INST_PER_CELL = {32: 3686138734 / 2621442, 16: 2145689134 / 2621442}
+TOPO_INST_PER_CELL = {32: 3153936979 / 2621442, 16: 1873542833 / 2621442}
 
 
 def one_pipeline_kernel_ms(eng, z, evals=3):
