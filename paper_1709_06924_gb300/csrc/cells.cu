@@ -896,7 +896,7 @@ __global__ void __launch_bounds__(128) k_topo(Grid g, CellOut out, CellBuf cb,
             // large cell: integrate here, edges in the canonical order
             cb.deg[p] = 0;
             const Density rho = g.rho ? g.rho[v.b] : g.rho0;
-            const double inv_alpha = 1.0 / rho.alpha;
+            const double inv_alpha = rho.inv_alpha;
             Acc acc = {0, 0, 0, 0, 0};
             V3 corners_first, va;
             for (int t2 = 0; t2 <= nv; ++t2) {
@@ -1648,7 +1648,7 @@ __device__ void series_of_cell(const Grid &g, const CellBuf &cb, int p, double *
     const V3 xc = mk(r.xc0, r.xc1, r.xc2);
     const double ci = dot(xc, zi);
     const double si = sqrt(dot(crs(xc, zi), crs(xc, zi)));
-    const double inv_alpha = 1.0 / r.alpha;
+    const double inv_alpha = r.inv_alpha;
     // the range of u over the cell, in FP32 from offsets (a bound only: the
     // FP32 errors, ~1e-7, are covered by the 5 % and the 1e-6 below): u =
     // x_c.(v - z_i) at the corners and x_c.(z_j - z_i) / 2 at the edge
@@ -1816,9 +1816,9 @@ __global__ void k_sum_counts(const unsigned *__restrict__ counts, int nch, DevSt
 //   e.q   = e.w + m (e.A + e.w)  (the density's argument: x_c.p - c_i = (x_c.z_i - c_i)
 //           + x_c.q for the tanh cap, p_z = A_z + e_z.q for X3)
 //   |q|^2 = |w|^2 + 2 m (|w|^2 + A.w) + m^2 |x|^2 = |p - z_i|^2
-// and sum wr q = b (S1 + T1) + c (S2 + T2) + A T0 with S = sums of wr (b1, b2),
-// T = sums of wr m (1, b1, b2), so wr p sums to z_i sum wr + sum wr q.  No
-// difference of nearby values is formed.  The signed area is 2 atan(t),
+// and sum wr q = b S1 + c S2 + A T0 with S1, S2 the sums of wr (1 + m) b1,
+// wr (1 + m) b2 and T0 that of wr m, so wr p sums to z_i sum wr + sum wr q.
+// No difference of nearby values is formed.  The signed area is 2 atan(t),
 // t = A.(b x c) / (4 + 3 (|A|^2 - 1) + 2 A.(b + c) + b.c) (Van Oosterom-Strackee
 // with B = A + b, C = A + c), atan(t) = t - t^3/3 to 1e-18 for the t <= 3e-4
 // of such triangles.  Per-edge mass, moment and energy match the FP64
@@ -1836,7 +1836,7 @@ __device__ __forceinline__ void tri_df(int kind, df g1, df gam, df3 A, df aA1, d
     const df den = df_add(df_add_f(df_mul_f(aA1, 3.0f), 4.0f), df_add(df_mul_f(df_add(Ab, Ac), 2.0f), bc));
     const df t = df_div(det, den);
     const df area = df_mul_f(df_add_f(t, -t.hi * t.hi * t.hi * (1.0f / 3.0f)), 2.0f);
-    df S0{0.0f, 0.0f}, S1{0.0f, 0.0f}, S2{0.0f, 0.0f}, T0{0.0f, 0.0f}, T1{0.0f, 0.0f}, T2{0.0f, 0.0f}, E{0.0f, 0.0f};
+    df S0{0.0f, 0.0f}, S1{0.0f, 0.0f}, S2{0.0f, 0.0f}, T0{0.0f, 0.0f}, E{0.0f, 0.0f};
 #pragma unroll 1
     for (int k = 0; k < 7; ++k) {
         const df b1{kQdf[k][0][0], kQdf[k][0][1]}, b2{kQdf[k][1][0], kQdf[k][1][1]}, W{kQdf[k][2][0], kQdf[k][2][1]};
@@ -1867,15 +1867,15 @@ __device__ __forceinline__ void tri_df(int kind, df g1, df gam, df3 A, df aA1, d
         // |q|^2 = |w|^2 + 2 m (|w|^2 + A.w) + m^2 - m^2 delta
         const df mwa = df_mul(m, df_add(ww, Aw)), msq = df_mul(m, m);
         const df e = df_add_f(df_add(df_add(ww, df{2.0f * mwa.hi, 2.0f * mwa.lo}), msq), -msq.hi * dl.hi);
+        // wr q = (wr + wm) w + wm A: sums of (wr + wm) b1, (wr + wm) b2 and wm
+        const df wp = df_add(wr, wm);
         S0 = df_add(S0, wr);
-        S1 = df_add(S1, df_mul(wr, b1));
-        S2 = df_add(S2, df_mul(wr, b2));
+        S1 = df_add(S1, df_mul(wp, b1));
+        S2 = df_add(S2, df_mul(wp, b2));
         T0 = df_add(T0, wm);
-        T1 = df_add(T1, df_mul(wm, b1));
-        T2 = df_add(T2, df_mul(wm, b2));
         E = df_add(E, df_mul(wr, e));
     }
-    const df a1 = df_add(S1, T1), a2 = df_add(S2, T2);
+    const df a1 = S1, a2 = S2;
     acc.m = df_add(acc.m, S0);
     acc.qx = df_add(acc.qx, df_add(df_add(df_mul(a1, b.x), df_mul(a2, c.x)), df_mul(T0, A.x)));
     acc.qy = df_add(acc.qy, df_add(df_add(df_mul(a1, b.y), df_mul(a2, c.y)), df_mul(T0, A.y)));
@@ -1963,7 +1963,7 @@ __global__ void __launch_bounds__(512) k_quad(Grid g, CellBuf cb, int ecap, Span
             continue;
         }
         const V3 mu = unit(add(zi, ld(g.zs + cb.nb[(size_t)p * kCellSlots + k])));
-        const double inv_alpha = (K > 0 || rho.kind < 2) ? 0.0 : 1.0 / rho.alpha;  // direct tanh cap only
+        const double inv_alpha = rho.inv_alpha;
         Acc acc = {0, 0, 0, 0, 0};
         if (g.fan) {
             tri(rho, inv_alpha, zi, va, vb, acc, ser, K);
@@ -2257,6 +2257,7 @@ Density to_device_density(const scvt_density &r) {
     d.xc0 = r.xc[0];
     d.xc1 = r.xc[1];
     d.xc2 = r.xc[2];
+    d.inv_alpha = 1.0 / r.alpha;
     return d;
 }
 

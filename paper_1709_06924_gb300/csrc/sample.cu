@@ -57,7 +57,7 @@ bool device_pointer(const void *p) {
 // centre for the tanh kinds)
 double rho_max(const Density &r) {
     if (r.kind == 0 || r.kind == 1) return 1.0;
-    const double inv_alpha = 1.0 / r.alpha;
+    const double inv_alpha = r.inv_alpha;
     double v = (1.0 - r.gamma) / (1.0 + exp(-2.0 * r.beta * inv_alpha)) + r.gamma;
     if (r.kind == 3) {
         v = v * v;

@@ -43,6 +43,7 @@ struct Density {
     int kind;
     double gamma, alpha, beta;
     double xc0, xc1, xc2;
+    double inv_alpha;  // 1 / alpha, divided once on the host
 };
 
 // the density in FP32 for the mixed-precision quadrature (inv_alpha = 1/alpha)
