@@ -678,7 +678,7 @@ def fp64_peak_tflops() -> float:
 # N = 2,621,442, divided by N (profiles/launches_tanh_2621442.md); the
 # topology pass's count depends on its lanes per cell.
 ISSUE_PEAK = 152 * 4 * 2.07e9
-QUAD_INST_PER_GENERATOR = 4740408363 / 2621442
+QUAD_INST_PER_GENERATOR = 4536632457 / 2621442
 TOPO_INST_PER_CELL = {32: 3153936979 / 2621442, 16: 1873542833 / 2621442}
 
 
