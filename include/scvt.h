@@ -40,7 +40,8 @@ typedef enum {
     SCVT_ERR_INVALID = 1,       /* bad argument: N < 4, non-finite or non-unit point (| |z|-1 | > 1e-12),
                                    duplicate points, null pointer, unsupported option */
     SCVT_ERR_DEGENERATE = 2,    /* origin not strictly inside the hull of Z (some cell leaves its
-                                   hemisphere), or c_i . z_i <= 0 */
+                                   hemisphere), c_i . z_i <= 0, or neighbouring cells that disagree
+                                   on a Voronoi vertex (four or more cocircular generators) */
     SCVT_ERR_OOM = 3,           /* device allocation failed */
     SCVT_ERR_CUDA = 4,          /* a CUDA runtime call failed */
     SCVT_ERR_KNN_EXHAUSTED = 5, /* a cell could not be certified (security radius) with any neighbour count */
@@ -72,10 +73,22 @@ typedef struct {
     int64_t n;          /* number of generators, >= 4 */
     scvt_density rho;
     int quad_points;    /* points per sub-triangle; 7 (Radon degree-5 rule) is the only value */
-    int precision;      /* 0 = FP64 throughout (parity mode).  1 = mixed: Voronoi corners and the
-                           quadrature in FP32 local coordinates (offsets from z_i), the
-                           near-degenerate clipping decisions, the sums over edges and cells
-                           and all LBFGS vectors in FP64; the topology is the FP64 mode's */
+    int precision;      /* Arithmetic of the geometry.  The topology (neighbour sets) is the same
+                           in every form: clipping decisions are filtered in FP32 and taken in
+                           FP64 where the filter cannot decide.  Sums over edges and cells and all
+                           LBFGS vectors are FP64 in every form.
+                           0 = FP64 form (parity mode): Voronoi corners and the rule points in
+                             double-float arithmetic (pairs of FP32 values, about 48 bits)
+                             relative to z_i, from FP64 offsets; corners that are poorly
+                             conditioned or far from z_i, and edges reaching beyond chord 0.03
+                             of z_i, in FP64; the tanh-cap density from an FP64 per-cell Taylor
+                             series (direct formula where the series is not validated).
+                             Results within 1e-12 (relative) of an FP64 evaluation.
+                           1 = mixed: corners and quadrature in FP32 local coordinates (offsets
+                             from z_i), density in FP32; error stated per quantity (about 1e-5
+                             relative for m_i, c_i and F_i).
+                           2 = plain FP64: corners, rule points and density in FP64 arithmetic
+                             (the density by the same FP64 series / direct formula as form 0). */
     int lbfgs_m;        /* number of (s, y) pairs kept, 0..32 (the paper uses 7) */
     int knn_k0;         /* first-pass neighbour count, 0 = default (32); 8..32 */
     int knn_kmax;       /* largest neighbour count of the retry passes, 0 = default (128) */
@@ -206,7 +219,9 @@ scvt_status scvt_lbfgs_direction(scvt_handle *h, const double *g, const double *
  * (N x 3), mass (N), moment (N x 3): device, nullable.  Host pointers for
  * z/grad/mass/moment are rejected (SCVT_ERR_INVALID).  Synchronises the
  * stream.  The first call on a device looks up the array's device address
- * with that device current; make it before any stream capture.  All calls
+ * with that device current and keeps it until the process exits; make that
+ * call before any stream capture, and do not call this entry point on a
+ * device after cudaDeviceReset (the kept address is then stale).  All calls
  * share the one array and it keeps the previous call's contents; each call
  * clears what must start at zero.  Calls whose GPU work overlaps (other
  * streams or host threads) race on the array: serialise them. */

@@ -174,6 +174,24 @@ def voronoi(z):
     return deg, [nbr[off[i]:off[i + 1]].copy() for i in range(n)], [vx[off[i]:off[i + 1]].copy() for i in range(n)]
 
 
+def voronoi_flat(z):
+    """Cells as (deg[n], off[n+1], neighbour ids of all cells end to end, each
+    cell's CCW cycle at off[i]:off[i+1]) -- the arrays of ``voronoi`` without
+    the per-cell lists, for comparisons at millions of cells."""
+    z = _f64(z)
+    n = z.shape[0]
+    cap = max(6 * n, 16)
+    deg = np.zeros(n, dtype=np.int32)
+    nbr = np.zeros(cap, dtype=np.int32)
+    vx = np.zeros((cap, 3), dtype=np.float64)
+    rc = lib().orc_voronoi(n, _p(z), deg.ctypes.data_as(_ip), nbr.ctypes.data_as(_ip), _p(vx), cap)
+    if rc != OK:
+        raise OracleError(rc, "voronoi")
+    off = np.zeros(n + 1, dtype=np.int64)
+    off[1:] = np.cumsum(deg)
+    return deg, off, nbr[:off[-1]].copy()
+
+
 def energy_grad(z, density, rule=None, exact_jacobian=False, nthreads=0, fan=False):
     """Evaluate the Sec. 3.1 quantities.  ``rule`` = (bary[nq,3], w[nq]) replaces
     the 7-point rule (weights summing to 1); ``exact_jacobian`` integrates with

@@ -81,7 +81,7 @@ scvt_status validate_config(const scvt_config &c) {
     if (c.n < 4 || c.n > (int64_t)200000000) return SCVT_ERR_INVALID;
     if (c.lbfgs_m < 0 || c.lbfgs_m > kLaneMaxM) return SCVT_ERR_INVALID;
     if (c.quad_points != 0 && c.quad_points != 7) return SCVT_ERR_INVALID;
-    if (c.precision != 0 && c.precision != 1) return SCVT_ERR_INVALID;
+    if (c.precision < 0 || c.precision > 2) return SCVT_ERR_INVALID;
     if (c.decomposition != 0 && c.decomposition != 1) return SCVT_ERR_INVALID;
     if (c.rho.kind < 0 || c.rho.kind > 3) return SCVT_ERR_INVALID;
     if (c.rho.kind != SCVT_RHO_UNIFORM) {

@@ -193,7 +193,7 @@ scvt_status evaluate_dev(scvt_handle *H, const double *zdev, double *grad, doubl
     cb.vo = B.vo;
     cb.ser = B.ser;
     cb.serK = B.serK;
-    cell_passes(g, out, cb, B.list1, B.list2, B.st, H->cfg.precision == 1, H->tune, s,
+    cell_passes(g, out, cb, B.list1, B.list2, B.st, H->cfg.precision, H->tune, s,
                 H->profiling ? H->ev_cell0 : nullptr, H->profiling ? H->ev_cell1 : nullptr, L,
                 &H->stats.cell_launches, &H->pipes, H->profiling ? H->ev_topo : nullptr);
     reduce_eval(n, fcell, grad, q, nrm, B.partials, B.st, s, L);
@@ -217,6 +217,8 @@ scvt_status evaluate_dev(scvt_handle *H, const double *zdev, double *grad, doubl
         return fail(H, SCVT_ERR_KNN_EXHAUSTED, "a Voronoi cell could not be certified by the security radius");
     if (st.flags & FLAG_VMAX) return fail(H, SCVT_ERR_KNN_EXHAUSTED, "a Voronoi cell has more than 64 vertices");
     if (st.flags & FLAG_NONPOSITIVE) return fail(H, SCVT_ERR_DEGENERATE, "a cell has c_i . z_i <= 0");
+    if (st.flags & FLAG_ECAP)
+        return fail(H, SCVT_ERR_DEGENERATE, "neighbouring cells disagree on a Voronoi vertex (cocircular generators)");
     if (F) *F = st.red[0];
     if (gn2) *gn2 = st.red[1];
     if (dphi) *dphi = st.red[2];
@@ -322,7 +324,7 @@ const char *scvt_status_string(scvt_status s) {
 
 const char *scvt_last_error(const scvt_handle *h) { return h ? h->err.c_str() : ""; }
 
-const char *scvt_version(void) { return "scvt-gb300 0.2 (sm_103a; FP64 parity mode, FP32/FP64 mixed mode)"; }
+const char *scvt_version(void) { return "scvt-gb300 0.3 (sm_103a; FP64 form (double-float rule points), mixed FP32/FP64 form, plain FP64 form)"; }
 
 void scvt_destroy(scvt_handle *H) {
     if (!H) return;
@@ -346,7 +348,7 @@ scvt_status scvt_create(const scvt_config *cfg, void *cuda_stream, scvt_handle *
     if (cfg->n < 4 || cfg->n > (int64_t)200000000) return SCVT_ERR_INVALID;
     if (cfg->lbfgs_m < 0 || cfg->lbfgs_m > kMaxM) return SCVT_ERR_INVALID;
     if (cfg->quad_points != 0 && cfg->quad_points != 7) return SCVT_ERR_INVALID;
-    if (cfg->precision != 0 && cfg->precision != 1) return SCVT_ERR_INVALID;
+    if (cfg->precision < 0 || cfg->precision > 2) return SCVT_ERR_INVALID;
     if (cfg->decomposition != 0 && cfg->decomposition != 1) return SCVT_ERR_INVALID;
     if (cfg->rho.kind < 0 || cfg->rho.kind > 3) return SCVT_ERR_INVALID;
     if (cfg->rho.kind != SCVT_RHO_UNIFORM) {
@@ -386,7 +388,7 @@ scvt_status scvt_create(const scvt_config *cfg, void *cuda_stream, scvt_handle *
     AL(b.cdeg, n); AL(b.eoff, n + 1); AL(b.ecell, 6 * (size_t)n); AL(b.escan, scan_tmp_ints(n));
     AL(b.eacc, 5 * 6 * (size_t)n);
     if (cfg->precision == 1) AL(b.vo, (size_t)n * kCellSlots);
-    if (cfg->precision == 0) { AL(b.ser, (size_t)n * kSerWords); AL(b.serK, n); }
+    if (cfg->precision != 1) { AL(b.ser, (size_t)n * kSerWords); AL(b.serK, n); }
     AL(b.bin_of, n); AL(b.count, nbins); AL(b.start, nbins + 1); AL(b.cursor, nbins);
     AL(b.scan_tmp, 2 * (nbins / 2048 + 64) + 64);
     AL(b.sidx, n); AL(b.list1, n); AL(b.list2, n); AL(b.deg, n); AL(b.radius, n);

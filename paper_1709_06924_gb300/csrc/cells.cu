@@ -1529,6 +1529,7 @@ __device__ __forceinline__ df inv_norm_m1(df dl) {
 // delta = -(|z_i|^2 - 1) - 2 z_i.(x - z_i) - |x - z_i|^2.  Corners farther
 // than chord 0.03 or poorly conditioned are solved in FP64 in the gnomonic
 // frame at z_i.
+template <bool PLAIN>
 __global__ void __launch_bounds__(256) k_corners(Grid g, CellBuf cb, Span sp) {
     const int ne = *sp.etot, eb = *sp.e0;
     for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < ne; it += gridDim.x * blockDim.x) {
@@ -1539,7 +1540,7 @@ __global__ void __launch_bounds__(256) k_corners(Grid g, CellBuf cb, Span sp) {
         const int *nb = cb.nb + (size_t)p * kCellSlots;
         const int ga = nb[(k == 0) ? deg - 1 : k - 1], gb = nb[k];
         const V3 zi = ld(g.zs + p);
-        {
+        if constexpr (!PLAIN) {
             const float4 hp = g.zf[p], lp = g.zl[p], llp = g.zll[p];
             float3 e1, e2;
             {
@@ -1762,12 +1763,14 @@ __device__ void series_of_cell(const Grid &g, const CellBuf &cb, int p, double *
 // -------------------------------------------------------------- quadrature
 // Edge list: cells' edges laid end to end in bin order (eoff = exclusive
 // scan of the degrees), ecell[e] = the cell of edge e.
+// Edges past the list's capacity ecap are dropped (k_rebase has flagged the
+// evaluation); a consistent tessellation has 6N - 12 < ecap edge sides.
 __global__ void k_edge_cells(int p0, int p1, const int *__restrict__ deg, const int *__restrict__ eoff,
-                             int *__restrict__ ecell) {
+                             int *__restrict__ ecell, int ecap) {
     int p = p0 + blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= p1) return;
     int d = deg[p], o = eoff[p];
-    for (int k = 0; k < d; ++k) ecell[o + k] = p;
+    for (int k = 0; k < d && o + k < ecap; ++k) ecell[o + k] = p;
 }
 
 // Chunk words (kChunkWords per chunk): retry counts of the three topology
@@ -1777,16 +1780,20 @@ enum { CW_R0 = 0, CW_R1 = 1, CW_R2 = 2, CW_ETOT = 3, CW_EBASE = 4 };
 
 // a chunk's exclusive scan of the degrees, moved to the chunk's first edge,
 // which follows the previous chunk's edges (prev: that chunk's words, null
-// for the first chunk); the last cell writes the chunk's edge count
+// for the first chunk); the last cell writes the chunk's edge count, cut to
+// the list's capacity ecap (FLAG_ECAP when cut: the edge kernels then stop
+// at the capacity and the evaluation reports the inconsistent cells)
 __global__ void k_rebase(int p0, int p1, const int *__restrict__ deg, int *__restrict__ eoff,
-                         const int *__restrict__ prev, int *__restrict__ mine) {
+                         const int *__restrict__ prev, int *__restrict__ mine, int ecap, unsigned *flags) {
     const int p = p0 + blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= p1) return;
     const int base = prev ? prev[CW_EBASE] + prev[CW_ETOT] : 0;
     const int local = eoff[p];
     eoff[p] = local + base;
     if (p == p1 - 1) {
-        mine[CW_ETOT] = local + deg[p];
+        const int tot = local + deg[p], room = ecap - base;
+        if (tot > room) atomicOr(flags, FLAG_ECAP);
+        mine[CW_ETOT] = tot > room ? (room > 0 ? room : 0) : tot;
         mine[CW_EBASE] = base;
     }
 }
@@ -1901,6 +1908,7 @@ __device__ __forceinline__ DensDF dens_df(const Density &r) {
     return d;
 }
 
+template <bool PLAIN>
 __global__ void __launch_bounds__(512) k_quad(Grid g, CellBuf cb, int ecap, Span sp) {
     const int ne = *sp.etot, eb = *sp.e0;
     const DensDF dd0 = dens_df(g.rho0);  // single-problem density, converted once
@@ -1921,46 +1929,48 @@ __global__ void __launch_bounds__(512) k_quad(Grid g, CellBuf cb, int ecap, Span
         // 0.03 (then delta <= 1e-3 at every rule point) and a density without
         // direct evaluation; otherwise FP64.  Offsets are FP64 differences of
         // nearby points (exact to 1e-16 of their size), rounded to pairs.
-        const V3 ba = sub(va, zi), bb = sub(vb, zi);
-        const df3 da = df3_from(ba.x, ba.y, ba.z), db = df3_from(bb.x, bb.y, bb.z);
-        const float4 hp = g.zf[p], lp = g.zl[p], llp = g.zll[p];
-        const df3 dj = gen_diff(g, cb.nb[(size_t)p * kCellSlots + k], hp, lp, llp);
-        const float r2 = fmaxf(fmaxf(da.x.hi * da.x.hi + da.y.hi * da.y.hi + da.z.hi * da.z.hi,
-                                     db.x.hi * db.x.hi + db.y.hi * db.y.hi + db.z.hi * db.z.hi),
-                               0.25f * (dj.x.hi * dj.x.hi + dj.y.hi * dj.y.hi + dj.z.hi * dj.z.hi));
-        if (r2 <= 0.9e-3f && (rho.kind < 2 || K > 0)) {
-            const df3 A{df{hp.x, lp.x}, df{hp.y, lp.y}, df{hp.z, lp.z}};
-            const df aA1{llp.w, 0.0f};
-            const DensDF dd = g.rho ? dens_df(rho) : dd0;
-            const df eA = df3_dot(dd.ev, A);
-            const df u0 = (K > 0) ? df_from(dot(mk(rho.xc0, rho.xc1, rho.xc2), zi) - ser[kSerMax]) : df{0.0f, 0.0f};
-            const float2 *sdf = reinterpret_cast<const float2 *>(ser + kSerMax + 1);
-            const float vs = (K > 0) ? (float)ser[2 * kSerMax + 1] : 1.0f;
-            // edge midpoint mu = (z_i + z_j) / |z_i + z_j|: with h = (z_j - z_i) / 2,
-            // mu - z_i = h + m (A + h), 1 - |A + h|^2 = -(|A|^2 - 1) - 2 A.h - |h|^2
-            const df3 hh{df{0.5f * dj.x.hi, 0.5f * dj.x.lo}, df{0.5f * dj.y.hi, 0.5f * dj.y.lo},
-                         df{0.5f * dj.z.hi, 0.5f * dj.z.lo}};
-            const df Ah = df3_dot(A, hh);
-            const df dl = df_neg(df_add(df_add(aA1, df{2.0f * Ah.hi, 2.0f * Ah.lo}), df3_dot(hh, hh)));
-            const df d2 = df_mul(dl, dl);
-            const float tail = d2.hi * dl.hi * (0.3125f + dl.hi * (0.2734375f + dl.hi * 0.24609375f));
-            const df mm = df_add_f(df_add(df{0.5f * dl.hi, 0.5f * dl.lo}, df_mul_f(d2, 0.375f)), tail);
-            const df3 dm{df_add(hh.x, df_mul(mm, df_add(A.x, hh.x))), df_add(hh.y, df_mul(mm, df_add(A.y, hh.y))),
-                         df_add(hh.z, df_mul(mm, df_add(A.z, hh.z)))};
-            AccDF ad{};
-            if (g.fan) {
-                tri_df(rho.kind, dd.g1, dd.gam, A, aA1, da, db, dd.ev, eA, u0, sdf, vs, K, ad);
-            } else {
-                tri_df(rho.kind, dd.g1, dd.gam, A, aA1, da, dm, dd.ev, eA, u0, sdf, vs, K, ad);
-                tri_df(rho.kind, dd.g1, dd.gam, A, aA1, dm, db, dd.ev, eA, u0, sdf, vs, K, ad);
+        if constexpr (!PLAIN) {
+            const V3 ba = sub(va, zi), bb = sub(vb, zi);
+            const df3 da = df3_from(ba.x, ba.y, ba.z), db = df3_from(bb.x, bb.y, bb.z);
+            const float4 hp = g.zf[p], lp = g.zl[p], llp = g.zll[p];
+            const df3 dj = gen_diff(g, cb.nb[(size_t)p * kCellSlots + k], hp, lp, llp);
+            const float r2 = fmaxf(fmaxf(da.x.hi * da.x.hi + da.y.hi * da.y.hi + da.z.hi * da.z.hi,
+                                         db.x.hi * db.x.hi + db.y.hi * db.y.hi + db.z.hi * db.z.hi),
+                                   0.25f * (dj.x.hi * dj.x.hi + dj.y.hi * dj.y.hi + dj.z.hi * dj.z.hi));
+            if (r2 <= 0.9e-3f && (rho.kind < 2 || K > 0)) {
+                const df3 A{df{hp.x, lp.x}, df{hp.y, lp.y}, df{hp.z, lp.z}};
+                const df aA1{llp.w, 0.0f};
+                const DensDF dd = g.rho ? dens_df(rho) : dd0;
+                const df eA = df3_dot(dd.ev, A);
+                const df u0 = (K > 0) ? df_from(dot(mk(rho.xc0, rho.xc1, rho.xc2), zi) - ser[kSerMax]) : df{0.0f, 0.0f};
+                const float2 *sdf = reinterpret_cast<const float2 *>(ser + kSerMax + 1);
+                const float vs = (K > 0) ? (float)ser[2 * kSerMax + 1] : 1.0f;
+                // edge midpoint mu = (z_i + z_j) / |z_i + z_j|: with h = (z_j - z_i) / 2,
+                // mu - z_i = h + m (A + h), 1 - |A + h|^2 = -(|A|^2 - 1) - 2 A.h - |h|^2
+                const df3 hh{df{0.5f * dj.x.hi, 0.5f * dj.x.lo}, df{0.5f * dj.y.hi, 0.5f * dj.y.lo},
+                             df{0.5f * dj.z.hi, 0.5f * dj.z.lo}};
+                const df Ah = df3_dot(A, hh);
+                const df dl = df_neg(df_add(df_add(aA1, df{2.0f * Ah.hi, 2.0f * Ah.lo}), df3_dot(hh, hh)));
+                const df d2 = df_mul(dl, dl);
+                const float tail = d2.hi * dl.hi * (0.3125f + dl.hi * (0.2734375f + dl.hi * 0.24609375f));
+                const df mm = df_add_f(df_add(df{0.5f * dl.hi, 0.5f * dl.lo}, df_mul_f(d2, 0.375f)), tail);
+                const df3 dm{df_add(hh.x, df_mul(mm, df_add(A.x, hh.x))), df_add(hh.y, df_mul(mm, df_add(A.y, hh.y))),
+                             df_add(hh.z, df_mul(mm, df_add(A.z, hh.z)))};
+                AccDF ad{};
+                if (g.fan) {
+                    tri_df(rho.kind, dd.g1, dd.gam, A, aA1, da, db, dd.ev, eA, u0, sdf, vs, K, ad);
+                } else {
+                    tri_df(rho.kind, dd.g1, dd.gam, A, aA1, da, dm, dd.ev, eA, u0, sdf, vs, K, ad);
+                    tri_df(rho.kind, dd.g1, dd.gam, A, aA1, dm, db, dd.ev, eA, u0, sdf, vs, K, ad);
+                }
+                const double m = df_to(ad.m);
+                ea[e] = m;
+                ea[(size_t)ecap + e] = fma(zi.x, m, df_to(ad.qx));
+                ea[2 * (size_t)ecap + e] = fma(zi.y, m, df_to(ad.qy));
+                ea[3 * (size_t)ecap + e] = fma(zi.z, m, df_to(ad.qz));
+                ea[4 * (size_t)ecap + e] = df_to(ad.e);
+                continue;
             }
-            const double m = df_to(ad.m);
-            ea[e] = m;
-            ea[(size_t)ecap + e] = fma(zi.x, m, df_to(ad.qx));
-            ea[2 * (size_t)ecap + e] = fma(zi.y, m, df_to(ad.qy));
-            ea[3 * (size_t)ecap + e] = fma(zi.z, m, df_to(ad.qz));
-            ea[4 * (size_t)ecap + e] = df_to(ad.e);
-            continue;
         }
         const V3 mu = unit(add(zi, ld(g.zs + cb.nb[(size_t)p * kCellSlots + k])));
         const double inv_alpha = rho.inv_alpha;
@@ -2161,6 +2171,7 @@ __global__ void __launch_bounds__(256) k_cell_sum(Grid g, CellOut out, CellBuf c
     const int deg = cb.deg[p];
     if (deg == 0) return;  // integrated by the topology kernel, failed, or inactive
     const int e0 = cb.eoff[p];
+    if (e0 + deg > ecap) return;  // past the edge list (FLAG_ECAP is set)
     Acc acc = {0, 0, 0, 0, 0};
     if (MIXED) {
         const float *ea = (const float *)cb.eacc;
@@ -2274,7 +2285,7 @@ DensityF to_density32(const Density &d) {
 }
 
 void cell_passes(const Grid &g, const CellOut &out, const CellBuf &cb, int *list1, int *list2, DevStatus *st,
-                 bool mixed, const Tune &t, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1, int64_t *launches,
+                 int precision, const Tune &t, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1, int64_t *launches,
                  int64_t *cell_launches, const Pipes *px, const cudaEvent_t *topo_ev) {
     // the cells are cut into nch chunks of consecutive bin positions, each run
     // through the whole pipeline on its own stream (the first on s); chunks
@@ -2322,28 +2333,32 @@ void cell_passes(const Grid &g, const CellOut &out, const CellBuf &cb, int *list
         // known once that chunk's count is, so the rebase waits for it
         exclusive_scan(cb.deg + p0, cb.eoff + p0, len, cb.scan_tmp + (size_t)c * scan_len, sc, launches);
         if (c > 0) cudaStreamWaitEvent(sc, px->rebased[c - 1], 0);
+        const int ecap = 6 * g.n;
         k_rebase<<<(len + 255) / 256, 256, 0, sc>>>(p0, p1, cb.deg, cb.eoff,
-                                                     c > 0 ? (const int *)(counts + kChunkWords * (c - 1)) : nullptr, cw);
+                                                     c > 0 ? (const int *)(counts + kChunkWords * (c - 1)) : nullptr, cw,
+                                                     ecap, &st->flags);
         if (c + 1 < nch) cudaEventRecord(px->rebased[c], sc);
-        k_edge_cells<<<(len + 255) / 256, 256, 0, sc>>>(p0, p1, cb.deg, cb.eoff, cb.ecell);
+        k_edge_cells<<<(len + 255) / 256, 256, 0, sc>>>(p0, p1, cb.deg, cb.eoff, cb.ecell, ecap);
         // the edge kernels loop over the chunk's edges (grid sized for about 6 per
         // cell; Euler: a full tessellation has 6N - 12 edge sides in all)
         const Span sp{p0, p1, cw + CW_EBASE, cw + CW_ETOT};
-        const int ecap = 6 * g.n;
         const unsigned eblocks = (unsigned)((6 * len + qb - 1) / qb);
         const unsigned e256 = (unsigned)((6 * len + 255) / 256);
         const unsigned cblocks = (unsigned)((len + 255) / 256);
-        if (mixed) {
+        if (precision == 1) {
             k_corners32<<<e256, 256, 0, sc>>>(g, cb, sp);
             if (timed && ev0) cudaEventRecord(ev0, sc);
             k_quad32<<<eblocks, qb, 0, sc>>>(g, cb, ecap, sp);
             if (timed && ev1) cudaEventRecord(ev1, sc);
             k_cell_sum<true><<<cblocks, 256, 0, sc>>>(g, out, cb, ecap, st, sp);
         } else {
-            k_corners<<<e256, 256, 0, sc>>>(g, cb, sp);
+            const bool plain = precision == 2;
+            if (plain) k_corners<true><<<e256, 256, 0, sc>>>(g, cb, sp);
+            else k_corners<false><<<e256, 256, 0, sc>>>(g, cb, sp);
             if (cb.serK) k_rho_series<<<(len + 127) / 128, 128, 0, sc>>>(g, cb, cb.ser, cb.serK, st, sp);
             if (timed && ev0) cudaEventRecord(ev0, sc);
-            k_quad<<<eblocks, qb, 0, sc>>>(g, cb, ecap, sp);
+            if (plain) k_quad<true><<<eblocks, qb, 0, sc>>>(g, cb, ecap, sp);
+            else k_quad<false><<<eblocks, qb, 0, sc>>>(g, cb, ecap, sp);
             if (timed && ev1) cudaEventRecord(ev1, sc);
             k_cell_sum<false><<<cblocks, 256, 0, sc>>>(g, out, cb, ecap, st, sp);
         }

@@ -86,7 +86,7 @@ void enqueue_eval(EvalSet &E, int64_t *launches, int64_t *cell_launches) {
     cb.vo = E.vo;
     cb.ser = E.ser;
     cb.serK = E.serK;
-    cell_passes(g, out, cb, E.list1, E.list2, E.d_st, E.precision == 1, E.tune, s, nullptr, nullptr, launches,
+    cell_passes(g, out, cb, E.list1, E.list2, E.d_st, E.precision, E.tune, s, nullptr, nullptr, launches,
                 cell_launches, &E.pipes);
     reduce_eval_batch(E.B, E.max_nb, E.d_inst, E.d_pbase, E.d_active, E.fc, E.gt, E.q, E.nrm, E.partials, E.d_ist, s,
                       launches);
@@ -143,7 +143,7 @@ scvt_status status_of_flags(unsigned f) {
     if (f & (FLAG_BAD_POINT | FLAG_DUPLICATE)) return SCVT_ERR_INVALID;
     if (f & (FLAG_UNBOUNDED | FLAG_EMPTY)) return SCVT_ERR_DEGENERATE;
     if (f & (FLAG_EXHAUSTED | FLAG_VMAX)) return SCVT_ERR_KNN_EXHAUSTED;
-    if (f & FLAG_NONPOSITIVE) return SCVT_ERR_DEGENERATE;
+    if (f & (FLAG_NONPOSITIVE | FLAG_ECAP)) return SCVT_ERR_DEGENERATE;
     return SCVT_OK;
 }
 
@@ -175,7 +175,7 @@ cudaError_t evalset_alloc(EvalSet &E, int64_t cap_n, int cap_b, int precision, c
     AL(E.cdeg, N); AL(E.eoff, N + 1); AL(E.ecell, 6 * N); AL(E.escan, scan_tmp_ints(N));
     AL(E.eacc, 5 * 6 * N);
     if (precision == 1) AL(E.vo, N * kCellSlots);
-    if (precision == 0) { AL(E.ser, N * kSerWords); AL(E.serK, N); }
+    if (precision != 1) { AL(E.ser, N * kSerWords); AL(E.serK, N); }
     AL(E.bin_of, N); AL(E.count, nb); AL(E.start, nb + 1); AL(E.cursor, nb); AL(E.scan_tmp, 2 * (nb / 2048 + 64) + 64);
     AL(E.sidx, N); AL(E.list1, N); AL(E.list2, N);
 #undef AL
@@ -257,6 +257,10 @@ cudaError_t evalset_run(EvalSet &E, scvt_stats *stats) {
     if (e == cudaSuccess) e = cudaGraphLaunch(E.graph, E.stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(E.stream);
     if (e != cudaSuccess) return e;
+    // an edge list overflow is global: every evaluated problem reports it
+    if (E.h_st->flags & FLAG_ECAP)
+        for (int b = 0; b < E.B; ++b)
+            if (E.h_active[b]) E.h_ist[b].flags |= FLAG_ECAP;
     if (stats) {
         stats->evaluations++;
         stats->kernel_launches += E.graph_launches;

@@ -23,6 +23,8 @@ enum : unsigned {
     FLAG_NONPOSITIVE = 32u,   // c_i . z_i <= 0
     FLAG_NONCONVEX = 64u,     // clip pattern with more than one outside run
     FLAG_EMPTY = 128u,        // clip removed every vertex
+    FLAG_ECAP = 256u,         // the cells' edges exceed the edge list (6 per generator): neighbouring
+                              // cells disagree on a Voronoi vertex (four or more cocircular generators)
 };
 
 // Device-side status of one evaluation; reset before each evaluation and
@@ -192,8 +194,10 @@ inline size_t scan_tmp_ints(int64_t n) { return (size_t)kMaxChunks * (2 * ((size
 
 // topo_ev (nullable): two events recorded around the first topology pass,
 // like ev0 / ev1 around the quadrature, when the cells run as one pipeline
+// precision: 0 = FP64 form (corners and rule points in double-float relative to z_i), 1 = mixed (FP32
+// corners and quadrature, FP64 sums), 2 = plain FP64 (corners and rule points in FP64 arithmetic)
 void cell_passes(const Grid &g, const CellOut &out, const CellBuf &cb, int *list1, int *list2, DevStatus *st,
-                 bool mixed, const Tune &t, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1, int64_t *launches,
+                 int precision, const Tune &t, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1, int64_t *launches,
                  int64_t *cell_launches, const Pipes *px, const cudaEvent_t *topo_ev = nullptr);
 Density to_device_density(const scvt_density &r);
 // exclusive scan of len ints (tmp: 2 * (len / 2048 + 64) + 64 ints)

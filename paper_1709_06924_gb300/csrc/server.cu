@@ -249,7 +249,7 @@ scvt_status scvt_server_create(const scvt_server_config *cfg, void *cuda_stream,
     *out = nullptr;
     if (cfg->max_jobs < 1 || cfg->max_jobs > 65535) return SCVT_ERR_INVALID;
     if (cfg->max_generators < 4 || cfg->max_generators > (int64_t)200000000) return SCVT_ERR_INVALID;
-    if (cfg->precision != 0 && cfg->precision != 1) return SCVT_ERR_INVALID;
+    if (cfg->precision < 0 || cfg->precision > 2) return SCVT_ERR_INVALID;
     if (cfg->lbfgs_m < 0 || cfg->lbfgs_m > kLaneMaxM) return SCVT_ERR_INVALID;
     if (cfg->memory_budget < 0) return SCVT_ERR_INVALID;
     const int64_t ws = evalset_bytes(cfg->max_generators, cfg->max_jobs, cfg->precision);

@@ -13,8 +13,10 @@
 //   - N <= SCVT_STATIC_MAX_N (16,384); larger N is rejected with
 //     SCVT_ERR_INVALID before any device work;
 //   - the array's device address is looked up once per device (first call
-//     on that device, with the device current); make that first call before
-//     any stream capture;
+//     on that device, with the device current) and kept for the life of the
+//     process; make that first call before any stream capture, and do not
+//     use this entry point on a device after cudaDeviceReset (the address
+//     kept from before the reset is no longer valid);
 //   - every call shares the one array and it keeps the last call's contents;
 //     whatever must start at zero is cleared on the stream by each call.
 //     Calls whose work overlaps on the GPU (other streams, other host
@@ -182,17 +184,21 @@ extern "C" scvt_status scvt_energy_grad_static(int64_t n, const scvt_density *rh
     cb.serK = (int *)(base + oSerK);
     Pipes px;  // one pipeline on the caller's stream, its counters in the scratch array
     px.counts = (unsigned *)(base + oCounts);
-    cell_passes(grid, out, cb, list1, list2, st, false, Tune(), s, nullptr, nullptr, &launches, &cell_launches, &px);
+    cell_passes(grid, out, cb, list1, list2, st, 0, Tune(), s, nullptr, nullptr, &launches, &cell_launches, &px);
     reduce_eval(N, fc, g, nullptr, nullptr, partials, st, s, &launches);
+    // a launch that failed (configuration, resources) leaves the status block
+    // as it was cleared: report it instead of the energy
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return SCVT_ERR_CUDA;
     DevStatus hs;
-    cudaError_t e = cudaMemcpyAsync(&hs, st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s);
+    e = cudaMemcpyAsync(&hs, st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return SCVT_ERR_CUDA;
     }
     if (hs.flags & (FLAG_BAD_POINT | FLAG_DUPLICATE)) return SCVT_ERR_INVALID;
-    if (hs.flags & (FLAG_UNBOUNDED | FLAG_EMPTY | FLAG_NONPOSITIVE)) return SCVT_ERR_DEGENERATE;
+    if (hs.flags & (FLAG_UNBOUNDED | FLAG_EMPTY | FLAG_NONPOSITIVE | FLAG_ECAP)) return SCVT_ERR_DEGENERATE;
     if (hs.flags & (FLAG_EXHAUSTED | FLAG_VMAX)) return SCVT_ERR_KNN_EXHAUSTED;
     *energy = hs.red[0];
     return SCVT_OK;

@@ -43,8 +43,9 @@ class Engine:
     def __init__(self, n: int, density: Density, lbfgs_m: int = 7, knn_k0: int = 0,
                  device: int | torch.device = 0, stream: torch.cuda.Stream | None = None, precision: int = 0,
                  decomposition: int = 0):
-        """precision: 0 = FP64 throughout, 1 = mixed (FP32 corners and quadrature in local
-        coordinates, FP64 predicates filter, sums and LBFGS).  decomposition: 0 = the
+        """precision: 0 = FP64 form (double-float corners and rule points relative to z_i,
+        results within 1e-12 of FP64), 1 = mixed (FP32 corners and quadrature in local
+        coordinates, FP64 predicates filter, sums and LBFGS), 2 = plain FP64 arithmetic.  decomposition: 0 = the
         paper's sub-triangles through the Delaunay-edge midpoints, 1 = the fan."""
         self.n = int(n)
         self.device = torch.device("cuda", device) if isinstance(device, int) else torch.device(device)

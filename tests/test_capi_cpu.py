@@ -58,7 +58,7 @@ def test_status_strings_and_version():
     assert b"sm_103a" in lib.scvt_version()
 
 
-@pytest.mark.parametrize("field,value", [("n", 3), ("lbfgs_m", 33), ("quad_points", 4), ("knn_k0", 4)])
+@pytest.mark.parametrize("field,value", [("n", 3), ("lbfgs_m", 33), ("quad_points", 4), ("knn_k0", 4), ("precision", 3)])
 def test_create_rejects_bad_config_before_device_work(field, value):
     cfg = capi.scvt_config()
     cfg.n = 100
@@ -114,7 +114,7 @@ def test_build_sources_target_sm103a():
     assert os.path.exists(capi.lib()._name)
 
 
-@pytest.mark.parametrize("field,value", [("max_jobs", 0), ("max_generators", 3), ("precision", 2),
+@pytest.mark.parametrize("field,value", [("max_jobs", 0), ("max_generators", 3), ("precision", 3),
                                          ("lbfgs_m", 40), ("memory_budget", -1)])
 def test_server_create_rejects_bad_config_before_device_work(field, value):
     cfg = capi.scvt_server_config(1 << 30, 100000, 8, 0, 7)

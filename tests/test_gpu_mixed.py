@@ -20,9 +20,7 @@ pytestmark = pytest.mark.gpu
 import oracle
 from paper_1709_06924_gb300 import inputs as I
 from paper_1709_06924_gb300.engine import Engine
-from tests.parity import assert_topology_equal
-
-BOUNDS = {"m": 1e-5, "c": 1e-5, "F_i": 2e-5, "g": 1e-6, "h": 1e-5, "F": 2e-6, "gnorm": 2e-6}
+from tests.parity import assert_mixed_within_bounds, assert_topology_equal
 
 
 def mixed_eval(z, dens, decomposition=0):
@@ -48,18 +46,8 @@ def test_mixed_precision_error_against_oracle(n, seed, dens, fan):
     o = oracle.energy_grad(z, dens, fan=bool(fan))
     _, nbr_o, _ = oracle.voronoi(z)
     assert_topology_equal(r["deg"], r["nbr"], nbr_o)
+    assert_mixed_within_bounds(r, o)
     cn = np.linalg.norm(o["c"], axis=1)
-    err = {
-        "m": np.max(np.abs(r["mass"] - o["m"]) / o["m"]),
-        "c": np.max(np.abs(r["moment"] - o["c"]).max(axis=1) / cn),
-        "F_i": np.max(np.abs(r["cell_energy"] - o["Fi"]) / o["Fi"]),
-        "g": np.max(np.abs(r["grad"] - o["g"]).max(axis=1) / cn),
-        "h": np.max(np.abs(r["precond"] - o["h"]) / o["h"]),
-        "F": abs(r["energy"] - o["F"]) / o["F"],
-        "gnorm": abs(r["grad_norm"] - o["gnorm"]) / o["gnorm"],
-    }
-    for k, v in err.items():
-        assert v <= BOUNDS[k], (k, v, err)
     # the gradient stays tangential
     gz = np.abs((r["grad"] * z).sum(axis=1))
     assert (gz <= 1e-12 * cn).all()
