@@ -160,7 +160,7 @@ scvt_status evaluate_dev(scvt_handle *H, const double *zdev, double *grad, doubl
     g.zs = B.zs;
     g.zf = B.zf;
     g.zl = B.zl;
-    g.zll = B.zll;
+    g.zll = H->cfg.precision != 1 ? B.zll : nullptr;  // not computed in the mixed form
     g.sidx = B.sidx;
     g.bstart = B.start;
     g.rho0 = to_device_density(H->cfg.rho);
@@ -170,7 +170,7 @@ scvt_status evaluate_dev(scvt_handle *H, const double *zdev, double *grad, doubl
         CK(cudaMemsetAsync(B.radius, 0, sizeof(float) * n, s), "reset radius hints");
         H->radius_valid = true;
     }
-    bin_points(zdev, g, B.bin_of, B.count, B.start, B.cursor, B.scan_tmp, B.zs, B.zf, B.zl, H->cfg.precision == 0 ? B.zll : nullptr, B.sidx, B.radius, B.st, s,
+    bin_points(zdev, g, B.bin_of, B.count, B.start, B.cursor, B.scan_tmp, B.zs, B.zf, B.zl, H->cfg.precision != 1 ? B.zll : nullptr, B.sidx, B.radius, B.st, s,
                L);
     CellOut out;
     out.grad = grad;

@@ -608,17 +608,44 @@ __device__ __forceinline__ double horner(const double *__restrict__ cf, int K, d
     return r;
 }
 
-// signed spherical triangle (A, B, C) with the 7-point rule; A = z_i.
+// Offsets from z_i (FP64).  A point x = z_i + w near the sphere projects to
+// p = x / |x|, and p - z_i = (1 + m) w + m z_i with m = 1/|x| - 1 and
+// |x|^2 - 1 = (|z_i|^2 - 1) + 2 z_i.w + |w|^2; m comes from the binomial
+// series of (1 + e)^(-1/2) - 1 for |e| < 1e-4 (exact to 3e-21 relative to e),
+// else from the square root.  The tangential part of p - z_i is then exact
+// to rounding relative to |w| (the radial part, m z_i, moves the point off
+// the sphere only at second order), so no difference of nearby unit vectors
+// is ever formed.
+__device__ __forceinline__ double inv_norm_minus1(double e) {
+    if (fabs(e) < 1e-4) return e * (-0.5 + e * (0.375 + e * (-0.3125 + e * 0.2734375)));
+    const double r = sqrt(1.0 + e);
+    return -e / (r * (1.0 + r));
+}
+
+__device__ __forceinline__ V3 project_offset(V3 zi, double aA1, V3 w) {
+    const double m = inv_norm_minus1(aA1 + 2.0 * dot(zi, w) + dot(w, w));
+    return add(scl(w, 1.0 + m), scl(zi, m));
+}
+
+// the edge midpoint mu_ij = normalize(z_i + z_j) as the offset mu - z_i
+__device__ __forceinline__ V3 midpoint_offset(V3 zi, double aA1, V3 zj) {
+    return project_offset(zi, aA1, scl(sub(zj, zi), 0.5));
+}
+
+// signed spherical triangle (A, A + ob, A + oc) with the 7-point rule; A = z_i,
+// ob, oc: offsets of the other two corners from z_i, aA1 = |A|^2 - 1.
 // inv_alpha: 1/alpha of the tanh cap.  ser / K: the cell's density series
-// (K = 0: evaluate the density directly).
-__device__ __forceinline__ void tri(const Density &r, double inv_alpha, V3 A, V3 B, V3 C, Acc &acc,
+// (K = 0: evaluate the density directly).  Accumulates m, the moment relative
+// to z_i (sum w rho (p - z_i); the caller adds m z_i) and the energy.
+__device__ __forceinline__ void tri(const Density &r, double inv_alpha, V3 A, double aA1, V3 ob, V3 oc, Acc &acc,
                                     const double *ser = nullptr, int K = 0) {
-    V3 cr = crs(sub(B, A), sub(C, A));
-    double det = dot(A, cr);
-    double den = 1.0 + dot(A, B) + dot(B, C) + dot(C, A);
-    // signed area 2 atan(det / den) (Van Oosterom-Strackee); for the small
-    // triangles of a cell |det / den| < 1e-2 and the odd Taylor series of atan
-    // to the x^7 term is exact to 1e-17 relative
+    // Van Oosterom-Strackee with B = A + ob, C = A + oc:
+    // det[A,B,C] = A.(ob x oc), 1 + A.B + B.C + C.A = 4 + 3 (|A|^2 - 1) + 2 A.(ob + oc) + ob.oc
+    const double det = dot(A, crs(ob, oc));
+    const double den = 4.0 + 3.0 * aA1 + 2.0 * dot(A, add(ob, oc)) + dot(ob, oc);
+    // signed area 2 atan(det / den); for the small triangles of a cell
+    // |det / den| < 1e-2 and the odd Taylor series of atan to the x^7 term is
+    // exact to 1e-17 relative
     double area;
     const double xa = det / den;
     if (den > 0.0 && fabs(xa) < 1e-2) {
@@ -628,36 +655,37 @@ __device__ __forceinline__ void tri(const Density &r, double inv_alpha, V3 A, V3
         area = 2.0 * atan2(det, den);
     }
     const V3 xc = mk(r.xc0, r.xc1, r.xc2);
+    const double u0 = (K > 0) ? dot(xc, A) - ser[kSerMax] : 0.0;
 #pragma unroll 1
     for (int k = 0; k < 7; ++k) {
-        // rule point x in the flat triangle, projected to p = x / |x|.  A small
-        // triangle's points lie within delta = 1 - |x|^2 < 1e-4 of the sphere,
-        // where (1 - delta)^(-1/2) to the delta^3 term (binomial series 1, 1/2,
-        // 3/8, 5/16) is exact to 3e-17; larger triangles take rsqrt
-        const V3 x = add(add(scl(A, kQb[k][0]), scl(B, kQb[k][1])), scl(C, kQb[k][2]));
-        const double x2 = dot(x, x);
-        const double dl = 1.0 - x2;
-        const double inv = (fabs(dl) < 1e-4) ? 1.0 + dl * (0.5 + dl * (0.375 + dl * 0.3125)) : rsqrt(x2);
+        // rule point x = A + b1 ob + b2 oc, projected: p - A from the offsets
+        const V3 w = add(scl(ob, kQb[k][1]), scl(oc, kQb[k][2]));
+        const V3 dp = project_offset(A, aA1, w);
         double rv;
         if (r.kind == 0) {
             rv = 1.0;
         } else if (r.kind == 1) {
-            const double pz = x.z * inv, z2 = pz * pz;
+            const double pz = A.z + dp.z, z2 = pz * pz;
             rv = (1.0 - r.gamma) * z2 * z2 + r.gamma;
         } else if (K > 0) {
-            rv = horner(ser, K, inv * dot(x, xc) - ser[kSerMax]);
+            rv = horner(ser, K, u0 + dot(xc, dp));
         } else {
-            rv = rho_direct(r, inv_alpha, scl(x, inv));
+            rv = rho_direct(r, inv_alpha, add(A, dp));
         }
         const double wr = kQw[k] * area * rv;
-        const double wi = wr * inv;  // wr p = wi x
-        const V3 dp = mk(fma(x.x, inv, -A.x), fma(x.y, inv, -A.y), fma(x.z, inv, -A.z));
         acc.m += wr;
-        acc.cx = fma(wi, x.x, acc.cx);
-        acc.cy = fma(wi, x.y, acc.cy);
-        acc.cz = fma(wi, x.z, acc.cz);
+        acc.cx = fma(wr, dp.x, acc.cx);
+        acc.cy = fma(wr, dp.y, acc.cy);
+        acc.cz = fma(wr, dp.z, acc.cz);
         acc.e = fma(wr, dot(dp, dp), acc.e);
     }
+}
+
+// moment relative to z_i -> moment c = m z_i + sum w rho (p - z_i)
+__device__ __forceinline__ void moment_from_offsets(V3 zi, Acc &acc) {
+    acc.cx = fma(zi.x, acc.m, acc.cx);
+    acc.cy = fma(zi.y, acc.m, acc.cy);
+    acc.cz = fma(zi.z, acc.m, acc.cz);
 }
 
 __device__ __forceinline__ void write_cell(const CellOut &out, int i, V3 zi, const Acc &acc, unsigned *flags) {
@@ -897,30 +925,31 @@ __global__ void __launch_bounds__(128) k_topo(Grid g, CellOut out, CellBuf cb,
             cb.deg[p] = 0;
             const Density rho = g.rho ? g.rho[v.b] : g.rho0;
             const double inv_alpha = rho.inv_alpha;
+            const double aA1 = dot(zi, zi) - 1.0;
             Acc acc = {0, 0, 0, 0, 0};
-            V3 corners_first, va;
+            V3 corners_first, va;  // corners as offsets from z_i
             for (int t2 = 0; t2 <= nv; ++t2) {
                 const int k = (k0 + t2) % nv;
                 double a, b, cc, u, w;
                 P.line64(F, P.ln[c][k], a, b, cc);
                 P.meet(pa, pb, pc, a, b, cc, u, w);
                 pa = a; pb = b; pc = cc;
-                V3 x = add(zi, add(scl(F.e1, u), scl(F.e2, w)));
-                V3 vb = (t2 == nv) ? corners_first : scl(x, rsqrt(dot(x, x)));
+                V3 vb = (t2 == nv) ? corners_first : project_offset(zi, aA1, add(scl(F.e1, u), scl(F.e2, w)));
                 if (t2 == 0) {
                     corners_first = vb;
                 } else {
                     const int kprev = (k0 + t2 - 1) % nv;
                     if (g.fan) {
-                        tri(rho, inv_alpha, zi, va, vb, acc);
+                        tri(rho, inv_alpha, zi, aA1, va, vb, acc);
                     } else {
-                        V3 mu = unit(add(zi, ld(g.zs + P.gen_of(P.ln[c][kprev]))));
-                        tri(rho, inv_alpha, zi, va, mu, acc);
-                        tri(rho, inv_alpha, zi, mu, vb, acc);
+                        const V3 om = midpoint_offset(zi, aA1, ld(g.zs + P.gen_of(P.ln[c][kprev])));
+                        tri(rho, inv_alpha, zi, aA1, va, om, acc);
+                        tri(rho, inv_alpha, zi, aA1, om, vb, acc);
                     }
                 }
                 va = vb;
             }
+            moment_from_offsets(zi, acc);
             write_cell(out, i, zi, acc, flags);
         }
     }
@@ -1515,6 +1544,21 @@ __device__ __forceinline__ df inv_norm_m1(df dl) {
     return df_add_f(df_add(df{0.5f * dl.hi, 0.5f * dl.lo}, df_mul_f(d2, 0.375f)), tail);
 }
 
+// FP64 line of neighbour gen in the frame at z_i for the corners: (a, b) =
+// (e1.d, e2.d), d = z_j - z_i, and c = -z_i.d taken as (|d|^2 + (|z_i|^2 - 1)
+// - (|z_j|^2 - 1)) / 2 with the exact |z|^2 - 1 of the binning (zll[].w):
+// the dot product -z_i.d cancels to |d|^2 / 2 and would carry an error of
+// 1e-16 |d|, a relative 2e-16 / |d| of the line's offset, which moves the
+// corners of close neighbours by ~1e-16 -- up to 1e-12 of a small cell's
+// energy.  Without zll (mixed form) the dot product is used.
+__device__ __forceinline__ void corner_line64(const Grid &g, int p, V3 zi, V3 e1, V3 e2, int gen, double &a,
+                                              double &b, double &c) {
+    const V3 d = sub(ld(g.zs + gen), zi);
+    a = dot(e1, d);
+    b = dot(e2, d);
+    c = g.zll ? 0.5 * (dot(d, d) + ((double)g.zll[p].w - (double)g.zll[gen].w)) : -dot(zi, d);
+}
+
 // Corner of every edge: vertex k of a cell is where the bisector planes of
 // edges k-1 and k meet the plane z_i + u e1 + w e2 (then projected).
 // Double-float path: e1, e2 are any FP32 vectors spanning a plane through
@@ -1527,8 +1571,12 @@ __device__ __forceinline__ df inv_norm_m1(df dl) {
 // u and w) gives the offset x - z_i = u e1 + w e2;
 // projecting, v - z_i = (1 + m)(x - z_i) + m z_i with m = 1/|x| - 1 from
 // delta = -(|z_i|^2 - 1) - 2 z_i.(x - z_i) - |x - z_i|^2.  Corners farther
-// than chord 0.03 or poorly conditioned are solved in FP64 in the gnomonic
-// frame at z_i.
+// than chord 0.03 or poorly conditioned, and every corner of the plain FP64
+// form, are solved in FP64 in the gnomonic frame at z_i and projected the
+// same way (project_offset).  The cell buffer keeps each corner as its
+// offset v - z_i in FP64, exact to rounding relative to the cell's size
+// (an absolute unit vector would carry 1e-16 of absolute error, up to 1e-12
+// of the smallest cells' energies).
 template <bool PLAIN>
 __global__ void __launch_bounds__(256) k_corners(Grid g, CellBuf cb, Span sp) {
     const int ne = *sp.etot, eb = *sp.e0;
@@ -1579,8 +1627,7 @@ __global__ void __launch_bounds__(256) k_corners(Grid g, CellBuf cb, Span sp) {
                     const df ox = df_add(dx.x, df_mul(m, df_add(Z.x, dx.x)));
                     const df oy = df_add(dx.y, df_mul(m, df_add(Z.y, dx.y)));
                     const df oz = df_add(dx.z, df_mul(m, df_add(Z.z, dx.z)));
-                    cb.vx[(size_t)p * kCellSlots + k] =
-                        P4{zi.x + df_to(ox), zi.y + df_to(oy), zi.z + df_to(oz), 0.0};
+                    cb.vx[(size_t)p * kCellSlots + k] = P4{df_to(ox), df_to(oy), df_to(oz), 0.0};
                     continue;
                 }
             }
@@ -1588,14 +1635,13 @@ __global__ void __launch_bounds__(256) k_corners(Grid g, CellBuf cb, Span sp) {
         V3 e1, e2;
         frame64(zi, e1, e2);
         double a1, b1, c1, a2, b2, c2;
-        line_of(g, zi, e1, e2, ga, a1, b1, c1);
-        line_of(g, zi, e1, e2, gb, a2, b2, c2);
+        corner_line64(g, p, zi, e1, e2, ga, a1, b1, c1);
+        corner_line64(g, p, zi, e1, e2, gb, a2, b2, c2);
         const double inv = 1.0 / (a1 * b2 - a2 * b1);
         const double u = (c1 * b2 - c2 * b1) * inv;
         const double w = (a1 * c2 - a2 * c1) * inv;
-        const V3 x = add(zi, add(scl(e1, u), scl(e2, w)));
-        const V3 v = scl(x, rsqrt(dot(x, x)));
-        cb.vx[(size_t)p * kCellSlots + k] = P4{v.x, v.y, v.z, 0.0};
+        const V3 o = project_offset(zi, dot(zi, zi) - 1.0, add(scl(e1, u), scl(e2, w)));
+        cb.vx[(size_t)p * kCellSlots + k] = P4{o.x, o.y, o.z, 0.0};
     }
 }
 
@@ -1660,8 +1706,8 @@ __device__ void series_of_cell(const Grid &g, const CellBuf &cb, int p, double *
     float umax = 0.0f, umin = 0.0f, h2 = 0.0f;
     int kmax = 0, kmin = 0;
     for (int k = 0; k < deg; ++k) {
-        const P4 v = cb.vx[(size_t)p * kCellSlots + k];
-        const float dx = (float)v.x - hp.x, dy = (float)v.y - hp.y, dz = (float)v.z - hp.z;
+        const P4 v = cb.vx[(size_t)p * kCellSlots + k];  // offset from z_i
+        const float dx = (float)v.x, dy = (float)v.y, dz = (float)v.z;
         const float u = xf.x * dx + xf.y * dy + xf.z * dz;
         if (u > umax) { umax = u; kmax = k; }
         if (u < umin) { umin = u; kmin = k; }
@@ -1734,9 +1780,9 @@ __device__ void series_of_cell(const Grid &g, const CellBuf &cb, int p, double *
             // both extreme corners must agree with the direct formula
             const int ks[2] = {kmax, kmin};
             for (int t = 0; t < 2 && K > 0; ++t) {
-                const V3 v = ld(cb.vx + (size_t)p * kCellSlots + ks[t]);
-                const double d = rho_direct(r, inv_alpha, v);
-                const double sv = horner(cf, K, dot(xc, v) - ci);
+                const V3 ov = ld(cb.vx + (size_t)p * kCellSlots + ks[t]);
+                const double d = rho_direct(r, inv_alpha, add(zi, ov));
+                const double sv = horner(cf, K, dot(xc, ov));
                 if (!(fabs(sv - d) <= 1e-14 * d)) K = 0;
             }
         }
@@ -1919,7 +1965,7 @@ __global__ void __launch_bounds__(512) k_quad(Grid g, CellBuf cb, int ecap, Span
         const int deg = cb.deg[p];
         const V3 zi = ld(g.zs + p);
         const P4 *vx = cb.vx + (size_t)p * kCellSlots;
-        const V3 va = ld(vx + k);
+        const V3 va = ld(vx + k);  // corner offsets from z_i
         const V3 vb = ld(vx + ((k + 1 == deg) ? 0 : k + 1));
         const Density rho = g.rho ? g.rho[view_of(g, p).b] : g.rho0;
         const int K = cb.serK ? cb.serK[p] : 0;
@@ -1927,11 +1973,10 @@ __global__ void __launch_bounds__(512) k_quad(Grid g, CellBuf cb, int ecap, Span
         double *ea = cb.eacc;
         // double-float path: offsets of the edge's points from z_i below chord
         // 0.03 (then delta <= 1e-3 at every rule point) and a density without
-        // direct evaluation; otherwise FP64.  Offsets are FP64 differences of
-        // nearby points (exact to 1e-16 of their size), rounded to pairs.
+        // direct evaluation; otherwise FP64.  The corner offsets (FP64, exact
+        // to rounding relative to their size) are rounded to pairs.
         if constexpr (!PLAIN) {
-            const V3 ba = sub(va, zi), bb = sub(vb, zi);
-            const df3 da = df3_from(ba.x, ba.y, ba.z), db = df3_from(bb.x, bb.y, bb.z);
+            const df3 da = df3_from(va.x, va.y, va.z), db = df3_from(vb.x, vb.y, vb.z);
             const float4 hp = g.zf[p], lp = g.zl[p], llp = g.zll[p];
             const df3 dj = gen_diff(g, cb.nb[(size_t)p * kCellSlots + k], hp, lp, llp);
             const float r2 = fmaxf(fmaxf(da.x.hi * da.x.hi + da.y.hi * da.y.hi + da.z.hi * da.z.hi,
@@ -1972,15 +2017,18 @@ __global__ void __launch_bounds__(512) k_quad(Grid g, CellBuf cb, int ecap, Span
                 continue;
             }
         }
-        const V3 mu = unit(add(zi, ld(g.zs + cb.nb[(size_t)p * kCellSlots + k])));
+        // FP64: every point relative to z_i (corner and midpoint offsets)
         const double inv_alpha = rho.inv_alpha;
+        const double aA1 = dot(zi, zi) - 1.0;
         Acc acc = {0, 0, 0, 0, 0};
         if (g.fan) {
-            tri(rho, inv_alpha, zi, va, vb, acc, ser, K);
+            tri(rho, inv_alpha, zi, aA1, va, vb, acc, ser, K);
         } else {
-            tri(rho, inv_alpha, zi, va, mu, acc, ser, K);
-            tri(rho, inv_alpha, zi, mu, vb, acc, ser, K);
+            const V3 om = midpoint_offset(zi, aA1, ld(g.zs + cb.nb[(size_t)p * kCellSlots + k]));
+            tri(rho, inv_alpha, zi, aA1, va, om, acc, ser, K);
+            tri(rho, inv_alpha, zi, aA1, om, vb, acc, ser, K);
         }
+        moment_from_offsets(zi, acc);
         ea[e] = acc.m;
         ea[(size_t)ecap + e] = acc.cx;
         ea[2 * (size_t)ecap + e] = acc.cy;

@@ -49,7 +49,7 @@ Grid make_grid(const EvalSet &E) {
     g.zs = E.zs;
     g.zf = E.zf;
     g.zl = E.zl;
-    g.zll = E.zll;
+    g.zll = E.precision != 1 ? E.zll : nullptr;  // not computed in the mixed form
     g.sidx = E.sidx;
     g.bstart = E.start;
     g.inst = E.d_inst;
@@ -67,7 +67,7 @@ void enqueue_eval(EvalSet &E, int64_t *launches, int64_t *cell_launches) {
     cudaMemsetAsync(E.d_st, 0, sizeof(DevStatus), s);
     cudaMemsetAsync(E.d_ist, 0, sizeof(DevStatus) * E.B, s);
     Grid g = make_grid(E);
-    bin_points(E.zt, g, E.bin_of, E.count, E.start, E.cursor, E.scan_tmp, E.zs, E.zf, E.zl, E.precision == 0 ? E.zll : nullptr, E.sidx, E.radius, E.d_st,
+    bin_points(E.zt, g, E.bin_of, E.count, E.start, E.cursor, E.scan_tmp, E.zs, E.zf, E.zl, E.precision != 1 ? E.zll : nullptr, E.sidx, E.radius, E.d_st,
                s, launches);
     CellOut out;
     memset(&out, 0, sizeof(out));
