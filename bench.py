@@ -5,8 +5,11 @@ A step is one LBFGS iteration of the whole hot path: the two-loop direction,
 the line search (each trial re-bins the generators, rebuilds every Voronoi
 cell and integrates it) and the accepted-pair update.  The default workload
 is the 2,621,442-generator tanh-cap problem (gamma = (1/8)^4, alpha = 0.10,
-beta = pi/9, x_c at 45N 270E, LBFGS memory 7, FP64) from seeded uniform
-points; the metric is generator-updates/s = N x accepted iterations / s.
+beta = pi/9, x_c at 45N 270E, LBFGS memory 7) from seeded uniform points, in
+the FP64 form; the metric is generator-updates/s = N x accepted iterations /
+s.  The same line reports the mixed and the plain FP64 forms, the time each
+takes to the paper's stopping rules at that size, batched and served forms,
+and the FP64 CPU oracle on the host cores.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -34,6 +37,11 @@ import numpy as np  # noqa: E402
 
 from paper_1709_06924_gb300 import inputs as I  # noqa: E402
 
+# precision forms of the engine (scvt_config.precision) and the arithmetic each computes in
+FORMS = {"fp64": 0, "mixed": 1, "plain": 2}
+FORM_NAME = {v: k for k, v in FORMS.items()}
+DTYPE = {0: "f64+f32x2", 1: "f32/f64", 2: "f64"}
+
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -44,10 +52,10 @@ def parse():
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--cpu-sample-n", type=int, default=163842,
                    help="generators of the bounded oracle sample (same density)")
-    p.add_argument("--cpu-sample-iters", type=int, default=3)
+    p.add_argument("--cpu-sample-iters", type=int, default=4)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--no-other-form", action="store_true", help="skip timing the other precision form")
+    p.add_argument("--no-other-form", action="store_true", help="skip timing the other precision forms")
     p.add_argument("--no-time-to-tol", action="store_true", help="skip the time-to-tolerance runs")
     p.add_argument("--no-batched", action="store_true", help="skip the 64-problem batch")
     p.add_argument("--no-tune", action="store_true", help="keep the default tuning (no autotuner run)")
@@ -56,11 +64,14 @@ def parse():
     p.add_argument("--no-serving", action="store_true", help="skip the request-stream measurement")
     p.add_argument("--no-table1", action="store_true", help="skip the 2,562-generator method comparison")
     p.add_argument("--no-chain", action="store_true", help="skip the 2,562 -> 655,362 bisection chain")
-    p.add_argument("--serve-jobs", type=int, default=32, help="jobs in the request stream")
-    p.add_argument("--serve-n-hi", type=int, default=655362, help="largest job size of the request stream")
+    p.add_argument("--serve-jobs", type=int, default=64, help="jobs in the request stream")
+    p.add_argument("--serve-n-hi", type=int, default=10485762, help="largest job size of the request stream")
     p.add_argument("--serve-max-iter", type=int, default=100, help="iteration cap per served job")
-    p.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
-                   help="fp64: everything in FP64; mixed: FP32 corners/quadrature, FP64 sums and LBFGS")
+    p.add_argument("--ttt-max-iter", type=int, default=3000,
+                   help="iteration cap of the time-to-tolerance solves at the workload's size")
+    p.add_argument("--precision", choices=sorted(FORMS), default="fp64",
+                   help="fp64: double-float rule points and corners, FP64 sums (within 1e-12 of FP64); "
+                        "mixed: FP32 corners/quadrature, FP64 sums and LBFGS; plain: FP64 arithmetic")
     return p.parse_args()
 
 
@@ -222,26 +233,381 @@ def pick_tuning(args, eng, z):
     return eng.tune(z) if not args.no_tune else eng.tuning()
 
 
-def time_to_tolerance(w, z_host, local, prec, tuning, tol=1e-6, max_iter=50):
-    """Wall time from the seeded start until ||grad E||_2 <= tol (the
-    workload's stated criterion), with the iterate on the device (the
-    tuning found once for the workload is applied, not re-searched)."""
+# ------------------------------------------------------------------ peaks
+def measured_peaks():
+    """MEASURED_PEAKS.json of this pool (driver-written), or {}."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def measured_hbm_gbs():
+    """HBM copy bandwidth measured on this machine, else the fallback figure."""
+    v = measured_peaks().get("hbm_gbs")
+    return (float(v), "measured") if v else (6800.0, "fallback")
+
+
+def device_sms(local=0) -> int:
+    import torch
+    return int(torch.cuda.get_device_properties(local).multi_processor_count)
+
+
+def max_sm_mhz(clock_summary=None):
+    """Maximum SM clock: the measured-peaks record, else nvidia-smi's
+    clocks.max.sm sampled during the run, else 2,070 MHz (GB300)."""
+    v = measured_peaks().get("sm_max_mhz")
+    if v:
+        return float(v), "MEASURED_PEAKS.json sm_max_mhz"
+    if clock_summary and clock_summary.get("sm_max_mhz"):
+        return float(clock_summary["sm_max_mhz"]), "nvidia-smi clocks.max.sm"
+    return 2070.0, "GB300 maximum SM clock"
+
+
+def issue_peak(sms, mhz):
+    """Warp instructions per second: every SM issues at most 4 (one per
+    scheduler) per clock."""
+    return sms * 4 * mhz * 1e6
+
+
+def fp64_peak_flops(sms, mhz):
+    """FP64 pipe: 2 DFMA (4 flop) per SM per clock on GB300 (a DFMA
+    microbenchmark of independent chains reaches 80 % of it)."""
+    return sms * 4 * mhz * 1e6
+
+
+# --------------------------------------------------- work per generator
+# FP64 cost of the transcendentals in FMA-pipe time, in DFMA equivalents
+# (measured on this GPU with CUDA events, one kernel per function)
+COST = {"rsqrt": 6.9, "sqrt": 9.6, "atan2": 41.2, "exp": 17.9, "div": 10.4}
+
+
+def fp64_flops_per_generator(kind: int, series_frac: float = 0.0, series_len: float = 0.0) -> float:
+    """The method's FP64 work per generator per evaluation of the quadrature,
+    in flop equivalents (SURVEY 8(d)'s count, written out).
+
+    Per Voronoi edge the method integrates two signed sub-triangles (Sec.
+    3.2.2): per sub-triangle the Van Oosterom-Strackee area (offsets, cross
+    and dot products: 38 flops, one atan2) and 7 rule points; per point the
+    projected point (combination, norm, rsqrt, scale: 37 + rsqrt), the
+    density, the weight and the accumulation of m, c and |p - z|^2 (24).  The
+    tanh cap evaluated directly costs a cross product, a norm and a dot (19)
+    plus sqrt, atan2, exp and a division (its logistic form) (+5); from a
+    Taylor series of series_len terms it costs a dot, a difference and a
+    Horner sweep (6 + 2 series_len), for the fraction series_frac of the
+    points that use one.  X3 costs 6.  Transcendentals are charged what they
+    cost on this GPU in FMA-pipe time (COST, DFMA equivalents x 2 flop).
+    The cell of a generator has 6 edges on average (Euler: 2E = 6N - 12)."""
+    c = {k: 2 * v for k, v in COST.items()}
+    direct = {0: 0.0, 1: 6.0, 2: 24.0 + c["sqrt"] + c["atan2"] + c["exp"] + c["div"],
+              3: 28.0 + c["sqrt"] + c["atan2"] + c["exp"] + c["div"]}[kind]
+    dens = direct
+    if kind >= 2:
+        dens = series_frac * (6.0 + 2.0 * series_len) + (1.0 - series_frac) * direct
+    point = 37.0 + c["rsqrt"] + 24.0 + dens
+    subtri = 38.0 + c["atan2"] + 7 * point
+    mu = 11.0 + c["rsqrt"]
+    return 6.0 * (2 * subtri + mu)
+
+
+# FP32 instructions of the double-float operations (csrc/df.cuh): TwoSum 6,
+# Fast2Sum 3, the FMA exact product 2
+DF_OPS = {"add": 11, "add_f": 10, "mul": 7, "mul_f": 6, "fma": 18, "div": 36}
+
+
+def df_inst_per_generator(series_len: float) -> float:
+    """FP32 instructions of the method's arithmetic per generator in the
+    double-float quadrature (the same SURVEY 8(d) steps, mapped to the
+    double-float operations the kernel uses), counted from the source:
+
+    * per rule point: A.w (2 mul, 1 add), |w|^2 (3 mul, 2 add), 1 - |x|^2
+      (2 add, 2 FP32), the binomial series of 1/|x| - 1 (1 mul, 1 mul_f,
+      1 add, 1 add_f, 6 FP32), x_c.(p - z_i) (3 mul, 3 add), the series
+      density (1 add, 2 FP32, series_len - 1 fma), the weight (3 mul),
+      |p - z_i|^2 (2 mul, 3 add, 1 add_f, 3 FP32) and the five sums with
+      their (1 + m) weights (6 add, 3 mul): 367 + 18 (series_len - 1);
+    * per sub-triangle: the offsets' dot products A.b, A.c, b.b, b.c, c.c,
+      x_c.b, x_c.c (21 mul, 14 add), the determinant A.(b x c) (9 mul,
+      5 add), the denominator (2 mul_f, 1 add_f, 3 add), the area (1 div,
+      1 add_f, 1 mul_f, 3 FP32) and the moment's assembly (9 mul, 11 add):
+      713;
+    * per edge: the generator difference from three-part coordinates
+      (~100), the midpoint's offset and projection and x_c.z_i (286), the
+      conversions of the offsets and of the outputs (~40), the centre and
+      term choice of the density table (~70): about 495;
+    * 6 edges of 2 sub-triangles of 7 points per generator."""
+    point = 367 + DF_OPS["fma"] * max(series_len - 1.0, 0.0)
+    edge = 2 * (713 + 7 * point) + 495
+    return 6.0 * edge
+
+
+# ---------------------------------------------------------- rooflines
+# Executed warp instructions per unit, from one-pass ncu captures of the
+# timed steps of this benchmark at N = 2,621,442 (smsp__inst_executed.sum of
+# one launch divided by N):
+#   ncu --metrics smsp__inst_executed.sum --clock-control none -k regex:k_quad -c 3
+#       python bench.py --steps 2 --warmup 1 --no-other-form --no-time-to-tol --no-batched
+#       --no-serving --no-table1 --no-chain --no-cpu-baseline --no-e2e
+# and likewise for k_topo_warp (per cell, by lanes per cell).
+QUAD_INST_PER_GENERATOR = 4536632457 / 2621442
+TOPO_INST_PER_CELL = {32: 3153936979 / 2621442, 16: 1873542833 / 2621442}
+# DRAM bytes of one k_quad launch at N = 163,842 (ncu dram__bytes_read.sum +
+# dram__bytes_write.sum), scaled by the number of generators; None once the
+# kernel has changed since that capture
+QUAD_DRAM_BYTES_163842 = None
+
+
+def quad_traffic_bytes(n: int):
+    if QUAD_DRAM_BYTES_163842 is None:
+        return None
+    return QUAD_DRAM_BYTES_163842 * n / 163842
+
+
+def one_pipeline_kernel_ms(eng, z, evals=3):
+    """Average CUDA-event time of the quadrature and of the first topology
+    pass over `evals` evaluations of z with one cell pipeline (the engine's
+    tuning is restored afterwards; stats are reset)."""
+    tsave = eng.tuning()
+    eng.set_tuning(**dict(tsave, chunks=1))
+    eng.set_profiling(True)
+    eng.evaluate(z)
+    eng.reset_stats()
+    for _ in range(evals):
+        eng.evaluate(z)
+    st = eng.stats()
+    eng.set_tuning(**tsave)
+    quad = st["cell_kernel_ms"] / max(st["cell_kernel_timed"], 1)
+    topo = st["topo_kernel_ms"] / max(st["topo_kernel_timed"], 1)
+    return quad, topo, st
+
+
+def series_stats(w, st):
+    """Fraction of quadrature edges whose density came from the density
+    table, and their average series length."""
+    edges = (6 * w.n - 12) * max(st["evaluations"], 1)
+    return st["series_edges"] / edges, st["series_terms"] / max(st["series_edges"], 1)
+
+
+def roofline_of(prec, w, quad_ms, topo_ms, st, lanes=32, sms=152, mhz=2070.0, clock_src="GB300"):
+    """Roofline of the step's dominant kernel.
+
+    FP64 form: the double-float quadrature k_quad, bound by instruction
+    issue.  `frac` is the issue fraction of its EXECUTED warp instructions
+    (an implementation count); `algorithmic` sets the method's own
+    arithmetic, mapped to the double-float operations, against the same
+    issue peak.  Plain FP64 form: k_quad<FP64>, bound by the FP64 pipe, with
+    the method's FP64 work.  Mixed form: the topology pass k_topo_warp,
+    bound by issue (executed instructions)."""
+    peak = issue_peak(sms, mhz)
+    base = {"avg_launch_ms": None, "sms": sms, "sm_mhz": mhz,
+            "peak_source": "%d SMs (device) x 4 schedulers x 1 warp-instruction/clk x %.0f MHz (%s)"
+                           % (sms, mhz, clock_src)}
+    sfrac, slen = series_stats(w, st)
+    if prec == 0:
+        achieved = w.n * QUAD_INST_PER_GENERATOR / (quad_ms * 1e-3)
+        alg = df_inst_per_generator(slen) / 32.0
+        alg_rate = w.n * alg / (quad_ms * 1e-3)
+        trf = quad_traffic_bytes(w.n)
+        return dict(base, **{
+            "bound": "alu", "kernel": "k_quad", "achieved": achieved / 1e12, "peak": peak / 1e12,
+            "unit": "Twarp-inst/s", "frac": achieved / peak,
+            "frac_kind": "FP32-issue fraction of executed warp instructions (implementation count)",
+            "traffic": trf, "avg_launch_ms": quad_ms, "inst_per_generator": QUAD_INST_PER_GENERATOR,
+            "algorithmic": {"warp_inst_per_generator": alg, "achieved": alg_rate / 1e12, "frac": alg_rate / peak,
+                            "what": "the method's quadrature arithmetic as double-float operations (FP32 "
+                                    "instruction counts of df.cuh), over the same issue peak"},
+            "traffic_over_algorithmic_bytes": (trf / (w.n * 88.0)) if trf else None,
+            "fp64_equivalent_tflops": w.n * fp64_flops_per_generator(w.density.kind, sfrac, slen)
+                                      / (quad_ms * 1e-3) / 1e12,
+            "series_edge_fraction": sfrac, "series_terms_avg": slen,
+            "work_source": "ncu one-pass smsp__inst_executed.sum of k_quad in the timed steps at N = 2,621,442"})
+    if prec == 2:
+        flops = fp64_flops_per_generator(w.density.kind, sfrac, slen)
+        fpk = fp64_peak_flops(sms, mhz)
+        achieved = w.n * flops / (quad_ms * 1e-3)
+        return dict(base, **{
+            "bound": "fp64", "kernel": "k_quad (plain FP64)", "achieved": achieved / 1e12, "peak": fpk / 1e12,
+            "unit": "TFLOP/s", "frac": achieved / fpk, "traffic": None, "avg_launch_ms": quad_ms,
+            "flop_equivalents_per_generator": flops, "series_edge_fraction": sfrac, "series_terms_avg": slen,
+            "frac_kind": "the method's FP64 flop equivalents (transcendentals at their measured cost) over the "
+                         "FP64 pipe peak (%d SMs x 4 flop/clk x %.0f MHz)" % (sms, mhz)})
+    ipc = TOPO_INST_PER_CELL[lanes]
+    achieved = w.n * ipc / (topo_ms * 1e-3)
+    return dict(base, **{
+        "bound": "alu", "kernel": "k_topo_warp", "achieved": achieved / 1e12, "peak": peak / 1e12,
+        "unit": "Twarp-inst/s", "frac": achieved / peak, "traffic": None, "avg_launch_ms": topo_ms,
+        "quad_kernel_ms": quad_ms, "inst_per_cell": ipc, "lanes_per_cell": lanes,
+        "frac_kind": "FP32-issue fraction of executed warp instructions (implementation count)",
+        "work_source": "ncu one-pass smsp__inst_executed.sum of k_topo_warp in the timed steps at N = 2,621,442"})
+
+
+def two_loop_roofline(w, warmup, iters, lbfgs_ms):
+    """HBM roofline of the LBFGS direction (the two-loop recursion of Sec.
+    2.2.2 with diag(h) as the initial inverse Hessian): algorithmic traffic
+    per generator (4c + 2) x 24 bytes with c stored pairs (each history
+    vector read twice, g read, q written), c = min(warm-up + i, m) in timed
+    iteration i, over the CUDA-event time of the direction launches in the
+    timed steps."""
+    if not iters or lbfgs_ms <= 0:
+        return None
+    counts = [min(warmup + i, w.lbfgs_m) for i in range(iters)]
+    alg = sum((4 * c + 2) * 24 for c in counts) * w.n
+    peak, src = measured_hbm_gbs()
+    achieved = alg / (lbfgs_ms * 1e-3) / 1e9
+    return {"bound": "hbm", "kernel": "LBFGS direction (two-loop)", "achieved": achieved, "peak": peak,
+            "unit": "GB/s", "frac": achieved / peak, "traffic": None, "algorithmic_bytes": alg,
+            "peak_source": src, "pairs_per_iteration": counts, "ms_total": lbfgs_ms}
+
+
+# ------------------------------------------------------------------ forms
+def run_form(args, w, z_host, local, prec, tuning=None):
+    """One precision form at the workload: W warm-up iterations from the
+    seeded start, the autotuner at the warmed iterate (or a fixed tuning),
+    then K timed iterations (CUDA events).  Returns the engine (kept open),
+    its iterate and the measurements."""
     import torch
     from paper_1709_06924_gb300.engine import Engine
     eng = Engine(w.n, w.density, lbfgs_m=w.lbfgs_m, device=local, precision=prec)
-    eng.set_tuning(**tuning)
     z = torch.from_numpy(z_host).cuda(local)
+    if tuning is not None:
+        eng.set_tuning(**tuning)
+    elif args.tuning:
+        tuning = pick_tuning(args, eng, z)
+    eng.lbfgs_solve(z, max_iter=args.warmup, grad_tol=0.0)
+    if tuning is None:
+        tuning = pick_tuning(args, eng, z)
+    eng.reset_stats()
+    eng.set_profiling(True)
+    torch.cuda.synchronize()
+    return eng, z, tuning
+
+
+def form_record(args, w, eng, z, prec, tuning, rep, t, sms, mhz, clock_src, local):
+    import torch
+    st = eng.stats()
+    quad_ms, topo_ms, stq = one_pipeline_kernel_ms(eng, z)
+    u, tt = combine_ranks(w.n * rep["iters"], t, device=torch.device("cuda", local))
+    return {"precision": FORM_NAME[prec], "dtype": DTYPE[prec], "value": u / tt,
+            "ms_per_step": 1e3 * tt / max(rep["iters"], 1), "iters": rep["iters"], "fevals": rep["fevals"],
+            "roofline": roofline_of(prec, w, quad_ms, topo_ms, stq, tuning["topo_cell_lanes"], sms, mhz, clock_src),
+            "eval_ms_avg": st["eval_ms"] / max(st["evaluations"], 1), "gpu_launches": st["kernel_launches"],
+            "tuning": tuning}, st
+
+
+def per_cell_error(w, z_host, local, prec, ref_prec=0):
+    """Worst per-cell relative error of form `prec` against form `ref_prec`
+    (the FP64 form, which matches the oracle to 1e-12 on every cell) at z:
+    m_i, c_i (relative to |c_i|), F_i, g_i (relative to |c_i|), h_i."""
+    import torch
+    from paper_1709_06924_gb300.engine import Engine
+    outs = []
+    for p in (prec, ref_prec):
+        with Engine(w.n, w.density, lbfgs_m=w.lbfgs_m, device=local, precision=p) as e:
+            r = e.evaluate(torch.from_numpy(z_host).cuda(local))
+            outs.append({k: (v.cpu().numpy() if isinstance(v, torch.Tensor) else v) for k, v in r.items()})
+    a, o = outs
+    cn = np.linalg.norm(o["moment"], axis=1)
+    return {"m": float(np.max(np.abs(a["mass"] - o["mass"]) / o["mass"])),
+            "c": float(np.max(np.abs(a["moment"] - o["moment"]).max(axis=1) / cn)),
+            "F_i": float(np.max(np.abs(a["cell_energy"] - o["cell_energy"]) / o["cell_energy"])),
+            "g": float(np.max(np.abs(a["grad"] - o["grad"]).max(axis=1) / cn)),
+            "h": float(np.max(np.abs(a["precond"] - o["precond"]) / o["precond"])),
+            "F": abs(a["energy"] - o["energy"]) / o["energy"], "cells": w.n,
+            "against": "the FP64 form (every cell within 1e-12 of the FP64 oracle, tests/test_gpu_fullsize.py)"}
+
+
+# ------------------------------------------------------- time to tolerance
+PAPER_RULES = {"rel_grad_tol": 5e-4, "rel_df_tol": 1e-7, "step_tol": 5e-4}
+
+
+def bisection_start(w, local, levels=5):
+    """The paper's initialisation of large meshes (Sec. 4.3): a Monte Carlo
+    start of 2,562 generators (by rho^(1/2)), solved to the paper's stopping
+    rules, bisected (every Delaunay-edge midpoint added, N -> 4N - 6) and
+    solved again, up to `levels` bisections (2,562 -> 2,621,442 at 5), with
+    the workload's density, in the FP64 form.  Returns the bisected
+    generators and the chain's record."""
+    import torch
+    from paper_1709_06924_gb300.engine import Engine, sample_density
+    cand, u = I.mc_candidates(400000, 2025)
+    z = torch.from_numpy(sample_density(w.density, cand, u, 2562, 0.5)).cuda(local)
+    lv = []
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    rep = eng.lbfgs_solve(z, max_iter=max_iter, grad_tol=tol)
+    for level in range(levels):
+        with Engine(z.shape[0], w.density, lbfgs_m=w.lbfgs_m, device=local) as en:
+            r = en.lbfgs_solve(z, max_iter=2000, grad_tol=0.0, **PAPER_RULES)
+            lv.append({"n": int(z.shape[0]), "iters": r["iters"], "status": r["status"]})
+            z = en.bisect(z).contiguous()
     torch.cuda.synchronize()
-    t = time.perf_counter() - t0
-    eng.close()
-    return {"grad_tol": tol, "seconds": t, "iters": rep["iters"], "fevals": rep["fevals"],
-            "converged": bool(rep["converged"]), "grad_norm": rep["grad_norm"],
-            "grad_norm_over_F": rep["grad_norm"] / rep["energy"]}
+    return z.cpu().numpy(), {"levels": lv, "seconds": time.perf_counter() - t0, "n": int(z.shape[0])}
 
 
+def time_to_rule(w, z_host, local, prec, tuning, max_iter, **rules):
+    """Wall time (host clock around the synchronous solve, iterate on the
+    device) from z until a stopping rule holds; the reached F and ||g||/F."""
+    import torch
+    from paper_1709_06924_gb300.engine import Engine
+    with Engine(w.n, w.density, lbfgs_m=w.lbfgs_m, device=local, precision=prec) as eng:
+        if tuning:
+            eng.set_tuning(**tuning)
+        z = torch.from_numpy(z_host).cuda(local)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rep = eng.lbfgs_solve(z, max_iter=max_iter, **rules)
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+    return {"seconds": t, "iters": rep["iters"], "fevals": rep["fevals"], "converged": bool(rep["converged"]),
+            "energy": rep["energy"], "grad_norm": rep["grad_norm"], "grad_norm_over_F": rep["grad_norm"] / rep["energy"],
+            "status": rep["status"]}
+
+
+def served_time_to_rule(w, z_host, local, prec, max_iter, **rules):
+    """The same solve as one job of the continuous-batching server: time
+    from submission until the job is done (server clock)."""
+    from paper_1709_06924_gb300.engine import Server
+    with Server(max_generators=w.n, max_jobs=4, precision=prec, lbfgs_m=w.lbfgs_m, device=local) as srv:
+        jid = srv.submit(z_host, w.density, max_iter=max_iter, **rules)
+        while True:
+            running, queued = srv.step()
+            if running == 0 and queued == 0:
+                break
+        info = srv.job(jid)
+    r = info["report"]
+    return {"seconds": info["t_done"] - info["t_submit"], "iters": r["iters"], "fevals": r["fevals"],
+            "converged": bool(r["converged"]), "energy": r["energy"], "grad_norm": r["grad_norm"],
+            "grad_norm_over_F": r["grad_norm"] / r["energy"], "status": r["status"]}
+
+
+def run_time_to_tol(args, w, z_uniform, local, tunings):
+    """Time to tolerance at N = 2,621,442 for the three forms and the served
+    mixed form.  (1) The workload's literal ||grad E||_2 <= 1e-6 from the
+    seeded uniform start.  (2) The paper's stopping rules (Sec. 4.1: ||g||/F
+    <= 5e-4, |dF|/F < 1e-7, max movement <= 5e-4) from the paper's own start
+    for large meshes, the bisection chain (Sec. 4.3); at this size the
+    movement rule, an absolute 5e-4 set for N = 2,562 (spacing ~0.07), holds
+    from the first iteration (spacing 2.2e-3), so (3) the same rules without
+    it measure convergence."""
+    zb, chain = bisection_start(w, local)
+    out = {"start": "bisection chain 2,562 -> %d (Sec. 4.3), FP64 form, paper's rules at every level" % chain["n"],
+           "chain": chain, "max_iter": args.ttt_max_iter}
+    rules_nomove = {"rel_grad_tol": PAPER_RULES["rel_grad_tol"], "rel_df_tol": PAPER_RULES["rel_df_tol"]}
+    for prec in (2, 0, 1):
+        name = FORM_NAME[prec]
+        tu = tunings.get(prec)
+        out[name] = {
+            "grad_1e-6_from_uniform": time_to_rule(w, z_uniform, local, prec, tu, 50, grad_tol=1e-6),
+            "paper_rules": time_to_rule(w, zb, local, prec, tu, args.ttt_max_iter, grad_tol=0.0, **PAPER_RULES),
+            "paper_rules_without_movement": time_to_rule(w, zb, local, prec, tu, args.ttt_max_iter, grad_tol=0.0,
+                                                         **rules_nomove),
+        }
+    out["served_mixed"] = {"paper_rules_without_movement": served_time_to_rule(
+        w, zb, local, 1, args.ttt_max_iter, grad_tol=0.0, **rules_nomove)}
+    return out
+
+
+# ---------------------------------------------------------- other workloads
 def run_batched(args, local, prec, count=64):
     """64 independent problems (N log-uniform in [10,242, 655,362], each its own
     tanh cap) as one batch: autotuned, W warm-up and K timed lockstep LBFGS
@@ -269,9 +635,10 @@ def run_batched(args, local, prec, count=64):
         bt.close()
     units = sum(n * r["iters"] for n, r in zip(ns, reps))
     return {"problems": count, "n_total": int(sum(ns)), "n_min": int(min(ns)), "n_max": int(max(ns)),
-            "precision": "mixed" if prec else "fp64", "value": units / t, "unit": "generator-updates/s",
+            "precision": FORM_NAME[prec], "value": units / t, "unit": "generator-updates/s",
             "seconds": t, "iters": [r["iters"] for r in reps][:4] + ["..."],
-            "evaluations": st["evaluations"], "gpu_launches": st["kernel_launches"], "tuning": tuning,
+            "evaluations": st["evaluations"], "gpu_launches": st["kernel_launches"],
+            "launches_per_iteration": st["kernel_launches"] / max(args.steps, 1), "tuning": tuning,
             "tune_seconds": t_tune, "timing": "host wall clock around the synchronous batch solve",
             "statuses": sorted({r["status"] for r in reps})}
 
@@ -312,7 +679,8 @@ def run_serving(args, local, prec, count=None):
     inst = I.sample_batched_instances(count, args.seed + 7, n_lo=40962, n_hi=args.serve_n_hi)
     jobs = [(I.uniform_sphere(n, sd), d) for n, d, sd in inst]
     max_iter, tol = args.serve_max_iter, 1e-6
-    cap_n = max(4 * max(n for n, _, _ in inst), 2_000_000)
+    n_max = max(n for n, _, _ in inst)
+    cap_n = max(3 * n_max, 2_000_000)
     with Server(max_generators=cap_n, max_jobs=32, precision=prec, device=local) as srv:
         closed = serve_stream(srv, jobs, [0.0] * count, max_iter, tol)
         t_closed = max(r["t_done"] for r in closed) - min(r["t_submit"] for r in closed)
@@ -328,16 +696,15 @@ def run_serving(args, local, prec, count=None):
     span = max(r["t_done"] for r in recs) - min(r["t_submit"] for r in recs)
     units = sum(n * r["report"]["iters"] for (n, _, _), r in zip(inst, recs))
     iters = [r["report"]["iters"] for r in recs]
-    return {"jobs": count, "n_range": [40962, args.serve_n_hi], "precision": "mixed" if prec else "fp64",
-            "grad_tol": tol, "max_iter": max_iter,
+    return {"jobs": count, "n_range": [40962, args.serve_n_hi], "n_max_drawn": int(n_max),
+            "precision": FORM_NAME[prec], "grad_tol": tol, "max_iter": max_iter,
             "converged": int(sum(r["report"]["converged"] for r in recs)),
             "closed_loop_seconds": t_closed, "arrival_rate_per_s": rate, "offered_load": 0.8,
             "p50_time_to_tol_s": float(np.percentile(lat, 50)), "p99_time_to_tol_s": float(np.percentile(lat, 99)),
             "p50_queue_wait_s": float(np.percentile(wait, 50)), "makespan_s": span,
             "value": units / span, "unit": "generator-updates/s", "evaluations": evs,
             "iters_min_median_max": [int(min(iters)), int(np.median(iters)), int(max(iters))],
-            "note": "jobs and N range scaled down from the 2,000-job stream for a minutes-long run"
-                    if count < 2000 else None}
+            "note": "%d of the 2,000 jobs of the full stream" % count if count < 2000 else None}
 
 
 def run_table1(local):
@@ -362,8 +729,7 @@ def run_table1(local):
                     z = torch.from_numpy(z0.copy()).cuda(local)
                     torch.cuda.synchronize()
                     t0 = time.perf_counter()
-                    r = en.lbfgs_solve(z, max_iter=2000, grad_tol=0.0, rel_grad_tol=5e-4, rel_df_tol=1e-7,
-                                       step_tol=5e-4, method=method)
+                    r = en.lbfgs_solve(z, max_iter=2000, grad_tol=0.0, method=method, **PAPER_RULES)
                     torch.cuda.synchronize()
                     t = time.perf_counter() - t0
                     cq, tq = en.mesh_quality(z)
@@ -382,8 +748,7 @@ def run_bisection_chain(local, levels=4):
     """The paper's large-scale run (Sec. 4.3): from a converged 2,562-generator
     SCVT, bisect (every Delaunay-edge midpoint added, N -> 4N - 6) and
     optimise again, up to 655,362 generators, with the paper's stopping
-    rules (movement 5e-4, ||g||/F <= 5e-4, |dF|/F < 1e-7, 2,000 iterations)
-    and M = 7; FP64 form, the whole chain timed on the host clock."""
+    rules and M = 7; FP64 form, the whole chain timed on the host clock."""
     import torch
     from paper_1709_06924_gb300.engine import Engine, sample_density
     out = {}
@@ -398,8 +763,7 @@ def run_bisection_chain(local, levels=4):
                 n = z.shape[0]
                 with Engine(n, dens, lbfgs_m=7, device=local) as en:
                     tl = time.perf_counter()
-                    r = en.lbfgs_solve(z, max_iter=2000, grad_tol=0.0, rel_grad_tol=5e-4, rel_df_tol=1e-7,
-                                       step_tol=5e-4)
+                    r = en.lbfgs_solve(z, max_iter=2000, grad_tol=0.0, **PAPER_RULES)
                     torch.cuda.synchronize()
                     lv.append({"n": n, "iters": r["iters"], "fevals": r["fevals"], "energy": r["energy"],
                                "grad_norm": r["grad_norm"], "seconds": time.perf_counter() - tl,
@@ -415,6 +779,41 @@ def run_bisection_chain(local, levels=4):
     return out
 
 
+def guarded(fn, *a, **kw):
+    """A secondary measurement: its failure is reported in the line, not fatal."""
+    try:
+        return fn(*a, **kw)
+    except Exception as ex:
+        return {"error": repr(ex)}
+
+
+def summary_of(line):
+    """The figures that compare the forms, compactly, for the end of the line."""
+    s = {"fp64_form_M_per_s": line["value"] / 1e6, "ms_per_step": line["ms_per_step"],
+         "roofline_frac": line["roofline"]["frac"],
+         "roofline_alg_frac": (line["roofline"].get("algorithmic") or {}).get("frac")}
+    for f in line.get("other_forms") or []:
+        s["%s_M_per_s" % f["precision"]] = f["value"] / 1e6
+    tt = line.get("time_to_tol")
+    if tt and "error" not in tt:
+        for name in ("plain", "fp64", "mixed"):
+            r = tt.get(name, {}).get("paper_rules_without_movement")
+            if r:
+                s["ttt_%s_s" % name] = r["seconds"]
+                s["ttt_%s_iters" % name] = r["iters"]
+        r = tt.get("served_mixed", {}).get("paper_rules_without_movement")
+        if r:
+            s["ttt_served_mixed_s"] = r["seconds"]
+    if line.get("roofline_two_loop"):
+        s["two_loop_frac"] = line["roofline_two_loop"]["frac"]
+    sv = line.get("serving")
+    if sv and "error" not in sv:
+        s["serve_p50_s"], s["serve_p99_s"] = sv["p50_time_to_tol_s"], sv["p99_time_to_tol_s"]
+    if line.get("cpu_baseline"):
+        s["oracle_M_per_s"] = line["cpu_baseline"]["value"] / 1e6
+    return s
+
+
 def run_ours(args, w):
     import torch
     ws, rank, local = dist_env()
@@ -426,25 +825,18 @@ def run_ours(args, w):
 
     seed = args.seed + rank          # each replica solves its own instance
     z_host = I.uniform_sphere(w.n, seed)
-    prec = 1 if args.precision == "mixed" else 0
-    eng = Engine(w.n, w.density, lbfgs_m=w.lbfgs_m, device=local, precision=prec)
-    z = torch.from_numpy(z_host).cuda(local)
+    prec = FORMS[args.precision]
+    sms = device_sms(local)
 
     def barrier():
         if ws > 1:
             torch.distributed.barrier()
 
-    # warm-up: W LBFGS iterations from the seeded start (history is kept);
-    # then the library's autotuner picks launch shapes at the warmed iterate,
-    # the state the timed steps run in (a fixed --tuning applies from the
-    # start; results do not depend on either)
-    if args.tuning:
-        tuning = {prec: pick_tuning(args, eng, z)}
-    eng.lbfgs_solve(z, max_iter=args.warmup, grad_tol=0.0)
-    if not args.tuning:
-        tuning = {prec: pick_tuning(args, eng, z)}
-    eng.reset_stats()
-    eng.set_profiling(True)
+    # headline form: W LBFGS iterations from the seeded start (history kept),
+    # the library's autotuner at the warmed iterate (the state the timed steps
+    # run in; a fixed --tuning applies from the start), then K timed steps
+    tunings = {}
+    eng, z, tunings[prec] = run_form(args, w, z_host, local, prec)
     try:
         uuid = str(torch.cuda.get_device_properties(local).uuid)
     except Exception:
@@ -457,6 +849,8 @@ def run_ours(args, w):
     rep, t = timed_steps(eng, z, args.steps)
     barrier()
     clocks.stop()
+    csum = clocks.summary()
+    mhz, clock_src = max_sm_mhz(csum)
     st = eng.stats()
     iters = rep["iters"]
     units, t_max = combine_ranks(w.n * iters, t, device=torch.device("cuda", local))
@@ -467,7 +861,8 @@ def run_ours(args, w):
     # are timed on three further evaluations of the same iterate with one
     # pipeline
     quad_ms, topo_ms, stq = one_pipeline_kernel_ms(eng, z)
-    roofline = roofline_of(prec, w, quad_ms, topo_ms, stq, tuning[prec]["topo_cell_lanes"])
+    roofline = roofline_of(prec, w, quad_ms, topo_ms, stq, tunings[prec]["topo_cell_lanes"], sms, mhz, clock_src)
+    eng.close()
 
     # end to end through the C ABI with host buffers: a second engine replays
     # the same warm-up (evaluations are deterministic, so it reaches the same
@@ -477,7 +872,7 @@ def run_ours(args, w):
     e2e = None
     if not args.no_e2e:
         eng2 = Engine(w.n, w.density, lbfgs_m=w.lbfgs_m, device=local, precision=prec)
-        eng2.set_tuning(**tuning[prec])
+        eng2.set_tuning(**tunings[prec])
         z2 = torch.from_numpy(z_host).cuda(local)
         eng2.lbfgs_solve(z2, max_iter=args.warmup, grad_tol=0.0)
         zp = torch.empty((w.n, 3), dtype=torch.float64, pin_memory=True)
@@ -500,68 +895,29 @@ def run_ours(args, w):
         e2e = {"value": ue / te, "unit": "generator-updates/s",
                "h2d_bytes_per_step": w.n * 24, "d2h_bytes_per_step": w.n * 24,
                "same_iterates_as_device_run": same}
+    del z
 
-    # the other precision form on the same workload, same W and K
-    other = None
+    # the other precision forms on the same workload, same W and K
+    others = []
     if not args.no_other_form:
-        oprec = 1 - prec
-        eng3 = Engine(w.n, w.density, lbfgs_m=w.lbfgs_m, device=local, precision=oprec)
-        z3 = torch.from_numpy(z_host).cuda(local)
-        if args.tuning:
-            tuning[oprec] = pick_tuning(args, eng3, z3)
-        eng3.lbfgs_solve(z3, max_iter=args.warmup, grad_tol=0.0)
-        if not args.tuning:
-            tuning[oprec] = pick_tuning(args, eng3, z3)
-        eng3.reset_stats()
-        eng3.set_profiling(True)
-        torch.cuda.synchronize()
-        rep3, t3 = timed_steps(eng3, z3, args.steps)
-        st3 = eng3.stats()
-        q3, tp3, stq3 = one_pipeline_kernel_ms(eng3, z3)
-        eng3.close()
-        u3, t3 = combine_ranks(w.n * rep3["iters"], t3, device=torch.device("cuda", local))
-        other = {"precision": "mixed" if oprec else "fp64", "dtype": "f32/f64" if oprec else "f64+f32x2",
-                 "value": u3 / t3, "ms_per_step": 1e3 * t3 / max(rep3["iters"], 1),
-                 "roofline": roofline_of(oprec, w, q3, tp3, stq3, tuning[oprec]["topo_cell_lanes"]),
-                 "eval_ms_avg": st3["eval_ms"] / max(st3["evaluations"], 1), "tuning": tuning[oprec]}
+        for op in (p for p in (0, 1, 2) if p != prec):
+            e3, z3, tunings[op] = run_form(args, w, z_host, local, op)
+            r3, t3 = timed_steps(e3, z3, args.steps)
+            rec, _ = form_record(args, w, e3, z3, op, tunings[op], r3, t3, sms, mhz, clock_src, local)
+            e3.close()
+            del z3
+            others.append(rec)
+        others_err = guarded(per_cell_error, w, z_host, local, 1)
+    else:
+        others_err = None
 
     batched = None
     if not args.no_batched:
-        try:
-            batched = {"fp64": run_batched(args, local, 0), "mixed": run_batched(args, local, 1)}
-        except Exception as ex:  # reported, not fatal to the headline line
-            batched = {"error": repr(ex)}
-
-    serving = None
-    if not args.no_serving:
-        try:
-            serving = run_serving(args, local, prec)
-        except Exception as ex:  # reported, not fatal to the headline line
-            serving = {"error": repr(ex)}
-
-    table1 = None
-    if not args.no_table1:
-        try:
-            table1 = run_table1(local)
-        except Exception as ex:  # reported, not fatal to the headline line
-            table1 = {"error": repr(ex)}
-
-    chain = None
-    if not args.no_chain:
-        try:
-            chain = run_bisection_chain(local)
-        except Exception as ex:  # reported, not fatal to the headline line
-            chain = {"error": repr(ex)}
-
-    ttt = None
-    if not args.no_time_to_tol:
-        for pr in (0, 1):
-            if pr not in tuning:
-                with Engine(w.n, w.density, lbfgs_m=w.lbfgs_m, device=local, precision=pr) as et:
-                    zt_ = torch.from_numpy(z_host).cuda(local)
-                    tuning[pr] = pick_tuning(args, et, zt_)
-        ttt = {"fp64": time_to_tolerance(w, z_host, local, 0, tuning[0]),
-               "mixed": time_to_tolerance(w, z_host, local, 1, tuning[1])}
+        batched = {"fp64": guarded(run_batched, args, local, 0), "mixed": guarded(run_batched, args, local, 1)}
+    serving = guarded(run_serving, args, local, 1) if not args.no_serving else None
+    table1 = guarded(run_table1, local) if not args.no_table1 else None
+    chain = guarded(run_bisection_chain, local) if not args.no_chain else None
+    ttt = guarded(run_time_to_tol, args, w, z_host, local, tunings) if not args.no_time_to_tol else None
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -572,170 +928,36 @@ def run_ours(args, w):
             "metric": "generator-updates/s", "value": value, "unit": "generator-updates/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_max / max(iters, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32/f64" if prec else "f64+f32x2", "data": "synthetic",
+            "dtype": DTYPE[prec], "data": "synthetic",
             "config": {"workload": w.name, "n_generators": w.n, "density": "tanh cap",
                        "gamma": w.density.gamma, "alpha": w.density.alpha, "beta": w.density.beta,
                        "lbfgs_m": w.lbfgs_m, "quadrature": "7-point per sub-triangle", "seed": args.seed,
                        "precision": args.precision, "parallelism": "replicas" if ws > 1 else "single",
                        "l2": "inputs larger than L2 (history %d MB per step)" % (2 * w.lbfgs_m * w.n * 24 >> 20),
-                       "iters_timed": iters, "fevals_timed": rep["fevals"], "tuning": tuning[prec]},
+                       "iters_timed": iters, "fevals_timed": rep["fevals"], "tuning": tunings[prec]},
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "clocks": clocks.summary(),
+            "clocks": csum,
             "gpu_launches": st["kernel_launches"],
-            "other_form": other,
-            "time_to_tol": ttt,
-            "batched": batched,
-            "serving": serving,
-            "paper_table1": table1,
-            "bisection_chain": chain,
             "knn_retries": st["knn_retries"],
             "ambiguous": st["ambiguous"],
             "eval_ms_avg": st["eval_ms"] / max(st["evaluations"], 1),
             "lbfgs_ms_total": st["lbfgs_ms"],
             "fevals_per_s": st["evaluations"] / t_max if t_max > 0 else None,
             "roofline_two_loop": two_loop_roofline(w, args.warmup, iters, st["lbfgs_ms"]),
+            "other_forms": others,
+            "mixed_error_vs_fp64_form": others_err,
+            "batched": batched,
+            "serving": serving,
+            "paper_table1": table1,
+            "bisection_chain": chain,
+            "time_to_tol": ttt,
         }
+        line["summary"] = summary_of(line)
         print(json.dumps(line), flush=True)
-    eng.close()
     if ws > 1:
         torch.distributed.destroy_process_group()
-
-
-# FP64 exp per call in DFMA equivalents (measured like the other per-call costs)
-EXP_DFMA = 17.9
-
-
-def fp64_flops_per_generator(kind: int, series_frac: float = 0.0, series_len: float = 0.0) -> float:
-    """FP64 work of the quadrature kernel per generator, in flop equivalents.
-
-    Per Voronoi edge the method integrates two signed sub-triangles (Sec.
-    3.2.2): per sub-triangle the Van Oosterom-Strackee area (differences,
-    cross and dot products: 38 flops, one atan2) and 7 rule points; per point
-    the projected point (combination, norm, rsqrt, scale: 37 + rsqrt), the
-    density, the weight and the accumulation of m, c and |p - z|^2 (24).  The
-    tanh cap evaluated directly costs a cross product, a norm and a dot (19),
-    sqrt, atan2, exp and a division (its logistic form) (+5); from the
-    cell's Taylor series it costs a dot, a difference and a Horner sweep of
-    series_len terms (6 + 2 series_len), for the fraction series_frac of the
-    cells that use one (the series themselves are built by a separate
-    kernel).  X3 costs 6.  A transcendental is charged what it costs on this
-    GPU in FMA-pipe time (per-call costs measured with CUDA events, in DFMA
-    equivalents x 2 flop).  The cell of a generator has 6 edges on average
-    (Euler: 2E = 6N - 12).
-    """
-    rsqrt, sqrt, atan2, exp, div = 2 * 6.9, 2 * 9.6, 2 * 41.0, 2 * EXP_DFMA, 2 * 10.4
-    direct = {0: 0.0, 1: 6.0, 2: 24.0 + sqrt + atan2 + exp + div, 3: 28.0 + sqrt + atan2 + exp + div}[kind]
-    dens = direct
-    if kind >= 2:
-        dens = series_frac * (6.0 + 2.0 * series_len) + (1.0 - series_frac) * direct
-    point = 37.0 + rsqrt + 24.0 + dens
-    subtri = 38.0 + atan2 + 7 * point
-    mu = 11.0 + rsqrt
-    return 6.0 * (2 * subtri + mu)
-
-
-def measured_hbm_gbs():
-    """HBM copy bandwidth measured on this machine (MEASURED_PEAKS.json), else
-    the fallback figure."""
-    try:
-        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
-            return float(json.load(f)["hbm_gbs"]), "measured"
-    except Exception:
-        return 6800.0, "fallback"
-
-
-def two_loop_roofline(w, warmup, iters, lbfgs_ms):
-    """HBM roofline of the two-loop recursion (Sec. 2.2.2 with diag(h) as the
-    initial inverse Hessian): algorithmic traffic per generator (4c + 2) x 24
-    bytes with c stored pairs (each history vector read twice, g read, q
-    written), c = min(warm-up + i, m) in timed iteration i, over the CUDA-event
-    time of the two-loop launches in the timed steps.  The fused kernels read
-    and write q once per pair step, 72 + 192 c bytes per generator."""
-    if not iters or lbfgs_ms <= 0:
-        return None
-    counts = [min(warmup + i, w.lbfgs_m) for i in range(iters)]
-    alg = sum((4 * c + 2) * 24 for c in counts) * w.n
-    impl = sum(72 + 192 * c for c in counts) * w.n
-    peak, src = measured_hbm_gbs()
-    achieved = alg / (lbfgs_ms * 1e-3) / 1e9
-    return {"bound": "hbm", "kernel": "two-loop (k_neg, k_axpy, k_finish_scalar)", "achieved": achieved,
-            "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
-            "algorithmic_bytes": alg, "implementation_bytes": impl,
-            "implementation_gbs": impl / (lbfgs_ms * 1e-3) / 1e9, "peak_source": src, "pairs_per_iteration": counts}
-
-
-def fp64_peak_tflops() -> float:
-    return 152 * 2 * 2 * 2.07e9 / 1e12
-
-
-# Instruction issue is what bounds the double-float quadrature and the
-# topology pass: each of the 152 SMs' four schedulers issues at most one warp
-# instruction per clock (2.07 GHz), 1.2586e12 warp instructions per second.
-# The work per unit is the instruction count ncu measured (one-pass
-# smsp__inst_executed.sum) for a launch of the timed steps of this bench at
-# N = 2,621,442, divided by N (profiles/launches_tanh_2621442.md); the
-# topology pass's count depends on its lanes per cell.
-ISSUE_PEAK = 152 * 4 * 2.07e9
-QUAD_INST_PER_GENERATOR = 4536632457 / 2621442
-TOPO_INST_PER_CELL = {32: 3153936979 / 2621442, 16: 1873542833 / 2621442}
-
-
-def one_pipeline_kernel_ms(eng, z, evals=3):
-    """Average CUDA-event time of the quadrature and of the first topology
-    pass over `evals` evaluations of z with one cell pipeline (the engine's
-    tuning is restored afterwards; stats are reset)."""
-    tsave = eng.tuning()
-    eng.set_tuning(**dict(tsave, chunks=1))
-    eng.set_profiling(True)
-    eng.evaluate(z)
-    eng.reset_stats()
-    for _ in range(evals):
-        eng.evaluate(z)
-    st = eng.stats()
-    eng.set_tuning(**tsave)
-    quad = st["cell_kernel_ms"] / max(st["cell_kernel_timed"], 1)
-    topo = st["topo_kernel_ms"] / max(st["topo_kernel_timed"], 1)
-    return quad, topo, st
-
-
-def roofline_of(prec, w, quad_ms, topo_ms, st, lanes=32):
-    """Roofline of the step's dominant kernel: the double-float quadrature in
-    the FP64 form, the topology pass in the mixed form; both issue-bound."""
-    if prec == 0:
-        sfrac = st["series_cells"] / max(w.n * st["evaluations"], 1)
-        slen = st["series_terms"] / max(st["series_cells"], 1)
-        flops_gen = fp64_flops_per_generator(w.density.kind, sfrac, slen)
-        achieved = w.n * QUAD_INST_PER_GENERATOR / (quad_ms * 1e-3) / 1e12
-        return {"bound": "alu", "kernel": "k_quad", "achieved": achieved, "peak": ISSUE_PEAK / 1e12,
-                "unit": "Twarp-inst/s", "frac": achieved * 1e12 / ISSUE_PEAK, "traffic": quad_traffic_bytes(w.n),
-                "avg_launch_ms": quad_ms, "inst_per_generator": QUAD_INST_PER_GENERATOR,
-                "fp64_equivalent_tflops": w.n * flops_gen / (quad_ms * 1e-3) / 1e12,
-                "fp64_flop_equivalents_per_generator": flops_gen,
-                "fp64_pipe_peak_tflops": fp64_peak_tflops(),
-                "series_cell_fraction": sfrac, "series_terms_avg": slen,
-                "peak_source": "instruction issue: 152 SMs x 4 schedulers x 1 warp-instruction/clk x 2.07 GHz",
-                "work_source": "ncu smsp__inst_executed.sum of a k_quad launch of the timed steps at "
-                               "N = 2,621,442, per generator (double-float arithmetic: FP32 pairs, FP64 for "
-                               "per-edge offsets)",
-                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_quad launch "
-                                  "at N = 163,842, scaled by N (profiles/k_quad_tanh_163842.md)"}
-    ipc = TOPO_INST_PER_CELL[lanes]
-    achieved = w.n * ipc / (topo_ms * 1e-3) / 1e12
-    return {"bound": "alu", "kernel": "k_topo_warp", "achieved": achieved, "peak": ISSUE_PEAK / 1e12,
-            "unit": "Twarp-inst/s", "frac": achieved * 1e12 / ISSUE_PEAK, "traffic": None,
-            "avg_launch_ms": topo_ms, "quad_kernel_ms": quad_ms, "inst_per_cell": ipc, "lanes_per_cell": lanes,
-            "peak_source": "instruction issue: 152 SMs x 4 schedulers x 1 warp-instruction/clk x 2.07 GHz",
-            "work_source": "ncu smsp__inst_executed.sum of a k_topo_warp launch of the timed steps at "
-                           "N = 2,621,442, per cell"}
-
-
-def quad_traffic_bytes(n: int):
-    """DRAM bytes of one k_quad launch: ncu at N = 163,842 (118.31 MB read +
-    19.11 MB written, tanh cap, density series on), scaled by the number of
-    generators."""
-    return (118.309376e6 + 19.114240e6) * n / 163842
 
 
 def main():

@@ -81,14 +81,15 @@ typedef struct {
                              double-float arithmetic (pairs of FP32 values, about 48 bits)
                              relative to z_i, from FP64 offsets; corners that are poorly
                              conditioned or far from z_i, and edges reaching beyond chord 0.03
-                             of z_i, in FP64; the tanh-cap density from an FP64 per-cell Taylor
-                             series (direct formula where the series is not validated).
+                             of z_i, in FP64; the tanh-cap density from a table of FP64 Taylor
+                             series in x_c.p built once per handle (direct formula where no
+                             series is validated over the edge's range).
                              Results within 1e-12 (relative) of an FP64 evaluation.
                            1 = mixed: corners and quadrature in FP32 local coordinates (offsets
                              from z_i), density in FP32; error stated per quantity (about 1e-5
                              relative for m_i, c_i and F_i).
                            2 = plain FP64: corners, rule points and density in FP64 arithmetic
-                             (the density by the same FP64 series / direct formula as form 0). */
+                             (the density from the same FP64 series table / direct formula). */
     int lbfgs_m;        /* number of (s, y) pairs kept, 0..32 (the paper uses 7) */
     int knn_k0;         /* first-pass neighbour count, 0 = default (32); 8..32 */
     int knn_kmax;       /* largest neighbour count of the retry passes, 0 = default (128) */
@@ -142,7 +143,8 @@ typedef struct {
     double lbfgs_ms;            /* device time of the two-loop / update kernels (profiling on) */
     int64_t cell_kernel_timed;  /* first-pass launches included in cell_kernel_ms */
     int64_t bytes_device;       /* device memory held by the handle */
-    int64_t series_cells;       /* FP64 form: cells whose density came from their Taylor series */
+    int64_t series_edges;       /* FP64 forms: quadrature edges whose density came from the density
+                                   table's Taylor series (the others evaluate it directly) */
     int64_t series_terms;       /* ... and the sum of those series' lengths */
     double topo_kernel_ms;      /* device time of the first topology pass (profiling on, one pipeline) */
     int64_t topo_kernel_timed;  /* first topology passes included in topo_kernel_ms */
@@ -211,7 +213,7 @@ scvt_status scvt_lbfgs_direction(scvt_handle *h, const double *g, const double *
  * host that forbids cudaMalloc after start-up).  The paper has no
  * counterpart: this is a deployment variant of scvt_energy_grad.
  * It needs no handle and allocates nothing: its scratch is one fixed array
- * in device memory (about 21.9 MB, held on every GPU that loads the library
+ * in device memory (about 16.4 MB, held on every GPU that loads the library
  * until the process exits), sized for n <= SCVT_STATIC_MAX_N.
  * n: generators (4 <= n <= SCVT_STATIC_MAX_N, else SCVT_ERR_INVALID before
  * any device work).  rho: host.  z: N x 3 device.  cuda_stream: cudaStream_t

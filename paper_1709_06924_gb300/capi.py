@@ -49,7 +49,7 @@ class scvt_stats(C.Structure):
     _fields_ = [("evaluations", C.c_int64), ("cell_launches", C.c_int64), ("kernel_launches", C.c_int64),
                 ("knn_retries", C.c_int64), ("ambiguous", C.c_int64), ("cell_kernel_ms", C.c_double),
                 ("eval_ms", C.c_double), ("lbfgs_ms", C.c_double), ("cell_kernel_timed", C.c_int64),
-                ("bytes_device", C.c_int64), ("series_cells", C.c_int64), ("series_terms", C.c_int64),
+                ("bytes_device", C.c_int64), ("series_edges", C.c_int64), ("series_terms", C.c_int64),
                 ("topo_kernel_ms", C.c_double), ("topo_kernel_timed", C.c_int64)]
 
 

@@ -45,8 +45,8 @@ struct Bufs {
     float4 *zf = nullptr, *zl = nullptr, *zll = nullptr;
     P4 *cvx = nullptr;
     int *cdeg = nullptr, *cnb = nullptr, *eoff = nullptr, *ecell = nullptr, *escan = nullptr;
-    double *eacc = nullptr, *ser = nullptr;
-    int *serK = nullptr;
+    double *eacc = nullptr;
+    void *tab = nullptr;                     // density table (FP64 forms, tanh-cap densities)
     float4 *vo = nullptr;
     int *bin_of = nullptr, *count = nullptr, *start = nullptr, *cursor = nullptr, *scan_tmp = nullptr;
     int *sidx = nullptr, *list1 = nullptr, *list2 = nullptr;
@@ -66,6 +66,7 @@ struct scvt_handle {
     Pipes pipes;
     cudaStream_t stream = nullptr;
     Bufs b;
+    DensTab tab{};                 // the density table in b.tab (M = 0: none)
     DevStatus *st_host = nullptr;  // pinned
     int64_t bytes = 0;
     // history ring: slot order (oldest first) and one spare slot
@@ -165,6 +166,7 @@ scvt_status evaluate_dev(scvt_handle *H, const double *zdev, double *grad, doubl
     g.bstart = B.start;
     g.rho0 = to_device_density(H->cfg.rho);
     g.rho0f = to_density32(g.rho0);
+    g.tab0 = H->tab;
     g.fan = H->cfg.decomposition;
     if (!H->radius_valid) {
         CK(cudaMemsetAsync(B.radius, 0, sizeof(float) * n, s), "reset radius hints");
@@ -191,8 +193,6 @@ scvt_status evaluate_dev(scvt_handle *H, const double *zdev, double *grad, doubl
     cb.scan_tmp = B.escan;
     cb.eacc = B.eacc;
     cb.vo = B.vo;
-    cb.ser = B.ser;
-    cb.serK = B.serK;
     cell_passes(g, out, cb, B.list1, B.list2, B.st, H->cfg.precision, H->tune, s,
                 H->profiling ? H->ev_cell0 : nullptr, H->profiling ? H->ev_cell1 : nullptr, L,
                 &H->stats.cell_launches, &H->pipes, H->profiling ? H->ev_topo : nullptr);
@@ -206,7 +206,7 @@ scvt_status evaluate_dev(scvt_handle *H, const double *zdev, double *grad, doubl
     H->stats.evaluations++;
     H->stats.knn_retries += st.retry_count[0];
     H->stats.ambiguous += (int64_t)st.ambiguous;
-    H->stats.series_cells += (int64_t)st.ser_cells;
+    H->stats.series_edges += (int64_t)st.ser_edges;
     H->stats.series_terms += (int64_t)st.ser_terms;
     if (st.flags & FLAG_BAD_POINT)
         return fail(H, SCVT_ERR_INVALID, "a generator is not finite or not on the unit sphere (| |z|^2 - 1 | > 2e-12)");
@@ -330,7 +330,7 @@ void scvt_destroy(scvt_handle *H) {
     if (!H) return;
     Bufs &b = H->b;
     void *ptrs[] = {b.z, b.zt, b.g, b.gt, b.h, b.ht, b.fc, b.q, b.yv, b.nrm, b.mass, b.moment, b.stage_a, b.stage_b,
-                    b.partials, b.scal, b.rho, b.gamma, b.hist, b.zs, b.zf, b.zl, b.zll, b.cvx, b.cnb, b.cdeg, b.eoff, b.ecell, b.escan, b.eacc, b.vo, b.ser, b.serK, b.bin_of, b.count, b.start, b.cursor, b.scan_tmp,
+                    b.partials, b.scal, b.rho, b.gamma, b.hist, b.zs, b.zf, b.zl, b.zll, b.cvx, b.cnb, b.cdeg, b.eoff, b.ecell, b.escan, b.eacc, b.vo, b.tab, b.bin_of, b.count, b.start, b.cursor, b.scan_tmp,
                     b.sidx, b.list1, b.list2, b.deg, b.radius, b.st};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -388,12 +388,18 @@ scvt_status scvt_create(const scvt_config *cfg, void *cuda_stream, scvt_handle *
     AL(b.cdeg, n); AL(b.eoff, n + 1); AL(b.ecell, 6 * (size_t)n); AL(b.escan, scan_tmp_ints(n));
     AL(b.eacc, 5 * 6 * (size_t)n);
     if (cfg->precision == 1) AL(b.vo, (size_t)n * kCellSlots);
-    if (cfg->precision != 1) { AL(b.ser, (size_t)n * kSerWords); AL(b.serK, n); }
+    const Density dens = to_device_density(cfg->rho);
+    const int tabM = (cfg->precision != 1 && dens.kind >= 2) ? dens_table_centres(n) : 0;
+    if (tabM > 0 && e == cudaSuccess) {
+        e = cudaMalloc(&b.tab, dens_table_bytes(tabM));
+        if (e == cudaSuccess) H->bytes += (int64_t)dens_table_bytes(tabM);
+    }
     AL(b.bin_of, n); AL(b.count, nbins); AL(b.start, nbins + 1); AL(b.cursor, nbins);
     AL(b.scan_tmp, 2 * (nbins / 2048 + 64) + 64);
     AL(b.sidx, n); AL(b.list1, n); AL(b.list2, n); AL(b.deg, n); AL(b.radius, n);
     AL(b.st, 1);
 #undef AL
+    if (e == cudaSuccess && tabM > 0) e = dens_table_build(dens, tabM, b.tab, &H->tab, H->stream);
     if (e == cudaSuccess) e = cudaMallocHost((void **)&H->st_host, sizeof(DevStatus));
     if (e == cudaSuccess) e = pipes_create(H->pipes, kMaxChunks - 1);
     cudaEvent_t *evs[] = {&H->ev_cell0, &H->ev_cell1, &H->ev_e0, &H->ev_e1, &H->ev_l0, &H->ev_l1, &H->ev_topo[0],

@@ -23,6 +23,7 @@
 // Results are written at the generator's original index, so that every
 // later reduction runs in index order and is independent of the binning.
 #include <math.h>
+#include <string.h>
 
 #include <algorithm>
 
@@ -593,15 +594,6 @@ __device__ __forceinline__ double rho_direct(const Density &r, double inv_alpha,
     return rv;
 }
 
-// Per-cell Taylor series of the tanh-cap density in u = x_c.p - x_c.z_i
-// (k_rho_series): up to kSerMax coefficients, then the expansion point x_c.z_i.
-constexpr int kSerMax = 20;
-constexpr int kSerStride = kSerWords;  // coefficients, expansion point, double-float pairs
-static_assert(kSerWords >= 2 * kSerMax + 2, "series buffer too short");
-__constant__ double kInv[kSerMax + 1] = {0.0,        1.0,        1.0 / 2,  1.0 / 3,  1.0 / 4,  1.0 / 5,  1.0 / 6,
-                                         1.0 / 7,    1.0 / 8,    1.0 / 9,  1.0 / 10, 1.0 / 11, 1.0 / 12, 1.0 / 13,
-                                         1.0 / 14,   1.0 / 15,   1.0 / 16, 1.0 / 17, 1.0 / 18, 1.0 / 19, 1.0 / 20};
-
 __device__ __forceinline__ double horner(const double *__restrict__ cf, int K, double u) {
     double r = cf[K - 1];
     for (int j = K - 2; j >= 0; --j) r = fma(r, u, cf[j]);
@@ -634,11 +626,12 @@ __device__ __forceinline__ V3 midpoint_offset(V3 zi, double aA1, V3 zj) {
 
 // signed spherical triangle (A, A + ob, A + oc) with the 7-point rule; A = z_i,
 // ob, oc: offsets of the other two corners from z_i, aA1 = |A|^2 - 1.
-// inv_alpha: 1/alpha of the tanh cap.  ser / K: the cell's density series
-// (K = 0: evaluate the density directly).  Accumulates m, the moment relative
-// to z_i (sum w rho (p - z_i); the caller adds m z_i) and the energy.
+// inv_alpha: 1/alpha of the tanh cap.  cf / K / cj: the density's series
+// about x_c.p = cj from the density table (K = 0: evaluate the density
+// directly).  Accumulates m, the moment relative to z_i (sum w rho (p - z_i);
+// the caller adds m z_i) and the energy.
 __device__ __forceinline__ void tri(const Density &r, double inv_alpha, V3 A, double aA1, V3 ob, V3 oc, Acc &acc,
-                                    const double *ser = nullptr, int K = 0) {
+                                    const double *cf = nullptr, int K = 0, double cj = 0.0) {
     // Van Oosterom-Strackee with B = A + ob, C = A + oc:
     // det[A,B,C] = A.(ob x oc), 1 + A.B + B.C + C.A = 4 + 3 (|A|^2 - 1) + 2 A.(ob + oc) + ob.oc
     const double det = dot(A, crs(ob, oc));
@@ -655,7 +648,7 @@ __device__ __forceinline__ void tri(const Density &r, double inv_alpha, V3 A, do
         area = 2.0 * atan2(det, den);
     }
     const V3 xc = mk(r.xc0, r.xc1, r.xc2);
-    const double u0 = (K > 0) ? dot(xc, A) - ser[kSerMax] : 0.0;
+    const double u0 = (K > 0) ? dot(xc, A) - cj : 0.0;
 #pragma unroll 1
     for (int k = 0; k < 7; ++k) {
         // rule point x = A + b1 ob + b2 oc, projected: p - A from the offsets
@@ -668,7 +661,7 @@ __device__ __forceinline__ void tri(const Density &r, double inv_alpha, V3 A, do
             const double pz = A.z + dp.z, z2 = pz * pz;
             rv = (1.0 - r.gamma) * z2 * z2 + r.gamma;
         } else if (K > 0) {
-            rv = horner(ser, K, u0 + dot(xc, dp));
+            rv = horner(cf, K, u0 + dot(xc, dp));
         } else {
             rv = rho_direct(r, inv_alpha, add(A, dp));
         }
@@ -1645,91 +1638,66 @@ __global__ void __launch_bounds__(256) k_corners(Grid g, CellBuf cb, Span sp) {
     }
 }
 
-// -------------------------------------------- density series per cell
-// The tanh cap depends on p only through c = x_c.p, and inside one cell c
-// stays within a small interval around c_i = x_c.z_i.  Its Taylor series in
-// u = c - c_i is built once per cell by power-series arithmetic on the exact
-// composition rho = gamma + (1 - gamma) / (1 + exp(-x)), x = 2 (beta - acos c)
-// / alpha:  (1 - (c_i + u)^2)^(-1/2) by the binomial recurrence of
-// h^(-1/2), h = 1 + tau1 u + tau2 u^2, integrated to acos; exp of a series;
-// the reciprocal of a series; squared twice for the 4th power.  The number
-// of terms K is the first at which two successive terms fall below 1e-17 of
-// the value over |u| <= U (U bounds |u| over the cell's corners, edge
-// midpoints and the rule points between them); the truncated series is then
-// compared with the direct formula at the cell's two corners of extreme u
-// and used only if both agree to 1e-14 (the direct formula's own rounding
-// sensitivity is ~1e-14 for alpha = 0.05; the parity budget is 1e-12).
-// Otherwise (cells near the cap
-// centre or its antipode, where acos is singular, or cells wide against
-// alpha) K = 0 and the quadrature evaluates the density directly.
-__device__ __forceinline__ void count_series(int K, DevStatus *st) {
-    const unsigned cells = __reduce_add_sync(0xffffffffu, K > 0 ? 1u : 0u);
-    const unsigned terms = __reduce_add_sync(0xffffffffu, (unsigned)K);
-    if ((threadIdx.x & 31) == 0 && cells) {
-        atomicAdd(&st->ser_cells, (unsigned long long)cells);
-        atomicAdd(&st->ser_terms, (unsigned long long)terms);
-    }
+// ------------------------------------------------------ density table
+// The tanh cap depends on p only through c = x_c.p.  At each centre c_j =
+// cos(theta_j) the table holds the Taylor series of rho in u = c - c_j, built
+// by power-series arithmetic on the exact composition rho = gamma + (1 -
+// gamma) / (1 + exp(-x)), x = 2 (beta - acos c) / alpha:  (1 - (c_j + u)^2)^(-1/2)
+// by the binomial recurrence of h^(-1/2), h = 1 + tau1 u + tau2 u^2,
+// integrated to acos; the exponential of a series; the reciprocal of a
+// series; squared twice for the 4th power.  A range |u| <= U takes the
+// terms up to the first two successive ones below 1e-17 of the value; the
+// centre's validated radius r_j is the largest r = 0.05 2^(-q/4) whose
+// truncated series matches the direct formula at u = +-r, +-r/2, +-r/8 to
+// 1e-14 (the direct formula's own sensitivity is ~1e-14 for alpha = 0.05;
+// the parity budget is 1e-12).  Near the cap centre and its antipode, where
+// acos is singular, and where cells are wide against alpha, the radius is
+// small or 0 and those edges evaluate the density directly.
+__constant__ double kInv[kTabK + 1] = {0.0,       1.0,       1.0 / 2,  1.0 / 3,  1.0 / 4,  1.0 / 5,  1.0 / 6,
+                                       1.0 / 7,   1.0 / 8,   1.0 / 9,  1.0 / 10, 1.0 / 11, 1.0 / 12, 1.0 / 13,
+                                       1.0 / 14,  1.0 / 15,  1.0 / 16, 1.0 / 17, 1.0 / 18, 1.0 / 19, 1.0 / 20,
+                                       1.0 / 21,  1.0 / 22,  1.0 / 23, 1.0 / 24};
+
+// the density as a function of c = x_c.p, from its definition
+__device__ double rho_of_c(const Density &r, double c) {
+    double rv = (1.0 - r.gamma) / (1.0 + exp(-2.0 * (r.beta - acos(c)) * r.inv_alpha)) + r.gamma;
+    if (r.kind == 3) { rv = rv * rv; rv = rv * rv; }
+    return rv;
 }
 
-__device__ void series_of_cell(const Grid &g, const CellBuf &cb, int p, double *__restrict__ ser,
-                               int *__restrict__ serK, int &Kout);
-
-__global__ void __launch_bounds__(128) k_rho_series(Grid g, CellBuf cb, double *__restrict__ ser, int *__restrict__ serK,
-                                                    DevStatus *st, Span sp) {
-    const int p0 = sp.p0 + blockIdx.x * blockDim.x + threadIdx.x;
-    int K = 0;
-    if (p0 < sp.p1) series_of_cell(g, cb, p0, ser, serK, K);
-    count_series(K, st);
+// terms needed over |u| <= U: the first K with terms K and K+1 below 1e-17 of
+// the value (0: none within kTabK)
+__device__ int series_terms(const double *cf, double U) {
+    const double tol = 1e-17 * fabs(cf[0]);
+    double Uk = 1.0;
+    int small = 0;
+    for (int k = 1; k < kTabK; ++k) {
+        Uk *= U;
+        small = (fabs(cf[k]) * Uk <= tol) ? small + 1 : 0;
+        if (small == 2) return k - 1;
+    }
+    return 0;
 }
 
-__device__ void series_of_cell(const Grid &g, const CellBuf &cb, int p, double *__restrict__ ser,
-                               int *__restrict__ serK, int &Kout) {
-    const int deg = cb.deg[p];
-    const int b = view_of(g, p).b;
-    const Density r = g.rho ? g.rho[b] : g.rho0;
-    if (deg == 0 || r.kind < 2) {
-        serK[p] = 0;
-        return;
-    }
-    const V3 zi = ld(g.zs + p);
-    const V3 xc = mk(r.xc0, r.xc1, r.xc2);
-    const double ci = dot(xc, zi);
-    const double si = sqrt(dot(crs(xc, zi), crs(xc, zi)));
-    const double inv_alpha = r.inv_alpha;
-    // the range of u over the cell, in FP32 from offsets (a bound only: the
-    // FP32 errors, ~1e-7, are covered by the 5 % and the 1e-6 below): u =
-    // x_c.(v - z_i) at the corners and x_c.(z_j - z_i) / 2 at the edge
-    // midpoints, whose radial part (<= |c_i| |z_j - z_i|^2 / 8) the |c_i| h^2
-    // term covers with the rule points' between them
-    const float3 xf = make_float3((float)r.xc0, (float)r.xc1, (float)r.xc2);
-    const float4 hp = g.zf[p];
-    float umax = 0.0f, umin = 0.0f, h2 = 0.0f;
-    int kmax = 0, kmin = 0;
-    for (int k = 0; k < deg; ++k) {
-        const P4 v = cb.vx[(size_t)p * kCellSlots + k];  // offset from z_i
-        const float dx = (float)v.x, dy = (float)v.y, dz = (float)v.z;
-        const float u = xf.x * dx + xf.y * dy + xf.z * dz;
-        if (u > umax) { umax = u; kmax = k; }
-        if (u < umin) { umin = u; kmin = k; }
-        h2 = fmaxf(h2, dx * dx + dy * dy + dz * dz);
-        const float4 hq = g.zf[cb.nb[(size_t)p * kCellSlots + k]];
-        const float um = 0.5f * (xf.x * (hq.x - hp.x) + xf.y * (hq.y - hp.y) + xf.z * (hq.z - hp.z));
-        umax = fmaxf(umax, um);
-        umin = fminf(umin, um);
-    }
-    const double U = 1.05 * (double)fmaxf(umax, -umin) + fabs(ci) * (double)h2 + 1e-6;
-    int K = 0;
-    double cf[kSerMax + 1];
+__global__ void k_dens_table(Density r, int M, double dth, double4 *meta, double *cfo, float2 *cdf, float *mag) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= M) return;
+    // the centre c_j = cos(j dth) as rounded; sqrt(1 - c_j^2) and acos c_j from it
+    const double ci = cos(j * dth);
+    const double si = sqrt((1.0 - ci) * (1.0 + ci));
+    const double th = atan2(si, ci);
+    double cf[kTabK];
+    for (int k = 0; k < kTabK; ++k) cf[k] = 0.0;
+    double rj = 0.0;
+    int Kj = 0;
     if (si > 1e-6) {
-        // h^(-1/2) with h = 1 + tau1 u + tau2 u^2; then acos, x, exp(-x), 1/(1+exp(-x)),
-        // built term by term until two successive terms are negligible over |u| <= U
         const double isi = 1.0 / si;
         const double tau1 = -2.0 * ci * isi * isi, tau2 = -isi * isi;
-        const double c2a = 2.0 * inv_alpha * isi;
+        const double c2a = 2.0 * r.inv_alpha * isi;
         const double om = 1.0 - r.gamma;
-        double gs[kSerMax + 1], xs[kSerMax + 1], es[kSerMax + 1], rs[kSerMax + 1], sq[kSerMax + 1];
+        double gs[kTabK], xs[kTabK], es[kTabK], rs[kTabK], sq[kTabK];
         gs[0] = 1.0;
-        xs[0] = 2.0 * (r.beta - atan2(si, ci)) * inv_alpha;
+        xs[0] = 2.0 * (r.beta - th) * r.inv_alpha;
         es[0] = exp(-xs[0]);
         const double r0 = 1.0 / (1.0 + es[0]);
         rs[0] = r0;
@@ -1738,72 +1706,96 @@ __device__ void series_of_cell(const Grid &g, const CellBuf &cb, int p, double *
             sq[0] = cf[0] * cf[0];
             cf[0] = sq[0] * sq[0];
         }
-        const double tol = 1e-17 * fabs(cf[0]);
-        double Uk = 1.0;
-        int small = 0;
-        for (int k = 1; k <= kSerMax; ++k) {
+        for (int k = 1; k < kTabK; ++k) {
             const double ik = kInv[k];
             double t = (0.5 - k) * tau1 * gs[k - 1];
             if (k >= 2) t += (1.0 - k) * tau2 * gs[k - 2];
             gs[k] = t * ik;
-            xs[k] = c2a * gs[k - 1] * ik;  // -2 a_k / alpha
+            xs[k] = c2a * gs[k - 1] * ik;  // -2 a_k / alpha, a_k the terms of acos
             t = 0.0;
-            for (int j = 1; j <= k; ++j) t += j * xs[j] * es[k - j];
+            for (int i = 1; i <= k; ++i) t += i * xs[i] * es[k - i];
             es[k] = -t * ik;
             t = 0.0;
-            for (int j = 1; j <= k; ++j) t += es[j] * rs[k - j];
+            for (int i = 1; i <= k; ++i) t += es[i] * rs[k - i];
             rs[k] = -r0 * t;
             if (r.kind == 3) {
-                // (gamma + om r)^4 as the square of the square: sq = rho^2 with
-                // rho_j = om rs_j (+ gamma at j = 0)
+                // (gamma + om r)^4 as the square of the square
                 t = 0.0;
-                for (int j = 0; j <= k; ++j) {
-                    const double rj = j == 0 ? om * rs[0] + r.gamma : om * rs[j];
-                    const double rk = (k - j) == 0 ? om * rs[0] + r.gamma : om * rs[k - j];
-                    t += rj * rk;
+                for (int i = 0; i <= k; ++i) {
+                    const double ri = i == 0 ? om * rs[0] + r.gamma : om * rs[i];
+                    const double rk = (k - i) == 0 ? om * rs[0] + r.gamma : om * rs[k - i];
+                    t += ri * rk;
                 }
                 sq[k] = t;
                 t = 0.0;
-                for (int j = 0; j <= k; ++j) t += sq[j] * sq[k - j];
+                for (int i = 0; i <= k; ++i) t += sq[i] * sq[k - i];
                 cf[k] = t;
             } else {
                 cf[k] = om * rs[k];
             }
-            Uk *= U;
-            small = (fabs(cf[k]) * Uk <= tol) ? small + 1 : 0;
-            if (small == 2) {
-                K = k - 1;  // terms 0 .. k-2; terms k-1 and k are negligible
-                break;
-            }
         }
-        if (K > 0) {
-            // both extreme corners must agree with the direct formula
-            const int ks[2] = {kmax, kmin};
-            for (int t = 0; t < 2 && K > 0; ++t) {
-                const V3 ov = ld(cb.vx + (size_t)p * kCellSlots + ks[t]);
-                const double d = rho_direct(r, inv_alpha, add(zi, ov));
-                const double sv = horner(cf, K, dot(xc, ov));
-                if (!(fabs(sv - d) <= 1e-14 * d)) K = 0;
+        for (int q = 0; q < 80 && rj == 0.0; ++q) {
+            const double rr = 0.05 * exp2(-0.25 * q);
+            const int K = series_terms(cf, rr);
+            if (K == 0) continue;
+            bool ok = true;
+            const double us[6] = {rr, -rr, 0.5 * rr, -0.5 * rr, 0.125 * rr, -0.125 * rr};
+            for (int t = 0; t < 6 && ok; ++t) {
+                const double c = ci + us[t];
+                if (c > 1.0 || c < -1.0) continue;
+                const double d = rho_of_c(r, c);
+                ok = fabs(horner(cf, K, us[t]) - d) <= 1e-14 * d;
+            }
+            if (ok) {
+                rj = rr;
+                Kj = K;
             }
         }
     }
-    serK[p] = K;
-    Kout = K;
-    if (K > 0) {
-        double *o = ser + (size_t)p * kSerStride;
-        // double-float copy in v = u / 2^e with 2^e >= U (exact scaling), so
-        // that the coefficients stay in FP32 range where 1 - c_i is small
-        int ex = 0;
-        if (U > 0.0) frexp(U, &ex);
-        float2 *od = reinterpret_cast<float2 *>(o + kSerMax + 1);
-        for (int k = 0; k < K; ++k) {
-            o[k] = cf[k];
-            const df c = df_from(ldexp(cf[k], ex * k));
-            od[k] = make_float2(c.hi, c.lo);
-        }
-        o[kSerMax] = ci;
-        o[2 * kSerMax + 1] = ldexp(1.0, -ex);
+    // double-float copy of the series in v = u 2^-e, 2^e >= r_j (exact
+    // scaling; keeps the coefficients in FP32 range), and |cf_k| r_j^k
+    int ex = 0;
+    if (rj > 0.0) frexp(rj, &ex);
+    meta[j] = make_double4(ci, ldexp(1.0, -ex), rj, (double)Kj);
+    double rk = 1.0;
+    for (int k = 0; k < kTabK; ++k) {
+        cfo[(size_t)j * kTabK + k] = cf[k];
+        const df c = df_from(ldexp(cf[k], ex * k));
+        cdf[(size_t)j * kTabK + k] = make_float2(c.hi, c.lo);
+        mag[(size_t)j * kTabK + k] = (float)(fabs(cf[k]) * rk);
+        rk *= rj;
     }
+}
+
+// The edge's series: the centre nearest in angle to x_c.z_i = ci, and the
+// terms its range needs.  xa, xb, xm: x_c.(v - z_i) at the edge's two
+// corners and its midpoint (FP32; the radial parts of the projected rule
+// points, |x_c.(p - z_i)| <= (1 + r2) max |x_c.o| + r2 |ci| for offsets of
+// squared length <= r2 <= 1/2, are covered by the bound's terms).  Returns 0
+// when the range exceeds the centre's validated radius (direct evaluation).
+__device__ __forceinline__ int table_terms(const DensTab &T, double ci, float xa, float xb, float xm, float r2,
+                                           int &j, double &cj) {
+    const float th = (ci >= 0.0) ? 2.0f * asinf(sqrtf((float)(0.5 * (1.0 - ci))))
+                                 : 3.14159265f - 2.0f * asinf(sqrtf((float)(0.5 * (1.0 + ci))));
+    j = min(T.M - 1, max(0, __float2int_rn(th / T.dth)));
+    const double4 mt = T.meta[j];
+    cj = mt.x;
+    if (!(mt.z > 0.0)) return 0;
+    const float U = (float)fabs(ci - cj) + (1.0f + r2) * fmaxf(fmaxf(fabsf(xa), fabsf(xb)), fabsf(xm)) +
+                    r2 * fabsf((float)ci) + 1e-6f * sqrtf(r2) + 1e-12f;
+    const float R = (float)mt.z;
+    if (!(U <= R)) return 0;
+    // terms |cf_k| U^k = mag_k (U / r_j)^k, no overflow
+    const float *mg = T.mag + (size_t)j * kTabK;
+    const float tol = 1e-17f * mg[0], x = U / R;
+    float xk = 1.0f;
+    int small = 0;
+    for (int k = 1; k < kTabK; ++k) {
+        xk *= x;
+        small = (mg[k] * xk <= tol) ? small + 1 : 0;
+        if (small == 2) return k - 1;
+    }
+    return 0;
 }
 
 // -------------------------------------------------------------- quadrature
@@ -1955,9 +1947,10 @@ __device__ __forceinline__ DensDF dens_df(const Density &r) {
 }
 
 template <bool PLAIN>
-__global__ void __launch_bounds__(512) k_quad(Grid g, CellBuf cb, int ecap, Span sp) {
+__global__ void __launch_bounds__(512) k_quad(Grid g, CellBuf cb, int ecap, Span sp, DevStatus *st) {
     const int ne = *sp.etot, eb = *sp.e0;
     const DensDF dd0 = dens_df(g.rho0);  // single-problem density, converted once
+    unsigned n_ser = 0, n_terms = 0;
     for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < ne; it += gridDim.x * blockDim.x) {
         const int e = eb + it;
         const int p = cb.ecell[e];
@@ -1967,10 +1960,32 @@ __global__ void __launch_bounds__(512) k_quad(Grid g, CellBuf cb, int ecap, Span
         const P4 *vx = cb.vx + (size_t)p * kCellSlots;
         const V3 va = ld(vx + k);  // corner offsets from z_i
         const V3 vb = ld(vx + ((k + 1 == deg) ? 0 : k + 1));
-        const Density rho = g.rho ? g.rho[view_of(g, p).b] : g.rho0;
-        const int K = cb.serK ? cb.serK[p] : 0;
-        const double *ser = cb.ser + (size_t)p * kSerStride;
+        const int b = view_of(g, p).b;
+        const Density rho = g.rho ? g.rho[b] : g.rho0;
+        const int q = cb.nb[(size_t)p * kCellSlots + k];
         double *ea = cb.eacc;
+        // the edge's density series from the table (tanh-cap kinds)
+        int K = 0, j = 0;
+        double cj = 0.0;
+        const double4 *tmeta = nullptr;
+        const double *tcf = nullptr;
+        const float2 *tcdf = nullptr;
+        {
+            const DensTab T = g.tabs ? g.tabs[b] : g.tab0;
+            const V3 hj = scl(sub(ld(g.zs + q), zi), 0.5);
+            const float r2 = fmaxf(fmaxf((float)dot(va, va), (float)dot(vb, vb)), (float)dot(hj, hj));
+            if (rho.kind >= 2 && T.M > 0 && r2 <= 0.5f) {
+                const V3 xc = mk(rho.xc0, rho.xc1, rho.xc2);
+                K = table_terms(T, dot(xc, zi), (float)dot(xc, va), (float)dot(xc, vb), (float)dot(xc, hj), r2, j, cj);
+                tmeta = T.meta;
+                tcf = T.cf + (size_t)j * kTabK;
+                tcdf = T.cdf + (size_t)j * kTabK;
+            }
+        }
+        if (K > 0) {
+            n_ser++;
+            n_terms += K;
+        }
         // double-float path: offsets of the edge's points from z_i below chord
         // 0.03 (then delta <= 1e-3 at every rule point) and a density without
         // direct evaluation; otherwise FP64.  The corner offsets (FP64, exact
@@ -1978,7 +1993,7 @@ __global__ void __launch_bounds__(512) k_quad(Grid g, CellBuf cb, int ecap, Span
         if constexpr (!PLAIN) {
             const df3 da = df3_from(va.x, va.y, va.z), db = df3_from(vb.x, vb.y, vb.z);
             const float4 hp = g.zf[p], lp = g.zl[p], llp = g.zll[p];
-            const df3 dj = gen_diff(g, cb.nb[(size_t)p * kCellSlots + k], hp, lp, llp);
+            const df3 dj = gen_diff(g, q, hp, lp, llp);
             const float r2 = fmaxf(fmaxf(da.x.hi * da.x.hi + da.y.hi * da.y.hi + da.z.hi * da.z.hi,
                                          db.x.hi * db.x.hi + db.y.hi * db.y.hi + db.z.hi * db.z.hi),
                                    0.25f * (dj.x.hi * dj.x.hi + dj.y.hi * dj.y.hi + dj.z.hi * dj.z.hi));
@@ -1987,9 +2002,8 @@ __global__ void __launch_bounds__(512) k_quad(Grid g, CellBuf cb, int ecap, Span
                 const df aA1{llp.w, 0.0f};
                 const DensDF dd = g.rho ? dens_df(rho) : dd0;
                 const df eA = df3_dot(dd.ev, A);
-                const df u0 = (K > 0) ? df_from(dot(mk(rho.xc0, rho.xc1, rho.xc2), zi) - ser[kSerMax]) : df{0.0f, 0.0f};
-                const float2 *sdf = reinterpret_cast<const float2 *>(ser + kSerMax + 1);
-                const float vs = (K > 0) ? (float)ser[2 * kSerMax + 1] : 1.0f;
+                const df u0 = (K > 0) ? df_from(dot(mk(rho.xc0, rho.xc1, rho.xc2), zi) - cj) : df{0.0f, 0.0f};
+                const float vs = (K > 0) ? (float)tmeta[j].y : 1.0f;
                 // edge midpoint mu = (z_i + z_j) / |z_i + z_j|: with h = (z_j - z_i) / 2,
                 // mu - z_i = h + m (A + h), 1 - |A + h|^2 = -(|A|^2 - 1) - 2 A.h - |h|^2
                 const df3 hh{df{0.5f * dj.x.hi, 0.5f * dj.x.lo}, df{0.5f * dj.y.hi, 0.5f * dj.y.lo},
@@ -2003,10 +2017,10 @@ __global__ void __launch_bounds__(512) k_quad(Grid g, CellBuf cb, int ecap, Span
                              df_add(hh.z, df_mul(mm, df_add(A.z, hh.z)))};
                 AccDF ad{};
                 if (g.fan) {
-                    tri_df(rho.kind, dd.g1, dd.gam, A, aA1, da, db, dd.ev, eA, u0, sdf, vs, K, ad);
+                    tri_df(rho.kind, dd.g1, dd.gam, A, aA1, da, db, dd.ev, eA, u0, tcdf, vs, K, ad);
                 } else {
-                    tri_df(rho.kind, dd.g1, dd.gam, A, aA1, da, dm, dd.ev, eA, u0, sdf, vs, K, ad);
-                    tri_df(rho.kind, dd.g1, dd.gam, A, aA1, dm, db, dd.ev, eA, u0, sdf, vs, K, ad);
+                    tri_df(rho.kind, dd.g1, dd.gam, A, aA1, da, dm, dd.ev, eA, u0, tcdf, vs, K, ad);
+                    tri_df(rho.kind, dd.g1, dd.gam, A, aA1, dm, db, dd.ev, eA, u0, tcdf, vs, K, ad);
                 }
                 const double m = df_to(ad.m);
                 ea[e] = m;
@@ -2022,11 +2036,11 @@ __global__ void __launch_bounds__(512) k_quad(Grid g, CellBuf cb, int ecap, Span
         const double aA1 = dot(zi, zi) - 1.0;
         Acc acc = {0, 0, 0, 0, 0};
         if (g.fan) {
-            tri(rho, inv_alpha, zi, aA1, va, vb, acc, ser, K);
+            tri(rho, inv_alpha, zi, aA1, va, vb, acc, tcf, K, cj);
         } else {
-            const V3 om = midpoint_offset(zi, aA1, ld(g.zs + cb.nb[(size_t)p * kCellSlots + k]));
-            tri(rho, inv_alpha, zi, aA1, va, om, acc, ser, K);
-            tri(rho, inv_alpha, zi, aA1, om, vb, acc, ser, K);
+            const V3 om = midpoint_offset(zi, aA1, ld(g.zs + q));
+            tri(rho, inv_alpha, zi, aA1, va, om, acc, tcf, K, cj);
+            tri(rho, inv_alpha, zi, aA1, om, vb, acc, tcf, K, cj);
         }
         moment_from_offsets(zi, acc);
         ea[e] = acc.m;
@@ -2034,6 +2048,22 @@ __global__ void __launch_bounds__(512) k_quad(Grid g, CellBuf cb, int ecap, Span
         ea[2 * (size_t)ecap + e] = acc.cy;
         ea[3 * (size_t)ecap + e] = acc.cz;
         ea[4 * (size_t)ecap + e] = acc.e;
+    }
+    // edges that took the density table, and their terms: one pair of
+    // atomics per block
+    __shared__ unsigned cnt[2];
+    if (threadIdx.x == 0) cnt[0] = cnt[1] = 0u;
+    __syncthreads();
+    n_ser = __reduce_add_sync(0xffffffffu, n_ser);
+    n_terms = __reduce_add_sync(0xffffffffu, n_terms);
+    if ((threadIdx.x & 31) == 0 && n_ser) {
+        atomicAdd(&cnt[0], n_ser);
+        atomicAdd(&cnt[1], n_terms);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && cnt[0]) {
+        atomicAdd(&st->ser_edges, (unsigned long long)cnt[0]);
+        atomicAdd(&st->ser_terms, (unsigned long long)cnt[1]);
     }
 }
 
@@ -2332,6 +2362,42 @@ DensityF to_density32(const Density &d) {
     return f;
 }
 
+int dens_table_centres(int64_t n) {
+    // theta spacing about half the smallest cells' angular size for a cap
+    // holding most generators at 8x the density contrast: 8 sqrt(n) centres
+    const double m = 8.0 * sqrt((double)n);
+    return (int)std::max(1024.0, std::min(32768.0, ceil(m)));
+}
+
+static size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+size_t dens_table_bytes(int M) {
+    return up256(sizeof(double4) * M) + up256(sizeof(double) * kTabK * M) + up256(sizeof(float2) * kTabK * M) +
+           up256(sizeof(float) * kTabK * M);
+}
+
+cudaError_t dens_table_build(const Density &r, int M, void *buf, DensTab *out, cudaStream_t s) {
+    memset(out, 0, sizeof(*out));
+    if (r.kind < 2 || M < 2 || !buf) return cudaSuccess;
+    unsigned char *b = (unsigned char *)buf;
+    double4 *meta = (double4 *)b;
+    b += up256(sizeof(double4) * M);
+    double *cf = (double *)b;
+    b += up256(sizeof(double) * kTabK * M);
+    float2 *cdf = (float2 *)b;
+    b += up256(sizeof(float2) * kTabK * M);
+    float *mag = (float *)b;
+    const double dth = 3.14159265358979323846 / (M - 1);
+    k_dens_table<<<(M + 127) / 128, 128, 0, s>>>(r, M, dth, meta, cf, cdf, mag);
+    out->M = M;
+    out->dth = (float)dth;
+    out->meta = meta;
+    out->cf = cf;
+    out->cdf = cdf;
+    out->mag = mag;
+    return cudaGetLastError();
+}
+
 void cell_passes(const Grid &g, const CellOut &out, const CellBuf &cb, int *list1, int *list2, DevStatus *st,
                  int precision, const Tune &t, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1, int64_t *launches,
                  int64_t *cell_launches, const Pipes *px, const cudaEvent_t *topo_ev) {
@@ -2403,10 +2469,9 @@ void cell_passes(const Grid &g, const CellOut &out, const CellBuf &cb, int *list
             const bool plain = precision == 2;
             if (plain) k_corners<true><<<e256, 256, 0, sc>>>(g, cb, sp);
             else k_corners<false><<<e256, 256, 0, sc>>>(g, cb, sp);
-            if (cb.serK) k_rho_series<<<(len + 127) / 128, 128, 0, sc>>>(g, cb, cb.ser, cb.serK, st, sp);
             if (timed && ev0) cudaEventRecord(ev0, sc);
-            if (plain) k_quad<true><<<eblocks, qb, 0, sc>>>(g, cb, ecap, sp);
-            else k_quad<false><<<eblocks, qb, 0, sc>>>(g, cb, ecap, sp);
+            if (plain) k_quad<true><<<eblocks, qb, 0, sc>>>(g, cb, ecap, sp, st);
+            else k_quad<false><<<eblocks, qb, 0, sc>>>(g, cb, ecap, sp, st);
             if (timed && ev1) cudaEventRecord(ev1, sc);
             k_cell_sum<false><<<cblocks, 256, 0, sc>>>(g, out, cb, ecap, st, sp);
         }

@@ -27,6 +27,16 @@ size_t max_bins(int64_t cap_n, int cap_b) {
 
 size_t max_partials(int64_t cap_n, int cap_b) { return 4 * ((size_t)cap_n / 4096 + (size_t)cap_b + 1024); }
 
+// density-table pool: the tables of any layout of at most cap_b problems with
+// cap_n generators in all fit (sum of 8 sqrt(n_b) <= 8 sqrt(cap_n cap_b), plus
+// the 1,024-centre minimum per problem), capped at 1 GiB; a problem whose
+// table does not fit evaluates its density directly
+size_t tab_pool_size(int64_t cap_n, int cap_b) {
+    const double centres = 8.0 * sqrt((double)cap_n * (double)cap_b) + 1024.0 * cap_b + 32768.0;
+    const double bytes = centres * (double)dens_table_bytes(1024) / 1024.0 + 1024.0 * cap_b;
+    return (size_t)std::min(bytes, (double)(1ull << 30));
+}
+
 // problem of every row, by binary search over the problems' first rows
 __global__ void k_fill_pinst(const InstGeom *__restrict__ inst, int B, int *__restrict__ pinst, int ntot) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -56,6 +66,7 @@ Grid make_grid(const EvalSet &E) {
     g.pinst = E.d_pinst;
     g.rho = E.d_rho;
     g.rhof = E.d_rhof;
+    g.tabs = E.precision != 1 ? E.d_tabs : nullptr;
     g.ist = E.d_ist;
     g.active = E.d_active;
     g.fan = E.fan;
@@ -84,8 +95,6 @@ void enqueue_eval(EvalSet &E, int64_t *launches, int64_t *cell_launches) {
     cb.scan_tmp = E.escan;
     cb.eacc = E.eacc;
     cb.vo = E.vo;
-    cb.ser = E.ser;
-    cb.serK = E.serK;
     cell_passes(g, out, cb, E.list1, E.list2, E.d_st, E.precision, E.tune, s, nullptr, nullptr, launches,
                 cell_launches, &E.pipes);
     reduce_eval_batch(E.B, E.max_nb, E.d_inst, E.d_pbase, E.d_active, E.fc, E.gt, E.q, E.nrm, E.partials, E.d_ist, s,
@@ -153,8 +162,8 @@ int64_t evalset_bytes(int64_t cap_n, int cap_b, int precision) {
                       + 32 + 48 + 16 * 32 + 16 * 4 + 4 + 4 + 24 + 240  // zs, zf+zl+zll, cvx, cnb, cdeg, eoff, ecell, eacc
                       + 4 * 4;                // bin_of, sidx, list1, list2
     if (precision == 1) per_row += 16 * 16;   // vo
-    else per_row += kSerWords * 8 + 4;       // density series
-    return N * per_row + nb * 12 + (int64_t)max_partials(cap_n, cap_b) * 8 + (int64_t)cap_b * 512 + (1 << 20);
+    const int64_t tabs = precision != 1 ? (int64_t)tab_pool_size(cap_n, cap_b) + (int64_t)cap_b * (int64_t)sizeof(DensTab) : 0;
+    return N * per_row + nb * 12 + (int64_t)max_partials(cap_n, cap_b) * 8 + (int64_t)cap_b * 512 + tabs + (1 << 20);
 }
 
 cudaError_t evalset_alloc(EvalSet &E, int64_t cap_n, int cap_b, int precision, cudaStream_t s) {
@@ -175,7 +184,11 @@ cudaError_t evalset_alloc(EvalSet &E, int64_t cap_n, int cap_b, int precision, c
     AL(E.cdeg, N); AL(E.eoff, N + 1); AL(E.ecell, 6 * N); AL(E.escan, scan_tmp_ints(N));
     AL(E.eacc, 5 * 6 * N);
     if (precision == 1) AL(E.vo, N * kCellSlots);
-    if (precision != 1) { AL(E.ser, N * kSerWords); AL(E.serK, N); }
+    if (precision != 1) {
+        E.tab_pool_bytes = tab_pool_size(cap_n, cap_b);
+        AL(E.d_tabs, cap_b);
+        if (e == cudaSuccess) e = ealloc(E, (unsigned char **)&E.tab_pool, E.tab_pool_bytes);
+    }
     AL(E.bin_of, N); AL(E.count, nb); AL(E.start, nb + 1); AL(E.cursor, nb); AL(E.scan_tmp, 2 * (nb / 2048 + 64) + 64);
     AL(E.sidx, N); AL(E.list1, N); AL(E.list2, N);
 #undef AL
@@ -195,7 +208,7 @@ void evalset_free(EvalSet &E) {
     E.graph = nullptr;
     void *ptrs[] = {E.d_inst, E.d_pinst, E.d_pbase, E.d_active, E.d_rho, E.d_rhof, E.d_ist, E.d_st, E.zt, E.gt,
                     E.ht, E.fc, E.q, E.nrm, E.radius, E.partials, E.zs, E.zf, E.zl, E.zll, E.cvx, E.cnb, E.cdeg, E.eoff,
-                    E.ecell, E.escan, E.eacc, E.vo, E.ser, E.serK, E.bin_of, E.count, E.start, E.cursor, E.scan_tmp, E.sidx,
+                    E.ecell, E.escan, E.eacc, E.vo, E.tab_pool, E.d_tabs, E.bin_of, E.count, E.start, E.cursor, E.scan_tmp, E.sidx,
                     E.list1, E.list2};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -216,6 +229,7 @@ cudaError_t evalset_layout(EvalSet &E, int B, const int *ns, const scvt_density 
     E.geom.resize(B);
     E.pbase.resize(B);
     E.max_nb = 1;
+    E.tabs.assign(B, DensTab{});
     std::vector<Density> rho(B);
     std::vector<DensityF> rhof(B);
     int64_t off = 0, nbt = 0;
@@ -238,6 +252,20 @@ cudaError_t evalset_layout(EvalSet &E, int B, const int *ns, const scvt_density 
         e = cudaMemcpyAsync(E.d_rhof, rhof.data(), sizeof(DensityF) * B, cudaMemcpyHostToDevice, E.stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(E.d_pbase, E.pbase.data(), sizeof(int) * B, cudaMemcpyHostToDevice, E.stream);
+    // each problem's density table, laid out in the pool in problem order
+    if (E.precision != 1) {
+        size_t used = 0;
+        for (int b = 0; b < B && e == cudaSuccess; ++b) {
+            if (rho[b].kind < 2) continue;
+            const int M = dens_table_centres(ns[b]);
+            const size_t need = dens_table_bytes(M);
+            if (used + need > E.tab_pool_bytes) continue;  // direct evaluation
+            e = dens_table_build(rho[b], M, (unsigned char *)E.tab_pool + used, &E.tabs[b], E.stream);
+            used += need;
+        }
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(E.d_tabs, E.tabs.data(), sizeof(DensTab) * B, cudaMemcpyHostToDevice, E.stream);
+    }
     if (e == cudaSuccess && ntot > 0)
         k_fill_pinst<<<(unsigned)((ntot + 255) / 256), 256, 0, E.stream>>>(E.d_inst, B, E.d_pinst, (int)ntot);
     if (e == cudaSuccess) e = cudaGetLastError();
@@ -267,7 +295,7 @@ cudaError_t evalset_run(EvalSet &E, scvt_stats *stats) {
         stats->cell_launches += E.graph_cell_launches;
         stats->knn_retries += E.h_st->retry_count[0];
         stats->ambiguous += (int64_t)E.h_st->ambiguous;
-        stats->series_cells += (int64_t)E.h_st->ser_cells;
+        stats->series_edges += (int64_t)E.h_st->ser_edges;
         stats->series_terms += (int64_t)E.h_st->ser_terms;
     }
     return cudaSuccess;

@@ -53,8 +53,12 @@ struct EvalSet {
     P4 *zs = nullptr, *cvx = nullptr;
     float4 *zf = nullptr, *zl = nullptr, *zll = nullptr, *vo = nullptr;
     int *cdeg = nullptr, *cnb = nullptr, *eoff = nullptr, *ecell = nullptr, *escan = nullptr;
-    double *eacc = nullptr, *ser = nullptr;
-    int *serK = nullptr;
+    double *eacc = nullptr;
+    // density tables of the problems (FP64 forms): a pool carved per layout
+    void *tab_pool = nullptr;
+    size_t tab_pool_bytes = 0;
+    DensTab *d_tabs = nullptr;
+    std::vector<DensTab> tabs;
     int *bin_of = nullptr, *count = nullptr, *start = nullptr, *cursor = nullptr, *scan_tmp = nullptr;
     int *sidx = nullptr, *list1 = nullptr, *list2 = nullptr;
     // the captured evaluation

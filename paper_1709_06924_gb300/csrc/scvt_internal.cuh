@@ -37,8 +37,8 @@ struct DevStatus {
     unsigned long long maxmove_bits;// max_i |s_i| as the bits of a nonnegative double
     double dots[4];                 // y.s, y.y, s.s, g.q
     unsigned differs;               // set by vec_differs
-    unsigned long long ser_cells;   // cells whose density came from a series
-    unsigned long long ser_terms;   // their terms, summed
+    unsigned long long ser_edges;   // edges whose density came from the density table
+    unsigned long long ser_terms;   // their series' terms, summed
 };
 
 struct Density {
@@ -75,6 +75,29 @@ __device__ __forceinline__ double rho_value(const Density &r, double px, double 
     return v;
 }
 
+// Density table of the FP64 forms (tanh-cap kinds).  The density depends on a
+// point p only through c = x_c.p; the table holds, at M centres c_j =
+// cos(theta_j), theta_j = j pi / (M - 1), the Taylor series of rho in
+// u = c - c_j to kTabK terms, each with the radius r_j over which it was
+// validated against the direct formula (0: none, evaluate directly).  Built
+// once per density and problem size; each quadrature edge takes the centre
+// nearest to its generator and as many terms as its own range of u needs.
+constexpr int kTabK = 24;
+struct DensTab {
+    int M;              // centres; 0 = no table (direct evaluation)
+    float dth;          // theta spacing pi / (M - 1)
+    const double4 *meta;  // per centre: c_j, 2^-e_j (scale of the pairs, 2^e_j >= r_j), r_j, terms at r_j
+    const double *cf;   // M x kTabK coefficients of the series in u
+    const float2 *cdf;  // M x kTabK the same as double-float pairs, coefficients of the series in u 2^-e_j
+    const float *mag;   // M x kTabK |cf_k| r_j^k in FP32 (the term count for a range |u| <= U <= r_j)
+};
+// centres for a problem of n generators; device bytes of a table of M centres
+int dens_table_centres(int64_t n);
+size_t dens_table_bytes(int M);
+// build the table of density r (kinds 2 and 3) in buf (dens_table_bytes(M)
+// bytes, 256-byte aligned) on stream s; *out describes it
+cudaError_t dens_table_build(const Density &r, int M, void *buf, DensTab *out, cudaStream_t s);
+
 // One problem of a batch: its generators occupy positions (and original
 // indices) [p0, p0 + n) of the concatenated arrays, its G x G x 6 bins start
 // at bin0 of the concatenated bin array.
@@ -100,12 +123,14 @@ struct Grid {
     const int *bstart;      // nbins + 1 offsets into zs
     Density rho0;           // density of a single problem
     DensityF rho0f;
+    DensTab tab0;           // its density table (M = 0: none)
     int fan;                // 1: one triangle (z_i, v_a, v_b) per Voronoi edge
     // batch of problems (all null for a single problem)
     const InstGeom *inst;   // per problem
     const int *pinst;       // problem of each position / original index
     const Density *rho;     // per-problem densities
     const DensityF *rhof;
+    const DensTab *tabs;    // per-problem density tables
     DevStatus *ist;         // per-problem status (flags, sums)
     const int *active;      // per-problem: evaluate (1) or skip (0); null = all
 };
@@ -124,11 +149,10 @@ struct CellOut {
 };
 
 // Certified cells between the topology and quadrature kernels, in bin
-// order: deg (0 = integrated elsewhere or failed), corners (unit vectors)
-// and the bin-order index of the neighbour across edge k (corner k -> k+1).
+// order: deg (0 = integrated elsewhere or failed), corners (offsets v - z_i
+// from the cell's generator) and the bin-order index of the neighbour across
+// edge k (corner k -> k+1).
 constexpr int kCellSlots = 16;
-// doubles per cell of the density-series buffer
-constexpr int kSerWords = 42;
 
 struct CellBuf {
     int *deg;          // n
@@ -139,10 +163,6 @@ struct CellBuf {
     int *scan_tmp;     // scratch of the scan over n (2 * (n / 2048 + 64) + 64 ints)
     double *eacc;      // 5 * 6n: per-edge sums (m, c or o, F), component-major; FP32 in the mixed form
     float4 *vo;        // n * kCellSlots corner offsets v - z_i in FP32 (mixed precision only)
-    double *ser;       // n * kSerWords: per-cell density series (FP64 form): 20 coefficients, the
-                       // expansion point, the coefficients of the series in u / 2^e as
-                       // double-float pairs, 2^-e
-    int *serK;         // n: terms of the cell's series, 0 = evaluate directly; null = no series
 };
 
 // ---- binning (cells.cu) ----

@@ -65,10 +65,8 @@ constexpr size_t oEoff = oG + up(sizeof(double) * 3 * kMaxN);
 constexpr size_t oEcell = oEoff + up(sizeof(int) * (kMaxN + 1));
 constexpr size_t oEscan = oEcell + up(sizeof(int) * 6 * kMaxN);
 constexpr size_t oEacc = oEscan + up(sizeof(int) * (2 * (kMaxN / 2048 + 64) + 64));
-constexpr size_t oSer = oEacc + up(sizeof(double) * 5 * 6 * kMaxN);
-constexpr size_t oSerK = oSer + up(sizeof(double) * kSerWords * kMaxN);
-constexpr size_t oCounts = oSerK + up(sizeof(int) * kMaxN);
-constexpr size_t kBytes = oCounts + up(sizeof(unsigned) * 8 * kMaxChunks);  // about 21.9 MB
+constexpr size_t oCounts = oEacc + up(sizeof(double) * 5 * 6 * kMaxN);
+constexpr size_t kBytes = oCounts + up(sizeof(unsigned) * 8 * kMaxChunks);  // about 16.4 MB
 
 __device__ __align__(256) unsigned char g_scratch[kBytes];
 
@@ -180,8 +178,6 @@ extern "C" scvt_status scvt_energy_grad_static(int64_t n, const scvt_density *rh
     cb.scan_tmp = (int *)(base + oEscan);
     cb.eacc = (double *)(base + oEacc);
     cb.vo = nullptr;
-    cb.ser = (double *)(base + oSer);
-    cb.serK = (int *)(base + oSerK);
     Pipes px;  // one pipeline on the caller's stream, its counters in the scratch array
     px.counts = (unsigned *)(base + oCounts);
     cell_passes(grid, out, cb, list1, list2, st, 0, Tune(), s, nullptr, nullptr, &launches, &cell_launches, &px);

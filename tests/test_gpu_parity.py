@@ -254,17 +254,17 @@ def test_invalid_and_degenerate_inputs_are_reported():
 @pytest.mark.parametrize("kind", [I.RHO_TANH_CAP, I.RHO_TANH_CAP_POW4])
 def test_density_series_and_its_fallback_match_oracle(kind):
     # a narrow cap (alpha = 0.05) centred on a generator, at a size where cells
-    # are wide against alpha: some cells take the per-cell series, the cell at
-    # the cap centre and the widest cells fall back to the direct formula
+    # are wide against alpha: most edges take the density table's series, the
+    # cells at the cap centre and the widest edges fall back to the direct formula
     n = 5000
     z = I.uniform_sphere(n, 77)
     dens = I.Density(kind, (1 / 16) ** 4, 0.05, math.pi / 12, tuple(z[123]))
     g = gpu_eval(z, dens)
     o = oracle.energy_grad(z, dens)
     st = g["stats"]
-    per_eval = st["series_cells"] / st["evaluations"]
-    assert 0 < per_eval < n
-    assert 3 <= st["series_terms"] / st["series_cells"] <= 19
+    per_eval = st["series_edges"] / st["evaluations"]
+    assert 0 < per_eval < 6 * n - 12
+    assert 3 <= st["series_terms"] / st["series_edges"] <= 23
     assert_geometry_close(g, o)
     assert abs(g["energy"] - o["F"]) <= RTOL * o["F"]
 
