@@ -60,7 +60,8 @@ struct Bufs {
 struct scvt_handle {
     scvt_config cfg;
     int n = 0;
-    int G = 1;
+    int G = 1;      // bins per face edge of the next evaluation (adapted to the generators' spread)
+    int Gmax = 1;   // largest the workspace holds
     int m = 0;
     Tune tune;
     Pipes pipes;
@@ -207,6 +208,7 @@ scvt_status evaluate_dev(scvt_handle *H, const double *zdev, double *grad, doubl
     H->stats.knn_retries += st.retry_count[0];
     H->stats.ambiguous += (int64_t)st.ambiguous;
     H->stats.series_edges += (int64_t)st.ser_edges;
+    H->G = adapt_bins(bins_per_edge(n, H->tune.bin_load), H->G, H->Gmax, st.max_bin, H->tune.bin_load);
     H->stats.series_terms += (int64_t)st.ser_terms;
     if (st.flags & FLAG_BAD_POINT)
         return fail(H, SCVT_ERR_INVALID, "a generator is not finite or not on the unit sphere (| |z|^2 - 1 | > 2e-12)");
@@ -373,8 +375,8 @@ scvt_status scvt_create(const scvt_config *cfg, void *cuda_stream, scvt_handle *
     H->G = bins_per_edge(H->n, H->tune.bin_load);
     const int n = H->n;
     const size_t n3 = 3 * (size_t)n;
-    const int g1 = bins_per_edge(H->n, 1);
-    const int nbins = 6 * g1 * g1;
+    H->Gmax = max_bins_per_edge(H->n);
+    const int nbins = 6 * H->Gmax * H->Gmax;
     Bufs &b = H->b;
     cudaError_t e = cudaSuccess;
 #define AL(ptr, cnt) \

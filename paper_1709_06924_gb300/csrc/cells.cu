@@ -161,6 +161,24 @@ __global__ void k_bin_count(const double *__restrict__ z, Grid g, int *__restric
     atomicAdd(&count[b], 1);
 }
 
+// fullest bin of each problem (blockIdx.y; gridDim.x blocks share its bins)
+// into its status block
+__global__ void k_bin_max(Grid g, const int *__restrict__ count, DevStatus *st) {
+    int b0 = 0, nb = g.nbins;
+    DevStatus *dst = st;
+    if (g.inst) {
+        const InstGeom I = g.inst[blockIdx.y];
+        b0 = I.bin0;
+        nb = 6 * I.G * I.G;
+        dst = g.ist + blockIdx.y;
+        if (inactive(g, blockIdx.y)) return;
+    }
+    int m = 0;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nb; k += gridDim.x * blockDim.x) m = max(m, count[b0 + k]);
+    m = __reduce_max_sync(0xffffffffu, m);
+    if ((threadIdx.x & 31) == 0) atomicMax(&dst->max_bin, (unsigned)m);
+}
+
 // The FP32 copy carries the generator's search-radius hint (from the previous
 // evaluation, 0 = none) in its w component, so the topology pass reads it with
 // the coordinates instead of through the original index.
@@ -1964,22 +1982,32 @@ __global__ void __launch_bounds__(512) k_quad(Grid g, CellBuf cb, int ecap, Span
         const Density rho = g.rho ? g.rho[b] : g.rho0;
         const int q = cb.nb[(size_t)p * kCellSlots + k];
         double *ea = cb.eacc;
-        // the edge's density series from the table (tanh-cap kinds)
+        // the edge's density series from the table (tanh-cap kinds): its range
+        // bound in FP32 from the corner offsets and z_j - z_i (FP32 pairs),
+        // x_c.z_i in FP64 (it sets the series' argument)
         int K = 0, j = 0;
-        double cj = 0.0;
+        double cj = 0.0, ci = 0.0;
         const double4 *tmeta = nullptr;
         const double *tcf = nullptr;
         const float2 *tcdf = nullptr;
-        {
+        if (rho.kind >= 2) {
             const DensTab T = g.tabs ? g.tabs[b] : g.tab0;
-            const V3 hj = scl(sub(ld(g.zs + q), zi), 0.5);
-            const float r2 = fmaxf(fmaxf((float)dot(va, va), (float)dot(vb, vb)), (float)dot(hj, hj));
-            if (rho.kind >= 2 && T.M > 0 && r2 <= 0.5f) {
-                const V3 xc = mk(rho.xc0, rho.xc1, rho.xc2);
-                K = table_terms(T, dot(xc, zi), (float)dot(xc, va), (float)dot(xc, vb), (float)dot(xc, hj), r2, j, cj);
-                tmeta = T.meta;
-                tcf = T.cf + (size_t)j * kTabK;
-                tcdf = T.cdf + (size_t)j * kTabK;
+            if (T.M > 0) {
+                const float3 fa = make_float3((float)va.x, (float)va.y, (float)va.z);
+                const float3 fb = make_float3((float)vb.x, (float)vb.y, (float)vb.z);
+                const float3 fh = dfdiff(g, q, g.zf[p], g.zl[p]);
+                const float r2 = fmaxf(fmaxf(fa.x * fa.x + fa.y * fa.y + fa.z * fa.z, fb.x * fb.x + fb.y * fb.y + fb.z * fb.z),
+                                       0.25f * (fh.x * fh.x + fh.y * fh.y + fh.z * fh.z));
+                if (r2 <= 0.5f) {
+                    const float3 xf = make_float3((float)rho.xc0, (float)rho.xc1, (float)rho.xc2);
+                    ci = rho.xc0 * zi.x + rho.xc1 * zi.y + rho.xc2 * zi.z;
+                    K = table_terms(T, ci,
+                                    xf.x * fa.x + xf.y * fa.y + xf.z * fa.z, xf.x * fb.x + xf.y * fb.y + xf.z * fb.z,
+                                    0.5f * (xf.x * fh.x + xf.y * fh.y + xf.z * fh.z), r2, j, cj);
+                    tmeta = T.meta;
+                    tcf = T.cf + (size_t)j * kTabK;
+                    tcdf = T.cdf + (size_t)j * kTabK;
+                }
             }
         }
         if (K > 0) {
@@ -2002,7 +2030,7 @@ __global__ void __launch_bounds__(512) k_quad(Grid g, CellBuf cb, int ecap, Span
                 const df aA1{llp.w, 0.0f};
                 const DensDF dd = g.rho ? dens_df(rho) : dd0;
                 const df eA = df3_dot(dd.ev, A);
-                const df u0 = (K > 0) ? df_from(dot(mk(rho.xc0, rho.xc1, rho.xc2), zi) - cj) : df{0.0f, 0.0f};
+                const df u0 = (K > 0) ? df_from(ci - cj) : df{0.0f, 0.0f};
                 const float vs = (K > 0) ? (float)tmeta[j].y : 1.0f;
                 // edge midpoint mu = (z_i + z_j) / |z_i + z_j|: with h = (z_j - z_i) / 2,
                 // mu - z_i = h + m (A + h), 1 - |A + h|^2 = -(|A|^2 - 1) - 2 A.h - |h|^2
@@ -2289,12 +2317,13 @@ void bin_points(const double *z, const Grid &g, int *bin_of, int *count, int *st
     cudaMemsetAsync(count, 0, sizeof(int) * nbins, s);
     int blocks = (n + 255) / 256;
     k_bin_count<<<blocks, 256, 0, s>>>(z, gb, bin_of, count, st);
+    k_bin_max<<<dim3(32, g.inst ? g.nprob : 1), 256, 0, s>>>(gb, count, st);
     exclusive_scan(count, start, nbins, scan_tmp, s, launches);
     k_set_total<<<1, 1, 0, s>>>(start, nbins, n);
     cudaMemcpyAsync(cursor, start, sizeof(int) * nbins, cudaMemcpyDeviceToDevice, s);
     k_bin_scatter<<<blocks, 256, 0, s>>>(z, n, bin_of, cursor, zs, zf, zl, zll, sidx, hint);
     k_bin_sort<<<(nbins + 255) / 256, 256, 0, s>>>(start, nbins, zs, zf, zl, zll, sidx);
-    (*launches) += 4;
+    (*launches) += 5;
 }
 
 
@@ -2305,6 +2334,16 @@ void exclusive_scan(const int *in, int *out, int len, int *tmp, cudaStream_t s, 
 int bins_per_edge(int64_t n, int bin_load) {
     const int G = (int)ceil(sqrt((double)n / (6.0 * (double)bin_load)));
     return std::max(1, std::min(G, 4096));
+}
+
+int adapt_bins(int G0, int Gcur, int Gmax, unsigned max_bin, int bin_load) {
+    if (max_bin == 0 || Gcur <= 0) return Gcur;
+    const double r = (double)Gcur / (double)G0;
+    const double m0 = (double)max_bin * r * r;
+    double G = G0 * sqrt(m0 / (6.0 * bin_load));
+    G = std::max((double)G0, std::min((double)Gmax, ceil(G)));
+    if (fabs(G - Gcur) <= 0.15 * Gcur) return Gcur;
+    return (int)G;
 }
 
 scvt_status tune_from(const scvt_tuning &t, Tune *out) {

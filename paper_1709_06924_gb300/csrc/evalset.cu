@@ -18,11 +18,12 @@ cudaError_t ealloc(EvalSet &E, T **p, size_t count) {
     return e;
 }
 
-// bins of the finest tuning (one generator per bin) over at most cap_b
-// problems of cap_n generators in total: sum 6 ceil(sqrt(n_b/6))^2 <=
-// cap_n + 2 sqrt(6 cap_n cap_b) + 6 cap_b
+// bins of the finest adapted resolution (max_bins_per_edge: twice the bins per
+// edge of one generator per bin) over at most cap_b problems of cap_n
+// generators in total: sum 6 (2 ceil(sqrt(n_b/6)))^2 <= 4 (cap_n + 2 sqrt(6
+// cap_n cap_b) + 6 cap_b)
 size_t max_bins(int64_t cap_n, int cap_b) {
-    return (size_t)cap_n + (size_t)(2.0 * sqrt(6.0 * (double)cap_n * (double)cap_b)) + 6 * (size_t)cap_b + 64;
+    return 4 * ((size_t)cap_n + (size_t)(2.0 * sqrt(6.0 * (double)cap_n * (double)cap_b)) + 6 * (size_t)cap_b) + 64;
 }
 
 size_t max_partials(int64_t cap_n, int cap_b) { return 4 * ((size_t)cap_n / 4096 + (size_t)cap_b + 1024); }
@@ -69,6 +70,7 @@ Grid make_grid(const EvalSet &E) {
     g.tabs = E.precision != 1 ? E.d_tabs : nullptr;
     g.ist = E.d_ist;
     g.active = E.d_active;
+    g.nprob = E.B;
     g.fan = E.fan;
     return g;
 }
@@ -129,7 +131,7 @@ cudaError_t capture(EvalSet &E) {
 cudaError_t rebin(EvalSet &E) {
     int bin0 = 0;
     for (int b = 0; b < E.B; ++b) {
-        const int G = bins_per_edge(E.geom[b].n, E.tune.bin_load);
+        const int G = E.gsel[b] > 0 ? E.gsel[b] : bins_per_edge(E.geom[b].n, E.tune.bin_load);
         E.geom[b].G = G;
         E.geom[b].bin0 = bin0;
         bin0 += 6 * G * G;
@@ -229,6 +231,7 @@ cudaError_t evalset_layout(EvalSet &E, int B, const int *ns, const scvt_density 
     E.geom.resize(B);
     E.pbase.resize(B);
     E.max_nb = 1;
+    E.gsel.assign(B, 0);
     E.tabs.assign(B, DensTab{});
     std::vector<Density> rho(B);
     std::vector<DensityF> rhof(B);
@@ -275,6 +278,7 @@ cudaError_t evalset_layout(EvalSet &E, int B, const int *ns, const scvt_density 
 
 cudaError_t evalset_set_tune(EvalSet &E, const Tune &t) {
     E.tune = t;
+    E.gsel.assign(E.B, 0);
     return rebin(E);
 }
 
@@ -289,6 +293,20 @@ cudaError_t evalset_run(EvalSet &E, scvt_stats *stats) {
     if (E.h_st->flags & FLAG_ECAP)
         for (int b = 0; b < E.B; ++b)
             if (E.h_active[b]) E.h_ist[b].flags |= FLAG_ECAP;
+    // bins refined (or relaxed) where an evaluated problem's generators
+    // concentrate; a change re-lays the bins out and drops the graph
+    bool rebinned = false;
+    for (int b = 0; b < E.B; ++b) {
+        if (!E.h_active[b]) continue;
+        const int n = E.geom[b].n;
+        const int G = adapt_bins(bins_per_edge(n, E.tune.bin_load), E.geom[b].G, max_bins_per_edge(n),
+                                 E.h_ist[b].max_bin, E.tune.bin_load);
+        if (G != E.geom[b].G) {
+            E.gsel[b] = G;
+            rebinned = true;
+        }
+    }
+    if (rebinned && (e = rebin(E)) != cudaSuccess) return e;
     if (stats) {
         stats->evaluations++;
         stats->kernel_launches += E.graph_launches;

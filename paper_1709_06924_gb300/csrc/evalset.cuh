@@ -31,6 +31,7 @@ struct EvalSet {
     int B = 0;
     int64_t ntot = 0;
     std::vector<InstGeom> geom;
+    std::vector<int> gsel;  // per problem: bins per face edge chosen by adapt_bins (0 = the tuning's)
     std::vector<int> pbase;
     int max_nb = 1;
     int nbins = 0;

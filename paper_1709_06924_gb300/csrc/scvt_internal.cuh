@@ -39,6 +39,7 @@ struct DevStatus {
     unsigned differs;               // set by vec_differs
     unsigned long long ser_edges;   // edges whose density came from the density table
     unsigned long long ser_terms;   // their series' terms, summed
+    unsigned max_bin;               // generators in the fullest cube-map bin (per problem in a batch)
 };
 
 struct Density {
@@ -133,6 +134,7 @@ struct Grid {
     const DensTab *tabs;    // per-problem density tables
     DevStatus *ist;         // per-problem status (flags, sums)
     const int *active;      // per-problem: evaluate (1) or skip (0); null = all
+    int nprob;              // problems of a batch (inst, ist, active have nprob entries)
 };
 
 // Per-cell outputs, indexed by ORIGINAL generator index.  Any may be null.
@@ -186,6 +188,18 @@ struct Tune {
     int quad_block = 256;  // threads per block of the quadrature (128, 256, 512)
 };
 int bins_per_edge(int64_t n, int bin_load);
+// largest bins per face edge the workspace of a problem of n generators holds
+// (twice the finest tuning's: four times its bins)
+inline int max_bins_per_edge(int64_t n) { return 2 * bins_per_edge(n, 1); }
+// Bins per face edge for the next evaluation.  G0 = bins_per_edge(n,
+// bin_load) suits generators spread evenly; where the last evaluation's
+// fullest bin (max_bin generators with Gcur bins per edge) shows them
+// concentrated beyond a uniform spread's fluctuations -- a converged mesh of
+// a graded density -- the bins are refined so the dense region's bins hold
+// about bin_load again: G = G0 sqrt(M0 / (6 bin_load)), M0 = max_bin
+// (Gcur / G0)^2, within [G0, Gmax], kept at Gcur unless it moves by more
+// than 15 %.  The bins do not change any result, only the search's cost.
+int adapt_bins(int G0, int Gcur, int Gmax, unsigned max_bin, int bin_load);
 // public tuning record <-> Tune (SCVT_ERR_INVALID when out of range)
 scvt_status tune_from(const scvt_tuning &t, Tune *out);
 scvt_tuning tuning_of(const Tune &t);
