@@ -157,7 +157,7 @@ scvt_status scvt_batch_create(const scvt_config *cfgs, int count, void *cuda_str
     if (e == cudaSuccess) e = balloc(BT, &(ptr), (cnt))
     AL(BT->z, n3); AL(BT->g, n3); AL(BT->h, N);
     AL(BT->hist, (size_t)(BT->m + 1) * 2 * n3); AL(BT->rho_hist, (size_t)count * kLaneRho);
-    AL(BT->partials, 4 * 1024); AL(BT->scal, 128);
+    AL(BT->partials, 4 * 1024); AL(BT->scal, kTwoLoopScratch);
 #undef AL
     std::vector<int> ns(count);
     std::vector<scvt_density> rhos(count);

@@ -37,7 +37,7 @@ struct Bufs {
     double *mass = nullptr, *moment = nullptr;
     double *stage_a = nullptr, *stage_b = nullptr;  // host-pointer staging (3n each)
     double *partials = nullptr;              // 4 * 1024
-    double *scal = nullptr;                  // 128 two-loop scalars
+    double *scal = nullptr;                  // two-loop scalars (kTwoLoopScratch)
     double *rho = nullptr;                   // kMaxM + 1
     double *gamma = nullptr;                 // plain LBFGS scaling of H0
     double *hist = nullptr;                  // (m + 1) slots of S and Y, 3n each
@@ -152,6 +152,7 @@ scvt_status evaluate_dev(scvt_handle *H, const double *zdev, double *grad, doubl
     Bufs &B = H->b;
     cudaStream_t s = H->stream;
     int64_t *L = &H->stats.kernel_launches;
+    Phase ph("scvt evaluate");
     if (H->profiling) cudaEventRecord(H->ev_e0, s);
     CK(cudaMemsetAsync(B.st, 0, sizeof(DevStatus), s), "reset status");
     Grid g;
@@ -173,8 +174,11 @@ scvt_status evaluate_dev(scvt_handle *H, const double *zdev, double *grad, doubl
         CK(cudaMemsetAsync(B.radius, 0, sizeof(float) * n, s), "reset radius hints");
         H->radius_valid = true;
     }
-    bin_points(zdev, g, B.bin_of, B.count, B.start, B.cursor, B.scan_tmp, B.zs, B.zf, B.zl, H->cfg.precision != 1 ? B.zll : nullptr, B.sidx, B.radius, B.st, s,
-               L);
+    {
+        Phase pb("scvt bin");
+        bin_points(zdev, g, B.bin_of, B.count, B.start, B.cursor, B.scan_tmp, B.zs, B.zf, B.zl,
+                   H->cfg.precision != 1 ? B.zll : nullptr, B.sidx, B.radius, B.st, s, L);
+    }
     CellOut out;
     out.grad = grad;
     out.hdiag = hdiag;
@@ -197,7 +201,10 @@ scvt_status evaluate_dev(scvt_handle *H, const double *zdev, double *grad, doubl
     cell_passes(g, out, cb, B.list1, B.list2, B.st, H->cfg.precision, H->tune, s,
                 H->profiling ? H->ev_cell0 : nullptr, H->profiling ? H->ev_cell1 : nullptr, L,
                 &H->stats.cell_launches, &H->pipes, H->profiling ? H->ev_topo : nullptr);
-    reduce_eval(n, fcell, grad, q, nrm, B.partials, B.st, s, L);
+    {
+        Phase pr("scvt reduce");
+        reduce_eval(n, fcell, grad, q, nrm, B.partials, B.st, s, L);
+    }
     if (H->profiling) cudaEventRecord(H->ev_e1, s);
     CK(cudaGetLastError(), "launch");
     CK(cudaMemcpyAsync(H->st_host, B.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s), "status copy");
@@ -264,6 +271,7 @@ scvt_status make_direction(scvt_handle *H, double *d0, int method) {
         Y[k] = slot_Y(H, sl);
         R[k] = H->b.rho + sl;
     }
+    Phase ph("scvt direction");
     if (H->profiling) cudaEventRecord(H->ev_l0, H->stream);
     two_loop(H->n, H->b.g, method == 1 ? nullptr : H->b.h, (method == 1 && count > 0) ? H->b.gamma : nullptr, count,
              S, Y, R, H->b.q, H->b.partials, H->b.scal, H->b.st, H->stream, &H->stats.kernel_launches);
@@ -384,7 +392,7 @@ scvt_status scvt_create(const scvt_config *cfg, void *cuda_stream, scvt_handle *
     AL(b.z, n3); AL(b.zt, n3); AL(b.g, n3); AL(b.gt, n3); AL(b.h, n); AL(b.ht, n); AL(b.fc, n);
     AL(b.q, n3); AL(b.yv, n3); AL(b.nrm, n); AL(b.mass, n); AL(b.moment, n3);
     AL(b.stage_a, n3); AL(b.stage_b, n3);
-    AL(b.partials, 4 * 1024); AL(b.scal, 128); AL(b.rho, kMaxM + 1); AL(b.gamma, 1);
+    AL(b.partials, 4 * 1024); AL(b.scal, kTwoLoopScratch); AL(b.rho, kMaxM + 1); AL(b.gamma, 1);
     AL(b.hist, (size_t)(H->m + 1) * 2 * n3);
     AL(b.zs, n); AL(b.zf, n); AL(b.zl, n); AL(b.zll, n); AL(b.cvx, (size_t)n * kCellSlots); AL(b.cnb, (size_t)n * kCellSlots);
     AL(b.cdeg, n); AL(b.eoff, n + 1); AL(b.ecell, 6 * (size_t)n); AL(b.escan, scan_tmp_ints(n));
@@ -690,7 +698,10 @@ scvt_status scvt_lbfgs_solve(scvt_handle *H, double *z, const scvt_solve_opts *o
         }
         scvt_status cb_status = SCVT_OK;
         auto phi = [&](double a, double &f, double &d) -> int {
-            trial_point(n, B.z, B.q, a, B.zt, B.nrm, s, &H->stats.kernel_launches);
+            {
+                Phase pt("scvt trial point");
+                trial_point(n, B.z, B.q, a, B.zt, B.nrm, s, &H->stats.kernel_launches);
+            }
             double g2;
             cb_status = evaluate_dev(H, B.zt, B.gt, B.ht, B.fc, nullptr, nullptr, nullptr, nullptr, 0, B.q, B.nrm, &f,
                                      &g2, &d);
@@ -717,6 +728,7 @@ scvt_status scvt_lbfgs_solve(scvt_handle *H, double *z, const scvt_solve_opts *o
             }
             info = cb < 0 ? -1 : 1;
         } else {
+            Phase pl("scvt line search");
             info = ls.run(phi, H->F, d0, a, fa, da, nfev);
         }
         rep.fevals += nfev;
@@ -732,6 +744,7 @@ scvt_status scvt_lbfgs_solve(scvt_handle *H, double *z, const scvt_solve_opts *o
             rep.resets++;
         }
         // accept the last evaluated point: s = z+ - z, y = g+ - g into the spare slot
+        Phase pa("scvt accept");
         const int slot = H->spare;
         CK(cudaMemsetAsync(&B.st->maxmove_bits, 0, sizeof(unsigned long long), s), "reset max move");
         accept_pair(n, B.zt, B.z, B.gt, B.g, slot_S(H, slot), slot_Y(H, slot), B.partials, B.st, s,

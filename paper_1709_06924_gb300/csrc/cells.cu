@@ -2463,6 +2463,7 @@ void cell_passes(const Grid &g, const CellOut &out, const CellBuf &cb, int *list
         unsigned *rc = counts + kChunkWords * c;
         int *cw = (int *)rc;  // this chunk's words
         const bool timed = (c == 0 && nch == 1);
+        nvtxRangePushA("scvt topology");
         if (timed && topo_ev) cudaEventRecord(topo_ev[0], sc);
         // first pass: a warp (or half warp) per cell, grid capped at topo_bpsm blocks per SM
         const int wblocks =
@@ -2498,6 +2499,8 @@ void cell_passes(const Grid &g, const CellOut &out, const CellBuf &cb, int *list
         const unsigned eblocks = (unsigned)((6 * len + qb - 1) / qb);
         const unsigned e256 = (unsigned)((6 * len + 255) / 256);
         const unsigned cblocks = (unsigned)((len + 255) / 256);
+        nvtxRangePop();
+        Phase pq("scvt corners, quadrature, cell sums");
         if (precision == 1) {
             k_corners32<<<e256, 256, 0, sc>>>(g, cb, sp);
             if (timed && ev0) cudaEventRecord(ev0, sc);

@@ -283,6 +283,7 @@ cudaError_t evalset_set_tune(EvalSet &E, const Tune &t) {
 }
 
 cudaError_t evalset_run(EvalSet &E, scvt_stats *stats) {
+    Phase ph("scvt batch evaluate");
     cudaError_t e;
     if (!E.graph && (e = capture(E)) != cudaSuccess) return e;
     e = cudaMemcpyAsync(E.d_active, E.h_active, sizeof(int) * E.B, cudaMemcpyHostToDevice, E.stream);

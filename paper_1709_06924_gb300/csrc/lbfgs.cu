@@ -9,8 +9,9 @@
 //
 // The two-loop recursion (Sec. 2.2.2) keeps its scalars alpha_k, beta_k on
 // the device: each pass fuses the axpy of one step with the dot product of
-// the next, and a one-block kernel turns the chunk sums into the next
-// scalar, so the whole direction is computed without a host round trip.
+// the next, and the pass's last block to finish turns the chunk sums into
+// the next scalar, so the whole direction is 2 count + 1 back-to-back
+// launches without a host round trip.
 #include <math.h>
 
 #include "scvt_internal.cuh"
@@ -99,44 +100,6 @@ __global__ void k_dot(int64_t len, const double *__restrict__ x, const double *_
     chunk_of(len, b0, b1);
     double v[1] = {0.0};
     for (int64_t i = b0 + threadIdx.x; i < b1; i += kRT) v[0] += x[i] * y[i];
-    block_sum_store<1>(v, partials + blockIdx.x);
-}
-
-// q = -g (if h: q = -h g; else if hs: q = -hs[0] g); partial dot w.q
-__global__ void k_neg(int64_t len, const double *__restrict__ g, const double *__restrict__ h,
-                      const double *__restrict__ hs, double *__restrict__ q, const double *__restrict__ w,
-                      double *__restrict__ partials) {
-    int64_t b0, b1;
-    chunk_of(len, b0, b1);
-    const double sc = hs ? hs[0] : 1.0;
-    double v[1] = {0.0};
-    for (int64_t i = b0 + threadIdx.x; i < b1; i += kRT) {
-        double x = -g[i];
-        if (h) x *= h[i / 3];
-        else if (hs) x *= sc;
-        q[i] = x;
-        v[0] += w[i] * x;
-    }
-    block_sum_store<1>(v, partials + blockIdx.x);
-}
-
-// q += sign * coef * x; if h: q *= h (per generator), else if hs: q *= hs[0];
-// partial dot w.q
-__global__ void k_axpy(int64_t len, double *__restrict__ q, const double *__restrict__ coef, double sign,
-                       const double *__restrict__ x, const double *__restrict__ h, const double *__restrict__ hs,
-                       const double *__restrict__ w, double *__restrict__ partials) {
-    int64_t b0, b1;
-    chunk_of(len, b0, b1);
-    const double a = sign * coef[0];
-    const double sc = hs ? hs[0] : 1.0;
-    double v[1] = {0.0};
-    for (int64_t i = b0 + threadIdx.x; i < b1; i += kRT) {
-        double t = q[i] + a * x[i];
-        if (h) t *= h[i / 3];
-        else if (hs) t *= sc;
-        q[i] = t;
-        v[0] += w[i] * t;
-    }
     block_sum_store<1>(v, partials + blockIdx.x);
 }
 
@@ -242,6 +205,95 @@ __global__ void k_set_rho(double *rho, const DevStatus *st) { rho[0] = 1.0 / st-
 // plain LBFGS: gamma = y.s / y.y of the newest pair (Sec. 2.2.2)
 __global__ void k_set_gamma(double *gamma, const DevStatus *st) { gamma[0] = st->dots[0] / st->dots[1]; }
 
+// ---- direction passes (two-loop recursion) ----
+// Vectors read once per pass (the history pairs, g) are loaded with an L2
+// evict-first policy, so the direction q -- written and read again by every
+// pass, 24 bytes per generator -- stays resident in L2 between passes.
+__device__ __forceinline__ unsigned long long policy_evict_first() {
+    unsigned long long p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+__device__ __forceinline__ double ld_stream(const double *a, unsigned long long pol) {
+    double v;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(a), "l"(pol));
+    return v;
+}
+
+// The scalar a pass leaves for the next one, taken by the last of its
+// blocks to finish: the chunk sums in block order (the same fixed partition
+// as every reduction here), out = scale * sum, or minus_from - scale * sum.
+// Each block's chunk sum is published before its ticket; the last ticket
+// holder therefore reads every sum, and resets the ticket counter for the
+// next pass.
+__device__ __forceinline__ void finish_by_last_block(double v, double *__restrict__ partials, unsigned *ticket,
+                                                     const double *scale, const double *minus_from, double *out) {
+    double vv[1] = {v};
+    block_sum_store<1>(vv, partials + blockIdx.x);
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double w[1] = {0.0};
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += kRT) w[0] += ((volatile double *)partials)[b];
+    double res[1];
+    block_sum_store<1>(w, res);
+    if (threadIdx.x == 0) {
+        double r = scale ? scale[0] * res[0] : res[0];
+        if (minus_from) r = minus_from[0] - r;
+        out[0] = r;
+        *ticket = 0u;
+    }
+}
+
+// one step of the recursion: q = (q0 + sign coef x) [* h or * hs[0]] with
+// q0 = q (or -g0 for the first pass: coef = null, x = g0), then the next
+// scalar from w.q (finish_by_last_block)
+__global__ void __launch_bounds__(kRT) k_step(int64_t len, double *__restrict__ q, const double *__restrict__ coef,
+                                              double sign, const double *__restrict__ x,
+                                              const double *__restrict__ h, const double *__restrict__ hs,
+                                              const double *__restrict__ w, double *__restrict__ partials,
+                                              unsigned *ticket, const double *scale, const double *minus_from,
+                                              double *out) {
+    int64_t b0, b1;
+    chunk_of(len, b0, b1);
+    const unsigned long long pol = policy_evict_first();
+    const double a = coef ? sign * coef[0] : 0.0;
+    const double sc = hs ? hs[0] : 1.0;
+    double v = 0.0;
+    // four elements per thread and iteration, their loads issued together
+    constexpr int U = 4;
+    for (int64_t i0 = b0 + threadIdx.x; i0 < b1; i0 += U * kRT) {
+        double xv[U], wv[U], qv[U], hv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t i = i0 + (int64_t)u * kRT;
+            if (i < b1) {
+                xv[u] = ld_stream(x + i, pol);
+                wv[u] = ld_stream(w + i, pol);
+                qv[u] = coef ? q[i] : 0.0;
+                hv[u] = h ? h[i / 3] : sc;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t i = i0 + (int64_t)u * kRT;
+            if (i < b1) {
+                double t = coef ? qv[u] + a * xv[u] : -xv[u];
+                if (h || hs) t *= hv[u];
+                q[i] = t;
+                v += wv[u] * t;
+            }
+        }
+    }
+    finish_by_last_block(v, partials, ticket, scale, minus_from, out);
+}
+
 __global__ void k_differs(int64_t len, const double *__restrict__ a, const double *__restrict__ b, unsigned *flag) {
     int any = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x)
@@ -320,34 +372,50 @@ void set_gamma(double *gamma_dev, const DevStatus *st, cudaStream_t s, int64_t *
 void two_loop(int n, const double *g, const double *h, const double *hs, int count, const double *const *S,
               const double *const *Y, const double *const *rho, double *q, double *partials, double *scal,
               DevStatus *st, cudaStream_t s, int64_t *launches) {
+    // one pass per step of the recursion (Sec. 2.2.2): q = -g, then per pair
+    // (newest first) q -= alpha_k y_k, the initial matrix (diag(h) per
+    // generator, hs[0] I or I) with the last backward step, then per pair
+    // (oldest first) q += (alpha_k - beta_k) s_k; each pass's last block turns
+    // the chunk sums of its dot product into the next step's scalar, so the
+    // 2 count + 1 passes run back to back without a host round trip
     const int64_t len = 3 * (int64_t)n;
     const int nb = reduce_blocks(len);
     double *alpha = scal, *coef = scal + 64;
+    unsigned *ticket = reinterpret_cast<unsigned *>(scal + 130);
+    cudaMemsetAsync(ticket, 0, sizeof(unsigned), s);
     if (count == 0) {
-        k_neg<<<nb, kRT, 0, s>>>(len, g, h, hs, q, g, partials);
-        k_finish_scalar<<<1, kRT, 0, s>>>(partials, nb, nullptr, nullptr, &st->dots[3]);
-        (*launches) += 2;
+        k_step<<<nb, kRT, 0, s>>>(len, q, nullptr, 0.0, g, h, hs, g, partials, ticket, nullptr, nullptr,
+                                  &st->dots[3]);
+        (*launches)++;
         return;
     }
-    // backward: newest (count-1) .. oldest (0)
-    k_neg<<<nb, kRT, 0, s>>>(len, g, nullptr, nullptr, q, S[count - 1], partials);
+    // backward: newest (count-1) .. oldest (0); the first pass gives alpha_{count-1}
+    k_step<<<nb, kRT, 0, s>>>(len, q, nullptr, 0.0, g, nullptr, nullptr, S[count - 1], partials, ticket,
+                              rho[count - 1], nullptr, alpha + count - 1);
     (*launches)++;
     for (int k = count - 1; k >= 0; --k) {
-        k_finish_scalar<<<1, kRT, 0, s>>>(partials, nb, rho[k], nullptr, alpha + k);
-        const double *w = (k > 0) ? S[k - 1] : Y[0];
-        k_axpy<<<nb, kRT, 0, s>>>(len, q, alpha + k, -1.0, Y[k], (k > 0) ? nullptr : h, (k > 0) ? nullptr : hs, w,
-                                  partials);
-        (*launches) += 2;
+        if (k > 0) {
+            // q -= alpha_k y_k; alpha_{k-1} = rho_{k-1} s_{k-1}.q
+            k_step<<<nb, kRT, 0, s>>>(len, q, alpha + k, -1.0, Y[k], nullptr, nullptr, S[k - 1], partials, ticket,
+                                      rho[k - 1], nullptr, alpha + k - 1);
+        } else {
+            // q = H0 (q - alpha_0 y_0); coef_0 = alpha_0 - rho_0 y_0.q
+            k_step<<<nb, kRT, 0, s>>>(len, q, alpha, -1.0, Y[0], h, hs, Y[0], partials, ticket, rho[0], alpha,
+                                      coef);
+        }
+        (*launches)++;
     }
-    // forward: oldest .. newest
+    // forward: oldest .. newest; q += coef_k s_k, coef_{k+1} = alpha_{k+1} - rho_{k+1} y_{k+1}.q, the
+    // last pass leaves g.q
     for (int k = 0; k < count; ++k) {
-        k_finish_scalar<<<1, kRT, 0, s>>>(partials, nb, rho[k], alpha + k, coef + k);
-        const double *w = (k + 1 < count) ? Y[k + 1] : g;
-        k_axpy<<<nb, kRT, 0, s>>>(len, q, coef + k, 1.0, S[k], nullptr, nullptr, w, partials);
-        (*launches) += 2;
+        if (k + 1 < count)
+            k_step<<<nb, kRT, 0, s>>>(len, q, coef + k, 1.0, S[k], nullptr, nullptr, Y[k + 1], partials, ticket,
+                                      rho[k + 1], alpha + k + 1, coef + k + 1);
+        else
+            k_step<<<nb, kRT, 0, s>>>(len, q, coef + k, 1.0, S[k], nullptr, nullptr, g, partials, ticket, nullptr,
+                                      nullptr, &st->dots[3]);
+        (*launches)++;
     }
-    k_finish_scalar<<<1, kRT, 0, s>>>(partials, nb, nullptr, nullptr, &st->dots[3]);
-    (*launches)++;
 }
 
 }  // namespace scvt

@@ -85,6 +85,7 @@ cudaError_t lockstep_round(EvalSet &E, std::vector<Lane *> &lanes, int m, double
     }
     // ---- directions (again, from an empty history, where one is not a descent direction)
     if (!act.empty()) {
+        Phase ph("scvt batch directions");
         for (Lane *L : act) enqueue_direction(E, *L, partials, scal, launches);
         if ((e = sync_statuses(E)) != cudaSuccess) return e;
         std::vector<Lane *> redo;
@@ -121,6 +122,7 @@ cudaError_t lockstep_round(EvalSet &E, std::vector<Lane *> &lanes, int m, double
         if (L->ls_state == 0) ls.push_back(L);
     }
     bool first = true;
+    Phase pl("scvt batch line search");
     while (!ls.empty() || (first && !init.empty())) {
         for (int b = 0; b < E.B; ++b) E.h_active[b] = 0;
         for (Lane *L : ls) {

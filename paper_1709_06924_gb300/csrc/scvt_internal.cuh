@@ -2,11 +2,23 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include "scvt.h"
 
 namespace scvt {
+
+// NVTX range over the host code that enqueues one phase of the method (bin,
+// topology, corners, quadrature, cell sums, reductions, direction, line
+// search, accept); profilers project it onto the GPU work it launches.
+// Header-only NVTX: a no-op unless a tool is attached.
+struct Phase {
+    explicit Phase(const char *name) { nvtxRangePushA(name); }
+    ~Phase() { nvtxRangePop(); }
+    Phase(const Phase &) = delete;
+    Phase &operator=(const Phase &) = delete;
+};
 
 // a generator in bin order: 32-byte aligned (x, y, z, unused)
 struct alignas(32) P4 {
@@ -269,8 +281,10 @@ void lloyd_project(int n, const double *c, double *zout, cudaStream_t s, int64_t
 void accept_pair(int n, const double *zt, const double *z, const double *gt, const double *g, double *S, double *Y,
                  double *partials, DevStatus *st, cudaStream_t s, int64_t *launches);
 // q = -H g by the two-loop recursion; pairs are given oldest first as host
-// arrays of device pointers, rho[k] -> 1/(y_k.s_k) on the device;
-// scal: device scratch of 128 doubles.  Leaves g.q in st->dots[3].
+// arrays of device pointers, rho[k] -> 1/(y_k.s_k) on the device; count <= 64;
+// scal: device scratch of kTwoLoopScratch doubles (the scalars alpha_k and
+// the coefficients, and a ticket counter).  Leaves g.q in st->dots[3].
+constexpr int kTwoLoopScratch = 136;
 // H0 = diag(h) per generator, or (h null) hs[0] I, or (both null) I.
 void two_loop(int n, const double *g, const double *h, const double *hs, int count, const double *const *S,
               const double *const *Y, const double *const *rho, double *q, double *partials, double *scal,

@@ -274,7 +274,7 @@ scvt_status scvt_server_create(const scvt_server_config *cfg, void *cuda_stream,
     if (e == cudaSuccess) e = cudaEventCreate(&S->ev_in);
     if (e == cudaSuccess) e = evalset_alloc(S->E, cfg->max_generators, cfg->max_jobs, cfg->precision, S->stream);
     if (e == cudaSuccess) e = cudaMalloc((void **)&S->partials, sizeof(double) * 4 * 1024);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&S->scal, sizeof(double) * 128);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&S->scal, sizeof(double) * kTwoLoopScratch);
     if (e != cudaSuccess) {
         cudaGetLastError();
         scvt_server_destroy(S);
