@@ -33,7 +33,6 @@ struct scvt_batch {
     EvalSet E;
     // resident vectors (concatenated)
     double *z = nullptr, *g = nullptr, *h = nullptr, *hist = nullptr, *rho_hist = nullptr;
-    double *partials = nullptr, *scal = nullptr;
     std::vector<Lane> lanes;
     bool solved_once = false;
     scvt_stats stats;
@@ -120,7 +119,7 @@ extern "C" {
 void scvt_batch_destroy(scvt_batch *BT) {
     if (!BT) return;
     evalset_free(BT->E);
-    void *ptrs[] = {BT->z, BT->g, BT->h, BT->hist, BT->rho_hist, BT->partials, BT->scal};
+    void *ptrs[] = {BT->z, BT->g, BT->h, BT->hist, BT->rho_hist};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (BT->ev_in) cudaEventDestroy(BT->ev_in);
@@ -157,7 +156,6 @@ scvt_status scvt_batch_create(const scvt_config *cfgs, int count, void *cuda_str
     if (e == cudaSuccess) e = balloc(BT, &(ptr), (cnt))
     AL(BT->z, n3); AL(BT->g, n3); AL(BT->h, N);
     AL(BT->hist, (size_t)(BT->m + 1) * 2 * n3); AL(BT->rho_hist, (size_t)count * kLaneRho);
-    AL(BT->partials, 4 * 1024); AL(BT->scal, kTwoLoopScratch);
 #undef AL
     std::vector<int> ns(count);
     std::vector<scvt_density> rhos(count);
@@ -247,7 +245,7 @@ scvt_status scvt_batch_lbfgs_solve(scvt_batch *BT, double *z, const scvt_solve_o
         bool any = false;
         for (Lane *L : lanes) any = any || !L->done;
         if (!any) break;
-        BK(lockstep_round(BT->E, lanes, BT->m, BT->partials, BT->scal, &BT->stats), "lockstep iteration");
+        BK(lockstep_round(BT->E, lanes, BT->m, &BT->stats), "lockstep iteration");
     }
     scvt_status ret = SCVT_OK;
     for (int b = 0; b < BT->B; ++b) {

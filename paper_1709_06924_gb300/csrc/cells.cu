@@ -1697,7 +1697,7 @@ __device__ int series_terms(const double *cf, double U) {
     return 0;
 }
 
-__global__ void k_dens_table(Density r, int M, double dth, double4 *meta, double *cfo, float2 *cdf, float *mag) {
+__global__ void k_dens_table(Density r, int M, double dth, TabCentre *meta, double *cfo, float2 *cdf, float *mag) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= M) return;
     // the centre c_j = cos(j dth) as rounded; sqrt(1 - c_j^2) and acos c_j from it
@@ -1774,7 +1774,7 @@ __global__ void k_dens_table(Density r, int M, double dth, double4 *meta, double
     // scaling; keeps the coefficients in FP32 range), and |cf_k| r_j^k
     int ex = 0;
     if (rj > 0.0) frexp(rj, &ex);
-    meta[j] = make_double4(ci, ldexp(1.0, -ex), rj, (double)Kj);
+    meta[j] = TabCentre{ci, ldexp(1.0, -ex), rj, (double)Kj};
     double rk = 1.0;
     for (int k = 0; k < kTabK; ++k) {
         cfo[(size_t)j * kTabK + k] = cf[k];
@@ -1796,12 +1796,12 @@ __device__ __forceinline__ int table_terms(const DensTab &T, double ci, float xa
     const float th = (ci >= 0.0) ? 2.0f * asinf(sqrtf((float)(0.5 * (1.0 - ci))))
                                  : 3.14159265f - 2.0f * asinf(sqrtf((float)(0.5 * (1.0 + ci))));
     j = min(T.M - 1, max(0, __float2int_rn(th / T.dth)));
-    const double4 mt = T.meta[j];
-    cj = mt.x;
-    if (!(mt.z > 0.0)) return 0;
+    const TabCentre mt = T.meta[j];
+    cj = mt.c;
+    if (!(mt.r > 0.0)) return 0;
     const float U = (float)fabs(ci - cj) + (1.0f + r2) * fmaxf(fmaxf(fabsf(xa), fabsf(xb)), fabsf(xm)) +
                     r2 * fabsf((float)ci) + 1e-6f * sqrtf(r2) + 1e-12f;
-    const float R = (float)mt.z;
+    const float R = (float)mt.r;
     if (!(U <= R)) return 0;
     // terms |cf_k| U^k = mag_k (U / r_j)^k, no overflow
     const float *mg = T.mag + (size_t)j * kTabK;
@@ -1987,7 +1987,7 @@ __global__ void __launch_bounds__(512) k_quad(Grid g, CellBuf cb, int ecap, Span
         // x_c.z_i in FP64 (it sets the series' argument)
         int K = 0, j = 0;
         double cj = 0.0, ci = 0.0;
-        const double4 *tmeta = nullptr;
+        const TabCentre *tmeta = nullptr;
         const double *tcf = nullptr;
         const float2 *tcdf = nullptr;
         if (rho.kind >= 2) {
@@ -2031,7 +2031,7 @@ __global__ void __launch_bounds__(512) k_quad(Grid g, CellBuf cb, int ecap, Span
                 const DensDF dd = g.rho ? dens_df(rho) : dd0;
                 const df eA = df3_dot(dd.ev, A);
                 const df u0 = (K > 0) ? df_from(ci - cj) : df{0.0f, 0.0f};
-                const float vs = (K > 0) ? (float)tmeta[j].y : 1.0f;
+                const float vs = (K > 0) ? (float)tmeta[j].scale : 1.0f;
                 // edge midpoint mu = (z_i + z_j) / |z_i + z_j|: with h = (z_j - z_i) / 2,
                 // mu - z_i = h + m (A + h), 1 - |A + h|^2 = -(|A|^2 - 1) - 2 A.h - |h|^2
                 const df3 hh{df{0.5f * dj.x.hi, 0.5f * dj.x.lo}, df{0.5f * dj.y.hi, 0.5f * dj.y.lo},
@@ -2411,7 +2411,7 @@ int dens_table_centres(int64_t n) {
 static size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 size_t dens_table_bytes(int M) {
-    return up256(sizeof(double4) * M) + up256(sizeof(double) * kTabK * M) + up256(sizeof(float2) * kTabK * M) +
+    return up256(sizeof(TabCentre) * M) + up256(sizeof(double) * kTabK * M) + up256(sizeof(float2) * kTabK * M) +
            up256(sizeof(float) * kTabK * M);
 }
 
@@ -2419,8 +2419,8 @@ cudaError_t dens_table_build(const Density &r, int M, void *buf, DensTab *out, c
     memset(out, 0, sizeof(*out));
     if (r.kind < 2 || M < 2 || !buf) return cudaSuccess;
     unsigned char *b = (unsigned char *)buf;
-    double4 *meta = (double4 *)b;
-    b += up256(sizeof(double4) * M);
+    TabCentre *meta = (TabCentre *)b;
+    b += up256(sizeof(TabCentre) * M);
     double *cf = (double *)b;
     b += up256(sizeof(double) * kTabK * M);
     float2 *cdf = (float2 *)b;

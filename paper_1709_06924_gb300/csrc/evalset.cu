@@ -28,6 +28,10 @@ size_t max_bins(int64_t cap_n, int cap_b) {
 
 size_t max_partials(int64_t cap_n, int cap_b) { return 4 * ((size_t)cap_n / 4096 + (size_t)cap_b + 1024); }
 
+// chunk sums of the segmented LBFGS kernels: per problem max(reduce_blocks(3n),
+// 4 reduce_blocks(n)) <= 4 (n / 4096 + 1) + 3 n / 4096 + 1
+size_t max_seg_partials(int64_t cap_n, int cap_b) { return 7 * ((size_t)cap_n / 4096) + 5 * (size_t)cap_b + 64; }
+
 // density-table pool: the tables of any layout of at most cap_b problems with
 // cap_n generators in all fit (sum of 8 sqrt(n_b) <= 8 sqrt(cap_n cap_b), plus
 // the 1,024-centre minimum per problem), capped at 1 GiB; a problem whose
@@ -165,7 +169,10 @@ int64_t evalset_bytes(int64_t cap_n, int cap_b, int precision) {
                       + 4 * 4;                // bin_of, sidx, list1, list2
     if (precision == 1) per_row += 16 * 16;   // vo
     const int64_t tabs = precision != 1 ? (int64_t)tab_pool_size(cap_n, cap_b) + (int64_t)cap_b * (int64_t)sizeof(DensTab) : 0;
-    return N * per_row + nb * 12 + (int64_t)max_partials(cap_n, cap_b) * 8 + (int64_t)cap_b * 512 + tabs + (1 << 20);
+    const int64_t seg = (int64_t)cap_b * (int64_t)(sizeof(SegLane) + 8 * kTwoLoopScratch) +
+                        8 * (int64_t)max_seg_partials(cap_n, cap_b);
+    return N * per_row + nb * 12 + (int64_t)max_partials(cap_n, cap_b) * 8 + (int64_t)cap_b * 512 + tabs + seg +
+           (1 << 20);
 }
 
 cudaError_t evalset_alloc(EvalSet &E, int64_t cap_n, int cap_b, int precision, cudaStream_t s) {
@@ -182,6 +189,8 @@ cudaError_t evalset_alloc(EvalSet &E, int64_t cap_n, int cap_b, int precision, c
     AL(E.d_rho, cap_b); AL(E.d_rhof, cap_b); AL(E.d_ist, cap_b); AL(E.d_st, 1);
     AL(E.zt, n3); AL(E.gt, n3); AL(E.ht, N); AL(E.fc, N); AL(E.q, n3); AL(E.nrm, N); AL(E.radius, N);
     AL(E.partials, E.partials_len);
+    E.seg_partials_len = max_seg_partials(cap_n, cap_b);
+    AL(E.d_seg, cap_b); AL(E.seg_partials, E.seg_partials_len); AL(E.seg_scal, (size_t)cap_b * kTwoLoopScratch);
     AL(E.zs, N); AL(E.zf, N); AL(E.zl, N); AL(E.zll, N); AL(E.cvx, N * kCellSlots); AL(E.cnb, N * kCellSlots);
     AL(E.cdeg, N); AL(E.eoff, N + 1); AL(E.ecell, 6 * N); AL(E.escan, scan_tmp_ints(N));
     AL(E.eacc, 5 * 6 * N);
@@ -198,6 +207,9 @@ cudaError_t evalset_alloc(EvalSet &E, int64_t cap_n, int cap_b, int precision, c
     if (e == cudaSuccess) e = cudaMallocHost((void **)&E.h_ist, sizeof(DevStatus) * cap_b);
     if (e == cudaSuccess) e = cudaMallocHost((void **)&E.h_st, sizeof(DevStatus));
     if (e == cudaSuccess) e = cudaMallocHost((void **)&E.h_active, sizeof(int) * cap_b);
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&E.h_seg, sizeof(SegLane) * cap_b);
+    // the segmented kernels' ticket counters start at 0 (each pass's last block resets its own)
+    if (e == cudaSuccess) e = cudaMemsetAsync(E.seg_scal, 0, sizeof(double) * cap_b * kTwoLoopScratch, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(E.radius, 0, sizeof(float) * N, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(E.q, 0, sizeof(double) * n3, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(E.nrm, 0, sizeof(double) * N, s);
@@ -210,11 +222,11 @@ void evalset_free(EvalSet &E) {
     E.graph = nullptr;
     void *ptrs[] = {E.d_inst, E.d_pinst, E.d_pbase, E.d_active, E.d_rho, E.d_rhof, E.d_ist, E.d_st, E.zt, E.gt,
                     E.ht, E.fc, E.q, E.nrm, E.radius, E.partials, E.zs, E.zf, E.zl, E.zll, E.cvx, E.cnb, E.cdeg, E.eoff,
-                    E.ecell, E.escan, E.eacc, E.vo, E.tab_pool, E.d_tabs, E.bin_of, E.count, E.start, E.cursor, E.scan_tmp, E.sidx,
+                    E.ecell, E.escan, E.eacc, E.vo, E.tab_pool, E.d_tabs, E.d_seg, E.seg_partials, E.seg_scal, E.bin_of, E.count, E.start, E.cursor, E.scan_tmp, E.sidx,
                     E.list1, E.list2};
     for (void *p : ptrs)
         if (p) cudaFree(p);
-    void *hp[] = {E.h_ist, E.h_st, E.h_active};
+    void *hp[] = {E.h_ist, E.h_st, E.h_active, E.h_seg};
     for (void *p : hp)
         if (p) cudaFreeHost(p);
     pipes_destroy(E.pipes);

@@ -62,6 +62,13 @@ struct EvalSet {
     std::vector<DensTab> tabs;
     int *bin_of = nullptr, *count = nullptr, *start = nullptr, *cursor = nullptr, *scan_tmp = nullptr;
     int *sidx = nullptr, *list1 = nullptr, *list2 = nullptr;
+    // segmented LBFGS of the problems (lockstep.cu): per-problem descriptors
+    // (device and pinned host copies), chunk sums and scalars; nblk3 / nblk1 =
+    // the blocks of the segmented grids of this layout
+    SegLane *d_seg = nullptr, *h_seg = nullptr;
+    double *seg_partials = nullptr, *seg_scal = nullptr;
+    size_t seg_partials_len = 0;
+    int nblk3 = 0, nblk1 = 0;
     // the captured evaluation
     cudaGraphExec_t graph = nullptr;
     int64_t graph_launches = 0, graph_cell_launches = 0;

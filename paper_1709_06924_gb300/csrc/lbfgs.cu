@@ -43,10 +43,15 @@ __device__ __forceinline__ void block_sum_store(double (&v)[NQ], double *dst) {
     }
 }
 
-__device__ __forceinline__ void chunk_of(int64_t n, int64_t &b0, int64_t &b1) {
-    int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
-    b0 = (int64_t)blockIdx.x * chunk;
+// contiguous chunk k of nb chunks of [0, n)
+__device__ __forceinline__ void chunk_range(int64_t n, int nb, int k, int64_t &b0, int64_t &b1) {
+    int64_t chunk = (n + nb - 1) / nb;
+    b0 = (int64_t)k * chunk;
     b1 = b0 + chunk < n ? b0 + chunk : n;
+}
+
+__device__ __forceinline__ void chunk_of(int64_t n, int64_t &b0, int64_t &b1) {
+    chunk_range(n, gridDim.x, blockIdx.x, b0, b1);
 }
 
 __global__ void k_reduce_eval(int n, const double *__restrict__ fcell, const double *__restrict__ g,
@@ -227,20 +232,22 @@ __device__ __forceinline__ double ld_stream(const double *a, unsigned long long 
 // Each block's chunk sum is published before its ticket; the last ticket
 // holder therefore reads every sum, and resets the ticket counter for the
 // next pass.
-__device__ __forceinline__ void finish_by_last_block(double v, double *__restrict__ partials, unsigned *ticket,
-                                                     const double *scale, const double *minus_from, double *out) {
+// (nb chunks; this block's chunk is k)
+__device__ __forceinline__ void finish_by_last_block(double v, double *__restrict__ partials, unsigned *ticket, int nb,
+                                                     int k, const double *scale, const double *minus_from,
+                                                     double *out) {
     double vv[1] = {v};
-    block_sum_store<1>(vv, partials + blockIdx.x);
+    block_sum_store<1>(vv, partials + k);
     __shared__ bool last;
     if (threadIdx.x == 0) {
         __threadfence();
-        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+        last = atomicAdd(ticket, 1u) == (unsigned)nb - 1;
     }
     __syncthreads();
     if (!last) return;
     __threadfence();
     double w[1] = {0.0};
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += kRT) w[0] += ((volatile double *)partials)[b];
+    for (int b = threadIdx.x; b < nb; b += kRT) w[0] += ((volatile double *)partials)[b];
     double res[1];
     block_sum_store<1>(w, res);
     if (threadIdx.x == 0) {
@@ -251,17 +258,13 @@ __device__ __forceinline__ void finish_by_last_block(double v, double *__restric
     }
 }
 
-// one step of the recursion: q = (q0 + sign coef x) [* h or * hs[0]] with
-// q0 = q (or -g0 for the first pass: coef = null, x = g0), then the next
-// scalar from w.q (finish_by_last_block)
-__global__ void __launch_bounds__(kRT) k_step(int64_t len, double *__restrict__ q, const double *__restrict__ coef,
-                                              double sign, const double *__restrict__ x,
-                                              const double *__restrict__ h, const double *__restrict__ hs,
-                                              const double *__restrict__ w, double *__restrict__ partials,
-                                              unsigned *ticket, const double *scale, const double *minus_from,
-                                              double *out) {
-    int64_t b0, b1;
-    chunk_of(len, b0, b1);
+// one step of the recursion over the chunk [b0, b1): q = (q0 + sign coef x)
+// [* h or * hs[0]] with q0 = q (or -x for the first pass: coef = null);
+// returns this thread's share of w.q
+__device__ __forceinline__ double step_chunk(int64_t b0, int64_t b1, double *__restrict__ q,
+                                             const double *__restrict__ coef, double sign, const double *__restrict__ x,
+                                             const double *__restrict__ h, const double *__restrict__ hs,
+                                             const double *__restrict__ w) {
     const unsigned long long pol = policy_evict_first();
     const double a = coef ? sign * coef[0] : 0.0;
     const double sc = hs ? hs[0] : 1.0;
@@ -291,7 +294,194 @@ __global__ void __launch_bounds__(kRT) k_step(int64_t len, double *__restrict__ 
             }
         }
     }
-    finish_by_last_block(v, partials, ticket, scale, minus_from, out);
+    return v;
+}
+
+// one step of the recursion, then the next scalar from w.q (finish_by_last_block)
+__global__ void __launch_bounds__(kRT) k_step(int64_t len, double *__restrict__ q, const double *__restrict__ coef,
+                                              double sign, const double *__restrict__ x,
+                                              const double *__restrict__ h, const double *__restrict__ hs,
+                                              const double *__restrict__ w, double *__restrict__ partials,
+                                              unsigned *ticket, const double *scale, const double *minus_from,
+                                              double *out) {
+    int64_t b0, b1;
+    chunk_of(len, b0, b1);
+    const double v = step_chunk(b0, b1, q, coef, sign, x, h, hs, w);
+    finish_by_last_block(v, partials, ticket, gridDim.x, blockIdx.x, scale, minus_from, out);
+}
+
+// ---- segmented LBFGS kernels (many problems per launch) ----
+// the problem whose blocks hold block `blk` (first block of each problem in
+// `first`, ascending)
+__device__ __forceinline__ int lane_of_block(const SegLane *__restrict__ L, int nl, int blk, bool acc) {
+    int lo = 0, hi = nl - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if ((acc ? L[mid].blk1 : L[mid].blk3) <= blk) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// pass t of every problem's two-loop recursion: t = 0 sets q = -g, passes
+// 1..c are the backward steps (newest pair first; the last applies the
+// initial matrix), passes c+1..2c the forward steps -- the same steps,
+// pointers and scalars as two_loop() for one problem
+__global__ void __launch_bounds__(kRT) k_seg_step(const SegLane *__restrict__ lanes, int nl, int t,
+                                                  double *__restrict__ q_rows) {
+    const int b = lane_of_block(lanes, nl, blockIdx.x, false);
+    const SegLane &L = lanes[b];
+    const int c = L.count;
+    if (!L.dir || t > 2 * c) return;
+    const int k = blockIdx.x - L.blk3;
+    if (k >= L.nb3) return;
+    const int64_t len = 3 * (int64_t)L.n;
+    double *q = q_rows + 3 * L.row;
+    double *alpha = L.scal, *coef = L.scal + 64;
+    unsigned *ticket = reinterpret_cast<unsigned *>(L.scal + 130);
+    auto S = [&](int j) { return (const double *)(L.hist + (size_t)L.slots[j] * L.slot_stride); };
+    auto Y = [&](int j) { return S(j) + L.y_off; };
+    auto R = [&](int j) { return (const double *)(L.rho + L.slots[j]); };
+    // initial matrix: diag(h), or gamma I (plain LBFGS with pairs), or I
+    const double *h0 = L.method == 1 ? nullptr : L.h;
+    const double *hs0 = (L.method == 1 && c > 0) ? L.rho + kLaneMaxM + 1 : nullptr;
+    const double *coef_p = nullptr, *x, *h = nullptr, *hs = nullptr, *w, *scale = nullptr, *minus = nullptr;
+    double sign = 0.0, *out;
+    if (t == 0) {
+        x = L.g;
+        if (c == 0) {
+            h = h0;
+            hs = hs0;
+            w = L.g;
+            out = &L.st->dots[3];
+        } else {
+            w = S(c - 1);
+            scale = R(c - 1);
+            out = alpha + c - 1;
+        }
+    } else if (t <= c) {
+        const int j = c - t;
+        coef_p = alpha + j;
+        sign = -1.0;
+        x = Y(j);
+        if (j > 0) {
+            w = S(j - 1);
+            scale = R(j - 1);
+            out = alpha + j - 1;
+        } else {
+            h = h0;
+            hs = hs0;
+            w = Y(0);
+            scale = R(0);
+            minus = alpha;
+            out = coef;
+        }
+    } else {
+        const int j = t - c - 1;
+        coef_p = coef + j;
+        sign = 1.0;
+        x = S(j);
+        if (j + 1 < c) {
+            w = Y(j + 1);
+            scale = R(j + 1);
+            minus = alpha + j + 1;
+            out = coef + j + 1;
+        } else {
+            w = L.g;
+            out = &L.st->dots[3];
+        }
+    }
+    int64_t b0, b1;
+    chunk_range(len, L.nb3, k, b0, b1);
+    const double v = step_chunk(b0, b1, q, coef_p, sign, x, h, hs, w);
+    finish_by_last_block(v, L.partials, ticket, L.nb3, k, scale, minus, out);
+}
+
+__global__ void k_seg_trial(const SegLane *__restrict__ lanes, const int *__restrict__ pinst, int64_t ntot,
+                            const double *__restrict__ q_rows, double *__restrict__ zt_rows,
+                            double *__restrict__ nrm_rows) {
+    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= ntot) return;
+    const SegLane &L = lanes[pinst[r]];
+    if (!L.trial) return;
+    const int64_t i = r - L.row;
+    const double a = L.alpha;
+    // the arithmetic of k_trial
+    double x = L.z[3 * i] + a * q_rows[3 * r];
+    double y = L.z[3 * i + 1] + a * q_rows[3 * r + 1];
+    double w = L.z[3 * i + 2] + a * q_rows[3 * r + 2];
+    double nr = sqrt(x * x + y * y + w * w);
+    zt_rows[3 * r] = x / nr;
+    zt_rows[3 * r + 1] = y / nr;
+    zt_rows[3 * r + 2] = w / nr;
+    nrm_rows[r] = nr;
+}
+
+__global__ void __launch_bounds__(kRT) k_seg_accept(const SegLane *__restrict__ lanes, int nl,
+                                                    const double *__restrict__ zt_rows,
+                                                    const double *__restrict__ gt_rows,
+                                                    const double *__restrict__ ht_rows) {
+    const int b = lane_of_block(lanes, nl, blockIdx.x, true);
+    const SegLane &L = lanes[b];
+    if (!L.accept) return;
+    const int k = blockIdx.x - L.blk1;
+    if (k >= L.nb1) return;
+    double *S = L.hist + (size_t)L.spare * L.slot_stride;
+    double *Y = S + L.y_off;
+    const double *zt = zt_rows + 3 * L.row, *gt = gt_rows + 3 * L.row, *ht = ht_rows + L.row;
+    int64_t b0, b1;
+    chunk_range(L.n, L.nb1, k, b0, b1);
+    // the arithmetic of k_accept, then the iterate moves to the trial point
+    double v[3] = {0.0, 0.0, 0.0};
+    double mv = 0.0;
+    for (int64_t i = b0 + threadIdx.x; i < b1; i += kRT) {
+        double s2 = 0.0;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const double zn = zt[3 * i + d], gn = gt[3 * i + d];
+            double s = zn - L.z[3 * i + d];
+            double y = gn - L.g[3 * i + d];
+            S[3 * i + d] = s;
+            Y[3 * i + d] = y;
+            v[0] += y * s;
+            v[1] += y * y;
+            v[2] += s * s;
+            s2 += s * s;
+            L.z[3 * i + d] = zn;
+            L.g[3 * i + d] = gn;
+        }
+        L.h[i] = ht[i];
+        mv = fmax(mv, s2);
+    }
+    if (mv > 0.0) atomicMax(&L.st->maxmove_bits, (unsigned long long)__double_as_longlong(sqrt(mv)));
+    // chunk sums, then the last block: the dots in the order of k_finish<3>,
+    // and 1/(y.s) (gamma) when the curvature test passes
+    block_sum_store<3>(v, L.partials + 4 * k);
+    __shared__ bool last;
+    unsigned *ticket = reinterpret_cast<unsigned *>(L.scal + 131);
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == (unsigned)L.nb1 - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double w[3] = {0.0, 0.0, 0.0};
+    for (int c = threadIdx.x; c < L.nb1; c += kRT)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) w[q] += ((volatile double *)L.partials)[4 * c + q];
+    double res[3];
+    block_sum_store<3>(w, res);
+    if (threadIdx.x == 0) {
+        L.st->dots[0] = res[0];
+        L.st->dots[1] = res[1];
+        L.st->dots[2] = res[2];
+        if (L.method != 2 && L.m > 0 && res[0] > 1e-12 * sqrt(res[1]) * sqrt(res[2])) {
+            L.rho[L.spare] = 1.0 / res[0];
+            if (L.method == 1) L.rho[kLaneMaxM + 1] = res[0] / res[1];
+        }
+        *ticket = 0u;
+    }
 }
 
 __global__ void k_differs(int64_t len, const double *__restrict__ a, const double *__restrict__ b, unsigned *flag) {
@@ -366,6 +556,26 @@ void set_rho(double *rho_dev, int k, const DevStatus *st, cudaStream_t s, int64_
 
 void set_gamma(double *gamma_dev, const DevStatus *st, cudaStream_t s, int64_t *launches) {
     k_set_gamma<<<1, 1, 0, s>>>(gamma_dev, st);
+    (*launches)++;
+}
+
+void seg_direction(const SegLane *lanes, int nl, int max_count, int nblk3, double *q_rows, cudaStream_t s,
+                   int64_t *launches) {
+    for (int t = 0; t <= 2 * max_count; ++t) {
+        k_seg_step<<<nblk3, kRT, 0, s>>>(lanes, nl, t, q_rows);
+        (*launches)++;
+    }
+}
+
+void seg_trial(const SegLane *lanes, const int *pinst, int64_t ntot, const double *q_rows, double *zt_rows,
+               double *nrm_rows, cudaStream_t s, int64_t *launches) {
+    k_seg_trial<<<(unsigned)((ntot + 255) / 256), 256, 0, s>>>(lanes, pinst, ntot, q_rows, zt_rows, nrm_rows);
+    (*launches)++;
+}
+
+void seg_accept(const SegLane *lanes, int nl, int nblk1, const double *zt_rows, const double *gt_rows,
+                const double *ht_rows, cudaStream_t s, int64_t *launches) {
+    k_seg_accept<<<nblk1, kRT, 0, s>>>(lanes, nl, zt_rows, gt_rows, ht_rows);
     (*launches)++;
 }
 

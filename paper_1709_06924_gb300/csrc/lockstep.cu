@@ -2,34 +2,78 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
+
 #include "lockstep.cuh"
 
 namespace scvt {
 
 namespace {
 
-double *slot_S(const Lane &L, int slot) { return L.hist + (size_t)slot * L.slot_stride; }
-double *slot_Y(const Lane &L, int slot) { return slot_S(L, slot) + L.y_off; }
-
-// two-loop direction of lane L into its q rows; g.q in the lane's status block
-void enqueue_direction(EvalSet &E, Lane &L, double *partials, double *scal, int64_t *launches) {
-    const double *S[kLaneMaxM], *Y[kLaneMaxM], *R[kLaneMaxM];
-    const int method = L.opt.method;
-    const int count = (method == 2) ? 0 : L.count;
-    for (int k = 0; k < count; ++k) {
-        const int sl = L.slots[k];
-        S[k] = slot_S(L, sl);
-        Y[k] = slot_Y(L, sl);
-        R[k] = L.rho + sl;
-    }
-    two_loop(L.n, L.g, method == 1 ? nullptr : L.h, (method == 1 && count > 0) ? L.rho + kLaneMaxM + 1 : nullptr,
-             count, S, Y, R, E.q + 3 * L.row, partials, scal, &E.d_ist[L.b], E.stream, launches);
-}
-
 cudaError_t sync_statuses(EvalSet &E) {
     cudaError_t e = cudaMemcpyAsync(E.h_ist, E.d_ist, sizeof(DevStatus) * E.B, cudaMemcpyDeviceToHost, E.stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(E.stream);
     return e;
+}
+
+// Descriptors of every problem of the layout for the segmented kernels:
+// geometry, resident buffers and chunking; the round's flags are cleared.
+// Problems without a lane this round keep all flags 0.
+void seg_layout(EvalSet &E, const std::vector<Lane *> &lanes, int m) {
+    int blk3 = 0, blk1 = 0;
+    size_t pb = 0;
+    for (int b = 0; b < E.B; ++b) {
+        SegLane &d = E.h_seg[b];
+        memset(&d, 0, sizeof(d));
+        d.row = E.geom[b].p0;
+        d.n = E.geom[b].n;
+        d.m = m;
+        d.nb3 = reduce_blocks(3 * (int64_t)d.n);
+        d.nb1 = reduce_blocks(d.n);
+        d.blk3 = blk3;
+        d.blk1 = blk1;
+        blk3 += d.nb3;
+        blk1 += d.nb1;
+        d.scal = E.seg_scal + (size_t)b * kTwoLoopScratch;
+        d.partials = E.seg_partials + pb;
+        pb += (size_t)std::max(d.nb3, 4 * d.nb1);
+        d.st = E.d_ist + b;
+    }
+    E.nblk3 = blk3;
+    E.nblk1 = blk1;
+    for (const Lane *L : lanes) {
+        SegLane &d = E.h_seg[L->b];
+        d.z = L->z;
+        d.g = L->g;
+        d.h = L->h;
+        d.hist = L->hist;
+        d.slot_stride = (int64_t)L->slot_stride;
+        d.y_off = (int64_t)L->y_off;
+        d.rho = L->rho;
+        d.method = L->opt.method;
+    }
+}
+
+cudaError_t seg_upload(EvalSet &E) {
+    return cudaMemcpyAsync(E.d_seg, E.h_seg, sizeof(SegLane) * E.B, cudaMemcpyHostToDevice, E.stream);
+}
+
+// the direction of every lane in dir (its history as the ring holds it; none for Lloyd)
+cudaError_t seg_directions(EvalSet &E, const std::vector<Lane *> &dir, int64_t *launches) {
+    for (int b = 0; b < E.B; ++b) E.h_seg[b].dir = 0;
+    int maxc = 0;
+    for (const Lane *L : dir) {
+        SegLane &d = E.h_seg[L->b];
+        d.dir = 1;
+        d.count = (L->opt.method == 2) ? 0 : L->count;
+        for (int k = 0; k < d.count; ++k) d.slots[k] = L->slots[k];
+        maxc = std::max(maxc, d.count);
+    }
+    cudaError_t e = seg_upload(E);
+    if (e != cudaSuccess) return e;
+    seg_direction(E.d_seg, E.B, maxc, E.nblk3, E.q, E.stream, launches);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return sync_statuses(E);
 }
 
 }  // namespace
@@ -55,8 +99,7 @@ scvt_status lane_options(const scvt_solve_opts *in, scvt_solve_opts *o) {
     return SCVT_OK;
 }
 
-cudaError_t lockstep_round(EvalSet &E, std::vector<Lane *> &lanes, int m, double *partials, double *scal,
-                           scvt_stats *stats) {
+cudaError_t lockstep_round(EvalSet &E, std::vector<Lane *> &lanes, int m, scvt_stats *stats) {
     cudaStream_t s = E.stream;
     int64_t *launches = &stats->kernel_launches;
     cudaError_t e;
@@ -83,11 +126,12 @@ cudaError_t lockstep_round(EvalSet &E, std::vector<Lane *> &lanes, int m, double
         if (stop) L->done = true;
         else act.push_back(L);
     }
-    // ---- directions (again, from an empty history, where one is not a descent direction)
+    seg_layout(E, lanes, m);
+    // ---- directions, one launch per pass for every lane (again, from an empty
+    // history, where one is not a descent direction)
     if (!act.empty()) {
         Phase ph("scvt batch directions");
-        for (Lane *L : act) enqueue_direction(E, *L, partials, scal, launches);
-        if ((e = sync_statuses(E)) != cudaSuccess) return e;
+        if ((e = seg_directions(E, act, launches)) != cudaSuccess) return e;
         std::vector<Lane *> redo;
         for (Lane *L : act) {
             L->d0 = E.h_ist[L->b].dots[3];
@@ -97,9 +141,8 @@ cudaError_t lockstep_round(EvalSet &E, std::vector<Lane *> &lanes, int m, double
             for (Lane *L : redo) {
                 lane_reset_history(*L, m);
                 L->rep.resets++;
-                enqueue_direction(E, *L, partials, scal, launches);
             }
-            if ((e = sync_statuses(E)) != cudaSuccess) return e;
+            if ((e = seg_directions(E, redo, launches)) != cudaSuccess) return e;
             for (Lane *L : redo) {
                 L->d0 = E.h_ist[L->b].dots[3];
                 if (!(L->d0 < 0.0)) {
@@ -124,11 +167,18 @@ cudaError_t lockstep_round(EvalSet &E, std::vector<Lane *> &lanes, int m, double
     bool first = true;
     Phase pl("scvt batch line search");
     while (!ls.empty() || (first && !init.empty())) {
-        for (int b = 0; b < E.B; ++b) E.h_active[b] = 0;
+        for (int b = 0; b < E.B; ++b) {
+            E.h_active[b] = 0;
+            E.h_seg[b].trial = 0;
+        }
         for (Lane *L : ls) {
-            const double a = L->unit_step ? 1.0 : L->ls.trial();
-            trial_point(L->n, L->z, E.q + 3 * L->row, a, E.zt + 3 * L->row, E.nrm + L->row, s, launches);
+            E.h_seg[L->b].alpha = L->unit_step ? 1.0 : L->ls.trial();
+            E.h_seg[L->b].trial = 1;
             E.h_active[L->b] = 1;
+        }
+        if (!ls.empty()) {
+            if ((e = seg_upload(E)) != cudaSuccess) return e;
+            seg_trial(E.d_seg, E.d_pinst, E.ntot, E.q, E.zt, E.nrm, s, launches);
         }
         if (first) {
             for (Lane *L : init) {
@@ -187,8 +237,12 @@ cudaError_t lockstep_round(EvalSet &E, std::vector<Lane *> &lanes, int m, double
         }
         ls.swap(next);
     }
-    // ---- accept (or restart)
+    // ---- accept (or restart): one launch for every accepting lane
     std::vector<Lane *> acc;
+    for (int b = 0; b < E.B; ++b) {
+        E.h_seg[b].accept = 0;
+        E.h_seg[b].trial = 0;
+    }
     for (Lane *L : act) {
         if (L->done) continue;
         L->rep.fevals += L->ls.nfev;
@@ -208,13 +262,14 @@ cudaError_t lockstep_round(EvalSet &E, std::vector<Lane *> &lanes, int m, double
             lane_reset_history(*L, m);
             L->rep.resets++;
         }
-        const int slot = L->spare;
-        cudaMemsetAsync(&E.d_ist[L->b].maxmove_bits, 0, sizeof(unsigned long long), s);
-        accept_pair(L->n, E.zt + 3 * L->row, L->z, E.gt + 3 * L->row, L->g, slot_S(*L, slot), slot_Y(*L, slot),
-                    partials, &E.d_ist[L->b], s, launches);
+        // (the status block's maxmove_bits was cleared by the last evaluation)
+        E.h_seg[L->b].accept = 1;
+        E.h_seg[L->b].spare = L->spare;
         acc.push_back(L);
     }
     if (!acc.empty()) {
+        if ((e = seg_upload(E)) != cudaSuccess) return e;
+        seg_accept(E.d_seg, E.B, E.nblk1, E.zt, E.gt, E.ht, s, launches);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if ((e = sync_statuses(E)) != cudaSuccess) return e;
     }
@@ -225,9 +280,8 @@ cudaError_t lockstep_round(EvalSet &E, std::vector<Lane *> &lanes, int m, double
         unsigned long long mb = ds.maxmove_bits;
         memcpy(&maxmove, &mb, sizeof(double));
         const int slot = L->spare;
+        // the same curvature test the accept kernel took (it has set 1/(y.s))
         if (L->opt.method != 2 && m > 0 && ys > 1e-12 * sqrt(yy) * sqrt(ss)) {
-            set_rho(L->rho, slot, &E.d_ist[L->b], s, launches);
-            if (L->opt.method == 1) set_gamma(L->rho + kLaneMaxM + 1, &E.d_ist[L->b], s, launches);
             if (L->count == m) {
                 int old = L->slots[0];
                 for (int k = 1; k < L->count; ++k) L->slots[k - 1] = L->slots[k];
@@ -244,9 +298,7 @@ cudaError_t lockstep_round(EvalSet &E, std::vector<Lane *> &lanes, int m, double
         } else if (L->opt.method != 2) {
             L->rep.skipped++;
         }
-        cudaMemcpyAsync(L->z, E.zt + 3 * L->row, sizeof(double) * 3 * L->n, cudaMemcpyDeviceToDevice, s);
-        cudaMemcpyAsync(L->g, E.gt + 3 * L->row, sizeof(double) * 3 * L->n, cudaMemcpyDeviceToDevice, s);
-        cudaMemcpyAsync(L->h, E.ht + L->row, sizeof(double) * L->n, cudaMemcpyDeviceToDevice, s);
+        // (z, g and h moved to the trial point in the accept kernel)
         L->Fprev = L->F;
         L->F = L->ls.last_f;
         L->gnorm = sqrt(L->g2_last);

@@ -20,8 +20,6 @@
 
 namespace scvt {
 
-constexpr int kLaneMaxM = 32;
-constexpr int kLaneRho = kLaneMaxM + 2;  // per-lane scalars: 1/(y.s) per slot, plain-LBFGS gamma last
 
 struct Lane {
     int b = 0;            // problem index in the EvalSet layout
@@ -49,10 +47,12 @@ void lane_reset_history(Lane &L, int m);
 scvt_status lane_options(const scvt_solve_opts *in, scvt_solve_opts *out);
 // one outer iteration of every lane that is not done, each with its own
 // options; lanes with need_init get their first evaluation (at z) in the
-// first evaluation round instead.  partials: >= 4 * 1024 doubles, scal: 128
-// doubles (shared scratch).  Returns a CUDA error only for failures of the
-// device itself; a problem's own failure ends that lane with rep.status set.
-cudaError_t lockstep_round(EvalSet &E, std::vector<Lane *> &lanes, int m, double *partials, double *scal,
-                           scvt_stats *stats);
+// first evaluation round instead.  The LBFGS steps of all lanes run as
+// segmented kernels (one launch per two-loop pass, one for the trial points
+// of a line-search round, one for the accepted pairs), each lane with the
+// single-problem kernels' chunking and arithmetic.  Returns a CUDA error only
+// for failures of the device itself; a problem's own failure ends that lane
+// with rep.status set.
+cudaError_t lockstep_round(EvalSet &E, std::vector<Lane *> &lanes, int m, scvt_stats *stats);
 
 }  // namespace scvt

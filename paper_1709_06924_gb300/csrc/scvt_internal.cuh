@@ -96,10 +96,16 @@ __device__ __forceinline__ double rho_value(const Density &r, double px, double 
 // once per density and problem size; each quadrature edge takes the centre
 // nearest to its generator and as many terms as its own range of u needs.
 constexpr int kTabK = 24;
+struct alignas(32) TabCentre {
+    double c;      // c_j = cos(theta_j)
+    double scale;  // 2^-e_j, the scale of the double-float coefficients (2^e_j >= r_j)
+    double r;      // validated radius r_j (0: none)
+    double K;      // terms at r_j
+};
 struct DensTab {
     int M;              // centres; 0 = no table (direct evaluation)
     float dth;          // theta spacing pi / (M - 1)
-    const double4 *meta;  // per centre: c_j, 2^-e_j (scale of the pairs, 2^e_j >= r_j), r_j, terms at r_j
+    const TabCentre *meta;  // per centre
     const double *cf;   // M x kTabK coefficients of the series in u
     const float2 *cdf;  // M x kTabK the same as double-float pairs, coefficients of the series in u 2^-e_j
     const float *mag;   // M x kTabK |cf_k| r_j^k in FP32 (the term count for a range |u| <= U <= r_j)
@@ -289,6 +295,50 @@ constexpr int kTwoLoopScratch = 136;
 void two_loop(int n, const double *g, const double *h, const double *hs, int count, const double *const *S,
               const double *const *Y, const double *const *rho, double *q, double *partials, double *scal,
               DevStatus *st, cudaStream_t s, int64_t *launches);
+// ---- segmented LBFGS kernels over the problems of a batch (lbfgs.cu) ----
+// A problem's LBFGS memory holds up to kLaneMaxM pairs; its scalars are
+// kLaneRho doubles: 1/(y.s) per history slot, then gamma (plain LBFGS).
+constexpr int kLaneMaxM = 32;
+constexpr int kLaneRho = kLaneMaxM + 2;
+// One problem of a batch as the segmented kernels see it.  Each problem
+// keeps the chunking of a single problem of its size (nb3 chunks of its 3n
+// direction components, nb1 chunks of its n generators), so its results
+// are bit for bit those of the single-problem kernels.
+struct SegLane {
+    int64_t row;                  // first row of the problem in the evaluation workspace
+    int n;                        // generators
+    int count;                    // pairs in this round's direction
+    int method;                   // 0 Lloyd-preconditioned LBFGS, 1 plain LBFGS, 2 Lloyd
+    int m;                        // LBFGS memory
+    int dir, trial, accept;       // takes part in the direction, the line-search round, the accept
+    int nb3, blk3, nb1, blk1;     // chunks, and the problem's first block in the segmented grids
+    int spare;                    // history slot that receives the accepted pair
+    int slots[kLaneMaxM];         // history slots of the direction's pairs, oldest first
+    double alpha;                 // trial step of the line-search round
+    double *z, *g, *h;            // resident iterate, gradient, preconditioner
+    double *hist;                 // S of slot k at hist + k slot_stride, Y at S + y_off
+    int64_t slot_stride, y_off;
+    double *rho;                  // kLaneRho scalars
+    double *scal;                 // kTwoLoopScratch
+    double *partials;             // max(nb3, 4 nb1) chunk sums
+    DevStatus *st;                // the problem's status block
+};
+// q of every problem taking part (rows of q_rows): 2 max_count + 1 passes,
+// each one launch over nblk3 = sum nb3 blocks; g.q in each problem's
+// st->dots[3]
+void seg_direction(const SegLane *lanes, int nl, int max_count, int nblk3, double *q_rows, cudaStream_t s,
+                   int64_t *launches);
+// zt = normalize(z + alpha q) for the rows of the problems of the round
+// (pinst: problem of each row)
+void seg_trial(const SegLane *lanes, const int *pinst, int64_t ntot, const double *q_rows, double *zt_rows,
+               double *nrm_rows, cudaStream_t s, int64_t *launches);
+// accepted pairs: s = zt - z, y = gt - g into the spare slot, y.s, y.y, s.s
+// and max |s_i| into st->dots / maxmove_bits, 1/(y.s) (and gamma) when the
+// curvature test passes, then z, g, h take the trial point's values; one
+// launch over nblk1 = sum nb1 blocks
+void seg_accept(const SegLane *lanes, int nl, int nblk1, const double *zt_rows, const double *gt_rows,
+                const double *ht_rows, cudaStream_t s, int64_t *launches);
+
 // gamma_dev[0] = y.s / y.y from st->dots (plain LBFGS scaling)
 void set_gamma(double *gamma_dev, const DevStatus *st, cudaStream_t s, int64_t *launches);
 void set_rho(double *rho_dev, int k, const DevStatus *st, cudaStream_t s, int64_t *launches);

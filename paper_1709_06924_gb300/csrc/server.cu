@@ -78,7 +78,6 @@ struct scvt_server {
     std::vector<int64_t> running;            // layout order
     std::vector<int64_t> laid_out;           // jobs in the current layout, in order
     bool relayout = false;
-    double *partials = nullptr, *scal = nullptr;
     std::chrono::steady_clock::time_point t0;
     scvt_stats stats;
     std::string err;
@@ -237,8 +236,6 @@ void scvt_server_destroy(scvt_server *S) {
         if (J && J->block) cudaFreeAsync(J->block, S->stream);
     if (S->stream) cudaStreamSynchronize(S->stream);
     evalset_free(S->E);
-    if (S->partials) cudaFree(S->partials);
-    if (S->scal) cudaFree(S->scal);
     if (S->ev_in) cudaEventDestroy(S->ev_in);
     if (S->stream) cudaStreamDestroy(S->stream);
     delete S;
@@ -273,8 +270,6 @@ scvt_status scvt_server_create(const scvt_server_config *cfg, void *cuda_stream,
     cudaError_t e = cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreate(&S->ev_in);
     if (e == cudaSuccess) e = evalset_alloc(S->E, cfg->max_generators, cfg->max_jobs, cfg->precision, S->stream);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&S->partials, sizeof(double) * 4 * 1024);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&S->scal, sizeof(double) * kTwoLoopScratch);
     if (e != cudaSuccess) {
         cudaGetLastError();
         scvt_server_destroy(S);
@@ -326,7 +321,7 @@ scvt_status scvt_server_step(scvt_server *S, int *running, int *queued) {
         if (S->relayout && (s = lay_out(S))) return s;
         std::vector<Lane *> lanes;
         for (int64_t id : S->running) lanes.push_back(&S->jobs[id]->lane);
-        SK(lockstep_round(S->E, lanes, S->cfg.lbfgs_m, S->partials, S->scal, &S->stats), "lockstep iteration");
+        SK(lockstep_round(S->E, lanes, S->cfg.lbfgs_m, &S->stats), "lockstep iteration");
         if ((s = retire(S))) return s;
     }
     if (running) *running = (int)S->running.size();
