@@ -643,53 +643,71 @@ def run_batched(args, local, prec, count=64):
             "statuses": sorted({r["status"] for r in reps})}
 
 
-def serve_stream(srv, jobs, arrivals, max_iter, tol):
+def serve_stream(srv, inst, arrivals, max_iter, tol, local, queue_cap=None):
     """Submit job k at arrivals[k] seconds (server clock, from the first
-    submission), stepping the server in between; returns per-job records."""
+    submission; None: whenever fewer than queue_cap jobs wait), stepping the
+    server in between.  A job's start is drawn on the device when it is
+    submitted and its result fetched to the device when it is done.
+    Returns per-job records."""
+    import torch
+    dev = torch.device("cuda", local)
     t0 = srv.clock()
-    ids = {}
-    k = 0
+    ids, recs = {}, {}
+    pending = set()
+    out = None
+    k = queued = 0
     while True:
         now = srv.clock() - t0
-        while k < len(jobs) and arrivals[k] <= now:
-            z, dens = jobs[k]
-            ids[k] = srv.submit(z, dens, max_iter=max_iter, grad_tol=tol)
-            k += 1
-        running, queued = srv.step()
-        if running == 0 and queued == 0:
-            if k == len(jobs):
+        while k < len(inst):
+            if arrivals is not None and arrivals[k] > now:
                 break
-            time.sleep(max(0.0, min(arrivals[k] - (srv.clock() - t0), 0.05)))
-    recs = []
-    for j in range(len(jobs)):
-        info = srv.job(ids[j])
-        recs.append(info)
-        srv.fetch(ids[j])
-    return recs
+            if arrivals is None and queued >= queue_cap:
+                break
+            n, dens, sd = inst[k]
+            ids[k] = srv.submit(I.uniform_sphere_device(n, sd, dev), dens, max_iter=max_iter, grad_tol=tol)
+            pending.add(k)
+            k += 1
+            queued += 1
+        running, queued = srv.step()
+        for j in sorted(pending):
+            info = srv.job(ids[j])
+            if info["state"] in (2, 3):
+                recs[j] = info
+                n = inst[j][0]
+                if out is None or out.shape[0] < n:
+                    out = torch.empty((n, 3), dtype=torch.float64, device=dev)
+                srv.fetch(ids[j], out[:n])
+                pending.discard(j)
+        if running == 0 and queued == 0 and not pending:
+            if k == len(inst):
+                break
+            if arrivals is not None:
+                time.sleep(max(0.0, min(arrivals[k] - (srv.clock() - t0), 0.05)))
+    return [recs[j] for j in range(len(inst))]
 
 
 def run_serving(args, local, prec, count=None):
     """A Poisson stream of solve requests through the continuous-batching
     server: N log-uniform in [40,962, n_hi], random tanh caps (the batched
     workloads' sampler), each job to ||grad E||_2 <= 1e-6 (at most max_iter
-    iterations).  A closed-loop pass (all jobs at t = 0) measures the service
-    capacity; the timed pass offers Poisson arrivals at 80 % of it."""
+    iterations).  A closed-loop pass (jobs submitted whenever fewer than 32
+    wait) measures the service capacity; the timed pass offers Poisson
+    arrivals at 80 % of it."""
     from paper_1709_06924_gb300.engine import Server
     count = count or args.serve_jobs
     inst = I.sample_batched_instances(count, args.seed + 7, n_lo=40962, n_hi=args.serve_n_hi)
-    jobs = [(I.uniform_sphere(n, sd), d) for n, d, sd in inst]
     max_iter, tol = args.serve_max_iter, 1e-6
     n_max = max(n for n, _, _ in inst)
     cap_n = max(3 * n_max, 2_000_000)
     with Server(max_generators=cap_n, max_jobs=32, precision=prec, device=local) as srv:
-        closed = serve_stream(srv, jobs, [0.0] * count, max_iter, tol)
+        closed = serve_stream(srv, inst, None, max_iter, tol, local, queue_cap=32)
         t_closed = max(r["t_done"] for r in closed) - min(r["t_submit"] for r in closed)
         rate = 0.8 * count / t_closed
         rng = np.random.default_rng(args.seed + 11)
         arrivals = np.cumsum(rng.exponential(1.0 / rate, size=count))
         arrivals -= arrivals[0]
         ev0 = srv.stats()["evaluations"]
-        recs = serve_stream(srv, jobs, list(arrivals), max_iter, tol)
+        recs = serve_stream(srv, inst, list(arrivals), max_iter, tol, local)
         evs = srv.stats()["evaluations"] - ev0
     lat = np.array([r["t_done"] - r["t_submit"] for r in recs])
     wait = np.array([r["t_admit"] - r["t_submit"] for r in recs])
@@ -697,6 +715,7 @@ def run_serving(args, local, prec, count=None):
     units = sum(n * r["report"]["iters"] for (n, _, _), r in zip(inst, recs))
     iters = [r["report"]["iters"] for r in recs]
     return {"jobs": count, "n_range": [40962, args.serve_n_hi], "n_max_drawn": int(n_max),
+            "generators_total": int(sum(n for n, _, _ in inst)),
             "precision": FORM_NAME[prec], "grad_tol": tol, "max_iter": max_iter,
             "converged": int(sum(r["report"]["converged"] for r in recs)),
             "closed_loop_seconds": t_closed, "arrival_rate_per_s": rate, "offered_load": 0.8,
@@ -704,6 +723,7 @@ def run_serving(args, local, prec, count=None):
             "p50_queue_wait_s": float(np.percentile(wait, 50)), "makespan_s": span,
             "value": units / span, "unit": "generator-updates/s", "evaluations": evs,
             "iters_min_median_max": [int(min(iters)), int(np.median(iters)), int(max(iters))],
+            "inputs": "seeded uniform starts drawn on the device per job (torch Philox)",
             "note": "%d of the 2,000 jobs of the full stream" % count if count < 2000 else None}
 
 

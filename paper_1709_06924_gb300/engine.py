@@ -340,9 +340,11 @@ class Server:
         d["report"] = {f: getattr(i.report, f) for f, _ in capi.scvt_solve_report._fields_}
         return d
 
-    def fetch(self, jid: int):
-        z = np.empty((self.sizes[jid], 3))
-        capi.scvt_server_fetch(self._s, jid, z.ctypes.data)
+    def fetch(self, jid: int, out=None):
+        """The finished job's generators: into `out` (a numpy array or a
+        device tensor, n x 3) or a new numpy array."""
+        z = np.empty((self.sizes[jid], 3)) if out is None else out
+        capi.scvt_server_fetch(self._s, jid, _ptr(z))
         return z
 
     def clock(self) -> float:

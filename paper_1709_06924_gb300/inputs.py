@@ -73,6 +73,25 @@ def uniform_sphere(n: int, seed: int) -> np.ndarray:
     return np.ascontiguousarray(out)
 
 
+def uniform_sphere_device(n: int, seed: int, device):
+    """n points uniform on S^2 drawn on a CUDA device (torch's Philox generator
+    seeded with `seed`): three standard normals per point, scaled to unit
+    length (the recipe of uniform_sphere, another generator).  For request
+    streams of millions of generators per job, where drawing on the host
+    would set the pace; nothing drawn here is compared with the oracle."""
+    import torch
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed))
+    x = torch.randn((n, 3), generator=gen, device=device, dtype=torch.float64)
+    r = torch.linalg.vector_norm(x, dim=1, keepdim=True)
+    bad = (r < 1e-3).squeeze(1)
+    while bool(bad.any()):
+        x[bad] = torch.randn((int(bad.sum()), 3), generator=gen, device=device, dtype=torch.float64)
+        r = torch.linalg.vector_norm(x, dim=1, keepdim=True)
+        bad = (r < 1e-3).squeeze(1)
+    return (x / r).contiguous()
+
+
 def _unit_rows(p) -> np.ndarray:
     p = np.asarray(p, dtype=np.float64)
     return np.ascontiguousarray(p / np.sqrt((p * p).sum(axis=1))[:, None])

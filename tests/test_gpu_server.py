@@ -117,3 +117,35 @@ def test_submit_rejects_jobs_that_can_never_run():
             srv.submit(z, I.density_uniform())
         with pytest.raises(capi.ScvtError):  # no job 0
             capi.scvt_server_fetch(srv._s, 0, z.ctypes.data)
+
+
+@pytest.mark.parametrize("iters", [1, 5])
+def test_served_job_in_a_mix_matches_the_oracle(iters):
+    # a 2,562-generator job served while larger jobs run beside it, against
+    # the FP64 oracle's Lloyd-preconditioned LBFGS in lockstep: same accepted
+    # iterations and evaluations, energy to 1e-12, iterate to 1e-11
+    import oracle
+    dens = I.density_x3()
+    z = I.uniform_sphere(2562, 321)
+    zo, rep_o, _ = oracle.lbfgs_solve(z, dens, lbfgs_m=7, max_iter=iters, grad_tol=0.0)
+    others = [(I.uniform_sphere(20001, 322), I.WORKLOADS["tanh-163842"].density),
+              (I.uniform_sphere(9001, 323), I.density_x64())]
+    with Server(max_generators=40000, max_jobs=3, lbfgs_m=7) as srv:
+        ids = [srv.submit(zz, d, max_iter=8, grad_tol=0.0) for zz, d in others[:1]]
+        srv.step()
+        jid = srv.submit(z, dens, max_iter=iters, grad_tol=0.0)
+        ids.append(srv.submit(*others[1], max_iter=8, grad_tol=0.0))
+        max_running = 0
+        while True:
+            running, queued = srv.step()
+            max_running = max(max_running, running)
+            if running == 0 and queued == 0:
+                break
+        info = srv.job(jid)
+        zs = srv.fetch(jid)
+    assert max_running == 3
+    r = info["report"]
+    assert r["iters"] == rep_o["iters"] == iters
+    assert r["fevals"] == rep_o["fevals"]
+    assert abs(r["energy"] - rep_o["energy"]) <= 1e-12 * rep_o["energy"]
+    assert np.abs(zs - zo).max() <= 1e-11
