@@ -350,12 +350,12 @@ def df_inst_per_generator(series_len: float) -> float:
 #       python bench.py --steps 2 --warmup 1 --no-other-form --no-time-to-tol --no-batched
 #       --no-serving --no-table1 --no-chain --no-cpu-baseline --no-e2e
 # and likewise for k_topo_warp (per cell, by lanes per cell).
-QUAD_INST_PER_GENERATOR = 4536632457 / 2621442
-TOPO_INST_PER_CELL = {32: 3153936979 / 2621442, 16: 1873542833 / 2621442}
-# DRAM bytes of one k_quad launch at N = 163,842 (ncu dram__bytes_read.sum +
-# dram__bytes_write.sum), scaled by the number of generators; None once the
-# kernel has changed since that capture
-QUAD_DRAM_BYTES_163842 = None
+QUAD_INST_PER_GENERATOR = 4940772009 / 2621442
+TOPO_INST_PER_CELL = {32: 3335526320 / 2621442, 16: 2225292670 / 2621442}
+# DRAM bytes of one k_quad launch at N = 163,842 (ncu --set full:
+# dram__bytes_read.sum + dram__bytes_write.sum, 71.75 + 11.06 MB), scaled
+# by the number of generators; None once the kernel has changed since
+QUAD_DRAM_BYTES_163842 = 82.811392e6
 
 
 def quad_traffic_bytes(n: int):
