@@ -442,22 +442,39 @@ def roofline_of(prec, w, quad_ms, topo_ms, st, lanes=32, sms=152, mhz=2070.0, cl
         "work_source": "ncu one-pass smsp__inst_executed.sum of k_topo_warp in the timed steps at N = 2,621,442"})
 
 
-def two_loop_roofline(w, warmup, iters, lbfgs_ms):
-    """HBM roofline of the LBFGS direction (the two-loop recursion of Sec.
-    2.2.2 with diag(h) as the initial inverse Hessian): algorithmic traffic
-    per generator (4c + 2) x 24 bytes with c stored pairs (each history
-    vector read twice, g read, q written), c = min(warm-up + i, m) in timed
-    iteration i, over the CUDA-event time of the direction launches in the
-    timed steps."""
+def two_loop_ops_per_component(c):
+    """FP64 operations of the two-loop recursion (Sec. 2.2.2) per direction
+    component with c stored pairs: one multiply-add per dot-product term and
+    per axpy term in each loop (4c), the initial matrix's multiply and the
+    g.q term of the line search's first derivative."""
+    return 4 * c + 2
+
+
+def two_loop_roofline(w, warmup, iters, lbfgs_ms, sms, mhz):
+    """Roofline of the LBFGS direction (the two-loop recursion of Sec. 2.2.2
+    with diag(h) as the initial inverse Hessian), c = min(warm-up + i, m)
+    pairs in timed iteration i, over the CUDA-event time of the direction
+    launches in the timed steps.  On GB300 the FP64 pipe bounds it: 4c + 2
+    FP64 operations per component (8c + 3 flop) against the HBM traffic of
+    the recursion with the direction kept on chip, (4c + 2) x 24 bytes per
+    generator (each history vector read twice, g read, q written), which
+    takes half the time at the measured copy bandwidth.  Both fractions are
+    reported; "frac" is the FP64 one."""
     if not iters or lbfgs_ms <= 0:
         return None
     counts = [min(warmup + i, w.lbfgs_m) for i in range(iters)]
+    secs = lbfgs_ms * 1e-3
+    flops = sum(3 * (2 * two_loop_ops_per_component(c) - 1) for c in counts) * w.n
     alg = sum((4 * c + 2) * 24 for c in counts) * w.n
-    peak, src = measured_hbm_gbs()
-    achieved = alg / (lbfgs_ms * 1e-3) / 1e9
-    return {"bound": "hbm", "kernel": "LBFGS direction (two-loop)", "achieved": achieved, "peak": peak,
-            "unit": "GB/s", "frac": achieved / peak, "traffic": None, "algorithmic_bytes": alg,
-            "peak_source": src, "pairs_per_iteration": counts, "ms_total": lbfgs_ms}
+    peak = fp64_peak_flops(sms, mhz)
+    hbm_peak, src = measured_hbm_gbs()
+    hbm = alg / secs / 1e9
+    return {"bound": "fp64", "kernel": "LBFGS direction (two-loop)", "achieved": flops / secs / 1e12,
+            "peak": peak / 1e12, "unit": "TFLOP/s", "frac": flops / secs / peak, "traffic": None,
+            "peak_source": "derived: %d SMs x 2 DFMA x 2 flop x %.0f MHz" % (sms, mhz),
+            "algorithmic_flops": flops, "pairs_per_iteration": counts, "ms_total": lbfgs_ms,
+            "hbm": {"achieved": hbm, "peak": hbm_peak, "unit": "GB/s", "frac": hbm / hbm_peak,
+                    "algorithmic_bytes": alg, "peak_source": src}}
 
 
 # ------------------------------------------------------------------ forms
@@ -965,7 +982,7 @@ def run_ours(args, w):
             "eval_ms_avg": st["eval_ms"] / max(st["evaluations"], 1),
             "lbfgs_ms_total": st["lbfgs_ms"],
             "fevals_per_s": st["evaluations"] / t_max if t_max > 0 else None,
-            "roofline_two_loop": two_loop_roofline(w, args.warmup, iters, st["lbfgs_ms"]),
+            "roofline_two_loop": two_loop_roofline(w, args.warmup, iters, st["lbfgs_ms"], sms, mhz),
             "other_forms": others,
             "mixed_error_vs_fp64_form": others_err,
             "batched": batched,

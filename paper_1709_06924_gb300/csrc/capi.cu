@@ -23,7 +23,7 @@ using namespace scvt;
 
 namespace {
 
-constexpr int kMaxM = 32;       // history pairs
+constexpr int kMaxM = kLaneMaxM;  // history pairs
 constexpr int kDefaultK0 = 32;
 
 struct Bufs {
@@ -36,10 +36,9 @@ struct Bufs {
     double *nrm = nullptr;                   // |z + alpha q|
     double *mass = nullptr, *moment = nullptr;
     double *stage_a = nullptr, *stage_b = nullptr;  // host-pointer staging (3n each)
-    double *partials = nullptr;              // 4 * 1024
+    double *partials = nullptr;              // kCmpQ * 1024 chunk sums
     double *scal = nullptr;                  // two-loop scalars (kTwoLoopScratch)
-    double *rho = nullptr;                   // kMaxM + 1
-    double *gamma = nullptr;                 // plain LBFGS scaling of H0
+    double *rho = nullptr;                   // kLaneRho: 1/(y.s) per slot, gamma, the products s_a.y_b
     double *hist = nullptr;                  // (m + 1) slots of S and Y, 3n each
     P4 *zs = nullptr;
     float4 *zf = nullptr, *zl = nullptr, *zll = nullptr;
@@ -73,6 +72,7 @@ struct scvt_handle {
     // history ring: slot order (oldest first) and one spare slot
     int hist_slots[kMaxM + 1];
     int hist_count = 0;
+    bool new_pair = false;  // a pair was stored after the last direction
     int spare = 0;
     bool state_valid = false;  // z, g, h, F describe the current iterate
     double F = 0.0, gnorm = 0.0;
@@ -257,24 +257,45 @@ scvt_status copy_out(scvt_handle *H, double *dst, const double *src, size_t coun
 // history bookkeeping
 void hist_reset(scvt_handle *H) {
     H->hist_count = 0;
+    H->new_pair = false;
     for (int k = 0; k <= H->m; ++k) H->hist_slots[k] = k;
     H->spare = H->m;  // slot m is the first spare
 }
 
 // method 0: H0 = diag(h); 1: gamma I (I with an empty memory); 2: Lloyd, diag(h) and no memory
+// the handle's LBFGS state as the direction kernels see one problem
+SegLane single_lane(scvt_handle *H, int count, int method) {
+    SegLane L;
+    memset(&L, 0, sizeof(L));
+    L.n = H->n;
+    L.count = count;
+    L.method = method;
+    L.m = H->m;
+    L.dir = 1;
+    L.nb3 = reduce_blocks(3 * (int64_t)H->n);
+    L.nb1 = reduce_blocks(H->n);
+    for (int k = 0; k < count; ++k) L.slots[k] = H->hist_slots[k];
+    L.z = H->b.z;
+    L.g = H->b.g;
+    L.h = H->b.h;
+    L.hist = slot_S(H, 0);
+    L.yhist = slot_Y(H, 0);
+    L.slot_stride = 2 * 3 * (int64_t)H->n;
+    L.rho = H->b.rho;
+    L.scal = H->b.scal;
+    L.partials = H->b.partials;
+    L.st = H->b.st;
+    return L;
+}
+
 scvt_status make_direction(scvt_handle *H, double *d0, int method) {
-    const double *S[kMaxM], *Y[kMaxM], *R[kMaxM];
     const int count = (method == 2) ? 0 : H->hist_count;
-    for (int k = 0; k < count; ++k) {
-        int sl = H->hist_slots[k];
-        S[k] = slot_S(H, sl);
-        Y[k] = slot_Y(H, sl);
-        R[k] = H->b.rho + sl;
-    }
     Phase ph("scvt direction");
     if (H->profiling) cudaEventRecord(H->ev_l0, H->stream);
-    two_loop(H->n, H->b.g, method == 1 ? nullptr : H->b.h, (method == 1 && count > 0) ? H->b.gamma : nullptr, count,
-             S, Y, R, H->b.q, H->b.partials, H->b.scal, H->b.st, H->stream, &H->stats.kernel_launches);
+    SegLane L = single_lane(H, count, method);
+    L.new_pair = H->new_pair ? 1 : 0;
+    H->new_pair = false;
+    lane_direction(L, H->b.q, H->stream, &H->stats.kernel_launches);
     if (H->profiling) cudaEventRecord(H->ev_l1, H->stream);
     CK(cudaGetLastError(), "two-loop launch");
     CK(cudaMemcpyAsync(&H->st_host->dots[3], &H->b.st->dots[3], sizeof(double), cudaMemcpyDeviceToHost, H->stream),
@@ -340,7 +361,7 @@ void scvt_destroy(scvt_handle *H) {
     if (!H) return;
     Bufs &b = H->b;
     void *ptrs[] = {b.z, b.zt, b.g, b.gt, b.h, b.ht, b.fc, b.q, b.yv, b.nrm, b.mass, b.moment, b.stage_a, b.stage_b,
-                    b.partials, b.scal, b.rho, b.gamma, b.hist, b.zs, b.zf, b.zl, b.zll, b.cvx, b.cnb, b.cdeg, b.eoff, b.ecell, b.escan, b.eacc, b.vo, b.tab, b.bin_of, b.count, b.start, b.cursor, b.scan_tmp,
+                    b.partials, b.scal, b.rho, b.hist, b.zs, b.zf, b.zl, b.zll, b.cvx, b.cnb, b.cdeg, b.eoff, b.ecell, b.escan, b.eacc, b.vo, b.tab, b.bin_of, b.count, b.start, b.cursor, b.scan_tmp,
                     b.sidx, b.list1, b.list2, b.deg, b.radius, b.st};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -392,7 +413,7 @@ scvt_status scvt_create(const scvt_config *cfg, void *cuda_stream, scvt_handle *
     AL(b.z, n3); AL(b.zt, n3); AL(b.g, n3); AL(b.gt, n3); AL(b.h, n); AL(b.ht, n); AL(b.fc, n);
     AL(b.q, n3); AL(b.yv, n3); AL(b.nrm, n); AL(b.mass, n); AL(b.moment, n3);
     AL(b.stage_a, n3); AL(b.stage_b, n3);
-    AL(b.partials, 4 * 1024); AL(b.scal, kTwoLoopScratch); AL(b.rho, kMaxM + 1); AL(b.gamma, 1);
+    AL(b.partials, kCmpQ * 1024); AL(b.scal, kTwoLoopScratch); AL(b.rho, kLaneRho);
     AL(b.hist, (size_t)(H->m + 1) * 2 * n3);
     AL(b.zs, n); AL(b.zf, n); AL(b.zl, n); AL(b.zll, n); AL(b.cvx, (size_t)n * kCellSlots); AL(b.cnb, (size_t)n * kCellSlots);
     AL(b.cdeg, n); AL(b.eoff, n + 1); AL(b.ecell, 6 * (size_t)n); AL(b.escan, scan_tmp_ints(n));
@@ -608,8 +629,13 @@ scvt_status scvt_lbfgs_direction(scvt_handle *H, const double *g, const double *
         return fail(H, SCVT_ERR_INVALID, "scvt_lbfgs_direction takes device pointers");
     const size_t n3 = 3 * (size_t)H->n;
     std::vector<const double *> Sp(count), Yp(count), Rp(count);
+    // 1/(y.s) of each pair (and, for the gathered passes, the products
+    // s_a.y_b), and the direction's own scratch: the handle's solver state
+    // stays untouched
     double *rho = nullptr;
-    if (count > 0) CK(cudaMallocAsync((void **)&rho, sizeof(double) * count, H->stream), "rho buffer");
+    const size_t nrho = count > kCmpMax ? (size_t)count : (size_t)kLaneRho;
+    CK(cudaMallocAsync((void **)&rho, sizeof(double) * (nrho + kTwoLoopScratch), H->stream), "rho buffer");
+    double *scal = rho + nrho;
     int64_t *L = &H->stats.kernel_launches;
     for (int k = 0; k < count; ++k) {
         Sp[k] = S + k * n3;
@@ -618,9 +644,24 @@ scvt_status scvt_lbfgs_direction(scvt_handle *H, const double *g, const double *
         dot_to((int64_t)n3, Yp[k], Sp[k], H->b.partials, &H->b.st->dots[0], H->stream, L);
         set_rho(rho, k, H->b.st, H->stream, L);
     }
-    two_loop(H->n, g, hdiag, nullptr, count, Sp.data(), Yp.data(), Rp.data(), q, H->b.partials, H->b.scal, H->b.st,
-             H->stream, L);
-    if (rho) cudaFreeAsync(rho, H->stream);
+    if (count >= 1 && count <= kCmpMax) {
+        SegLane D = single_lane(H, 0, 0);
+        D.count = count;
+        for (int k = 0; k < count; ++k) D.slots[k] = k;
+        D.g = const_cast<double *>(g);
+        D.h = const_cast<double *>(hdiag);
+        D.hist = const_cast<double *>(S);
+        D.yhist = const_cast<double *>(Y);
+        D.slot_stride = (int64_t)n3;
+        D.rho = rho;
+        D.scal = scal;
+        lane_pair_products(D, H->stream, L);
+        lane_direction(D, q, H->stream, L);
+    } else {
+        two_loop(H->n, g, hdiag, nullptr, count, Sp.data(), Yp.data(), Rp.data(), q, H->b.partials, scal, H->b.st,
+                 H->stream, L);
+    }
+    cudaFreeAsync(rho, H->stream);
     CK(cudaGetLastError(), "two-loop launch");
     CK(cudaStreamSynchronize(H->stream), "two-loop");
     return SCVT_OK;
@@ -758,7 +799,7 @@ scvt_status scvt_lbfgs_solve(scvt_handle *H, double *z, const scvt_solve_opts *o
         memcpy(&maxmove, &mb, sizeof(double));
         if (o.method != 2 && H->m > 0 && ys > 1e-12 * sqrt(yy) * sqrt(ss)) {
             set_rho(B.rho, slot, B.st, s, &H->stats.kernel_launches);
-            if (o.method == 1) set_gamma(B.gamma, B.st, s, &H->stats.kernel_launches);
+            if (o.method == 1) set_gamma(B.rho + kLaneMaxM + 1, B.st, s, &H->stats.kernel_launches);
             if (H->hist_count == H->m) {
                 // the oldest pair's slot becomes the spare
                 int old = H->hist_slots[0];
@@ -774,6 +815,7 @@ scvt_status scvt_lbfgs_solve(scvt_handle *H, double *z, const scvt_solve_opts *o
                     if (!used[k]) { H->spare = k; break; }
             }
             H->hist_slots[H->hist_count++] = slot;
+            H->new_pair = true;
         } else if (o.method != 2) {
             rep.skipped++;
         }

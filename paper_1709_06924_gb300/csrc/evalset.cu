@@ -28,9 +28,12 @@ size_t max_bins(int64_t cap_n, int cap_b) {
 
 size_t max_partials(int64_t cap_n, int cap_b) { return 4 * ((size_t)cap_n / 4096 + (size_t)cap_b + 1024); }
 
-// chunk sums of the segmented LBFGS kernels: per problem max(reduce_blocks(3n),
-// 4 reduce_blocks(n)) <= 4 (n / 4096 + 1) + 3 n / 4096 + 1
-size_t max_seg_partials(int64_t cap_n, int cap_b) { return 7 * ((size_t)cap_n / 4096) + 5 * (size_t)cap_b + 64; }
+// chunk sums of the segmented LBFGS kernels: per problem max(kCmpQ nb3,
+// 4 nb1) <= kCmpQ (3n/4096 + 1) + 4 (n/4096 + 1), nb3 = reduce_blocks(3n),
+// nb1 = reduce_blocks(n)
+size_t max_seg_partials(int64_t cap_n, int cap_b) {
+    return (3 * kCmpQ + 4) * ((size_t)cap_n / 4096) + (kCmpQ + 4) * (size_t)cap_b + 64 + 3 * kCmpQ + 4;
+}
 
 // density-table pool: the tables of any layout of at most cap_b problems with
 // cap_n generators in all fit (sum of 8 sqrt(n_b) <= 8 sqrt(cap_n cap_b), plus

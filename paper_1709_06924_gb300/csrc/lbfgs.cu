@@ -8,11 +8,14 @@
 // on the binning of an evaluation.
 //
 // The two-loop recursion (Sec. 2.2.2) keeps its scalars alpha_k, beta_k on
-// the device: each pass fuses the axpy of one step with the dot product of
-// the next, and the pass's last block to finish turns the chunk sums into
-// the next scalar, so the whole direction is 2 count + 1 back-to-back
-// launches without a host round trip.
+// the device.  With up to kCmpMax pairs it runs as three gathered passes
+// (each vector of the history read once or twice per direction, see the
+// comment above cmp_pass_a); otherwise one pass per step, each fusing the
+// axpy of one step with the dot product of the next.  A pass's last block
+// to finish turns the chunk sums into the next scalars, so the direction
+// runs back to back without a host round trip.
 #include <math.h>
+#include <string.h>
 
 #include "scvt_internal.cuh"
 
@@ -230,8 +233,9 @@ __device__ __forceinline__ double ld_stream(const double *a, unsigned long long 
 // blocks to finish: the chunk sums in block order (the same fixed partition
 // as every reduction here), out = scale * sum, or minus_from - scale * sum.
 // Each block's chunk sum is published before its ticket; the last ticket
-// holder therefore reads every sum, and resets the ticket counter for the
-// next pass.
+// holder therefore reads every sum (at L2, where they were published: the
+// loads bypass L1 and need not be ordered among themselves), and resets the
+// ticket counter for the next pass.
 // (nb chunks; this block's chunk is k)
 __device__ __forceinline__ void finish_by_last_block(double v, double *__restrict__ partials, unsigned *ticket, int nb,
                                                      int k, const double *scale, const double *minus_from,
@@ -247,7 +251,7 @@ __device__ __forceinline__ void finish_by_last_block(double v, double *__restric
     if (!last) return;
     __threadfence();
     double w[1] = {0.0};
-    for (int b = threadIdx.x; b < nb; b += kRT) w[0] += ((volatile double *)partials)[b];
+    for (int b = threadIdx.x; b < nb; b += kRT) w[0] += __ldcg(partials + b);
     double res[1];
     block_sum_store<1>(w, res);
     if (threadIdx.x == 0) {
@@ -323,24 +327,25 @@ __device__ __forceinline__ int lane_of_block(const SegLane *__restrict__ L, int 
     return lo;
 }
 
-// pass t of every problem's two-loop recursion: t = 0 sets q = -g, passes
-// 1..c are the backward steps (newest pair first; the last applies the
-// initial matrix), passes c+1..2c the forward steps -- the same steps,
-// pointers and scalars as two_loop() for one problem
+// pass t of the two-loop recursion of every problem with 0 or more than
+// kCmpMax pairs: t = 0 sets q = -g, passes 1..c are the backward steps
+// (newest pair first; the last applies the initial matrix), passes c+1..2c
+// the forward steps -- the same steps, pointers and scalars as two_loop()
+// for one problem
 __global__ void __launch_bounds__(kRT) k_seg_step(const SegLane *__restrict__ lanes, int nl, int t,
                                                   double *__restrict__ q_rows) {
     const int b = lane_of_block(lanes, nl, blockIdx.x, false);
     const SegLane &L = lanes[b];
     const int c = L.count;
-    if (!L.dir || t > 2 * c) return;
+    if (!L.dir || (c >= 1 && c <= kCmpMax) || t > 2 * c) return;
     const int k = blockIdx.x - L.blk3;
     if (k >= L.nb3) return;
     const int64_t len = 3 * (int64_t)L.n;
     double *q = q_rows + 3 * L.row;
-    double *alpha = L.scal, *coef = L.scal + 64;
-    unsigned *ticket = reinterpret_cast<unsigned *>(L.scal + 130);
+    double *alpha = L.scal + kScalAlpha, *coef = L.scal + kScalCoef;
+    unsigned *ticket = reinterpret_cast<unsigned *>(L.scal + kScalTicket);
     auto S = [&](int j) { return (const double *)(L.hist + (size_t)L.slots[j] * L.slot_stride); };
-    auto Y = [&](int j) { return S(j) + L.y_off; };
+    auto Y = [&](int j) { return (const double *)(L.yhist + (size_t)L.slots[j] * L.slot_stride); };
     auto R = [&](int j) { return (const double *)(L.rho + L.slots[j]); };
     // initial matrix: diag(h), or gamma I (plain LBFGS with pairs), or I
     const double *h0 = L.method == 1 ? nullptr : L.h;
@@ -427,7 +432,7 @@ __global__ void __launch_bounds__(kRT) k_seg_accept(const SegLane *__restrict__ 
     const int k = blockIdx.x - L.blk1;
     if (k >= L.nb1) return;
     double *S = L.hist + (size_t)L.spare * L.slot_stride;
-    double *Y = S + L.y_off;
+    double *Y = L.yhist + (size_t)L.spare * L.slot_stride;
     const double *zt = zt_rows + 3 * L.row, *gt = gt_rows + 3 * L.row, *ht = ht_rows + L.row;
     int64_t b0, b1;
     chunk_range(L.n, L.nb1, k, b0, b1);
@@ -458,7 +463,7 @@ __global__ void __launch_bounds__(kRT) k_seg_accept(const SegLane *__restrict__ 
     // and 1/(y.s) (gamma) when the curvature test passes
     block_sum_store<3>(v, L.partials + 4 * k);
     __shared__ bool last;
-    unsigned *ticket = reinterpret_cast<unsigned *>(L.scal + 131);
+    unsigned *ticket = reinterpret_cast<unsigned *>(L.scal + kScalAcceptTicket);
     if (threadIdx.x == 0) {
         __threadfence();
         last = atomicAdd(ticket, 1u) == (unsigned)L.nb1 - 1;
@@ -469,7 +474,7 @@ __global__ void __launch_bounds__(kRT) k_seg_accept(const SegLane *__restrict__ 
     double w[3] = {0.0, 0.0, 0.0};
     for (int c = threadIdx.x; c < L.nb1; c += kRT)
 #pragma unroll
-        for (int q = 0; q < 3; ++q) w[q] += ((volatile double *)L.partials)[4 * c + q];
+        for (int q = 0; q < 3; ++q) w[q] += __ldcg(L.partials + 4 * c + q);
     double res[3];
     block_sum_store<3>(w, res);
     if (threadIdx.x == 0) {
@@ -482,6 +487,261 @@ __global__ void __launch_bounds__(kRT) k_seg_accept(const SegLane *__restrict__ 
         }
         *ticket = 0u;
     }
+}
+
+// ---- gathered direction passes (1 .. kCmpMax pairs) ----
+// The two-loop recursion with each loop's vector updates gathered into one
+// pass.  Backward loop: q_c = -g, alpha_j = rho_j s_j.q_{j+1}, q_j = q_{j+1}
+// - alpha_j y_j; as q_{j+1} = -g - sum_{i>j} alpha_i y_i,
+//     s_j.q_{j+1} = -s_j.g - sum_{i>j} alpha_i (s_j.y_i).
+// Forward loop: r_0 = H0 q_0, beta_j = rho_j y_j.r_j, r_{j+1} = r_j +
+// coef_j s_j with coef_j = alpha_j - beta_j; as r_j = r_0 + sum_{i<j} coef_i
+// s_i,
+//     y_j.r_j = y_j.r_0 + sum_{i<j} coef_i (s_i.y_j).
+// The products s_a.y_b (a older than b) stay in the problem's scalars by
+// history slot.  The newest pair's products with the older pairs come from
+// the s_a.g of two successive directions: y = g' - g, so s_a.y = s_a.g' -
+// s_a.g, with g the gradient its direction used and g' the next one.  That
+// saves count - 1 FP64 multiply-adds per component, and on this GPU the
+// FP64 pipe, not HBM, bounds the direction: one FP64 multiply-add per
+// component and step of the recursion (4 count + 2 in all) against
+// 8 bytes moved per component and step.
+//   A: s_j.g for every pair; the last block forms the newest pair's
+//      products (if it is new), keeps s_j.g, and runs the backward
+//      recursion, newest first;
+//   B: q_0 = -g - sum alpha_j y_j (newest first), r_0 = H0 q_0 into q;
+//      y_j.r_0 and g.r_0; the last block runs the forward recursion, oldest
+//      first, and leaves g.q = g.r_0 + sum coef_j s_j.g;
+//   C: q = r_0 + sum coef_j s_j (oldest first).
+// Per component, q is formed by the fused multiply-adds of the step-by-step
+// passes in their order; the dot products are summed differently, so the two
+// agree to rounding.  Each block takes one chunk of the 3n components (the
+// partition of every reduction here) with kCT threads and at most 72
+// registers a thread, so that the 1024 chunks of the largest problems are
+// resident at once on 152 SMs (7 blocks each).
+constexpr int kCT = 128;
+
+__device__ __forceinline__ const double *lane_S(const SegLane &L, int j) {
+    return L.hist + (size_t)L.slots[j] * L.slot_stride;
+}
+__device__ __forceinline__ const double *lane_Y(const SegLane &L, int j) {
+    return L.yhist + (size_t)L.slots[j] * L.slot_stride;
+}
+
+// The block's sums of v go to partials[q nb + k]; the last block to finish
+// (ticket counter) returns true, its thread 0 holding in res the sums over
+// all chunks in chunk order, and resets the counter.
+template <int NQ>
+__device__ __forceinline__ bool cmp_sums(const double (&v)[NQ], double *__restrict__ partials, unsigned *ticket,
+                                         int nb, int k, double (&res)[NQ]) {
+    __shared__ double sh[NQ][kCT / 32];
+    __shared__ bool last;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        double x = v[q];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) sh[q][w] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < NQ) {
+        double t = 0.0;
+#pragma unroll
+        for (int j = 0; j < kCT / 32; ++j) t += sh[threadIdx.x][j];
+        partials[(size_t)threadIdx.x * nb + k] = t;
+        __threadfence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == (unsigned)nb - 1;
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    double a[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) a[q] = 0.0;
+    for (int b = threadIdx.x; b < nb; b += kCT)
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) a[q] += __ldcg(partials + (size_t)q * nb + b);
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        double x = a[q];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) sh[q][w] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            double t = 0.0;
+#pragma unroll
+            for (int j = 0; j < kCT / 32; ++j) t += sh[q][j];
+            res[q] = t;
+        }
+        *ticket = 0u;
+    }
+    return true;
+}
+
+// DIRECT: the newest pair's products as dot products s_j.y_newest (for a
+// history given from outside, without the previous directions' s_j.g)
+template <bool DIRECT>
+__device__ __forceinline__ void cmp_pass_a(const SegLane &L, int k) {
+    const int c = L.count;
+    int64_t b0, b1;
+    chunk_range(3 * (int64_t)L.n, L.nb3, k, b0, b1);
+    const unsigned long long pol = policy_evict_first();
+    const double *S[kCmpMax];
+#pragma unroll
+    for (int j = 0; j < kCmpMax; ++j) S[j] = lane_S(L, j < c ? j : 0);
+    const double *yn = lane_Y(L, c - 1);
+    constexpr int NQ = DIRECT ? 2 * kCmpMax - 1 : kCmpMax;
+    double v[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) v[q] = 0.0;
+    for (int64_t i = b0 + threadIdx.x; i < b1; i += kCT) {
+        const double gi = ld_stream(L.g + i, pol);
+        const double yi = DIRECT ? ld_stream(yn + i, pol) : 0.0;
+#pragma unroll
+        for (int j = 0; j < kCmpMax; ++j)
+            if (j < c) {
+                const double sj = ld_stream(S[j] + i, pol);
+                v[j] = fma(sj, gi, v[j]);
+                if (DIRECT && j + 1 < kCmpMax && j + 1 < c) v[kCmpMax + j] = fma(sj, yi, v[kCmpMax + j]);
+            }
+    }
+    double res[NQ];
+    if (!cmp_sums<NQ>(v, L.partials, reinterpret_cast<unsigned *>(L.scal + kScalTicket), L.nb3, k, res)) return;
+    if (threadIdx.x != 0) return;
+    double *alpha = L.scal + kScalAlpha, *u = L.scal + kScalU, *G = L.rho + kLaneGram, *sg = L.rho + kLaneSg;
+    const int sn = L.slots[c - 1];
+    if (DIRECT)
+        for (int j = 0; j + 1 < c; ++j) G[L.slots[j] * kGramDim + sn] = res[kCmpMax + j];
+    else if (L.new_pair)
+        for (int j = 0; j + 1 < c; ++j) G[L.slots[j] * kGramDim + sn] = res[j] - sg[L.slots[j]];
+    for (int j = 0; j < c; ++j) {
+        u[j] = res[j];
+        sg[L.slots[j]] = res[j];
+    }
+    for (int j = c - 1; j >= 0; --j) {
+        const int sj = L.slots[j];
+        double d = -res[j];
+        for (int i = c - 1; i > j; --i) d = fma(-alpha[i], G[sj * kGramDim + L.slots[i]], d);
+        alpha[j] = L.rho[sj] * d;
+    }
+}
+
+__device__ __forceinline__ void cmp_pass_b(const SegLane &L, int k, double *__restrict__ q) {
+    const int c = L.count;
+    int64_t b0, b1;
+    chunk_range(3 * (int64_t)L.n, L.nb3, k, b0, b1);
+    const unsigned long long pol = policy_evict_first();
+    const double *alpha = L.scal + kScalAlpha;
+    const double *Y[kCmpMax];
+    double na[kCmpMax];
+#pragma unroll
+    for (int j = 0; j < kCmpMax; ++j) {
+        Y[j] = lane_Y(L, j < c ? j : 0);
+        na[j] = j < c ? -alpha[j] : 0.0;
+    }
+    // initial matrix: diag(h), or gamma I (plain LBFGS)
+    const double *h = L.method == 1 ? nullptr : L.h;
+    const double gam = L.method == 1 ? L.rho[kLaneMaxM + 1] : 1.0;
+    constexpr int NQ = kCmpMax + 1;
+    double v[NQ];
+#pragma unroll
+    for (int j = 0; j < NQ; ++j) v[j] = 0.0;
+    for (int64_t i = b0 + threadIdx.x; i < b1; i += kCT) {
+        const double gi = ld_stream(L.g + i, pol);
+        double yv[kCmpMax];
+#pragma unroll
+        for (int j = 0; j < kCmpMax; ++j) yv[j] = j < c ? ld_stream(Y[j] + i, pol) : 0.0;
+        const double hv = h ? h[i / 3] : gam;
+        double t = -gi;
+#pragma unroll
+        for (int j = kCmpMax - 1; j >= 0; --j)
+            if (j < c) t = fma(na[j], yv[j], t);
+        t *= hv;
+        q[i] = t;
+#pragma unroll
+        for (int j = 0; j < kCmpMax; ++j)
+            if (j < c) v[j] = fma(yv[j], t, v[j]);
+        v[kCmpMax] = fma(gi, t, v[kCmpMax]);
+    }
+    double res[NQ];
+    if (!cmp_sums<NQ>(v, L.partials, reinterpret_cast<unsigned *>(L.scal + kScalTicket), L.nb3, k, res)) return;
+    if (threadIdx.x != 0) return;
+    double *coef = L.scal + kScalCoef;
+    const double *u = L.scal + kScalU, *G = L.rho + kLaneGram;
+    for (int j = 0; j < c; ++j) {
+        const int sj = L.slots[j];
+        double d = res[j];
+        for (int i = 0; i < j; ++i) d = fma(coef[i], G[L.slots[i] * kGramDim + sj], d);
+        coef[j] = fma(-L.rho[sj], d, alpha[j]);
+    }
+    double gd = res[kCmpMax];
+    for (int j = 0; j < c; ++j) gd = fma(coef[j], u[j], gd);
+    L.st->dots[3] = gd;
+}
+
+__device__ __forceinline__ void cmp_pass_c(const SegLane &L, int k, double *__restrict__ q) {
+    const int c = L.count;
+    int64_t b0, b1;
+    chunk_range(3 * (int64_t)L.n, L.nb3, k, b0, b1);
+    const unsigned long long pol = policy_evict_first();
+    const double *coef = L.scal + kScalCoef;
+    const double *S[kCmpMax];
+    double cf[kCmpMax];
+#pragma unroll
+    for (int j = 0; j < kCmpMax; ++j) {
+        S[j] = lane_S(L, j < c ? j : 0);
+        cf[j] = j < c ? coef[j] : 0.0;
+    }
+    for (int64_t i = b0 + threadIdx.x; i < b1; i += kCT) {
+        double sv[kCmpMax];
+#pragma unroll
+        for (int j = 0; j < kCmpMax; ++j) sv[j] = j < c ? ld_stream(S[j] + i, pol) : 0.0;
+        double t = q[i];
+#pragma unroll
+        for (int j = 0; j < kCmpMax; ++j)
+            if (j < c) t = fma(cf[j], sv[j], t);
+        q[i] = t;
+    }
+}
+
+// the lane and chunk of this block: the one lane (chunk = block), or the
+// block's problem in the segmented grid; null if the block has no work here
+template <bool SEG>
+__device__ __forceinline__ const SegLane *cmp_lane(const SegLane *__restrict__ lanes, int nl, const SegLane &one,
+                                                   int &k) {
+    if (!SEG) {
+        k = blockIdx.x;
+        return &one;
+    }
+    const SegLane &L = lanes[lane_of_block(lanes, nl, blockIdx.x, false)];
+    k = blockIdx.x - L.blk3;
+    if (!L.dir || L.count < 1 || L.count > kCmpMax || k >= L.nb3) return nullptr;
+    return &L;
+}
+
+template <bool SEG, bool DIRECT>
+__global__ void __launch_bounds__(kCT, 7) k_cmp_a(const SegLane *__restrict__ lanes, int nl,
+                                                  const __grid_constant__ SegLane one) {
+    int k;
+    if (const SegLane *L = cmp_lane<SEG>(lanes, nl, one, k)) cmp_pass_a<DIRECT>(*L, k);
+}
+
+template <bool SEG>
+__global__ void __launch_bounds__(kCT, 7) k_cmp_b(const SegLane *__restrict__ lanes, int nl,
+                                               const __grid_constant__ SegLane one, double *__restrict__ q_rows) {
+    int k;
+    if (const SegLane *L = cmp_lane<SEG>(lanes, nl, one, k)) cmp_pass_b(*L, k, q_rows + 3 * L->row);
+}
+
+template <bool SEG>
+__global__ void __launch_bounds__(kCT, 7) k_cmp_c(const SegLane *__restrict__ lanes, int nl,
+                                               const __grid_constant__ SegLane one, double *__restrict__ q_rows) {
+    int k;
+    if (const SegLane *L = cmp_lane<SEG>(lanes, nl, one, k)) cmp_pass_c(*L, k, q_rows + 3 * L->row);
 }
 
 __global__ void k_differs(int64_t len, const double *__restrict__ a, const double *__restrict__ b, unsigned *flag) {
@@ -559,10 +819,50 @@ void set_gamma(double *gamma_dev, const DevStatus *st, cudaStream_t s, int64_t *
     (*launches)++;
 }
 
-void seg_direction(const SegLane *lanes, int nl, int max_count, int nblk3, double *q_rows, cudaStream_t s,
-                   int64_t *launches) {
-    for (int t = 0; t <= 2 * max_count; ++t) {
+void seg_direction(const SegLane *lanes, int nl, bool any_gathered, int max_step_count, int nblk3, double *q_rows,
+                   cudaStream_t s, int64_t *launches) {
+    if (any_gathered) {
+        SegLane none;
+        memset(&none, 0, sizeof(none));
+        k_cmp_a<true, false><<<nblk3, kCT, 0, s>>>(lanes, nl, none);
+        k_cmp_b<true><<<nblk3, kCT, 0, s>>>(lanes, nl, none, q_rows);
+        k_cmp_c<true><<<nblk3, kCT, 0, s>>>(lanes, nl, none, q_rows);
+        (*launches) += 3;
+    }
+    for (int t = 0; t <= 2 * max_step_count; ++t) {
         k_seg_step<<<nblk3, kRT, 0, s>>>(lanes, nl, t, q_rows);
+        (*launches)++;
+    }
+}
+
+void lane_direction(const SegLane &L, double *q, cudaStream_t s, int64_t *launches) {
+    const int c = L.count;
+    if (c >= 1 && c <= kCmpMax) {
+        cudaMemsetAsync(L.scal + kScalTicket, 0, sizeof(unsigned), s);
+        k_cmp_a<false, false><<<L.nb3, kCT, 0, s>>>(nullptr, 1, L);
+        k_cmp_b<false><<<L.nb3, kCT, 0, s>>>(nullptr, 1, L, q);
+        k_cmp_c<false><<<L.nb3, kCT, 0, s>>>(nullptr, 1, L, q);
+        (*launches) += 3;
+        return;
+    }
+    const double *S[kLaneMaxM], *Y[kLaneMaxM], *R[kLaneMaxM];
+    for (int k = 0; k < c; ++k) {
+        S[k] = L.hist + (size_t)L.slots[k] * L.slot_stride;
+        Y[k] = L.yhist + (size_t)L.slots[k] * L.slot_stride;
+        R[k] = L.rho + L.slots[k];
+    }
+    two_loop(L.n, L.g, L.method == 1 ? nullptr : L.h, (L.method == 1 && c > 0) ? L.rho + kLaneMaxM + 1 : nullptr, c,
+             S, Y, R, q, L.partials, L.scal, L.st, s, launches);
+}
+
+void lane_pair_products(const SegLane &L, cudaStream_t s, int64_t *launches) {
+    // pass A over the first k pairs forms pair k-1's products with the older
+    // ones as dot products (its scalars alpha are left unused)
+    cudaMemsetAsync(L.scal + kScalTicket, 0, sizeof(unsigned), s);
+    for (int k = 2; k <= L.count; ++k) {
+        SegLane P = L;
+        P.count = k;
+        k_cmp_a<false, true><<<P.nb3, kCT, 0, s>>>(nullptr, 1, P);
         (*launches)++;
     }
 }
@@ -590,8 +890,8 @@ void two_loop(int n, const double *g, const double *h, const double *hs, int cou
     // 2 count + 1 passes run back to back without a host round trip
     const int64_t len = 3 * (int64_t)n;
     const int nb = reduce_blocks(len);
-    double *alpha = scal, *coef = scal + 64;
-    unsigned *ticket = reinterpret_cast<unsigned *>(scal + 130);
+    double *alpha = scal + kScalAlpha, *coef = scal + kScalCoef;
+    unsigned *ticket = reinterpret_cast<unsigned *>(scal + kScalTicket);
     cudaMemsetAsync(ticket, 0, sizeof(unsigned), s);
     if (count == 0) {
         k_step<<<nb, kRT, 0, s>>>(len, q, nullptr, 0.0, g, h, hs, g, partials, ticket, nullptr, nullptr,

@@ -36,7 +36,7 @@ void seg_layout(EvalSet &E, const std::vector<Lane *> &lanes, int m) {
         blk1 += d.nb1;
         d.scal = E.seg_scal + (size_t)b * kTwoLoopScratch;
         d.partials = E.seg_partials + pb;
-        pb += (size_t)std::max(d.nb3, 4 * d.nb1);
+        pb += (size_t)std::max(kCmpQ * d.nb3, 4 * d.nb1);
         d.st = E.d_ist + b;
     }
     E.nblk3 = blk3;
@@ -47,8 +47,8 @@ void seg_layout(EvalSet &E, const std::vector<Lane *> &lanes, int m) {
         d.g = L->g;
         d.h = L->h;
         d.hist = L->hist;
+        d.yhist = L->hist + L->y_off;
         d.slot_stride = (int64_t)L->slot_stride;
-        d.y_off = (int64_t)L->y_off;
         d.rho = L->rho;
         d.method = L->opt.method;
     }
@@ -61,17 +61,21 @@ cudaError_t seg_upload(EvalSet &E) {
 // the direction of every lane in dir (its history as the ring holds it; none for Lloyd)
 cudaError_t seg_directions(EvalSet &E, const std::vector<Lane *> &dir, int64_t *launches) {
     for (int b = 0; b < E.B; ++b) E.h_seg[b].dir = 0;
-    int maxc = 0;
-    for (const Lane *L : dir) {
+    bool gathered = false;
+    int max_step = -1;
+    for (Lane *L : dir) {
         SegLane &d = E.h_seg[L->b];
         d.dir = 1;
         d.count = (L->opt.method == 2) ? 0 : L->count;
         for (int k = 0; k < d.count; ++k) d.slots[k] = L->slots[k];
-        maxc = std::max(maxc, d.count);
+        d.new_pair = L->new_pair ? 1 : 0;
+        L->new_pair = false;
+        if (d.count >= 1 && d.count <= kCmpMax) gathered = true;
+        else max_step = std::max(max_step, d.count);
     }
     cudaError_t e = seg_upload(E);
     if (e != cudaSuccess) return e;
-    seg_direction(E.d_seg, E.B, maxc, E.nblk3, E.q, E.stream, launches);
+    seg_direction(E.d_seg, E.B, gathered, max_step, E.nblk3, E.q, E.stream, launches);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     return sync_statuses(E);
 }
@@ -80,6 +84,7 @@ cudaError_t seg_directions(EvalSet &E, const std::vector<Lane *> &dir, int64_t *
 
 void lane_reset_history(Lane &L, int m) {
     L.count = 0;
+    L.new_pair = false;
     for (int k = 0; k <= m; ++k) L.slots[k] = k;
     L.spare = m;
 }
@@ -295,6 +300,7 @@ cudaError_t lockstep_round(EvalSet &E, std::vector<Lane *> &lanes, int m, scvt_s
                     if (!used[k]) { L->spare = k; break; }
             }
             L->slots[L->count++] = slot;
+            L->new_pair = true;
         } else if (L->opt.method != 2) {
             L->rep.skipped++;
         }

@@ -33,6 +33,7 @@ struct Lane {
     // solver state
     int slots[kLaneMaxM + 1];
     int count = 0, spare = 0;
+    bool new_pair = false;                  // a pair was stored after the last direction
     double F = 0.0, gnorm = 0.0, Fprev = 0.0;
     bool done = false, need_init = false, state_valid = false;
     scvt_solve_report rep;

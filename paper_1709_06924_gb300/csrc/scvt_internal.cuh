@@ -286,20 +286,34 @@ void trial_point(int n, const double *z, const double *q, double alpha, double *
 void lloyd_project(int n, const double *c, double *zout, cudaStream_t s, int64_t *launches);
 void accept_pair(int n, const double *zt, const double *z, const double *gt, const double *g, double *S, double *Y,
                  double *partials, DevStatus *st, cudaStream_t s, int64_t *launches);
-// q = -H g by the two-loop recursion; pairs are given oldest first as host
-// arrays of device pointers, rho[k] -> 1/(y_k.s_k) on the device; count <= 64;
-// scal: device scratch of kTwoLoopScratch doubles (the scalars alpha_k and
-// the coefficients, and a ticket counter).  Leaves g.q in st->dots[3].
-constexpr int kTwoLoopScratch = 136;
-// H0 = diag(h) per generator, or (h null) hs[0] I, or (both null) I.
+// Scratch of one direction (kTwoLoopScratch doubles): the scalars alpha_k,
+// the coefficients alpha_k - beta_k, the products s_k.g, and the ticket
+// counters of the passes whose last block finishes a reduction.
+constexpr int kScalAlpha = 0, kScalCoef = 64, kScalU = 128, kScalTicket = 192, kScalAcceptTicket = 193;
+constexpr int kTwoLoopScratch = 200;
+// q = -H g by the two-loop recursion one step per pass; pairs are given
+// oldest first as host arrays of device pointers, rho[k] -> 1/(y_k.s_k) on
+// the device; count <= 64.  Leaves g.q in st->dots[3]; partials: 1024
+// doubles.  H0 = diag(h) per generator, or (h null) hs[0] I, or (both null) I.
 void two_loop(int n, const double *g, const double *h, const double *hs, int count, const double *const *S,
               const double *const *Y, const double *const *rho, double *q, double *partials, double *scal,
               DevStatus *st, cudaStream_t s, int64_t *launches);
 // ---- segmented LBFGS kernels over the problems of a batch (lbfgs.cu) ----
-// A problem's LBFGS memory holds up to kLaneMaxM pairs; its scalars are
-// kLaneRho doubles: 1/(y.s) per history slot, then gamma (plain LBFGS).
+// A problem's LBFGS memory holds up to kLaneMaxM pairs in kLaneMaxM + 1
+// history slots.  Its kLaneRho scalars: 1/(y.s) per slot, then gamma (plain
+// LBFGS), then s_k.g per slot as the last gathered direction formed it, then
+// the products s_a.y_b of the stored pairs by slot (rho[kLaneGram + a
+// kGramDim + b], a older than b).
 constexpr int kLaneMaxM = 32;
-constexpr int kLaneRho = kLaneMaxM + 2;
+constexpr int kGramDim = kLaneMaxM + 1;
+constexpr int kLaneSg = kLaneMaxM + 2;
+constexpr int kLaneGram = kLaneSg + kGramDim;
+constexpr int kLaneRho = kLaneGram + kGramDim * kGramDim;
+// Directions with 1 .. kCmpMax pairs take the three gathered passes; the
+// others one pass per step of the recursion.  Chunk sums of the gathered
+// passes: kCmpQ per chunk.
+constexpr int kCmpMax = 8;
+constexpr int kCmpQ = 16;
 // One problem of a batch as the segmented kernels see it.  Each problem
 // keeps the chunking of a single problem of its size (nb3 chunks of its 3n
 // direction components, nb1 chunks of its n generators), so its results
@@ -313,21 +327,31 @@ struct SegLane {
     int dir, trial, accept;       // takes part in the direction, the line-search round, the accept
     int nb3, blk3, nb1, blk1;     // chunks, and the problem's first block in the segmented grids
     int spare;                    // history slot that receives the accepted pair
+    int new_pair;                 // the newest pair was stored after the last direction
     int slots[kLaneMaxM];         // history slots of the direction's pairs, oldest first
     double alpha;                 // trial step of the line-search round
     double *z, *g, *h;            // resident iterate, gradient, preconditioner
-    double *hist;                 // S of slot k at hist + k slot_stride, Y at S + y_off
-    int64_t slot_stride, y_off;
+    double *hist, *yhist;         // S of slot k at hist + k slot_stride, Y at yhist + k slot_stride
+    int64_t slot_stride;
     double *rho;                  // kLaneRho scalars
     double *scal;                 // kTwoLoopScratch
-    double *partials;             // max(nb3, 4 nb1) chunk sums
+    double *partials;             // max(kCmpQ nb3, 4 nb1) chunk sums
     DevStatus *st;                // the problem's status block
 };
-// q of every problem taking part (rows of q_rows): 2 max_count + 1 passes,
-// each one launch over nblk3 = sum nb3 blocks; g.q in each problem's
+// q = -H g for one problem described by a lane (row 0 of q): the gathered
+// passes for 1 .. kCmpMax pairs, else two_loop(); g.q in st->dots[3]
+void lane_direction(const SegLane &L, double *q, cudaStream_t s, int64_t *launches);
+// the products s_a.y_b (a < b) of pairs 0 .. count-1 of a lane whose history
+// holds no products yet, as dot products (a solver's are formed by its
+// directions); count <= kCmpMax
+void lane_pair_products(const SegLane &L, cudaStream_t s, int64_t *launches);
+// q of every problem taking part (rows of q_rows): the gathered passes for
+// the problems with 1 .. kCmpMax pairs (three launches if any), then
+// 2 max_step_count + 1 step passes for the others (none if max_step_count <
+// 0); each launch over nblk3 = sum nb3 blocks; g.q in each problem's
 // st->dots[3]
-void seg_direction(const SegLane *lanes, int nl, int max_count, int nblk3, double *q_rows, cudaStream_t s,
-                   int64_t *launches);
+void seg_direction(const SegLane *lanes, int nl, bool any_gathered, int max_step_count, int nblk3, double *q_rows,
+                   cudaStream_t s, int64_t *launches);
 // zt = normalize(z + alpha q) for the rows of the problems of the round
 // (pinst: problem of each row)
 void seg_trial(const SegLane *lanes, const int *pinst, int64_t ntot, const double *q_rows, double *zt_rows,

@@ -103,9 +103,15 @@ def test_two_loop_roofline():
     import bench
     from paper_1709_06924_gb300 import inputs as I
     w = I.WORKLOADS["tanh-2621442"]
-    r = bench.two_loop_roofline(w, 3, 5, 4.0)
-    assert r["bound"] == "hbm" and r["pairs_per_iteration"] == [3, 4, 5, 6, 7]
+    r = bench.two_loop_roofline(w, 3, 5, 4.0, 152, 2070.0)
+    assert r["bound"] == "fp64" and r["pairs_per_iteration"] == [3, 4, 5, 6, 7]
     assert r["ms_total"] == 4.0
-    assert r["algorithmic_bytes"] == sum((4 * c + 2) * 24 for c in (3, 4, 5, 6, 7)) * w.n
+    # 4c + 2 FP64 operations per component, all multiply-adds but the initial matrix's multiply
+    assert bench.two_loop_ops_per_component(7) == 30
+    assert r["algorithmic_flops"] == sum(3 * (8 * c + 3) for c in (3, 4, 5, 6, 7)) * w.n
     assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-12
-    assert bench.two_loop_roofline(w, 3, 0, 4.0) is None
+    assert abs(r["peak"] - 1.25856) < 1e-9
+    h = r["hbm"]
+    assert h["algorithmic_bytes"] == sum((4 * c + 2) * 24 for c in (3, 4, 5, 6, 7)) * w.n
+    assert abs(h["frac"] - h["achieved"] / h["peak"]) < 1e-12
+    assert bench.two_loop_roofline(w, 3, 0, 4.0, 152, 2070.0) is None

@@ -131,7 +131,9 @@ def test_lloyd_step_matches_oracle():
     assert np.array_equal(zl, zl_host)
 
 
-@pytest.mark.parametrize("count", [0, 1, 3, 7])
+# 1 .. 8 pairs take the gathered passes (the products s_a.y_b formed first
+# for the external history), 0 and 9+ the step-by-step passes
+@pytest.mark.parametrize("count", [0, 1, 2, 3, 7, 8, 9, 12])
 def test_two_loop_matches_oracle(count):
     n = 3001
     rng = np.random.default_rng(100 + count)
@@ -174,6 +176,23 @@ def test_solver_lockstep_with_oracle(iters):
     assert rep["fevals"] == rep_o["fevals"]
     assert abs(rep["energy"] - rep_o["energy"]) <= 1e-12 * rep_o["energy"]
     assert np.abs(zt.cpu().numpy() - zo).max() <= 1e-11
+
+
+def test_solver_lockstep_with_oracle_through_a_full_memory():
+    # m = 7 over 12 iterations: the history ring fills, drops its oldest pair
+    # and reuses slots, so the products s_a.y_b kept by slot are reused across
+    # directions
+    z = I.uniform_sphere(2562, 29)
+    dens = DENS["x3"]
+    zo, rep_o, tr = oracle.lbfgs_solve(z, dens, lbfgs_m=7, max_iter=12, grad_tol=0.0)
+    with Engine(len(z), dens, lbfgs_m=7) as e:
+        zt = dev(z)
+        rep = e.lbfgs_solve(zt, max_iter=12, grad_tol=0.0)
+    assert rep["iters"] == rep_o["iters"] == 12
+    assert rep["fevals"] == rep_o["fevals"]
+    assert rep["skipped"] == rep_o["skipped"] and rep["resets"] == rep_o["resets"]
+    assert abs(rep["energy"] - rep_o["energy"]) <= 1e-12 * rep_o["energy"]
+    assert np.abs(zt.cpu().numpy() - zo).max() <= 1e-10
 
 
 def test_solver_reaches_tolerance_uniform_2562():
