@@ -582,19 +582,21 @@ __device__ __forceinline__ bool cmp_sums(const double (&v)[NQ], double *__restri
     return true;
 }
 
+// The pair count C is a compile-time constant of each pass (the kernels
+// switch on the lane's count): FP64 instructions of absent pairs, even
+// predicated off, would hold the FP64 pipe.
 // DIRECT: the newest pair's products as dot products s_j.y_newest (for a
 // history given from outside, without the previous directions' s_j.g)
-template <bool DIRECT>
+template <bool DIRECT, int C>
 __device__ __forceinline__ void cmp_pass_a(const SegLane &L, int k) {
-    const int c = L.count;
     int64_t b0, b1;
     chunk_range(3 * (int64_t)L.n, L.nb3, k, b0, b1);
     const unsigned long long pol = policy_evict_first();
-    const double *S[kCmpMax];
+    const double *S[C];
 #pragma unroll
-    for (int j = 0; j < kCmpMax; ++j) S[j] = lane_S(L, j < c ? j : 0);
-    const double *yn = lane_Y(L, c - 1);
-    constexpr int NQ = DIRECT ? 2 * kCmpMax - 1 : kCmpMax;
+    for (int j = 0; j < C; ++j) S[j] = lane_S(L, j);
+    const double *yn = lane_Y(L, C - 1);
+    constexpr int NQ = DIRECT ? 2 * C - 1 : C;
     double v[NQ];
 #pragma unroll
     for (int q = 0; q < NQ; ++q) v[q] = 0.0;
@@ -602,108 +604,105 @@ __device__ __forceinline__ void cmp_pass_a(const SegLane &L, int k) {
         const double gi = ld_stream(L.g + i, pol);
         const double yi = DIRECT ? ld_stream(yn + i, pol) : 0.0;
 #pragma unroll
-        for (int j = 0; j < kCmpMax; ++j)
-            if (j < c) {
-                const double sj = ld_stream(S[j] + i, pol);
-                v[j] = fma(sj, gi, v[j]);
-                if (DIRECT && j + 1 < kCmpMax && j + 1 < c) v[kCmpMax + j] = fma(sj, yi, v[kCmpMax + j]);
-            }
+        for (int j = 0; j < C; ++j) {
+            const double sj = ld_stream(S[j] + i, pol);
+            v[j] = fma(sj, gi, v[j]);
+            if constexpr (DIRECT)
+                if (j + 1 < C) v[C + j] = fma(sj, yi, v[C + j]);
+        }
     }
     double res[NQ];
     if (!cmp_sums<NQ>(v, L.partials, reinterpret_cast<unsigned *>(L.scal + kScalTicket), L.nb3, k, res)) return;
     if (threadIdx.x != 0) return;
     double *alpha = L.scal + kScalAlpha, *u = L.scal + kScalU, *G = L.rho + kLaneGram, *sg = L.rho + kLaneSg;
-    const int sn = L.slots[c - 1];
+    const int sn = L.slots[C - 1];
     if (DIRECT)
-        for (int j = 0; j + 1 < c; ++j) G[L.slots[j] * kGramDim + sn] = res[kCmpMax + j];
+        for (int j = 0; j + 1 < C; ++j) G[L.slots[j] * kGramDim + sn] = res[C + j];
     else if (L.new_pair)
-        for (int j = 0; j + 1 < c; ++j) G[L.slots[j] * kGramDim + sn] = res[j] - sg[L.slots[j]];
-    for (int j = 0; j < c; ++j) {
+        for (int j = 0; j + 1 < C; ++j) G[L.slots[j] * kGramDim + sn] = res[j] - sg[L.slots[j]];
+    for (int j = 0; j < C; ++j) {
         u[j] = res[j];
         sg[L.slots[j]] = res[j];
     }
-    for (int j = c - 1; j >= 0; --j) {
+    for (int j = C - 1; j >= 0; --j) {
         const int sj = L.slots[j];
         double d = -res[j];
-        for (int i = c - 1; i > j; --i) d = fma(-alpha[i], G[sj * kGramDim + L.slots[i]], d);
+        for (int i = C - 1; i > j; --i) d = fma(-alpha[i], G[sj * kGramDim + L.slots[i]], d);
         alpha[j] = L.rho[sj] * d;
     }
 }
 
+template <int C>
 __device__ __forceinline__ void cmp_pass_b(const SegLane &L, int k, double *__restrict__ q) {
-    const int c = L.count;
     int64_t b0, b1;
     chunk_range(3 * (int64_t)L.n, L.nb3, k, b0, b1);
     const unsigned long long pol = policy_evict_first();
     const double *alpha = L.scal + kScalAlpha;
-    const double *Y[kCmpMax];
-    double na[kCmpMax];
+    const double *Y[C];
+    double na[C];
 #pragma unroll
-    for (int j = 0; j < kCmpMax; ++j) {
-        Y[j] = lane_Y(L, j < c ? j : 0);
-        na[j] = j < c ? -alpha[j] : 0.0;
+    for (int j = 0; j < C; ++j) {
+        Y[j] = lane_Y(L, j);
+        na[j] = -alpha[j];
     }
     // initial matrix: diag(h), or gamma I (plain LBFGS)
     const double *h = L.method == 1 ? nullptr : L.h;
     const double gam = L.method == 1 ? L.rho[kLaneMaxM + 1] : 1.0;
-    constexpr int NQ = kCmpMax + 1;
+    constexpr int NQ = C + 1;
     double v[NQ];
 #pragma unroll
     for (int j = 0; j < NQ; ++j) v[j] = 0.0;
     for (int64_t i = b0 + threadIdx.x; i < b1; i += kCT) {
         const double gi = ld_stream(L.g + i, pol);
-        double yv[kCmpMax];
+        double yv[C];
 #pragma unroll
-        for (int j = 0; j < kCmpMax; ++j) yv[j] = j < c ? ld_stream(Y[j] + i, pol) : 0.0;
+        for (int j = 0; j < C; ++j) yv[j] = ld_stream(Y[j] + i, pol);
         const double hv = h ? h[i / 3] : gam;
         double t = -gi;
 #pragma unroll
-        for (int j = kCmpMax - 1; j >= 0; --j)
-            if (j < c) t = fma(na[j], yv[j], t);
+        for (int j = C - 1; j >= 0; --j) t = fma(na[j], yv[j], t);
         t *= hv;
         q[i] = t;
 #pragma unroll
-        for (int j = 0; j < kCmpMax; ++j)
-            if (j < c) v[j] = fma(yv[j], t, v[j]);
-        v[kCmpMax] = fma(gi, t, v[kCmpMax]);
+        for (int j = 0; j < C; ++j) v[j] = fma(yv[j], t, v[j]);
+        v[C] = fma(gi, t, v[C]);
     }
     double res[NQ];
     if (!cmp_sums<NQ>(v, L.partials, reinterpret_cast<unsigned *>(L.scal + kScalTicket), L.nb3, k, res)) return;
     if (threadIdx.x != 0) return;
     double *coef = L.scal + kScalCoef;
     const double *u = L.scal + kScalU, *G = L.rho + kLaneGram;
-    for (int j = 0; j < c; ++j) {
+    for (int j = 0; j < C; ++j) {
         const int sj = L.slots[j];
         double d = res[j];
         for (int i = 0; i < j; ++i) d = fma(coef[i], G[L.slots[i] * kGramDim + sj], d);
         coef[j] = fma(-L.rho[sj], d, alpha[j]);
     }
-    double gd = res[kCmpMax];
-    for (int j = 0; j < c; ++j) gd = fma(coef[j], u[j], gd);
+    double gd = res[C];
+    for (int j = 0; j < C; ++j) gd = fma(coef[j], u[j], gd);
     L.st->dots[3] = gd;
 }
 
+template <int C>
 __device__ __forceinline__ void cmp_pass_c(const SegLane &L, int k, double *__restrict__ q) {
-    const int c = L.count;
     int64_t b0, b1;
     chunk_range(3 * (int64_t)L.n, L.nb3, k, b0, b1);
     const unsigned long long pol = policy_evict_first();
     const double *coef = L.scal + kScalCoef;
-    const double *S[kCmpMax];
-    double cf[kCmpMax];
+    const double *S[C];
+    double cf[C];
 #pragma unroll
-    for (int j = 0; j < kCmpMax; ++j) {
-        S[j] = lane_S(L, j < c ? j : 0);
-        cf[j] = j < c ? coef[j] : 0.0;
+    for (int j = 0; j < C; ++j) {
+        S[j] = lane_S(L, j);
+        cf[j] = coef[j];
     }
     for (int64_t i = b0 + threadIdx.x; i < b1; i += kCT) {
-        double sv[kCmpMax];
+        double sv[C];
 #pragma unroll
-        for (int j = 0; j < kCmpMax; ++j) sv[j] = j < c ? ld_stream(S[j] + i, pol) : 0.0;
+        for (int j = 0; j < C; ++j) sv[j] = ld_stream(S[j] + i, pol);
         double t = q[i];
 #pragma unroll
-        for (int j = 0; j < kCmpMax; ++j)
-            if (j < c) t = fma(cf[j], sv[j], t);
+        for (int j = 0; j < C; ++j) t = fma(cf[j], sv[j], t);
         q[i] = t;
     }
 }
@@ -723,26 +722,55 @@ __device__ __forceinline__ const SegLane *cmp_lane(const SegLane *__restrict__ l
     return &L;
 }
 
+// the pass for the lane's pair count (1 .. kCmpMax, uniform over a block)
+#define SCVT_CMP_COUNTS(F) \
+    switch (L->count) {    \
+        case 1: F(1); break; \
+        case 2: F(2); break; \
+        case 3: F(3); break; \
+        case 4: F(4); break; \
+        case 5: F(5); break; \
+        case 6: F(6); break; \
+        case 7: F(7); break; \
+        case 8: F(8); break; \
+    }
+static_assert(kCmpMax == 8, "SCVT_CMP_COUNTS lists the counts 1 .. kCmpMax");
+
 template <bool SEG, bool DIRECT>
 __global__ void __launch_bounds__(kCT, 7) k_cmp_a(const SegLane *__restrict__ lanes, int nl,
                                                   const __grid_constant__ SegLane one) {
     int k;
-    if (const SegLane *L = cmp_lane<SEG>(lanes, nl, one, k)) cmp_pass_a<DIRECT>(*L, k);
+    const SegLane *L = cmp_lane<SEG>(lanes, nl, one, k);
+    if (!L) return;
+#define SCVT_A(C) cmp_pass_a<DIRECT, C>(*L, k)
+    SCVT_CMP_COUNTS(SCVT_A)
+#undef SCVT_A
 }
 
 template <bool SEG>
 __global__ void __launch_bounds__(kCT, 7) k_cmp_b(const SegLane *__restrict__ lanes, int nl,
-                                               const __grid_constant__ SegLane one, double *__restrict__ q_rows) {
+                                                  const __grid_constant__ SegLane one, double *__restrict__ q_rows) {
     int k;
-    if (const SegLane *L = cmp_lane<SEG>(lanes, nl, one, k)) cmp_pass_b(*L, k, q_rows + 3 * L->row);
+    const SegLane *L = cmp_lane<SEG>(lanes, nl, one, k);
+    if (!L) return;
+    double *q = q_rows + 3 * L->row;
+#define SCVT_B(C) cmp_pass_b<C>(*L, k, q)
+    SCVT_CMP_COUNTS(SCVT_B)
+#undef SCVT_B
 }
 
 template <bool SEG>
 __global__ void __launch_bounds__(kCT, 7) k_cmp_c(const SegLane *__restrict__ lanes, int nl,
-                                               const __grid_constant__ SegLane one, double *__restrict__ q_rows) {
+                                                  const __grid_constant__ SegLane one, double *__restrict__ q_rows) {
     int k;
-    if (const SegLane *L = cmp_lane<SEG>(lanes, nl, one, k)) cmp_pass_c(*L, k, q_rows + 3 * L->row);
+    const SegLane *L = cmp_lane<SEG>(lanes, nl, one, k);
+    if (!L) return;
+    double *q = q_rows + 3 * L->row;
+#define SCVT_C(C) cmp_pass_c<C>(*L, k, q)
+    SCVT_CMP_COUNTS(SCVT_C)
+#undef SCVT_C
 }
+#undef SCVT_CMP_COUNTS
 
 __global__ void k_differs(int64_t len, const double *__restrict__ a, const double *__restrict__ b, unsigned *flag) {
     int any = 0;
