@@ -33,7 +33,7 @@ struct Bufs {
     double *fc = nullptr;                    // per-cell energy (scratch)
     double *q = nullptr;                     // direction
     double *yv = nullptr;                    // y of the newest candidate pair (scratch)
-    double *nrm = nullptr;                   // |z + alpha q|
+    double *nrm = nullptr;                   // 1 / |z + alpha q|
     double *mass = nullptr, *moment = nullptr;
     double *stage_a = nullptr, *stage_b = nullptr;  // host-pointer staging (3n each)
     double *partials = nullptr;              // kCmpQ * 1024 chunk sums

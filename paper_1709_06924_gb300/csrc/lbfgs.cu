@@ -67,7 +67,7 @@ __global__ void k_reduce_eval(int n, const double *__restrict__ fcell, const dou
         double gx = g[3 * i], gy = g[3 * i + 1], gz = g[3 * i + 2];
         v[0] += fcell[i];
         v[1] += gx * gx + gy * gy + gz * gz;
-        if (q) v[2] += (gx * q[3 * i] + gy * q[3 * i + 1] + gz * q[3 * i + 2]) / nrm[i];
+        if (q) v[2] += (gx * q[3 * i] + gy * q[3 * i + 1] + gz * q[3 * i + 2]) * nrm[i];
     }
     block_sum_store<3>(v, partials + 4 * blockIdx.x);
 }
@@ -118,10 +118,12 @@ __global__ void k_trial(int n, const double *__restrict__ z, const double *__res
     double x = z[3 * (size_t)i] + alpha * q[3 * (size_t)i];
     double y = z[3 * (size_t)i + 1] + alpha * q[3 * (size_t)i + 1];
     double w = z[3 * (size_t)i + 2] + alpha * q[3 * (size_t)i + 2];
-    double r = sqrt(x * x + y * y + w * w);
-    zt[3 * (size_t)i] = x / r;
-    zt[3 * (size_t)i + 1] = y / r;
-    zt[3 * (size_t)i + 2] = w / r;
+    // one reciprocal square root (FP64 divisions and square roots are
+    // sequences on the FP64 pipe, which bounds these vector kernels)
+    double r = rsqrt(x * x + y * y + w * w);
+    zt[3 * (size_t)i] = x * r;
+    zt[3 * (size_t)i + 1] = y * r;
+    zt[3 * (size_t)i + 2] = w * r;
     nrm[i] = r;
 }
 
@@ -133,6 +135,13 @@ __global__ void k_lloyd(int n, const double *__restrict__ c, double *__restrict_
     zout[3 * (size_t)i] = x / r;
     zout[3 * (size_t)i + 1] = y / r;
     zout[3 * (size_t)i + 2] = w / r;
+}
+
+// *out = max(*out, sqrt of the warp's largest v) for v >= 0: one atomic per
+// warp (nonnegative doubles order like their bit patterns)
+__device__ __forceinline__ void warp_max_to(double v, unsigned long long *out) {
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0 && v > 0.0) atomicMax(out, (unsigned long long)__double_as_longlong(sqrt(v)));
 }
 
 // s = zt - z, y = gt - g; partial sums of y.s, y.y, s.s; max |s_i|
@@ -153,13 +162,12 @@ __global__ void k_accept(int n, const double *__restrict__ zt, const double *__r
             Y[3 * i + d] = y;
             v[0] += y * s;
             v[1] += y * y;
-            v[2] += s * s;
             s2 += s * s;
         }
+        v[2] += s2;
         mv = fmax(mv, s2);
     }
-    // nonnegative doubles order like their bit patterns
-    if (mv > 0.0) atomicMax(maxmove, (unsigned long long)__double_as_longlong(sqrt(mv)));
+    warp_max_to(mv, maxmove);
     block_sum_store<3>(v, partials + 4 * blockIdx.x);
 }
 
@@ -183,7 +191,7 @@ __global__ void k_reduce_eval_batch(const InstGeom *__restrict__ inst, const int
         double gx = g[3 * i], gy = g[3 * i + 1], gz = g[3 * i + 2];
         v[0] += fcell[i];
         v[1] += gx * gx + gy * gy + gz * gz;
-        if (q) v[2] += (gx * q[3 * i] + gy * q[3 * i + 1] + gz * q[3 * i + 2]) / nrm[i];
+        if (q) v[2] += (gx * q[3 * i] + gy * q[3 * i + 1] + gz * q[3 * i + 2]) * nrm[i];
     }
     block_sum_store<3>(v, partials + 4 * ((int64_t)pbase[b] + blockIdx.x));
 }
@@ -415,10 +423,10 @@ __global__ void k_seg_trial(const SegLane *__restrict__ lanes, const int *__rest
     double x = L.z[3 * i] + a * q_rows[3 * r];
     double y = L.z[3 * i + 1] + a * q_rows[3 * r + 1];
     double w = L.z[3 * i + 2] + a * q_rows[3 * r + 2];
-    double nr = sqrt(x * x + y * y + w * w);
-    zt_rows[3 * r] = x / nr;
-    zt_rows[3 * r + 1] = y / nr;
-    zt_rows[3 * r + 2] = w / nr;
+    double nr = rsqrt(x * x + y * y + w * w);
+    zt_rows[3 * r] = x * nr;
+    zt_rows[3 * r + 1] = y * nr;
+    zt_rows[3 * r + 2] = w * nr;
     nrm_rows[r] = nr;
 }
 
@@ -450,15 +458,15 @@ __global__ void __launch_bounds__(kRT) k_seg_accept(const SegLane *__restrict__ 
             Y[3 * i + d] = y;
             v[0] += y * s;
             v[1] += y * y;
-            v[2] += s * s;
             s2 += s * s;
             L.z[3 * i + d] = zn;
             L.g[3 * i + d] = gn;
         }
+        v[2] += s2;
         L.h[i] = ht[i];
         mv = fmax(mv, s2);
     }
-    if (mv > 0.0) atomicMax(&L.st->maxmove_bits, (unsigned long long)__double_as_longlong(sqrt(mv)));
+    warp_max_to(mv, &L.st->maxmove_bits);
     // chunk sums, then the last block: the dots in the order of k_finish<3>,
     // and 1/(y.s) (gamma) when the curvature test passes
     block_sum_store<3>(v, L.partials + 4 * k);

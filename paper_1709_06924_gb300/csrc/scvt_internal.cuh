@@ -267,7 +267,7 @@ cudaError_t mesh_quality(int n, const double *z, const int *deg, const int *nbr,
 
 // ---- reductions and vector kernels (lbfgs.cu) ----
 int reduce_blocks(int64_t n);
-// red[0] = sum fcell, red[1] = sum |g|^2, red[2] = sum g_i.q_i / nrm_i (if q)
+// red[0] = sum fcell, red[1] = sum |g|^2, red[2] = sum g_i.q_i nrm_i (if q), nrm_i = 1 / |z_i + alpha q_i|
 void reduce_eval(int n, const double *fcell, const double *grad, const double *q, const double *nrm,
                  double *partials, DevStatus *st, cudaStream_t s, int64_t *launches);
 // the same per problem of a batch: problem b sums its own range with the
@@ -281,6 +281,7 @@ void reduce_eval_batch(int nprob, int max_nb, const InstGeom *inst, const int *p
 // out[slot] = sum x.y (deterministic), optionally scaled: out[slot] = scale[si] * sum
 void dot_to(int64_t len, const double *x, const double *y, double *partials, double *out, cudaStream_t s,
             int64_t *launches);
+// zt = (z + alpha q) / |z + alpha q| per generator, nrm = 1 / |z + alpha q|
 void trial_point(int n, const double *z, const double *q, double alpha, double *zt, double *nrm, cudaStream_t s,
                  int64_t *launches);
 void lloyd_project(int n, const double *c, double *zout, cudaStream_t s, int64_t *launches);
