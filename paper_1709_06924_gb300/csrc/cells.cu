@@ -1588,6 +1588,20 @@ __device__ __forceinline__ void corner_line64(const Grid &g, int p, V3 zi, V3 e1
 // offset v - z_i in FP64, exact to rounding relative to the cell's size
 // (an absolute unit vector would carry 1e-16 of absolute error, up to 1e-12
 // of the smallest cells' energies).
+// Corner slots: FP64 offsets v - z_i (P4) in the plain FP64 form; in the
+// FP64 form the same 32 bytes hold the offset as double-float pairs (hi.x,
+// hi.y, hi.z, lo.x | lo.y, lo.z), the form the quadrature computes in.
+__device__ __forceinline__ void store_corner_df(P4 *slot, df3 o) {
+    float4 *f = reinterpret_cast<float4 *>(slot);
+    f[0] = make_float4(o.x.hi, o.y.hi, o.z.hi, o.x.lo);
+    f[1] = make_float4(o.y.lo, o.z.lo, 0.0f, 0.0f);
+}
+__device__ __forceinline__ df3 load_corner_df(const P4 *slot) {
+    const float4 *f = reinterpret_cast<const float4 *>(slot);
+    const float4 a = f[0], b = f[1];
+    return df3{df{a.x, a.w}, df{a.y, b.x}, df{a.z, b.y}};
+}
+
 template <bool PLAIN>
 __global__ void __launch_bounds__(256) k_corners(Grid g, CellBuf cb, Span sp) {
     const int ne = *sp.etot, eb = *sp.e0;
@@ -1638,7 +1652,7 @@ __global__ void __launch_bounds__(256) k_corners(Grid g, CellBuf cb, Span sp) {
                     const df ox = df_add(dx.x, df_mul(m, df_add(Z.x, dx.x)));
                     const df oy = df_add(dx.y, df_mul(m, df_add(Z.y, dx.y)));
                     const df oz = df_add(dx.z, df_mul(m, df_add(Z.z, dx.z)));
-                    cb.vx[(size_t)p * kCellSlots + k] = P4{df_to(ox), df_to(oy), df_to(oz), 0.0};
+                    store_corner_df(cb.vx + (size_t)p * kCellSlots + k, df3{ox, oy, oz});
                     continue;
                 }
             }
@@ -1652,7 +1666,8 @@ __global__ void __launch_bounds__(256) k_corners(Grid g, CellBuf cb, Span sp) {
         const double u = (c1 * b2 - c2 * b1) * inv;
         const double w = (a1 * c2 - a2 * c1) * inv;
         const V3 o = project_offset(zi, dot(zi, zi) - 1.0, add(scl(e1, u), scl(e2, w)));
-        cb.vx[(size_t)p * kCellSlots + k] = P4{o.x, o.y, o.z, 0.0};
+        if constexpr (PLAIN) cb.vx[(size_t)p * kCellSlots + k] = P4{o.x, o.y, o.z, 0.0};
+        else store_corner_df(cb.vx + (size_t)p * kCellSlots + k, df3_from(o.x, o.y, o.z));
     }
 }
 
@@ -1976,8 +1991,17 @@ __global__ void __launch_bounds__(512) k_quad(Grid g, CellBuf cb, int ecap, Span
         const int deg = cb.deg[p];
         const V3 zi = ld(g.zs + p);
         const P4 *vx = cb.vx + (size_t)p * kCellSlots;
-        const V3 va = ld(vx + k);  // corner offsets from z_i
-        const V3 vb = ld(vx + ((k + 1 == deg) ? 0 : k + 1));
+        const int kb = (k + 1 == deg) ? 0 : k + 1;
+        // corner offsets from z_i: FP64, or double-float pairs in the FP64 form
+        df3 da, db;
+        V3 va, vb;
+        if constexpr (PLAIN) {
+            va = ld(vx + k);
+            vb = ld(vx + kb);
+        } else {
+            da = load_corner_df(vx + k);
+            db = load_corner_df(vx + kb);
+        }
         const int b = view_of(g, p).b;
         const Density rho = g.rho ? g.rho[b] : g.rho0;
         const int q = cb.nb[(size_t)p * kCellSlots + k];
@@ -1993,8 +2017,14 @@ __global__ void __launch_bounds__(512) k_quad(Grid g, CellBuf cb, int ecap, Span
         if (rho.kind >= 2) {
             const DensTab T = g.tabs ? g.tabs[b] : g.tab0;
             if (T.M > 0) {
-                const float3 fa = make_float3((float)va.x, (float)va.y, (float)va.z);
-                const float3 fb = make_float3((float)vb.x, (float)vb.y, (float)vb.z);
+                float3 fa, fb;
+                if constexpr (PLAIN) {
+                    fa = make_float3((float)va.x, (float)va.y, (float)va.z);
+                    fb = make_float3((float)vb.x, (float)vb.y, (float)vb.z);
+                } else {
+                    fa = make_float3(da.x.hi, da.y.hi, da.z.hi);
+                    fb = make_float3(db.x.hi, db.y.hi, db.z.hi);
+                }
                 const float3 fh = dfdiff(g, q, g.zf[p], g.zl[p]);
                 const float r2 = fmaxf(fmaxf(fa.x * fa.x + fa.y * fa.y + fa.z * fa.z, fb.x * fb.x + fb.y * fb.y + fb.z * fb.z),
                                        0.25f * (fh.x * fh.x + fh.y * fh.y + fh.z * fh.z));
@@ -2016,10 +2046,11 @@ __global__ void __launch_bounds__(512) k_quad(Grid g, CellBuf cb, int ecap, Span
         }
         // double-float path: offsets of the edge's points from z_i below chord
         // 0.03 (then delta <= 1e-3 at every rule point) and a density without
-        // direct evaluation; otherwise FP64.  The corner offsets (FP64, exact
-        // to rounding relative to their size) are rounded to pairs.
+        // direct evaluation; otherwise FP64.  The FP64 form's edge sums are
+        // stored as double-float pairs (m, o = sum w rho (p - z_i), F), the
+        // plain form's in FP64 (m, c, F).
+        float2 *ef = reinterpret_cast<float2 *>(cb.eacc);
         if constexpr (!PLAIN) {
-            const df3 da = df3_from(va.x, va.y, va.z), db = df3_from(vb.x, vb.y, vb.z);
             const float4 hp = g.zf[p], lp = g.zl[p], llp = g.zll[p];
             const df3 dj = gen_diff(g, q, hp, lp, llp);
             const float r2 = fmaxf(fmaxf(da.x.hi * da.x.hi + da.y.hi * da.y.hi + da.z.hi * da.z.hi,
@@ -2050,14 +2081,15 @@ __global__ void __launch_bounds__(512) k_quad(Grid g, CellBuf cb, int ecap, Span
                     tri_df(rho.kind, dd.g1, dd.gam, A, aA1, da, dm, dd.ev, eA, u0, tcdf, vs, K, ad);
                     tri_df(rho.kind, dd.g1, dd.gam, A, aA1, dm, db, dd.ev, eA, u0, tcdf, vs, K, ad);
                 }
-                const double m = df_to(ad.m);
-                ea[e] = m;
-                ea[(size_t)ecap + e] = fma(zi.x, m, df_to(ad.qx));
-                ea[2 * (size_t)ecap + e] = fma(zi.y, m, df_to(ad.qy));
-                ea[3 * (size_t)ecap + e] = fma(zi.z, m, df_to(ad.qz));
-                ea[4 * (size_t)ecap + e] = df_to(ad.e);
+                ef[e] = make_float2(ad.m.hi, ad.m.lo);
+                ef[(size_t)ecap + e] = make_float2(ad.qx.hi, ad.qx.lo);
+                ef[2 * (size_t)ecap + e] = make_float2(ad.qy.hi, ad.qy.lo);
+                ef[3 * (size_t)ecap + e] = make_float2(ad.qz.hi, ad.qz.lo);
+                ef[4 * (size_t)ecap + e] = make_float2(ad.e.hi, ad.e.lo);
                 continue;
             }
+            va = V3{df_to(da.x), df_to(da.y), df_to(da.z)};
+            vb = V3{df_to(db.x), df_to(db.y), df_to(db.z)};
         }
         // FP64: every point relative to z_i (corner and midpoint offsets)
         const double inv_alpha = rho.inv_alpha;
@@ -2069,6 +2101,16 @@ __global__ void __launch_bounds__(512) k_quad(Grid g, CellBuf cb, int ecap, Span
             const V3 om = midpoint_offset(zi, aA1, ld(g.zs + q));
             tri(rho, inv_alpha, zi, aA1, va, om, acc, tcf, K, cj);
             tri(rho, inv_alpha, zi, aA1, om, vb, acc, tcf, K, cj);
+        }
+        if constexpr (!PLAIN) {
+            const df em = df_from(acc.m), ex = df_from(acc.cx), ey = df_from(acc.cy), ez = df_from(acc.cz),
+                     ee = df_from(acc.e);
+            ef[e] = make_float2(em.hi, em.lo);
+            ef[(size_t)ecap + e] = make_float2(ex.hi, ex.lo);
+            ef[2 * (size_t)ecap + e] = make_float2(ey.hi, ey.lo);
+            ef[3 * (size_t)ecap + e] = make_float2(ez.hi, ez.lo);
+            ef[4 * (size_t)ecap + e] = make_float2(ee.hi, ee.lo);
+            continue;
         }
         moment_from_offsets(zi, acc);
         ea[e] = acc.m;
@@ -2268,9 +2310,13 @@ __global__ void __launch_bounds__(512) k_quad32(Grid g, CellBuf cb, int ecap, Sp
     }
 }
 
-// thread per cell: the cell's edge sums added in edge order (FP64), then the
-// cell's outputs (g_i, h_i, m_i, c_i, F_i at the original index)
-template <bool MIXED>
+// thread per cell: the cell's edge sums added in edge order, then the cell's
+// outputs (g_i, h_i, m_i, c_i, F_i at the original index).  KIND 0: the FP64
+// form's double-float pairs (m, o, F), added as pairs; 1: the mixed form's
+// FP32 sums (m, o, F), added in FP64; 2: the plain form's FP64 sums (m, c, F).
+// With o = sum w rho (p - z_i) the gradient -2 (o - (o.z_i) z_i) never
+// subtracts m_i z_i from itself.
+template <int KIND>
 __global__ void __launch_bounds__(256) k_cell_sum(Grid g, CellOut out, CellBuf cb, int ecap, DevStatus *st, Span sp) {
     const int p = sp.p0 + blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= sp.p1) return;
@@ -2279,7 +2325,19 @@ __global__ void __launch_bounds__(256) k_cell_sum(Grid g, CellOut out, CellBuf c
     const int e0 = cb.eoff[p];
     if (e0 + deg > ecap) return;  // past the edge list (FLAG_ECAP is set)
     Acc acc = {0, 0, 0, 0, 0};
-    if (MIXED) {
+    if (KIND == 0) {
+        const float2 *ef = reinterpret_cast<const float2 *>(cb.eacc);
+        df s[5] = {};
+        for (int k = 0; k < deg; ++k) {
+            const int e = e0 + k;
+#pragma unroll
+            for (int c = 0; c < 5; ++c) {
+                const float2 v = ef[(size_t)c * ecap + e];
+                s[c] = df_add(s[c], df{v.x, v.y});
+            }
+        }
+        acc = Acc{df_to(s[0]), df_to(s[1]), df_to(s[2]), df_to(s[3]), df_to(s[4])};
+    } else if (KIND == 1) {
         const float *ea = (const float *)cb.eacc;
         for (int k = 0; k < deg; ++k) {
             const int e = e0 + k;
@@ -2302,8 +2360,8 @@ __global__ void __launch_bounds__(256) k_cell_sum(Grid g, CellOut out, CellBuf c
     }
     const V3 zi = ld(g.zs + p);
     unsigned *flags = flags_of(g, st, view_of(g, p).b);
-    if (MIXED) write_cell_offsets(out, g.sidx[p], zi, acc, flags);
-    else write_cell(out, g.sidx[p], zi, acc, flags);
+    if (KIND == 2) write_cell(out, g.sidx[p], zi, acc, flags);
+    else write_cell_offsets(out, g.sidx[p], zi, acc, flags);
 }
 
 }  // namespace
@@ -2506,7 +2564,7 @@ void cell_passes(const Grid &g, const CellOut &out, const CellBuf &cb, int *list
             if (timed && ev0) cudaEventRecord(ev0, sc);
             k_quad32<<<eblocks, qb, 0, sc>>>(g, cb, ecap, sp);
             if (timed && ev1) cudaEventRecord(ev1, sc);
-            k_cell_sum<true><<<cblocks, 256, 0, sc>>>(g, out, cb, ecap, st, sp);
+            k_cell_sum<1><<<cblocks, 256, 0, sc>>>(g, out, cb, ecap, st, sp);
         } else {
             const bool plain = precision == 2;
             if (plain) k_corners<true><<<e256, 256, 0, sc>>>(g, cb, sp);
@@ -2515,7 +2573,8 @@ void cell_passes(const Grid &g, const CellOut &out, const CellBuf &cb, int *list
             if (plain) k_quad<true><<<eblocks, qb, 0, sc>>>(g, cb, ecap, sp, st);
             else k_quad<false><<<eblocks, qb, 0, sc>>>(g, cb, ecap, sp, st);
             if (timed && ev1) cudaEventRecord(ev1, sc);
-            k_cell_sum<false><<<cblocks, 256, 0, sc>>>(g, out, cb, ecap, st, sp);
+            if (plain) k_cell_sum<2><<<cblocks, 256, 0, sc>>>(g, out, cb, ecap, st, sp);
+            else k_cell_sum<0><<<cblocks, 256, 0, sc>>>(g, out, cb, ecap, st, sp);
         }
         (*launches) += 10;
         (*cell_launches) += 5;
