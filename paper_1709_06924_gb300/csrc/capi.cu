@@ -46,7 +46,7 @@ struct Bufs {
     int *cdeg = nullptr, *cnb = nullptr, *eoff = nullptr, *ecell = nullptr, *escan = nullptr;
     double *eacc = nullptr;
     void *tab = nullptr;                     // density table (FP64 forms, tanh-cap densities)
-    float4 *vo = nullptr;
+    float4 *vo = nullptr, *ctab = nullptr;
     int *bin_of = nullptr, *count = nullptr, *start = nullptr, *cursor = nullptr, *scan_tmp = nullptr;
     int *sidx = nullptr, *list1 = nullptr, *list2 = nullptr;
     int *deg = nullptr;
@@ -198,6 +198,7 @@ scvt_status evaluate_dev(scvt_handle *H, const double *zdev, double *grad, doubl
     cb.scan_tmp = B.escan;
     cb.eacc = B.eacc;
     cb.vo = B.vo;
+    cb.ctab = B.ctab;
     cell_passes(g, out, cb, B.list1, B.list2, B.st, H->cfg.precision, H->tune, s,
                 H->profiling ? H->ev_cell0 : nullptr, H->profiling ? H->ev_cell1 : nullptr, L,
                 &H->stats.cell_launches, &H->pipes, H->profiling ? H->ev_topo : nullptr);
@@ -361,7 +362,7 @@ void scvt_destroy(scvt_handle *H) {
     if (!H) return;
     Bufs &b = H->b;
     void *ptrs[] = {b.z, b.zt, b.g, b.gt, b.h, b.ht, b.fc, b.q, b.yv, b.nrm, b.mass, b.moment, b.stage_a, b.stage_b,
-                    b.partials, b.scal, b.rho, b.hist, b.zs, b.zf, b.zl, b.zll, b.cvx, b.cnb, b.cdeg, b.eoff, b.ecell, b.escan, b.eacc, b.vo, b.tab, b.bin_of, b.count, b.start, b.cursor, b.scan_tmp,
+                    b.partials, b.scal, b.rho, b.hist, b.zs, b.zf, b.zl, b.zll, b.cvx, b.cnb, b.cdeg, b.eoff, b.ecell, b.escan, b.eacc, b.vo, b.ctab, b.tab, b.bin_of, b.count, b.start, b.cursor, b.scan_tmp,
                     b.sidx, b.list1, b.list2, b.deg, b.radius, b.st};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -419,6 +420,7 @@ scvt_status scvt_create(const scvt_config *cfg, void *cuda_stream, scvt_handle *
     AL(b.cdeg, n); AL(b.eoff, n + 1); AL(b.ecell, 6 * (size_t)n); AL(b.escan, scan_tmp_ints(n));
     AL(b.eacc, 5 * 6 * (size_t)n);
     if (cfg->precision == 1) AL(b.vo, (size_t)n * kCellSlots);
+    if (cfg->precision == 0) AL(b.ctab, n);
     const Density dens = to_device_density(cfg->rho);
     const int tabM = (cfg->precision != 1 && dens.kind >= 2) ? dens_table_centres(n) : 0;
     if (tabM > 0 && e == cudaSuccess) {

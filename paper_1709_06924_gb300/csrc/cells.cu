@@ -1602,6 +1602,8 @@ __device__ __forceinline__ df3 load_corner_df(const P4 *slot) {
     return df3{df{a.x, a.w}, df{a.y, b.x}, df{a.z, b.y}};
 }
 
+__device__ __forceinline__ float4 cell_table_record(const DensTab &T, const Density &rho, V3 zi);
+
 template <bool PLAIN>
 __global__ void __launch_bounds__(256) k_corners(Grid g, CellBuf cb, Span sp) {
     const int ne = *sp.etot, eb = *sp.e0;
@@ -1613,6 +1615,16 @@ __global__ void __launch_bounds__(256) k_corners(Grid g, CellBuf cb, Span sp) {
         const int *nb = cb.nb + (size_t)p * kCellSlots;
         const int ga = nb[(k == 0) ? deg - 1 : k - 1], gb = nb[k];
         const V3 zi = ld(g.zs + p);
+        if constexpr (!PLAIN) {
+            // the cell's density-table record (tanh caps), from its first edge
+            if (k == 0 && cb.ctab) {
+                const int b = view_of(g, p).b;
+                const Density rho = g.rho ? g.rho[b] : g.rho0;
+                const DensTab T = g.tabs ? g.tabs[b] : g.tab0;
+                cb.ctab[p] = (rho.kind >= 2 && T.M > 0) ? cell_table_record(T, rho, zi)
+                                                         : make_float4(__int_as_float(-1), 1.0f, 0.0f, 0.0f);
+            }
+        }
         if constexpr (!PLAIN) {
             const float4 hp = g.zf[p], lp = g.zl[p], llp = g.zll[p];
             float3 e1, e2;
@@ -1789,7 +1801,7 @@ __global__ void k_dens_table(Density r, int M, double dth, TabCentre *meta, doub
     // scaling; keeps the coefficients in FP32 range), and |cf_k| r_j^k
     int ex = 0;
     if (rj > 0.0) frexp(rj, &ex);
-    meta[j] = TabCentre{ci, ldexp(1.0, -ex), rj, (double)Kj};
+    meta[j] = TabCentre{ci, rj, (float)ldexp(1.0, -ex), (float)rj, (float)Kj, 0.0f};
     double rk = 1.0;
     for (int k = 0; k < kTabK; ++k) {
         cfo[(size_t)j * kTabK + k] = cf[k];
@@ -1806,17 +1818,16 @@ __global__ void k_dens_table(Density r, int M, double dth, TabCentre *meta, doub
 // points, |x_c.(p - z_i)| <= (1 + r2) max |x_c.o| + r2 |ci| for offsets of
 // squared length <= r2 <= 1/2, are covered by the bound's terms).  Returns 0
 // when the range exceeds the centre's validated radius (direct evaluation).
-__device__ __forceinline__ int table_terms(const DensTab &T, double ci, float xa, float xb, float xm, float r2,
-                                           int &j, double &cj) {
+// the centre nearest in angle to c = x_c.z_i
+__device__ __forceinline__ int table_centre(const DensTab &T, double ci) {
     const float th = (ci >= 0.0) ? 2.0f * asinf(sqrtf((float)(0.5 * (1.0 - ci))))
                                  : 3.14159265f - 2.0f * asinf(sqrtf((float)(0.5 * (1.0 + ci))));
-    j = min(T.M - 1, max(0, __float2int_rn(th / T.dth)));
-    const TabCentre mt = T.meta[j];
-    cj = mt.c;
-    if (!(mt.r > 0.0)) return 0;
-    const float U = (float)fabs(ci - cj) + (1.0f + r2) * fmaxf(fmaxf(fabsf(xa), fabsf(xb)), fabsf(xm)) +
-                    r2 * fabsf((float)ci) + 1e-6f * sqrtf(r2) + 1e-12f;
-    const float R = (float)mt.r;
+    return min(T.M - 1, max(0, __float2int_rn(th / T.dth)));
+}
+
+// the terms of centre j's series over |u| <= U (0: U beyond its radius)
+__device__ __forceinline__ int terms_within(const DensTab &T, int j, float U) {
+    const float R = T.meta[j].rf;
     if (!(U <= R)) return 0;
     // terms |cf_k| U^k = mag_k (U / r_j)^k, no overflow
     const float *mg = T.mag + (size_t)j * kTabK;
@@ -1829,6 +1840,29 @@ __device__ __forceinline__ int table_terms(const DensTab &T, double ci, float xa
         if (small == 2) return k - 1;
     }
     return 0;
+}
+
+__device__ __forceinline__ int table_terms(const DensTab &T, double ci, float xa, float xb, float xm, float r2,
+                                           int &j, double &cj) {
+    j = table_centre(T, ci);
+    const TabCentre mt = T.meta[j];
+    cj = mt.c;
+    if (!(mt.r > 0.0)) return 0;
+    const float U = (float)fabs(ci - cj) + (1.0f + r2) * fmaxf(fmaxf(fabsf(xa), fabsf(xb)), fabsf(xm)) +
+                    r2 * fabsf((float)ci) + 1e-6f * sqrtf(r2) + 1e-12f;
+    return terms_within(T, j, U);
+}
+
+// The FP64 form takes the centre per cell (k_corners): the record holds j,
+// the scale, and u0 = x_c.z_i - c_j as a pair; then per edge only the range
+// bound, with |x_c.z_i| <= 1 for its radial term.
+__device__ __forceinline__ float4 cell_table_record(const DensTab &T, const Density &rho, V3 zi) {
+    const double ci = rho.xc0 * zi.x + rho.xc1 * zi.y + rho.xc2 * zi.z;
+    const int j = table_centre(T, ci);
+    const TabCentre mt = T.meta[j];
+    if (!(mt.r > 0.0)) return make_float4(__int_as_float(-1), 1.0f, 0.0f, 0.0f);
+    const df u = df_from(ci - mt.c);
+    return make_float4(__int_as_float(j), mt.scale, u.hi, u.lo);
 }
 
 // -------------------------------------------------------------- quadrature
@@ -2011,7 +2045,8 @@ __global__ void __launch_bounds__(512) k_quad(Grid g, CellBuf cb, int ecap, Span
         // x_c.z_i in FP64 (it sets the series' argument)
         int K = 0, j = 0;
         double cj = 0.0, ci = 0.0;
-        const TabCentre *tmeta = nullptr;
+        df u0c{0.0f, 0.0f};  // FP64 form: x_c.z_i - c_j from the cell's record
+        float vsc = 1.0f;
         const double *tcf = nullptr;
         const float2 *tcdf = nullptr;
         if (rho.kind >= 2) {
@@ -2029,12 +2064,27 @@ __global__ void __launch_bounds__(512) k_quad(Grid g, CellBuf cb, int ecap, Span
                 const float r2 = fmaxf(fmaxf(fa.x * fa.x + fa.y * fa.y + fa.z * fa.z, fb.x * fb.x + fb.y * fb.y + fb.z * fb.z),
                                        0.25f * (fh.x * fh.x + fh.y * fh.y + fh.z * fh.z));
                 if (r2 <= 0.5f) {
-                    const float3 xf = make_float3((float)rho.xc0, (float)rho.xc1, (float)rho.xc2);
-                    ci = rho.xc0 * zi.x + rho.xc1 * zi.y + rho.xc2 * zi.z;
-                    K = table_terms(T, ci,
-                                    xf.x * fa.x + xf.y * fa.y + xf.z * fa.z, xf.x * fb.x + xf.y * fb.y + xf.z * fb.z,
-                                    0.5f * (xf.x * fh.x + xf.y * fh.y + xf.z * fh.z), r2, j, cj);
-                    tmeta = T.meta;
+                    const DensityF rf = g.rhof ? g.rhof[b] : g.rho0f;
+                    const float xa = rf.xc0 * fa.x + rf.xc1 * fa.y + rf.xc2 * fa.z;
+                    const float xb = rf.xc0 * fb.x + rf.xc1 * fb.y + rf.xc2 * fb.z;
+                    const float xm = 0.5f * (rf.xc0 * fh.x + rf.xc1 * fh.y + rf.xc2 * fh.z);
+                    if constexpr (PLAIN) {
+                        ci = rho.xc0 * zi.x + rho.xc1 * zi.y + rho.xc2 * zi.z;
+                        K = table_terms(T, ci, xa, xb, xm, r2, j, cj);
+                    } else {
+                        const float4 rec = cb.ctab[p];
+                        j = __float_as_int(rec.x);
+                        if (j >= 0) {
+                            const float U = fabsf(rec.z) + (1.0f + r2) * fmaxf(fmaxf(fabsf(xa), fabsf(xb)), fabsf(xm)) +
+                                            r2 + 1e-6f * sqrtf(r2) + 1e-12f;
+                            K = terms_within(T, j, U);
+                            cj = T.meta[j].c;
+                            vsc = rec.y;
+                            u0c = df{rec.z, rec.w};
+                        } else {
+                            j = 0;
+                        }
+                    }
                     tcf = T.cf + (size_t)j * kTabK;
                     tcdf = T.cdf + (size_t)j * kTabK;
                 }
@@ -2061,8 +2111,8 @@ __global__ void __launch_bounds__(512) k_quad(Grid g, CellBuf cb, int ecap, Span
                 const df aA1{llp.w, 0.0f};
                 const DensDF dd = g.rho ? dens_df(rho) : dd0;
                 const df eA = df3_dot(dd.ev, A);
-                const df u0 = (K > 0) ? df_from(ci - cj) : df{0.0f, 0.0f};
-                const float vs = (K > 0) ? (float)tmeta[j].scale : 1.0f;
+                const df u0 = (K > 0) ? u0c : df{0.0f, 0.0f};
+                const float vs = (K > 0) ? vsc : 1.0f;
                 // edge midpoint mu = (z_i + z_j) / |z_i + z_j|: with h = (z_j - z_i) / 2,
                 // mu - z_i = h + m (A + h), 1 - |A + h|^2 = -(|A|^2 - 1) - 2 A.h - |h|^2
                 const df3 hh{df{0.5f * dj.x.hi, 0.5f * dj.x.lo}, df{0.5f * dj.y.hi, 0.5f * dj.y.lo},

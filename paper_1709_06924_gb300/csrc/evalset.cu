@@ -104,6 +104,7 @@ void enqueue_eval(EvalSet &E, int64_t *launches, int64_t *cell_launches) {
     cb.scan_tmp = E.escan;
     cb.eacc = E.eacc;
     cb.vo = E.vo;
+    cb.ctab = E.ctab;
     cell_passes(g, out, cb, E.list1, E.list2, E.d_st, E.precision, E.tune, s, nullptr, nullptr, launches,
                 cell_launches, &E.pipes);
     reduce_eval_batch(E.B, E.max_nb, E.d_inst, E.d_pbase, E.d_active, E.fc, E.gt, E.q, E.nrm, E.partials, E.d_ist, s,
@@ -171,6 +172,7 @@ int64_t evalset_bytes(int64_t cap_n, int cap_b, int precision) {
                       + 32 + 48 + 16 * 32 + 16 * 4 + 4 + 4 + 24 + 240  // zs, zf+zl+zll, cvx, cnb, cdeg, eoff, ecell, eacc
                       + 4 * 4;                // bin_of, sidx, list1, list2
     if (precision == 1) per_row += 16 * 16;   // vo
+    if (precision == 0) per_row += 16;        // ctab
     const int64_t tabs = precision != 1 ? (int64_t)tab_pool_size(cap_n, cap_b) + (int64_t)cap_b * (int64_t)sizeof(DensTab) : 0;
     const int64_t seg = (int64_t)cap_b * (int64_t)(sizeof(SegLane) + 8 * kTwoLoopScratch) +
                         8 * (int64_t)max_seg_partials(cap_n, cap_b);
@@ -198,6 +200,7 @@ cudaError_t evalset_alloc(EvalSet &E, int64_t cap_n, int cap_b, int precision, c
     AL(E.cdeg, N); AL(E.eoff, N + 1); AL(E.ecell, 6 * N); AL(E.escan, scan_tmp_ints(N));
     AL(E.eacc, 5 * 6 * N);
     if (precision == 1) AL(E.vo, N * kCellSlots);
+    if (precision == 0) AL(E.ctab, N);
     if (precision != 1) {
         E.tab_pool_bytes = tab_pool_size(cap_n, cap_b);
         AL(E.d_tabs, cap_b);
@@ -225,7 +228,7 @@ void evalset_free(EvalSet &E) {
     E.graph = nullptr;
     void *ptrs[] = {E.d_inst, E.d_pinst, E.d_pbase, E.d_active, E.d_rho, E.d_rhof, E.d_ist, E.d_st, E.zt, E.gt,
                     E.ht, E.fc, E.q, E.nrm, E.radius, E.partials, E.zs, E.zf, E.zl, E.zll, E.cvx, E.cnb, E.cdeg, E.eoff,
-                    E.ecell, E.escan, E.eacc, E.vo, E.tab_pool, E.d_tabs, E.d_seg, E.seg_partials, E.seg_scal, E.bin_of, E.count, E.start, E.cursor, E.scan_tmp, E.sidx,
+                    E.ecell, E.escan, E.eacc, E.vo, E.ctab, E.tab_pool, E.d_tabs, E.d_seg, E.seg_partials, E.seg_scal, E.bin_of, E.count, E.start, E.cursor, E.scan_tmp, E.sidx,
                     E.list1, E.list2};
     for (void *p : ptrs)
         if (p) cudaFree(p);

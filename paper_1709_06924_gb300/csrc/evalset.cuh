@@ -52,7 +52,7 @@ struct EvalSet {
     size_t partials_len = 0;
     // workspace
     P4 *zs = nullptr, *cvx = nullptr;
-    float4 *zf = nullptr, *zl = nullptr, *zll = nullptr, *vo = nullptr;
+    float4 *zf = nullptr, *zl = nullptr, *zll = nullptr, *vo = nullptr, *ctab = nullptr;
     int *cdeg = nullptr, *cnb = nullptr, *eoff = nullptr, *ecell = nullptr, *escan = nullptr;
     double *eacc = nullptr;
     // density tables of the problems (FP64 forms): a pool carved per layout

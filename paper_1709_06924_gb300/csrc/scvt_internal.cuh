@@ -98,9 +98,11 @@ __device__ __forceinline__ double rho_value(const Density &r, double px, double 
 constexpr int kTabK = 24;
 struct alignas(32) TabCentre {
     double c;      // c_j = cos(theta_j)
-    double scale;  // 2^-e_j, the scale of the double-float coefficients (2^e_j >= r_j)
     double r;      // validated radius r_j (0: none)
-    double K;      // terms at r_j
+    float scale;   // 2^-e_j, the scale of the double-float coefficients (2^e_j >= r_j)
+    float rf;      // r_j in FP32
+    float K;       // terms at r_j
+    float pad;
 };
 struct DensTab {
     int M;              // centres; 0 = no table (direct evaluation)
@@ -183,6 +185,8 @@ struct CellBuf {
     int *scan_tmp;     // scratch of the scan over n (2 * (n / 2048 + 64) + 64 ints)
     double *eacc;      // 5 * 6n: per-edge sums (m, c or o, F), component-major; FP32 in the mixed form
     float4 *vo;        // n * kCellSlots corner offsets v - z_i in FP32 (mixed precision only)
+    float4 *ctab;      // n (FP64 form): the cell's density-table centre j (int bits, -1: none), its
+                       // scale 2^-e_j, and x_c.z_i - c_j as a double-float pair
 };
 
 // ---- binning (cells.cu) ----

@@ -178,6 +178,7 @@ extern "C" scvt_status scvt_energy_grad_static(int64_t n, const scvt_density *rh
     cb.scan_tmp = (int *)(base + oEscan);
     cb.eacc = (double *)(base + oEacc);
     cb.vo = nullptr;
+    cb.ctab = nullptr;  // the density is evaluated directly (no table)
     Pipes px;  // one pipeline on the caller's stream, its counters in the scratch array
     px.counts = (unsigned *)(base + oCounts);
     cell_passes(grid, out, cb, list1, list2, st, 0, Tune(), s, nullptr, nullptr, &launches, &cell_launches, &px);
