@@ -1602,8 +1602,6 @@ __device__ __forceinline__ df3 load_corner_df(const P4 *slot) {
     return df3{df{a.x, a.w}, df{a.y, b.x}, df{a.z, b.y}};
 }
 
-__device__ __forceinline__ float4 cell_table_record(const DensTab &T, const Density &rho, V3 zi);
-
 template <bool PLAIN>
 __global__ void __launch_bounds__(256) k_corners(Grid g, CellBuf cb, Span sp) {
     const int ne = *sp.etot, eb = *sp.e0;
@@ -1615,16 +1613,6 @@ __global__ void __launch_bounds__(256) k_corners(Grid g, CellBuf cb, Span sp) {
         const int *nb = cb.nb + (size_t)p * kCellSlots;
         const int ga = nb[(k == 0) ? deg - 1 : k - 1], gb = nb[k];
         const V3 zi = ld(g.zs + p);
-        if constexpr (!PLAIN) {
-            // the cell's density-table record (tanh caps), from its first edge
-            if (k == 0 && cb.ctab) {
-                const int b = view_of(g, p).b;
-                const Density rho = g.rho ? g.rho[b] : g.rho0;
-                const DensTab T = g.tabs ? g.tabs[b] : g.tab0;
-                cb.ctab[p] = (rho.kind >= 2 && T.M > 0) ? cell_table_record(T, rho, zi)
-                                                         : make_float4(__int_as_float(-1), 1.0f, 0.0f, 0.0f);
-            }
-        }
         if constexpr (!PLAIN) {
             const float4 hp = g.zf[p], lp = g.zl[p], llp = g.zll[p];
             float3 e1, e2;
@@ -1853,7 +1841,7 @@ __device__ __forceinline__ int table_terms(const DensTab &T, double ci, float xa
     return terms_within(T, j, U);
 }
 
-// The FP64 form takes the centre per cell (k_corners): the record holds j,
+// The FP64 form takes the centre per cell (k_cell_table): the record holds j,
 // the scale, and u0 = x_c.z_i - c_j as a pair; then per edge only the range
 // bound, with |x_c.z_i| <= 1 for its radial term.
 __device__ __forceinline__ float4 cell_table_record(const DensTab &T, const Density &rho, V3 zi) {
@@ -1863,6 +1851,17 @@ __device__ __forceinline__ float4 cell_table_record(const DensTab &T, const Dens
     if (!(mt.r > 0.0)) return make_float4(__int_as_float(-1), 1.0f, 0.0f, 0.0f);
     const df u = df_from(ci - mt.c);
     return make_float4(__int_as_float(j), mt.scale, u.hi, u.lo);
+}
+
+// thread per cell of cells [p0, p1): the cells' table records
+__global__ void __launch_bounds__(256) k_cell_table(Grid g, CellBuf cb, int p0, int p1) {
+    const int p = p0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= p1) return;
+    const int b = view_of(g, p).b;
+    const Density rho = g.rho ? g.rho[b] : g.rho0;
+    const DensTab T = g.tabs ? g.tabs[b] : g.tab0;
+    cb.ctab[p] = (rho.kind >= 2 && T.M > 0) ? cell_table_record(T, rho, ld(g.zs + p))
+                                             : make_float4(__int_as_float(-1), 1.0f, 0.0f, 0.0f);
 }
 
 // -------------------------------------------------------------- quadrature
@@ -2617,8 +2616,15 @@ void cell_passes(const Grid &g, const CellOut &out, const CellBuf &cb, int *list
             k_cell_sum<1><<<cblocks, 256, 0, sc>>>(g, out, cb, ecap, st, sp);
         } else {
             const bool plain = precision == 2;
-            if (plain) k_corners<true><<<e256, 256, 0, sc>>>(g, cb, sp);
-            else k_corners<false><<<e256, 256, 0, sc>>>(g, cb, sp);
+            if (plain) {
+                k_corners<true><<<e256, 256, 0, sc>>>(g, cb, sp);
+            } else {
+                if (cb.ctab) {
+                    k_cell_table<<<cblocks, 256, 0, sc>>>(g, cb, p0, p1);
+                    (*launches)++;
+                }
+                k_corners<false><<<e256, 256, 0, sc>>>(g, cb, sp);
+            }
             if (timed && ev0) cudaEventRecord(ev0, sc);
             if (plain) k_quad<true><<<eblocks, qb, 0, sc>>>(g, cb, ecap, sp, st);
             else k_quad<false><<<eblocks, qb, 0, sc>>>(g, cb, ecap, sp, st);
