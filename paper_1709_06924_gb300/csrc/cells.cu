@@ -124,20 +124,25 @@ struct Span {
     const int *e0, *etot;
 };
 
-__device__ __forceinline__ int bin_index(double x, double y, double z, int G) {
-    double ax = fabs(x), ay = fabs(y), az = fabs(z);
+// Cube-map bin of a unit vector: face = its largest component, then the
+// gnomonic coordinates s, t in [-1, 1] on G x G bins.  In FP32 from the
+// rounded coordinates: s and t are within 2e-7 of their exact values, and
+// the cap queries widen their bin ranges by at least 1e-6 in s and t; a
+// point whose two largest components agree to 1e-7 may take either face,
+// and a query takes every face its cap reaches (|q_a| + S >= 1/sqrt3 - 1e-6).
+__device__ __forceinline__ int bin_index(float x, float y, float z, int G) {
+    const float ax = fabsf(x), ay = fabsf(y), az = fabsf(z);
     int a;
-    double m, pb, pc;
+    float m, pb, pc;
     if (ax >= ay && ax >= az) { a = 0; m = x; pb = y; pc = z; }
     else if (ay >= az) { a = 1; m = y; pb = z; pc = x; }
     else { a = 2; m = z; pb = x; pc = y; }
-    double am = fabs(m);
-    double s = pb / am, t = pc / am;
-    int iu = (int)floor((s + 1.0) * 0.5 * G);
-    int iv = (int)floor((t + 1.0) * 0.5 * G);
+    const float inv = 1.0f / fabsf(m);
+    int iu = (int)floorf((pb * inv + 1.0f) * 0.5f * G);
+    int iv = (int)floorf((pc * inv + 1.0f) * 0.5f * G);
     iu = min(max(iu, 0), G - 1);
     iv = min(max(iv, 0), G - 1);
-    int face = 2 * a + (m < 0.0 ? 1 : 0);
+    const int face = 2 * a + (m < 0.0f ? 1 : 0);
     return (face * G + iv) * G + iu;
 }
 
@@ -156,7 +161,7 @@ __global__ void k_bin_count(const double *__restrict__ z, Grid g, int *__restric
         atomicAdd(&count[base], 1);
         return;
     }
-    int b = base + bin_index(x, y, w, v.G);
+    int b = base + bin_index((float)x, (float)y, (float)w, v.G);
     bin_of[i] = b;
     atomicAdd(&count[b], 1);
 }
@@ -779,7 +784,7 @@ __global__ void __launch_bounds__(128) k_topo(Grid g, CellOut out, CellBuf cb,
                 r = 1.1f * hint;
             } else {
                 // local density from the own bin: lambda = count / solid angle
-                int b = bin_index(zi.x, zi.y, zi.z, v.G);
+                int b = bin_index((float)zi.x, (float)zi.y, (float)zi.z, v.G);
                 int cbn = v.bstart[b + 1] - v.bstart[b];
                 float ax = fabsf(zif.x), ay = fabsf(zif.y), az = fabsf(zif.z);
                 float am = fmaxf(ax, fmaxf(ay, az));
@@ -1121,7 +1126,7 @@ __global__ void __launch_bounds__(WPB * 32, 24 / WPB) k_topo_warp(Grid g, CellOu
             if (hint > 0.0f) {
                 r = hint;
             } else {
-                const int b = bin_index((double)hp.x, (double)hp.y, (double)hp.z, v.G);
+                const int b = bin_index(hp.x, hp.y, hp.z, v.G);
                 const int cbn = v.bstart[b + 1] - v.bstart[b];
                 const float ax = fabsf(hp.x), ay = fabsf(hp.y), az = fabsf(hp.z);
                 const float am = fmaxf(ax, fmaxf(ay, az));
@@ -2424,7 +2429,7 @@ void bin_points(const double *z, const Grid &g, int *bin_of, int *count, int *st
     cudaMemsetAsync(count, 0, sizeof(int) * nbins, s);
     int blocks = (n + 255) / 256;
     k_bin_count<<<blocks, 256, 0, s>>>(z, gb, bin_of, count, st);
-    k_bin_max<<<dim3(32, g.inst ? g.nprob : 1), 256, 0, s>>>(gb, count, st);
+    k_bin_max<<<dim3(g.inst ? 32 : 4 * 152, g.inst ? g.nprob : 1), 256, 0, s>>>(gb, count, st);
     exclusive_scan(count, start, nbins, scan_tmp, s, launches);
     k_set_total<<<1, 1, 0, s>>>(start, nbins, n);
     cudaMemcpyAsync(cursor, start, sizeof(int) * nbins, cudaMemcpyDeviceToDevice, s);
