@@ -2129,11 +2129,14 @@ __global__ void __launch_bounds__(512) k_quad(Grid g, CellBuf cb, int ecap, Span
                 const df3 dm{df_add(hh.x, df_mul(mm, df_add(A.x, hh.x))), df_add(hh.y, df_mul(mm, df_add(A.y, hh.y))),
                              df_add(hh.z, df_mul(mm, df_add(A.z, hh.z)))};
                 AccDF ad{};
-                if (g.fan) {
-                    tri_df(rho.kind, dd.g1, dd.gam, A, aA1, da, db, dd.ev, eA, u0, tcdf, vs, K, ad);
-                } else {
-                    tri_df(rho.kind, dd.g1, dd.gam, A, aA1, da, dm, dd.ev, eA, u0, tcdf, vs, K, ad);
-                    tri_df(rho.kind, dd.g1, dd.gam, A, aA1, dm, db, dd.ev, eA, u0, tcdf, vs, K, ad);
+                // the edge's sub-triangles (z_i, v_a, mu), (z_i, mu, v_b), or the fan's
+                // (z_i, v_a, v_b), in order, through one copy of the rule's code
+                const int ntri = g.fan ? 1 : 2;
+#pragma unroll 1
+                for (int t = 0; t < ntri; ++t) {
+                    const df3 tb = (t == 0) ? da : dm;
+                    const df3 tc = (t == 0 && !g.fan) ? dm : db;
+                    tri_df(rho.kind, dd.g1, dd.gam, A, aA1, tb, tc, dd.ev, eA, u0, tcdf, vs, K, ad);
                 }
                 ef[e] = make_float2(ad.m.hi, ad.m.lo);
                 ef[(size_t)ecap + e] = make_float2(ad.qx.hi, ad.qx.lo);
