@@ -344,18 +344,19 @@ def df_inst_per_generator(series_len: float) -> float:
 
 # ---------------------------------------------------------- rooflines
 # Executed warp instructions per unit, from one-pass ncu captures of the
-# timed steps of this benchmark at N = 2,621,442 (smsp__inst_executed.sum of
-# one launch divided by N):
-#   ncu --metrics smsp__inst_executed.sum --clock-control none -k regex:k_quad -c 3
-#       python bench.py --steps 2 --warmup 1 --no-other-form --no-time-to-tol --no-batched
-#       --no-serving --no-table1 --no-chain --no-cpu-baseline --no-e2e
-# and likewise for k_topo_warp (per cell, by lanes per cell).
-QUAD_INST_PER_GENERATOR = 4940772009 / 2621442
-TOPO_INST_PER_CELL = {32: 3335526320 / 2621442, 16: 2225292670 / 2621442}
+# timed steps of this benchmark at N = 2,621,442 (smsp__inst_executed.sum,
+# mean of two launches, divided by N):
+#   F="--steps 2 --warmup 2 --no-other-form --no-time-to-tol --no-batched --no-serving
+#      --no-table1 --no-chain --no-cpu-baseline --no-e2e --tuning chunks=1,topo_cell_lanes=16,quad_block=128"
+#   ncu --metrics smsp__inst_executed.sum --clock-control none -k regex:"k_quad|k_topo_warp" -s 6 -c 4
+#       python bench.py $F
+# and likewise for k_topo_warp with 32 lanes per cell.
+QUAD_INST_PER_GENERATOR = 4892967348 / 2621442
+TOPO_INST_PER_CELL = {32: 3335526320 / 2621442, 16: 2225676756 / 2621442}
 # DRAM bytes of one k_quad launch at N = 163,842 (ncu --set full:
-# dram__bytes_read.sum + dram__bytes_write.sum, 71.75 + 11.06 MB), scaled
+# dram__bytes_read.sum + dram__bytes_write.sum, 74.30 + 11.15 MB), scaled
 # by the number of generators; None once the kernel has changed since
-QUAD_DRAM_BYTES_163842 = 82.811392e6
+QUAD_DRAM_BYTES_163842 = 85.444352e6
 
 
 def quad_traffic_bytes(n: int):
