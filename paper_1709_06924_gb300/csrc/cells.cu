@@ -2003,19 +2003,6 @@ __device__ __forceinline__ void tri_df(int kind, df g1, df gam, df3 A, df aA1, d
 // rule points, summed in order).  The edge's five sums go to the edge list;
 // k_cell_sum adds a cell's edges in edge order, so a cell's result depends
 // on its own edges only (not on where they fall in the launch).
-// the density's direction as a double-float vector (x_c for the tanh cap,
-// e_z for X3) and its constants 1 - gamma, gamma
-struct DensDF {
-    df3 ev;
-    df g1, gam;
-};
-__device__ __forceinline__ DensDF dens_df(const Density &r) {
-    DensDF d;
-    d.ev = (r.kind == 1) ? df3{df{0.0f, 0.0f}, df{0.0f, 0.0f}, df{1.0f, 0.0f}} : df3_from(r.xc0, r.xc1, r.xc2);
-    d.g1 = df_from(1.0 - r.gamma);
-    d.gam = df_from(r.gamma);
-    return d;
-}
 
 template <bool PLAIN>
 __global__ void __launch_bounds__(512) k_quad(Grid g, CellBuf cb, int ecap, Span sp, DevStatus *st) {
@@ -2113,7 +2100,7 @@ __global__ void __launch_bounds__(512) k_quad(Grid g, CellBuf cb, int ecap, Span
             if (r2 <= 0.9e-3f && (rho.kind < 2 || K > 0)) {
                 const df3 A{df{hp.x, lp.x}, df{hp.y, lp.y}, df{hp.z, lp.z}};
                 const df aA1{llp.w, 0.0f};
-                const DensDF dd = g.rho ? dens_df(rho) : dd0;
+                const DensDF dd = g.rho ? g.rhodf[b] : dd0;
                 const df eA = df3_dot(dd.ev, A);
                 const df u0 = (K > 0) ? u0c : df{0.0f, 0.0f};
                 const float vs = (K > 0) ? vsc : 1.0f;

@@ -74,6 +74,7 @@ Grid make_grid(const EvalSet &E) {
     g.pinst = E.d_pinst;
     g.rho = E.d_rho;
     g.rhof = E.d_rhof;
+    g.rhodf = E.d_rhodf;
     g.tabs = E.precision != 1 ? E.d_tabs : nullptr;
     g.ist = E.d_ist;
     g.active = E.d_active;
@@ -191,7 +192,7 @@ cudaError_t evalset_alloc(EvalSet &E, int64_t cap_n, int cap_b, int precision, c
 #define AL(ptr, cnt) \
     if (e == cudaSuccess) e = ealloc(E, &(ptr), (cnt))
     AL(E.d_inst, cap_b); AL(E.d_pinst, N); AL(E.d_pbase, cap_b); AL(E.d_active, cap_b);
-    AL(E.d_rho, cap_b); AL(E.d_rhof, cap_b); AL(E.d_ist, cap_b); AL(E.d_st, 1);
+    AL(E.d_rho, cap_b); AL(E.d_rhof, cap_b); AL(E.d_rhodf, cap_b); AL(E.d_ist, cap_b); AL(E.d_st, 1);
     AL(E.zt, n3); AL(E.gt, n3); AL(E.ht, N); AL(E.fc, N); AL(E.q, n3); AL(E.nrm, N); AL(E.radius, N);
     AL(E.partials, E.partials_len);
     E.seg_partials_len = max_seg_partials(cap_n, cap_b);
@@ -226,7 +227,7 @@ cudaError_t evalset_alloc(EvalSet &E, int64_t cap_n, int cap_b, int precision, c
 void evalset_free(EvalSet &E) {
     if (E.graph) cudaGraphExecDestroy(E.graph);
     E.graph = nullptr;
-    void *ptrs[] = {E.d_inst, E.d_pinst, E.d_pbase, E.d_active, E.d_rho, E.d_rhof, E.d_ist, E.d_st, E.zt, E.gt,
+    void *ptrs[] = {E.d_inst, E.d_pinst, E.d_pbase, E.d_active, E.d_rho, E.d_rhof, E.d_rhodf, E.d_ist, E.d_st, E.zt, E.gt,
                     E.ht, E.fc, E.q, E.nrm, E.radius, E.partials, E.zs, E.zf, E.zl, E.zll, E.cvx, E.cnb, E.cdeg, E.eoff,
                     E.ecell, E.escan, E.eacc, E.vo, E.ctab, E.tab_pool, E.d_tabs, E.d_seg, E.seg_partials, E.seg_scal, E.bin_of, E.count, E.start, E.cursor, E.scan_tmp, E.sidx,
                     E.list1, E.list2};
@@ -253,6 +254,7 @@ cudaError_t evalset_layout(EvalSet &E, int B, const int *ns, const scvt_density 
     E.tabs.assign(B, DensTab{});
     std::vector<Density> rho(B);
     std::vector<DensityF> rhof(B);
+    std::vector<DensDF> rhodf(B);
     int64_t off = 0, nbt = 0;
     for (int b = 0; b < B; ++b) {
         E.geom[b].p0 = (int)off;
@@ -263,6 +265,7 @@ cudaError_t evalset_layout(EvalSet &E, int B, const int *ns, const scvt_density 
         E.max_nb = std::max(E.max_nb, nb);
         rho[b] = to_device_density(rhos[b]);
         rhof[b] = to_density32(rho[b]);
+        rhodf[b] = dens_df(rho[b]);
         off += ns[b];
     }
     if (B == 0) return cudaSuccess;
@@ -271,6 +274,8 @@ cudaError_t evalset_layout(EvalSet &E, int B, const int *ns, const scvt_density 
         e = cudaMemcpyAsync(E.d_rho, rho.data(), sizeof(Density) * B, cudaMemcpyHostToDevice, E.stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(E.d_rhof, rhof.data(), sizeof(DensityF) * B, cudaMemcpyHostToDevice, E.stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(E.d_rhodf, rhodf.data(), sizeof(DensDF) * B, cudaMemcpyHostToDevice, E.stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(E.d_pbase, E.pbase.data(), sizeof(int) * B, cudaMemcpyHostToDevice, E.stream);
     // each problem's density table, laid out in the pool in problem order

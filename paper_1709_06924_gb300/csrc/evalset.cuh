@@ -42,6 +42,7 @@ struct EvalSet {
     int *d_pinst = nullptr, *d_pbase = nullptr, *d_active = nullptr;
     Density *d_rho = nullptr;
     DensityF *d_rhof = nullptr;
+    DensDF *d_rhodf = nullptr;
     DevStatus *d_ist = nullptr, *d_st = nullptr;
     DevStatus *h_ist = nullptr, *h_st = nullptr;
     int *h_active = nullptr;

@@ -5,6 +5,7 @@
 #include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
+#include "df.cuh"
 #include "scvt.h"
 
 namespace scvt {
@@ -62,6 +63,21 @@ struct Density {
 };
 
 // the density in FP32 for the mixed-precision quadrature (inv_alpha = 1/alpha)
+// The density's direction as a double-float vector (x_c for the tanh cap,
+// e_z for X3) and its constants 1 - gamma, gamma: the double-float
+// quadrature's view of a density, converted once per problem.
+struct DensDF {
+    df3 ev;
+    df g1, gam;
+};
+__host__ __device__ inline DensDF dens_df(const Density &r) {
+    DensDF d;
+    d.ev = (r.kind == 1) ? df3{df{0.0f, 0.0f}, df{0.0f, 0.0f}, df{1.0f, 0.0f}} : df3_from(r.xc0, r.xc1, r.xc2);
+    d.g1 = df_from(1.0 - r.gamma);
+    d.gam = df_from(r.gamma);
+    return d;
+}
+
 struct DensityF {
     int kind;
     float gamma, beta, inv_alpha, xc0, xc1, xc2;
@@ -151,6 +167,7 @@ struct Grid {
     const int *pinst;       // problem of each position / original index
     const Density *rho;     // per-problem densities
     const DensityF *rhof;
+    const DensDF *rhodf;    // the same as double-float constants (FP64 form)
     const DensTab *tabs;    // per-problem density tables
     DevStatus *ist;         // per-problem status (flags, sums)
     const int *active;      // per-problem: evaluate (1) or skip (0); null = all
