@@ -2357,7 +2357,8 @@ __global__ void __launch_bounds__(512) k_quad32(Grid g, CellBuf cb, int ecap, Sp
 // thread per cell: the cell's edge sums added in edge order, then the cell's
 // outputs (g_i, h_i, m_i, c_i, F_i at the original index).  KIND 0: the FP64
 // form's double-float pairs (m, o, F), added as pairs; 1: the mixed form's
-// FP32 sums (m, o, F), added in FP64; 2: the plain form's FP64 sums (m, c, F).
+// FP32 sums (m, o, F), added as pairs (FP32 operations instead of FP64 ones
+// on GB300's narrow FP64 pipe); 2: the plain form's FP64 sums (m, c, F).
 // With o = sum w rho (p - z_i) the gradient -2 (o - (o.z_i) z_i) never
 // subtracts m_i z_i from itself.
 template <int KIND>
@@ -2382,15 +2383,15 @@ __global__ void __launch_bounds__(256) k_cell_sum(Grid g, CellOut out, CellBuf c
         }
         acc = Acc{df_to(s[0]), df_to(s[1]), df_to(s[2]), df_to(s[3]), df_to(s[4])};
     } else if (KIND == 1) {
+        // FP32 edge sums added exactly enough as pairs (no FP64 instruction per edge)
         const float *ea = (const float *)cb.eacc;
+        df s[5] = {};
         for (int k = 0; k < deg; ++k) {
             const int e = e0 + k;
-            acc.m += (double)ea[e];
-            acc.cx += (double)ea[(size_t)ecap + e];
-            acc.cy += (double)ea[2 * (size_t)ecap + e];
-            acc.cz += (double)ea[3 * (size_t)ecap + e];
-            acc.e += (double)ea[4 * (size_t)ecap + e];
+#pragma unroll
+            for (int c = 0; c < 5; ++c) s[c] = df_add_f(s[c], ea[(size_t)c * ecap + e]);
         }
+        acc = Acc{df_to(s[0]), df_to(s[1]), df_to(s[2]), df_to(s[3]), df_to(s[4])};
     } else {
         const double *ea = cb.eacc;
         for (int k = 0; k < deg; ++k) {
