@@ -1072,6 +1072,50 @@ __device__ __forceinline__ int gather(const Grid &g, int p, float4 hp, float4 lp
     return cnt;
 }
 
+// append every generator of up to L bin rows, scanned as one list: lane k < nr
+// holds row k's range [q0, q0 + len); the L lanes of the sub-warp take the
+// rows' generators L at a time in row order, so the candidates arrive in the
+// same order as row by row, with fewer partly filled rounds and the rows'
+// ranges loaded in one round
+template <int L>
+__device__ __forceinline__ int gather_rows(const Grid &g, int p, float4 hp, float4 lp, int q0, int len, int nr,
+                                           float r2acc, int cnt, float *cd, int *cj, int sl, int sbase, unsigned smask,
+                                           unsigned *flags) {
+    constexpr unsigned lfull = (L == 32) ? 0xffffffffu : ((1u << L) - 1u);
+    int inc = len;
+#pragma unroll
+    for (int o = 1; o < L; o <<= 1) {
+        const int t = __shfl_up_sync(smask, inc, o, L);
+        if (sl >= o) inc += t;
+    }
+    const int total = __shfl_sync(smask, inc, L - 1, L);
+    const int pre = inc - len;  // first list position of this lane's row
+    for (int base = 0; base < total; base += L) {
+        const int f = base + sl;
+        // the row holding position f: the last k < nr with pre_k <= f
+        int k = 0;
+        for (int j = 1; j < nr; ++j)
+            if (__shfl_sync(smask, pre, j, L) <= f) k = j;
+        const int q = __shfl_sync(smask, q0, k, L) + f - __shfl_sync(smask, pre, k, L);
+        bool pred = false;
+        float d2 = 0.0f;
+        if (f < total && q != p) {
+            const float3 d = dfdiff(g, q, hp, lp);
+            d2 = fmaf(d.x, d.x, fmaf(d.y, d.y, d.z * d.z));
+            if (d2 == 0.0f) check_duplicate(g, ld(g.zs + p), q, flags);
+            pred = d2 <= r2acc;
+        }
+        const unsigned m = (__ballot_sync(smask, pred) >> sbase) & lfull;
+        const int pos = cnt + __popc(m & ((1u << sl) - 1u));
+        if (pred && pos < 2 * L) {
+            cd[pos] = d2;
+            cj[pos] = q;
+        }
+        cnt += __popc(m);
+    }
+    return cnt;
+}
+
 // WPB warps per block, L lanes per cell (32: one cell per warp, 16: two);
 // every collective runs on the cell's sub-warp.  knn_target: the number of
 // candidates the first radius aims at when the cell has no radius hint.
@@ -1178,10 +1222,16 @@ __global__ void __launch_bounds__(WPB * 32, 32 / WPB) k_topo_warp(Grid g, CellOu
                         hi[rr] = min(max((int)floorf((s1 + 1.0f) * 0.5f * v.G), 0), v.G - 1);
                     }
                     if (empty) continue;
-                    for (int iv = lo[1]; iv <= hi[1]; ++iv) {
-                        const int row = (face * v.G + iv) * v.G;
-                        cnt = gather<L>(g, p, hp, lp, v.bstart[row + lo[0]], v.bstart[row + hi[0] + 1], r2acc, cnt,
-                                        cd, cj, sl, sbase, smask, flags);
+                    // the face's bin rows lo[1] .. hi[1], up to L at a time
+                    for (int iv0 = lo[1]; iv0 <= hi[1]; iv0 += L) {
+                        const int nr = min(L, hi[1] - iv0 + 1);
+                        int q0 = 0, len = 0;
+                        if (sl < nr) {
+                            const int row = (face * v.G + iv0 + sl) * v.G;
+                            q0 = v.bstart[row + lo[0]];
+                            len = v.bstart[row + hi[0] + 1] - q0;
+                        }
+                        cnt = gather_rows<L>(g, p, hp, lp, q0, len, nr, r2acc, cnt, cd, cj, sl, sbase, smask, flags);
                     }
                 }
             }
