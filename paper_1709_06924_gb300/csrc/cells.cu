@@ -2009,40 +2009,48 @@ __device__ __forceinline__ void tri_df(int kind, df g1, df gam, df3 A, df aA1, d
     for (int k = 0; k < 7; ++k) {
         const df b1{kQdf[k][0][0], kQdf[k][0][1]}, b2{kQdf[k][1][0], kQdf[k][1][1]}, W{kQdf[k][2][0], kQdf[k][2][1]};
         const df B11{kQdf[k][3][0], kQdf[k][3][1]}, B12{kQdf[k][4][0], kQdf[k][4][1]}, B22{kQdf[k][5][0], kQdf[k][5][1]};
-        const df Aw = df_add(df_mul(b1, Ab), df_mul(b2, Ac));
-        const df ww = df_add(df_add(df_mul(B11, bb), df_mul(B12, bc)), df_mul(B22, cc));
-        const df dl = df_neg(df_add(df_add(aA1, df{2.0f * Aw.hi, 2.0f * Aw.lo}), ww));
-        const df d2 = df_mul(dl, dl);
+        // unnormalized chains (dfl_*); the sums that cancel (delta, |w|^2 + A.w,
+        // the series argument) and the values used in several products are
+        // normalized
+        const df Aw = dfl_add(dfl_mul(b1, Ab), dfl_mul(b2, Ac));
+        const df ww = dfl_add(dfl_add(dfl_mul(B11, bb), dfl_mul(B12, bc)), dfl_mul(B22, cc));
+        const df dl = df_norm(df_neg(dfl_add(dfl_add(aA1, df{2.0f * Aw.hi, 2.0f * Aw.lo}), ww)));
+        const df d2 = dfl_mul(dl, dl);
         const float tail = d2.hi * dl.hi * (0.3125f + dl.hi * (0.2734375f + dl.hi * 0.24609375f));
-        const df m = df_add_f(df_add(df{0.5f * dl.hi, 0.5f * dl.lo}, df_mul_f(d2, 0.375f)), tail);
-        const df xw = df_add(df_mul(b1, eb), df_mul(b2, ec));
-        const df eq = df_add(xw, df_mul(m, df_add(eA, xw)));
+        const df m = df_norm(dfl_add_f(dfl_add(df{0.5f * dl.hi, 0.5f * dl.lo}, dfl_mul_f(d2, 0.375f)), tail));
+        const df xw = dfl_add(dfl_mul(b1, eb), dfl_mul(b2, ec));
+        const df eq = dfl_add(xw, dfl_mul(m, dfl_add(eA, xw)));
         df rv;
         if (kind == 0) {
             rv = df{1.0f, 0.0f};
         } else if (kind == 1) {
-            const df pz = df_add(eA, eq), z2 = df_mul(pz, pz);
-            rv = df_add(df_mul(g1, df_mul(z2, z2)), gam);
+            const df pz = df_norm(dfl_add(eA, eq)), z2 = df_norm(dfl_mul(pz, pz));
+            rv = dfl_add(dfl_mul(g1, dfl_mul(z2, z2)), gam);
         } else {
             // the argument of the cell's series, scaled by its power of two
-            const df u = df_add(u0, eq);
+            const df u = df_norm(dfl_add(u0, eq));
             const df v{u.hi * vs, u.lo * vs};
             rv = df{sdf[K - 1].x, sdf[K - 1].y};
-            for (int j = K - 2; j >= 0; --j) rv = df_fma(rv, v, df{sdf[j].x, sdf[j].y});
+            for (int j = K - 2; j >= 0; --j) rv = dfl_fma(rv, v, df{sdf[j].x, sdf[j].y});
         }
-        const df wr = df_mul(df_mul(W, area), rv);
-        const df wm = df_mul(wr, m);
+        const df wr = df_norm(dfl_mul(dfl_mul(W, area), rv));
+        const df wm = dfl_mul(wr, m);
         // |q|^2 = |w|^2 + 2 m (|w|^2 + A.w) + m^2 - m^2 delta
-        const df mwa = df_mul(m, df_add(ww, Aw)), msq = df_mul(m, m);
-        const df e = df_add_f(df_add(df_add(ww, df{2.0f * mwa.hi, 2.0f * mwa.lo}), msq), -msq.hi * dl.hi);
+        const df mwa = dfl_mul(m, df_norm(dfl_add(ww, Aw))), msq = dfl_mul(m, m);
+        const df e = dfl_add_f(dfl_add(dfl_add(ww, df{2.0f * mwa.hi, 2.0f * mwa.lo}), msq), -msq.hi * dl.hi);
         // wr q = (wr + wm) w + wm A: sums of (wr + wm) b1, (wr + wm) b2 and wm
-        const df wp = df_add(wr, wm);
-        S0 = df_add(S0, wr);
-        S1 = df_add(S1, df_mul(wp, b1));
-        S2 = df_add(S2, df_mul(wp, b2));
-        T0 = df_add(T0, wm);
-        E = df_add(E, df_mul(wr, e));
+        const df wp = dfl_add(wr, wm);
+        S0 = dfl_add(S0, wr);
+        S1 = dfl_add(S1, dfl_mul(wp, b1));
+        S2 = dfl_add(S2, dfl_mul(wp, b2));
+        T0 = dfl_add(T0, wm);
+        E = dfl_add(E, dfl_mul(wr, e));
     }
+    S0 = df_norm(S0);
+    S1 = df_norm(S1);
+    S2 = df_norm(S2);
+    T0 = df_norm(T0);
+    E = df_norm(E);
     const df a1 = S1, a2 = S2;
     acc.m = df_add(acc.m, S0);
     acc.qx = df_add(acc.qx, df_add(df_add(df_mul(a1, b.x), df_mul(a2, c.x)), df_mul(T0, A.x)));

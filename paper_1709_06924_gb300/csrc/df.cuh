@@ -99,6 +99,36 @@ SCVT_HD df df_div(df x, df y) {
     return fast_two_sum(q1, q2);
 }
 
+// ---- unnormalized operations for chains of intermediate values: the same
+// as df_add / df_mul without the closing Fast2Sum, so lo may grow to a few
+// ulps of hi (hi + lo is the value).  Their errors stay of the same order
+// while no sum cancels; a pair that comes out of a cancelling sum is
+// normalized (df_norm) before it is multiplied, since the product takes only
+// FP32 precision of lo.
+SCVT_HD df df_norm(df x) { return fast_two_sum(x.hi, x.lo); }
+SCVT_HD df dfl_add(df x, df y) {
+    df s = two_sum(x.hi, y.hi);
+    s.lo += x.lo + y.lo;
+    return s;
+}
+SCVT_HD df dfl_add_f(df x, float f) {
+    df s = two_sum(x.hi, f);
+    s.lo += x.lo;
+    return s;
+}
+SCVT_HD df dfl_mul(df x, df y) {
+    df p = two_prod(x.hi, y.hi);
+    p.lo = df_fma_f(x.hi, y.lo, p.lo);
+    p.lo = df_fma_f(x.lo, y.hi, p.lo);
+    return p;
+}
+SCVT_HD df dfl_mul_f(df x, float f) {
+    df p = two_prod(x.hi, f);
+    p.lo = df_fma_f(x.lo, f, p.lo);
+    return p;
+}
+SCVT_HD df dfl_fma(df x, df y, df z) { return dfl_add(dfl_mul(x, y), z); }
+
 struct df3 {
     df x, y, z;
 };
