@@ -1600,16 +1600,16 @@ __global__ void __launch_bounds__(WPB * 32, 32 / WPB) k_topo_warp(Grid g, CellOu
 // (both differences of parts are exact by TwoSum; the third parts are tiny)
 __device__ __forceinline__ df3 gen_diff(const Grid &g, int q, float4 hp, float4 lp, float4 llp) {
     const float4 hq = g.zf[q], lq = g.zl[q], llq = g.zll[q];
-    return df3{df_add_f(df_add(two_sum(hq.x, -hp.x), two_sum(lq.x, -lp.x)), llq.x - llp.x),
-               df_add_f(df_add(two_sum(hq.y, -hp.y), two_sum(lq.y, -lp.y)), llq.y - llp.y),
-               df_add_f(df_add(two_sum(hq.z, -hp.z), two_sum(lq.z, -lp.z)), llq.z - llp.z)};
+    return df3{df_norm(dfl_add_f(dfl_add(two_sum(hq.x, -hp.x), two_sum(lq.x, -lp.x)), llq.x - llp.x)),
+               df_norm(dfl_add_f(dfl_add(two_sum(hq.y, -hp.y), two_sum(lq.y, -lp.y)), llq.y - llp.y)),
+               df_norm(dfl_add_f(dfl_add(two_sum(hq.z, -hp.z), two_sum(lq.z, -lp.z)), llq.z - llp.z))};
 }
 
 // 1/|x| - 1 for delta = 1 - |x|^2 <= 1e-3 (binomial series, exact to 3e-19)
 __device__ __forceinline__ df inv_norm_m1(df dl) {
-    const df d2 = df_mul(dl, dl);
+    const df d2 = dfl_mul(dl, dl);
     const float tail = d2.hi * dl.hi * (0.3125f + dl.hi * (0.2734375f + dl.hi * 0.24609375f));
-    return df_add_f(df_add(df{0.5f * dl.hi, 0.5f * dl.lo}, df_mul_f(d2, 0.375f)), tail);
+    return df_norm(dfl_add_f(dfl_add(df{0.5f * dl.hi, 0.5f * dl.lo}, dfl_mul_f(d2, 0.375f)), tail));
 }
 
 // FP64 line of neighbour gen in the frame at z_i for the corners: (a, b) =
@@ -1688,27 +1688,30 @@ __global__ void __launch_bounds__(256) k_corners(Grid g, CellBuf cb, Span sp) {
             for (int t = 0; t < 2; ++t) {
                 const int q = t == 0 ? ga : gb;
                 const df3 d = gen_diff(g, q, hp, lp, llp);
-                la[t] = df_add(df_add(df_mul_f(d.x, e1.x), df_mul_f(d.y, e1.y)), df_mul_f(d.z, e1.z));
-                lb[t] = df_add(df_add(df_mul_f(d.x, e2.x), df_mul_f(d.y, e2.y)), df_mul_f(d.z, e2.z));
-                const df c2 = df_add_f(df3_dot(d, d), llp.w - g.zll[q].w);
+                // unnormalized chains (dfl_*), normalized where sums cancel
+                la[t] = df_norm(dfl_add(dfl_add(dfl_mul_f(d.x, e1.x), dfl_mul_f(d.y, e1.y)), dfl_mul_f(d.z, e1.z)));
+                lb[t] = df_norm(dfl_add(dfl_add(dfl_mul_f(d.x, e2.x), dfl_mul_f(d.y, e2.y)), dfl_mul_f(d.z, e2.z)));
+                const df c2 = df_norm(dfl_add_f(df3_dot_n(d, d), llp.w - g.zll[q].w));
                 lc[t] = df{0.5f * c2.hi, 0.5f * c2.lo};
             }
-            const df p1 = df_mul(la[0], lb[1]), p2 = df_mul(la[1], lb[0]);
-            const df det = df_sub(p1, p2);
+            const df p1 = dfl_mul(la[0], lb[1]), p2 = dfl_mul(la[1], lb[0]);
+            const df det = df_norm(dfl_add(p1, df_neg(p2)));
             if (fabsf(det.hi) * 8.0f >= fabsf(p1.hi) + fabsf(p2.hi)) {
-                const df u = df_div(df_sub(df_mul(lc[0], lb[1]), df_mul(lc[1], lb[0])), det);
-                const df w = df_div(df_sub(df_mul(la[0], lc[1]), df_mul(la[1], lc[0])), det);
-                const df3 dx{df_add(df_mul_f(u, e1.x), df_mul_f(w, e2.x)), df_add(df_mul_f(u, e1.y), df_mul_f(w, e2.y)),
-                             df_add(df_mul_f(u, e1.z), df_mul_f(w, e2.z))};
+                const df u = df_div(df_norm(dfl_add(dfl_mul(lc[0], lb[1]), df_neg(dfl_mul(lc[1], lb[0])))), det);
+                const df w = df_div(df_norm(dfl_add(dfl_mul(la[0], lc[1]), df_neg(dfl_mul(la[1], lc[0])))), det);
+                const df3 dx{df_norm(dfl_add(dfl_mul_f(u, e1.x), dfl_mul_f(w, e2.x))),
+                             df_norm(dfl_add(dfl_mul_f(u, e1.y), dfl_mul_f(w, e2.y))),
+                             df_norm(dfl_add(dfl_mul_f(u, e1.z), dfl_mul_f(w, e2.z)))};
                 const float r2 = dx.x.hi * dx.x.hi + dx.y.hi * dx.y.hi + dx.z.hi * dx.z.hi;
                 if (r2 <= 0.9e-3f) {
                     const df3 Z{df{hp.x, lp.x}, df{hp.y, lp.y}, df{hp.z, lp.z}};
-                    const df zd = df3_dot(Z, dx);
-                    const df dl = df_neg(df_add(df_add_f(df{2.0f * zd.hi, 2.0f * zd.lo}, llp.w), df3_dot(dx, dx)));
+                    const df zd = df3_dot_n(Z, dx);
+                    const df dl =
+                        df_norm(df_neg(dfl_add(dfl_add_f(df{2.0f * zd.hi, 2.0f * zd.lo}, llp.w), df3_dot_n(dx, dx))));
                     const df m = inv_norm_m1(dl);
-                    const df ox = df_add(dx.x, df_mul(m, df_add(Z.x, dx.x)));
-                    const df oy = df_add(dx.y, df_mul(m, df_add(Z.y, dx.y)));
-                    const df oz = df_add(dx.z, df_mul(m, df_add(Z.z, dx.z)));
+                    const df ox = df_norm(dfl_add(dx.x, dfl_mul(m, dfl_add(Z.x, dx.x))));
+                    const df oy = df_norm(dfl_add(dx.y, dfl_mul(m, dfl_add(Z.y, dx.y))));
+                    const df oz = df_norm(dfl_add(dx.z, dfl_mul(m, dfl_add(Z.z, dx.z))));
                     store_corner_df(cb.vx + (size_t)p * kCellSlots + k, df3{ox, oy, oz});
                     continue;
                 }
@@ -1997,11 +2000,11 @@ struct AccDF {
 
 __device__ __forceinline__ void tri_df(int kind, df g1, df gam, df3 A, df aA1, df3 b, df3 c, df3 ev, df eA, df u0,
                                        const float2 *__restrict__ sdf, float vs, int K, AccDF &acc) {
-    const df Ab = df3_dot(A, b), Ac = df3_dot(A, c);
-    const df bb = df3_dot(b, b), cc = df3_dot(c, c), bc = df3_dot(b, c);
-    const df eb = df3_dot(ev, b), ec = df3_dot(ev, c);
-    const df det = df3_dot(A, df3_cross(b, c));
-    const df den = df_add(df_add_f(df_mul_f(aA1, 3.0f), 4.0f), df_add(df_mul_f(df_add(Ab, Ac), 2.0f), bc));
+    const df Ab = df3_dot_n(A, b), Ac = df3_dot_n(A, c);
+    const df bb = df3_dot_n(b, b), cc = df3_dot_n(c, c), bc = df3_dot_n(b, c);
+    const df eb = df3_dot_n(ev, b), ec = df3_dot_n(ev, c);
+    const df det = df3_dot_n(A, df3_cross_n(b, c));
+    const df den = df_norm(dfl_add(dfl_add_f(dfl_mul_f(aA1, 3.0f), 4.0f), dfl_add(dfl_mul_f(dfl_add(Ab, Ac), 2.0f), bc)));
     const df t = df_div(det, den);
     const df area = df_mul_f(df_add_f(t, -t.hi * t.hi * t.hi * (1.0f / 3.0f)), 2.0f);
     df S0{0.0f, 0.0f}, S1{0.0f, 0.0f}, S2{0.0f, 0.0f}, T0{0.0f, 0.0f}, E{0.0f, 0.0f};
@@ -2052,11 +2055,11 @@ __device__ __forceinline__ void tri_df(int kind, df g1, df gam, df3 A, df aA1, d
     T0 = df_norm(T0);
     E = df_norm(E);
     const df a1 = S1, a2 = S2;
-    acc.m = df_add(acc.m, S0);
-    acc.qx = df_add(acc.qx, df_add(df_add(df_mul(a1, b.x), df_mul(a2, c.x)), df_mul(T0, A.x)));
-    acc.qy = df_add(acc.qy, df_add(df_add(df_mul(a1, b.y), df_mul(a2, c.y)), df_mul(T0, A.y)));
-    acc.qz = df_add(acc.qz, df_add(df_add(df_mul(a1, b.z), df_mul(a2, c.z)), df_mul(T0, A.z)));
-    acc.e = df_add(acc.e, E);
+    acc.m = df_norm(dfl_add(acc.m, S0));
+    acc.qx = df_norm(dfl_add(acc.qx, dfl_add(dfl_add(dfl_mul(a1, b.x), dfl_mul(a2, c.x)), dfl_mul(T0, A.x))));
+    acc.qy = df_norm(dfl_add(acc.qy, dfl_add(dfl_add(dfl_mul(a1, b.y), dfl_mul(a2, c.y)), dfl_mul(T0, A.y))));
+    acc.qz = df_norm(dfl_add(acc.qz, dfl_add(dfl_add(dfl_mul(a1, b.z), dfl_mul(a2, c.z)), dfl_mul(T0, A.z))));
+    acc.e = df_norm(dfl_add(acc.e, E));
 }
 
 // One thread per Voronoi edge (two signed sub-triangles of Sec. 3.2.2, 14
@@ -2161,20 +2164,19 @@ __global__ void __launch_bounds__(512) k_quad(Grid g, CellBuf cb, int ecap, Span
                 const df3 A{df{hp.x, lp.x}, df{hp.y, lp.y}, df{hp.z, lp.z}};
                 const df aA1{llp.w, 0.0f};
                 const DensDF dd = g.rho ? g.rhodf[b] : dd0;
-                const df eA = df3_dot(dd.ev, A);
+                const df eA = df3_dot_n(dd.ev, A);
                 const df u0 = (K > 0) ? u0c : df{0.0f, 0.0f};
                 const float vs = (K > 0) ? vsc : 1.0f;
                 // edge midpoint mu = (z_i + z_j) / |z_i + z_j|: with h = (z_j - z_i) / 2,
                 // mu - z_i = h + m (A + h), 1 - |A + h|^2 = -(|A|^2 - 1) - 2 A.h - |h|^2
                 const df3 hh{df{0.5f * dj.x.hi, 0.5f * dj.x.lo}, df{0.5f * dj.y.hi, 0.5f * dj.y.lo},
                              df{0.5f * dj.z.hi, 0.5f * dj.z.lo}};
-                const df Ah = df3_dot(A, hh);
-                const df dl = df_neg(df_add(df_add(aA1, df{2.0f * Ah.hi, 2.0f * Ah.lo}), df3_dot(hh, hh)));
-                const df d2 = df_mul(dl, dl);
-                const float tail = d2.hi * dl.hi * (0.3125f + dl.hi * (0.2734375f + dl.hi * 0.24609375f));
-                const df mm = df_add_f(df_add(df{0.5f * dl.hi, 0.5f * dl.lo}, df_mul_f(d2, 0.375f)), tail);
-                const df3 dm{df_add(hh.x, df_mul(mm, df_add(A.x, hh.x))), df_add(hh.y, df_mul(mm, df_add(A.y, hh.y))),
-                             df_add(hh.z, df_mul(mm, df_add(A.z, hh.z)))};
+                const df Ah = df3_dot_n(A, hh);
+                const df dl = df_norm(df_neg(dfl_add(dfl_add(aA1, df{2.0f * Ah.hi, 2.0f * Ah.lo}), df3_dot_n(hh, hh))));
+                const df mm = inv_norm_m1(dl);
+                const df3 dm{df_norm(dfl_add(hh.x, dfl_mul(mm, dfl_add(A.x, hh.x)))),
+                             df_norm(dfl_add(hh.y, dfl_mul(mm, dfl_add(A.y, hh.y)))),
+                             df_norm(dfl_add(hh.z, dfl_mul(mm, dfl_add(A.z, hh.z))))};
                 AccDF ad{};
                 // the edge's sub-triangles (z_i, v_a, mu), (z_i, mu, v_b), or the fan's
                 // (z_i, v_a, v_b), in order, through one copy of the rule's code

@@ -134,6 +134,15 @@ struct df3 {
 };
 
 SCVT_HD df3 df3_from(double x, double y, double z) { return df3{df_from(x), df_from(y), df_from(z)}; }
+// dot and cross products from unnormalized steps, the results normalized
+SCVT_HD df df3_dot_n(df3 a, df3 b) {
+    return df_norm(dfl_add(dfl_add(dfl_mul(a.x, b.x), dfl_mul(a.y, b.y)), dfl_mul(a.z, b.z)));
+}
+SCVT_HD df3 df3_cross_n(df3 a, df3 b) {
+    return df3{df_norm(dfl_add(dfl_mul(a.y, b.z), df_neg(dfl_mul(a.z, b.y)))),
+               df_norm(dfl_add(dfl_mul(a.z, b.x), df_neg(dfl_mul(a.x, b.z)))),
+               df_norm(dfl_add(dfl_mul(a.x, b.y), df_neg(dfl_mul(a.y, b.x))))};
+}
 SCVT_HD df df3_dot(df3 a, df3 b) { return df_add(df_add(df_mul(a.x, b.x), df_mul(a.y, b.y)), df_mul(a.z, b.z)); }
 SCVT_HD df3 df3_cross(df3 a, df3 b) {
     return df3{df_sub(df_mul(a.y, b.z), df_mul(a.z, b.y)), df_sub(df_mul(a.z, b.x), df_mul(a.x, b.z)),
