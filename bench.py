@@ -313,7 +313,10 @@ def fp64_flops_per_generator(kind: int, series_frac: float = 0.0, series_len: fl
 
 # FP32 instructions of the double-float operations (csrc/df.cuh): TwoSum 6,
 # Fast2Sum 3, the FMA exact product 2
-DF_OPS = {"add": 11, "add_f": 10, "mul": 7, "mul_f": 6, "fma": 18, "div": 36}
+# FP32 instructions of the double-float operations the quadrature uses
+# (df.cuh): unnormalized add / add of an FP32 / multiply / multiply by an
+# FP32 / multiply-add, the normalization of a pair, and the divide
+DF_OPS = {"add": 8, "add_f": 7, "mul": 4, "mul_f": 3, "fma": 12, "norm": 3, "div": 36}
 
 
 def df_inst_per_generator(series_len: float) -> float:
@@ -322,23 +325,23 @@ def df_inst_per_generator(series_len: float) -> float:
     double-float operations the kernel uses), counted from the source:
 
     * per rule point: A.w (2 mul, 1 add), |w|^2 (3 mul, 2 add), 1 - |x|^2
-      (2 add, 2 FP32), the binomial series of 1/|x| - 1 (1 mul, 1 mul_f,
-      1 add, 1 add_f, 6 FP32), x_c.(p - z_i) (3 mul, 3 add), the series
-      density (1 add, 2 FP32, series_len - 1 fma), the weight (3 mul),
-      |p - z_i|^2 (2 mul, 3 add, 1 add_f, 3 FP32) and the five sums with
-      their (1 + m) weights (6 add, 3 mul): 367 + 18 (series_len - 1);
+      (2 add, 1 norm, 2 FP32), the binomial series of 1/|x| - 1 (1 mul, 1
+      mul_f, 1 add, 1 add_f, 1 norm, 8 FP32), x_c.(p - z_i) (3 mul, 3 add),
+      the series density (1 add, 1 norm, 2 FP32, series_len - 1 fma), the
+      weight (3 mul, 1 norm), |p - z_i|^2 (2 mul, 3 add, 1 add_f, 1 norm,
+      3 FP32) and the five sums with their (1 + m) weights (6 add, 3 mul):
+      267 + 12 (series_len - 1);
     * per sub-triangle: the offsets' dot products A.b, A.c, b.b, b.c, c.c,
-      x_c.b, x_c.c (21 mul, 14 add), the determinant A.(b x c) (9 mul,
-      5 add), the denominator (2 mul_f, 1 add_f, 3 add), the area (1 div,
-      1 add_f, 1 mul_f, 3 FP32) and the moment's assembly (9 mul, 11 add):
-      713;
-    * per edge: the generator difference from three-part coordinates
-      (~100), the midpoint's offset and projection and x_c.z_i (286), the
-      conversions of the offsets and of the outputs (~40), the centre and
-      term choice of the density table (~70): about 495;
+      x_c.b, x_c.c and the determinant A.(b x c) (30 mul, 19 add, 11 norm),
+      the denominator (2 mul_f, 1 add_f, 3 add, 1 norm), the area (1 div,
+      1 add_f, 1 mul_f, 3 FP32; normalized operations), the sums' and the
+      moment's assembly (9 mul, 13 add, 10 norm): 554;
+    * per edge: the generator difference from three-part coordinates (93),
+      the midpoint's offset and projection (191), x_c.z_i's direction (31),
+      the table's term choice (~70): about 385;
     * 6 edges of 2 sub-triangles of 7 points per generator."""
-    point = 367 + DF_OPS["fma"] * max(series_len - 1.0, 0.0)
-    edge = 2 * (713 + 7 * point) + 495
+    point = 267 + DF_OPS["fma"] * max(series_len - 1.0, 0.0)
+    edge = 2 * (554 + 7 * point) + 385
     return 6.0 * edge
 
 
@@ -350,13 +353,14 @@ def df_inst_per_generator(series_len: float) -> float:
 #      --no-table1 --no-chain --no-cpu-baseline --no-e2e --tuning chunks=1,topo_cell_lanes=16,quad_block=128"
 #   ncu --metrics smsp__inst_executed.sum --clock-control none -k regex:"k_quad|k_topo_warp" -s 6 -c 4
 #       python bench.py $F
-# and likewise for k_topo_warp with 32 lanes per cell.
-QUAD_INST_PER_GENERATOR = 4892967348 / 2621442
-TOPO_INST_PER_CELL = {32: 3335526320 / 2621442, 16: 2225676756 / 2621442}
+# and likewise for k_topo_warp with 32 lanes per cell (that figure predates
+# the merged gather of a cap's bin rows).
+QUAD_INST_PER_GENERATOR = 3782349826 / 2621442
+TOPO_INST_PER_CELL = {32: 3335526320 / 2621442, 16: 2110683409 / 2621442}
 # DRAM bytes of one k_quad launch at N = 163,842 (ncu --set full:
-# dram__bytes_read.sum + dram__bytes_write.sum, 74.30 + 11.15 MB), scaled
+# dram__bytes_read.sum + dram__bytes_write.sum, 74.29 + 11.87 MB), scaled
 # by the number of generators; None once the kernel has changed since
-QUAD_DRAM_BYTES_163842 = 85.444352e6
+QUAD_DRAM_BYTES_163842 = 86.15936e6
 
 
 def quad_traffic_bytes(n: int):

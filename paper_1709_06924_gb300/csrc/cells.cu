@@ -1076,7 +1076,9 @@ __device__ __forceinline__ int gather(const Grid &g, int p, float4 hp, float4 lp
 // holds row k's range [q0, q0 + len); the L lanes of the sub-warp take the
 // rows' generators L at a time in row order, so the candidates arrive in the
 // same order as row by row, with fewer partly filled rounds and the rows'
-// ranges loaded in one round
+// ranges loaded in one round.  (Faster on the small caps of cells with radius
+// hints; the large caps of a random start's first evaluations take longer
+// than row by row.)
 template <int L>
 __device__ __forceinline__ int gather_rows(const Grid &g, int p, float4 hp, float4 lp, int q0, int len, int nr,
                                            float r2acc, int cnt, float *cd, int *cj, int sl, int sbase, unsigned smask,
@@ -1092,10 +1094,15 @@ __device__ __forceinline__ int gather_rows(const Grid &g, int p, float4 hp, floa
     const int pre = inc - len;  // first list position of this lane's row
     for (int base = 0; base < total; base += L) {
         const int f = base + sl;
-        // the row holding position f: the last k < nr with pre_k <= f
+        // the row holding position f: the last k < nr with pre_k <= f (pre is
+        // non-decreasing; a binary search in log2(L) shuffles)
         int k = 0;
-        for (int j = 1; j < nr; ++j)
-            if (__shfl_sync(smask, pre, j, L) <= f) k = j;
+#pragma unroll
+        for (int step = L / 2; step > 0; step >>= 1) {
+            const int c = k + step;
+            const int pc = __shfl_sync(smask, pre, c < L ? c : L - 1, L);
+            if (c < nr && pc <= f) k = c;
+        }
         const int q = __shfl_sync(smask, q0, k, L) + f - __shfl_sync(smask, pre, k, L);
         bool pred = false;
         float d2 = 0.0f;
