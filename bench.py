@@ -326,11 +326,11 @@ def df_inst_per_generator(series_len: float) -> float:
 
     * per rule point: A.w (2 mul, 1 add), |w|^2 (3 mul, 2 add), 1 - |x|^2
       (2 add, 1 norm, 2 FP32), the binomial series of 1/|x| - 1 (1 mul, 1
-      mul_f, 1 add, 1 add_f, 1 norm, 8 FP32), x_c.(p - z_i) (3 mul, 3 add),
-      the series density (1 add, 1 norm, 2 FP32, series_len - 1 fma), the
-      weight (3 mul, 1 norm), |p - z_i|^2 (2 mul, 3 add, 1 add_f, 1 norm,
-      3 FP32) and the five sums with their (1 + m) weights (6 add, 3 mul):
-      267 + 12 (series_len - 1);
+      mul_f, 1 add, 1 add_f, 8 FP32), x_c.(p - z_i) (3 mul, 3 add), the
+      series density (1 add, 1 norm, 2 FP32, series_len - 1 fma), the
+      weight (3 mul), |p - z_i|^2 (2 mul, 3 add, 1 add_f, 1 norm, 3 FP32)
+      and the five sums with their (1 + m) weights (6 add, 3 mul):
+      261 + 12 (series_len - 1);
     * per sub-triangle: the offsets' dot products A.b, A.c, b.b, b.c, c.c,
       x_c.b, x_c.c and the determinant A.(b x c) (30 mul, 19 add, 11 norm),
       the denominator (2 mul_f, 1 add_f, 3 add, 1 norm), the area (1 div,
@@ -340,7 +340,7 @@ def df_inst_per_generator(series_len: float) -> float:
       the midpoint's offset and projection (191), x_c.z_i's direction (31),
       the table's term choice (~70): about 385;
     * 6 edges of 2 sub-triangles of 7 points per generator."""
-    point = 267 + DF_OPS["fma"] * max(series_len - 1.0, 0.0)
+    point = 261 + DF_OPS["fma"] * max(series_len - 1.0, 0.0)
     edge = 2 * (554 + 7 * point) + 385
     return 6.0 * edge
 
@@ -355,7 +355,7 @@ def df_inst_per_generator(series_len: float) -> float:
 #       python bench.py $F
 # and likewise for k_topo_warp with 32 lanes per cell (that figure predates
 # the merged gather of a cap's bin rows).
-QUAD_INST_PER_GENERATOR = 3782349826 / 2621442
+QUAD_INST_PER_GENERATOR = 3741062171 / 2621442
 TOPO_INST_PER_CELL = {32: 3335526320 / 2621442, 16: 2110683409 / 2621442}
 # DRAM bytes of one k_quad launch at N = 163,842 (ncu --set full:
 # dram__bytes_read.sum + dram__bytes_write.sum, 74.29 + 11.87 MB), scaled

@@ -2020,14 +2020,14 @@ __device__ __forceinline__ void tri_df(int kind, df g1, df gam, df3 A, df aA1, d
         const df b1{kQdf[k][0][0], kQdf[k][0][1]}, b2{kQdf[k][1][0], kQdf[k][1][1]}, W{kQdf[k][2][0], kQdf[k][2][1]};
         const df B11{kQdf[k][3][0], kQdf[k][3][1]}, B12{kQdf[k][4][0], kQdf[k][4][1]}, B22{kQdf[k][5][0], kQdf[k][5][1]};
         // unnormalized chains (dfl_*); the sums that cancel (delta, |w|^2 + A.w,
-        // the series argument) and the values used in several products are
-        // normalized
+        // the series argument) are normalized before they are multiplied (m
+        // and the weight come from sums and products of one sign)
         const df Aw = dfl_add(dfl_mul(b1, Ab), dfl_mul(b2, Ac));
         const df ww = dfl_add(dfl_add(dfl_mul(B11, bb), dfl_mul(B12, bc)), dfl_mul(B22, cc));
         const df dl = df_norm(df_neg(dfl_add(dfl_add(aA1, df{2.0f * Aw.hi, 2.0f * Aw.lo}), ww)));
         const df d2 = dfl_mul(dl, dl);
         const float tail = d2.hi * dl.hi * (0.3125f + dl.hi * (0.2734375f + dl.hi * 0.24609375f));
-        const df m = df_norm(dfl_add_f(dfl_add(df{0.5f * dl.hi, 0.5f * dl.lo}, dfl_mul_f(d2, 0.375f)), tail));
+        const df m = dfl_add_f(dfl_add(df{0.5f * dl.hi, 0.5f * dl.lo}, dfl_mul_f(d2, 0.375f)), tail);
         const df xw = dfl_add(dfl_mul(b1, eb), dfl_mul(b2, ec));
         const df eq = dfl_add(xw, dfl_mul(m, dfl_add(eA, xw)));
         df rv;
@@ -2043,7 +2043,7 @@ __device__ __forceinline__ void tri_df(int kind, df g1, df gam, df3 A, df aA1, d
             rv = df{sdf[K - 1].x, sdf[K - 1].y};
             for (int j = K - 2; j >= 0; --j) rv = dfl_fma(rv, v, df{sdf[j].x, sdf[j].y});
         }
-        const df wr = df_norm(dfl_mul(dfl_mul(W, area), rv));
+        const df wr = dfl_mul(dfl_mul(W, area), rv);
         const df wm = dfl_mul(wr, m);
         // |q|^2 = |w|^2 + 2 m (|w|^2 + A.w) + m^2 - m^2 delta
         const df mwa = dfl_mul(m, df_norm(dfl_add(ww, Aw))), msq = dfl_mul(m, m);
